@@ -1,0 +1,513 @@
+"""Plain FP64 CPU oracle of the OctaOctree query and its training step.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import or call
+this module: only tests, the smoke check and the benchmark's CPU-baseline leg
+do.  It shares no code with the CUDA library (no kernels, headers, helpers or
+table generators); both sides receive the same seeded inputs and nothing else.
+
+Every function follows the paper's definitions step by step, in FP64, with
+numpy array primitives (elementwise ops, matmul, bincount) and no blocking,
+fusion or reordering of its own:
+
+  locate            Section 3.4 (the level-l cell that contains x)
+  octa_encode       Section 3.3, Eq. 4 (projection) and Eq. 5 (fold)
+  octa_decode       inverse of Eq. 4/5 (used only by the pins)
+  corner_base_f32   canonical binary32 form of Eq. 4/5 + texel lookup,
+                    which fixes the integer texel coordinates
+  wrap              octahedral edge wrap of the texel grid (Section 3.3: the
+                    map is continuous across the unfolded edges)
+  encode_features   Eq. 10 in the single-cell, bilinear form + Eq. 11
+  mlp_forward       Eq. 13 (decoder; ReLU hidden layers, exp output)
+  residual_loss     Eq. 14 with the Monte-Carlo target of Eq. 3 (M = 1)
+  query_backward    derivative of Eq. 13, then of Eq. 10/11 w.r.t. the table
+  adam_update       Kingma & Ba (2015), with bias correction
+  LossScaler        dynamic loss scaling, Micikevicius et al. (2018)
+  build_tree        seeded octree (SplitMix64, Steele et al. 2014)
+
+Readings where the paper is silent (sign(0) = +1, the wrap rule, eps = 1e-2,
+no decoder biases, Adam hyper-parameters, the tree generator) are listed in
+the design notes.  Every function here is pinned by a CPU test against a
+closed form, a brute-force search, an invariant or finite differences.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+
+
+# ---------------------------------------------------------------------------
+# SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+# generators", OOPSLA 2014), written from its published definition.
+# ---------------------------------------------------------------------------
+
+def splitmix64_next(state):
+    """Advance the state by the golden gamma and return (state, output)."""
+    state = (state + 0x9E3779B97F4A7C15) & MASK64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return state, z ^ (z >> 31)
+
+
+def splitmix64_unit(z):
+    """Top 53 bits of an output as a double in [0, 1)."""
+    return (z >> 11) * (2.0 ** -53)
+
+
+# ---------------------------------------------------------------------------
+# Octree (Section 3.4: a multi-level sparse octree; every non-empty cell of
+# every level stores an octahedral map).
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Tree:
+    first_child: np.ndarray       # [num_nodes] int64, -1 = leaf
+    node_coord: np.ndarray        # [num_nodes][3] int64, integer cell coords at its level
+    node_level: np.ndarray        # [num_nodes] int64
+    level_node_start: np.ndarray  # [K+1]
+    level_texel_base: np.ndarray  # [K+1]
+    map_offset: np.ndarray        # [num_nodes] int64, texel index of texel (0,0)
+    R: list                       # map side per level
+
+    @property
+    def num_levels(self):
+        return len(self.R)
+
+    @property
+    def num_nodes(self):
+        return len(self.first_child)
+
+    @property
+    def num_texels(self):
+        return int(self.level_texel_base[-1])
+
+
+def _finish_tree(first_child, coords, levels, R):
+    K = len(R)
+    first_child = np.asarray(first_child, dtype=np.int64)
+    coords = np.asarray(coords, dtype=np.int64).reshape(-1, 3)
+    levels = np.asarray(levels, dtype=np.int64)
+    n = len(levels)
+    start = np.empty(K + 1, dtype=np.int64)
+    for l in range(K + 1):
+        # first node whose level is >= l (levels are non-decreasing in BFS order)
+        start[l] = int(np.searchsorted(levels, l, side="left"))
+    start[K] = n
+    base = np.zeros(K + 1, dtype=np.int64)
+    for l in range(K):
+        base[l + 1] = base[l] + (start[l + 1] - start[l]) * R[l] * R[l]
+    offs = np.empty(n, dtype=np.int64)
+    for i in range(n):
+        l = levels[i]
+        offs[i] = base[l] + (i - start[l]) * R[l] * R[l]
+    return Tree(first_child, coords, levels, start, base, offs, list(R))
+
+
+def _bfs_tree(decide, max_depth, R):
+    """Breadth-first construction; decide(node_index, depth) -> subdivide?"""
+    coords = [(0, 0, 0)]
+    levels = [0]
+    first_child = []
+    i = 0
+    while i < len(coords):
+        d = levels[i]
+        if d < max_depth and decide(i, d):
+            first_child.append(len(coords))
+            cx, cy, cz = coords[i]
+            for b in range(8):            # child slot b = bx | by<<1 | bz<<2
+                coords.append((2 * cx + (b & 1), 2 * cy + ((b >> 1) & 1), 2 * cz + ((b >> 2) & 1)))
+                levels.append(d + 1)
+        else:
+            first_child.append(-1)
+        i += 1
+    return _finish_tree(first_child, coords, levels, R)
+
+
+def build_tree(seed, max_depth, p_base, R):
+    """Seeded probabilistic octree: a node at depth d < max_depth draws one
+    SplitMix64 uniform (in node order) and splits iff u < p_base^d, where
+    p_base^d is the product of d factors p_base taken left to right from 1."""
+    assert len(R) == max_depth + 1
+    thr = [1.0]
+    for _ in range(max_depth):
+        thr.append(thr[-1] * p_base)
+    st = [seed & MASK64]
+
+    def decide(i, d):
+        st[0], z = splitmix64_next(st[0])
+        return splitmix64_unit(z) < thr[d]
+
+    return _bfs_tree(decide, max_depth, R)
+
+
+def tree_from_flags(flags, max_depth, R):
+    """Hand-written tree: flags[k] decides the k-th node (in node order) whose
+    depth is below max_depth; missing flags mean 'leaf'."""
+    k = [0]
+
+    def decide(i, d):
+        j = k[0]
+        k[0] += 1
+        return j < len(flags) and bool(flags[j])
+
+    return _bfs_tree(decide, max_depth, R)
+
+
+def table_entries(node_counts, sides):
+    """Storage accounting: sum over levels of nodes x (map side)^2."""
+    return int(sum(int(n) * int(s) * int(s) for n, s in zip(node_counts, sides)))
+
+
+# ---------------------------------------------------------------------------
+# Point location (Section 3.4; single containing cell per level)
+# ---------------------------------------------------------------------------
+
+def cell_coords(x, l):
+    """Integer coordinates of the level-l cell containing x (clamped to [0,1];
+    cells are half-open and x = 1 falls in the last cell)."""
+    x64 = np.clip(np.asarray(x, dtype=np.float64), 0.0, 1.0)
+    n = 1 << l
+    return np.minimum(np.floor(x64 * n), n - 1).astype(np.int64)
+
+
+def locate(tree, x):
+    """Node index per level [N][K] by descent from the root; -1 below a leaf."""
+    N = len(x)
+    K = tree.num_levels
+    out = np.full((N, K), -1, dtype=np.int64)
+    node = np.zeros(N, dtype=np.int64)
+    out[:, 0] = 0
+    c_prev = cell_coords(x, 0)
+    for l in range(1, K):
+        c = cell_coords(x, l)
+        b = c - 2 * c_prev
+        slot = b[:, 0] | (b[:, 1] << 1) | (b[:, 2] << 2)
+        alive = node >= 0
+        fc = np.where(alive, tree.first_child[np.maximum(node, 0)], -1)
+        node = np.where(fc >= 0, fc + slot, -1)
+        out[:, l] = node
+        c_prev = c
+    return out
+
+
+def locate_bruteforce(tree, x):
+    """Scan every node of level l for the one whose cell holds x."""
+    N = len(x)
+    K = tree.num_levels
+    out = np.full((N, K), -1, dtype=np.int64)
+    for l in range(K):
+        c = cell_coords(x, l)
+        lo, hi = tree.level_node_start[l], tree.level_node_start[l + 1]
+        for n in range(lo, hi):
+            hit = np.all(c == tree.node_coord[n], axis=1)
+            out[hit, l] = n
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Octahedral map (Section 3.3, Eq. 4 and Eq. 5)
+# ---------------------------------------------------------------------------
+
+def _sgn(a):
+    """sign with sign(0) = +1 (the paper leaves sign(0) open)."""
+    return np.where(a >= 0, 1.0, -1.0)
+
+
+def octa_encode(omega):
+    """Eq. 4 then Eq. 5: omega [N][3] -> u [N][2] in [-1,1]^2 (FP64)."""
+    w = np.asarray(omega, dtype=np.float64)
+    s = np.abs(w[:, 0]) + np.abs(w[:, 1]) + np.abs(w[:, 2])
+    ux = w[:, 0] / s
+    uy = w[:, 1] / s
+    lower = w[:, 2] < 0
+    fx = (1.0 - np.abs(uy)) * _sgn(ux)
+    fy = (1.0 - np.abs(ux)) * _sgn(uy)
+    return np.stack([np.where(lower, fx, ux), np.where(lower, fy, uy)], axis=1)
+
+
+def octa_uv(omega):
+    """Eq. 4/5 remapped to [0,1]^2."""
+    return (octa_encode(omega) + 1.0) * 0.5
+
+
+def octa_decode(u):
+    """Inverse of Eq. 4/5 on [-1,1]^2 -> unit direction."""
+    u = np.asarray(u, dtype=np.float64)
+    ux, uy = u[:, 0], u[:, 1]
+    z = 1.0 - np.abs(ux) - np.abs(uy)
+    lower = z < 0
+    fx = (1.0 - np.abs(uy)) * _sgn(ux)
+    fy = (1.0 - np.abs(ux)) * _sgn(uy)
+    vx = np.where(lower, fx, ux)
+    vy = np.where(lower, fy, uy)
+    v = np.stack([vx, vy, z], axis=1)
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def corner_base_f32(omega32, R):
+    """Integer texel corner (i0, j0) from the canonical binary32 sequence.
+
+    Eq. 4/5 evaluated in IEEE binary32, round-to-nearest-even, one rounding
+    per operation (numpy float32 ufuncs, no fused multiply-add):
+      s = (|wx| + |wy|) + |wz|;  u = (wx / s, wy / s);  fold if wz < 0;
+      uv = u * 0.5 + 0.5;  p = uv * R - 0.5;  (i0, j0) = floor(p).
+    Texel (i, j) is centred at ((i + 1/2)/R, (j + 1/2)/R); i runs along u_x.
+    """
+    f = np.float32
+    w = np.asarray(omega32, dtype=np.float32)
+    ax, ay, az = np.abs(w[:, 0]), np.abs(w[:, 1]), np.abs(w[:, 2])
+    s = (ax + ay) + az
+    ux = w[:, 0] / s
+    uy = w[:, 1] / s
+    one = f(1.0)
+    sx = np.where(ux >= 0, one, -one).astype(np.float32)
+    sy = np.where(uy >= 0, one, -one).astype(np.float32)
+    fx = (one - np.abs(uy)) * sx
+    fy = (one - np.abs(ux)) * sy
+    lower = w[:, 2] < 0
+    ux = np.where(lower, fx, ux).astype(np.float32)
+    uy = np.where(lower, fy, uy).astype(np.float32)
+    px = (ux * f(0.5) + f(0.5)) * f(R) - f(0.5)
+    py = (uy * f(0.5) + f(0.5)) * f(R) - f(0.5)
+    assert px.dtype == np.float32 and py.dtype == np.float32
+    return np.floor(px).astype(np.int64), np.floor(py).astype(np.int64)
+
+
+def wrap(i, j, R):
+    """Octahedral wrap of a corner in [-1, R]^2 onto the R x R grid.
+
+    Across the edge u_x = +-1 the map continues mirrored in u_y, across
+    u_y = +-1 mirrored in u_x (the lower-hemisphere fold of Eq. 5 glues the
+    square's edges this way); applied to i first, then to j.
+    """
+    i = np.asarray(i, dtype=np.int64).copy()
+    j = np.asarray(j, dtype=np.int64).copy()
+    lo = i == -1
+    hi = i == R
+    j = np.where(lo | hi, R - 1 - j, j)
+    i = np.where(lo, 0, np.where(hi, R - 1, i))
+    lo = j == -1
+    hi = j == R
+    i = np.where(lo | hi, R - 1 - i, i)
+    j = np.where(lo, 0, np.where(hi, R - 1, j))
+    return i, j
+
+
+@dataclass
+class Encoding:
+    h: np.ndarray           # [N][K*F] FP64 concatenated features (Eq. 11)
+    node: np.ndarray        # [N][K] node index per level (-1 absent)
+    addr: np.ndarray        # [N][K][4] texel index per corner (-1 absent)
+    weight: np.ndarray      # [N][K][4] FP64 bilinear weights (0 where absent)
+
+
+def encode_features(tree, tables, x, omega):
+    """Per level: containing node, octahedral texel lookup, bilinear blend of
+    the 4 surrounding texels; levels concatenated (Eq. 10 single-cell form,
+    Eq. 11).  An absent cell contributes zero features (the indicator of
+    Eq. 10).  Corner order k = a + 2b for corner (i0 + a, j0 + b)."""
+    T = np.asarray(tables, dtype=np.float64)
+    F = T.shape[1]
+    N = len(x)
+    K = tree.num_levels
+    node = locate(tree, x)
+    uv = octa_uv(np.asarray(omega, dtype=np.float32).astype(np.float64))
+    h = np.zeros((N, K * F))
+    addr = np.full((N, K, 4), -1, dtype=np.int64)
+    wgt = np.zeros((N, K, 4))
+    for l in range(K):
+        R = tree.R[l]
+        i0, j0 = corner_base_f32(omega, R)
+        fx = uv[:, 0] * R - 0.5 - i0
+        fy = uv[:, 1] * R - 0.5 - j0
+        w4 = [(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy]
+        present = node[:, l] >= 0
+        base = np.where(present, tree.map_offset[np.maximum(node[:, l], 0)], 0)
+        for k in range(4):
+            ci, cj = wrap(i0 + (k & 1), j0 + (k >> 1), R)
+            a = base + cj * R + ci
+            addr[:, l, k] = np.where(present, a, -1)
+            wgt[:, l, k] = np.where(present, w4[k], 0.0)
+            h[:, l * F:(l + 1) * F] += wgt[:, l, k][:, None] * T[np.where(present, a, 0)] \
+                * present[:, None]
+    return Encoding(h, node, addr, wgt)
+
+
+# ---------------------------------------------------------------------------
+# Decoder (Section 3.5, Eq. 13): bias-free MLP, ReLU hidden, exp output
+# ---------------------------------------------------------------------------
+
+def mlp_forward(weights, h):
+    """Returns (rgb, pre-activations z_i, layer inputs a_{i-1})."""
+    Ws = [np.asarray(W, dtype=np.float64) for W in weights]
+    a = np.asarray(h, dtype=np.float64)
+    inputs, zs = [], []
+    for i, W in enumerate(Ws):
+        inputs.append(a)
+        z = a @ W.T
+        zs.append(z)
+        if i < len(Ws) - 1:
+            a = np.maximum(z, 0.0)
+    return np.exp(zs[-1]), zs, inputs
+
+
+def query_forward(tree, tables, weights, x, omega):
+    """L_hat(x, omega): encoding then decoder.  Returns (rgb, Encoding)."""
+    enc = encode_features(tree, tables, x, omega)
+    rgb, _, _ = mlp_forward(weights, enc.h)
+    return rgb, enc
+
+
+# ---------------------------------------------------------------------------
+# Training objective (Section 3.2 Eq. 3, Section 3.6 Eq. 14)
+# ---------------------------------------------------------------------------
+
+def residual_loss(Lp, Ls, E, w, eps=1e-2, rhs_grad=True, scale=1.0):
+    """Relative L2 between L_hat(x, omega) and the one-sample RHS
+    T = E + w * L_hat(x', -omega') (Eq. 3 with M = 1, w = f_r |n.omega'| / p).
+    The normaliser sg[L_hat + T + eps] is detached (Eq. 14).  With rhs_grad
+    the gradient also flows into L_hat(x', -omega') through T in the
+    numerator; without it T is detached as in Eq. 14.  The loss averages the
+    per-channel squares over pairs and channels.  Gradients are for
+    scale * loss."""
+    Lp = np.asarray(Lp, dtype=np.float64)
+    Ls = np.asarray(Ls, dtype=np.float64)
+    E = np.asarray(E, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    T = E + w * Ls
+    den = Lp + T + eps
+    r = (Lp - T) / den
+    n = Lp.size
+    loss = float(np.sum(r * r) / n)
+    dLp = scale * 2.0 * r / (n * den)
+    dLs = -scale * 2.0 * r * w / (n * den) if rhs_grad else np.zeros_like(Ls)
+    return loss, dLp, dLs
+
+
+def query_backward(tree, tables, weights, x, omega, d_rgb):
+    """Gradients of sum(d_rgb * L_hat) w.r.t. the table and the weights.
+
+    Decoder: delta_L = d_rgb * exp(z_L); dW_i = delta_i^T a_{i-1};
+    delta_{i-1} = (delta_i W_i) * 1[z_{i-1} > 0]; dh = delta_1 W_1.
+    Encoding: each present corner k of level l receives weight_k * dh_l.
+    """
+    T = np.asarray(tables, dtype=np.float64)
+    F = T.shape[1]
+    K = tree.num_levels
+    enc = encode_features(tree, T, x, omega)
+    rgb, zs, inputs = mlp_forward(weights, enc.h)
+    Ws = [np.asarray(W, dtype=np.float64) for W in weights]
+    delta = np.asarray(d_rgb, dtype=np.float64) * rgb
+    dWs = [None] * len(Ws)
+    for i in range(len(Ws) - 1, -1, -1):
+        dWs[i] = delta.T @ inputs[i]
+        g = delta @ Ws[i]
+        if i > 0:
+            delta = g * (zs[i - 1] > 0)
+        else:
+            dh = g
+    dT = np.zeros_like(T)
+    for l in range(K):
+        for k in range(4):
+            a = enc.addr[:, l, k]
+            ok = a >= 0
+            for f in range(F):
+                dT[:, f] += np.bincount(a[ok], weights=enc.weight[ok, l, k] * dh[ok, l * F + f],
+                                        minlength=len(T))
+    return dT, dWs, rgb
+
+
+def surrogate_loss(tree, tables, weights, pairs_x, pairs_w, x2, w2neg, E, w, D0, T0, eps, rhs_grad):
+    """Eq. 14 with its stop-gradients made explicit: the normaliser (and the
+    target when rhs_grad is off) frozen at their values D0, T0.  Central
+    finite differences of this function equal the analytic gradient."""
+    Lp, _ = query_forward(tree, tables, weights, pairs_x, pairs_w)
+    if rhs_grad:
+        Ls, _ = query_forward(tree, tables, weights, x2, w2neg)
+        T = np.asarray(E, np.float64) + np.asarray(w, np.float64) * Ls
+    else:
+        T = T0
+    r = (Lp - T) / (D0 + eps)
+    return float(np.sum(r * r) / Lp.size)
+
+
+# ---------------------------------------------------------------------------
+# Optimiser (paper silent; Adam, Kingma & Ba 2015) and loss scaling
+# (Micikevicius et al. 2018)
+# ---------------------------------------------------------------------------
+
+def adam_update(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step at step number t >= 1 with bias correction."""
+    p = np.asarray(p, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+class LossScaler:
+    """Dynamic loss scale: gradients are computed for S * loss and divided by
+    S; a non-finite gradient skips the step and halves S; after
+    growth_interval consecutive finite steps S doubles."""
+
+    def __init__(self, scale=2.0 ** 15, growth_interval=2000):
+        self.scale = float(scale)
+        self.growth_interval = growth_interval
+        self.good = 0
+
+    def update(self, finite):
+        """Returns True when the optimiser step must be skipped."""
+        if not finite:
+            self.scale *= 0.5
+            self.good = 0
+            return True
+        self.good += 1
+        if self.good == self.growth_interval:
+            self.scale *= 2.0
+            self.good = 0
+        return False
+
+
+@dataclass
+class TrainState:
+    tables: np.ndarray
+    weights: list
+    m_t: np.ndarray
+    v_t: np.ndarray
+    m_w: list
+    v_w: list
+    step: int = 0
+
+
+def train_step(tree, state, pairs, scaler=None, eps=1e-2, rhs_grad=True,
+               lr_tables=1e-2, lr_mlp=1e-3):
+    """One step: queries at (x, omega) and (x', -omega') (Eq. 2 gives the
+    sign), Eq. 14 loss, backward, unscale, non-finite check, Adam.
+    Returns (loss, grad_norm, skipped)."""
+    N = len(pairs.x)
+    X = np.concatenate([pairs.x, pairs.x2])
+    Om = np.concatenate([pairs.omega, -pairs.omega2])
+    rgb, _ = query_forward(tree, state.tables, state.weights, X, Om)
+    S = scaler.scale if scaler is not None else 1.0
+    loss, dLp, dLs = residual_loss(rgb[:N], rgb[N:], pairs.E, pairs.w, eps, rhs_grad, S)
+    dT, dWs, _ = query_backward(tree, state.tables, state.weights, X, Om,
+                                np.concatenate([dLp, dLs]))
+    dT = dT / S
+    dWs = [d / S for d in dWs]
+    sq = float(np.sum(dT * dT)) + sum(float(np.sum(d * d)) for d in dWs)
+    finite = bool(np.isfinite(sq))
+    skipped = scaler.update(finite) if scaler is not None else not finite
+    if not skipped:
+        state.step += 1
+        t = state.step
+        state.tables, state.m_t, state.v_t = adam_update(state.tables, dT, state.m_t, state.v_t,
+                                                         t, lr_tables)
+        for i in range(len(state.weights)):
+            state.weights[i], state.m_w[i], state.v_w[i] = adam_update(
+                state.weights[i], dWs[i], state.m_w[i], state.v_w[i], t, lr_mlp)
+    return loss, float(np.sqrt(sq)), skipped
