@@ -1,0 +1,348 @@
+"""Benchmark of the OctaOctree training step (and forward) on GB300.
+
+Default workload: the FP32 training step of config [1] -- a depth-6 octree
+(R = 32,32,16,16,8,8,8, F = 8 FP32 features), decoder 56-64-64-3, 262,144
+training pairs = 524,288 queries per step (a primary and a secondary query
+per pair): forward, Eq. 14 residual loss, backward with recompute and
+scatter-add, Adam with dynamic loss scaling.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the step on
+its own GPU (the step shards by independent pairs; weak scaling), timing is
+the max over ranks.  --impl reference times the FP64 CPU oracle on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "OctaOctree query Mq/s fwd and fwd+bwd, BF16 vs FP32, at stated error vs FP64"
+UNIT = "Mq/s"
+FP32_LANES_PER_SM = 128
+SMS = 152
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index  # nvidia-smi -i accepts an index or a GPU UUID
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.th.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample (fresh single-threaded process)
+# ---------------------------------------------------------------------------
+
+def oracle_step_rate(n_pairs, repeats=1):
+    """Mq/s of the FP64 oracle training step on n_pairs pairs of config [1]."""
+    import numpy as np
+    from oracle import octaoctree_oracle as O
+    from paper_2606_08469_gb300 import inputs as I
+    cfg = I.CONFIGS[1]
+    tree = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    tables = I.make_tables(cfg.seed("tables"), tree.num_texels, cfg.F, cfg.sigma)
+    W = I.make_mlp(cfg.seed("mlp"), cfg.widths)
+    pairs = I.training_pairs(cfg.seed("queries"), n_pairs)
+    st = O.TrainState(tables.astype(np.float64), [w.astype(np.float64) for w in W],
+                      np.zeros(tables.shape), np.zeros(tables.shape), [np.zeros(w.shape) for w in W],
+                      [np.zeros(w.shape) for w in W])
+    sc = O.LossScaler()
+    times = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        O.train_step(tree, st, pairs, sc)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def cpu_baseline(n_pairs=65536, repeats=2):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--_oracle-sample",
+                          str(n_pairs), str(repeats)], env=env, capture_output=True, text=True,
+                         timeout=900)
+    if out.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"failed: {out.stderr.strip()[-200:]}"}
+    times = json.loads(out.stdout.strip().splitlines()[-1])
+    t = min(times)
+    return {"value": 2 * n_pairs / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, one training step on {n_pairs} of the 262144 pairs "
+                      f"({2 * n_pairs} queries), best of {repeats}: {t:.2f} s, single thread"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2606_08469_gb300 import build
+    build.build()
+    from paper_2606_08469_gb300 import api
+    from paper_2606_08469_gb300 import inputs as I
+    from paper_2606_08469_gb300 import workloads as WL
+
+    cfg = I.CONFIGS[1]
+    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, device=dev)
+    n_q = 2 * pairs.n
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step.step()
+    barrier()
+
+    # device-resident timed region: per step, flush L2 (outside the events),
+    # then time the whole step and, inside it, the backward kernel
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    try:
+        smi_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        smi_id = str(local)
+    with ClockSampler(smi_id) as clocks:
+        barrier()
+        for k in range(args.steps):
+            flush.zero_()
+            a, b, c, d = ev[k]
+            a.record(stream)
+            step.forward()
+            step.loss_and_grad()
+            c.record(stream)
+            step.backward()
+            d.record(stream)
+            step.optimizer()
+            b.record(stream)
+        barrier()
+    step_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    bwd_ms = [e[2].elapsed_time(e[3]) for e in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    launches = 5 * args.steps  # fwd, residual_loss, bwd, adam norm, adam update
+
+    # forward-only rate (same queries), L2 flushed between launches
+    fwd_ms = []
+    for _ in range(max(3, args.steps)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step.forward()
+        b.record(stream)
+        fwd_ms.append((a, b))
+    torch.cuda.synchronize(dev)
+    fwd_ms = [a.elapsed_time(b) for a, b in fwd_ms]
+
+    # end to end through the public API: pinned host inputs copied in every
+    # step, the loss read back every step
+    host = {k: torch.from_numpy(v).pin_memory() for k, v in
+            {"X": step.X.cpu().numpy(), "Om": step.Om.cpu().numpy(), "E": step.E[0].cpu().numpy(),
+             "w": step.w[0].cpu().numpy()}.items()}
+    loss_host = torch.empty(1, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step.X.copy_(host["X"], non_blocking=True)
+        step.Om.copy_(host["Om"], non_blocking=True)
+        step.E[0].copy_(host["E"], non_blocking=True)
+        step.w[0].copy_(host["w"], non_blocking=True)
+        step.step()
+        loss_host.copy_(step.loss, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank == 0:
+        peaks, src = _peaks()
+        sc = api.read_scaler(step.scaler)
+        # dominant kernel: the FP32 backward (recomputed forward + backward),
+        # bound by FP32 FFMA issue; algorithmic flops at the real widths
+        W = cfg.widths
+        fwd_flop = 2 * sum(a * b for a, b in zip(W[:-1], W[1:]))
+        bwd_flop = 3 * fwd_flop
+        bwd_s = statistics.mean(bwd_ms) / 1e3
+        achieved = bwd_flop * n_q / bwd_s / 1e12
+        clk = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+        out = {
+            "metric": METRIC,
+            "value": round(world * n_q * args.steps / (total_ms / 1e3) / 1e6, 3),
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic (seeded octree, features, MLP, surface samples; no scene assets)",
+            "config": {"workload": "config[1] FP32 training step: depth-6 seeded octree "
+                                   f"({tree.num_nodes} nodes, R 32..8, F=8 FP32), decoder 56-64-64-3, "
+                                   f"262144 pairs = {n_q} queries per step (fwd, Eq.14 loss, bwd, Adam)",
+                       "l2": "flushed between timed steps (256 MB write outside the events)",
+                       "parallelism": f"replicas x{world}"},
+            "fwd_only": {"value": round(world * n_q / (statistics.mean(fwd_ms) / 1e3) / 1e6, 3),
+                         "unit": UNIT, "ms": round(statistics.mean(fwd_ms), 4)},
+            "loss": float(step.loss.item()),
+            "grad_norm": float(sc.grad_norm),
+            "roofline": {"bound": "alu", "kernel": "f32 engine backward (recompute + bwd + scatter)",
+                         "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {clk:.0f} MHz "
+                                        f"({src} sm_max_mhz)",
+                         "bwd_ms": round(statistics.mean(bwd_ms), 4)},
+            "e2e": {"value": round(world * n_q * args.steps / (e2e_ms / 1e3) / 1e6, 3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+        }
+        out["cpu_baseline"] = cpu_baseline() if not args.no_cpu else None
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_pairs = 8192
+    times = oracle_step_rate(n_pairs, repeats=args.warmup + args.steps)
+    t = sum(times[args.warmup:])
+    v = 2 * n_pairs * args.steps / t / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * t / args.steps, 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "config[1] training step, FP64 oracle on a bounded sample of "
+                                  f"{n_pairs} of the 262144 pairs per step"},
+           "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{n_pairs} pairs ({2 * n_pairs} queries) per step"},
+           "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--_oracle-sample":
+        print(json.dumps(oracle_step_rate(int(sys.argv[2]), int(sys.argv[3]))))
+        return
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,238 @@
+/*
+ * octaoctree.h -- C ABI of the GB300 (sm_103a) OctaOctree query and its
+ * training step.
+ *
+ * The method (arxiv 2606.08469): outgoing radiance L(x, w) is read from a
+ * multi-level sparse octree whose every non-empty cell stores an octahedral
+ * feature map (Section 3.4).  A query finds, at every level, the node that
+ * contains x, maps w onto the octahedral square (Section 3.3, Eq. 4 and
+ * Eq. 5), blends the four surrounding texels of that node's map bilinearly,
+ * concatenates the levels (Eq. 11) and decodes the features with a small MLP
+ * (Section 3.5, Eq. 13).  Training minimises the relative-L2 residual between
+ * the query and its emission-plus-secondary-query estimate (Eq. 3, Eq. 14).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an int status: OCTA_OK or a negative OCTA_E* code.
+ *    No exception or abort crosses the ABI.  octa_last_error() returns a
+ *    thread-local message for the last failing call on the calling thread.
+ *  - Pointers documented as "device" are CUDA device pointers owned by the
+ *    caller; the library never allocates, frees, synchronises or prints.
+ *    GPU work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and runs asynchronously: results are valid once the stream
+ *    reaches that point.
+ *  - Pointers documented as "host" are read during the call only.
+ *  - Scratch space comes from a caller-provided device workspace of at least
+ *    octa_workspace_bytes(op, n) bytes, 256-byte aligned.  Two calls that
+ *    share a workspace must not overlap on the GPU.
+ *  - Device-detected malformed input (a child index or texel range outside
+ *    the arrays) is never dereferenced: the level is treated as absent and
+ *    the OCTA_STATUS_* bit is OR-ed into *status (device int32, nullable).
+ */
+#ifndef OCTAOCTREE_H
+#define OCTAOCTREE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define OCTA_OK 0
+#define OCTA_EINVAL (-1)      /* bad argument: NULL, shape, dtype, alignment  */
+#define OCTA_ERANGE (-2)      /* size outside the supported range             */
+#define OCTA_ECUDA (-3)       /* CUDA launch error; text in octa_last_error() */
+#define OCTA_ETIMEOUT (-4)    /* a bounded device wait gave up                */
+#define OCTA_EUNSUPPORTED (-6)/* valid but not built (e.g. a width/dtype mix) */
+
+/* bits OR-ed into the device status word */
+#define OCTA_STATUS_BAD_CHILD 1   /* first_child[n] + 7 >= num_nodes          */
+#define OCTA_STATUS_BAD_MAP 2     /* map_offset[n] + R^2 > num_texels         */
+#define OCTA_STATUS_TIMEOUT 4     /* bounded grid barrier gave up             */
+
+/* ---- limits ------------------------------------------------------------ */
+#define OCTA_MAX_LEVELS 16
+#define OCTA_MAX_LAYERS 6         /* weight matrices per MLP                  */
+#define OCTA_MAX_SCENES 16
+#define OCTA_MAX_GROUPS 16        /* Adam parameter groups per call           */
+
+/* ---- element types ----------------------------------------------------- */
+#define OCTA_F32 0
+#define OCTA_F16 1
+#define OCTA_BF16 2
+
+/* ---- octree ------------------------------------------------------------ */
+/* Level-ordered flat octree.  Level l holds nodes
+ * [level_node_start[l], level_node_start[l+1]); the 8 children of node n are
+ * first_child[n] + b, b = bx | by<<1 | bz<<2 (Morton order), or
+ * first_child[n] = -1 for a leaf.  Node n of level l owns the R[l] x R[l]
+ * texels starting at map_offset[n]; texel (i, j) of that map (i along u_x)
+ * is texel index map_offset[n] + j*R[l] + i of the feature table
+ * [num_texels][F].  level_texel_base[l] is the first texel of level l.   */
+typedef struct octa_tree_desc {
+  int32_t num_levels;                          /* K = max_depth + 1        */
+  int32_t num_nodes;
+  int64_t num_texels;
+  int32_t R[OCTA_MAX_LEVELS];                  /* map side per level       */
+  int32_t level_node_start[OCTA_MAX_LEVELS + 1];
+  int64_t level_texel_base[OCTA_MAX_LEVELS + 1];
+} octa_tree_desc;
+
+/* octree_build -- seeded adaptive octree over [0,1]^3 (host only).
+ * Nodes are created breadth first.  A node at depth d < max_depth draws one
+ * SplitMix64 uniform u (Steele et al. 2014; state seeded with `seed`, one
+ * draw per such node in node order, u = (z >> 11) * 2^-53) and splits into 8
+ * children iff u < p_base^d (p_base^d = product of d factors, from 1.0).
+ * The paper builds its octree from the scene geometry (Section 3.4, Section
+ * 4.1); this seeded generator stands in for it.
+ * Two-call sizing: with first_child == NULL only *desc is filled; then call
+ * again with caller-owned host arrays first_child[num_nodes],
+ * node_coord[num_nodes][3] (integer cell coordinates at the node's level)
+ * and map_offset[num_nodes].
+ * R: host [max_depth+1], each 2..4096.  max_depth 0..OCTA_MAX_LEVELS-1.
+ * Errors: OCTA_EINVAL (NULL desc/R, p_base outside [0,1]), OCTA_ERANGE
+ * (depth, R, more than 2^31-1 nodes or texels).                            */
+int octree_build(uint64_t seed, int32_t max_depth, double p_base, const int32_t* R,
+                 octa_tree_desc* desc, int32_t* first_child, int32_t* node_coord,
+                 int32_t* map_offset);
+
+/* octree_from_flags -- same output for a hand-written tree: the k-th node (in
+ * breadth-first order) whose depth is below max_depth splits iff
+ * k < n_flags && flags[k] != 0.  flags: host, may be NULL when n_flags == 0.*/
+int octree_from_flags(const uint8_t* flags, int64_t n_flags, int32_t max_depth,
+                      const int32_t* R, octa_tree_desc* desc, int32_t* first_child,
+                      int32_t* node_coord, int32_t* map_offset);
+
+/* ---- scene: one octree, its feature table and its decoder -------------- */
+typedef struct octa_scene {
+  const int32_t* first_child;  /* device [num_nodes]                       */
+  const int32_t* map_offset;   /* device [num_nodes]                       */
+  const void* tables;          /* device [num_texels][F], table_dtype      */
+  const void* weights;         /* device: W_1..W_L back to back, each      */
+                               /* row-major [widths[i+1]][widths[i]]       */
+  int32_t num_levels;          /* K (1..OCTA_MAX_LEVELS)                   */
+  int32_t num_nodes;
+  int64_t num_texels;          /* < 2^31                                   */
+  int32_t R[OCTA_MAX_LEVELS];  /* map side per level (2..4096)             */
+  int32_t F;                   /* features per texel: 4 or 8               */
+  int32_t table_dtype;         /* OCTA_F32 or OCTA_F16                     */
+  int32_t weight_dtype;        /* OCTA_F32 or OCTA_BF16                    */
+  int32_t n_layers;            /* weight matrices L (2..OCTA_MAX_LAYERS)   */
+  int32_t widths[OCTA_MAX_LAYERS + 1]; /* widths[0] = K*F, widths[L] = 3   */
+} octa_scene;
+
+/* Queries: scene s answers queries [scene_start[s], scene_start[s+1]).   */
+typedef struct octa_queries {
+  const float* x;              /* device [n][3], position (clamped to [0,1])*/
+  const float* omega;          /* device [n][3], direction (any length > 0) */
+  int64_t n;
+  int64_t scene_start[OCTA_MAX_SCENES + 1];
+} octa_queries;
+
+/* octa_encode -- the OctaOctree encoding alone (Eq. 10 single-cell bilinear
+ * form, Eq. 11): features [n][W] with W = sum over scenes of nothing: each
+ * query writes its own scene's K*F features into a row of row_stride
+ * elements (row_stride >= K*F of every scene; unused tail left untouched).
+ * feat_dtype OCTA_F32 or OCTA_BF16.  Absent levels write zeros.
+ * node_idx: device [n][K_max] int32 or NULL (K_max = largest K of the
+ * scenes, unused columns -1); texel_addr: device [n][K_max][4] int32 or NULL,
+ * corner order k = a + 2b for corner (i0+a, j0+b), -1 where absent.      */
+int octa_encode(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
+                void* features, int32_t feat_dtype, int64_t row_stride,
+                int32_t* node_idx, int32_t* texel_addr, int32_t* status, void* stream);
+
+/* octa_query_fwd -- L_hat(x, omega) = exp(W_L relu(... relu(W_1 h))) per
+ * query (Eq. 13), h the encoding above.  rgb: device [n][3] float32.
+ * node_idx / texel_addr / status as in octa_encode (nullable).
+ * The FP32 path (weight_dtype F32) runs on the CUDA cores in FP32; the
+ * BF16 path runs the decoder on the tcgen05 tensor cores (BF16 operands,
+ * FP32 accumulation in tensor memory).                                     */
+int octa_query_fwd(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
+                   float* rgb, int32_t* node_idx, int32_t* texel_addr, int32_t* status,
+                   void* stream);
+
+/* Gradient buffers of one scene: FP32, same layouts as tables / weights.  */
+typedef struct octa_scene_grads {
+  float* d_tables;             /* device [num_texels][F], 16-byte aligned  */
+  float* d_weights;            /* device, layout of octa_scene.weights     */
+} octa_scene_grads;
+
+/* octa_query_bwd -- gradients of sum_q d_rgb[q] . L_hat(q) with respect to
+ * the feature tables and the decoder weights.  Recomputes the forward pass
+ * (no activations are kept between calls), back-propagates through the
+ * decoder (exp, ReLU masks 1[z > 0]) and scatter-adds weight_k * dh_l into
+ * the four texels each present level read.  ACCUMULATES (+=) into
+ * grads[s].d_tables / d_weights, which the caller zeroes (adam_step zeroes
+ * them after each update).  d_rgb: device [n][3] float32.                 */
+int octa_query_bwd(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
+                   const float* d_rgb, const octa_scene_grads* grads, int32_t* status,
+                   void* stream);
+
+/* ---- loss scaler / optimiser state (device resident) ------------------- */
+typedef struct octa_scaler {
+  float scale;                 /* current loss scale S                     */
+  float inv_scale_used;        /* 1/S applied to the last step's gradients */
+  int32_t good_steps;          /* consecutive finite steps since a change  */
+  int32_t growth_interval;     /* double S after this many finite steps;   */
+                               /* 0 = static scale                         */
+  int32_t step;                /* Adam step count t of applied steps       */
+  int32_t skipped;             /* 1 if the last step was skipped           */
+  int32_t n_skipped;           /* total skipped steps                      */
+  int32_t reserved;
+  double grad_norm;            /* ||g / S||_2 of the last step (FP64)      */
+  double loss;                 /* free slot for residual_loss's output     */
+} octa_scaler;
+
+/* residual_loss -- Eq. 14 with the one-sample target of Eq. 3:
+ * T = E + w * L_s,  r = (L_p - T) / (L_p + T + eps),
+ * loss = sum(r^2) / (3 n_pairs)  (FP64 reduction, deterministic),
+ * dL_p = S * 2 r / (3 n (L_p + T + eps)), and, if rhs_grad,
+ * dL_s = -S * 2 r w / (3 n (L_p + T + eps)) (gradient through the target's
+ * secondary query; the normaliser stays detached).  S = scaler->scale or 1
+ * when scaler is NULL.  All arrays device [n_pairs][3] float32; dL_s may be
+ * NULL when rhs_grad == 0 (else it is written with zeros).
+ * loss_dev: device double.  Workspace: octa_workspace_bytes(OCTA_OP_LOSS, n).*/
+int residual_loss(const float* L_p, const float* L_s, const float* E, const float* w,
+                  int64_t n_pairs, float eps, int32_t rhs_grad, const octa_scaler* scaler,
+                  double* loss_dev, float* dL_p, float* dL_s, void* workspace,
+                  size_t workspace_bytes, void* stream);
+
+/* One parameter group of adam_step (all device pointers, n elements).     */
+typedef struct octa_param_group {
+  float* param;                /* FP32 master copy                          */
+  float* grad;                 /* FP32 gradient of S * loss; zeroed after   */
+  float* m;                    /* first moment                              */
+  float* v;                    /* second moment                             */
+  void* work;                  /* low-precision working copy or NULL        */
+  int32_t work_dtype;          /* OCTA_F16 or OCTA_BF16                     */
+  float lr;
+  int64_t n;
+} octa_param_group;
+
+typedef struct octa_adam_cfg {
+  float beta1, beta2, eps;     /* Kingma & Ba defaults 0.9, 0.999, 1e-8     */
+} octa_adam_cfg;
+
+/* adam_step -- unscale by 1/S, FP64 gradient norm and non-finite check,
+ * then either skip the step and halve S (non-finite; scaler->skipped = 1) or
+ * apply Adam with bias correction at t = ++scaler->step and, after
+ * growth_interval consecutive finite steps, double S (Micikevicius et al.
+ * 2018).  Writes the working copies, zeroes every grad.  All decisions are
+ * taken on the device (no host sync).  scaler: device, initialised by the
+ * caller.  Workspace: octa_workspace_bytes(OCTA_OP_ADAM, total elements).  */
+int adam_step(const octa_param_group* groups, int32_t n_groups, const octa_adam_cfg* cfg,
+              octa_scaler* scaler, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---- workspace sizing, errors ------------------------------------------ */
+#define OCTA_OP_LOSS 1
+#define OCTA_OP_ADAM 2
+size_t octa_workspace_bytes(int32_t op, int64_t n);
+
+const char* octa_last_error(void);
+int32_t octa_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OCTAOCTREE_H */

@@ -1,0 +1,169 @@
+"""ctypes binding of include/octaoctree.h (argument marshalling only).
+
+Loads the in-tree shared library built by paper_2606_08469_gb300.build and
+declares every exported entry point with the header's names and signatures.
+There is no fallback: a missing library raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+OCTA_OK = 0
+OCTA_EINVAL = -1
+OCTA_ERANGE = -2
+OCTA_ECUDA = -3
+OCTA_ETIMEOUT = -4
+OCTA_EUNSUPPORTED = -6
+
+OCTA_STATUS_BAD_CHILD = 1
+OCTA_STATUS_BAD_MAP = 2
+OCTA_STATUS_TIMEOUT = 4
+
+OCTA_MAX_LEVELS = 16
+OCTA_MAX_LAYERS = 6
+OCTA_MAX_SCENES = 16
+OCTA_MAX_GROUPS = 16
+
+OCTA_F32 = 0
+OCTA_F16 = 1
+OCTA_BF16 = 2
+
+OCTA_OP_LOSS = 1
+OCTA_OP_ADAM = 2
+
+
+class octa_tree_desc(C.Structure):
+    _fields_ = [
+        ("num_levels", C.c_int32),
+        ("num_nodes", C.c_int32),
+        ("num_texels", C.c_int64),
+        ("R", C.c_int32 * OCTA_MAX_LEVELS),
+        ("level_node_start", C.c_int32 * (OCTA_MAX_LEVELS + 1)),
+        ("level_texel_base", C.c_int64 * (OCTA_MAX_LEVELS + 1)),
+    ]
+
+
+class octa_scene(C.Structure):
+    _fields_ = [
+        ("first_child", C.c_void_p),
+        ("map_offset", C.c_void_p),
+        ("tables", C.c_void_p),
+        ("weights", C.c_void_p),
+        ("num_levels", C.c_int32),
+        ("num_nodes", C.c_int32),
+        ("num_texels", C.c_int64),
+        ("R", C.c_int32 * OCTA_MAX_LEVELS),
+        ("F", C.c_int32),
+        ("table_dtype", C.c_int32),
+        ("weight_dtype", C.c_int32),
+        ("n_layers", C.c_int32),
+        ("widths", C.c_int32 * (OCTA_MAX_LAYERS + 1)),
+    ]
+
+
+class octa_queries(C.Structure):
+    _fields_ = [
+        ("x", C.c_void_p),
+        ("omega", C.c_void_p),
+        ("n", C.c_int64),
+        ("scene_start", C.c_int64 * (OCTA_MAX_SCENES + 1)),
+    ]
+
+
+class octa_scene_grads(C.Structure):
+    _fields_ = [("d_tables", C.c_void_p), ("d_weights", C.c_void_p)]
+
+
+class octa_scaler(C.Structure):
+    _fields_ = [
+        ("scale", C.c_float),
+        ("inv_scale_used", C.c_float),
+        ("good_steps", C.c_int32),
+        ("growth_interval", C.c_int32),
+        ("step", C.c_int32),
+        ("skipped", C.c_int32),
+        ("n_skipped", C.c_int32),
+        ("reserved", C.c_int32),
+        ("grad_norm", C.c_double),
+        ("loss", C.c_double),
+    ]
+
+
+class octa_param_group(C.Structure):
+    _fields_ = [
+        ("param", C.c_void_p),
+        ("grad", C.c_void_p),
+        ("m", C.c_void_p),
+        ("v", C.c_void_p),
+        ("work", C.c_void_p),
+        ("work_dtype", C.c_int32),
+        ("lr", C.c_float),
+        ("n", C.c_int64),
+    ]
+
+
+class octa_adam_cfg(C.Structure):
+    _fields_ = [("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
+
+
+# Every symbol the header declares, with its ctypes signature.
+_P = C.c_void_p
+_SIGNATURES = {
+    "octree_build": (C.c_int, [C.c_uint64, C.c_int32, C.c_double, _P, C.POINTER(octa_tree_desc),
+                               _P, _P, _P]),
+    "octree_from_flags": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.POINTER(octa_tree_desc),
+                                    _P, _P, _P]),
+    "octa_encode": (C.c_int, [C.POINTER(octa_scene), C.c_int32, C.POINTER(octa_queries), _P,
+                              C.c_int32, C.c_int64, _P, _P, _P, _P]),
+    "octa_query_fwd": (C.c_int, [C.POINTER(octa_scene), C.c_int32, C.POINTER(octa_queries), _P,
+                                 _P, _P, _P, _P]),
+    "octa_query_bwd": (C.c_int, [C.POINTER(octa_scene), C.c_int32, C.POINTER(octa_queries), _P,
+                                 C.POINTER(octa_scene_grads), _P, _P]),
+    "residual_loss": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_float, C.c_int32, _P, _P, _P, _P,
+                                _P, C.c_size_t, _P]),
+    "adam_step": (C.c_int, [C.POINTER(octa_param_group), C.c_int32, C.POINTER(octa_adam_cfg), _P,
+                            _P, C.c_size_t, _P]),
+    "octa_workspace_bytes": (C.c_size_t, [C.c_int32, C.c_int64]),
+    "octa_last_error": (C.c_char_p, []),
+    "octa_abi_version": (C.c_int32, []),
+}
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(path=None):
+    """Load (once) and return the ctypes handle of the CUDA library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(
+            f"OctaOctree CUDA library not built ({path}); run paper_2606_08469_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class OctaError(RuntimeError):
+    def __init__(self, code, where):
+        msg = load().octa_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with status {code}: {msg}")
+        self.code = code
+
+
+def check(code, where):
+    if code != OCTA_OK:
+        raise OctaError(code, where)
+    return code

@@ -1,0 +1,315 @@
+"""Thin torch-facing binding of the C ABI: argument marshalling only.
+
+Every computation runs in the CUDA library; this module only turns torch
+tensors (device memory) and the current torch stream into the ABI's plain
+pointers, sizes and structs.  Function names follow the header.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_DT = {torch.float32: L.OCTA_F32, torch.float16: L.OCTA_F16, torch.bfloat16: L.OCTA_BF16}
+
+
+def _lib():
+    return L.load()
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# octree (host)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class HostTree:
+    desc: L.octa_tree_desc
+    first_child: np.ndarray   # int32 [num_nodes]
+    node_coord: np.ndarray    # int32 [num_nodes][3]
+    map_offset: np.ndarray    # int32 [num_nodes]
+
+    @property
+    def num_levels(self):
+        return self.desc.num_levels
+
+    @property
+    def num_nodes(self):
+        return self.desc.num_nodes
+
+    @property
+    def num_texels(self):
+        return self.desc.num_texels
+
+    @property
+    def R(self):
+        return [self.desc.R[l] for l in range(self.num_levels)]
+
+    @property
+    def level_node_start(self):
+        return np.array([self.desc.level_node_start[l] for l in range(self.num_levels + 1)])
+
+    @property
+    def level_texel_base(self):
+        return np.array([self.desc.level_texel_base[l] for l in range(self.num_levels + 1)])
+
+
+def _two_call(fn, *head):
+    desc = L.octa_tree_desc()
+    L.check(fn(*head, C.byref(desc), None, None, None), fn.__name__)
+    n = desc.num_nodes
+    fc = np.empty(n, np.int32)
+    nc = np.empty((n, 3), np.int32)
+    mo = np.empty(n, np.int32)
+    L.check(fn(*head, C.byref(desc), fc.ctypes.data_as(C.c_void_p), nc.ctypes.data_as(C.c_void_p),
+               mo.ctypes.data_as(C.c_void_p)), fn.__name__)
+    return HostTree(desc, fc, nc, mo)
+
+
+def octree_build(seed, max_depth, p_base, R):
+    Ra = np.ascontiguousarray(R, dtype=np.int32)
+    assert len(Ra) == max_depth + 1
+    return _two_call(_lib().octree_build, C.c_uint64(seed), C.c_int32(max_depth),
+                     C.c_double(p_base), Ra.ctypes.data_as(C.c_void_p))
+
+
+def octree_from_flags(flags, max_depth, R):
+    fl = np.ascontiguousarray(flags, dtype=np.uint8)
+    Ra = np.ascontiguousarray(R, dtype=np.int32)
+    fp = fl.ctypes.data_as(C.c_void_p) if len(fl) else None
+    return _two_call(_lib().octree_from_flags, fp, C.c_int64(len(fl)), C.c_int32(max_depth),
+                     Ra.ctypes.data_as(C.c_void_p))
+
+
+# ---------------------------------------------------------------------------
+# scenes and queries (device)
+# ---------------------------------------------------------------------------
+
+class Scene:
+    """One octree with its feature table and decoder on the device.
+
+    tables: tensor [num_texels][F] float32/float16; weights: list of tensors
+    [out][in] (float32 or bfloat16), stored back to back.
+    """
+
+    def __init__(self, tree: HostTree, tables, weights, device="cuda"):
+        self.tree = tree
+        self.device = torch.device(device)
+        self.first_child = torch.from_numpy(tree.first_child).to(self.device)
+        self.map_offset = torch.from_numpy(tree.map_offset).to(self.device)
+        self.tables = tables
+        self.widths = [int(weights[0].shape[1])] + [int(W.shape[0]) for W in weights]
+        self.weights = torch.cat([W.reshape(-1) for W in weights]).contiguous()
+        self.set_tables(tables)
+
+    def set_tables(self, tables):
+        assert tables.is_contiguous() and tables.shape[0] == self.tree.num_texels
+        self.tables = tables
+
+    def set_weights_flat(self, flat):
+        assert flat.numel() == self.weights.numel()
+        self.weights = flat
+
+    @property
+    def F(self):
+        return int(self.tables.shape[1])
+
+    def weight_slices(self):
+        out, off = [], 0
+        for a, b in zip(self.widths[:-1], self.widths[1:]):
+            out.append((off, b, a))
+            off += a * b
+        return out
+
+    def as_c(self):
+        s = L.octa_scene()
+        s.first_child = self.first_child.data_ptr()
+        s.map_offset = self.map_offset.data_ptr()
+        s.tables = self.tables.data_ptr()
+        s.weights = self.weights.data_ptr()
+        s.num_levels = self.tree.num_levels
+        s.num_nodes = self.tree.num_nodes
+        s.num_texels = self.tree.num_texels
+        for l, r in enumerate(self.tree.R):
+            s.R[l] = r
+        s.F = self.F
+        s.table_dtype = _DT[self.tables.dtype]
+        s.weight_dtype = _DT[self.weights.dtype]
+        s.n_layers = len(self.widths) - 1
+        for i, w in enumerate(self.widths):
+            s.widths[i] = w
+        return s
+
+
+def _scene_array(scenes):
+    if isinstance(scenes, Scene):
+        scenes = [scenes]
+    arr = (L.octa_scene * len(scenes))(*[s.as_c() for s in scenes])
+    return arr, len(scenes)
+
+
+def _queries(x, omega, counts):
+    q = L.octa_queries()
+    n = int(x.shape[0])
+    q.x = x.data_ptr() if n else None
+    q.omega = omega.data_ptr() if n else None
+    q.n = n
+    counts = [n] if counts is None else list(counts)
+    assert sum(counts) == n
+    acc = 0
+    q.scene_start[0] = 0
+    for i, c in enumerate(counts):
+        acc += c
+        q.scene_start[i + 1] = acc
+    return q
+
+
+def octa_encode(scenes, x, omega, counts=None, feat_dtype=torch.float32, want_nodes=False,
+                want_addr=False, status=None, stream=None):
+    arr, ns = _scene_array(scenes)
+    sl = [scenes] if isinstance(scenes, Scene) else scenes
+    kmax = max(s.tree.num_levels for s in sl)
+    W = max(s.tree.num_levels * s.F for s in sl)
+    n = x.shape[0]
+    dev = x.device
+    feat = torch.zeros((n, W), dtype=feat_dtype, device=dev)
+    nodes = torch.empty((n, kmax), dtype=torch.int32, device=dev) if want_nodes else None
+    addr = torch.empty((n, kmax, 4), dtype=torch.int32, device=dev) if want_addr else None
+    q = _queries(x, omega, counts)
+    L.check(_lib().octa_encode(arr, ns, C.byref(q), _ptr(feat), _DT[feat_dtype], W, _ptr(nodes),
+                               _ptr(addr), _ptr(status), _stream(stream)), "octa_encode")
+    return feat, nodes, addr
+
+
+def octa_query_fwd(scenes, x, omega, counts=None, want_nodes=False, want_addr=False, rgb=None,
+                   status=None, stream=None):
+    arr, ns = _scene_array(scenes)
+    sl = [scenes] if isinstance(scenes, Scene) else scenes
+    kmax = max(s.tree.num_levels for s in sl)
+    n = x.shape[0]
+    dev = x.device
+    if rgb is None:
+        rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    nodes = torch.empty((n, kmax), dtype=torch.int32, device=dev) if want_nodes else None
+    addr = torch.empty((n, kmax, 4), dtype=torch.int32, device=dev) if want_addr else None
+    q = _queries(x, omega, counts)
+    L.check(_lib().octa_query_fwd(arr, ns, C.byref(q), _ptr(rgb), _ptr(nodes), _ptr(addr),
+                                  _ptr(status), _stream(stream)), "octa_query_fwd")
+    return rgb, nodes, addr
+
+
+def octa_query_bwd(scenes, x, omega, d_rgb, grads, counts=None, status=None, stream=None):
+    """grads: list of (d_tables fp32, d_weights fp32) per scene; accumulated."""
+    arr, ns = _scene_array(scenes)
+    g = (L.octa_scene_grads * ns)(*[L.octa_scene_grads(dt.data_ptr(), dw.data_ptr())
+                                    for dt, dw in grads])
+    q = _queries(x, omega, counts)
+    L.check(_lib().octa_query_bwd(arr, ns, C.byref(q), _ptr(d_rgb), g, _ptr(status),
+                                  _stream(stream)), "octa_query_bwd")
+
+
+# ---------------------------------------------------------------------------
+# loss, optimiser
+# ---------------------------------------------------------------------------
+
+SCALER_BYTES = C.sizeof(L.octa_scaler)
+
+
+def make_scaler(scale=2.0 ** 15, growth_interval=2000, device="cuda"):
+    s = L.octa_scaler()
+    s.scale = scale
+    s.inv_scale_used = 1.0 / scale
+    s.growth_interval = growth_interval
+    raw = bytes(s)
+    return torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+
+
+def read_scaler(buf):
+    raw = bytes(buf.cpu().numpy().tobytes())
+    return L.octa_scaler.from_buffer_copy(raw)
+
+
+def workspace(op, n, device="cuda"):
+    nbytes = _lib().octa_workspace_bytes(op, n)
+    return torch.zeros(nbytes, dtype=torch.uint8, device=device)
+
+
+def residual_loss(Lp, Ls, E, w, dLp, dLs, loss_out, ws, eps=1e-2, rhs_grad=True, scaler=None,
+                  stream=None):
+    n = int(Lp.shape[0])
+    L.check(_lib().residual_loss(_ptr(Lp), _ptr(Ls), _ptr(E), _ptr(w), n, C.c_float(eps),
+                                 int(bool(rhs_grad)), _ptr(scaler), _ptr(loss_out), _ptr(dLp),
+                                 _ptr(dLs), _ptr(ws), ws.numel(), _stream(stream)),
+            "residual_loss")
+
+
+@dataclass
+class ParamGroup:
+    param: torch.Tensor
+    grad: torch.Tensor
+    m: torch.Tensor
+    v: torch.Tensor
+    lr: float
+    work: torch.Tensor | None = None
+
+    def as_c(self):
+        g = L.octa_param_group()
+        g.param = self.param.data_ptr()
+        g.grad = self.grad.data_ptr()
+        g.m = self.m.data_ptr()
+        g.v = self.v.data_ptr()
+        g.work = self.work.data_ptr() if self.work is not None else None
+        g.work_dtype = _DT[self.work.dtype] if self.work is not None else L.OCTA_F16
+        g.lr = self.lr
+        g.n = self.param.numel()
+        return g
+
+
+def adam_step(groups, scaler, ws, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    arr = (L.octa_param_group * len(groups))(*[g.as_c() for g in groups])
+    cfg = L.octa_adam_cfg(beta1, beta2, eps)
+    L.check(_lib().adam_step(arr, len(groups), C.byref(cfg), _ptr(scaler), _ptr(ws), ws.numel(),
+                             _stream(stream)), "adam_step")
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+
+class OctaQueryFunction(torch.autograd.Function):
+    """L_hat(x, omega) differentiable w.r.t. the feature table and the flat
+    decoder weights; backward runs octa_query_bwd (forward recomputed)."""
+
+    @staticmethod
+    def forward(ctx, x, omega, tables, weights_flat, scene):
+        scene.set_tables(tables.detach())
+        scene.set_weights_flat(weights_flat.detach())
+        rgb, _, _ = octa_query_fwd(scene, x, omega)
+        ctx.save_for_backward(x, omega)
+        ctx.scene = scene
+        return rgb
+
+    @staticmethod
+    def backward(ctx, d_rgb):
+        x, omega = ctx.saved_tensors
+        sc = ctx.scene
+        dT = torch.zeros(sc.tables.shape, dtype=torch.float32, device=x.device)
+        dW = torch.zeros(sc.weights.shape, dtype=torch.float32, device=x.device)
+        octa_query_bwd(sc, x, omega, d_rgb.contiguous().float(), [(dT, dW)])
+        return None, None, dT, dW, None
+
+
+def octa_query(scene, x, omega, tables, weights_flat):
+    return OctaQueryFunction.apply(x, omega, tables, weights_flat, scene)

@@ -1,0 +1,521 @@
+// FP32 path of the OctaOctree query (forward and backward) on the CUDA cores.
+//
+// One persistent CTA of 256 threads works on tiles of QT = 128 queries of
+// one scene.  Per tile:
+//   1. locate   one thread per query: octahedral fold of omega (Eq. 4, 5) and
+//               the descent from the root to the containing node of every
+//               level (Section 3.4);
+//   2. gather   one thread per (query, level): bilinear blend of the 4
+//               wrapped texels of that node's map, written feature-major into
+//               shared memory (the concatenation of Eq. 11 is the row index);
+//   3. decoder  Eq. 13 as register-blocked FP32 GEMMs over the tile, weights
+//               and activations in shared memory;
+//   4. backward (BWD) delta chain, dW accumulated in registers across all
+//               tiles the CTA handles, dh, then float4 atomics into the FP32
+//               table gradient.
+// Shared-memory activations are stored [feature][query] with row stride
+// LDA = QT + 4 floats, so every GEMM operand read is a 16-byte vector and
+// rows of neighbouring features fall into different banks.
+#pragma once
+#include "octa_device.cuh"
+
+namespace octa {
+namespace f32 {
+
+constexpr int NT = 256;        // threads per CTA
+constexpr int LDA = QT + 4;    // activation row stride (floats)
+
+template <int F_, int WP_, int H_, int NH_, bool BWD_>
+struct Shape {
+  static constexpr int F = F_, WP = WP_, H = H_, NH = NH_;
+  static constexpr bool BWD = BWD_;
+  static constexpr int KMAX = WP / F;
+  static_assert(WP % F == 0 && WP % 4 == 0, "padded input width");
+  static_assert(H % 16 == 0, "hidden width");
+  // weights: W_0 [H][WP], W_1..W_{NH-1} [H][H], W_L [4][H] (row 3 zero)
+  static constexpr int WSM = H * WP + (NH - 1) * H * H + 4 * H;
+  static constexpr int ACT0 = 0;
+  static constexpr int MAXW = WP > H ? WP : H;
+  // BWD keeps h, a_1..a_NH and delta_L; FWD ping-pongs two buffers
+  static constexpr int ACT_ROWS = BWD ? (WP + NH * H + 4) : 2 * MAXW;
+  static constexpr size_t SMEM =
+      sizeof(float) * (size_t(WSM) + size_t(ACT_ROWS) * LDA) + sizeof(int) * KMAX * QT +
+      sizeof(float) * 2 * QT;
+};
+
+// ---------------------------------------------------------------------------
+// Tile GEMMs (all operands in shared memory)
+// ---------------------------------------------------------------------------
+
+// Y[m][q] = relu(sum_k W[m][k] X[k][q]);  W row-major [M][KD].
+// Warp w owns rows [w*M/8, (w+1)*M/8) (weight reads are warp-uniform
+// broadcasts); lane owns queries [4 lane, 4 lane + 4).
+template <int M, int KD>
+__device__ __forceinline__ void gemm_fwd_relu(const float* __restrict__ W,
+                                              const float* __restrict__ X,
+                                              float* __restrict__ Y) {
+  constexpr int TM = M / 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = warp * TM, q0 = lane * 4;
+  float acc[TM][4];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 2
+  for (int k = 0; k < KD; k += 4) {
+    float4 x[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) x[c] = *reinterpret_cast<const float4*>(X + (k + c) * LDA + q0);
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const float4 w = *reinterpret_cast<const float4*>(W + (m0 + i) * KD + k);
+      const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        acc[i][0] = fmaf(wv[c], x[c].x, acc[i][0]);
+        acc[i][1] = fmaf(wv[c], x[c].y, acc[i][1]);
+        acc[i][2] = fmaf(wv[c], x[c].z, acc[i][2]);
+        acc[i][3] = fmaf(wv[c], x[c].w, acc[i][3]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    float4 o;
+    o.x = fmaxf(acc[i][0], 0.f);
+    o.y = fmaxf(acc[i][1], 0.f);
+    o.z = fmaxf(acc[i][2], 0.f);
+    o.w = fmaxf(acc[i][3], 0.f);
+    *reinterpret_cast<float4*>(Y + (m0 + i) * LDA + q0) = o;
+  }
+}
+
+// Y[k][q] = (sum_m W[m][k] D[m][q]) * (MASK ? 1[Y[k][q] > 0] : 1), W
+// row-major [M][KD].  Rows k come in chunks of 4; chunk c goes to warp c % 8.
+// With MASK the result overwrites the activation it is masked with (each
+// element is read and written by the same thread).
+template <int M, int KD, bool MASK>
+__device__ __forceinline__ void gemm_bwd_data(const float* __restrict__ W,
+                                              const float* __restrict__ D, float* Y) {
+  constexpr int NCH = KD / 4;
+  constexpr int CPW = (NCH + 7) / 8;
+  static_assert(KD % 4 == 0, "KD");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q0 = lane * 4;
+  float acc[CPW][4][4];
+#pragma unroll
+  for (int j = 0; j < CPW; ++j)
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[j][r][c] = 0.f;
+#pragma unroll 4
+  for (int m = 0; m < M; ++m) {
+    const float4 d = *reinterpret_cast<const float4*>(D + m * LDA + q0);
+#pragma unroll
+    for (int j = 0; j < CPW; ++j) {
+      const int ch = warp + 8 * j;
+      if (ch < NCH) {
+        const float4 w = *reinterpret_cast<const float4*>(W + m * KD + 4 * ch);
+        const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          acc[j][r][0] = fmaf(wv[r], d.x, acc[j][r][0]);
+          acc[j][r][1] = fmaf(wv[r], d.y, acc[j][r][1]);
+          acc[j][r][2] = fmaf(wv[r], d.z, acc[j][r][2]);
+          acc[j][r][3] = fmaf(wv[r], d.w, acc[j][r][3]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < CPW; ++j) {
+    const int ch = warp + 8 * j;
+    if (ch < NCH) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        float* y = Y + (4 * ch + r) * LDA + q0;
+        float4 o = make_float4(acc[j][r][0], acc[j][r][1], acc[j][r][2], acc[j][r][3]);
+        if (MASK) {
+          const float4 a = *reinterpret_cast<const float4*>(y);
+          o.x = a.x > 0.f ? o.x : 0.f;
+          o.y = a.y > 0.f ? o.y : 0.f;
+          o.z = a.z > 0.f ? o.z : 0.f;
+          o.w = a.w > 0.f ? o.w : 0.f;
+        }
+        *reinterpret_cast<float4*>(y) = o;
+      }
+    }
+  }
+}
+
+// Weight-gradient tile of one thread: rows m = mb + 16 r, columns
+// k = kb + 16 c with (mb, kb) = (tid % 16, tid / 16).
+template <int M, int KD>
+struct WGrad {
+  static constexpr int TMW = M / 16;
+  static constexpr int TKW = (KD + 15) / 16;
+  float a[TMW][TKW];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int r = 0; r < TMW; ++r)
+#pragma unroll
+      for (int c = 0; c < TKW; ++c) a[r][c] = 0.f;
+  }
+  // a[r][c] += sum_q D[m_r][q] X[k_c][q]
+  __device__ __forceinline__ void accumulate(const float* __restrict__ D,
+                                             const float* __restrict__ X) {
+    const int mb = threadIdx.x & 15, kb = threadIdx.x >> 4;
+#pragma unroll 2
+    for (int q = 0; q < QT; q += 4) {
+      float4 d[TMW], x[TKW];
+#pragma unroll
+      for (int r = 0; r < TMW; ++r)
+        d[r] = *reinterpret_cast<const float4*>(D + (mb + 16 * r) * LDA + q);
+#pragma unroll
+      for (int c = 0; c < TKW; ++c)
+        x[c] = (kb + 16 * c < KD) ? *reinterpret_cast<const float4*>(X + (kb + 16 * c) * LDA + q)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int r = 0; r < TMW; ++r)
+#pragma unroll
+        for (int c = 0; c < TKW; ++c) {
+          float s = a[r][c];
+          s = fmaf(d[r].x, x[c].x, s);
+          s = fmaf(d[r].y, x[c].y, s);
+          s = fmaf(d[r].z, x[c].z, s);
+          s = fmaf(d[r].w, x[c].w, s);
+          a[r][c] = s;
+        }
+    }
+  }
+  // d_weights[off + m * in + k] += a (k < in only: padded columns are zero)
+  __device__ __forceinline__ void flush(float* dW, int in) const {
+    const int mb = threadIdx.x & 15, kb = threadIdx.x >> 4;
+#pragma unroll
+    for (int r = 0; r < TMW; ++r)
+#pragma unroll
+      for (int c = 0; c < TKW; ++c) {
+        const int k = kb + 16 * c;
+        if (k < KD && k < in) atomicAdd(dW + (mb + 16 * r) * in + k, a[r][c]);
+      }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// The engine
+// ---------------------------------------------------------------------------
+
+template <class S>
+struct Grads {
+  WGrad<S::H, S::WP> w0;
+  WGrad<S::H, S::H> wh[S::NH > 1 ? S::NH - 1 : 1];
+  float wl;
+  __device__ __forceinline__ void zero() {
+    w0.zero();
+#pragma unroll
+    for (int i = 0; i < S::NH - 1; ++i) wh[i].zero();
+    wl = 0.f;
+  }
+  __device__ __forceinline__ void flush(const DevScene& sc) const {
+    float* dW = sc.d_weights;
+    w0.flush(dW + sc.w_offset[0], sc.widths[0]);
+#pragma unroll
+    for (int i = 0; i < S::NH - 1; ++i) wh[i].flush(dW + sc.w_offset[i + 1], S::H);
+    if (threadIdx.x < 3 * S::H) atomicAdd(dW + sc.w_offset[S::NH] + threadIdx.x, wl);
+  }
+};
+
+template <class S>
+__device__ __forceinline__ void load_weights(const DevScene& sc, float* wsm) {
+  const float* Wg = static_cast<const float*>(sc.weights);
+  const int in0 = sc.widths[0];
+  for (int i = threadIdx.x; i < S::H * S::WP; i += NT) {
+    const int m = i / S::WP, k = i % S::WP;
+    wsm[i] = k < in0 ? Wg[sc.w_offset[0] + m * in0 + k] : 0.f;
+  }
+  float* dst = wsm + S::H * S::WP;
+  for (int l = 1; l < S::NH; ++l, dst += S::H * S::H)
+    for (int i = threadIdx.x; i < S::H * S::H; i += NT) dst[i] = Wg[sc.w_offset[l] + i];
+  for (int i = threadIdx.x; i < 4 * S::H; i += NT)
+    dst[i] = i < 3 * S::H ? Wg[sc.w_offset[S::NH] + i] : 0.f;
+}
+
+// Phase 1: fold omega and walk the tree (one thread per query).
+template <int KMAX>
+__device__ __forceinline__ void locate_tile(const QueryParams& p, const DevScene& sc, int64_t q0,
+                                            int nq, int* node_sm, float* u_sm) {
+  const int q = threadIdx.x;
+  if (q >= QT) return;
+  const bool valid = q < nq;
+  const int64_t gq = q0 + q;
+  float x0 = 0.f, x1 = 0.f, x2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 1.f;
+  if (valid) {
+    x0 = p.x[3 * gq];
+    x1 = p.x[3 * gq + 1];
+    x2 = p.x[3 * gq + 2];
+    w0 = p.omega[3 * gq];
+    w1 = p.omega[3 * gq + 1];
+    w2 = p.omega[3 * gq + 2];
+  }
+  float ux, uy;
+  octa_fold(w0, w1, w2, ux, uy);
+  u_sm[q] = ux;
+  u_sm[QT + q] = uy;
+  x0 = clamp01(x0);
+  x1 = clamp01(x1);
+  x2 = clamp01(x2);
+  int node = valid ? 0 : -1;
+  node_sm[q] = node;
+  int cp0 = 0, cp1 = 0, cp2 = 0;
+#pragma unroll
+  for (int l = 1; l < KMAX; ++l) {
+    if (l < sc.K) {
+      const int c0 = cell_coord(x0, l), c1 = cell_coord(x1, l), c2 = cell_coord(x2, l);
+      const int slot = (c0 - 2 * cp0) | ((c1 - 2 * cp1) << 1) | ((c2 - 2 * cp2) << 2);
+      if (node >= 0) {
+        int fc = __ldg(sc.first_child + node);
+        if (fc >= 0 && fc > sc.num_nodes - 8) {
+          if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
+          fc = -1;
+        }
+        node = fc >= 0 ? fc + slot : -1;
+      }
+      cp0 = c0;
+      cp1 = c1;
+      cp2 = c2;
+    } else {
+      node = -1;
+    }
+    node_sm[l * QT + q] = node;
+  }
+  if (p.node_idx && valid) {
+    for (int l = 0; l < p.kmax_out; ++l)
+      p.node_idx[gq * p.kmax_out + l] = l < KMAX ? node_sm[l * QT + q] : -1;
+  }
+}
+
+// Base texel of a node's map, or -1 if the map would leave the table.
+__device__ __forceinline__ int64_t map_base(const QueryParams& p, const DevScene& sc, int node,
+                                            int R) {
+  const int64_t mo = __ldg(sc.map_offset + node);
+  if (mo < 0 || mo + int64_t(R) * R > sc.num_texels) {
+    if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_MAP);
+    return -1;
+  }
+  return mo;
+}
+
+// Phase 2: one thread per (query, level) item for levels [0, nlev); writes
+// feature f of level l for query q to h[(l*F + f) * ld_feat + q * ld_q].
+template <int F, typename TT>
+__device__ __forceinline__ void gather_tile(const QueryParams& p, const DevScene& sc, int64_t q0,
+                                            int nq, int nlev, const int* node_sm,
+                                            const float* u_sm, float* h, int ld_feat, int ld_q) {
+  for (int it = threadIdx.x; it < nlev * QT; it += NT) {
+    const int l = it / QT, q = it % QT;
+    const int node = node_sm[l * QT + q];
+    float v[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) v[f] = 0.f;
+    int64_t a4[4] = {-1, -1, -1, -1};
+    if (node >= 0) {
+      const int R = sc.R[l];
+      const int64_t mo = map_base(p, sc, node, R);
+      if (mo >= 0) {
+        const Footprint fp = footprint(u_sm[q], u_sm[QT + q], R);
+        float t[4][F];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          a4[k] = mo + fp.idx[k];
+          TexelLoad<TT, F>::load(sc.tables, a4[k], t[k]);
+        }
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+          float s = fp.w[0] * t[0][f];
+          s = fmaf(fp.w[1], t[1][f], s);
+          s = fmaf(fp.w[2], t[2][f], s);
+          s = fmaf(fp.w[3], t[3][f], s);
+          v[f] = s;
+        }
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f) h[(l * F + f) * ld_feat + q * ld_q] = v[f];
+    if (p.texel_addr && q < nq && l < p.kmax_out) {
+      int4 o = make_int4(int(a4[0]), int(a4[1]), int(a4[2]), int(a4[3]));
+      *reinterpret_cast<int4*>(p.texel_addr + ((q0 + q) * p.kmax_out + l) * 4) = o;
+    }
+  }
+  // texel_addr columns of levels this scene does not have
+  if (p.texel_addr && p.kmax_out > nlev) {
+    for (int it = threadIdx.x; it < (p.kmax_out - nlev) * QT; it += NT) {
+      const int l = nlev + it / QT, q = it % QT;
+      if (q < nq)
+        *reinterpret_cast<int4*>(p.texel_addr + ((q0 + q) * p.kmax_out + l) * 4) =
+            make_int4(-1, -1, -1, -1);
+    }
+  }
+}
+
+// Phase 4 (BWD): d_tables[texel] += w_k * dh_l for the 4 corners of every
+// present level (float4 vector atomics).
+template <int KMAX, int F>
+__device__ __forceinline__ void scatter_tile(const QueryParams& p, const DevScene& sc,
+                                             const int* node_sm, const float* u_sm,
+                                             const float* dh) {
+  for (int it = threadIdx.x; it < KMAX * QT; it += NT) {
+    const int l = it / QT, q = it % QT;
+    const int node = node_sm[l * QT + q];
+    if (node < 0) continue;
+    const int R = sc.R[l];
+    const int64_t mo = map_base(p, sc, node, R);
+    if (mo < 0) continue;
+    const Footprint fp = footprint(u_sm[q], u_sm[QT + q], R);
+#pragma unroll
+    for (int c = 0; c < F / 4; ++c) {
+      const float g0 = dh[(l * F + 4 * c + 0) * LDA + q];
+      const float g1 = dh[(l * F + 4 * c + 1) * LDA + q];
+      const float g2 = dh[(l * F + 4 * c + 2) * LDA + q];
+      const float g3 = dh[(l * F + 4 * c + 3) * LDA + q];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float w = fp.w[k];
+        float4* dst = reinterpret_cast<float4*>(sc.d_tables + (mo + fp.idx[k]) * F) + c;
+        atomicAdd(dst, make_float4(w * g0, w * g1, w * g2, w * g3));
+      }
+    }
+  }
+}
+
+template <class S, typename TT>
+__global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ QueryParams p) {
+  constexpr int H = S::H, WP = S::WP, NH = S::NH;
+  extern __shared__ __align__(16) float smem[];
+  float* wsm = smem;
+  float* act = wsm + S::WSM;
+  int* node_sm = reinterpret_cast<int*>(act + S::ACT_ROWS * LDA);
+  float* u_sm = reinterpret_cast<float*>(node_sm + S::KMAX * QT);
+  // activation buffers
+  auto act_bwd = [&](int i) { return i == 0 ? act : act + (WP + (i - 1) * H) * LDA; };
+  float* dL = act + (WP + NH * H) * LDA;  // delta_L (BWD)
+  float* buf[2] = {act, act + S::MAXW * LDA};
+
+  Grads<S> g;
+  if (S::BWD) g.zero();
+  int cur = -1;
+  for (int64_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+    const int s = scene_of_tile(p, tile);
+    const DevScene& sc = p.sc[s];
+    __syncthreads();  // previous tile finished with shared memory
+    if (s != cur) {
+      if (S::BWD && cur >= 0) {
+        g.flush(p.sc[cur]);
+        g.zero();
+      }
+      load_weights<S>(sc, wsm);
+      cur = s;
+    }
+    const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * QT;
+    const int nq = static_cast<int>(sc.q_end - q0 < QT ? sc.q_end - q0 : int64_t(QT));
+    float* h = S::BWD ? act_bwd(0) : buf[0];
+    locate_tile<S::KMAX>(p, sc, q0, nq, node_sm, u_sm);
+    __syncthreads();
+    gather_tile<S::F, TT>(p, sc, q0, nq, S::KMAX, node_sm, u_sm, h, LDA, 1);
+    __syncthreads();
+
+    // ---- decoder forward (Eq. 13)
+    const float* Wl = wsm + H * WP + (NH - 1) * H * H;  // last layer [4][H]
+    float* a_last;
+    if (S::BWD) {
+      gemm_fwd_relu<H, WP>(wsm, act_bwd(0), act_bwd(1));
+      __syncthreads();
+#pragma unroll
+      for (int i = 1; i < NH; ++i) {
+        gemm_fwd_relu<H, H>(wsm + H * WP + (i - 1) * H * H, act_bwd(i), act_bwd(i + 1));
+        __syncthreads();
+      }
+      a_last = act_bwd(NH);
+    } else {
+      gemm_fwd_relu<H, WP>(wsm, buf[0], buf[1]);
+      __syncthreads();
+#pragma unroll
+      for (int i = 1; i < NH; ++i) {
+        gemm_fwd_relu<H, H>(wsm + H * WP + (i - 1) * H * H, buf[i & 1], buf[(i + 1) & 1]);
+        __syncthreads();
+      }
+      a_last = buf[NH & 1];
+    }
+    if (threadIdx.x < QT) {
+      const int q = threadIdx.x;
+      float z0 = 0.f, z1 = 0.f, z2 = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < H; ++k) {
+        const float a = a_last[k * LDA + q];
+        z0 = fmaf(Wl[k], a, z0);
+        z1 = fmaf(Wl[H + k], a, z1);
+        z2 = fmaf(Wl[2 * H + k], a, z2);
+      }
+      const float r0 = expf(z0), r1 = expf(z1), r2 = expf(z2);
+      const int64_t gq = q0 + q;
+      if (!S::BWD) {
+        if (q < nq) {
+          p.rgb[3 * gq] = r0;
+          p.rgb[3 * gq + 1] = r1;
+          p.rgb[3 * gq + 2] = r2;
+        }
+      } else {
+        float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+        if (q < nq) {
+          d0 = p.d_rgb[3 * gq];
+          d1 = p.d_rgb[3 * gq + 1];
+          d2 = p.d_rgb[3 * gq + 2];
+        }
+        dL[q] = d0 * r0;  // d exp(z) / dz = exp(z)
+        dL[LDA + q] = d1 * r1;
+        dL[2 * LDA + q] = d2 * r2;
+        dL[3 * LDA + q] = 0.f;
+      }
+    }
+    if (!S::BWD) continue;
+
+    // ---- backward
+    __syncthreads();
+    if (threadIdx.x < 3 * H) {  // dW_L[m][k] += sum_q delta_L[m][q] a_NH[k][q]
+      const int m = threadIdx.x / H, k = threadIdx.x % H;
+      float sacc = g.wl;
+#pragma unroll 4
+      for (int q = 0; q < QT; q += 4) {
+        const float4 d = *reinterpret_cast<const float4*>(dL + m * LDA + q);
+        const float4 a = *reinterpret_cast<const float4*>(a_last + k * LDA + q);
+        sacc = fmaf(d.x, a.x, sacc);
+        sacc = fmaf(d.y, a.y, sacc);
+        sacc = fmaf(d.z, a.z, sacc);
+        sacc = fmaf(d.w, a.w, sacc);
+      }
+      g.wl = sacc;
+    }
+    __syncthreads();
+    gemm_bwd_data<3, H, true>(Wl, dL, act_bwd(NH));  // delta_NH in place
+    __syncthreads();
+#pragma unroll
+    for (int i = NH - 1; i >= 0; --i) {
+      if (i == 0)
+        g.w0.accumulate(act_bwd(1), act_bwd(0));
+      else
+        g.wh[i - 1].accumulate(act_bwd(i + 1), act_bwd(i));
+      __syncthreads();
+      if (i == 0)
+        gemm_bwd_data<H, WP, false>(wsm, act_bwd(1), act_bwd(0));  // dh
+      else
+        gemm_bwd_data<H, H, true>(wsm + H * WP + (i - 1) * H * H, act_bwd(i + 1), act_bwd(i));
+      __syncthreads();
+    }
+    scatter_tile<S::KMAX, S::F>(p, sc, node_sm, u_sm, act_bwd(0));
+  }
+  if (S::BWD && cur >= 0) g.flush(p.sc[cur]);
+}
+
+}  // namespace f32
+}  // namespace octa

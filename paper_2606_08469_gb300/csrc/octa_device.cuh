@@ -1,0 +1,198 @@
+// Device-side building blocks of the OctaOctree query shared by the FP32 and
+// the tensor-core kernels: kernel parameter blocks, the canonical binary32
+// octahedral encoding, the texel wrap and the tree descent.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "octaoctree.h"
+
+namespace octa {
+
+// Queries per tile: one CTA works on QT queries at a time.
+constexpr int QT = 128;
+
+// Per-scene descriptor, passed by value inside the kernel parameter block.
+struct DevScene {
+  const int32_t* first_child;
+  const int32_t* map_offset;
+  const void* tables;
+  const void* weights;
+  float* d_tables;
+  float* d_weights;
+  int64_t num_texels;
+  int64_t q_begin, q_end;  // query range of this scene
+  int64_t tile_begin;      // first global tile of this scene
+  int32_t num_nodes;
+  int32_t K;
+  int32_t n_layers;
+  int32_t R[OCTA_MAX_LEVELS];
+  int32_t widths[OCTA_MAX_LAYERS + 1];
+  int32_t w_offset[OCTA_MAX_LAYERS + 1];  // element offset of W_i; [L] = total
+};
+
+struct QueryParams {
+  DevScene sc[OCTA_MAX_SCENES];
+  int32_t n_scenes;
+  int32_t kmax_out;        // columns of node_idx / texel_addr
+  int64_t n_tiles;
+  const float* x;
+  const float* omega;
+  float* rgb;
+  const float* d_rgb;
+  int32_t* node_idx;
+  int32_t* texel_addr;
+  int32_t* status;
+  void* features;
+  int64_t row_stride;
+  int32_t feat_dtype;
+};
+
+// Scene owning global tile t (tiles never straddle scenes).
+__device__ __forceinline__ int scene_of_tile(const QueryParams& p, int64_t t) {
+  int s = 0;
+#pragma unroll 1
+  while (s + 1 < p.n_scenes && t >= p.sc[s + 1].tile_begin) ++s;
+  return s;
+}
+
+// Eq. 4 and Eq. 5 in the canonical binary32 order (one IEEE rounding per
+// operation, no contraction), so the integer texel coordinates agree
+// bit-exactly with any other implementation of the same sequence:
+// s = (|wx| + |wy|) + |wz|; u = (wx / s, wy / s); if wz < 0 fold with
+// sign(0) = +1.
+__device__ __forceinline__ void octa_fold(float wx, float wy, float wz, float& ux, float& uy) {
+  const float s = __fadd_rn(__fadd_rn(fabsf(wx), fabsf(wy)), fabsf(wz));
+  float a = __fdiv_rn(wx, s);
+  float b = __fdiv_rn(wy, s);
+  if (wz < 0.f) {
+    const float sa = a >= 0.f ? 1.f : -1.f;
+    const float sb = b >= 0.f ? 1.f : -1.f;
+    const float na = __fmul_rn(__fsub_rn(1.f, fabsf(b)), sa);
+    const float nb = __fmul_rn(__fsub_rn(1.f, fabsf(a)), sb);
+    a = na;
+    b = nb;
+  }
+  ux = a;
+  uy = b;
+}
+
+// Continuous texel coordinate p = (u * 0.5 + 0.5) * R - 0.5 (texel (i, j) is
+// centred at uv = ((i + 1/2)/R, (j + 1/2)/R)).
+__device__ __forceinline__ float octa_texel_coord(float u, float R) {
+  return __fsub_rn(__fmul_rn(__fadd_rn(__fmul_rn(u, 0.5f), 0.5f), R), 0.5f);
+}
+
+// Bilinear footprint of one direction on an R x R map: texel indices (within
+// the node's map) of the 4 corners (i0+a, j0+b), k = a + 2b, after the
+// octahedral wrap, and their weights.
+struct Footprint {
+  int idx[4];
+  float w[4];
+};
+
+// Octahedral wrap of a corner in [-1, R]^2: across u_x = +-1 the map
+// continues mirrored in u_y, across u_y = +-1 mirrored in u_x (i first).
+__device__ __forceinline__ int wrap_index(int i, int j, int R) {
+  if (i < 0) {
+    i = 0;
+    j = R - 1 - j;
+  } else if (i >= R) {
+    i = R - 1;
+    j = R - 1 - j;
+  }
+  if (j < 0) {
+    j = 0;
+    i = R - 1 - i;
+  } else if (j >= R) {
+    j = R - 1;
+    i = R - 1 - i;
+  }
+  return j * R + i;
+}
+
+__device__ __forceinline__ Footprint footprint(float ux, float uy, int R) {
+  const float Rf = static_cast<float>(R);
+  const float px = octa_texel_coord(ux, Rf);
+  const float py = octa_texel_coord(uy, Rf);
+  const float flx = floorf(px), fly = floorf(py);
+  // p lies in [-1/2, R - 1/2] for any finite direction; the clamp only
+  // guards non-finite input (zero direction) against out-of-map indices.
+  const int i0 = min(max(static_cast<int>(flx), -1), R - 1);
+  const int j0 = min(max(static_cast<int>(fly), -1), R - 1);
+  const float fx = __fsub_rn(px, flx);
+  const float fy = __fsub_rn(py, fly);
+  Footprint f;
+  f.idx[0] = wrap_index(i0, j0, R);
+  f.idx[1] = wrap_index(i0 + 1, j0, R);
+  f.idx[2] = wrap_index(i0, j0 + 1, R);
+  f.idx[3] = wrap_index(i0 + 1, j0 + 1, R);
+  const float gx = 1.f - fx, gy = 1.f - fy;
+  f.w[0] = gx * gy;
+  f.w[1] = fx * gy;
+  f.w[2] = gx * fy;
+  f.w[3] = fx * fy;
+  return f;
+}
+
+// Level-l cell coordinate of x in [0,1] (x * 2^l is exact in binary32).
+__device__ __forceinline__ int cell_coord(float x, int l) {
+  const int n = 1 << l;
+  return min(static_cast<int>(floorf(x * static_cast<float>(n))), n - 1);
+}
+
+__device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
+
+// Loads of one texel's F features as FP32.
+template <typename TT, int F>
+struct TexelLoad;
+
+template <>
+struct TexelLoad<float, 4> {
+  static __device__ __forceinline__ void load(const void* t, int64_t texel, float (&v)[4]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(t) + texel);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+};
+
+template <>
+struct TexelLoad<float, 8> {
+  static __device__ __forceinline__ void load(const void* t, int64_t texel, float (&v)[8]) {
+    const float4* p = reinterpret_cast<const float4*>(t) + 2 * texel;
+    const float4 a = __ldg(p), b = __ldg(p + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+};
+
+template <>
+struct TexelLoad<__half, 8> {
+  static __device__ __forceinline__ void load(const void* t, int64_t texel, float (&v)[8]) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(t) + texel);
+    const __half2* h = reinterpret_cast<const __half2*>(&a);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __half22float2(h[i]);
+      v[2 * i] = f.x;
+      v[2 * i + 1] = f.y;
+    }
+  }
+};
+
+template <>
+struct TexelLoad<__half, 4> {
+  static __device__ __forceinline__ void load(const void* t, int64_t texel, float (&v)[4]) {
+    const uint2 a = __ldg(reinterpret_cast<const uint2*>(t) + texel);
+    const __half2* h = reinterpret_cast<const __half2*>(&a);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float2 f = __half22float2(h[i]);
+      v[2 * i] = f.x;
+      v[2 * i + 1] = f.y;
+    }
+  }
+};
+
+}  // namespace octa

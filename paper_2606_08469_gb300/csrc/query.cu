@@ -1,0 +1,346 @@
+// C ABI of the query path: octa_encode, octa_query_fwd, octa_query_bwd.
+// Host-side validation, the kernel parameter block, dispatch to the FP32
+// engine (CUDA cores) or the BF16 tensor-core kernels, and the standalone
+// encoding kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "engine_f32.cuh"
+#include "octa_internal.h"
+#include "tc_path.h"
+
+namespace octa {
+
+// ---------------------------------------------------------------------------
+// Standalone encoding kernel (Eq. 10 single-cell bilinear form + Eq. 11)
+// ---------------------------------------------------------------------------
+// Tile of QT queries: locate (one thread per query), gather (one thread per
+// (query, level)) into a [query][feature] staging area whose odd row stride
+// keeps the scalar writes conflict-free, then a coalesced copy of the tile's
+// rows to global memory.
+template <int F, typename TT, typename OT>
+__global__ void __launch_bounds__(f32::NT) encode_kernel(const __grid_constant__ QueryParams p) {
+  extern __shared__ __align__(16) float smem[];
+  int* node_sm = reinterpret_cast<int*>(smem);
+  float* u_sm = smem + OCTA_MAX_LEVELS * QT;
+  float* stage = u_sm + 2 * QT;
+  for (int64_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+    const int s = scene_of_tile(p, tile);
+    const DevScene& sc = p.sc[s];
+    const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * QT;
+    const int nq = static_cast<int>(sc.q_end - q0 < QT ? sc.q_end - q0 : int64_t(QT));
+    const int W = sc.K * F;
+    const int ws = W | 1;  // odd staging stride
+    __syncthreads();
+    f32::locate_tile<OCTA_MAX_LEVELS>(p, sc, q0, nq, node_sm, u_sm);
+    __syncthreads();
+    f32::gather_tile<F, TT>(p, sc, q0, nq, sc.K, node_sm, u_sm, stage, 1, ws);
+    __syncthreads();
+    OT* out = static_cast<OT*>(p.features);
+    for (int i = threadIdx.x; i < nq * W; i += f32::NT) {
+      const int q = i / W, k = i % W;
+      const float v = stage[q * ws + k];
+      OT o;
+      if constexpr (sizeof(OT) == 4)
+        o = v;
+      else
+        o = __float2bfloat16_rn(v);
+      out[(q0 + q) * p.row_stride + k] = o;
+    }
+  }
+}
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+int sm_count() {
+  static int cache[kMaxDevices] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 148;
+  if (cache[dev] == 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = n > 0 ? n : 148;
+  }
+  return cache[dev];
+}
+
+// Per-kernel launch facts, queried once per device (outside any stream
+// capture: the first call of each kernel must be eager).
+struct LaunchInfo {
+  const void* fn;
+  int dev;
+  size_t smem;
+  int per_sm;
+};
+LaunchInfo g_launch_cache[256];
+int g_launch_count = 0;
+std::mutex g_launch_mutex;
+
+template <class Kern>
+int blocks_per_sm(Kern kernel, size_t smem, int threads, int* out) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const void* fn = reinterpret_cast<const void*>(kernel);
+  std::lock_guard<std::mutex> lock(g_launch_mutex);
+  for (int i = 0; i < g_launch_count; ++i)
+    if (g_launch_cache[i].fn == fn && g_launch_cache[i].dev == dev &&
+        g_launch_cache[i].smem == smem) {
+      *out = g_launch_cache[i].per_sm;
+      return OCTA_OK;
+    }
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess)
+      return fail(OCTA_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+  if (per_sm < 1) return fail(OCTA_ECUDA, "kernel does not fit on an SM (smem %zu)", smem);
+  if (g_launch_count < 256) g_launch_cache[g_launch_count++] = LaunchInfo{fn, dev, smem, per_sm};
+  *out = per_sm;
+  return OCTA_OK;
+}
+
+// Persistent grid: as many CTAs as fit on the device, never more than tiles.
+template <class Kern>
+int launch_persistent(Kern kernel, size_t smem, const QueryParams& p, cudaStream_t stream,
+                      int threads) {
+  if (p.n_tiles == 0) return OCTA_OK;
+  int per_sm = 0;
+  int rc = blocks_per_sm(kernel, smem, threads, &per_sm);
+  if (rc) return rc;
+  const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * sm_count());
+  kernel<<<static_cast<unsigned>(grid), threads, smem, stream>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+  return OCTA_OK;
+}
+
+bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
+
+}  // namespace
+
+// Validates scenes + queries and fills the kernel parameter block.
+int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
+                       const octa_scene_grads* grads, QueryParams& p) {
+  std::memset(&p, 0, sizeof(p));
+  if (!scenes || !q) return fail(OCTA_EINVAL, "scenes and queries must be non-NULL");
+  if (n_scenes < 1 || n_scenes > OCTA_MAX_SCENES)
+    return fail(OCTA_ERANGE, "n_scenes %d outside [1, %d]", n_scenes, OCTA_MAX_SCENES);
+  if (q->n < 0) return fail(OCTA_EINVAL, "negative query count");
+  if (q->n > 0 && (!q->x || !q->omega)) return fail(OCTA_EINVAL, "x / omega must be non-NULL");
+  if (q->scene_start[0] != 0 || q->scene_start[n_scenes] != q->n)
+    return fail(OCTA_EINVAL, "scene_start must run from 0 to n");
+  p.n_scenes = n_scenes;
+  int64_t tiles = 0;
+  for (int s = 0; s < n_scenes; ++s) {
+    const octa_scene& c = scenes[s];
+    DevScene& d = p.sc[s];
+    if (q->scene_start[s + 1] < q->scene_start[s])
+      return fail(OCTA_EINVAL, "scene_start must be non-decreasing");
+    if (!c.first_child || !c.map_offset || !c.tables || !c.weights)
+      return fail(OCTA_EINVAL, "scene %d: NULL tree, table or weight pointer", s);
+    if (c.num_levels < 1 || c.num_levels > OCTA_MAX_LEVELS)
+      return fail(OCTA_ERANGE, "scene %d: num_levels %d outside [1, %d]", s, c.num_levels,
+                  OCTA_MAX_LEVELS);
+    if (c.num_nodes < 1) return fail(OCTA_EINVAL, "scene %d: empty tree", s);
+    if (c.num_texels < 1 || c.num_texels > 2147483647LL)
+      return fail(OCTA_ERANGE, "scene %d: num_texels outside [1, 2^31)", s);
+    if (c.F != 4 && c.F != 8) return fail(OCTA_EINVAL, "scene %d: F must be 4 or 8", s);
+    if (c.table_dtype != OCTA_F32 && c.table_dtype != OCTA_F16)
+      return fail(OCTA_EINVAL, "scene %d: table dtype must be F32 or F16", s);
+    if (c.weight_dtype != OCTA_F32 && c.weight_dtype != OCTA_BF16)
+      return fail(OCTA_EINVAL, "scene %d: weight dtype must be F32 or BF16", s);
+    if (c.n_layers < 2 || c.n_layers > OCTA_MAX_LAYERS)
+      return fail(OCTA_ERANGE, "scene %d: n_layers %d outside [2, %d]", s, c.n_layers,
+                  OCTA_MAX_LAYERS);
+    if (c.widths[0] != c.num_levels * c.F)
+      return fail(OCTA_EINVAL, "scene %d: widths[0] must equal K*F", s);
+    if (c.widths[c.n_layers] != 3) return fail(OCTA_EINVAL, "scene %d: output width must be 3", s);
+    if (!aligned16(c.tables)) return fail(OCTA_EINVAL, "scene %d: tables not 16-byte aligned", s);
+    for (int l = 0; l < c.num_levels; ++l)
+      if (c.R[l] < 2 || c.R[l] > 4096)
+        return fail(OCTA_ERANGE, "scene %d: R[%d] = %d outside [2, 4096]", s, l, c.R[l]);
+    d.first_child = c.first_child;
+    d.map_offset = c.map_offset;
+    d.tables = c.tables;
+    d.weights = c.weights;
+    d.num_texels = c.num_texels;
+    d.num_nodes = c.num_nodes;
+    d.K = c.num_levels;
+    d.n_layers = c.n_layers;
+    for (int l = 0; l < c.num_levels; ++l) d.R[l] = c.R[l];
+    int off = 0;
+    for (int i = 0; i <= c.n_layers; ++i) {
+      if (c.widths[i] < 1) return fail(OCTA_EINVAL, "scene %d: width %d < 1", s, i);
+      d.widths[i] = c.widths[i];
+      d.w_offset[i] = off;
+      if (i < c.n_layers) off += c.widths[i] * c.widths[i + 1];
+    }
+    if (grads) {
+      if (!grads[s].d_tables || !grads[s].d_weights)
+        return fail(OCTA_EINVAL, "scene %d: NULL gradient buffer", s);
+      if (!aligned16(grads[s].d_tables))
+        return fail(OCTA_EINVAL, "scene %d: d_tables not 16-byte aligned", s);
+      d.d_tables = grads[s].d_tables;
+      d.d_weights = grads[s].d_weights;
+    }
+    d.q_begin = q->scene_start[s];
+    d.q_end = q->scene_start[s + 1];
+    d.tile_begin = tiles;
+    tiles += (d.q_end - d.q_begin + QT - 1) / QT;
+  }
+  p.n_tiles = tiles;
+  p.x = q->x;
+  p.omega = q->omega;
+  return OCTA_OK;
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// FP32 engine dispatch
+// ---------------------------------------------------------------------------
+struct EngineKey {
+  int F, WP, H, NH, tdt;
+};
+
+template <int F, int WP, int H, int NH, typename TT>
+int run_engine(const QueryParams& p, bool bwd, cudaStream_t stream) {
+  if (bwd) {
+    using S = f32::Shape<F, WP, H, NH, true>;
+    return launch_persistent(f32::engine_kernel<S, TT>, S::SMEM, p, stream, f32::NT);
+  }
+  using S = f32::Shape<F, WP, H, NH, false>;
+  return launch_persistent(f32::engine_kernel<S, TT>, S::SMEM, p, stream, f32::NT);
+}
+
+// Built shapes of the FP32 engine: (F, padded input width, hidden width,
+// hidden layers) x table type.  A scene set uses the smallest padded width
+// that holds every scene's K*F.
+int dispatch_engine(const octa_scene* scenes, int n_scenes, const QueryParams& p, bool bwd,
+                    cudaStream_t stream) {
+  const octa_scene& c0 = scenes[0];
+  const int F = c0.F, L = c0.n_layers, H = c0.widths[1], tdt = c0.table_dtype;
+  int need = 0;
+  for (int s = 0; s < n_scenes; ++s) {
+    const octa_scene& c = scenes[s];
+    if (c.F != F || c.n_layers != L || c.table_dtype != tdt || c.weight_dtype != OCTA_F32)
+      return fail(OCTA_EUNSUPPORTED, "scenes of one call must share F, depth of the MLP and dtypes");
+    for (int i = 1; i < L; ++i)
+      if (c.widths[i] != H)
+        return fail(OCTA_EUNSUPPORTED, "FP32 path: hidden widths must all equal %d", H);
+    need = std::max(need, c.widths[0]);
+  }
+  const int NH = L - 1;
+  const bool f16 = tdt == OCTA_F16;
+#define OCTA_TRY(F_, WP_, H_, NH_)                                                      \
+  if (F == F_ && H == H_ && NH == NH_ && need <= WP_)                                   \
+    return f16 ? run_engine<F_, WP_, H_, NH_, __half>(p, bwd, stream)                  \
+               : run_engine<F_, WP_, H_, NH_, float>(p, bwd, stream);
+  OCTA_TRY(4, 24, 32, 2)
+  OCTA_TRY(8, 56, 64, 2)
+  OCTA_TRY(8, 72, 64, 2)
+  OCTA_TRY(8, 80, 64, 2)
+  OCTA_TRY(8, 72, 64, 3)
+  OCTA_TRY(8, 80, 64, 3)
+#undef OCTA_TRY
+  return fail(OCTA_EUNSUPPORTED,
+              "FP32 path: no built shape for F=%d, K*F=%d, hidden %d x %d", F, need, NH, H);
+}
+
+}  // namespace
+}  // namespace octa
+
+using namespace octa;
+
+extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
+                           void* features, int32_t feat_dtype, int64_t row_stride,
+                           int32_t* node_idx, int32_t* texel_addr, int32_t* status,
+                           void* stream) {
+  clear_error();
+  QueryParams p;
+  int rc = build_query_params(scenes, n_scenes, q, nullptr, p);
+  if (rc) return rc;
+  if (q->n > 0 && !features) return fail(OCTA_EINVAL, "features must be non-NULL");
+  if (feat_dtype != OCTA_F32 && feat_dtype != OCTA_BF16)
+    return fail(OCTA_EINVAL, "feature dtype must be F32 or BF16");
+  int kmax = 0, F = scenes[0].F, tdt = scenes[0].table_dtype;
+  for (int s = 0; s < n_scenes; ++s) {
+    kmax = std::max(kmax, scenes[s].num_levels);
+    if (row_stride < scenes[s].num_levels * scenes[s].F)
+      return fail(OCTA_EINVAL, "row_stride smaller than K*F of scene %d", s);
+    if (scenes[s].F != F || scenes[s].table_dtype != tdt)
+      return fail(OCTA_EUNSUPPORTED, "scenes of one call must share F and table dtype");
+  }
+  if (texel_addr && (reinterpret_cast<uintptr_t>(texel_addr) & 15u))
+    return fail(OCTA_EINVAL, "texel_addr not 16-byte aligned");
+  p.features = features;
+  p.row_stride = row_stride;
+  p.feat_dtype = feat_dtype;
+  p.node_idx = node_idx;
+  p.texel_addr = texel_addr;
+  p.kmax_out = kmax;
+  p.status = status;
+  const size_t smem =
+      sizeof(float) * (OCTA_MAX_LEVELS * QT + 2 * QT + size_t(QT) * ((kmax * F) | 1));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool f16 = tdt == OCTA_F16, bf = feat_dtype == OCTA_BF16;
+  if (F == 4) {
+    if (f16)
+      return bf ? launch_persistent(encode_kernel<4, __half, __nv_bfloat16>, smem, p, st, f32::NT)
+                : launch_persistent(encode_kernel<4, __half, float>, smem, p, st, f32::NT);
+    return bf ? launch_persistent(encode_kernel<4, float, __nv_bfloat16>, smem, p, st, f32::NT)
+              : launch_persistent(encode_kernel<4, float, float>, smem, p, st, f32::NT);
+  }
+  if (f16)
+    return bf ? launch_persistent(encode_kernel<8, __half, __nv_bfloat16>, smem, p, st, f32::NT)
+              : launch_persistent(encode_kernel<8, __half, float>, smem, p, st, f32::NT);
+  return bf ? launch_persistent(encode_kernel<8, float, __nv_bfloat16>, smem, p, st, f32::NT)
+            : launch_persistent(encode_kernel<8, float, float>, smem, p, st, f32::NT);
+}
+
+extern "C" int octa_query_fwd(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
+                              float* rgb, int32_t* node_idx, int32_t* texel_addr,
+                              int32_t* status, void* stream) {
+  clear_error();
+  QueryParams p;
+  int rc = build_query_params(scenes, n_scenes, q, nullptr, p);
+  if (rc) return rc;
+  if (q->n > 0 && !rgb) return fail(OCTA_EINVAL, "rgb must be non-NULL");
+  if (texel_addr && (reinterpret_cast<uintptr_t>(texel_addr) & 15u))
+    return fail(OCTA_EINVAL, "texel_addr not 16-byte aligned");
+  int kmax = 0;
+  for (int s = 0; s < n_scenes; ++s) kmax = std::max(kmax, scenes[s].num_levels);
+  p.rgb = rgb;
+  p.node_idx = node_idx;
+  p.texel_addr = texel_addr;
+  p.kmax_out = kmax;
+  p.status = status;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (scenes[0].weight_dtype == OCTA_BF16) return tc::query_fwd(scenes, n_scenes, p, st);
+  return dispatch_engine(scenes, n_scenes, p, false, st);
+}
+
+extern "C" int octa_query_bwd(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
+                              const float* d_rgb, const octa_scene_grads* grads,
+                              int32_t* status, void* stream) {
+  clear_error();
+  if (!grads) return fail(OCTA_EINVAL, "grads must be non-NULL");
+  QueryParams p;
+  int rc = build_query_params(scenes, n_scenes, q, grads, p);
+  if (rc) return rc;
+  if (q->n > 0 && !d_rgb) return fail(OCTA_EINVAL, "d_rgb must be non-NULL");
+  p.d_rgb = d_rgb;
+  p.status = status;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (scenes[0].weight_dtype == OCTA_BF16) return tc::query_bwd(scenes, n_scenes, p, st);
+  return dispatch_engine(scenes, n_scenes, p, true, st);
+}

@@ -1,0 +1,262 @@
+// Training-side entry points: the residual loss (Eq. 3, Eq. 14) and the Adam
+// step with dynamic loss scaling.  Both reduce in FP64 (the loss value and
+// the gradient norm) through per-block partials in the caller's workspace;
+// the last block to finish sums the partials in block order, so results are
+// deterministic for a given launch shape.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "octa_internal.h"
+
+namespace octa {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxBlocks = 1024;
+// workspace layout: [kMaxBlocks] doubles of partials, then a 256-byte
+// aligned completion counter
+constexpr size_t kPartialBytes = sizeof(double) * kMaxBlocks;
+constexpr size_t kWorkspaceBytes = kPartialBytes + 256;
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 148;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+  return t;  // valid in thread 0
+}
+
+// Publishes this block's partial; returns true in thread 0 of the last block,
+// which then holds the ordered total in *total.
+__device__ __forceinline__ bool last_block_total(double mine, double* partials,
+                                                 unsigned* counter, double* total) {
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = mine;
+    __threadfence();
+    const unsigned done = atomicAdd(counter, 1u);
+    is_last = done == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last || threadIdx.x != 0) return false;
+  __threadfence();
+  double t = 0.0;
+  for (unsigned b = 0; b < gridDim.x; ++b) t += reinterpret_cast<volatile double*>(partials)[b];
+  *counter = 0;  // ready for the next call
+  *total = t;
+  return true;
+}
+
+// Eq. 14 per channel: T = E + w L_s, r = (L_p - T) / (L_p + T + eps), loss =
+// mean r^2; gradients of S * loss with the normaliser detached.
+__global__ void __launch_bounds__(kThreads) residual_loss_kernel(
+    const float* __restrict__ Lp, const float* __restrict__ Ls, const float* __restrict__ E,
+    const float* __restrict__ w, int64_t n3, float eps, int rhs_grad,
+    const octa_scaler* __restrict__ scaler, double* loss_dev, float* __restrict__ dLp,
+    float* __restrict__ dLs, double* partials, unsigned* counter) {
+  __shared__ double red[kThreads / 32];
+  const float S = scaler ? scaler->scale : 1.f;
+  const float gscale = 2.f * S / static_cast<float>(n3);
+  double acc = 0.0;
+  const int64_t stride = int64_t(gridDim.x) * kThreads;
+  for (int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x; i < n3; i += stride) {
+    const float lp = Lp[i], ls = Ls[i], ww = w[i];
+    const float T = E[i] + ww * ls;
+    const float den = lp + T + eps;
+    const float r = (lp - T) / den;
+    acc += double(r) * double(r);
+    const float g = gscale * r / den;
+    dLp[i] = g;
+    if (dLs) dLs[i] = rhs_grad ? -g * ww : 0.f;
+  }
+  const double bsum = block_sum(acc, red);
+  double total;
+  if (last_block_total(bsum, partials, counter, &total)) *loss_dev = total / double(n3);
+}
+
+struct AdamParams {
+  octa_param_group g[OCTA_MAX_GROUPS];
+  int32_t n_groups;
+  float beta1, beta2, eps;
+  octa_scaler* scaler;
+  double* partials;
+  unsigned* counter;
+};
+
+// Pass 1: FP64 sum of squares of the unscaled gradient; the last block takes
+// the skip / scale decision and advances the step count.
+__global__ void __launch_bounds__(kThreads) adam_norm_kernel(const __grid_constant__ AdamParams p) {
+  __shared__ double red[kThreads / 32];
+  const float inv_s = 1.f / p.scaler->scale;
+  double acc = 0.0;
+  const int64_t stride = int64_t(gridDim.x) * kThreads;
+  for (int gi = 0; gi < p.n_groups; ++gi) {
+    const float* __restrict__ g = p.g[gi].grad;
+    const int64_t n = p.g[gi].n;
+    for (int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x; i < n; i += stride) {
+      const double v = double(g[i] * inv_s);
+      acc += v * v;
+    }
+  }
+  const double bsum = block_sum(acc, red);
+  double total;
+  if (last_block_total(bsum, p.partials, p.counter, &total)) {
+    octa_scaler* s = p.scaler;
+    s->inv_scale_used = inv_s;
+    s->grad_norm = sqrt(total);
+    if (!isfinite(total)) {  // inf or NaN anywhere makes the sum non-finite
+      s->skipped = 1;
+      s->n_skipped += 1;
+      if (s->growth_interval > 0) {
+        s->scale *= 0.5f;
+        s->good_steps = 0;
+      }
+    } else {
+      s->skipped = 0;
+      s->step += 1;
+      if (s->growth_interval > 0 && ++s->good_steps >= s->growth_interval) {
+        s->scale *= 2.f;
+        s->good_steps = 0;
+      }
+    }
+  }
+}
+
+// Pass 2: Adam with bias correction (Kingma & Ba 2015) unless the step was
+// skipped; working copies refreshed; gradients zeroed either way.
+__global__ void __launch_bounds__(kThreads) adam_update_kernel(const __grid_constant__ AdamParams p) {
+  const octa_scaler* s = p.scaler;
+  const bool skip = s->skipped != 0;
+  const float inv_s = s->inv_scale_used;
+  const double t = double(s->step);
+  const float bc1 = static_cast<float>(1.0 - pow(double(p.beta1), t));
+  const float bc2 = static_cast<float>(1.0 - pow(double(p.beta2), t));
+  const float b1 = p.beta1, b2 = p.beta2, eps = p.eps;
+  const int64_t stride = int64_t(gridDim.x) * kThreads;
+  for (int gi = 0; gi < p.n_groups; ++gi) {
+    const octa_param_group& G = p.g[gi];
+    for (int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x; i < G.n; i += stride) {
+      const float g = G.grad[i] * inv_s;
+      G.grad[i] = 0.f;
+      if (skip) continue;
+      const float m = b1 * G.m[i] + (1.f - b1) * g;
+      const float v = b2 * G.v[i] + (1.f - b2) * g * g;
+      G.m[i] = m;
+      G.v[i] = v;
+      const float mhat = m / bc1, vhat = v / bc2;
+      const float pv = G.param[i] - G.lr * mhat / (sqrtf(vhat) + eps);
+      G.param[i] = pv;
+      if (G.work) {
+        if (G.work_dtype == OCTA_F16)
+          static_cast<__half*>(G.work)[i] = __float2half_rn(pv);
+        else
+          static_cast<__nv_bfloat16*>(G.work)[i] = __float2bfloat16_rn(pv);
+      }
+    }
+  }
+}
+
+int check_workspace(void* ws, size_t bytes) {
+  if (!ws) return fail(OCTA_EINVAL, "workspace must be non-NULL");
+  if (reinterpret_cast<uintptr_t>(ws) & 255u)
+    return fail(OCTA_EINVAL, "workspace must be 256-byte aligned");
+  if (bytes < kWorkspaceBytes)
+    return fail(OCTA_EINVAL, "workspace of %zu bytes < %zu", bytes, kWorkspaceBytes);
+  return OCTA_OK;
+}
+
+int launched(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  return OCTA_OK;
+}
+
+}  // namespace
+}  // namespace octa
+
+using namespace octa;
+
+extern "C" size_t octa_workspace_bytes(int32_t op, int64_t n) {
+  (void)n;
+  if (op == OCTA_OP_LOSS || op == OCTA_OP_ADAM) return kWorkspaceBytes;
+  return 0;
+}
+
+extern "C" int residual_loss(const float* L_p, const float* L_s, const float* E, const float* w,
+                             int64_t n_pairs, float eps, int32_t rhs_grad,
+                             const octa_scaler* scaler, double* loss_dev, float* dL_p,
+                             float* dL_s, void* workspace, size_t workspace_bytes,
+                             void* stream) {
+  clear_error();
+  if (n_pairs < 1) return fail(OCTA_EINVAL, "n_pairs must be >= 1");
+  if (!L_p || !L_s || !E || !w || !loss_dev || !dL_p)
+    return fail(OCTA_EINVAL, "NULL array argument");
+  if (rhs_grad && !dL_s) return fail(OCTA_EINVAL, "dL_s must be non-NULL when rhs_grad");
+  if (!(eps > 0.f)) return fail(OCTA_EINVAL, "eps must be > 0");
+  int rc = check_workspace(workspace, workspace_bytes);
+  if (rc) return rc;
+  const int64_t n3 = 3 * n_pairs;
+  const int blocks = static_cast<int>(
+      std::min<int64_t>({(n3 + kThreads - 1) / kThreads, int64_t(kMaxBlocks), 4LL * sm_count()}));
+  double* partials = static_cast<double*>(workspace);
+  unsigned* counter = reinterpret_cast<unsigned*>(static_cast<char*>(workspace) + kPartialBytes);
+  residual_loss_kernel<<<blocks, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      L_p, L_s, E, w, n3, eps, rhs_grad, scaler, loss_dev, dL_p, dL_s, partials, counter);
+  return launched("residual_loss");
+}
+
+extern "C" int adam_step(const octa_param_group* groups, int32_t n_groups,
+                         const octa_adam_cfg* cfg, octa_scaler* scaler, void* workspace,
+                         size_t workspace_bytes, void* stream) {
+  clear_error();
+  if (!groups || !cfg || !scaler) return fail(OCTA_EINVAL, "NULL argument");
+  if (n_groups < 1 || n_groups > OCTA_MAX_GROUPS)
+    return fail(OCTA_ERANGE, "n_groups %d outside [1, %d]", n_groups, OCTA_MAX_GROUPS);
+  if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f &&
+        cfg->eps >= 0.f))
+    return fail(OCTA_EINVAL, "Adam hyper-parameters out of range");
+  int rc = check_workspace(workspace, workspace_bytes);
+  if (rc) return rc;
+  AdamParams p{};
+  int64_t total = 0;
+  for (int i = 0; i < n_groups; ++i) {
+    const octa_param_group& g = groups[i];
+    if (g.n < 0) return fail(OCTA_EINVAL, "group %d: negative size", i);
+    if (g.n > 0 && (!g.param || !g.grad || !g.m || !g.v))
+      return fail(OCTA_EINVAL, "group %d: NULL array", i);
+    if (g.work && g.work_dtype != OCTA_F16 && g.work_dtype != OCTA_BF16)
+      return fail(OCTA_EINVAL, "group %d: working copy dtype must be F16 or BF16", i);
+    p.g[i] = g;
+    total += g.n;
+  }
+  p.n_groups = n_groups;
+  p.beta1 = cfg->beta1;
+  p.beta2 = cfg->beta2;
+  p.eps = cfg->eps;
+  p.scaler = scaler;
+  p.partials = static_cast<double*>(workspace);
+  p.counter = reinterpret_cast<unsigned*>(static_cast<char*>(workspace) + kPartialBytes);
+  const int blocks = static_cast<int>(std::max<int64_t>(
+      1, std::min<int64_t>({(total + kThreads - 1) / kThreads, int64_t(kMaxBlocks),
+                            4LL * sm_count()})));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  adam_norm_kernel<<<blocks, kThreads, 0, st>>>(p);
+  rc = launched("adam_step (norm)");
+  if (rc) return rc;
+  adam_update_kernel<<<blocks, kThreads, 0, st>>>(p);
+  return launched("adam_step (update)");
+}

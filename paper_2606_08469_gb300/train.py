@@ -1,0 +1,98 @@
+"""One neural-radiosity training step through the C ABI.
+
+A step queries L_hat at every primary (x, omega) and secondary (x', -omega')
+(Eq. 2 gives the sign), evaluates the Eq. 14 residual against the one-sample
+target of Eq. 3, back-propagates into the feature tables and the decoder and
+applies Adam with dynamic loss scaling.  Each of these is one library call on
+the caller's stream; the sequence can be captured in a CUDA graph.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib as L
+from . import api
+
+
+class SceneState:
+    """Master parameters, gradients, Adam moments and working copies of one scene."""
+
+    def __init__(self, tree, tables, weights, table_dtype, weight_dtype, device):
+        dev = torch.device(device)
+        self.master_t = torch.as_tensor(tables, dtype=torch.float32).to(dev).contiguous()
+        self.master_w = torch.cat([torch.as_tensor(W, dtype=torch.float32).reshape(-1)
+                                   for W in weights]).to(dev).contiguous()
+        self.grad_t = torch.zeros_like(self.master_t)
+        self.grad_w = torch.zeros_like(self.master_w)
+        self.m_t = torch.zeros_like(self.master_t)
+        self.v_t = torch.zeros_like(self.master_t)
+        self.m_w = torch.zeros_like(self.master_w)
+        self.v_w = torch.zeros_like(self.master_w)
+        self.work_t = None if table_dtype == torch.float32 else self.master_t.to(table_dtype)
+        self.work_w = None if weight_dtype == torch.float32 else self.master_w.to(weight_dtype)
+        shaped = [torch.empty(W.shape) for W in weights]
+        self.scene = api.Scene(tree, self.work_t if self.work_t is not None else self.master_t,
+                               shaped, device=dev)
+        self.scene.set_weights_flat(self.work_w if self.work_w is not None else self.master_w)
+
+    def groups(self, lr_tables, lr_mlp):
+        return [api.ParamGroup(self.master_t, self.grad_t, self.m_t, self.v_t, lr_tables, self.work_t),
+                api.ParamGroup(self.master_w, self.grad_w, self.m_w, self.v_w, lr_mlp, self.work_w)]
+
+
+class TrainStep:
+    """Training step over one or several scenes (queries ordered scene by
+    scene, each scene's primaries followed by its secondaries)."""
+
+    def __init__(self, scene_states, pairs, eps=1e-2, rhs_grad=True, lr_tables=1e-2, lr_mlp=1e-3,
+                 scale=2.0 ** 15, growth_interval=2000, device="cuda"):
+        dev = torch.device(device)
+        self.states = scene_states
+        self.scenes = [s.scene for s in scene_states]
+        self.n = [int(p["x"].shape[0]) for p in pairs]
+        xs, oms, Es, ws = [], [], [], []
+        for p in pairs:
+            xs += [p["x"], p["x2"]]
+            oms += [p["omega"], -p["omega2"]]
+            Es.append(p["E"])
+            ws.append(p["w"])
+        self.X = torch.cat(xs).to(dev).contiguous()
+        self.Om = torch.cat(oms).to(dev).contiguous()
+        self.E = [e.to(dev).contiguous() for e in Es]
+        self.w = [w.to(dev).contiguous() for w in ws]
+        self.counts = [2 * n for n in self.n]
+        total = sum(self.counts)
+        self.rgb = torch.empty((total, 3), dtype=torch.float32, device=dev)
+        self.d_rgb = torch.zeros((total, 3), dtype=torch.float32, device=dev)
+        self.loss = torch.zeros(len(self.n), dtype=torch.float64, device=dev)
+        self.scaler = api.make_scaler(scale, growth_interval, device=dev)
+        self.ws_loss = api.workspace(L.OCTA_OP_LOSS, max(self.n), device=dev)
+        self.ws_adam = api.workspace(L.OCTA_OP_ADAM, 0, device=dev)
+        self.eps, self.rhs_grad = eps, rhs_grad
+        self.groups = [g for s in scene_states for g in s.groups(lr_tables, lr_mlp)]
+        self.grads = [(s.grad_t, s.grad_w) for s in scene_states]
+
+    def forward(self, stream=None):
+        api.octa_query_fwd(self.scenes, self.X, self.Om, self.counts, rgb=self.rgb, stream=stream)
+
+    def loss_and_grad(self, stream=None):
+        off = 0
+        for s, n in enumerate(self.n):
+            api.residual_loss(self.rgb[off:off + n], self.rgb[off + n:off + 2 * n], self.E[s],
+                              self.w[s], self.d_rgb[off:off + n], self.d_rgb[off + n:off + 2 * n],
+                              self.loss[s:s + 1], self.ws_loss, self.eps, self.rhs_grad,
+                              self.scaler, stream=stream)
+            off += 2 * n
+
+    def backward(self, stream=None):
+        api.octa_query_bwd(self.scenes, self.X, self.Om, self.d_rgb, self.grads, self.counts,
+                           stream=stream)
+
+    def optimizer(self, stream=None):
+        api.adam_step(self.groups, self.scaler, self.ws_adam, stream=stream)
+
+    def step(self, stream=None):
+        self.forward(stream)
+        self.loss_and_grad(stream)
+        self.backward(stream)
+        self.optimizer(stream)

@@ -1,0 +1,95 @@
+"""Assemble the synthetic workloads (seeded inputs + octree + parameters) on
+the device, for tests, the benchmark and the smoke check."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import api
+from . import inputs as I
+from .train import SceneState, TrainStep
+
+_TORCH_DT = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+
+
+def table_dtype(cfg):
+    return _TORCH_DT[cfg.table_dtype]
+
+
+def weight_dtype(cfg):
+    return _TORCH_DT[cfg.weight_dtype]
+
+
+def host_params(cfg, tree_seed=None, tables_seed=None, mlp_seed=None):
+    """Host tree (library builder) plus FP32 master tables and weights."""
+    tree = api.octree_build(cfg.seed("tree") if tree_seed is None else tree_seed, cfg.max_depth,
+                            cfg.p_base, cfg.R)
+    tables = I.make_tables(cfg.seed("tables") if tables_seed is None else tables_seed,
+                           tree.num_texels, cfg.F, cfg.sigma)
+    widths = [tree.num_levels * cfg.F] + list(cfg.widths[1:])
+    weights = I.make_mlp(cfg.seed("mlp") if mlp_seed is None else mlp_seed, widths)
+    return tree, tables, weights
+
+
+def pairs_on_device(pairs, device="cuda"):
+    return {k: torch.from_numpy(getattr(pairs, k)).to(device)
+            for k in ("x", "omega", "x2", "omega2", "E", "w")}
+
+
+def train_step_for(cfg, n_pairs=None, device="cuda", precision=None, **kw):
+    """TrainStep of a 'pairs' workload.  precision='f32' forces the FP32 path
+    on the same shapes (FP32 tables and weights)."""
+    tree, tables, weights = host_params(cfg)
+    tdt, wdt = table_dtype(cfg), weight_dtype(cfg)
+    if precision == "f32":
+        tdt = wdt = torch.float32
+    st = SceneState(tree, tables, weights, tdt, wdt, device)
+    n = cfg.n if n_pairs is None else n_pairs
+    pairs = I.training_pairs(cfg.seed("queries"), n)
+    return TrainStep([st], [pairs_on_device(pairs, device)], **kw), (tree, tables, weights, pairs)
+
+
+def batched_train_step(device="cuda", counts=None, precision=None, **kw):
+    cfg = I.CONFIGS[4]
+    counts = I.batched_pair_counts(cfg) if counts is None else counts
+    states, plist, host = [], [], []
+    for s, n in enumerate(counts):
+        sc = I.batched_scene_config(s, cfg)
+        tree = api.octree_build(I.batched_seed(s, "tree"), sc.max_depth, sc.p_base, sc.R)
+        tables = I.make_tables(I.batched_seed(s, "tables"), tree.num_texels, sc.F, sc.sigma)
+        weights = I.make_mlp(I.batched_seed(s, "mlp"), [tree.num_levels * sc.F, 64, 64, 3])
+        tdt, wdt = table_dtype(sc), weight_dtype(sc)
+        if precision == "f32":
+            tdt = wdt = torch.float32
+        states.append(SceneState(tree, tables, weights, tdt, wdt, device))
+        pairs = I.training_pairs(I.batched_seed(s, "queries"), n)
+        plist.append(pairs_on_device(pairs, device))
+        host.append((tree, tables, weights, pairs))
+    return TrainStep(states, plist, **kw), host
+
+
+def forward_scene(cfg, device="cuda", precision=None):
+    """Device scene of a forward workload (tables/weights in the config's
+    precision, or FP32 with precision='f32')."""
+    tree, tables, weights = host_params(cfg)
+    tdt, wdt = table_dtype(cfg), weight_dtype(cfg)
+    if precision == "f32":
+        tdt = wdt = torch.float32
+    T = torch.from_numpy(tables).to(device).to(tdt).contiguous()
+    Ws = [torch.from_numpy(W).to(device).to(wdt) for W in weights]
+    return api.Scene(tree, T, Ws, device=device), (tree, tables, weights)
+
+
+def queries_for(cfg, n=None):
+    """Host (x, omega) of a forward workload."""
+    if cfg.kind == "uniform":
+        return I.uniform_queries(cfg.seed("queries"), cfg.n if n is None else n)
+    if cfg.kind == "gbuffer":
+        w, h = cfg.extra["width"], cfg.extra["height"]
+        return I.gbuffer_queries(cfg.seed("queries"), w, h)
+    pairs = I.training_pairs(cfg.seed("queries"), cfg.n if n is None else n)
+    return pairs.x, pairs.omega
+
+
+def to_dev(a, device="cuda"):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device)

@@ -1,0 +1,177 @@
+"""GPU parity of the training-side entry points (residual_loss, adam_step,
+dynamic loss scaling) and of a whole FP32 training step, against the oracle."""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import octaoctree_oracle as O
+from paper_2606_08469_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2606_08469_gb300 import build
+    build.build()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.mark.parametrize("rhs_grad,n", [(True, 1), (True, 100003), (False, 4096)])
+def test_residual_loss_matches_oracle(rhs_grad, n):
+    from paper_2606_08469_gb300 import api as A
+    from paper_2606_08469_gb300 import _lib as L
+    g = np.random.default_rng(n)
+    Lp, Ls = (g.uniform(0.2, 3.0, size=(n, 3)).astype(np.float32) for _ in range(2))
+    E = (g.random((n, 3)) * (g.random((n, 1)) < 0.05)).astype(np.float32)
+    w = g.random((n, 3)).astype(np.float32)
+    scaler = A.make_scaler(2.0 ** 15, 2000)
+    dLp = torch.empty((n, 3), device=DEV)
+    dLs = torch.full((n, 3), 7.0, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+    ws = A.workspace(L.OCTA_OP_LOSS, n)
+    for _ in range(2):                         # the workspace is reusable
+        A.residual_loss(dev(Lp), dev(Ls), dev(E), dev(w), dLp, dLs, loss, ws, 1e-2, rhs_grad, scaler)
+    rl, rdp, rds = O.residual_loss(Lp, Ls, E, w, 1e-2, rhs_grad, 2.0 ** 15)
+    assert abs(loss.item() - rl) <= 1e-6 * rl
+    np.testing.assert_allclose(dLp.cpu().numpy(), rdp, rtol=2e-5, atol=1e-7 * np.abs(rdp).max())
+    np.testing.assert_allclose(dLs.cpu().numpy(), rds, rtol=2e-5, atol=1e-7 * np.abs(rdp).max())
+
+
+def test_adam_matches_oracle_and_scaler():
+    from paper_2606_08469_gb300 import api as A
+    from paper_2606_08469_gb300 import _lib as L
+    g = np.random.default_rng(0)
+    n1, n2 = 1000, 37
+    p1 = g.normal(size=n1).astype(np.float32)
+    p2 = g.normal(size=n2).astype(np.float32)
+    P1, P2 = dev(p1), dev(p2)
+    G1, G2 = torch.zeros(n1, device=DEV), torch.zeros(n2, device=DEV)
+    M1, V1, M2, V2 = (torch.zeros(n, device=DEV) for n in (n1, n1, n2, n2))
+    W1 = torch.zeros(n1, dtype=torch.float16, device=DEV)
+    W2 = torch.zeros(n2, dtype=torch.bfloat16, device=DEV)
+    groups = [A.ParamGroup(P1, G1, M1, V1, 1e-2, W1), A.ParamGroup(P2, G2, M2, V2, 1e-3, W2)]
+    S = 2.0 ** 15
+    scaler = A.make_scaler(S, growth_interval=2)
+    ws = A.workspace(L.OCTA_OP_ADAM, n1 + n2)
+    r1, r2 = p1.astype(np.float64), p2.astype(np.float64)
+    m1 = v1 = np.zeros(n1)
+    m2 = v2 = np.zeros(n2)
+    t = 0
+    scales = [S]
+    for step in range(5):
+        g1 = g.normal(size=n1).astype(np.float32)
+        g2 = g.normal(size=n2).astype(np.float32)
+        inject = step == 2
+        if inject:
+            g2[5] = np.inf                     # host-injected overflow
+        G1.copy_(dev(g1 * np.float32(scales[-1])))
+        G2.copy_(dev(g2 * np.float32(scales[-1])))
+        A.adam_step(groups, scaler, ws)
+        st = A.read_scaler(scaler)
+        assert st.skipped == int(inject)
+        assert torch.count_nonzero(G1).item() == 0 and torch.count_nonzero(G2).item() == 0
+        if not inject:
+            t += 1
+            r1, m1, v1 = O.adam_update(r1, g1, m1, v1, t, 1e-2)
+            r2, m2, v2 = O.adam_update(r2, g2, m2, v2, t, 1e-3)
+            assert abs(st.grad_norm - np.sqrt(np.sum(g1.astype(np.float64) ** 2) +
+                                              np.sum(g2.astype(np.float64) ** 2))) < 1e-5 * st.grad_norm
+        assert st.step == t
+        scales.append(st.scale)
+        np.testing.assert_allclose(P1.cpu().numpy(), r1, rtol=0, atol=2e-6)
+        np.testing.assert_allclose(P2.cpu().numpy(), r2, rtol=0, atol=2e-6)
+        np.testing.assert_array_equal(W1.cpu().numpy(), P1.cpu().numpy().astype(np.float16))
+    # trajectory: finite, finite -> grow, overflow -> halve, finite, finite -> grow
+    ref = O.LossScaler(S, growth_interval=2)
+    want = [S]
+    for step in range(5):
+        ref.update(step != 2)
+        want.append(ref.scale)
+    assert scales == want
+
+
+def _oracle_state(tables, weights):
+    T = tables.astype(np.float64)
+    Ws = [W.astype(np.float64) for W in weights]
+    return O.TrainState(T, Ws, np.zeros_like(T), np.zeros_like(T), [np.zeros_like(w) for w in Ws],
+                        [np.zeros_like(w) for w in Ws])
+
+
+def test_train_step_matches_oracle():
+    """Two full FP32 steps (fwd, loss, bwd, Adam + scaler) of config-1 shapes
+    on 4096 pairs vs the oracle's step."""
+    from paper_2606_08469_gb300 import api as A
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[1]
+    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=4096)
+    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    st = _oracle_state(tables, weights)
+    scaler = O.LossScaler()
+    for _ in range(2):
+        step.step()
+        torch.cuda.synchronize()
+        loss, gn, skipped = O.train_step(ot, st, pairs, scaler)
+        sc = A.read_scaler(step.scaler)
+        assert not skipped and sc.skipped == 0
+        assert abs(step.loss.item() - loss) <= 1e-5 * loss
+        assert abs(sc.grad_norm - gn) <= 1e-4 * gn
+        np.testing.assert_allclose(step.states[0].master_t.cpu().numpy(), st.tables, rtol=0,
+                                   atol=1e-2 * 1e-3)
+        W = np.concatenate([w.reshape(-1) for w in st.weights])
+        np.testing.assert_allclose(step.states[0].master_w.cpu().numpy(), W, rtol=0, atol=1e-3 * 1e-3)
+
+
+def test_train_step_full_config1_loss_and_samples():
+    """The full 262,144-pair config-1 step on the GPU: the forward on sampled
+    queries and the loss value of the whole batch vs the oracle."""
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[1]
+    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg)
+    step.forward()
+    step.loss_and_grad()
+    torch.cuda.synchronize()
+    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    N = pairs.n
+    X = np.concatenate([pairs.x, pairs.x2])
+    Om = np.concatenate([pairs.omega, -pairs.omega2])
+    rgb = step.rgb.cpu().numpy()
+    idx = np.random.default_rng(0).choice(2 * N, 4096, replace=False)
+    ref, _ = O.query_forward(ot, tables, weights, X[idx], Om[idx])
+    assert np.max(np.abs(rgb[idx] - ref) / ref) <= 1e-5
+    ref_all, _ = O.query_forward(ot, tables, weights, X, Om)
+    loss, _, _ = O.residual_loss(ref_all[:N], ref_all[N:], pairs.E, pairs.w)
+    assert abs(step.loss.item() - loss) <= 1e-5 * loss
+    step.backward()
+    step.optimizer()
+    torch.cuda.synchronize()
+    assert torch.isfinite(step.states[0].master_t).all()
+
+
+def test_train_step_graph_replay_equals_eager():
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[1]
+    a, _ = WL.train_step_for(cfg, n_pairs=8192)
+    b, _ = WL.train_step_for(cfg, n_pairs=8192)
+    a.step()                                   # eager warm-up of every kernel
+    b.step()
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            b.step()
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(3):
+        a.step()
+        graph.replay()
+    torch.cuda.synchronize()
+    torch.testing.assert_close(a.states[0].master_t, b.states[0].master_t, rtol=1e-5, atol=1e-6)
+    torch.testing.assert_close(a.loss, b.loss, rtol=1e-6, atol=0)

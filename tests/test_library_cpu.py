@@ -1,0 +1,113 @@
+"""CPU-only checks of the C-ABI library: it loads, exports every symbol the
+header declares, and its host-only octree builder matches the oracle's
+independent rebuild bit for bit.  No GPU compute is called here."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import octaoctree_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_08469_gb300 import build
+    build.build()
+    from paper_2606_08469_gb300 import _lib
+    return _lib.load()
+
+
+def _declared_functions():
+    txt = open(os.path.join(ROOT, "include", "octaoctree.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w \t\*]*?\b([a-z_][a-z0-9_]*)\s*\([^;{]*\)\s*;", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_symbols_exported(lib):
+    names = _declared_functions()
+    assert {"octree_build", "octa_query_fwd", "octa_query_bwd", "residual_loss",
+            "adam_step"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2606_08469_gb300 import _lib
+    assert set(_lib._SIGNATURES) >= set(names)
+
+
+def test_struct_sizes_match_header(lib):
+    """The ctypes mirrors have the C layout (checked through a sizing call)."""
+    from paper_2606_08469_gb300 import _lib as L
+    assert C.sizeof(L.octa_tree_desc) == 4 + 4 + 8 + 4 * 16 + 4 * 17 + 4 + 8 * 17
+    assert lib.octa_abi_version() == 1
+
+
+@pytest.mark.parametrize("seed,depth,R", [
+    (1000, 4, [16, 16, 8, 8, 8]),
+    (1001, 6, [32, 32, 16, 16, 8, 8, 8]),
+    (1002, 8, [64, 64, 32, 32, 16, 16, 8, 8, 8]),
+    (1403, 7, [64, 64, 32, 32, 16, 16, 8, 8]),
+    (1407, 9, [64, 64, 32, 32, 16, 16, 8, 8, 8, 8]),
+    (0, 0, [4]),
+])
+def test_octree_build_matches_oracle(lib, seed, depth, R):
+    from paper_2606_08469_gb300 import api
+    t = api.octree_build(seed, depth, 0.6, R)
+    o = O.build_tree(seed, depth, 0.6, R)
+    assert t.num_nodes == o.num_nodes and t.num_texels == o.num_texels
+    np.testing.assert_array_equal(t.first_child, o.first_child)
+    np.testing.assert_array_equal(t.node_coord, o.node_coord)
+    np.testing.assert_array_equal(t.map_offset, o.map_offset)
+    np.testing.assert_array_equal(t.level_node_start, o.level_node_start)
+    np.testing.assert_array_equal(t.level_texel_base, o.level_texel_base)
+
+
+def test_octree_dense_and_flags(lib):
+    from paper_2606_08469_gb300 import api
+    t = api.octree_build(5, 3, 1.0, [2, 2, 2, 2])     # p = 1: full octree
+    assert t.num_nodes == 1 + 8 + 64 + 512
+    flags = [1, 0, 0, 1, 0, 0, 0, 0, 0]
+    t = api.octree_from_flags(flags, 2, [4, 2, 2])
+    o = O.tree_from_flags(flags, 2, [4, 2, 2])
+    np.testing.assert_array_equal(t.first_child, o.first_child)
+    np.testing.assert_array_equal(t.map_offset, o.map_offset)
+    t = api.octree_from_flags([], 3, [2, 2, 2, 2])     # root only
+    assert t.num_nodes == 1 and t.num_texels == 4
+
+
+def test_octree_errors(lib):
+    from paper_2606_08469_gb300 import _lib as L
+    desc = L.octa_tree_desc()
+    R = (C.c_int32 * 3)(4, 1, 4)
+    assert lib.octree_build(1, 2, 0.6, R, C.byref(desc), None, None, None) == L.OCTA_ERANGE
+    assert b"R[1]" in lib.octa_last_error()
+    R = (C.c_int32 * 3)(4, 4, 4)
+    assert lib.octree_build(1, 2, 1.5, R, C.byref(desc), None, None, None) == L.OCTA_EINVAL
+    assert lib.octree_build(1, 16, 0.5, R, C.byref(desc), None, None, None) == L.OCTA_ERANGE
+    assert lib.octree_build(1, 2, 0.5, None, C.byref(desc), None, None, None) == L.OCTA_EINVAL
+    assert lib.octree_build(1, 2, 0.5, R, C.byref(desc), None, None, None) == L.OCTA_OK
+    assert lib.octree_from_flags(None, 3, 2, R, C.byref(desc), None, None, None) == L.OCTA_EINVAL
+
+
+def test_query_validation_without_gpu(lib):
+    """Argument checks run on the host before any launch."""
+    from paper_2606_08469_gb300 import _lib as L
+    q = L.octa_queries()
+    q.n = 0
+    s = L.octa_scene()
+    # NULL scenes / queries
+    assert lib.octa_query_fwd(None, 1, C.byref(q), None, None, None, None, None) == L.OCTA_EINVAL
+    # zero scenes
+    assert lib.octa_query_fwd(C.byref(s), 0, C.byref(q), None, None, None, None, None) == L.OCTA_ERANGE
+    # scene with NULL arrays
+    q.scene_start[1] = 0
+    assert lib.octa_query_fwd(C.byref(s), 1, C.byref(q), None, None, None, None, None) == L.OCTA_EINVAL
+    assert b"NULL" in lib.octa_last_error()
+    # residual_loss: bad sizes and NULLs
+    assert lib.residual_loss(None, None, None, None, 0, C.c_float(0.01), 1, None, None, None, None,
+                             None, 0, None) == L.OCTA_EINVAL
+    assert lib.octa_workspace_bytes(L.OCTA_OP_LOSS, 100) >= 8 * 1024
+    assert lib.octa_workspace_bytes(99, 100) == 0
