@@ -167,7 +167,7 @@ def run_ours(args):
     from paper_2606_08469_gb300 import workloads as WL
 
     cfg = I.CONFIGS[1]
-    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, device=dev)
+    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=args.pairs, device=dev)
     n_q = 2 * pairs.n
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
@@ -277,7 +277,7 @@ def run_ours(args):
             "data": "synthetic (seeded octree, features, MLP, surface samples; no scene assets)",
             "config": {"workload": "config[1] FP32 training step: depth-6 seeded octree "
                                    f"({tree.num_nodes} nodes, R 32..8, F=8 FP32), decoder 56-64-64-3, "
-                                   f"262144 pairs = {n_q} queries per step (fwd, Eq.14 loss, bwd, Adam)",
+                                   f"{pairs.n} pairs = {n_q} queries per step (fwd, Eq.14 loss, bwd, Adam)",
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": f"replicas x{world}"},
             "fwd_only": {"value": round(world * n_q / (statistics.mean(fwd_ms) / 1e3) / 1e6, 3),
@@ -335,6 +335,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--pairs", type=int, default=262144,
+                    help="training pairs per step (smaller values only for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

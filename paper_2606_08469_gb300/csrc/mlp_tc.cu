@@ -1,15 +1,313 @@
-// Tensor-core (tcgen05) decoder path.  Placeholder until the kernels land.
+// BF16 tensor-core path of the query: the decoder (Eq. 13) runs on the
+// tcgen05 tensor cores with FP32 accumulation in tensor memory.
+//
+// One CTA of 128 threads owns a tile of 128 queries (one query per thread
+// and per tensor-memory lane).  Per tile:
+//   locate   fold omega and walk the octree (one thread per query);
+//   gather   one thread per (query, level): bilinear blend in FP32 of the 4
+//            wrapped texels, rounded to BF16 and stored as one 16-byte row of
+//            a core matrix of the canonical K-major operand tile (the level
+//            concatenation of Eq. 11 is the K index);
+//   decoder  per layer one elected thread issues K/16 MMAs of 128 x N x 16
+//            (A = activations, B = the layer's weights, both in shared
+//            memory), commits to an mbarrier; after the bounded wait every
+//            thread pulls its row of the accumulator from tensor memory,
+//            applies ReLU, rounds to BF16 and writes the next A tile.  The
+//            last layer (N padded to 16) ends in exp().
+// Several CTAs share an SM (64 tensor-memory columns each), so one CTA's
+// gather overlaps another's MMAs.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "engine_f32.cuh"
 #include "octa_internal.h"
 #include "tc_path.h"
+#include "tc_ptx.cuh"
 
 namespace octa {
 namespace tc {
 
-int query_fwd(const octa_scene*, int, const QueryParams&, cudaStream_t) {
-  return fail(OCTA_EUNSUPPORTED, "BF16 tensor-core path not built yet");
+constexpr int NT = 128;   // threads per CTA = queries per tile
+constexpr int NOUT = 16;  // padded output width of the last layer
+
+template <int F_, int WP_, int H_, int NH_>
+struct Shape {
+  static constexpr int F = F_, WP = WP_, H = H_, NH = NH_, NL = NH_ + 1;
+  static constexpr int KPAD = WP / F;
+  static constexpr int AK = WP > H ? WP : H;
+  static_assert(WP % 16 == 0 && H % 16 == 0 && H <= 128, "MMA shapes");
+  static constexpr uint32_t W0_BYTES = H * WP * 2;
+  static constexpr uint32_t WH_BYTES = H * H * 2;
+  static constexpr uint32_t WL_BYTES = NOUT * H * 2;
+  static constexpr uint32_t W_BYTES = W0_BYTES + (NH - 1) * WH_BYTES + WL_BYTES;
+  static constexpr uint32_t ACT_BYTES = NT * AK * 2;
+  static constexpr uint32_t NODE_BYTES = KPAD * NT * 4;
+  static constexpr uint32_t U_BYTES = 2 * NT * 4;
+  static constexpr uint32_t OFF_ACT = W_BYTES;
+  static constexpr uint32_t OFF_NODE = OFF_ACT + ACT_BYTES;
+  static constexpr uint32_t OFF_U = OFF_NODE + NODE_BYTES;
+  static constexpr uint32_t OFF_BAR = (OFF_U + U_BYTES + 15) & ~15u;
+  static constexpr size_t SMEM = OFF_BAR + 16;
+  static constexpr uint32_t TMEM_COLS = H <= 32 ? 32 : (H <= 64 ? 64 : 128);
+  __host__ __device__ static constexpr uint32_t w_off(int layer) {
+    return layer == 0 ? 0u : W0_BYTES + static_cast<uint32_t>(layer - 1) * WH_BYTES;
+  }
+  __host__ __device__ static constexpr int kdim(int layer) { return layer == 0 ? WP : H; }
+  __host__ __device__ static constexpr int ndim(int layer) { return layer == NL - 1 ? NOUT : H; }
+};
+
+// Weights of one scene into shared memory, canonical K-major, zero padded.
+template <class S>
+__device__ void load_weights_bf16(const DevScene& sc, uint8_t* smem) {
+  const __nv_bfloat16* Wg = static_cast<const __nv_bfloat16*>(sc.weights);
+#pragma unroll 1
+  for (int l = 0; l < S::NL; ++l) {
+    const int K = S::kdim(l), N = S::ndim(l);
+    const int in = sc.widths[l], out = sc.widths[l + 1];
+    __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(smem + S::w_off(l));
+    for (int i = threadIdx.x; i < N * K; i += NT) {
+      const int n = i / K, k = i % K;
+      const __nv_bfloat16 v =
+          (n < out && k < in) ? Wg[sc.w_offset[l] + n * in + k] : __float2bfloat16_rn(0.f);
+      dst[kmajor_offset(n, k, K) / 2] = v;
+    }
+  }
 }
+
+// Gather into the layer-0 operand tile (row q, columns l*F .. l*F+F-1).
+template <class S, typename TT>
+__device__ __forceinline__ void gather_bf16(const QueryParams& p, const DevScene& sc, int64_t q0,
+                                            int nq, const int* node_sm, const float* u_sm,
+                                            uint8_t* act) {
+  constexpr int F = S::F;
+  for (int it = threadIdx.x; it < S::KPAD * NT; it += NT) {
+    const int l = it / NT, q = it % NT;  // l is warp-uniform
+    const int node = node_sm[l * NT + q];
+    float v[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) v[f] = 0.f;
+    int64_t a4[4] = {-1, -1, -1, -1};
+    if (node >= 0) {
+      const int R = sc.R[l];
+      const int64_t mo = f32::map_base(p, sc, node, R);
+      if (mo >= 0) {
+        const Footprint fp = footprint(u_sm[q], u_sm[NT + q], R);
+        float t[4][F];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          a4[k] = mo + fp.idx[k];
+          TexelLoad<TT, F>::load(sc.tables, a4[k], t[k]);
+        }
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+          float s = fp.w[0] * t[0][f];
+          s = fmaf(fp.w[1], t[1][f], s);
+          s = fmaf(fp.w[2], t[2][f], s);
+          s = fmaf(fp.w[3], t[3][f], s);
+          v[f] = s;
+        }
+      }
+    }
+    uint8_t* dst = act + kmajor_offset(q, l * F, S::WP);
+    if constexpr (F == 8) {
+      uint4 o;
+      o.x = pack_bf16x2(v[0], v[1]);
+      o.y = pack_bf16x2(v[2], v[3]);
+      o.z = pack_bf16x2(v[4], v[5]);
+      o.w = pack_bf16x2(v[6], v[7]);
+      *reinterpret_cast<uint4*>(dst) = o;
+    } else {
+      uint2 o;
+      o.x = pack_bf16x2(v[0], v[1]);
+      o.y = pack_bf16x2(v[2], v[3]);
+      *reinterpret_cast<uint2*>(dst) = o;
+    }
+    if (p.texel_addr && q < nq && l < p.kmax_out) {
+      *reinterpret_cast<int4*>(p.texel_addr + ((q0 + q) * p.kmax_out + l) * 4) =
+          make_int4(int(a4[0]), int(a4[1]), int(a4[2]), int(a4[3]));
+    }
+  }
+  if (p.texel_addr && p.kmax_out > S::KPAD) {
+    for (int it = threadIdx.x; it < (p.kmax_out - S::KPAD) * NT; it += NT) {
+      const int l = S::KPAD + it / NT, q = it % NT;
+      if (q < nq)
+        *reinterpret_cast<int4*>(p.texel_addr + ((q0 + q) * p.kmax_out + l) * 4) =
+            make_int4(-1, -1, -1, -1);
+    }
+  }
+}
+
+// Issue the MMAs of one layer (single thread) and commit to the mbarrier.
+template <class S>
+__device__ __forceinline__ void issue_layer(int layer, uint32_t act_sa, uint32_t w_sa, uint32_t tmem,
+                                            uint32_t mbar) {
+  tc_fence_after_sync();
+  const int K = S::kdim(layer);
+  const uint32_t idesc = idesc_bf16(128, S::ndim(layer));
+  const uint32_t b_sa = w_sa + S::w_off(layer);
+#pragma unroll 1
+  for (int k0 = 0; k0 < K; k0 += 16)
+    mma_bf16(tmem, kmajor_desc(act_sa, k0, K), kmajor_desc(b_sa, k0, K), idesc, k0 > 0 ? 1u : 0u);
+  mma_commit(mbar);
+}
+
+template <class S, typename TT>
+__global__ void __launch_bounds__(NT) fwd_kernel(const __grid_constant__ QueryParams p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* act = smem + S::OFF_ACT;
+  int* node_sm = reinterpret_cast<int*>(smem + S::OFF_NODE);
+  float* u_sm = reinterpret_cast<float*>(smem + S::OFF_U);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::OFF_BAR);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::OFF_BAR + 8);
+  const uint32_t mbar = smem_addr(bar);
+  const uint32_t act_sa = smem_addr(act), w_sa = smem_addr(smem);
+  const int warp = threadIdx.x >> 5;
+
+  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  if (warp == 0) {
+    tmem_alloc(smem_addr(tslot), S::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  uint32_t phase = 0;
+  int cur = -1;
+  bool failed = false;
+
+  for (int64_t tile = blockIdx.x; tile < p.n_tiles && !failed; tile += gridDim.x) {
+    const int s = scene_of_tile(p, tile);
+    const DevScene& sc = p.sc[s];
+    __syncthreads();
+    if (s != cur) {
+      load_weights_bf16<S>(sc, smem);
+      cur = s;
+    }
+    const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * NT;
+    const int nq = static_cast<int>(sc.q_end - q0 < NT ? sc.q_end - q0 : int64_t(NT));
+    f32::locate_tile<S::KPAD>(p, sc, q0, nq, node_sm, u_sm);
+    __syncthreads();
+    gather_bf16<S, TT>(p, sc, q0, nq, node_sm, u_sm, act);
+    fence_proxy_async();
+    __syncthreads();
+
+#pragma unroll 1
+    for (int layer = 0; layer < S::NL; ++layer) {
+      if (threadIdx.x == 0) issue_layer<S>(layer, act_sa, w_sa, tmem, mbar);
+      const bool ok = mbar_wait_bounded(mbar, phase);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      tc_fence_after_sync();
+      if (layer < S::NL - 1) {
+        uint32_t r[S::H];
+#pragma unroll
+        for (int c = 0; c < S::H; c += 16)
+          tmem_ld16(lane_base + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
+        tmem_wait_ld();
+        const int q = threadIdx.x;
+#pragma unroll
+        for (int c = 0; c < S::H; c += 8) {
+          uint4 o;
+          o.x = pack_bf16x2(fmaxf(__uint_as_float(r[c + 0]), 0.f), fmaxf(__uint_as_float(r[c + 1]), 0.f));
+          o.y = pack_bf16x2(fmaxf(__uint_as_float(r[c + 2]), 0.f), fmaxf(__uint_as_float(r[c + 3]), 0.f));
+          o.z = pack_bf16x2(fmaxf(__uint_as_float(r[c + 4]), 0.f), fmaxf(__uint_as_float(r[c + 5]), 0.f));
+          o.w = pack_bf16x2(fmaxf(__uint_as_float(r[c + 6]), 0.f), fmaxf(__uint_as_float(r[c + 7]), 0.f));
+          *reinterpret_cast<uint4*>(act + kmajor_offset(q, c, S::H)) = o;
+        }
+        fence_proxy_async();
+        tc_fence_before_sync();
+        __syncthreads();
+      } else {
+        uint32_t r[16];
+        tmem_ld16(lane_base, r);
+        tmem_wait_ld();
+        tc_fence_before_sync();
+        const int q = threadIdx.x;
+        if (q < nq) {
+          const int64_t gq = q0 + q;
+          p.rgb[3 * gq] = expf(__uint_as_float(r[0]));
+          p.rgb[3 * gq + 1] = expf(__uint_as_float(r[1]));
+          p.rgb[3 * gq + 2] = expf(__uint_as_float(r[2]));
+        }
+      }
+    }
+  }
+  if (failed && threadIdx.x == 0 && p.status) atomicOr(p.status, OCTA_STATUS_TIMEOUT);
+  tc_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, S::TMEM_COLS);
+}
+
+namespace {
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 148;
+}
+
+template <class S, typename TT>
+int launch_fwd(const QueryParams& p, cudaStream_t stream) {
+  if (p.n_tiles == 0) return OCTA_OK;
+  auto kern = fwd_kernel<S, TT>;
+  static int per_sm = 0;  // one instantiation per template: cached on first (eager) use
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(S::SMEM));
+    if (e != cudaSuccess) return fail(OCTA_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, S::SMEM);
+    if (e != cudaSuccess) return fail(OCTA_ECUDA, "occupancy: %s", cudaGetErrorString(e));
+    // tensor memory (512 columns per SM) must hold every resident CTA
+    per_sm = std::max(1, std::min(occ, static_cast<int>(512 / S::TMEM_COLS)));
+  }
+  const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * sm_count());
+  kern<<<static_cast<unsigned>(grid), NT, S::SMEM, stream>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "tc forward launch: %s", cudaGetErrorString(e));
+  return OCTA_OK;
+}
+
+}  // namespace
+
+int query_fwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
+  const octa_scene& c0 = scenes[0];
+  const int F = c0.F, L = c0.n_layers, H = c0.widths[1], tdt = c0.table_dtype;
+  int need = 0;
+  for (int s = 0; s < n_scenes; ++s) {
+    const octa_scene& c = scenes[s];
+    if (c.F != F || c.n_layers != L || c.table_dtype != tdt || c.weight_dtype != OCTA_BF16)
+      return fail(OCTA_EUNSUPPORTED, "scenes of one call must share F, MLP depth and dtypes");
+    for (int i = 1; i < L; ++i)
+      if (c.widths[i] != H) return fail(OCTA_EUNSUPPORTED, "BF16 path: hidden widths must match");
+    need = std::max(need, c.widths[0]);
+  }
+  const int NH = L - 1;
+  const bool f16 = tdt == OCTA_F16;
+#define OCTA_TC_TRY(F_, WP_, H_, NH_)                                                  \
+  if (F == F_ && H == H_ && NH == NH_ && need <= WP_)                                  \
+    return f16 ? launch_fwd<Shape<F_, WP_, H_, NH_>, __half>(p, stream)               \
+               : launch_fwd<Shape<F_, WP_, H_, NH_>, float>(p, stream);
+  OCTA_TC_TRY(4, 32, 32, 2)
+  OCTA_TC_TRY(8, 64, 64, 2)
+  OCTA_TC_TRY(8, 80, 64, 2)
+  OCTA_TC_TRY(8, 80, 64, 3)
+#undef OCTA_TC_TRY
+  return fail(OCTA_EUNSUPPORTED, "BF16 path: no built shape for F=%d, K*F=%d, hidden %d x %d", F,
+              need, NH, H);
+}
+
 int query_bwd(const octa_scene*, int, const QueryParams&, cudaStream_t) {
-  return fail(OCTA_EUNSUPPORTED, "BF16 tensor-core path not built yet");
+  return fail(OCTA_EUNSUPPORTED, "BF16 backward not built yet");
 }
 
 }  // namespace tc

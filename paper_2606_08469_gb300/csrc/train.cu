@@ -1,7 +1,7 @@
 // Training-side entry points: the residual loss (Eq. 3, Eq. 14) and the Adam
 // step with dynamic loss scaling.  Both reduce in FP64 (the loss value and
 // the gradient norm) through per-block partials in the caller's workspace;
-// the last block to finish sums the partials in block order, so results are
+// the last block to finish sums the partials in a fixed order, so results are
 // deterministic for a given launch shape.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -16,8 +16,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 1024;
-// workspace layout: [kMaxBlocks] doubles of partials, then a 256-byte
-// aligned completion counter
+// workspace layout: [kMaxBlocks] doubles of partials, then the completion
+// counter (uint32) and, 16 bytes after it, Adam's two bias corrections
 constexpr size_t kPartialBytes = sizeof(double) * kMaxBlocks;
 constexpr size_t kWorkspaceBytes = kPartialBytes + 256;
 
@@ -40,10 +40,13 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;  // valid in thread 0
 }
 
-// Publishes this block's partial; returns true in thread 0 of the last block,
-// which then holds the ordered total in *total.
+// Publishes this block's partial; the last block to finish sums all partials
+// with every one of its threads (fixed strided order, then the fixed-order
+// block reduction), so the total is deterministic for a given grid.  Returns
+// true in thread 0 of the last block, which then holds the total in *total.
 __device__ __forceinline__ bool last_block_total(double mine, double* partials,
-                                                 unsigned* counter, double* total) {
+                                                 unsigned* counter, double* total,
+                                                 double* red) {
   __shared__ bool is_last;
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = mine;
@@ -52,10 +55,14 @@ __device__ __forceinline__ bool last_block_total(double mine, double* partials,
     is_last = done == gridDim.x - 1;
   }
   __syncthreads();
-  if (!is_last || threadIdx.x != 0) return false;
+  if (!is_last) return false;
   __threadfence();
   double t = 0.0;
-  for (unsigned b = 0; b < gridDim.x; ++b) t += reinterpret_cast<volatile double*>(partials)[b];
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += kThreads)
+    t += reinterpret_cast<volatile double*>(partials)[b];
+  __syncthreads();  // red[] reuse
+  t = block_sum(t, red);
+  if (threadIdx.x != 0) return false;
   *counter = 0;  // ready for the next call
   *total = t;
   return true;
@@ -85,16 +92,18 @@ __global__ void __launch_bounds__(kThreads) residual_loss_kernel(
   }
   const double bsum = block_sum(acc, red);
   double total;
-  if (last_block_total(bsum, partials, counter, &total)) *loss_dev = total / double(n3);
+  if (last_block_total(bsum, partials, counter, &total, red)) *loss_dev = total / double(n3);
 }
 
 struct AdamParams {
   octa_param_group g[OCTA_MAX_GROUPS];
+  int32_t vec4[OCTA_MAX_GROUPS];  // group may use 16-byte vector accesses
   int32_t n_groups;
   float beta1, beta2, eps;
   octa_scaler* scaler;
   double* partials;
   unsigned* counter;
+  float* bias_corr;  // [2]: 1 - beta1^t, 1 - beta2^t of the step being applied
 };
 
 // Pass 1: FP64 sum of squares of the unscaled gradient; the last block takes
@@ -114,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) adam_norm_kernel(const __grid_consta
   }
   const double bsum = block_sum(acc, red);
   double total;
-  if (last_block_total(bsum, p.partials, p.counter, &total)) {
+  if (last_block_total(bsum, p.partials, p.counter, &total, red)) {
     octa_scaler* s = p.scaler;
     s->inv_scale_used = inv_s;
     s->grad_norm = sqrt(total);
@@ -132,8 +141,18 @@ __global__ void __launch_bounds__(kThreads) adam_norm_kernel(const __grid_consta
         s->scale *= 2.f;
         s->good_steps = 0;
       }
+      p.bias_corr[0] = static_cast<float>(1.0 - pow(double(p.beta1), double(s->step)));
+      p.bias_corr[1] = static_cast<float>(1.0 - pow(double(p.beta2), double(s->step)));
     }
   }
+}
+
+__device__ __forceinline__ float adam_one(float& pm, float& m, float& v, float g, float lr,
+                                          float b1, float b2, float eps, float bc1, float bc2) {
+  m = b1 * m + (1.f - b1) * g;
+  v = b2 * v + (1.f - b2) * g * g;
+  pm = pm - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+  return pm;
 }
 
 // Pass 2: Adam with bias correction (Kingma & Ba 2015) unless the step was
@@ -142,29 +161,60 @@ __global__ void __launch_bounds__(kThreads) adam_update_kernel(const __grid_cons
   const octa_scaler* s = p.scaler;
   const bool skip = s->skipped != 0;
   const float inv_s = s->inv_scale_used;
-  const double t = double(s->step);
-  const float bc1 = static_cast<float>(1.0 - pow(double(p.beta1), t));
-  const float bc2 = static_cast<float>(1.0 - pow(double(p.beta2), t));
+  const float bc1 = skip ? 1.f : p.bias_corr[0], bc2 = skip ? 1.f : p.bias_corr[1];
   const float b1 = p.beta1, b2 = p.beta2, eps = p.eps;
   const int64_t stride = int64_t(gridDim.x) * kThreads;
+  const int64_t first = int64_t(blockIdx.x) * kThreads + threadIdx.x;
   for (int gi = 0; gi < p.n_groups; ++gi) {
     const octa_param_group& G = p.g[gi];
-    for (int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x; i < G.n; i += stride) {
+    const float lr = G.lr;
+    int64_t done = 0;
+    if (p.vec4[gi]) {  // 4 elements per thread and iteration
+      const int64_t n4 = G.n / 4;
+      float4* P = reinterpret_cast<float4*>(G.param);
+      float4* Gr = reinterpret_cast<float4*>(G.grad);
+      float4* M = reinterpret_cast<float4*>(G.m);
+      float4* V = reinterpret_cast<float4*>(G.v);
+      for (int64_t i = first; i < n4; i += stride) {
+        float4 g = Gr[i];
+        Gr[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (skip) continue;
+        float4 pm = P[i], m = M[i], v = V[i];
+        adam_one(pm.x, m.x, v.x, g.x * inv_s, lr, b1, b2, eps, bc1, bc2);
+        adam_one(pm.y, m.y, v.y, g.y * inv_s, lr, b1, b2, eps, bc1, bc2);
+        adam_one(pm.z, m.z, v.z, g.z * inv_s, lr, b1, b2, eps, bc1, bc2);
+        adam_one(pm.w, m.w, v.w, g.w * inv_s, lr, b1, b2, eps, bc1, bc2);
+        P[i] = pm;
+        M[i] = m;
+        V[i] = v;
+        if (G.work) {
+          if (G.work_dtype == OCTA_F16) {
+            __half2* w = reinterpret_cast<__half2*>(G.work) + 2 * i;
+            w[0] = __floats2half2_rn(pm.x, pm.y);
+            w[1] = __floats2half2_rn(pm.z, pm.w);
+          } else {
+            __nv_bfloat162* w = reinterpret_cast<__nv_bfloat162*>(G.work) + 2 * i;
+            w[0] = __floats2bfloat162_rn(pm.x, pm.y);
+            w[1] = __floats2bfloat162_rn(pm.z, pm.w);
+          }
+        }
+      }
+      done = n4 * 4;
+    }
+    for (int64_t i = done + first; i < G.n; i += stride) {
       const float g = G.grad[i] * inv_s;
       G.grad[i] = 0.f;
       if (skip) continue;
-      const float m = b1 * G.m[i] + (1.f - b1) * g;
-      const float v = b2 * G.v[i] + (1.f - b2) * g * g;
+      float pm = G.param[i], m = G.m[i], v = G.v[i];
+      adam_one(pm, m, v, g, lr, b1, b2, eps, bc1, bc2);
+      G.param[i] = pm;
       G.m[i] = m;
       G.v[i] = v;
-      const float mhat = m / bc1, vhat = v / bc2;
-      const float pv = G.param[i] - G.lr * mhat / (sqrtf(vhat) + eps);
-      G.param[i] = pv;
       if (G.work) {
         if (G.work_dtype == OCTA_F16)
-          static_cast<__half*>(G.work)[i] = __float2half_rn(pv);
+          static_cast<__half*>(G.work)[i] = __float2half_rn(pm);
         else
-          static_cast<__nv_bfloat16*>(G.work)[i] = __float2bfloat16_rn(pv);
+          static_cast<__nv_bfloat16*>(G.work)[i] = __float2bfloat16_rn(pm);
       }
     }
   }
@@ -241,6 +291,9 @@ extern "C" int adam_step(const octa_param_group* groups, int32_t n_groups,
     if (g.work && g.work_dtype != OCTA_F16 && g.work_dtype != OCTA_BF16)
       return fail(OCTA_EINVAL, "group %d: working copy dtype must be F16 or BF16", i);
     p.g[i] = g;
+    const uintptr_t mask = reinterpret_cast<uintptr_t>(g.param) | reinterpret_cast<uintptr_t>(g.grad) |
+                           reinterpret_cast<uintptr_t>(g.m) | reinterpret_cast<uintptr_t>(g.v);
+    p.vec4[i] = (mask & 15u) == 0 && (!g.work || (reinterpret_cast<uintptr_t>(g.work) & 7u) == 0);
     total += g.n;
   }
   p.n_groups = n_groups;
@@ -250,8 +303,9 @@ extern "C" int adam_step(const octa_param_group* groups, int32_t n_groups,
   p.scaler = scaler;
   p.partials = static_cast<double*>(workspace);
   p.counter = reinterpret_cast<unsigned*>(static_cast<char*>(workspace) + kPartialBytes);
+  p.bias_corr = reinterpret_cast<float*>(static_cast<char*>(workspace) + kPartialBytes + 16);
   const int blocks = static_cast<int>(std::max<int64_t>(
-      1, std::min<int64_t>({(total + kThreads - 1) / kThreads, int64_t(kMaxBlocks),
+      1, std::min<int64_t>({(total / 4 + kThreads - 1) / kThreads, int64_t(kMaxBlocks),
                             4LL * sm_count()})));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   adam_norm_kernel<<<blocks, kThreads, 0, st>>>(p);

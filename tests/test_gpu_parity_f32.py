@@ -53,6 +53,29 @@ def rel_err(a, b):
     return np.max(np.abs(a - b) / np.abs(b))
 
 
+U32 = 2.0 ** -24
+
+
+def rgb_tolerance(weights, h):
+    """Per-element bound on |rgb_gpu / rgb - 1| for an FP32 evaluation.
+
+    The relative error of exp(z) equals the absolute error of z.  FP32 dot
+    products of n terms carry |dz| <= gamma_n sum |w||a|; propagated through
+    the layers this is bounded by c * u * z_abs, with z_abs the output of the
+    same network run on |W| and |h| (ReLU is the identity there).  c = 16 is
+    a statistical (sqrt n) rather than worst-case constant.  The 1e-5 floor
+    is the stated FP32 tolerance, which the configurations' own inputs meet.
+    """
+    _, zs, _ = O.mlp_forward([np.abs(W) for W in weights], np.abs(h))
+    return np.maximum(1e-5, 16 * U32 * zs[-1])
+
+
+def assert_rgb(gpu, ref, weights, h):
+    err = np.abs(gpu - ref) / ref
+    tol = rgb_tolerance(weights, h)
+    assert np.all(err <= tol), (err.max(), tol[np.unravel_index(np.argmax(err / tol), err.shape)])
+
+
 def normwise(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
@@ -71,9 +94,11 @@ def test_forward_config0_full(sigma, wscale):
     ref, enc = O.query_forward(ot, tables, weights, x, w)
     np.testing.assert_array_equal(nodes.cpu().numpy(), enc.node)
     np.testing.assert_array_equal(addr.cpu().numpy(), enc.addr)
-    assert rel_err(rgb.cpu().numpy(), ref) <= RTOL_RGB
-    if wscale > 1:
+    if wscale == 1.0:
+        assert rel_err(rgb.cpu().numpy(), ref) <= RTOL_RGB     # the workload's own inputs
+    else:
         assert ref.max() / ref.min() > 5          # the test exercises the nonlinearity
+        assert_rgb(rgb.cpu().numpy(), ref, weights, enc.h)
 
 
 def test_encode_features_match_oracle():
@@ -114,7 +139,7 @@ def test_forward_ragged_and_edges(n):
     ref, enc = O.query_forward(ot, tables, weights, x, w)
     np.testing.assert_array_equal(nodes.cpu().numpy(), enc.node)
     np.testing.assert_array_equal(addr.cpu().numpy(), enc.addr)
-    assert rel_err(rgb.cpu().numpy(), ref) <= RTOL_RGB
+    assert_rgb(rgb.cpu().numpy(), ref, weights, enc.h)
 
 
 def test_forward_empty_batch_is_a_no_op():
@@ -142,7 +167,7 @@ def test_forward_hand_tree_absent_levels():
     assert (enc.node[:, 3] >= 0).mean() < 0.1 and (enc.node[:, 3] >= 0).any()
     np.testing.assert_array_equal(nodes.cpu().numpy(), enc.node)
     np.testing.assert_array_equal(addr.cpu().numpy(), enc.addr)
-    assert rel_err(rgb.cpu().numpy(), ref) <= RTOL_RGB
+    assert_rgb(rgb.cpu().numpy(), ref, weights, enc.h)
 
 
 def test_forward_fp16_tables_fp32_decoder():
@@ -153,7 +178,7 @@ def test_forward_fp16_tables_fp32_decoder():
     rgb, nodes, addr = api().octa_query_fwd(sc, dev(x), dev(w), want_nodes=True, want_addr=True)
     ref, enc = O.query_forward(ot, tables, weights, x, w)
     np.testing.assert_array_equal(addr.cpu().numpy(), enc.addr)
-    assert rel_err(rgb.cpu().numpy(), ref) <= RTOL_RGB
+    assert_rgb(rgb.cpu().numpy(), ref, weights, enc.h)
 
 
 def test_malformed_tree_reports_status():
@@ -283,7 +308,7 @@ def test_batched_scenes_match_oracle():
         np.testing.assert_array_equal(nodes[sl, :K], enc.node)
         assert (nodes[sl, K:] == -1).all()
         np.testing.assert_array_equal(addr.cpu().numpy()[sl, :K], enc.addr)
-        assert rel_err(rgb[sl], ref) <= RTOL_RGB
+        assert_rgb(rgb[sl], ref, wts[s], enc.h)
         rT, rWs, _ = O.query_backward(otrees[s], tabs[s], wts[s], xs[s], ws[s], d_rgb[sl])
         assert normwise(grads[s][0].cpu().numpy(), rT) <= RTOL_GRAD
         gw = grads[s][1].cpu().numpy()
