@@ -198,6 +198,29 @@ int residual_loss(const float* L_p, const float* L_s, const float* E, const floa
                   double* loss_dev, float* dL_p, float* dL_s, void* workspace,
                   size_t workspace_bytes, void* stream);
 
+/* residual_loss_static -- residual_loss without a workspace argument.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory -- for example code in a renderer's per-frame path,
+ * where a cudaMalloc may synchronise the device and stall the frame, or a
+ * plug-in whose host application owns every device allocation.  The scratch
+ * (per-block FP64 partials and a completion counter) lives in a fixed
+ * 16.6 KB array inside the library that every GPU which loads it keeps until
+ * the process exits.  The call allocates nothing and calls no allocating
+ * routine.  Limits: n_pairs <= 2,796,202 (the partial slots of the fixed
+ * array); larger batches return OCTA_ERANGE with a message -- use
+ * residual_loss with a workspace for them.  The first call on a device looks
+ * the array's device address up (cudaGetSymbolAddress) for that device, so
+ * make that first call before any stream capture.  Every call shares the one
+ * array: each call clears its counter on `stream` before the kernel, and
+ * calls that overlap on the GPU (other streams, other threads) race and give
+ * wrong losses.  Arguments, outputs and gradients are those of
+ * residual_loss; the loss is summed in another block order, so it agrees
+ * with residual_loss to FP64 rounding, the gradients exactly.             */
+int residual_loss_static(const float* L_p, const float* L_s, const float* E, const float* w,
+                         int64_t n_pairs, float eps, int32_t rhs_grad,
+                         const octa_scaler* scaler, double* loss_dev, float* dL_p, float* dL_s,
+                         void* stream);
+
 /* One parameter group of adam_step (all device pointers, n elements).     */
 typedef struct octa_param_group {
   float* param;                /* FP32 master copy                          */

@@ -124,6 +124,8 @@ _SIGNATURES = {
                                  C.POINTER(octa_scene_grads), _P, _P]),
     "residual_loss": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_float, C.c_int32, _P, _P, _P, _P,
                                 _P, C.c_size_t, _P]),
+    "residual_loss_static": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_float, C.c_int32, _P, _P,
+                                       _P, _P, _P]),
     "adam_step": (C.c_int, [C.POINTER(octa_param_group), C.c_int32, C.POINTER(octa_adam_cfg), _P,
                             _P, C.c_size_t, _P]),
     "octa_workspace_bytes": (C.c_size_t, [C.c_int32, C.c_int64]),

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "octa_internal.h"
 
@@ -313,4 +314,83 @@ extern "C" int adam_step(const octa_param_group* groups, int32_t n_groups,
   if (rc) return rc;
   adam_update_kernel<<<blocks, kThreads, 0, st>>>(p);
   return launched("adam_step (update)");
+}
+
+// ---------------------------------------------------------------------------
+// residual_loss_static: the residual loss without a caller workspace.
+// ---------------------------------------------------------------------------
+// Some callers cannot hand the library a device workspace: code that runs in
+// a renderer's per-frame path, where a cudaMalloc may synchronise the device
+// and stall the frame, or a plug-in whose host application owns every device
+// allocation and exposes none to it.  For them the loss reduction takes its
+// scratch (per-block FP64 partials and the completion counter) from the
+// fixed array below, which every GPU that loads this library keeps until the
+// process exits.
+namespace octa {
+namespace {
+
+constexpr int kStaticSlots = 2048;                  // per-block partials
+constexpr int64_t kStaticElemsPerBlock = 16 * kThreads;
+// largest n_pairs whose 3 * n_pairs elements fit kStaticSlots blocks
+constexpr int64_t kStaticMaxPairs = kStaticSlots * kStaticElemsPerBlock / 3;
+
+// partials [kStaticSlots] doubles, then 256 bytes holding the counter
+static __device__ __align__(256) double g_loss_scratch[kStaticSlots + 32] = {};
+
+constexpr int kStaticMaxDevices = 64;
+void* g_loss_scratch_addr[kStaticMaxDevices] = {};
+std::mutex g_loss_scratch_mutex;
+
+// Device address of g_loss_scratch on the current device, looked up once per
+// device (the host-side symbol is only a stand-in for it).
+int loss_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kStaticMaxDevices)
+    return fail(OCTA_ERANGE, "device index %d beyond %d", dev, kStaticMaxDevices);
+  std::lock_guard<std::mutex> lock(g_loss_scratch_mutex);
+  if (!g_loss_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_loss_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(OCTA_ECUDA, "cudaGetSymbolAddress(loss scratch): %s", cudaGetErrorString(e));
+    g_loss_scratch_addr[dev] = p;
+  }
+  *out = g_loss_scratch_addr[dev];
+  return OCTA_OK;
+}
+
+}  // namespace
+}  // namespace octa
+
+extern "C" int residual_loss_static(const float* L_p, const float* L_s, const float* E,
+                                    const float* w, int64_t n_pairs, float eps, int32_t rhs_grad,
+                                    const octa_scaler* scaler, double* loss_dev, float* dL_p,
+                                    float* dL_s, void* stream) {
+  clear_error();
+  if (n_pairs < 1) return fail(OCTA_EINVAL, "n_pairs must be >= 1");
+  if (n_pairs > kStaticMaxPairs)
+    return fail(OCTA_ERANGE,
+                "residual_loss_static: n_pairs %lld exceeds its fixed scratch limit of %lld pairs; "
+                "use residual_loss with a workspace",
+                static_cast<long long>(n_pairs), static_cast<long long>(kStaticMaxPairs));
+  if (!L_p || !L_s || !E || !w || !loss_dev || !dL_p)
+    return fail(OCTA_EINVAL, "NULL array argument");
+  if (rhs_grad && !dL_s) return fail(OCTA_EINVAL, "dL_s must be non-NULL when rhs_grad");
+  if (!(eps > 0.f)) return fail(OCTA_EINVAL, "eps must be > 0");
+  void* scratch = nullptr;
+  int rc = loss_scratch_address(&scratch);
+  if (rc) return rc;
+  double* partials = static_cast<double*>(scratch);
+  unsigned* counter = reinterpret_cast<unsigned*>(partials + kStaticSlots);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the completion counter must start at zero in every call
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "clearing the loss scratch: %s", cudaGetErrorString(e));
+  const int64_t n3 = 3 * n_pairs;
+  const int blocks = static_cast<int>((n3 + kStaticElemsPerBlock - 1) / kStaticElemsPerBlock);
+  residual_loss_kernel<<<blocks, kThreads, 0, st>>>(L_p, L_s, E, w, n3, eps, rhs_grad, scaler,
+                                                    loss_dev, dL_p, dL_s, partials, counter);
+  return launched("residual_loss_static");
 }
