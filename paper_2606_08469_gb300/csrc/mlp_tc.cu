@@ -246,6 +246,267 @@ __global__ void __launch_bounds__(NT) fwd_kernel(const __grid_constant__ QueryPa
   if (warp == 0) tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
+// ---------------------------------------------------------------------------
+// Backward (recomputed forward, then the delta chain on the tensor cores)
+// ---------------------------------------------------------------------------
+// Shared memory: weights | h tile | a_1 .. a_NH tiles | delta_L tile | slack |
+// node / u tables | mbarrier.  Tensor memory: a working accumulator of WORK
+// columns (every forward layer and every data-gradient GEMM), then the
+// transposed weight gradients dW_i^T = a_i^T delta_{i+1} (rows = input
+// features, one column per output feature), accumulated over every tile the
+// CTA handles and flushed with atomics when the scene changes or at the end.
+template <int F_, int WP_, int H_, int NH_>
+struct BShape : Shape<F_, WP_, H_, NH_> {
+  using B = Shape<F_, WP_, H_, NH_>;
+  static constexpr uint32_t H_TILE = NT * WP_ * 2;
+  static constexpr uint32_t A_TILE = NT * H_ * 2;
+  static constexpr uint32_t DL_TILE = NT * NOUT * 2;
+  static constexpr uint32_t OFF_H = B::W_BYTES;
+  static constexpr uint32_t OFF_DL = OFF_H + H_TILE + NH_ * A_TILE;
+  // MN-major reads with M = 128 rows run past a tile narrower than 128
+  // features into the next buffer; the slack keeps the last one in bounds.
+  static constexpr uint32_t OFF_NODE = OFF_DL + DL_TILE + 2048;
+  static constexpr uint32_t OFF_U = OFF_NODE + B::NODE_BYTES;
+  static constexpr uint32_t OFF_BAR = (OFF_U + B::U_BYTES + 15) & ~15u;
+  static constexpr size_t SMEM = OFF_BAR + 16;
+  static constexpr int WORK = WP_ > H_ ? WP_ : H_;
+  static constexpr int COLS = WORK + H_ * NH_ + NOUT;
+  static constexpr uint32_t TMEM_COLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128
+                                        : COLS <= 256 ? 256 : 512;
+  static_assert(COLS <= 512, "tensor memory");
+  __host__ __device__ static constexpr uint32_t off_act(int i) {
+    return i == 0 ? OFF_H : OFF_H + H_TILE + static_cast<uint32_t>(i - 1) * A_TILE;
+  }
+  __host__ __device__ static constexpr int dw_col(int i) { return WORK + H_ * i; }
+};
+
+// Adds the CTA's dW^T accumulators of one scene to its FP32 weight gradient
+// (thread r holds row r = input feature r of every matrix).
+template <class S>
+__device__ void flush_weight_grads(const DevScene& sc, uint32_t lane_base) {
+  const int r = threadIdx.x;
+  tc_fence_after_sync();
+#pragma unroll 1
+  for (int i = 0; i < S::NL; ++i) {
+    const int n_pad = S::ndim(i);
+    const int in = sc.widths[i], out = sc.widths[i + 1];
+    float* dW = sc.d_weights + sc.w_offset[i];
+#pragma unroll 1
+    for (int c = 0; c < n_pad; c += 16) {
+      uint32_t v[16];
+      tmem_ld16(lane_base + S::dw_col(i) + c, v);
+      tmem_wait_ld();
+      if (r < in) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c + j < out) atomicAdd(dW + (c + j) * in + r, __uint_as_float(v[j]));
+      }
+    }
+  }
+  tc_fence_before_sync();
+}
+
+template <class S, typename TT>
+__global__ void __launch_bounds__(NT) bwd_kernel(const __grid_constant__ QueryParams p) {
+  constexpr int H = S::H, NL = S::NL;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  int* node_sm = reinterpret_cast<int*>(smem + S::OFF_NODE);
+  float* u_sm = reinterpret_cast<float*>(smem + S::OFF_U);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::OFF_BAR);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::OFF_BAR + 8);
+  const uint32_t mbar = smem_addr(bar);
+  const uint32_t base_sa = smem_addr(smem);
+  const uint32_t dl_sa = base_sa + S::OFF_DL;
+  const int warp = threadIdx.x >> 5;
+  const int q = threadIdx.x;
+
+  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  if (warp == 0) {
+    tmem_alloc(smem_addr(tslot), S::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  uint32_t phase = 0;
+  int cur = -1;
+  bool first = true, failed = false;
+
+  for (int64_t tile = blockIdx.x; tile < p.n_tiles && !failed; tile += gridDim.x) {
+    const int s = scene_of_tile(p, tile);
+    const DevScene& sc = p.sc[s];
+    __syncthreads();
+    if (s != cur) {
+      if (cur >= 0 && !first) flush_weight_grads<S>(p.sc[cur], lane_base);
+      load_weights_bf16<S>(sc, smem);
+      cur = s;
+      first = true;
+    }
+    const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * NT;
+    const int nq = static_cast<int>(sc.q_end - q0 < NT ? sc.q_end - q0 : int64_t(NT));
+    f32::locate_tile<S::KPAD>(p, sc, q0, nq, node_sm, u_sm);
+    __syncthreads();
+    gather_bf16<S, TT>(p, sc, q0, nq, node_sm, u_sm, smem + S::OFF_H);
+    fence_proxy_async();
+    __syncthreads();
+
+    // ---- forward, keeping a_1 .. a_NH and delta_L
+#pragma unroll 1
+    for (int layer = 0; layer < NL && !failed; ++layer) {
+      if (threadIdx.x == 0) issue_layer<S>(layer, base_sa + S::off_act(layer), base_sa, tmem, mbar);
+      const bool ok = mbar_wait_bounded(mbar, phase);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      tc_fence_after_sync();
+      if (layer < NL - 1) {
+        uint32_t r[H];
+#pragma unroll
+        for (int c = 0; c < H; c += 16)
+          tmem_ld16(lane_base + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
+        tmem_wait_ld();
+        uint8_t* dst = smem + S::off_act(layer + 1);
+#pragma unroll
+        for (int c = 0; c < H; c += 8) {
+          uint4 o;
+          o.x = pack_bf16x2(fmaxf(__uint_as_float(r[c + 0]), 0.f), fmaxf(__uint_as_float(r[c + 1]), 0.f));
+          o.y = pack_bf16x2(fmaxf(__uint_as_float(r[c + 2]), 0.f), fmaxf(__uint_as_float(r[c + 3]), 0.f));
+          o.z = pack_bf16x2(fmaxf(__uint_as_float(r[c + 4]), 0.f), fmaxf(__uint_as_float(r[c + 5]), 0.f));
+          o.w = pack_bf16x2(fmaxf(__uint_as_float(r[c + 6]), 0.f), fmaxf(__uint_as_float(r[c + 7]), 0.f));
+          *reinterpret_cast<uint4*>(dst + kmajor_offset(q, c, H)) = o;
+        }
+      } else {
+        uint32_t r[16];
+        tmem_ld16(lane_base, r);
+        tmem_wait_ld();
+        float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+        if (q < nq) {
+          const int64_t gq = q0 + q;
+          d0 = p.d_rgb[3 * gq];
+          d1 = p.d_rgb[3 * gq + 1];
+          d2 = p.d_rgb[3 * gq + 2];
+        }
+        // delta_L = d_rgb * exp(z_L): the derivative of exp is exp
+        uint8_t* dst = smem + S::OFF_DL;
+        uint4 o0, o1;
+        o0.x = pack_bf16x2(d0 * expf(__uint_as_float(r[0])), d1 * expf(__uint_as_float(r[1])));
+        o0.y = pack_bf16x2(d2 * expf(__uint_as_float(r[2])), 0.f);
+        o0.z = o0.w = 0u;
+        o1.x = o1.y = o1.z = o1.w = 0u;
+        *reinterpret_cast<uint4*>(dst + kmajor_offset(q, 0, NOUT)) = o0;
+        *reinterpret_cast<uint4*>(dst + kmajor_offset(q, 8, NOUT)) = o1;
+      }
+      fence_proxy_async();
+      tc_fence_before_sync();
+      __syncthreads();
+    }
+    if (failed) break;
+
+    // ---- backward through the decoder
+#pragma unroll 1
+    for (int i = NL - 1; i >= 0; --i) {
+      const int out = S::ndim(i), in = S::kdim(i);
+      const uint32_t d_sa = i == NL - 1 ? dl_sa : base_sa + S::off_act(i + 1);
+      const int dk = out;  // row length of the delta tile
+      if (threadIdx.x == 0) {
+        tc_fence_after_sync();
+        // dW_i^T += a_i^T delta_{i+1}: M = 128 input features, N = out, K = 128 queries
+        const uint32_t act_sa = base_sa + S::off_act(i);
+        const uint32_t idw = idesc_bf16(128, out, 1, 1);
+#pragma unroll 1
+        for (int kq = 0; kq < NT; kq += 16)
+          mma_bf16(tmem + S::dw_col(i), mnmajor_desc(act_sa, kq, in), mnmajor_desc(d_sa, kq, dk),
+                   idw, (!first || kq > 0) ? 1u : 0u);
+        // G = delta_{i+1} W_i: M = 128 queries, N = in, K = out
+        const uint32_t ig = idesc_bf16(128, in, 0, 1);
+        const uint32_t w_sa = base_sa + S::w_off(i);
+#pragma unroll 1
+        for (int ko = 0; ko < out; ko += 16)
+          mma_bf16(tmem, kmajor_desc(d_sa, ko, dk), mnmajor_desc(w_sa, ko, in), ig,
+                   ko > 0 ? 1u : 0u);
+        mma_commit(mbar);
+      }
+      const bool ok = mbar_wait_bounded(mbar, phase);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      tc_fence_after_sync();
+      if (i > 0) {
+        // delta_i = G * 1[a_i > 0], written over a_i (its MMAs have completed)
+        uint32_t r[H];
+#pragma unroll
+        for (int c = 0; c < H; c += 16)
+          tmem_ld16(lane_base + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
+        tmem_wait_ld();
+        uint8_t* act = smem + S::off_act(i);
+#pragma unroll
+        for (int c = 0; c < H; c += 8) {
+          uint4* pa = reinterpret_cast<uint4*>(act + kmajor_offset(q, c, H));
+          const uint4 a = *pa;
+          const uint32_t av[4] = {a.x, a.y, a.z, a.w};
+          uint32_t ov[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            // a ReLU output in bf16 is > 0 iff its magnitude bits are non-zero
+            const float g0 = (av[j] & 0x7FFFu) ? __uint_as_float(r[c + 2 * j]) : 0.f;
+            const float g1 = ((av[j] >> 16) & 0x7FFFu) ? __uint_as_float(r[c + 2 * j + 1]) : 0.f;
+            ov[j] = pack_bf16x2(g0, g1);
+          }
+          *pa = make_uint4(ov[0], ov[1], ov[2], ov[3]);
+        }
+        fence_proxy_async();
+        tc_fence_before_sync();
+        __syncthreads();
+      } else {
+        // dh = G; scatter w_k * dh_l into the four texels of every present level
+        uint32_t r[S::WP];
+#pragma unroll
+        for (int c = 0; c < S::WP; c += 16)
+          tmem_ld16(lane_base + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
+        tmem_wait_ld();
+        tc_fence_before_sync();
+#pragma unroll
+        for (int l = 0; l < S::KPAD; ++l) {
+          const int node = node_sm[l * NT + q];
+          if (node < 0) continue;
+          const int R = sc.R[l];
+          const int64_t mo = f32::map_base(p, sc, node, R);
+          if (mo < 0) continue;
+          const Footprint fp = footprint(u_sm[q], u_sm[NT + q], R);
+#pragma unroll
+          for (int c4 = 0; c4 < S::F / 4; ++c4) {
+            const float g0 = __uint_as_float(r[l * S::F + 4 * c4 + 0]);
+            const float g1 = __uint_as_float(r[l * S::F + 4 * c4 + 1]);
+            const float g2 = __uint_as_float(r[l * S::F + 4 * c4 + 2]);
+            const float g3 = __uint_as_float(r[l * S::F + 4 * c4 + 3]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float w = fp.w[k];
+              float4* dst = reinterpret_cast<float4*>(sc.d_tables + (mo + fp.idx[k]) * S::F) + c4;
+              atomicAdd(dst, make_float4(w * g0, w * g1, w * g2, w * g3));
+            }
+          }
+        }
+      }
+    }
+    first = false;
+  }
+  if (!failed && cur >= 0 && !first) {
+    __syncthreads();
+    flush_weight_grads<S>(p.sc[cur], lane_base);
+  }
+  if (failed && threadIdx.x == 0 && p.status) atomicOr(p.status, OCTA_STATUS_TIMEOUT);
+  tc_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, S::TMEM_COLS);
+}
+
 namespace {
 
 int sm_count() {
@@ -277,7 +538,67 @@ int launch_fwd(const QueryParams& p, cudaStream_t stream) {
   return OCTA_OK;
 }
 
+template <class S, typename TT>
+int launch_bwd(const QueryParams& p, cudaStream_t stream) {
+  if (p.n_tiles == 0) return OCTA_OK;
+  auto kern = bwd_kernel<S, TT>;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(S::SMEM));
+    if (e != cudaSuccess) return fail(OCTA_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, S::SMEM);
+    if (e != cudaSuccess) return fail(OCTA_ECUDA, "occupancy: %s", cudaGetErrorString(e));
+    per_sm = std::max(1, std::min(occ, static_cast<int>(512 / S::TMEM_COLS)));
+  }
+  const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * sm_count());
+  kern<<<static_cast<unsigned>(grid), NT, S::SMEM, stream>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "tc backward launch: %s", cudaGetErrorString(e));
+  return OCTA_OK;
+}
+
+// Common shape selection of the BF16 path.
+int select_shape(const octa_scene* scenes, int n_scenes, int* F, int* need, int* H, int* NH,
+                 bool* f16) {
+  const octa_scene& c0 = scenes[0];
+  const int L = c0.n_layers, tdt = c0.table_dtype;
+  *F = c0.F;
+  *H = c0.widths[1];
+  *need = 0;
+  for (int s = 0; s < n_scenes; ++s) {
+    const octa_scene& c = scenes[s];
+    if (c.F != *F || c.n_layers != L || c.table_dtype != tdt || c.weight_dtype != OCTA_BF16)
+      return fail(OCTA_EUNSUPPORTED, "scenes of one call must share F, MLP depth and dtypes");
+    for (int i = 1; i < L; ++i)
+      if (c.widths[i] != *H) return fail(OCTA_EUNSUPPORTED, "BF16 path: hidden widths must match");
+    *need = std::max(*need, c.widths[0]);
+  }
+  *NH = L - 1;
+  *f16 = tdt == OCTA_F16;
+  return OCTA_OK;
+}
+
 }  // namespace
+
+int query_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
+  int F, need, H, NH;
+  bool f16;
+  int rc = select_shape(scenes, n_scenes, &F, &need, &H, &NH, &f16);
+  if (rc) return rc;
+#define OCTA_TC_TRY(F_, WP_, H_, NH_)                                                  \
+  if (F == F_ && H == H_ && NH == NH_ && need <= WP_)                                  \
+    return f16 ? launch_bwd<BShape<F_, WP_, H_, NH_>, __half>(p, stream)              \
+               : launch_bwd<BShape<F_, WP_, H_, NH_>, float>(p, stream);
+  OCTA_TC_TRY(4, 32, 32, 2)
+  OCTA_TC_TRY(8, 64, 64, 2)
+  OCTA_TC_TRY(8, 80, 64, 2)
+  OCTA_TC_TRY(8, 80, 64, 3)
+#undef OCTA_TC_TRY
+  return fail(OCTA_EUNSUPPORTED, "BF16 path: no built shape for F=%d, K*F=%d, hidden %d x %d", F,
+              need, NH, H);
+}
 
 int query_fwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
   const octa_scene& c0 = scenes[0];
@@ -304,10 +625,6 @@ int query_fwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cuda
 #undef OCTA_TC_TRY
   return fail(OCTA_EUNSUPPORTED, "BF16 path: no built shape for F=%d, K*F=%d, hidden %d x %d", F,
               need, NH, H);
-}
-
-int query_bwd(const octa_scene*, int, const QueryParams&, cudaStream_t) {
-  return fail(OCTA_EUNSUPPORTED, "BF16 backward not built yet");
 }
 
 }  // namespace tc

@@ -38,9 +38,21 @@ __device__ __forceinline__ uint64_t kmajor_desc(uint32_t tile_saddr, int k0, int
                    static_cast<uint32_t>(kdim * 16));
 }
 
-// Instruction descriptor, kind::f16: D = FP32, A = B = BF16, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+// The same canonical tile read as an MN-major operand: MN runs along the
+// tile's k (8 contiguous elements per core-matrix row), K along its rows.
+// Core matrices adjacent along K (the next 8 rows) sit kdim*16 bytes apart,
+// along MN (the next 8 elements) 128 bytes apart.  r0 = first row (multiple
+// of 8) of the K range.
+__device__ __forceinline__ uint64_t mnmajor_desc(uint32_t tile_saddr, int r0, int kdim) {
+  return smem_desc(tile_saddr + static_cast<uint32_t>(r0 / 8) * static_cast<uint32_t>(kdim * 16),
+                   static_cast<uint32_t>(kdim * 16), 128u);
+}
+
+// Instruction descriptor, kind::f16: D = FP32, A = B = BF16; a_mn / b_mn set
+// the operand's MN-major (transposed) bit.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn = 0, int b_mn = 0) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(a_mn) << 15) |
+         (static_cast<uint32_t>(b_mn) << 16) | (static_cast<uint32_t>(N >> 3) << 17) |
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 
