@@ -149,6 +149,91 @@ def cpu_baseline(n_pairs=65536, repeats=2):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def _timed(fn, n, flush, stream):
+    """Median device time (ms) of fn over n runs, L2 flushed before each."""
+    import torch
+    evs = []
+    for _ in range(n):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+
+def bf16_vs_f32_leg(dev, flush, stream, steps, peaks):
+    """Config [2] training step (1,048,576 pairs, depth-8 tree, decoder
+    72-64-64-64-3): BF16 tensor-core path vs the FP32 path on the same shapes."""
+    from paper_2606_08469_gb300 import api
+    from paper_2606_08469_gb300 import inputs as I
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[2]
+    out = {"workload": "config[2] training step: depth-8 octree, R 64..8, F=8, decoder 72-64-64-64-3, "
+                       "1048576 pairs = 2097152 queries, dynamic loss scaling"}
+    W = cfg.widths
+    fwd_flop = 2 * sum(a * b for a, b in zip(W[:-1], W[1:]))
+    for prec in ("bf16", "f32"):
+        step, _ = WL.train_step_for(cfg, device=dev, precision=None if prec == "bf16" else "f32")
+        for _ in range(3):
+            step.step()
+        torch_sync = stream.synchronize
+        torch_sync()
+        t_step = _timed(step.step, steps, flush, stream)
+        step.forward()
+        t_fwd = _timed(step.forward, steps, flush, stream)
+        step.loss_and_grad()
+        t_bwd = _timed(step.backward, steps, flush, stream)
+        nq = 2 * cfg.n
+        sc = api.read_scaler(step.scaler)
+        leg = {"Mq/s": round(nq / t_step / 1e3, 2), "ms_per_step": round(t_step, 4),
+               "fwd_ms": round(t_fwd, 4), "bwd_ms": round(t_bwd, 4), "loss": float(step.loss.item()),
+               "loss_scale": float(sc.scale)}
+        if prec == "bf16":
+            peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+            ach = 3 * fwd_flop * nq / (t_bwd / 1e3) / 1e12
+            leg["roofline_bwd"] = {"bound": "tensor", "achieved": round(ach, 2), "peak": peak,
+                                   "unit": "TFLOP/s", "frac": round(ach / peak, 5)}
+        out[prec] = leg
+        del step
+    out["speedup_bf16_over_f32"] = round(out["bf16"]["Mq/s"] / out["f32"]["Mq/s"], 3)
+    return out
+
+
+def inference_leg(dev, flush, stream, steps, peaks):
+    """Config [3]: one query per pixel of a synthetic G-buffer, BF16 decoder
+    72-64-64-3 on the tensor cores (FP32 path for comparison)."""
+    import torch
+    from paper_2606_08469_gb300 import api
+    from paper_2606_08469_gb300 import inputs as I
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[3]
+    W = cfg.widths
+    fwd_flop = 2 * sum(a * b for a, b in zip(W[:-1], W[1:]))
+    out = {"workload": "config[3] inference: depth-8 octree, FP16 features, BF16 decoder 72-64-64-3"}
+    for (w_, h_) in ((1280, 720), (1024, 1024)):
+        x, om = I.gbuffer_queries(cfg.seed("queries"), w_, h_)
+        X, Om = WL.to_dev(x, dev), WL.to_dev(om, dev)
+        rgb = torch.empty((len(x), 3), device=dev)
+        res = {}
+        for prec in ("bf16", "f32"):
+            sc, _ = WL.forward_scene(cfg, device=dev, precision=None if prec == "bf16" else "f32")
+            fn = lambda: api.octa_query_fwd(sc, X, Om, rgb=rgb)
+            for _ in range(3):
+                fn()
+            t = _timed(fn, steps, flush, stream)
+            res[prec] = {"ms_per_frame": round(t, 4), "Mq/s": round(len(x) / t / 1e3, 1)}
+            if prec == "bf16":
+                peak = float(peaks.get("bf16_tflops", 1886.6))
+                ach = fwd_flop * len(x) / (t / 1e3) / 1e12
+                res[prec]["roofline"] = {"bound": "tensor", "achieved": round(ach, 2), "peak": peak,
+                                         "unit": "TFLOP/s", "frac": round(ach / peak, 5)}
+        out[f"{w_}x{h_}"] = res
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -295,6 +380,9 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clocks.summary(),
         }
+        if not args.no_extra:
+            out["bf16_vs_f32"] = bf16_vs_f32_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
+            out["inference"] = inference_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
         out["cpu_baseline"] = cpu_baseline() if not args.no_cpu else None
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -335,6 +423,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the BF16-vs-FP32 and inference legs (profiling captures)")
     ap.add_argument("--pairs", type=int, default=262144,
                     help="training pairs per step (smaller values only for profiling captures)")
     args = ap.parse_args()

@@ -1,0 +1,104 @@
+// Host helpers shared by the kernel launchers: per-kernel shared-memory
+// attributes and resident CTAs per SM.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "octa_internal.h"
+
+namespace octa {
+
+inline int device_sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 148;
+}
+
+// Resident CTAs per SM from the kernel's registers and shared memory and the
+// device limits (threads, registers, shared memory incl. the per-CTA
+// reservation, CTA slots).
+inline int ctas_from_resources(const void* fn, size_t smem, int threads) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) return 1;
+  int dev = 0, sm_smem = 0, rsv = 0, sm_regs = 0, sm_thr = 0, sm_blk = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&sm_thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaDeviceGetAttribute(&sm_blk, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+  const int warps = (threads + 31) / 32;
+  const int regs_per_warp = ((a.numRegs * 32 + 255) / 256) * 256;  // 256-register granules
+  const size_t smem_cta = smem + a.sharedSizeBytes + static_cast<size_t>(rsv);
+  int n = sm_blk > 0 ? sm_blk : 32;
+  if (sm_thr > 0) n = std::min(n, sm_thr / (warps * 32));
+  if (sm_regs > 0 && regs_per_warp > 0) n = std::min(n, sm_regs / (regs_per_warp * warps));
+  if (sm_smem > 0 && smem_cta > 0) n = std::min(n, static_cast<int>(sm_smem / smem_cta));
+  return std::max(1, n);
+}
+
+// Sets the kernel's dynamic shared-memory limit and the largest shared-memory
+// carveout, then returns the resident CTAs per SM.  For kernels that
+// allocate tensor memory (tmem_cols > 0) the count comes from the kernel's
+// registers and shared memory (the runtime's occupancy query reports one CTA
+// per SM for them) and is capped by the 512 tensor-memory columns of an SM.
+// Called once per kernel and device, outside any stream capture.
+inline int resident_ctas(const void* fn, size_t smem, int threads, int tmem_cols, int* out) {
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "cudaFuncSetAttribute(smem): %s", cudaGetErrorString(e));
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess)
+    return fail(OCTA_ECUDA, "cudaFuncSetAttribute(carveout): %s", cudaGetErrorString(e));
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+  if (occ < 1) return fail(OCTA_ECUDA, "kernel does not fit on an SM (%zu B shared)", smem);
+  if (tmem_cols > 0) occ = std::min(ctas_from_resources(fn, smem, threads), 512 / tmem_cols);
+  *out = std::max(1, occ);
+  return OCTA_OK;
+}
+
+// Cache of resident_ctas() per (kernel, device, shared-memory size).
+class LaunchCache {
+ public:
+  int get(const void* fn, size_t smem, int threads, int tmem_cols, int* out) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu_);
+    for (int i = 0; i < n_; ++i)
+      if (e_[i].fn == fn && e_[i].dev == dev && e_[i].smem == smem) {
+        *out = e_[i].per_sm;
+        return OCTA_OK;
+      }
+    int per_sm = 0;
+    int rc = resident_ctas(fn, smem, threads, tmem_cols, &per_sm);
+    if (rc) return rc;
+    if (n_ < kMax) e_[n_++] = Entry{fn, dev, smem, per_sm};
+    *out = per_sm;
+    return OCTA_OK;
+  }
+
+ private:
+  struct Entry {
+    const void* fn;
+    int dev;
+    size_t smem;
+    int per_sm;
+  };
+  static constexpr int kMax = 256;
+  Entry e_[kMax];
+  int n_ = 0;
+  std::mutex mu_;
+};
+
+inline LaunchCache& launch_cache() {
+  static LaunchCache c;
+  return c;
+}
+
+}  // namespace octa

@@ -23,6 +23,7 @@
 #include <algorithm>
 
 #include "engine_f32.cuh"
+#include "launch_util.h"
 #include "octa_internal.h"
 #include "tc_path.h"
 #include "tc_ptx.cuh"
@@ -77,67 +78,129 @@ __device__ void load_weights_bf16(const DevScene& sc, uint8_t* smem) {
   }
 }
 
-// Gather into the layer-0 operand tile (row q, columns l*F .. l*F+F-1).
+// Locate and gather of one query per thread, fused: the thread folds omega,
+// walks its query's path down the octree, loads the map base of every
+// present level, then gathers two levels at a time (both levels' texel loads
+// in flight together; one at a time for 32-byte texels) into its row of the
+// layer-0 operand tile.  node_sm /
+// u_sm (nullable) keep the path and the folded direction for a later scatter.
 template <class S, typename TT>
-__device__ __forceinline__ void gather_bf16(const QueryParams& p, const DevScene& sc, int64_t q0,
-                                            int nq, const int* node_sm, const float* u_sm,
-                                            uint8_t* act) {
-  constexpr int F = S::F;
-  for (int it = threadIdx.x; it < S::KPAD * NT; it += NT) {
-    const int l = it / NT, q = it % NT;  // l is warp-uniform
-    const int node = node_sm[l * NT + q];
-    float v[F];
+__device__ __forceinline__ void locate_gather_bf16(const QueryParams& p, const DevScene& sc,
+                                                   int64_t q0, int nq, uint8_t* act,
+                                                   int* node_sm, float* u_sm) {
+  constexpr int F = S::F, KP = S::KPAD;
+  // levels gathered together: two for texels of up to 16 bytes, else one
+  constexpr int WIN = TexelRaw<TT, F>::BYTES <= 16 ? 2 : 1;
+  const int q = threadIdx.x;
+  const bool valid = q < nq;
+  const int64_t gq = q0 + q;
+  float x0 = 0.f, x1 = 0.f, x2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 1.f;
+  if (valid) {
+    x0 = p.x[3 * gq];
+    x1 = p.x[3 * gq + 1];
+    x2 = p.x[3 * gq + 2];
+    w0 = p.omega[3 * gq];
+    w1 = p.omega[3 * gq + 1];
+    w2 = p.omega[3 * gq + 2];
+  }
+  float ux, uy;
+  octa_fold(w0, w1, w2, ux, uy);
+  x0 = clamp01(x0);
+  x1 = clamp01(x1);
+  x2 = clamp01(x2);
+  int node[KP];
+  node[0] = valid ? 0 : -1;
+  int cp0 = 0, cp1 = 0, cp2 = 0;
 #pragma unroll
-    for (int f = 0; f < F; ++f) v[f] = 0.f;
-    int64_t a4[4] = {-1, -1, -1, -1};
-    if (node >= 0) {
-      const int R = sc.R[l];
-      const int64_t mo = f32::map_base(p, sc, node, R);
-      if (mo >= 0) {
-        const Footprint fp = footprint(u_sm[q], u_sm[NT + q], R);
-        float t[4][F];
+  for (int l = 1; l < KP; ++l) {
+    int nd = -1;
+    if (l < sc.K && node[l - 1] >= 0) {
+      const int c0 = cell_coord(x0, l), c1 = cell_coord(x1, l), c2 = cell_coord(x2, l);
+      const int slot = (c0 - 2 * cp0) | ((c1 - 2 * cp1) << 1) | ((c2 - 2 * cp2) << 2);
+      int fc = __ldg(sc.first_child + node[l - 1]);
+      if (fc >= 0 && fc > sc.num_nodes - 8) {
+        if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
+        fc = -1;
+      }
+      nd = fc >= 0 ? fc + slot : -1;
+      cp0 = c0;
+      cp1 = c1;
+      cp2 = c2;
+    }
+    node[l] = nd;
+  }
+  if (node_sm) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          a4[k] = mo + fp.idx[k];
-          TexelLoad<TT, F>::load(sc.tables, a4[k], t[k]);
-        }
+    for (int l = 0; l < KP; ++l) node_sm[l * NT + q] = node[l];
+    u_sm[q] = ux;
+    u_sm[NT + q] = uy;
+  }
+  if (p.node_idx && valid) {
 #pragma unroll
-        for (int f = 0; f < F; ++f) {
-          float s = fp.w[0] * t[0][f];
-          s = fmaf(fp.w[1], t[1][f], s);
-          s = fmaf(fp.w[2], t[2][f], s);
-          s = fmaf(fp.w[3], t[3][f], s);
-          v[f] = s;
-        }
+    for (int l = 0; l < KP; ++l)
+      if (l < p.kmax_out) p.node_idx[gq * p.kmax_out + l] = node[l];
+    for (int l = KP; l < p.kmax_out; ++l) p.node_idx[gq * p.kmax_out + l] = -1;
+  }
+  int64_t mo[KP];
+#pragma unroll
+  for (int l = 0; l < KP; ++l) mo[l] = node[l] >= 0 ? f32::map_base(p, sc, node[l], sc.R[l]) : -1;
+#pragma unroll
+  for (int l0 = 0; l0 < KP; l0 += WIN) {
+    TexelRaw<TT, F> t[WIN][4];
+    Footprint fp[WIN];
+#pragma unroll
+    for (int j = 0; j < WIN; ++j) {
+      const int l = l0 + j;
+      if (l < KP && mo[l] >= 0) {
+        fp[j] = footprint(ux, uy, sc.R[l]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t[j][k].load(sc.tables, mo[l] + fp[j].idx[k]);
       }
     }
-    uint8_t* dst = act + kmajor_offset(q, l * F, S::WP);
-    if constexpr (F == 8) {
-      uint4 o;
-      o.x = pack_bf16x2(v[0], v[1]);
-      o.y = pack_bf16x2(v[2], v[3]);
-      o.z = pack_bf16x2(v[4], v[5]);
-      o.w = pack_bf16x2(v[6], v[7]);
-      *reinterpret_cast<uint4*>(dst) = o;
-    } else {
-      uint2 o;
-      o.x = pack_bf16x2(v[0], v[1]);
-      o.y = pack_bf16x2(v[2], v[3]);
-      *reinterpret_cast<uint2*>(dst) = o;
-    }
-    if (p.texel_addr && q < nq && l < p.kmax_out) {
-      *reinterpret_cast<int4*>(p.texel_addr + ((q0 + q) * p.kmax_out + l) * 4) =
-          make_int4(int(a4[0]), int(a4[1]), int(a4[2]), int(a4[3]));
+#pragma unroll
+    for (int j = 0; j < WIN; ++j) {
+      const int l = l0 + j;
+      if (l >= KP) continue;
+      float v[F];
+      if (mo[l] >= 0) {
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+          float s = fp[j].w[0] * t[j][0].get(f);
+          s = fmaf(fp[j].w[1], t[j][1].get(f), s);
+          s = fmaf(fp[j].w[2], t[j][2].get(f), s);
+          s = fmaf(fp[j].w[3], t[j][3].get(f), s);
+          v[f] = s;
+        }
+      } else {
+#pragma unroll
+        for (int f = 0; f < F; ++f) v[f] = 0.f;
+      }
+      uint8_t* dst = act + kmajor_offset(q, l * F, S::WP);
+      if constexpr (F == 8) {
+        uint4 o;
+        o.x = pack_bf16x2(v[0], v[1]);
+        o.y = pack_bf16x2(v[2], v[3]);
+        o.z = pack_bf16x2(v[4], v[5]);
+        o.w = pack_bf16x2(v[6], v[7]);
+        *reinterpret_cast<uint4*>(dst) = o;
+      } else {
+        uint2 o;
+        o.x = pack_bf16x2(v[0], v[1]);
+        o.y = pack_bf16x2(v[2], v[3]);
+        *reinterpret_cast<uint2*>(dst) = o;
+      }
+      if (p.texel_addr && valid && l < p.kmax_out) {
+        int4 a = make_int4(-1, -1, -1, -1);
+        if (mo[l] >= 0)
+          a = make_int4(int(mo[l] + fp[j].idx[0]), int(mo[l] + fp[j].idx[1]),
+                        int(mo[l] + fp[j].idx[2]), int(mo[l] + fp[j].idx[3]));
+        *reinterpret_cast<int4*>(p.texel_addr + (gq * p.kmax_out + l) * 4) = a;
+      }
     }
   }
-  if (p.texel_addr && p.kmax_out > S::KPAD) {
-    for (int it = threadIdx.x; it < (p.kmax_out - S::KPAD) * NT; it += NT) {
-      const int l = S::KPAD + it / NT, q = it % NT;
-      if (q < nq)
-        *reinterpret_cast<int4*>(p.texel_addr + ((q0 + q) * p.kmax_out + l) * 4) =
-            make_int4(-1, -1, -1, -1);
-    }
-  }
+  if (p.texel_addr && valid)
+    for (int l = KP; l < p.kmax_out; ++l)
+      *reinterpret_cast<int4*>(p.texel_addr + (gq * p.kmax_out + l) * 4) = make_int4(-1, -1, -1, -1);
 }
 
 // Issue the MMAs of one layer (single thread) and commit to the mbarrier.
@@ -155,7 +218,7 @@ __device__ __forceinline__ void issue_layer(int layer, uint32_t act_sa, uint32_t
 }
 
 template <class S, typename TT>
-__global__ void __launch_bounds__(NT) fwd_kernel(const __grid_constant__ QueryParams p) {
+__global__ void __launch_bounds__(NT, 4) fwd_kernel(const __grid_constant__ QueryParams p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* act = smem + S::OFF_ACT;
   int* node_sm = reinterpret_cast<int*>(smem + S::OFF_NODE);
@@ -190,9 +253,7 @@ __global__ void __launch_bounds__(NT) fwd_kernel(const __grid_constant__ QueryPa
     }
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * NT;
     const int nq = static_cast<int>(sc.q_end - q0 < NT ? sc.q_end - q0 : int64_t(NT));
-    f32::locate_tile<S::KPAD>(p, sc, q0, nq, node_sm, u_sm);
-    __syncthreads();
-    gather_bf16<S, TT>(p, sc, q0, nq, node_sm, u_sm, act);
+    locate_gather_bf16<S, TT>(p, sc, q0, nq, act, nullptr, nullptr);
     fence_proxy_async();
     __syncthreads();
 
@@ -346,9 +407,7 @@ __global__ void __launch_bounds__(NT) bwd_kernel(const __grid_constant__ QueryPa
     }
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * NT;
     const int nq = static_cast<int>(sc.q_end - q0 < NT ? sc.q_end - q0 : int64_t(NT));
-    f32::locate_tile<S::KPAD>(p, sc, q0, nq, node_sm, u_sm);
-    __syncthreads();
-    gather_bf16<S, TT>(p, sc, q0, nq, node_sm, u_sm, smem + S::OFF_H);
+    locate_gather_bf16<S, TT>(p, sc, q0, nq, smem + S::OFF_H, node_sm, u_sm);
     fence_proxy_async();
     __syncthreads();
 
@@ -509,32 +568,18 @@ __global__ void __launch_bounds__(NT) bwd_kernel(const __grid_constant__ QueryPa
 
 namespace {
 
-int sm_count() {
-  int dev = 0, n = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-  return n > 0 ? n : 148;
-}
-
 template <class S, typename TT>
 int launch_fwd(const QueryParams& p, cudaStream_t stream) {
   if (p.n_tiles == 0) return OCTA_OK;
   auto kern = fwd_kernel<S, TT>;
-  static int per_sm = 0;  // one instantiation per template: cached on first (eager) use
-  if (per_sm == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(S::SMEM));
-    if (e != cudaSuccess) return fail(OCTA_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, S::SMEM);
-    if (e != cudaSuccess) return fail(OCTA_ECUDA, "occupancy: %s", cudaGetErrorString(e));
-    // tensor memory (512 columns per SM) must hold every resident CTA
-    per_sm = std::max(1, std::min(occ, static_cast<int>(512 / S::TMEM_COLS)));
-  }
-  const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * sm_count());
+  int per_sm = 0;
+  int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, NT,
+                              static_cast<int>(S::TMEM_COLS), &per_sm);
+  if (rc) return rc;
+  const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * device_sm_count());
   kern<<<static_cast<unsigned>(grid), NT, S::SMEM, stream>>>(p);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(OCTA_ECUDA, "tc forward launch: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "tc fwd launch: %s", cudaGetErrorString(e));
   return OCTA_OK;
 }
 
@@ -542,20 +587,14 @@ template <class S, typename TT>
 int launch_bwd(const QueryParams& p, cudaStream_t stream) {
   if (p.n_tiles == 0) return OCTA_OK;
   auto kern = bwd_kernel<S, TT>;
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(S::SMEM));
-    if (e != cudaSuccess) return fail(OCTA_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, S::SMEM);
-    if (e != cudaSuccess) return fail(OCTA_ECUDA, "occupancy: %s", cudaGetErrorString(e));
-    per_sm = std::max(1, std::min(occ, static_cast<int>(512 / S::TMEM_COLS)));
-  }
-  const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * sm_count());
+  int per_sm = 0;
+  int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, NT,
+                              static_cast<int>(S::TMEM_COLS), &per_sm);
+  if (rc) return rc;
+  const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * device_sm_count());
   kern<<<static_cast<unsigned>(grid), NT, S::SMEM, stream>>>(p);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(OCTA_ECUDA, "tc backward launch: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "tc bwd launch: %s", cudaGetErrorString(e));
   return OCTA_OK;
 }
 

@@ -195,4 +195,39 @@ struct TexelLoad<__half, 4> {
   }
 };
 
+// Raw texel record kept in registers until the blend: the F features as
+// stored (8, 16 or 32 bytes), loaded with the matching vector width.
+template <typename TT, int F>
+struct TexelRaw {
+  static constexpr int BYTES = F * int(sizeof(TT));
+  static_assert(BYTES == 8 || BYTES == 16 || BYTES == 32, "texel size");
+  static constexpr int WORDS = BYTES / 4;
+  uint32_t w[WORDS];
+  __device__ __forceinline__ void load(const void* t, int64_t texel) {
+    if constexpr (BYTES == 8) {
+      const uint2 a = __ldg(reinterpret_cast<const uint2*>(t) + texel);
+      w[0] = a.x;
+      w[1] = a.y;
+    } else {
+      const uint4* p = reinterpret_cast<const uint4*>(t) + texel * (BYTES / 16);
+#pragma unroll
+      for (int i = 0; i < BYTES / 16; ++i) {
+        const uint4 a = __ldg(p + i);
+        w[4 * i] = a.x;
+        w[4 * i + 1] = a.y;
+        w[4 * i + 2] = a.z;
+        w[4 * i + 3] = a.w;
+      }
+    }
+  }
+  __device__ __forceinline__ float get(int f) const {
+    if constexpr (sizeof(TT) == 2) {
+      const uint32_t v = w[f >> 1];
+      return __half2float(__ushort_as_half(static_cast<unsigned short>((f & 1) ? (v >> 16) : (v & 0xFFFFu))));
+    } else {
+      return __uint_as_float(w[f]);
+    }
+  }
+};
+
 }  // namespace octa

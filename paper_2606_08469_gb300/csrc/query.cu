@@ -6,9 +6,9 @@
 
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 
 #include "engine_f32.cuh"
+#include "launch_util.h"
 #include "octa_internal.h"
 #include "tc_path.h"
 
@@ -55,68 +55,15 @@ __global__ void __launch_bounds__(f32::NT) encode_kernel(const __grid_constant__
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-
-int sm_count() {
-  static int cache[kMaxDevices] = {0};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 148;
-  if (cache[dev] == 0) {
-    int n = 0;
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    cache[dev] = n > 0 ? n : 148;
-  }
-  return cache[dev];
-}
-
-// Per-kernel launch facts, queried once per device (outside any stream
-// capture: the first call of each kernel must be eager).
-struct LaunchInfo {
-  const void* fn;
-  int dev;
-  size_t smem;
-  int per_sm;
-};
-LaunchInfo g_launch_cache[256];
-int g_launch_count = 0;
-std::mutex g_launch_mutex;
-
-template <class Kern>
-int blocks_per_sm(Kern kernel, size_t smem, int threads, int* out) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const void* fn = reinterpret_cast<const void*>(kernel);
-  std::lock_guard<std::mutex> lock(g_launch_mutex);
-  for (int i = 0; i < g_launch_count; ++i)
-    if (g_launch_cache[i].fn == fn && g_launch_cache[i].dev == dev &&
-        g_launch_cache[i].smem == smem) {
-      *out = g_launch_cache[i].per_sm;
-      return OCTA_OK;
-    }
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess)
-      return fail(OCTA_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-  }
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-  if (e != cudaSuccess) return fail(OCTA_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
-  if (per_sm < 1) return fail(OCTA_ECUDA, "kernel does not fit on an SM (smem %zu)", smem);
-  if (g_launch_count < 256) g_launch_cache[g_launch_count++] = LaunchInfo{fn, dev, smem, per_sm};
-  *out = per_sm;
-  return OCTA_OK;
-}
-
 // Persistent grid: as many CTAs as fit on the device, never more than tiles.
 template <class Kern>
 int launch_persistent(Kern kernel, size_t smem, const QueryParams& p, cudaStream_t stream,
                       int threads) {
   if (p.n_tiles == 0) return OCTA_OK;
   int per_sm = 0;
-  int rc = blocks_per_sm(kernel, smem, threads, &per_sm);
+  int rc = launch_cache().get(reinterpret_cast<const void*>(kernel), smem, threads, 0, &per_sm);
   if (rc) return rc;
-  const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * sm_count());
+  const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * device_sm_count());
   kernel<<<static_cast<unsigned>(grid), threads, smem, stream>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(OCTA_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
