@@ -87,11 +87,10 @@ __device__ void load_weights_bf16(const DevScene& sc, uint8_t* smem) {
 template <class S, typename TT>
 __device__ __forceinline__ void locate_gather_bf16(const QueryParams& p, const DevScene& sc,
                                                    int64_t q0, int nq, uint8_t* act,
-                                                   int* node_sm, float* u_sm) {
+                                                   int* node_sm, float* u_sm, int q) {
   constexpr int F = S::F, KP = S::KPAD;
   // levels gathered together: two for texels of up to 16 bytes, else one
   constexpr int WIN = TexelRaw<TT, F>::BYTES <= 16 ? 2 : 1;
-  const int q = threadIdx.x;
   const bool valid = q < nq;
   const int64_t gq = q0 + q;
   float x0 = 0.f, x1 = 0.f, x2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 1.f;
@@ -253,7 +252,7 @@ __global__ void __launch_bounds__(NT, 4) fwd_kernel(const __grid_constant__ Quer
     }
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * NT;
     const int nq = static_cast<int>(sc.q_end - q0 < NT ? sc.q_end - q0 : int64_t(NT));
-    locate_gather_bf16<S, TT>(p, sc, q0, nq, act, nullptr, nullptr);
+    locate_gather_bf16<S, TT>(p, sc, q0, nq, act, nullptr, nullptr, threadIdx.x);
     fence_proxy_async();
     __syncthreads();
 
@@ -310,53 +309,75 @@ __global__ void __launch_bounds__(NT, 4) fwd_kernel(const __grid_constant__ Quer
 // ---------------------------------------------------------------------------
 // Backward (recomputed forward, then the delta chain on the tensor cores)
 // ---------------------------------------------------------------------------
-// Shared memory: weights | h tile | a_1 .. a_NH tiles | delta_L tile | slack |
-// node / u tables | mbarrier.  Tensor memory: a working accumulator of WORK
-// columns (every forward layer and every data-gradient GEMM), then the
-// transposed weight gradients dW_i^T = a_i^T delta_{i+1} (rows = input
-// features, one column per output feature), accumulated over every tile the
-// CTA handles and flushed with atomics when the scene changes or at the end.
+// A CTA of G = 2 groups of 128 threads works on two tiles of the same scene
+// at once; each group runs the per-tile pipeline below on its own shared-
+// memory region, mbarrier and tensor-memory working columns, synchronising
+// with named barriers.  The groups share the weights (shared memory) and the
+// transposed weight gradients dW_i^T = a_i^T delta_{i+1} (tensor memory:
+// rows = input features, one column per output feature), which every tile's
+// MMAs accumulate into; they are zeroed with tcgen05.st and flushed to the
+// FP32 weight gradient with coalesced atomics when the scene changes and at
+// the end.
+//   per tile: fused locate + gather into h; forward layers keeping the BF16
+//   activation tiles a_1..a_NH; delta_L = d_rgb * exp(z_L); then per layer
+//   dW_i^T += a_i^T delta (both read MN-major from the forward's K-major
+//   tiles) and G = delta W_i (W_i read MN-major); the epilogue masks G with
+//   1[a_i > 0] in place; layer 0's G = dh is scattered with float4 atomics.
 template <int F_, int WP_, int H_, int NH_>
 struct BShape : Shape<F_, WP_, H_, NH_> {
   using B = Shape<F_, WP_, H_, NH_>;
+  static constexpr int G = 2;
+  static constexpr int NTB = G * NT;
   static constexpr uint32_t H_TILE = NT * WP_ * 2;
   static constexpr uint32_t A_TILE = NT * H_ * 2;
   static constexpr uint32_t DL_TILE = NT * NOUT * 2;
-  static constexpr uint32_t OFF_H = B::W_BYTES;
-  static constexpr uint32_t OFF_DL = OFF_H + H_TILE + NH_ * A_TILE;
-  // MN-major reads with M = 128 rows run past a tile narrower than 128
-  // features into the next buffer; the slack keeps the last one in bounds.
-  static constexpr uint32_t OFF_NODE = OFF_DL + DL_TILE + 2048;
-  static constexpr uint32_t OFF_U = OFF_NODE + B::NODE_BYTES;
-  static constexpr uint32_t OFF_BAR = (OFF_U + B::U_BYTES + 15) & ~15u;
-  static constexpr size_t SMEM = OFF_BAR + 16;
+  // group region: h | a_1 .. a_NH | delta_L | slack | node | u.  MN-major
+  // reads with M = 128 rows run past a tile narrower than 128 features into
+  // the next buffer; the slack keeps the last one inside the region.
+  static constexpr uint32_t GR_DL = H_TILE + NH_ * A_TILE;
+  static constexpr uint32_t GR_NODE = GR_DL + DL_TILE + 2048;
+  static constexpr uint32_t GR_U = GR_NODE + B::NODE_BYTES;
+  static constexpr uint32_t GR_BYTES = (GR_U + B::U_BYTES + 1023) & ~1023u;
+  static constexpr uint32_t OFF_GROUP = (B::W_BYTES + 1023) & ~1023u;
+  static constexpr uint32_t OFF_BAR = OFF_GROUP + G * GR_BYTES;
+  static constexpr size_t SMEM = OFF_BAR + 8 * G + 8;
   static constexpr int WORK = WP_ > H_ ? WP_ : H_;
-  static constexpr int COLS = WORK + H_ * NH_ + NOUT;
+  static constexpr int DW0 = G * WORK;
+  static constexpr int DW_COLS = H_ * NH_ + NOUT;
+  static constexpr int COLS = DW0 + DW_COLS;
   static constexpr uint32_t TMEM_COLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128
                                         : COLS <= 256 ? 256 : 512;
   static_assert(COLS <= 512, "tensor memory");
-  __host__ __device__ static constexpr uint32_t off_act(int i) {
-    return i == 0 ? OFF_H : OFF_H + H_TILE + static_cast<uint32_t>(i - 1) * A_TILE;
+  static_assert(DW_COLS % 16 == 0, "dW columns");
+  __host__ __device__ static constexpr uint32_t off_act(int g, int i) {
+    return OFF_GROUP + static_cast<uint32_t>(g) * GR_BYTES +
+           (i == 0 ? 0u : H_TILE + static_cast<uint32_t>(i - 1) * A_TILE);
   }
-  __host__ __device__ static constexpr int dw_col(int i) { return WORK + H_ * i; }
+  __host__ __device__ static constexpr uint32_t off_dl(int g) {
+    return OFF_GROUP + static_cast<uint32_t>(g) * GR_BYTES + GR_DL;
+  }
+  __host__ __device__ static constexpr int dw_col(int i) { return DW0 + H_ * i; }
 };
 
-// Adds the CTA's dW^T accumulators of one scene to its FP32 weight gradient
-// (thread r holds row r = input feature r of every matrix).
+// Adds the dW^T accumulators of the matrices [i0, i1) to the scene's FP32
+// weight gradient and zeroes them (thread t holds row t = input feature t).
 template <class S>
-__device__ void flush_weight_grads(const DevScene& sc, uint32_t lane_base) {
-  const int r = threadIdx.x;
-  tc_fence_after_sync();
+__device__ void flush_weight_grads(const DevScene& sc, uint32_t lane_addr, int i0, int i1) {
+  const int r = threadIdx.x % NT;
+  uint32_t zero[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) zero[j] = 0u;
 #pragma unroll 1
-  for (int i = 0; i < S::NL; ++i) {
+  for (int i = i0; i < i1; ++i) {
     const int n_pad = S::ndim(i);
     const int in = sc.widths[i], out = sc.widths[i + 1];
     float* dW = sc.d_weights + sc.w_offset[i];
 #pragma unroll 1
     for (int c = 0; c < n_pad; c += 16) {
       uint32_t v[16];
-      tmem_ld16(lane_base + S::dw_col(i) + c, v);
+      tmem_ld16(lane_addr + S::dw_col(i) + c, v);
       tmem_wait_ld();
+      tmem_st16(lane_addr + S::dw_col(i) + c, zero);
       if (r < in) {
 #pragma unroll
         for (int j = 0; j < 16; ++j)
@@ -364,24 +385,29 @@ __device__ void flush_weight_grads(const DevScene& sc, uint32_t lane_base) {
       }
     }
   }
-  tc_fence_before_sync();
+  tmem_wait_st();
 }
 
 template <class S, typename TT>
-__global__ void __launch_bounds__(NT) bwd_kernel(const __grid_constant__ QueryParams p) {
+__global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ QueryParams p) {
   constexpr int H = S::H, NL = S::NL;
   extern __shared__ __align__(1024) uint8_t smem[];
-  int* node_sm = reinterpret_cast<int*>(smem + S::OFF_NODE);
-  float* u_sm = reinterpret_cast<float*>(smem + S::OFF_U);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::OFF_BAR);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::OFF_BAR + 8);
-  const uint32_t mbar = smem_addr(bar);
+  const int g = threadIdx.x / NT, t = threadIdx.x % NT, warp = threadIdx.x >> 5;
+  uint8_t* gbase = smem + S::OFF_GROUP + g * S::GR_BYTES;
+  int* node_sm = reinterpret_cast<int*>(gbase + S::GR_NODE);
+  float* u_sm = reinterpret_cast<float*>(gbase + S::GR_U);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::OFF_BAR);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::OFF_BAR + 8 * S::G);
+  __shared__ int abort_flag;
+  const uint32_t mbar = smem_addr(bars + g);
   const uint32_t base_sa = smem_addr(smem);
-  const uint32_t dl_sa = base_sa + S::OFF_DL;
-  const int warp = threadIdx.x >> 5;
-  const int q = threadIdx.x;
+  const uint32_t dl_sa = base_sa + S::off_dl(g);
+  const int gbar = 1 + g;  // named barrier of this group
 
-  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S::G; ++i) mbar_init(smem_addr(bars + i), 1);
+    abort_flag = 0;
+  }
   if (warp == 0) {
     tmem_alloc(smem_addr(tslot), S::TMEM_COLS);
     tmem_relinquish();
@@ -390,34 +416,67 @@ __global__ void __launch_bounds__(NT) bwd_kernel(const __grid_constant__ QueryPa
   __syncthreads();
   tc_fence_after_sync();
   const uint32_t tmem = *tslot;
-  const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  const uint32_t lane_addr = tmem + (static_cast<uint32_t>((warp % 4) * 32) << 16);
+  const uint32_t work = tmem + static_cast<uint32_t>(g * S::WORK);           // MMA D address
+  const uint32_t lane_work = lane_addr + static_cast<uint32_t>(g * S::WORK);  // epilogue loads
+  if (g == 0) {  // zero the shared dW^T accumulators
+    uint32_t zero[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) zero[j] = 0u;
+#pragma unroll 1
+    for (int c = 0; c < S::DW_COLS; c += 16) tmem_st16(lane_addr + S::DW0 + c, zero);
+    tmem_wait_st();
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
   uint32_t phase = 0;
   int cur = -1;
-  bool first = true, failed = false;
 
-  for (int64_t tile = blockIdx.x; tile < p.n_tiles && !failed; tile += gridDim.x) {
-    const int s = scene_of_tile(p, tile);
+  for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+    int s = 0;
+    while (s + 1 < p.n_scenes && item >= p.item_begin[s + 1]) ++s;
     const DevScene& sc = p.sc[s];
+    tc_fence_before_sync();
     __syncthreads();
+    if (abort_flag) break;
     if (s != cur) {
-      if (cur >= 0 && !first) flush_weight_grads<S>(p.sc[cur], lane_base);
-      load_weights_bf16<S>(sc, smem);
+      tc_fence_after_sync();
+      if (cur >= 0) {
+        flush_weight_grads<S>(p.sc[cur], lane_addr, g == 0 ? 0 : NL / 2, g == 0 ? NL / 2 : NL);
+        tc_fence_before_sync();
+      }
+      for (int l = 0; l < S::NL; ++l) {  // weights, all 256 threads
+        const int K = S::kdim(l), N = S::ndim(l);
+        const int in = sc.widths[l], out = sc.widths[l + 1];
+        const __nv_bfloat16* Wg = static_cast<const __nv_bfloat16*>(sc.weights);
+        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(smem + S::w_off(l));
+        for (int i = threadIdx.x; i < N * K; i += S::NTB) {
+          const int n = i / K, k = i % K;
+          dst[kmajor_offset(n, k, K) / 2] =
+              (n < out && k < in) ? Wg[sc.w_offset[l] + n * in + k] : __float2bfloat16_rn(0.f);
+        }
+      }
       cur = s;
-      first = true;
+      __syncthreads();
     }
-    const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * NT;
+    const int64_t tiles_s = (sc.q_end - sc.q_begin + NT - 1) / NT;
+    const int64_t tile_s = 2 * (item - p.item_begin[s]) + g;
+    if (tile_s >= tiles_s) continue;  // odd tile count: this group idles
+    const int64_t q0 = sc.q_begin + tile_s * NT;
     const int nq = static_cast<int>(sc.q_end - q0 < NT ? sc.q_end - q0 : int64_t(NT));
-    locate_gather_bf16<S, TT>(p, sc, q0, nq, smem + S::OFF_H, node_sm, u_sm);
+    locate_gather_bf16<S, TT>(p, sc, q0, nq, smem + S::off_act(g, 0), node_sm, u_sm, t);
     fence_proxy_async();
-    __syncthreads();
+    named_sync(gbar, NT);
 
+    bool failed = false;
     // ---- forward, keeping a_1 .. a_NH and delta_L
 #pragma unroll 1
-    for (int layer = 0; layer < NL && !failed; ++layer) {
-      if (threadIdx.x == 0) issue_layer<S>(layer, base_sa + S::off_act(layer), base_sa, tmem, mbar);
+    for (int layer = 0; layer < NL; ++layer) {
+      if (t == 0) issue_layer<S>(layer, base_sa + S::off_act(g, layer), base_sa, work, mbar);
       const bool ok = mbar_wait_bounded(mbar, phase);
       phase ^= 1u;
-      if (__syncthreads_or(!ok)) {
+      if (named_sync_or(gbar, NT, !ok)) {
         failed = true;
         break;
       }
@@ -426,9 +485,9 @@ __global__ void __launch_bounds__(NT) bwd_kernel(const __grid_constant__ QueryPa
         uint32_t r[H];
 #pragma unroll
         for (int c = 0; c < H; c += 16)
-          tmem_ld16(lane_base + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
+          tmem_ld16(lane_work + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
         tmem_wait_ld();
-        uint8_t* dst = smem + S::off_act(layer + 1);
+        uint8_t* dst = smem + S::off_act(g, layer + 1);
 #pragma unroll
         for (int c = 0; c < H; c += 8) {
           uint4 o;
@@ -436,62 +495,61 @@ __global__ void __launch_bounds__(NT) bwd_kernel(const __grid_constant__ QueryPa
           o.y = pack_bf16x2(fmaxf(__uint_as_float(r[c + 2]), 0.f), fmaxf(__uint_as_float(r[c + 3]), 0.f));
           o.z = pack_bf16x2(fmaxf(__uint_as_float(r[c + 4]), 0.f), fmaxf(__uint_as_float(r[c + 5]), 0.f));
           o.w = pack_bf16x2(fmaxf(__uint_as_float(r[c + 6]), 0.f), fmaxf(__uint_as_float(r[c + 7]), 0.f));
-          *reinterpret_cast<uint4*>(dst + kmajor_offset(q, c, H)) = o;
+          *reinterpret_cast<uint4*>(dst + kmajor_offset(t, c, H)) = o;
         }
       } else {
         uint32_t r[16];
-        tmem_ld16(lane_base, r);
+        tmem_ld16(lane_work, r);
         tmem_wait_ld();
         float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-        if (q < nq) {
-          const int64_t gq = q0 + q;
+        if (t < nq) {
+          const int64_t gq = q0 + t;
           d0 = p.d_rgb[3 * gq];
           d1 = p.d_rgb[3 * gq + 1];
           d2 = p.d_rgb[3 * gq + 2];
         }
         // delta_L = d_rgb * exp(z_L): the derivative of exp is exp
-        uint8_t* dst = smem + S::OFF_DL;
+        uint8_t* dst = smem + S::off_dl(g);
         uint4 o0, o1;
         o0.x = pack_bf16x2(d0 * expf(__uint_as_float(r[0])), d1 * expf(__uint_as_float(r[1])));
         o0.y = pack_bf16x2(d2 * expf(__uint_as_float(r[2])), 0.f);
         o0.z = o0.w = 0u;
         o1.x = o1.y = o1.z = o1.w = 0u;
-        *reinterpret_cast<uint4*>(dst + kmajor_offset(q, 0, NOUT)) = o0;
-        *reinterpret_cast<uint4*>(dst + kmajor_offset(q, 8, NOUT)) = o1;
+        *reinterpret_cast<uint4*>(dst + kmajor_offset(t, 0, NOUT)) = o0;
+        *reinterpret_cast<uint4*>(dst + kmajor_offset(t, 8, NOUT)) = o1;
       }
       fence_proxy_async();
       tc_fence_before_sync();
-      __syncthreads();
+      named_sync(gbar, NT);
     }
-    if (failed) break;
 
     // ---- backward through the decoder
 #pragma unroll 1
-    for (int i = NL - 1; i >= 0; --i) {
+    for (int i = NL - 1; i >= 0 && !failed; --i) {
       const int out = S::ndim(i), in = S::kdim(i);
-      const uint32_t d_sa = i == NL - 1 ? dl_sa : base_sa + S::off_act(i + 1);
+      const uint32_t d_sa = i == NL - 1 ? dl_sa : base_sa + S::off_act(g, i + 1);
       const int dk = out;  // row length of the delta tile
-      if (threadIdx.x == 0) {
+      if (t == 0) {
         tc_fence_after_sync();
         // dW_i^T += a_i^T delta_{i+1}: M = 128 input features, N = out, K = 128 queries
-        const uint32_t act_sa = base_sa + S::off_act(i);
+        const uint32_t act_sa = base_sa + S::off_act(g, i);
         const uint32_t idw = idesc_bf16(128, out, 1, 1);
 #pragma unroll 1
         for (int kq = 0; kq < NT; kq += 16)
           mma_bf16(tmem + S::dw_col(i), mnmajor_desc(act_sa, kq, in), mnmajor_desc(d_sa, kq, dk),
-                   idw, (!first || kq > 0) ? 1u : 0u);
+                   idw, 1u);
         // G = delta_{i+1} W_i: M = 128 queries, N = in, K = out
         const uint32_t ig = idesc_bf16(128, in, 0, 1);
         const uint32_t w_sa = base_sa + S::w_off(i);
 #pragma unroll 1
         for (int ko = 0; ko < out; ko += 16)
-          mma_bf16(tmem, kmajor_desc(d_sa, ko, dk), mnmajor_desc(w_sa, ko, in), ig,
+          mma_bf16(work, kmajor_desc(d_sa, ko, dk), mnmajor_desc(w_sa, ko, in), ig,
                    ko > 0 ? 1u : 0u);
         mma_commit(mbar);
       }
       const bool ok = mbar_wait_bounded(mbar, phase);
       phase ^= 1u;
-      if (__syncthreads_or(!ok)) {
+      if (named_sync_or(gbar, NT, !ok)) {
         failed = true;
         break;
       }
@@ -501,12 +559,12 @@ __global__ void __launch_bounds__(NT) bwd_kernel(const __grid_constant__ QueryPa
         uint32_t r[H];
 #pragma unroll
         for (int c = 0; c < H; c += 16)
-          tmem_ld16(lane_base + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
+          tmem_ld16(lane_work + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
         tmem_wait_ld();
-        uint8_t* act = smem + S::off_act(i);
+        uint8_t* act = smem + S::off_act(g, i);
 #pragma unroll
         for (int c = 0; c < H; c += 8) {
-          uint4* pa = reinterpret_cast<uint4*>(act + kmajor_offset(q, c, H));
+          uint4* pa = reinterpret_cast<uint4*>(act + kmajor_offset(t, c, H));
           const uint4 a = *pa;
           const uint32_t av[4] = {a.x, a.y, a.z, a.w};
           uint32_t ov[4];
@@ -521,23 +579,23 @@ __global__ void __launch_bounds__(NT) bwd_kernel(const __grid_constant__ QueryPa
         }
         fence_proxy_async();
         tc_fence_before_sync();
-        __syncthreads();
+        named_sync(gbar, NT);
       } else {
         // dh = G; scatter w_k * dh_l into the four texels of every present level
         uint32_t r[S::WP];
 #pragma unroll
         for (int c = 0; c < S::WP; c += 16)
-          tmem_ld16(lane_base + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
+          tmem_ld16(lane_work + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
         tmem_wait_ld();
         tc_fence_before_sync();
 #pragma unroll
         for (int l = 0; l < S::KPAD; ++l) {
-          const int node = node_sm[l * NT + q];
+          const int node = node_sm[l * NT + t];
           if (node < 0) continue;
           const int R = sc.R[l];
           const int64_t mo = f32::map_base(p, sc, node, R);
           if (mo < 0) continue;
-          const Footprint fp = footprint(u_sm[q], u_sm[NT + q], R);
+          const Footprint fp = footprint(u_sm[t], u_sm[NT + t], R);
 #pragma unroll
           for (int c4 = 0; c4 < S::F / 4; ++c4) {
             const float g0 = __uint_as_float(r[l * S::F + 4 * c4 + 0]);
@@ -554,13 +612,16 @@ __global__ void __launch_bounds__(NT) bwd_kernel(const __grid_constant__ QueryPa
         }
       }
     }
-    first = false;
+    if (failed && t == 0) {
+      abort_flag = 1;
+      if (p.status) atomicOr(p.status, OCTA_STATUS_TIMEOUT);
+    }
   }
-  if (!failed && cur >= 0 && !first) {
-    __syncthreads();
-    flush_weight_grads<S>(p.sc[cur], lane_base);
-  }
-  if (failed && threadIdx.x == 0 && p.status) atomicOr(p.status, OCTA_STATUS_TIMEOUT);
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  if (cur >= 0 && !abort_flag)
+    flush_weight_grads<S>(p.sc[cur], lane_addr, g == 0 ? 0 : NL / 2, g == 0 ? NL / 2 : NL);
   tc_fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, S::TMEM_COLS);
@@ -584,15 +645,24 @@ int launch_fwd(const QueryParams& p, cudaStream_t stream) {
 }
 
 template <class S, typename TT>
-int launch_bwd(const QueryParams& p, cudaStream_t stream) {
-  if (p.n_tiles == 0) return OCTA_OK;
+int launch_bwd(const QueryParams& p0, cudaStream_t stream) {
+  if (p0.n_tiles == 0) return OCTA_OK;
+  QueryParams p = p0;  // work items: pairs of tiles of one scene
+  int64_t items = 0;
+  for (int s = 0; s < p.n_scenes; ++s) {
+    p.item_begin[s] = items;
+    const int64_t tiles = (p.sc[s].q_end - p.sc[s].q_begin + NT - 1) / NT;
+    items += (tiles + S::G - 1) / S::G;
+  }
+  p.item_begin[p.n_scenes] = items;
+  p.n_items = items;
   auto kern = bwd_kernel<S, TT>;
   int per_sm = 0;
-  int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, NT,
+  int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, S::NTB,
                               static_cast<int>(S::TMEM_COLS), &per_sm);
   if (rc) return rc;
-  const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * device_sm_count());
-  kern<<<static_cast<unsigned>(grid), NT, S::SMEM, stream>>>(p);
+  const int64_t grid = std::min<int64_t>(items, int64_t(per_sm) * device_sm_count());
+  kern<<<static_cast<unsigned>(grid), S::NTB, S::SMEM, stream>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(OCTA_ECUDA, "tc bwd launch: %s", cudaGetErrorString(e));
   return OCTA_OK;

@@ -48,6 +48,10 @@ struct QueryParams {
   void* features;
   int64_t row_stride;
   int32_t feat_dtype;
+  // work items of kernels that take several tiles of one scene at a time:
+  // scene s owns items [item_begin[s], item_begin[s+1])
+  int64_t n_items;
+  int64_t item_begin[OCTA_MAX_SCENES + 1];
 };
 
 // Scene owning global tile t (tiles never straddle scenes).
