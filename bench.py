@@ -223,8 +223,11 @@ def inference_leg(dev, flush, stream, steps, peaks):
             fn = lambda: api.octa_query_fwd(sc, X, Om, rgb=rgb)
             for _ in range(3):
                 fn()
-            t = _timed(fn, steps, flush, stream)
-            res[prec] = {"ms_per_frame": round(t, 4), "Mq/s": round(len(x) / t / 1e3, 1)}
+            g = _graph(fn, stream)
+            g.replay()
+            t = _timed(g.replay, steps, flush, stream)
+            res[prec] = {"ms_per_frame": round(t, 4), "Mq/s": round(len(x) / t / 1e3, 1),
+                         "timing": "CUDA-graph replay"}
             if prec == "bf16":
                 peak = float(peaks.get("bf16_tflops", 1886.6))
                 ach = fwd_flop * len(x) / (t / 1e3) / 1e12
@@ -232,6 +235,68 @@ def inference_leg(dev, flush, stream, steps, peaks):
                                          "unit": "TFLOP/s", "frac": round(ach / peak, 5)}
         out[f"{w_}x{h_}"] = res
     return out
+
+
+def _graph(fn, stream):
+    """Capture fn (already run eagerly) into a CUDA graph on a side stream."""
+    import torch
+    side = torch.cuda.Stream(device=stream.device)
+    side.wait_stream(stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            fn()
+    stream.wait_stream(side)
+    return g
+
+
+def small_forward_leg(dev, flush, stream, steps):
+    """Config [0]: 16,384 queries, depth-4 tree, F=4 FP32, decoder 20-32-32-3
+    (FP32 path), replayed from a CUDA graph."""
+    import torch
+    from paper_2606_08469_gb300 import api
+    from paper_2606_08469_gb300 import inputs as I
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[0]
+    sc, _ = WL.forward_scene(cfg, device=dev)
+    x, om = WL.queries_for(cfg)
+    X, Om = WL.to_dev(x, dev), WL.to_dev(om, dev)
+    rgb = torch.empty((len(x), 3), device=dev)
+    nodes = torch.empty((len(x), cfg.num_levels), dtype=torch.int32, device=dev)
+    addr = torch.empty((len(x), cfg.num_levels, 4), dtype=torch.int32, device=dev)
+    q = api._queries(X, Om, None)
+    arr, ns = api._scene_array(sc)
+    lib = api._lib()
+
+    def fn():
+        api.L.check(lib.octa_query_fwd(arr, ns, api.C.byref(q), api._ptr(rgb), api._ptr(nodes),
+                                       api._ptr(addr), None, api._stream()), "octa_query_fwd")
+    fn()
+    g = _graph(fn, stream)
+    g.replay()
+    t = _timed(g.replay, steps, flush, stream)
+    return {"workload": "config[0] forward: 16384 queries, depth-4 octree, F=4 FP32, decoder 20-32-32-3, "
+                        "node indices and texel addresses written, CUDA-graph replay",
+            "ms": round(t, 5), "Mq/s": round(len(x) / t / 1e3, 1)}
+
+
+def batched_leg(dev, flush, stream, steps):
+    """Config [4]: 8 octrees (depth 4..9) with their own BF16 decoders and
+    log-uniform pair counts, forward + loss + backward + Adam of all scenes,
+    replayed from one captured CUDA graph."""
+    from paper_2606_08469_gb300 import inputs as I
+    from paper_2606_08469_gb300 import workloads as WL
+    counts = I.batched_pair_counts()
+    step, _ = WL.batched_train_step(device=dev)
+    for _ in range(3):
+        step.step()
+    g = _graph(step.step, stream)
+    g.replay()
+    t = _timed(g.replay, steps, flush, stream)
+    nq = 2 * sum(counts)
+    return {"workload": f"config[4] batched training step: 8 scenes (depth 4..9), pairs per scene {counts}, "
+                        "BF16 decoders 8L-64-64-3, FP16 tables, one CUDA-graph replay per step",
+            "ms_per_step": round(t, 4), "Mq/s": round(nq / t / 1e3, 1), "queries": nq}
 
 
 def run_ours(args):
@@ -383,6 +448,8 @@ def run_ours(args):
         if not args.no_extra:
             out["bf16_vs_f32"] = bf16_vs_f32_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
             out["inference"] = inference_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
+            out["small_forward"] = small_forward_leg(dev, flush, stream, max(5, args.steps // 2))
+            out["batched"] = batched_leg(dev, flush, stream, max(5, args.steps // 2))
         out["cpu_baseline"] = cpu_baseline() if not args.no_cpu else None
         print(json.dumps(out), flush=True)
     if world > 1:

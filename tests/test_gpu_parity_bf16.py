@@ -255,3 +255,36 @@ def test_bf16_train_step_config2_shapes():
     d_ref = st.tables - T
     d_gpu = step.states[0].master_t.cpu().numpy() - T
     assert np.linalg.norm(d_gpu - d_ref) <= 0.2 * np.linalg.norm(d_ref)
+
+
+def test_bf16_backward_batched_scenes():
+    """Three scenes in one backward launch (tile counts 3, 32 and 1, so one
+    group idles in some work items and the dW accumulators are flushed at
+    every scene change) against the per-scene FP64 oracle."""
+    from paper_2606_08469_gb300 import api as A
+    specs = [(1400, 4), (1402, 6), (1407, 9)]
+    counts = [300, 4096, 77]
+    parts = [make_bf16_scene(seed, depth, I.R_DEEP[:depth + 1], 8, 0.3, [64, 64], wscale=1.5,
+                             tseed=2400 + s, wseed=3400 + s)
+             for s, (seed, depth) in enumerate(specs)]
+    xs, ws = zip(*[I.uniform_queries(4500 + s, n) for s, n in enumerate(counts)])
+    X, W = np.concatenate(xs), np.concatenate(ws)
+    d_rgb = np.random.default_rng(10).normal(size=(len(X), 3)).astype(np.float32)
+    grads = [(torch.zeros(p[0].tables.shape, device=DEV), torch.zeros(p[0].weights.shape, device=DEV))
+             for p in parts]
+    A.octa_query_bwd([p[0] for p in parts], dev(X), dev(W), dev(d_rgb), grads, counts)
+    off = 0
+    for s, n in enumerate(counts):
+        sc, ot, tables, weights, tq, wq = parts[s]
+        sl = slice(off, off + n)
+        rT, rWs, _ = O.query_backward(ot, tq, wq, xs[s], ws[s], d_rgb[sl])
+        enc = O.encode_features(ot, tq, xs[s], ws[s])
+        frac = float(np.mean(np.concatenate([m.ravel() < 1.0 for m in _mask_margin(wq, enc.h)])))
+        gT, gW = grads[s][0].cpu().numpy(), grads[s][1].cpu().numpy()
+        errs = [normwise(gT, rT)]
+        for (o_, a, b), rW in zip(sc.weight_slices(), rWs):
+            errs.append(normwise(gW[o_:o_ + a * b].reshape(a, b), rW))
+        print("batched scene", s, round(frac, 4), [round(e, 4) for e in errs])
+        assert errs[-1] <= 1e-2
+        assert max(errs) <= 3.0 * np.sqrt(frac) + 1e-2
+        off += n
