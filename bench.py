@@ -175,27 +175,31 @@ def bf16_vs_f32_leg(dev, flush, stream, steps, peaks):
                        "1048576 pairs = 2097152 queries, dynamic loss scaling"}
     W = cfg.widths
     fwd_flop = 2 * sum(a * b for a, b in zip(W[:-1], W[1:]))
-    for prec in ("bf16", "f32"):
-        step, _ = WL.train_step_for(cfg, device=dev, precision=None if prec == "bf16" else "f32")
+    for prec in ("bf16", "bf16_unfused", "f32"):
+        step, _ = WL.train_step_for(cfg, device=dev, precision="f32" if prec == "f32" else None,
+                                    fused=prec == "bf16")
         for _ in range(3):
             step.step()
-        torch_sync = stream.synchronize
-        torch_sync()
+        stream.synchronize()
         t_step = _timed(step.step, steps, flush, stream)
-        step.forward()
-        t_fwd = _timed(step.forward, steps, flush, stream)
-        step.loss_and_grad()
-        t_bwd = _timed(step.backward, steps, flush, stream)
         nq = 2 * cfg.n
         sc = api.read_scaler(step.scaler)
         leg = {"Mq/s": round(nq / t_step / 1e3, 2), "ms_per_step": round(t_step, 4),
-               "fwd_ms": round(t_fwd, 4), "bwd_ms": round(t_bwd, 4), "loss": float(step.loss.item()),
-               "loss_scale": float(sc.scale)}
+               "loss": float(step.loss.item()), "loss_scale": float(sc.scale)}
         if prec == "bf16":
+            t_pass = _timed(step.fused_pass, steps, flush, stream)
             peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
-            ach = 3 * fwd_flop * nq / (t_bwd / 1e3) / 1e12
-            leg["roofline_bwd"] = {"bound": "tensor", "achieved": round(ach, 2), "peak": peak,
-                                   "unit": "TFLOP/s", "frac": round(ach / peak, 5)}
+            ach = 3 * fwd_flop * nq / (t_pass / 1e3) / 1e12
+            leg["fused_pass_ms"] = round(t_pass, 4)
+            leg["roofline_fused_pass"] = {"bound": "tensor", "achieved": round(ach, 2), "peak": peak,
+                                          "unit": "TFLOP/s", "frac": round(ach / peak, 5)}
+            leg["path"] = "octa_train_fused (forward + Eq.14 gradient + backward in one launch) + adam_step"
+        else:
+            step.forward()
+            leg["fwd_ms"] = round(_timed(step.forward, steps, flush, stream), 4)
+            step.loss_and_grad()
+            leg["bwd_ms"] = round(_timed(step.backward, steps, flush, stream), 4)
+            leg["path"] = "octa_query_fwd + residual_loss + octa_query_bwd + adam_step"
         out[prec] = leg
         del step
     out["speedup_bf16_over_f32"] = round(out["bf16"]["Mq/s"] / out["f32"]["Mq/s"], 3)
@@ -287,7 +291,7 @@ def batched_leg(dev, flush, stream, steps):
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
     counts = I.batched_pair_counts()
-    step, _ = WL.batched_train_step(device=dev)
+    step, _ = WL.batched_train_step(device=dev, fused=True)
     for _ in range(3):
         step.step()
     g = _graph(step.step, stream)
@@ -295,7 +299,8 @@ def batched_leg(dev, flush, stream, steps):
     t = _timed(g.replay, steps, flush, stream)
     nq = 2 * sum(counts)
     return {"workload": f"config[4] batched training step: 8 scenes (depth 4..9), pairs per scene {counts}, "
-                        "BF16 decoders 8L-64-64-3, FP16 tables, one CUDA-graph replay per step",
+                        "BF16 decoders 8L-64-64-3, FP16 tables, fused training pass + Adam, one CUDA-graph replay "
+                        "per step",
             "ms_per_step": round(t, 4), "Mq/s": round(nq / t / 1e3, 1), "queries": nq}
 
 

@@ -221,6 +221,35 @@ int residual_loss_static(const float* L_p, const float* L_s, const float* E, con
                          const octa_scaler* scaler, double* loss_dev, float* dL_p, float* dL_s,
                          void* stream);
 
+/* Training pairs: pair i of scene s (scene_start[s] <= i < scene_start[s+1])
+ * is the primary query (x[i], omega[i]) and the secondary query
+ * (x2[i], omega2[i]); omega2 is the secondary query's direction itself,
+ * i.e. -omega' for a sampled incident direction omega' (Eq. 2).          */
+typedef struct octa_pairs {
+  const float* x;              /* device [n][3] primary positions           */
+  const float* omega;          /* device [n][3] primary outgoing directions */
+  const float* x2;             /* device [n][3] secondary positions x'      */
+  const float* omega2;         /* device [n][3] secondary query directions  */
+  const float* E;              /* device [n][3] emitted radiance at x       */
+  const float* w;              /* device [n][3] f_r |n.omega'| / p(omega')  */
+  int64_t n;
+  int64_t scene_start[OCTA_MAX_SCENES + 1];
+} octa_pairs;
+
+/* octa_train_fused -- octa_query_fwd + residual_loss + octa_query_bwd of a
+ * training batch in one launch (BF16 decoders on the tensor cores only).
+ * Every 64-pair tile runs the primary and secondary queries together, forms
+ * the Eq. 14 gradient of each pair from its two radiances in the tile
+ * (the target's dependence on the secondary query enters iff rhs_grad; the
+ * normaliser is detached), and back-propagates into the tables and the
+ * decoder (gradients of S * loss, S = scaler->scale or 1; accumulated into
+ * grads as in octa_query_bwd).  loss_dev: device double [n_scenes], set to
+ * each scene's mean r^2 over its pairs and channels (zeroed by the call;
+ * FP64 partials, summed with atomics).  OCTA_EUNSUPPORTED for FP32 decoders.*/
+int octa_train_fused(const octa_scene* scenes, int32_t n_scenes, const octa_pairs* pairs,
+                     float eps, int32_t rhs_grad, const octa_scaler* scaler, double* loss_dev,
+                     const octa_scene_grads* grads, int32_t* status, void* stream);
+
 /* One parameter group of adam_step (all device pointers, n elements).     */
 typedef struct octa_param_group {
   float* param;                /* FP32 master copy                          */

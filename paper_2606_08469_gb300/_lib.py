@@ -77,6 +77,19 @@ class octa_scene_grads(C.Structure):
     _fields_ = [("d_tables", C.c_void_p), ("d_weights", C.c_void_p)]
 
 
+class octa_pairs(C.Structure):
+    _fields_ = [
+        ("x", C.c_void_p),
+        ("omega", C.c_void_p),
+        ("x2", C.c_void_p),
+        ("omega2", C.c_void_p),
+        ("E", C.c_void_p),
+        ("w", C.c_void_p),
+        ("n", C.c_int64),
+        ("scene_start", C.c_int64 * (OCTA_MAX_SCENES + 1)),
+    ]
+
+
 class octa_scaler(C.Structure):
     _fields_ = [
         ("scale", C.c_float),
@@ -122,6 +135,8 @@ _SIGNATURES = {
                                  _P, _P, _P, _P]),
     "octa_query_bwd": (C.c_int, [C.POINTER(octa_scene), C.c_int32, C.POINTER(octa_queries), _P,
                                  C.POINTER(octa_scene_grads), _P, _P]),
+    "octa_train_fused": (C.c_int, [C.POINTER(octa_scene), C.c_int32, C.POINTER(octa_pairs), C.c_float,
+                                   C.c_int32, _P, _P, C.POINTER(octa_scene_grads), _P, _P]),
     "residual_loss": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_float, C.c_int32, _P, _P, _P, _P,
                                 _P, C.c_size_t, _P]),
     "residual_loss_static": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_float, C.c_int32, _P, _P,

@@ -220,6 +220,27 @@ def octa_query_bwd(scenes, x, omega, d_rgb, grads, counts=None, status=None, str
                                   _stream(stream)), "octa_query_bwd")
 
 
+def octa_train_fused(scenes, x, omega, x2, omega2, E, w, grads, loss_out, counts=None, eps=1e-2,
+                     rhs_grad=True, scaler=None, status=None, stream=None):
+    """Fused forward + Eq. 14 loss + backward over training pairs (BF16)."""
+    arr, ns = _scene_array(scenes)
+    g = (L.octa_scene_grads * ns)(*[L.octa_scene_grads(dt.data_ptr(), dw.data_ptr())
+                                    for dt, dw in grads])
+    pr = L.octa_pairs()
+    n = int(x.shape[0])
+    pr.x, pr.omega, pr.x2, pr.omega2 = (t.data_ptr() if n else None for t in (x, omega, x2, omega2))
+    pr.E, pr.w = (t.data_ptr() if n else None for t in (E, w))
+    pr.n = n
+    counts = [n] if counts is None else list(counts)
+    acc = 0
+    for i, c in enumerate(counts):
+        acc += c
+        pr.scene_start[i + 1] = acc
+    L.check(_lib().octa_train_fused(arr, ns, C.byref(pr), C.c_float(eps), int(bool(rhs_grad)),
+                                    _ptr(scaler), _ptr(loss_out), g, _ptr(status), _stream(stream)),
+            "octa_train_fused")
+
+
 # ---------------------------------------------------------------------------
 # loss, optimiser
 # ---------------------------------------------------------------------------

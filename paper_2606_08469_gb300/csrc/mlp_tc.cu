@@ -86,21 +86,21 @@ __device__ void load_weights_bf16(const DevScene& sc, uint8_t* smem) {
 // u_sm (nullable) keep the path and the folded direction for a later scatter.
 template <class S, typename TT>
 __device__ __forceinline__ void locate_gather_bf16(const QueryParams& p, const DevScene& sc,
-                                                   int64_t q0, int nq, uint8_t* act,
-                                                   int* node_sm, float* u_sm, int q) {
+                                                   const float* __restrict__ xs,
+                                                   const float* __restrict__ ws, int64_t gq,
+                                                   bool valid, uint8_t* act, int* node_sm,
+                                                   float* u_sm, int q) {
   constexpr int F = S::F, KP = S::KPAD;
   // levels gathered together: two for texels of up to 16 bytes, else one
   constexpr int WIN = TexelRaw<TT, F>::BYTES <= 16 ? 2 : 1;
-  const bool valid = q < nq;
-  const int64_t gq = q0 + q;
   float x0 = 0.f, x1 = 0.f, x2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 1.f;
   if (valid) {
-    x0 = p.x[3 * gq];
-    x1 = p.x[3 * gq + 1];
-    x2 = p.x[3 * gq + 2];
-    w0 = p.omega[3 * gq];
-    w1 = p.omega[3 * gq + 1];
-    w2 = p.omega[3 * gq + 2];
+    x0 = xs[3 * gq];
+    x1 = xs[3 * gq + 1];
+    x2 = xs[3 * gq + 2];
+    w0 = ws[3 * gq];
+    w1 = ws[3 * gq + 1];
+    w2 = ws[3 * gq + 2];
   }
   float ux, uy;
   octa_fold(w0, w1, w2, ux, uy);
@@ -252,7 +252,8 @@ __global__ void __launch_bounds__(NT, 4) fwd_kernel(const __grid_constant__ Quer
     }
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * NT;
     const int nq = static_cast<int>(sc.q_end - q0 < NT ? sc.q_end - q0 : int64_t(NT));
-    locate_gather_bf16<S, TT>(p, sc, q0, nq, act, nullptr, nullptr, threadIdx.x);
+    locate_gather_bf16<S, TT>(p, sc, p.x, p.omega, q0 + threadIdx.x, int(threadIdx.x) < nq, act,
+                              nullptr, nullptr, threadIdx.x);
     fence_proxy_async();
     __syncthreads();
 
@@ -337,7 +338,8 @@ struct BShape : Shape<F_, WP_, H_, NH_> {
   static constexpr uint32_t GR_DL = H_TILE + NH_ * A_TILE;
   static constexpr uint32_t GR_NODE = GR_DL + DL_TILE + 2048;
   static constexpr uint32_t GR_U = GR_NODE + B::NODE_BYTES;
-  static constexpr uint32_t GR_BYTES = (GR_U + B::U_BYTES + 1023) & ~1023u;
+  static constexpr uint32_t GR_XCH = GR_U + B::U_BYTES;  // [64][4] floats (fused pass)
+  static constexpr uint32_t GR_BYTES = (GR_XCH + 64 * 4 * 4 + 1023) & ~1023u;
   static constexpr uint32_t OFF_GROUP = (B::W_BYTES + 1023) & ~1023u;
   static constexpr uint32_t OFF_BAR = OFF_GROUP + G * GR_BYTES;
   static constexpr size_t SMEM = OFF_BAR + 8 * G + 8;
@@ -388,9 +390,33 @@ __device__ void flush_weight_grads(const DevScene& sc, uint32_t lane_addr, int i
   tmem_wait_st();
 }
 
-template <class S, typename TT>
+// Loss partials of a fused training pass: every thread's FP64 sum of r^2 for
+// the current scene is added to loss[s] / (3 n_s) (one atomic per CTA).
+__device__ __forceinline__ void flush_loss(double& acc, double* loss, int64_t n_pairs) {
+  __shared__ double red[16];
+  double v = acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) t += red[i];
+    atomicAdd(loss, t / (3.0 * double(n_pairs)));
+  }
+  __syncthreads();
+  acc = 0.0;
+}
+
+// TRAIN = false: gradients of sum(d_rgb . L_hat) for the given d_rgb.
+// TRAIN = true: the fused training pass over pairs; a tile holds 64 pairs,
+// rows 0..63 their primary queries and rows 64..127 their secondary queries,
+// and the Eq. 14 gradient of every pair is formed in the tile from the two
+// radiances (only the loss value leaves the CTA, as FP64 partials).
+template <class S, typename TT, bool TRAIN>
 __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ QueryParams p) {
   constexpr int H = S::H, NL = S::NL;
+  constexpr int ROWS = TRAIN ? NT / 2 : NT;  // pairs or queries per tile
   extern __shared__ __align__(1024) uint8_t smem[];
   const int g = threadIdx.x / NT, t = threadIdx.x % NT, warp = threadIdx.x >> 5;
   uint8_t* gbase = smem + S::OFF_GROUP + g * S::GR_BYTES;
@@ -432,6 +458,9 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   tc_fence_after_sync();
   uint32_t phase = 0;
   int cur = -1;
+  double loss_acc = 0.0;
+  const float lscale = TRAIN ? (p.scaler ? p.scaler->scale : 1.f) : 1.f;
+  float* xch = reinterpret_cast<float*>(gbase + S::GR_XCH);  // radiance exchange (TRAIN)
 
   for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
     int s = 0;
@@ -445,6 +474,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
       if (cur >= 0) {
         flush_weight_grads<S>(p.sc[cur], lane_addr, g == 0 ? 0 : NL / 2, g == 0 ? NL / 2 : NL);
         tc_fence_before_sync();
+        if (TRAIN) flush_loss(loss_acc, p.loss + cur, p.sc[cur].q_end - p.sc[cur].q_begin);
       }
       for (int l = 0; l < S::NL; ++l) {  // weights, all 256 threads
         const int K = S::kdim(l), N = S::ndim(l);
@@ -460,12 +490,17 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
       cur = s;
       __syncthreads();
     }
-    const int64_t tiles_s = (sc.q_end - sc.q_begin + NT - 1) / NT;
+    const int64_t tiles_s = (sc.q_end - sc.q_begin + ROWS - 1) / ROWS;
     const int64_t tile_s = 2 * (item - p.item_begin[s]) + g;
     if (tile_s >= tiles_s) continue;  // odd tile count: this group idles
-    const int64_t q0 = sc.q_begin + tile_s * NT;
-    const int nq = static_cast<int>(sc.q_end - q0 < NT ? sc.q_end - q0 : int64_t(NT));
-    locate_gather_bf16<S, TT>(p, sc, q0, nq, smem + S::off_act(g, 0), node_sm, u_sm, t);
+    const int64_t q0 = sc.q_begin + tile_s * ROWS;  // first query (pair) of the tile
+    const int nq = static_cast<int>(sc.q_end - q0 < ROWS ? sc.q_end - q0 : int64_t(ROWS));
+    const int row = TRAIN ? (t & (ROWS - 1)) : t;   // query (pair) of this thread in the tile
+    const bool primary = !TRAIN || t < ROWS;
+    const bool valid = row < nq;
+    const int64_t gq = q0 + row;
+    locate_gather_bf16<S, TT>(p, sc, primary ? p.x : p.x2, primary ? p.omega : p.omega2, gq, valid,
+                              smem + S::off_act(g, 0), node_sm, u_sm, t);
     fence_proxy_async();
     named_sync(gbar, NT);
 
@@ -501,18 +536,60 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
         uint32_t r[16];
         tmem_ld16(lane_work, r);
         tmem_wait_ld();
+        const float L0 = expf(__uint_as_float(r[0]));
+        const float L1 = expf(__uint_as_float(r[1]));
+        const float L2 = expf(__uint_as_float(r[2]));
         float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-        if (t < nq) {
-          const int64_t gq = q0 + t;
-          d0 = p.d_rgb[3 * gq];
-          d1 = p.d_rgb[3 * gq + 1];
-          d2 = p.d_rgb[3 * gq + 2];
+        if (!TRAIN) {
+          if (valid) {
+            d0 = p.d_rgb[3 * gq];
+            d1 = p.d_rgb[3 * gq + 1];
+            d2 = p.d_rgb[3 * gq + 2];
+          }
+        } else {
+          // Eq. 14 with the one-sample target of Eq. 3, per pair and channel:
+          // T = E + w L_s, r = (L_p - T) / (L_p + T + eps) (normaliser
+          // detached), d/dL_p = S 2 r / (3 n den), d/dL_s = -w d/dL_p.
+          if (!primary) {
+            xch[4 * row] = L0;
+            xch[4 * row + 1] = L1;
+            xch[4 * row + 2] = L2;
+          }
+          named_sync(gbar, NT);
+          if (primary && valid) {
+            const float Ls[3] = {xch[4 * row], xch[4 * row + 1], xch[4 * row + 2]};
+            const float Lp[3] = {L0, L1, L2};
+            const float n3 = 3.f * static_cast<float>(sc.q_end - sc.q_begin);
+            float dp[3], ds[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const float ww = p.w[3 * gq + c];
+              const float T = p.E[3 * gq + c] + ww * Ls[c];
+              const float den = Lp[c] + T + p.eps;
+              const float rr = (Lp[c] - T) / den;
+              loss_acc += double(rr) * double(rr);
+              dp[c] = 2.f * lscale * rr / (n3 * den);
+              ds[c] = p.rhs_grad ? -dp[c] * ww : 0.f;
+            }
+            d0 = dp[0];
+            d1 = dp[1];
+            d2 = dp[2];
+            xch[4 * row] = ds[0];
+            xch[4 * row + 1] = ds[1];
+            xch[4 * row + 2] = ds[2];
+          }
+          named_sync(gbar, NT);
+          if (!primary && valid) {
+            d0 = xch[4 * row];
+            d1 = xch[4 * row + 1];
+            d2 = xch[4 * row + 2];
+          }
         }
         // delta_L = d_rgb * exp(z_L): the derivative of exp is exp
         uint8_t* dst = smem + S::off_dl(g);
         uint4 o0, o1;
-        o0.x = pack_bf16x2(d0 * expf(__uint_as_float(r[0])), d1 * expf(__uint_as_float(r[1])));
-        o0.y = pack_bf16x2(d2 * expf(__uint_as_float(r[2])), 0.f);
+        o0.x = pack_bf16x2(d0 * L0, d1 * L1);
+        o0.y = pack_bf16x2(d2 * L2, 0.f);
         o0.z = o0.w = 0u;
         o1.x = o1.y = o1.z = o1.w = 0u;
         *reinterpret_cast<uint4*>(dst + kmajor_offset(t, 0, NOUT)) = o0;
@@ -620,8 +697,10 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   tc_fence_before_sync();
   __syncthreads();
   tc_fence_after_sync();
-  if (cur >= 0 && !abort_flag)
+  if (cur >= 0 && !abort_flag) {
     flush_weight_grads<S>(p.sc[cur], lane_addr, g == 0 ? 0 : NL / 2, g == 0 ? NL / 2 : NL);
+    if (TRAIN) flush_loss(loss_acc, p.loss + cur, p.sc[cur].q_end - p.sc[cur].q_begin);
+  }
   tc_fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, S::TMEM_COLS);
@@ -644,19 +723,21 @@ int launch_fwd(const QueryParams& p, cudaStream_t stream) {
   return OCTA_OK;
 }
 
-template <class S, typename TT>
+template <class S, typename TT, bool TRAIN>
 int launch_bwd(const QueryParams& p0, cudaStream_t stream) {
   if (p0.n_tiles == 0) return OCTA_OK;
+  constexpr int ROWS = TRAIN ? NT / 2 : NT;
   QueryParams p = p0;  // work items: pairs of tiles of one scene
   int64_t items = 0;
   for (int s = 0; s < p.n_scenes; ++s) {
     p.item_begin[s] = items;
-    const int64_t tiles = (p.sc[s].q_end - p.sc[s].q_begin + NT - 1) / NT;
+    const int64_t tiles = (p.sc[s].q_end - p.sc[s].q_begin + ROWS - 1) / ROWS;
     items += (tiles + S::G - 1) / S::G;
   }
   p.item_begin[p.n_scenes] = items;
   p.n_items = items;
-  auto kern = bwd_kernel<S, TT>;
+  if (items == 0) return OCTA_OK;
+  auto kern = bwd_kernel<S, TT, TRAIN>;
   int per_sm = 0;
   int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, S::NTB,
                               static_cast<int>(S::TMEM_COLS), &per_sm);
@@ -664,7 +745,8 @@ int launch_bwd(const QueryParams& p0, cudaStream_t stream) {
   const int64_t grid = std::min<int64_t>(items, int64_t(per_sm) * device_sm_count());
   kern<<<static_cast<unsigned>(grid), S::NTB, S::SMEM, stream>>>(p);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(OCTA_ECUDA, "tc bwd launch: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "tc %s launch: %s", TRAIN ? "train" : "bwd",
+                                    cudaGetErrorString(e));
   return OCTA_OK;
 }
 
@@ -691,15 +773,16 @@ int select_shape(const octa_scene* scenes, int n_scenes, int* F, int* need, int*
 
 }  // namespace
 
-int query_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
+template <bool TRAIN>
+int dispatch_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
   int F, need, H, NH;
   bool f16;
   int rc = select_shape(scenes, n_scenes, &F, &need, &H, &NH, &f16);
   if (rc) return rc;
 #define OCTA_TC_TRY(F_, WP_, H_, NH_)                                                  \
   if (F == F_ && H == H_ && NH == NH_ && need <= WP_)                                  \
-    return f16 ? launch_bwd<BShape<F_, WP_, H_, NH_>, __half>(p, stream)              \
-               : launch_bwd<BShape<F_, WP_, H_, NH_>, float>(p, stream);
+    return f16 ? launch_bwd<BShape<F_, WP_, H_, NH_>, __half, TRAIN>(p, stream)       \
+               : launch_bwd<BShape<F_, WP_, H_, NH_>, float, TRAIN>(p, stream);
   OCTA_TC_TRY(4, 32, 32, 2)
   OCTA_TC_TRY(8, 64, 64, 2)
   OCTA_TC_TRY(8, 80, 64, 2)
@@ -707,6 +790,14 @@ int query_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cuda
 #undef OCTA_TC_TRY
   return fail(OCTA_EUNSUPPORTED, "BF16 path: no built shape for F=%d, K*F=%d, hidden %d x %d", F,
               need, NH, H);
+}
+
+int query_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
+  return dispatch_bwd<false>(scenes, n_scenes, p, stream);
+}
+
+int train_fused(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
+  return dispatch_bwd<true>(scenes, n_scenes, p, stream);
 }
 
 int query_fwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {

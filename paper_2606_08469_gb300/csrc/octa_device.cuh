@@ -52,6 +52,16 @@ struct QueryParams {
   // scene s owns items [item_begin[s], item_begin[s+1])
   int64_t n_items;
   int64_t item_begin[OCTA_MAX_SCENES + 1];
+  // fused training pass: pairs of scene s are [q_begin, q_end) of the pair
+  // arrays; x / omega hold the primaries, x2 / omega2 the secondary queries
+  const float* x2;
+  const float* omega2;
+  const float* E;
+  const float* w;
+  const octa_scaler* scaler;
+  double* loss;  // [n_scenes], accumulated
+  float eps;
+  int32_t rhs_grad;
 };
 
 // Scene owning global tile t (tiles never straddle scenes).

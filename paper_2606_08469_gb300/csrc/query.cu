@@ -291,3 +291,39 @@ extern "C" int octa_query_bwd(const octa_scene* scenes, int32_t n_scenes, const 
   if (scenes[0].weight_dtype == OCTA_BF16) return tc::query_bwd(scenes, n_scenes, p, st);
   return dispatch_engine(scenes, n_scenes, p, true, st);
 }
+
+extern "C" int octa_train_fused(const octa_scene* scenes, int32_t n_scenes, const octa_pairs* pairs,
+                                float eps, int32_t rhs_grad, const octa_scaler* scaler,
+                                double* loss_dev, const octa_scene_grads* grads, int32_t* status,
+                                void* stream) {
+  clear_error();
+  if (!pairs || !grads || !loss_dev) return fail(OCTA_EINVAL, "pairs, grads and loss_dev must be non-NULL");
+  if (pairs->n > 0 && (!pairs->x2 || !pairs->omega2 || !pairs->E || !pairs->w))
+    return fail(OCTA_EINVAL, "pair arrays must be non-NULL");
+  if (!(eps > 0.f)) return fail(OCTA_EINVAL, "eps must be > 0");
+  octa_queries q;
+  std::memset(&q, 0, sizeof(q));
+  q.x = pairs->x;
+  q.omega = pairs->omega;
+  q.n = pairs->n;
+  for (int s = 0; s <= OCTA_MAX_SCENES; ++s) q.scene_start[s] = pairs->scene_start[s];
+  QueryParams p;
+  int rc = build_query_params(scenes, n_scenes, &q, grads, p);
+  if (rc) return rc;
+  for (int s = 0; s < n_scenes; ++s)
+    if (scenes[s].weight_dtype != OCTA_BF16)
+      return fail(OCTA_EUNSUPPORTED, "octa_train_fused needs BF16 decoders (tensor-core path)");
+  p.x2 = pairs->x2;
+  p.omega2 = pairs->omega2;
+  p.E = pairs->E;
+  p.w = pairs->w;
+  p.scaler = scaler;
+  p.loss = loss_dev;
+  p.eps = eps;
+  p.rhs_grad = rhs_grad;
+  p.status = status;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(loss_dev, 0, sizeof(double) * n_scenes, st);
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "clearing loss_dev: %s", cudaGetErrorString(e));
+  return tc::train_fused(scenes, n_scenes, p, st);
+}

@@ -10,6 +10,7 @@ namespace tc {
 
 int query_fwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream);
 int query_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream);
+int train_fused(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream);
 
 }  // namespace tc
 }  // namespace octa

@@ -45,7 +45,7 @@ class TrainStep:
     scene, each scene's primaries followed by its secondaries)."""
 
     def __init__(self, scene_states, pairs, eps=1e-2, rhs_grad=True, lr_tables=1e-2, lr_mlp=1e-3,
-                 scale=2.0 ** 15, growth_interval=2000, device="cuda"):
+                 scale=2.0 ** 15, growth_interval=2000, device="cuda", fused=False):
         dev = torch.device(device)
         self.states = scene_states
         self.scenes = [s.scene for s in scene_states]
@@ -71,6 +71,14 @@ class TrainStep:
         self.eps, self.rhs_grad = eps, rhs_grad
         self.groups = [g for s in scene_states for g in s.groups(lr_tables, lr_mlp)]
         self.grads = [(s.grad_t, s.grad_w) for s in scene_states]
+        # fused mode (BF16 decoders): one octa_train_fused launch replaces
+        # forward + loss + backward; the pair arrays are kept per role
+        self.fused = fused
+        if fused:
+            cat = lambda k: torch.cat([p[k] for p in pairs]).to(dev).contiguous()
+            self.Px, self.Pw, self.Sx = cat("x"), cat("omega"), cat("x2")
+            self.Sw = torch.cat([-p["omega2"] for p in pairs]).to(dev).contiguous()
+            self.Ecat, self.wcat = cat("E"), cat("w")
 
     def forward(self, stream=None):
         api.octa_query_fwd(self.scenes, self.X, self.Om, self.counts, rgb=self.rgb, stream=stream)
@@ -91,8 +99,16 @@ class TrainStep:
     def optimizer(self, stream=None):
         api.adam_step(self.groups, self.scaler, self.ws_adam, stream=stream)
 
+    def fused_pass(self, stream=None):
+        api.octa_train_fused(self.scenes, self.Px, self.Pw, self.Sx, self.Sw, self.Ecat, self.wcat,
+                             self.grads, self.loss, self.n, self.eps, self.rhs_grad, self.scaler,
+                             stream=stream)
+
     def step(self, stream=None):
-        self.forward(stream)
-        self.loss_and_grad(stream)
-        self.backward(stream)
+        if self.fused:
+            self.fused_pass(stream)
+        else:
+            self.forward(stream)
+            self.loss_and_grad(stream)
+            self.backward(stream)
         self.optimizer(stream)

@@ -50,6 +50,8 @@ def train_step_for(cfg, n_pairs=None, device="cuda", precision=None, **kw):
 
 
 def batched_train_step(device="cuda", counts=None, precision=None, **kw):
+    """TrainStep of the batched workload (8 scenes); counts overrides the
+    per-scene pair counts."""
     cfg = I.CONFIGS[4]
     counts = I.batched_pair_counts(cfg) if counts is None else counts
     states, plist, host = [], [], []

@@ -288,3 +288,91 @@ def test_bf16_backward_batched_scenes():
         assert errs[-1] <= 1e-2
         assert max(errs) <= 3.0 * np.sqrt(frac) + 1e-2
         off += n
+
+
+# ------------------------------------------------------------ fused training
+
+def _grads_close(a_states, b_states, tol):
+    errs = []
+    for a, b in zip(a_states, b_states):
+        for ga, gb in ((a.grad_t, b.grad_t), (a.grad_w, b.grad_w)):
+            errs.append(float(torch.linalg.norm(ga - gb) / torch.linalg.norm(gb)))
+    assert max(errs) <= tol, errs
+    return errs
+
+
+@pytest.mark.parametrize("rhs_grad", [True, False])
+def test_fused_training_pass_matches_unfused(rhs_grad):
+    """octa_train_fused vs octa_query_fwd + residual_loss + octa_query_bwd on
+    config-[2] shapes (4,097 pairs: a ragged last tile): same loss, same
+    gradients up to the order of the FP32 atomics; loss vs the FP64 oracle."""
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[2]
+    a, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=4097, rhs_grad=rhs_grad)
+    b, _ = WL.train_step_for(cfg, n_pairs=4097, rhs_grad=rhs_grad, fused=True)
+    a.forward()
+    a.loss_and_grad()
+    a.backward()
+    b.fused_pass()
+    torch.cuda.synchronize()
+    assert abs(a.loss.item() - b.loss.item()) <= 1e-6 * a.loss.item()
+    print("fused vs unfused grads", _grads_close(a.states, b.states, 1e-4))
+    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    N = pairs.n
+    X = np.concatenate([pairs.x, pairs.x2])
+    Om = np.concatenate([pairs.omega, -pairs.omega2])
+    rgb, _ = O.query_forward(ot, tables, weights, X, Om)
+    loss, _, _ = O.residual_loss(rgb[:N], rgb[N:], pairs.E, pairs.w, rhs_grad=rhs_grad)
+    assert abs(b.loss.item() - loss) <= 1e-2 * loss
+
+
+def test_fused_training_batched_scenes():
+    """Fused pass over three scenes of different depth in one launch vs the
+    unfused path: per-scene losses and gradients."""
+    from paper_2606_08469_gb300 import workloads as WL
+    counts = [3000, 129, 20000]
+    a, _ = WL.batched_train_step(counts=counts + [64] * 5)
+    b, _ = WL.batched_train_step(counts=counts + [64] * 5, fused=True)
+    a.forward()
+    a.loss_and_grad()
+    a.backward()
+    b.fused_pass()
+    torch.cuda.synchronize()
+    torch.testing.assert_close(b.loss, a.loss, rtol=1e-6, atol=0)
+    _grads_close(a.states, b.states, 1e-4)
+
+
+def test_fused_training_step_graph_and_scaler():
+    """Whole fused steps (fused pass + Adam) replayed from a CUDA graph agree
+    with eager fused steps; a host-injected overflow skips and halves."""
+    from paper_2606_08469_gb300 import api as A
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[2]
+    a, _ = WL.train_step_for(cfg, n_pairs=8192, fused=True)
+    b, _ = WL.train_step_for(cfg, n_pairs=8192, fused=True)
+    a.step()
+    b.step()
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            b.step()
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(3):
+        a.step()
+        graph.replay()
+    torch.cuda.synchronize()
+    torch.testing.assert_close(a.loss, b.loss, rtol=1e-5, atol=0)
+    # overflow: an inf in the table gradient after the fused pass
+    a.fused_pass()
+    a.states[0].grad_t[3, 1] = float("inf")
+    before = a.states[0].master_t.clone()
+    scale = A.read_scaler(a.scaler).scale
+    a.optimizer()
+    torch.cuda.synchronize()
+    st = A.read_scaler(a.scaler)
+    assert st.skipped == 1 and st.scale == scale / 2
+    assert torch.equal(a.states[0].master_t, before)
+    assert torch.count_nonzero(a.states[0].grad_t).item() == 0
