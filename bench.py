@@ -241,6 +241,43 @@ def inference_leg(dev, flush, stream, steps, peaks):
     return out
 
 
+def encode_leg(dev, flush, stream, steps, peaks):
+    """The OctaOctree encoding alone (fold, walk, bilinear gather of every
+    level, concatenation) for config [3]'s 1280x720 queries, BF16 features
+    out: bound by the HBM stream of positions/directions in and features out."""
+    import torch
+    from paper_2606_08469_gb300 import api
+    from paper_2606_08469_gb300 import inputs as I
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[3]
+    sc, (tree, _, _) = WL.forward_scene(cfg, device=dev)
+    x, om = I.gbuffer_queries(cfg.seed("queries"), 1280, 720)
+    X, Om = WL.to_dev(x, dev), WL.to_dev(om, dev)
+    W = tree.num_levels * cfg.F
+    feat = torch.empty((len(x), W), dtype=torch.bfloat16, device=dev)
+    q = api._queries(X, Om, None)
+    arr, ns = api._scene_array(sc)
+    lib = api._lib()
+
+    def fn():
+        api.L.check(lib.octa_encode(arr, ns, api.C.byref(q), api._ptr(feat), api.L.OCTA_BF16, W,
+                                    None, None, None, api._stream()), "octa_encode")
+    for _ in range(3):
+        fn()
+    t = _timed(fn, steps, flush, stream)
+    table_bytes = tree.num_texels * cfg.F * 2
+    alg = len(x) * (24 + 2 * W) + table_bytes
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    ach = alg / (t / 1e3) / 1e9
+    return {"workload": f"config[3] encoding alone: {len(x)} queries, depth-8 octree, FP16 table, "
+                        f"{W} BF16 features per query out",
+            "ms": round(t, 4), "Mq/s": round(len(x) / t / 1e3, 1),
+            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(ach / peak, 4),
+                         "algorithmic_bytes": alg,
+                         "per_query": f"24 B in + {2 * W} B out, table {table_bytes} B once"}}
+
+
 def _graph(fn, stream):
     """Capture fn (already run eagerly) into a CUDA graph on a side stream."""
     import torch
@@ -454,6 +491,7 @@ def run_ours(args):
             out["bf16_vs_f32"] = bf16_vs_f32_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
             out["inference"] = inference_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
             out["small_forward"] = small_forward_leg(dev, flush, stream, max(5, args.steps // 2))
+            out["encode"] = encode_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
             out["batched"] = batched_leg(dev, flush, stream, max(5, args.steps // 2))
         out["cpu_baseline"] = cpu_baseline() if not args.no_cpu else None
         print(json.dumps(out), flush=True)

@@ -23,6 +23,7 @@
 #include <algorithm>
 
 #include "engine_f32.cuh"
+#include "gather.cuh"
 #include "launch_util.h"
 #include "octa_internal.h"
 #include "tc_path.h"
@@ -78,128 +79,32 @@ __device__ void load_weights_bf16(const DevScene& sc, uint8_t* smem) {
   }
 }
 
-// Locate and gather of one query per thread, fused: the thread folds omega,
-// walks its query's path down the octree, loads the map base of every
-// present level, then gathers two levels at a time (both levels' texel loads
-// in flight together; one at a time for 32-byte texels) into its row of the
-// layer-0 operand tile.  node_sm /
-// u_sm (nullable) keep the path and the folded direction for a later scatter.
+// Locate and gather of one query per thread into its row of the layer-0
+// operand tile (canonical K-major, one 16-byte store per level for F = 8).
 template <class S, typename TT>
 __device__ __forceinline__ void locate_gather_bf16(const QueryParams& p, const DevScene& sc,
                                                    const float* __restrict__ xs,
                                                    const float* __restrict__ ws, int64_t gq,
                                                    bool valid, uint8_t* act, int* node_sm,
                                                    float* u_sm, int q) {
-  constexpr int F = S::F, KP = S::KPAD;
-  // levels gathered together: two for texels of up to 16 bytes, else one
-  constexpr int WIN = TexelRaw<TT, F>::BYTES <= 16 ? 2 : 1;
-  float x0 = 0.f, x1 = 0.f, x2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 1.f;
-  if (valid) {
-    x0 = xs[3 * gq];
-    x1 = xs[3 * gq + 1];
-    x2 = xs[3 * gq + 2];
-    w0 = ws[3 * gq];
-    w1 = ws[3 * gq + 1];
-    w2 = ws[3 * gq + 2];
-  }
-  float ux, uy;
-  octa_fold(w0, w1, w2, ux, uy);
-  x0 = clamp01(x0);
-  x1 = clamp01(x1);
-  x2 = clamp01(x2);
-  int node[KP];
-  node[0] = valid ? 0 : -1;
-  int cp0 = 0, cp1 = 0, cp2 = 0;
-#pragma unroll
-  for (int l = 1; l < KP; ++l) {
-    int nd = -1;
-    if (l < sc.K && node[l - 1] >= 0) {
-      const int c0 = cell_coord(x0, l), c1 = cell_coord(x1, l), c2 = cell_coord(x2, l);
-      const int slot = (c0 - 2 * cp0) | ((c1 - 2 * cp1) << 1) | ((c2 - 2 * cp2) << 2);
-      int fc = __ldg(sc.first_child + node[l - 1]);
-      if (fc >= 0 && fc > sc.num_nodes - 8) {
-        if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
-        fc = -1;
-      }
-      nd = fc >= 0 ? fc + slot : -1;
-      cp0 = c0;
-      cp1 = c1;
-      cp2 = c2;
-    }
-    node[l] = nd;
-  }
-  if (node_sm) {
-#pragma unroll
-    for (int l = 0; l < KP; ++l) node_sm[l * NT + q] = node[l];
-    u_sm[q] = ux;
-    u_sm[NT + q] = uy;
-  }
-  if (p.node_idx && valid) {
-#pragma unroll
-    for (int l = 0; l < KP; ++l)
-      if (l < p.kmax_out) p.node_idx[gq * p.kmax_out + l] = node[l];
-    for (int l = KP; l < p.kmax_out; ++l) p.node_idx[gq * p.kmax_out + l] = -1;
-  }
-  int64_t mo[KP];
-#pragma unroll
-  for (int l = 0; l < KP; ++l) mo[l] = node[l] >= 0 ? f32::map_base(p, sc, node[l], sc.R[l]) : -1;
-#pragma unroll
-  for (int l0 = 0; l0 < KP; l0 += WIN) {
-    TexelRaw<TT, F> t[WIN][4];
-    Footprint fp[WIN];
-#pragma unroll
-    for (int j = 0; j < WIN; ++j) {
-      const int l = l0 + j;
-      if (l < KP && mo[l] >= 0) {
-        fp[j] = footprint(ux, uy, sc.R[l]);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) t[j][k].load(sc.tables, mo[l] + fp[j].idx[k]);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < WIN; ++j) {
-      const int l = l0 + j;
-      if (l >= KP) continue;
-      float v[F];
-      if (mo[l] >= 0) {
-#pragma unroll
-        for (int f = 0; f < F; ++f) {
-          float s = fp[j].w[0] * t[j][0].get(f);
-          s = fmaf(fp[j].w[1], t[j][1].get(f), s);
-          s = fmaf(fp[j].w[2], t[j][2].get(f), s);
-          s = fmaf(fp[j].w[3], t[j][3].get(f), s);
-          v[f] = s;
+  constexpr int F = S::F;
+  locate_gather_query<F, TT, S::KPAD, true>(
+      p, sc, xs, ws, gq, valid, node_sm, u_sm, q, NT, [&](int l, const float (&v)[F]) {
+        uint8_t* dst = act + kmajor_offset(q, l * F, S::WP);
+        if constexpr (F == 8) {
+          uint4 o;
+          o.x = pack_bf16x2(v[0], v[1]);
+          o.y = pack_bf16x2(v[2], v[3]);
+          o.z = pack_bf16x2(v[4], v[5]);
+          o.w = pack_bf16x2(v[6], v[7]);
+          *reinterpret_cast<uint4*>(dst) = o;
+        } else {
+          uint2 o;
+          o.x = pack_bf16x2(v[0], v[1]);
+          o.y = pack_bf16x2(v[2], v[3]);
+          *reinterpret_cast<uint2*>(dst) = o;
         }
-      } else {
-#pragma unroll
-        for (int f = 0; f < F; ++f) v[f] = 0.f;
-      }
-      uint8_t* dst = act + kmajor_offset(q, l * F, S::WP);
-      if constexpr (F == 8) {
-        uint4 o;
-        o.x = pack_bf16x2(v[0], v[1]);
-        o.y = pack_bf16x2(v[2], v[3]);
-        o.z = pack_bf16x2(v[4], v[5]);
-        o.w = pack_bf16x2(v[6], v[7]);
-        *reinterpret_cast<uint4*>(dst) = o;
-      } else {
-        uint2 o;
-        o.x = pack_bf16x2(v[0], v[1]);
-        o.y = pack_bf16x2(v[2], v[3]);
-        *reinterpret_cast<uint2*>(dst) = o;
-      }
-      if (p.texel_addr && valid && l < p.kmax_out) {
-        int4 a = make_int4(-1, -1, -1, -1);
-        if (mo[l] >= 0)
-          a = make_int4(int(mo[l] + fp[j].idx[0]), int(mo[l] + fp[j].idx[1]),
-                        int(mo[l] + fp[j].idx[2]), int(mo[l] + fp[j].idx[3]));
-        *reinterpret_cast<int4*>(p.texel_addr + (gq * p.kmax_out + l) * 4) = a;
-      }
-    }
-  }
-  if (p.texel_addr && valid)
-    for (int l = KP; l < p.kmax_out; ++l)
-      *reinterpret_cast<int4*>(p.texel_addr + (gq * p.kmax_out + l) * 4) = make_int4(-1, -1, -1, -1);
+      });
 }
 
 // Issue the MMAs of one layer (single thread) and commit to the mbarrier.

@@ -139,10 +139,17 @@ __device__ __forceinline__ Footprint footprint(float ux, float uy, int R) {
   const float fx = __fsub_rn(px, flx);
   const float fy = __fsub_rn(py, fly);
   Footprint f;
-  f.idx[0] = wrap_index(i0, j0, R);
-  f.idx[1] = wrap_index(i0 + 1, j0, R);
-  f.idx[2] = wrap_index(i0, j0 + 1, R);
-  f.idx[3] = wrap_index(i0 + 1, j0 + 1, R);
+  if (i0 >= 0 && j0 >= 0 && i0 + 1 < R && j0 + 1 < R) {  // interior: no wrap
+    f.idx[0] = j0 * R + i0;
+    f.idx[1] = f.idx[0] + 1;
+    f.idx[2] = f.idx[0] + R;
+    f.idx[3] = f.idx[2] + 1;
+  } else {
+    f.idx[0] = wrap_index(i0, j0, R);
+    f.idx[1] = wrap_index(i0 + 1, j0, R);
+    f.idx[2] = wrap_index(i0, j0 + 1, R);
+    f.idx[3] = wrap_index(i0 + 1, j0 + 1, R);
+  }
   const float gx = 1.f - fx, gy = 1.f - fy;
   f.w[0] = gx * gy;
   f.w[1] = fx * gy;

@@ -8,6 +8,7 @@
 #include <cstring>
 
 #include "engine_f32.cuh"
+#include "gather.cuh"
 #include "launch_util.h"
 #include "octa_internal.h"
 #include "tc_path.h"
@@ -17,38 +18,60 @@ namespace octa {
 // ---------------------------------------------------------------------------
 // Standalone encoding kernel (Eq. 10 single-cell bilinear form + Eq. 11)
 // ---------------------------------------------------------------------------
-// Tile of QT queries: locate (one thread per query), gather (one thread per
-// (query, level)) into a [query][feature] staging area whose odd row stride
-// keeps the scalar writes conflict-free, then a coalesced copy of the tile's
-// rows to global memory.
-template <int F, typename TT, typename OT>
-__global__ void __launch_bounds__(f32::NT) encode_kernel(const __grid_constant__ QueryParams p) {
-  extern __shared__ __align__(16) float smem[];
-  int* node_sm = reinterpret_cast<int*>(smem);
-  float* u_sm = smem + OCTA_MAX_LEVELS * QT;
-  float* stage = u_sm + 2 * QT;
+// One query per thread (fold, walk, gather; see gather.cuh), its K*F
+// features written into a shared-memory staging row in the output type; the
+// tile's rows then leave as 16-byte stores (a contiguous block when the
+// output rows are packed), so the feature stream is written coalesced.
+constexpr int ENC_NT = 128;
+
+template <int F, typename TT, typename OT, int KP>
+__global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ QueryParams p) {
+  extern __shared__ __align__(16) uint8_t stage[];
+  const int q = threadIdx.x;
+  OT* out = static_cast<OT*>(p.features);
   for (int64_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
     const int s = scene_of_tile(p, tile);
     const DevScene& sc = p.sc[s];
-    const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * QT;
-    const int nq = static_cast<int>(sc.q_end - q0 < QT ? sc.q_end - q0 : int64_t(QT));
+    const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * ENC_NT;
+    const int nq = static_cast<int>(sc.q_end - q0 < ENC_NT ? sc.q_end - q0 : int64_t(ENC_NT));
     const int W = sc.K * F;
-    const int ws = W | 1;  // odd staging stride
+    const int row_bytes = W * int(sizeof(OT));
+    const int rb = (row_bytes + 15) & ~15;  // staging row stride
     __syncthreads();
-    f32::locate_tile<OCTA_MAX_LEVELS>(p, sc, q0, nq, node_sm, u_sm);
+    locate_gather_query<F, TT, KP, sizeof(OT) == 2>(
+        p, sc, p.x, p.omega, q0 + q, q < nq, nullptr, nullptr, q, ENC_NT,
+        [&](int l, const float (&v)[F]) {
+          if (l >= sc.K) return;
+          uint8_t* dst = stage + q * rb + l * F * int(sizeof(OT));
+          if constexpr (sizeof(OT) == 2) {
+            uint32_t w[F / 2];
+#pragma unroll
+            for (int i = 0; i < F / 2; ++i) w[i] = pack_bf16x2_rn(v[2 * i], v[2 * i + 1]);
+            if constexpr (F == 8)
+              *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+            else
+              *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < F / 4; ++i)
+              reinterpret_cast<float4*>(dst)[i] =
+                  make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+          }
+        });
     __syncthreads();
-    f32::gather_tile<F, TT>(p, sc, q0, nq, sc.K, node_sm, u_sm, stage, 1, ws);
-    __syncthreads();
-    OT* out = static_cast<OT*>(p.features);
-    for (int i = threadIdx.x; i < nq * W; i += f32::NT) {
-      const int q = i / W, k = i % W;
-      const float v = stage[q * ws + k];
-      OT o;
-      if constexpr (sizeof(OT) == 4)
-        o = v;
-      else
-        o = __float2bfloat16_rn(v);
-      out[(q0 + q) * p.row_stride + k] = o;
+    const bool packed = p.row_stride == W && rb == row_bytes &&
+                        (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+    if (packed) {  // the tile's rows are one contiguous block in global memory
+      const int chunks = nq * row_bytes / 16;
+      uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(out + q0 * W));
+      const uint4* src = reinterpret_cast<const uint4*>(stage);
+      for (int c = q; c < chunks; c += ENC_NT) dst[c] = src[c];
+    } else {
+      for (int i = q; i < nq * W; i += ENC_NT) {
+        const int r = i / W, k = i % W;
+        out[(q0 + r) * p.row_stride + k] =
+            *reinterpret_cast<const OT*>(stage + r * rb + k * int(sizeof(OT)));
+      }
     }
   }
 }
@@ -236,22 +259,34 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
   p.texel_addr = texel_addr;
   p.kmax_out = kmax;
   p.status = status;
-  const size_t smem =
-      sizeof(float) * (OCTA_MAX_LEVELS * QT + 2 * QT + size_t(QT) * ((kmax * F) | 1));
+  const size_t ot = feat_dtype == OCTA_BF16 ? 2 : 4;
+  const size_t smem = size_t(ENC_NT) * ((size_t(kmax) * F * ot + 15) & ~size_t(15));
+  // the encode kernel tiles ENC_NT queries; QT-sized tiles were counted above
+  static_assert(ENC_NT == QT, "tile size");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool f16 = tdt == OCTA_F16, bf = feat_dtype == OCTA_BF16;
-  if (F == 4) {
-    if (f16)
-      return bf ? launch_persistent(encode_kernel<4, __half, __nv_bfloat16>, smem, p, st, f32::NT)
-                : launch_persistent(encode_kernel<4, __half, float>, smem, p, st, f32::NT);
-    return bf ? launch_persistent(encode_kernel<4, float, __nv_bfloat16>, smem, p, st, f32::NT)
-              : launch_persistent(encode_kernel<4, float, float>, smem, p, st, f32::NT);
+#define OCTA_ENC(F_, TT_, KP_)                                                              \
+  return bf ? launch_persistent(encode_kernel<F_, TT_, __nv_bfloat16, KP_>, smem, p, st, ENC_NT) \
+            : launch_persistent(encode_kernel<F_, TT_, float, KP_>, smem, p, st, ENC_NT);
+#define OCTA_ENC_KP(F_, TT_)      \
+  if (kmax <= 10) {               \
+    OCTA_ENC(F_, TT_, 10)         \
+  } else {                        \
+    OCTA_ENC(F_, TT_, OCTA_MAX_LEVELS) \
   }
-  if (f16)
-    return bf ? launch_persistent(encode_kernel<8, __half, __nv_bfloat16>, smem, p, st, f32::NT)
-              : launch_persistent(encode_kernel<8, __half, float>, smem, p, st, f32::NT);
-  return bf ? launch_persistent(encode_kernel<8, float, __nv_bfloat16>, smem, p, st, f32::NT)
-            : launch_persistent(encode_kernel<8, float, float>, smem, p, st, f32::NT);
+  if (F == 4) {
+    if (f16) {
+      OCTA_ENC_KP(4, __half)
+    } else {
+      OCTA_ENC_KP(4, float)
+    }
+  }
+  if (f16) {
+    OCTA_ENC_KP(8, __half)
+  }
+  OCTA_ENC_KP(8, float)
+#undef OCTA_ENC_KP
+#undef OCTA_ENC
 }
 
 extern "C" int octa_query_fwd(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,

@@ -5,7 +5,8 @@ with the FP32 master parameters (tables and weights before quantisation).
 Node indices and texel addresses stay bit-exact (the address path is the
 same canonical binary32 sequence).  The error against FP64 on the quantised
 parameters (FP16 tables and BF16 weights widened exactly) isolates the
-arithmetic: BF16 operands with FP32 accumulation, bounded here by 6e-3."""
+arithmetic: BF16 operands with FP32 accumulation.  Its bound is derived
+from the network (arith_tolerance)."""
 import numpy as np
 import pytest
 import torch
@@ -16,7 +17,18 @@ from paper_2606_08469_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
 TOL_E2E = 1e-2
-TOL_ARITH = 6e-3
+
+
+def arith_tolerance(weights, h):
+    """Normwise bound on the BF16 path's radiance error against FP64 on the
+    same (quantised) parameters.  The relative error of exp(z) is the
+    absolute error of z; every BF16 rounding point (the features, each
+    hidden activation) adds at most 2^-9 relative to the values it rounds,
+    propagated through |W|, so |dz| <~ 2^-9 * z_abs per rounding point, z_abs
+    the network run on |W| and |h|.  2^-8 * rms(z_abs) allows about four
+    such contributions adding in quadrature; 2^-9 is the floor."""
+    _, zs, _ = O.mlp_forward([np.abs(np.asarray(W, np.float64)) for W in weights], np.abs(h))
+    return max(2.0 ** -9, 2.0 ** -8 * float(np.sqrt(np.mean(zs[-1] ** 2))))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -50,7 +62,7 @@ def make_bf16_scene(seed, depth, R, F, sigma, hidden, wscale=1.0, tseed=2000, ws
     return sc, O.build_tree(seed, depth, 0.6, R), tables, weights, tq, wq
 
 
-def check_forward(sc, ot, tables, weights, tq, wq, x, w, counts=None, tol_arith=TOL_ARITH):
+def check_forward(sc, ot, tables, weights, tq, wq, x, w, counts=None):
     from paper_2606_08469_gb300 import api as A
     rgb, nodes, addr = A.octa_query_fwd(sc, dev(x), dev(w), counts, want_nodes=True, want_addr=True)
     rgb = rgb.cpu().numpy()
@@ -59,8 +71,9 @@ def check_forward(sc, ot, tables, weights, tq, wq, x, w, counts=None, tol_arith=
     np.testing.assert_array_equal(nodes.cpu().numpy(), enc.node)
     np.testing.assert_array_equal(addr.cpu().numpy(), enc.addr)
     e2e, arith = normwise(rgb, ref), normwise(rgb, refq)
+    tol_arith = arith_tolerance(wq, O.encode_features(ot, tq, x, w).h)
     assert e2e <= TOL_E2E, e2e
-    assert arith <= tol_arith, arith
+    assert arith <= tol_arith, (arith, tol_arith)
     return e2e, arith
 
 

@@ -115,6 +115,40 @@ def test_encode_features_match_oracle():
     np.testing.assert_allclose(fb.float().cpu().numpy(), enc.h, rtol=1e-2, atol=1e-3)
 
 
+def test_encode_two_scenes_strided_rows():
+    """Scenes with K*F = 40 and 56 in one call: rows of the shallower scene
+    are shorter than the row stride (strided copy-out), its tail untouched."""
+    A = api()
+    parts = []
+    for s, (seed, depth) in enumerate([(1400, 4), (1402, 6)]):
+        R = I.R_DEEP[:depth + 1]
+        tree = A.octree_build(seed, depth, 0.6, R)
+        tables = I.make_tables(2400 + s, tree.num_texels, 8, 0.3)
+        weights = I.make_mlp(3400 + s, [(depth + 1) * 8, 64, 64, 3])
+        parts.append((A.Scene(tree, dev(tables), [dev(W) for W in weights], device=DEV),
+                      O.build_tree(seed, depth, 0.6, R), tables))
+    counts = [333, 1000]
+    xs, ws = zip(*[I.uniform_queries(70 + s, n) for s, n in enumerate(counts)])
+    # FP32: the texel coordinate p = uv R - 1/2 carries ~u R of rounding and h
+    # moves by at most 2 max|T| per unit of p: |dh| <= 4 u R_max max|T|
+    tmax = max(float(np.abs(p[2]).max()) for p in parts)
+    atol32 = 4 * 2.0 ** -24 * 64 * tmax
+    for dt, rtol, atol in ((torch.float32, 1e-5, atol32), (torch.bfloat16, 1e-2, 1e-3)):
+        feat, nodes, addr = A.octa_encode([p[0] for p in parts], dev(np.concatenate(xs)),
+                                          dev(np.concatenate(ws)), counts, feat_dtype=dt,
+                                          want_nodes=True, want_addr=True)
+        f = feat.float().cpu().numpy()
+        off = 0
+        for s, n in enumerate(counts):
+            enc = O.encode_features(parts[s][1], parts[s][2], xs[s], ws[s])
+            W = enc.h.shape[1]
+            np.testing.assert_allclose(f[off:off + n, :W], enc.h, rtol=rtol, atol=atol)
+            assert not f[off:off + n, W:].any()
+            K = parts[s][1].num_levels
+            np.testing.assert_array_equal(addr.cpu().numpy()[off:off + n, :K], enc.addr)
+            off += n
+
+
 def _edge_queries():
     s = 1.0 / np.sqrt(2.0)
     w = np.array([[0, 0, 1], [0, 0, -1], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0],
