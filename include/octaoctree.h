@@ -22,8 +22,9 @@
  *    reaches that point.
  *  - Pointers documented as "host" are read during the call only.
  *  - Scratch space comes from a caller-provided device workspace of at least
- *    octa_workspace_bytes(op, n) bytes, 256-byte aligned.  Two calls that
- *    share a workspace must not overlap on the GPU.
+ *    octa_workspace_bytes(op, n) bytes, 256-byte aligned and zero-filled
+ *    before its first use (every call leaves it ready for the next).  Two
+ *    calls that share a workspace must not overlap on the GPU.
  *  - Device-detected malformed input (a child index or texel range outside
  *    the arrays) is never dereferenced: the level is treated as absent and
  *    the OCTA_STATUS_* bit is OR-ed into *status (device int32, nullable).
@@ -276,9 +277,37 @@ typedef struct octa_adam_cfg {
 int adam_step(const octa_param_group* groups, int32_t n_groups, const octa_adam_cfg* cfg,
               octa_scaler* scaler, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Options of octa_train_step_batched (nullable: defaults).                */
+typedef struct octa_step_options {
+  uint64_t barrier_timeout_ns; /* bound of each grid-barrier wait; 0 = 1 s  */
+  int32_t extra_barrier_arrivals; /* test hook: arrivals the barriers await
+                                  beyond the grid (0 in use; > 0 makes every
+                                  wait run out, report OCTA_STATUS_TIMEOUT and
+                                  skip the optimiser)                        */
+  int32_t reserved;
+} octa_step_options;
+
+/* octa_train_step_batched -- a whole training step of up to 16 scenes in one
+ * persistent cooperative launch: the fused pass of octa_train_fused over all
+ * pairs, then (after a grid-wide barrier) the FP64 gradient norm from
+ * per-CTA partials, the loss-scale decision and Adam over the parameter
+ * groups (after a second barrier), exactly as adam_step.  grads[s] must
+ * alias the grad buffers of the groups that hold scene s's parameters and
+ * start zeroed (every step leaves them zeroed).  Every barrier wait is
+ * bounded; on timeout OCTA_STATUS_TIMEOUT is set in *status and the step is
+ * incomplete.  Workspace: octa_workspace_bytes(OCTA_OP_STEP, 0), zero-filled
+ * before its first use.  BF16 decoders only.                              */
+int octa_train_step_batched(const octa_scene* scenes, int32_t n_scenes, const octa_pairs* pairs,
+                            const octa_scene_grads* grads, const octa_param_group* groups,
+                            int32_t n_groups, float eps, int32_t rhs_grad,
+                            const octa_adam_cfg* adam, octa_scaler* scaler, double* loss_dev,
+                            const octa_step_options* options, void* workspace,
+                            size_t workspace_bytes, int32_t* status, void* stream);
+
 /* ---- workspace sizing, errors ------------------------------------------ */
 #define OCTA_OP_LOSS 1
 #define OCTA_OP_ADAM 2
+#define OCTA_OP_STEP 3
 size_t octa_workspace_bytes(int32_t op, int64_t n);
 
 const char* octa_last_error(void);

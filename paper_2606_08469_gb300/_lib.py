@@ -33,6 +33,7 @@ OCTA_BF16 = 2
 
 OCTA_OP_LOSS = 1
 OCTA_OP_ADAM = 2
+OCTA_OP_STEP = 3
 
 
 class octa_tree_desc(C.Structure):
@@ -122,6 +123,11 @@ class octa_adam_cfg(C.Structure):
     _fields_ = [("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
 
 
+class octa_step_options(C.Structure):
+    _fields_ = [("barrier_timeout_ns", C.c_uint64), ("extra_barrier_arrivals", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 # Every symbol the header declares, with its ctypes signature.
 _P = C.c_void_p
 _SIGNATURES = {
@@ -137,6 +143,11 @@ _SIGNATURES = {
                                  C.POINTER(octa_scene_grads), _P, _P]),
     "octa_train_fused": (C.c_int, [C.POINTER(octa_scene), C.c_int32, C.POINTER(octa_pairs), C.c_float,
                                    C.c_int32, _P, _P, C.POINTER(octa_scene_grads), _P, _P]),
+    "octa_train_step_batched": (C.c_int, [C.POINTER(octa_scene), C.c_int32, C.POINTER(octa_pairs),
+                                          C.POINTER(octa_scene_grads), C.POINTER(octa_param_group),
+                                          C.c_int32, C.c_float, C.c_int32, C.POINTER(octa_adam_cfg),
+                                          _P, _P, C.POINTER(octa_step_options), _P, C.c_size_t, _P,
+                                          _P]),
     "residual_loss": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_float, C.c_int32, _P, _P, _P, _P,
                                 _P, C.c_size_t, _P]),
     "residual_loss_static": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_float, C.c_int32, _P, _P,

@@ -241,6 +241,34 @@ def octa_train_fused(scenes, x, omega, x2, omega2, E, w, grads, loss_out, counts
             "octa_train_fused")
 
 
+def octa_train_step_batched(scenes, x, omega, x2, omega2, E, w, grads, groups, loss_out, scaler, ws,
+                            counts=None, eps=1e-2, rhs_grad=True, beta1=0.9, beta2=0.999,
+                            adam_eps=1e-8, timeout_ns=0, extra_arrivals=0, status=None,
+                            stream=None):
+    """Whole training step (fused pass + Adam) in one persistent launch."""
+    arr, ns = _scene_array(scenes)
+    g = (L.octa_scene_grads * ns)(*[L.octa_scene_grads(dt.data_ptr(), dw.data_ptr())
+                                    for dt, dw in grads])
+    pg = (L.octa_param_group * len(groups))(*[gr.as_c() for gr in groups])
+    pr = L.octa_pairs()
+    n = int(x.shape[0])
+    pr.x, pr.omega, pr.x2, pr.omega2 = (t.data_ptr() for t in (x, omega, x2, omega2))
+    pr.E, pr.w = E.data_ptr(), w.data_ptr()
+    pr.n = n
+    counts = [n] if counts is None else list(counts)
+    acc = 0
+    for i, c in enumerate(counts):
+        acc += c
+        pr.scene_start[i + 1] = acc
+    opt = L.octa_step_options(timeout_ns, extra_arrivals, 0)
+    cfg = L.octa_adam_cfg(beta1, beta2, adam_eps)
+    L.check(_lib().octa_train_step_batched(arr, ns, C.byref(pr), g, pg, len(groups), C.c_float(eps),
+                                           int(bool(rhs_grad)), C.byref(cfg), _ptr(scaler),
+                                           _ptr(loss_out), C.byref(opt), _ptr(ws), ws.numel(),
+                                           _ptr(status), _stream(stream)),
+            "octa_train_step_batched")
+
+
 # ---------------------------------------------------------------------------
 # loss, optimiser
 # ---------------------------------------------------------------------------

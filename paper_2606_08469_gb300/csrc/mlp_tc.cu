@@ -295,6 +295,213 @@ __device__ void flush_weight_grads(const DevScene& sc, uint32_t lane_addr, int i
   tmem_wait_st();
 }
 
+struct BwdParams {
+  QueryParams p;
+  AdamBlock a;
+};
+
+// Grid-wide barrier of a cooperative launch: arrival counter plus a
+// generation word.  The wait is bounded by timeout_ns (globaltimer); on
+// timeout it returns false in every thread of the CTA.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned expected, uint64_t timeout_ns) {
+  __shared__ int ok_sm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vbar = bar;
+    const unsigned gen = vbar[1];
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == expected - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const uint64_t t0 = globaltimer_ns();
+      while (vbar[1] == gen) {
+        if (globaltimer_ns() - t0 > timeout_ns) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();
+    ok_sm = ok;
+  }
+  __syncthreads();
+  return ok_sm != 0;
+}
+
+// Block-wide FP64 sum in a fixed order (result in every thread).
+__device__ __forceinline__ double block_sum_all(double v) {
+  __shared__ double red[32];
+  __shared__ double total;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) t += red[i];
+    total = t;
+  }
+  __syncthreads();
+  return total;
+}
+
+__device__ __forceinline__ void adam_elem(float& pm, float& m, float& v, float g, float lr, float b1,
+                                          float b2, float eps, float bc1, float bc2) {
+  m = b1 * m + (1.f - b1) * g;
+  v = b2 * v + (1.f - b2) * g * g;
+  pm = pm - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+}
+
+// The optimiser phase of the persistent step (all CTAs, after the fused
+// pass): FP64 gradient norm from per-CTA partials, the skip / scale decision
+// taken identically in every CTA (same partials, same summation order) from
+// the scaler state read after the first barrier, Adam with bias correction over this
+// CTA's slice (16-byte accesses where a group allows them), gradients zeroed.
+__device__ __noinline__ void persistent_adam(const AdamBlock& a, int32_t* status) {
+  const uint64_t tmo = a.timeout_ns;
+  const unsigned expected = gridDim.x + static_cast<unsigned>(a.extra_arrivals);
+  if (!grid_barrier(a.bar, expected, tmo)) {  // every gradient is in
+    if (threadIdx.x == 0 && status) atomicOr(status, OCTA_STATUS_TIMEOUT);
+    return;
+  }
+  // the scaler state of this step: every CTA reads it here, between the two
+  // barriers, and CTA 0 writes the new state only after the second one
+  octa_scaler s0;
+  {
+    const volatile octa_scaler* vs = a.scaler;
+    s0.scale = vs->scale;
+    s0.good_steps = vs->good_steps;
+    s0.growth_interval = vs->growth_interval;
+    s0.step = vs->step;
+    s0.n_skipped = vs->n_skipped;
+  }
+  const float inv_s = 1.f / s0.scale;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int64_t first = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  for (int gi = 0; gi < a.n_groups; ++gi) {
+    const octa_param_group& G = a.g[gi];
+    int64_t done = 0;
+    if (a.vec4[gi]) {
+      const float4* g4 = reinterpret_cast<const float4*>(G.grad);
+      const int64_t n4 = G.n / 4;
+#pragma unroll 4
+      for (int64_t i = first; i < n4; i += stride) {
+        const float4 g = __ldcg(g4 + i);
+        const double x = g.x * inv_s, y = g.y * inv_s, z = g.z * inv_s, w = g.w * inv_s;
+        acc += x * x + y * y + z * z + w * w;
+      }
+      done = n4 * 4;
+    }
+    for (int64_t i = done + first; i < G.n; i += stride) {
+      const double v = double(__ldcg(G.grad + i) * inv_s);
+      acc += v * v;
+    }
+  }
+  acc = block_sum_all(acc);
+  if (threadIdx.x == 0) a.partials[blockIdx.x] = acc;
+  if (!grid_barrier(a.bar, expected, tmo)) {
+    if (threadIdx.x == 0 && status) atomicOr(status, OCTA_STATUS_TIMEOUT);
+    return;
+  }
+  double part = 0.0;  // thread t takes partials t, t + blockDim, ...: fixed order
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) part += __ldcg(a.partials + b);
+  const double total = block_sum_all(part);
+  const bool skip = !isfinite(total);
+  const int32_t t_new = s0.step + (skip ? 0 : 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    octa_scaler* sc = a.scaler;
+    sc->inv_scale_used = inv_s;
+    sc->grad_norm = sqrt(total);
+    if (skip) {
+      sc->skipped = 1;
+      sc->n_skipped = s0.n_skipped + 1;
+      if (s0.growth_interval > 0) {
+        sc->scale = s0.scale * 0.5f;
+        sc->good_steps = 0;
+      }
+    } else {
+      sc->skipped = 0;
+      sc->step = t_new;
+      int good = s0.good_steps + 1;
+      float scale = s0.scale;
+      if (s0.growth_interval > 0 && good >= s0.growth_interval) {
+        scale *= 2.f;
+        good = 0;
+      }
+      sc->good_steps = s0.growth_interval > 0 ? good : s0.good_steps;
+      sc->scale = scale;
+    }
+  }
+  __shared__ float bc[2];
+  if (threadIdx.x == 0) {
+    bc[0] = skip ? 1.f : static_cast<float>(1.0 - pow(double(a.beta1), double(t_new)));
+    bc[1] = skip ? 1.f : static_cast<float>(1.0 - pow(double(a.beta2), double(t_new)));
+  }
+  __syncthreads();
+  const float bc1 = bc[0], bc2 = bc[1];
+  const float b1 = a.beta1, b2 = a.beta2, eps = a.eps;
+  for (int gi = 0; gi < a.n_groups; ++gi) {
+    const octa_param_group& G = a.g[gi];
+    const float lr = G.lr;
+    int64_t done = 0;
+    if (a.vec4[gi]) {
+      const int64_t n4 = G.n / 4;
+      float4* P = reinterpret_cast<float4*>(G.param);
+      float4* Gr = reinterpret_cast<float4*>(G.grad);
+      float4* M = reinterpret_cast<float4*>(G.m);
+      float4* V = reinterpret_cast<float4*>(G.v);
+#pragma unroll 2
+      for (int64_t i = first; i < n4; i += stride) {
+        const float4 g = __ldcg(Gr + i);
+        Gr[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (skip) continue;
+        float4 pm = P[i], m = M[i], v = V[i];
+        adam_elem(pm.x, m.x, v.x, g.x * inv_s, lr, b1, b2, eps, bc1, bc2);
+        adam_elem(pm.y, m.y, v.y, g.y * inv_s, lr, b1, b2, eps, bc1, bc2);
+        adam_elem(pm.z, m.z, v.z, g.z * inv_s, lr, b1, b2, eps, bc1, bc2);
+        adam_elem(pm.w, m.w, v.w, g.w * inv_s, lr, b1, b2, eps, bc1, bc2);
+        P[i] = pm;
+        M[i] = m;
+        V[i] = v;
+        if (G.work) {
+          if (G.work_dtype == OCTA_F16) {
+            __half2* w = reinterpret_cast<__half2*>(G.work) + 2 * i;
+            w[0] = __floats2half2_rn(pm.x, pm.y);
+            w[1] = __floats2half2_rn(pm.z, pm.w);
+          } else {
+            __nv_bfloat162* w = reinterpret_cast<__nv_bfloat162*>(G.work) + 2 * i;
+            w[0] = __floats2bfloat162_rn(pm.x, pm.y);
+            w[1] = __floats2bfloat162_rn(pm.z, pm.w);
+          }
+        }
+      }
+      done = n4 * 4;
+    }
+    for (int64_t i = done + first; i < G.n; i += stride) {
+      const float g = __ldcg(G.grad + i) * inv_s;
+      G.grad[i] = 0.f;
+      if (skip) continue;
+      float pm = G.param[i], m = G.m[i], v = G.v[i];
+      adam_elem(pm, m, v, g, lr, b1, b2, eps, bc1, bc2);
+      G.param[i] = pm;
+      G.m[i] = m;
+      G.v[i] = v;
+      if (G.work) {
+        if (G.work_dtype == OCTA_F16)
+          static_cast<__half*>(G.work)[i] = __float2half_rn(pm);
+        else
+          static_cast<__nv_bfloat16*>(G.work)[i] = __float2bfloat16_rn(pm);
+      }
+    }
+  }
+}
+
 // Loss partials of a fused training pass: every thread's FP64 sum of r^2 for
 // the current scene is added to loss[s] / (3 n_s) (one atomic per CTA).
 __device__ __forceinline__ void flush_loss(double& acc, double* loss, int64_t n_pairs) {
@@ -318,8 +525,11 @@ __device__ __forceinline__ void flush_loss(double& acc, double* loss, int64_t n_
 // rows 0..63 their primary queries and rows 64..127 their secondary queries,
 // and the Eq. 14 gradient of every pair is formed in the tile from the two
 // radiances (only the loss value leaves the CTA, as FP64 partials).
-template <class S, typename TT, bool TRAIN>
-__global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ QueryParams p) {
+// PERSIST (with TRAIN, cooperative launch): after the fused pass the same
+// launch applies Adam to every parameter group (persistent_adam).
+template <class S, typename TT, bool TRAIN, bool PERSIST = false>
+__global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ BwdParams bp) {
+  const QueryParams& p = bp.p;
   constexpr int H = S::H, NL = S::NL;
   constexpr int ROWS = TRAIN ? NT / 2 : NT;  // pairs or queries per tile
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -609,6 +819,9 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   tc_fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, S::TMEM_COLS);
+  if constexpr (PERSIST) {
+    if (!abort_flag) persistent_adam(bp.a, p.status);
+  }
 }
 
 namespace {
@@ -628,11 +841,14 @@ int launch_fwd(const QueryParams& p, cudaStream_t stream) {
   return OCTA_OK;
 }
 
-template <class S, typename TT, bool TRAIN>
-int launch_bwd(const QueryParams& p0, cudaStream_t stream) {
-  if (p0.n_tiles == 0) return OCTA_OK;
+template <class S, typename TT, bool TRAIN, bool PERSIST>
+int launch_bwd(const QueryParams& p0, const AdamBlock* adam, cudaStream_t stream) {
+  if (p0.n_tiles == 0 && !PERSIST) return OCTA_OK;
   constexpr int ROWS = TRAIN ? NT / 2 : NT;
-  QueryParams p = p0;  // work items: pairs of tiles of one scene
+  BwdParams bp{};
+  bp.p = p0;  // work items: pairs of tiles of one scene
+  QueryParams& p = bp.p;
+  if (adam) bp.a = *adam;
   int64_t items = 0;
   for (int s = 0; s < p.n_scenes; ++s) {
     p.item_begin[s] = items;
@@ -641,15 +857,23 @@ int launch_bwd(const QueryParams& p0, cudaStream_t stream) {
   }
   p.item_begin[p.n_scenes] = items;
   p.n_items = items;
-  if (items == 0) return OCTA_OK;
-  auto kern = bwd_kernel<S, TT, TRAIN>;
+  if (items == 0 && !PERSIST) return OCTA_OK;
+  auto kern = bwd_kernel<S, TT, TRAIN, PERSIST>;
   int per_sm = 0;
   int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, S::NTB,
                               static_cast<int>(S::TMEM_COLS), &per_sm);
   if (rc) return rc;
-  const int64_t grid = std::min<int64_t>(items, int64_t(per_sm) * device_sm_count());
-  kern<<<static_cast<unsigned>(grid), S::NTB, S::SMEM, stream>>>(p);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (PERSIST) {  // every CTA co-resident: the grid barriers need it
+    const int grid = per_sm * device_sm_count();
+    void* args[] = {&bp};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kern), dim3(grid), dim3(S::NTB),
+                                    args, S::SMEM, stream);
+  } else {
+    const int64_t grid = std::min<int64_t>(items, int64_t(per_sm) * device_sm_count());
+    kern<<<static_cast<unsigned>(grid), S::NTB, S::SMEM, stream>>>(bp);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return fail(OCTA_ECUDA, "tc %s launch: %s", TRAIN ? "train" : "bwd",
                                     cudaGetErrorString(e));
   return OCTA_OK;
@@ -678,16 +902,17 @@ int select_shape(const octa_scene* scenes, int n_scenes, int* F, int* need, int*
 
 }  // namespace
 
-template <bool TRAIN>
-int dispatch_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
+template <bool TRAIN, bool PERSIST>
+int dispatch_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, const AdamBlock* adam,
+                 cudaStream_t stream) {
   int F, need, H, NH;
   bool f16;
   int rc = select_shape(scenes, n_scenes, &F, &need, &H, &NH, &f16);
   if (rc) return rc;
-#define OCTA_TC_TRY(F_, WP_, H_, NH_)                                                  \
-  if (F == F_ && H == H_ && NH == NH_ && need <= WP_)                                  \
-    return f16 ? launch_bwd<BShape<F_, WP_, H_, NH_>, __half, TRAIN>(p, stream)       \
-               : launch_bwd<BShape<F_, WP_, H_, NH_>, float, TRAIN>(p, stream);
+#define OCTA_TC_TRY(F_, WP_, H_, NH_)                                                        \
+  if (F == F_ && H == H_ && NH == NH_ && need <= WP_)                                        \
+    return f16 ? launch_bwd<BShape<F_, WP_, H_, NH_>, __half, TRAIN, PERSIST>(p, adam, stream) \
+               : launch_bwd<BShape<F_, WP_, H_, NH_>, float, TRAIN, PERSIST>(p, adam, stream);
   OCTA_TC_TRY(4, 32, 32, 2)
   OCTA_TC_TRY(8, 64, 64, 2)
   OCTA_TC_TRY(8, 80, 64, 2)
@@ -698,11 +923,16 @@ int dispatch_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, c
 }
 
 int query_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
-  return dispatch_bwd<false>(scenes, n_scenes, p, stream);
+  return dispatch_bwd<false, false>(scenes, n_scenes, p, nullptr, stream);
 }
 
 int train_fused(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
-  return dispatch_bwd<true>(scenes, n_scenes, p, stream);
+  return dispatch_bwd<true, false>(scenes, n_scenes, p, nullptr, stream);
+}
+
+int train_step_persistent(const octa_scene* scenes, int n_scenes, const QueryParams& p,
+                          const AdamBlock& adam, cudaStream_t stream) {
+  return dispatch_bwd<true, true>(scenes, n_scenes, p, &adam, stream);
 }
 
 int query_fwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {

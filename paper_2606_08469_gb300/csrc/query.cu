@@ -362,3 +362,69 @@ extern "C" int octa_train_fused(const octa_scene* scenes, int32_t n_scenes, cons
   if (e != cudaSuccess) return fail(OCTA_ECUDA, "clearing loss_dev: %s", cudaGetErrorString(e));
   return tc::train_fused(scenes, n_scenes, p, st);
 }
+
+extern "C" int octa_train_step_batched(const octa_scene* scenes, int32_t n_scenes,
+                                       const octa_pairs* pairs, const octa_scene_grads* grads,
+                                       const octa_param_group* groups, int32_t n_groups, float eps,
+                                       int32_t rhs_grad, const octa_adam_cfg* adam,
+                                       octa_scaler* scaler, double* loss_dev,
+                                       const octa_step_options* options, void* workspace,
+                                       size_t workspace_bytes, int32_t* status, void* stream) {
+  clear_error();
+  if (!pairs || !grads || !loss_dev || !groups || !adam || !scaler || !workspace)
+    return fail(OCTA_EINVAL, "NULL argument");
+  if (n_groups < 1 || n_groups > OCTA_MAX_GROUPS)
+    return fail(OCTA_ERANGE, "n_groups %d outside [1, %d]", n_groups, OCTA_MAX_GROUPS);
+  if (reinterpret_cast<uintptr_t>(workspace) & 255u)
+    return fail(OCTA_EINVAL, "workspace must be 256-byte aligned");
+  if (workspace_bytes < octa_workspace_bytes(OCTA_OP_STEP, 0))
+    return fail(OCTA_EINVAL, "workspace too small for the persistent step");
+  if (!(eps > 0.f)) return fail(OCTA_EINVAL, "eps must be > 0");
+  octa_queries q;
+  std::memset(&q, 0, sizeof(q));
+  q.x = pairs->x;
+  q.omega = pairs->omega;
+  q.n = pairs->n;
+  for (int s = 0; s <= OCTA_MAX_SCENES; ++s) q.scene_start[s] = pairs->scene_start[s];
+  QueryParams p;
+  int rc = build_query_params(scenes, n_scenes, &q, grads, p);
+  if (rc) return rc;
+  for (int s = 0; s < n_scenes; ++s)
+    if (scenes[s].weight_dtype != OCTA_BF16)
+      return fail(OCTA_EUNSUPPORTED, "the persistent step needs BF16 decoders");
+  p.x2 = pairs->x2;
+  p.omega2 = pairs->omega2;
+  p.E = pairs->E;
+  p.w = pairs->w;
+  p.scaler = scaler;
+  p.loss = loss_dev;
+  p.eps = eps;
+  p.rhs_grad = rhs_grad;
+  p.status = status;
+  tc::AdamBlock a{};
+  for (int i = 0; i < n_groups; ++i) {
+    const octa_param_group& g = groups[i];
+    if (g.n < 0 || (g.n > 0 && (!g.param || !g.grad || !g.m || !g.v)))
+      return fail(OCTA_EINVAL, "group %d: bad arrays", i);
+    if (g.work && g.work_dtype != OCTA_F16 && g.work_dtype != OCTA_BF16)
+      return fail(OCTA_EINVAL, "group %d: working copy dtype must be F16 or BF16", i);
+    a.g[i] = g;
+    const uintptr_t mask = reinterpret_cast<uintptr_t>(g.param) | reinterpret_cast<uintptr_t>(g.grad) |
+                           reinterpret_cast<uintptr_t>(g.m) | reinterpret_cast<uintptr_t>(g.v);
+    a.vec4[i] = (mask & 15u) == 0 && (!g.work || (reinterpret_cast<uintptr_t>(g.work) & 7u) == 0);
+  }
+  a.n_groups = n_groups;
+  a.beta1 = adam->beta1;
+  a.beta2 = adam->beta2;
+  a.eps = adam->eps;
+  a.scaler = scaler;
+  a.bar = static_cast<unsigned*>(workspace);
+  a.partials = reinterpret_cast<double*>(static_cast<char*>(workspace) + 256);
+  a.timeout_ns = options && options->barrier_timeout_ns ? options->barrier_timeout_ns : 1000000000ull;
+  a.extra_arrivals = options ? options->extra_barrier_arrivals : 0;
+  if (a.extra_arrivals < 0) return fail(OCTA_EINVAL, "extra_barrier_arrivals must be >= 0");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(loss_dev, 0, sizeof(double) * n_scenes, st);
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "clearing loss_dev: %s", cudaGetErrorString(e));
+  return tc::train_step_persistent(scenes, n_scenes, p, a, st);
+}

@@ -8,9 +8,26 @@
 namespace octa {
 namespace tc {
 
+// Optimiser block of the persistent training step (one launch: fused pass,
+// then Adam over every parameter group after grid-wide barriers).
+struct AdamBlock {
+  octa_param_group g[OCTA_MAX_GROUPS];
+  int32_t vec4[OCTA_MAX_GROUPS];  // group may use 16-byte vector accesses
+  int32_t n_groups;
+  float beta1, beta2, eps;
+  octa_scaler* scaler;
+  unsigned* bar;            // [0] arrivals, [1] generation (workspace, zeroed once)
+  double* partials;         // [gridDim.x] FP64 sums of squares
+  uint64_t timeout_ns;      // bound of every barrier wait
+  int32_t extra_arrivals;   // arrivals awaited beyond the grid (0; tests use > 0)
+};
+
+
 int query_fwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream);
 int query_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream);
 int train_fused(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream);
+int train_step_persistent(const octa_scene* scenes, int n_scenes, const QueryParams& p,
+                          const AdamBlock& adam, cudaStream_t stream);
 
 }  // namespace tc
 }  // namespace octa

@@ -244,6 +244,7 @@ using namespace octa;
 extern "C" size_t octa_workspace_bytes(int32_t op, int64_t n) {
   (void)n;
   if (op == OCTA_OP_LOSS || op == OCTA_OP_ADAM) return kWorkspaceBytes;
+  if (op == OCTA_OP_STEP) return 256 + sizeof(double) * 1024;  // barrier words + CTA partials
   return 0;
 }
 

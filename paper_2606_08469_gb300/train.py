@@ -45,7 +45,8 @@ class TrainStep:
     scene, each scene's primaries followed by its secondaries)."""
 
     def __init__(self, scene_states, pairs, eps=1e-2, rhs_grad=True, lr_tables=1e-2, lr_mlp=1e-3,
-                 scale=2.0 ** 15, growth_interval=2000, device="cuda", fused=False):
+                 scale=2.0 ** 15, growth_interval=2000, device="cuda", fused=False,
+                 persistent=False):
         dev = torch.device(device)
         self.states = scene_states
         self.scenes = [s.scene for s in scene_states]
@@ -73,8 +74,12 @@ class TrainStep:
         self.grads = [(s.grad_t, s.grad_w) for s in scene_states]
         # fused mode (BF16 decoders): one octa_train_fused launch replaces
         # forward + loss + backward; the pair arrays are kept per role
-        self.fused = fused
-        if fused:
+        # persistent mode: the fused pass and Adam in one cooperative launch
+        self.persistent = persistent
+        self.fused = fused or persistent
+        if persistent:
+            self.ws_step = api.workspace(L.OCTA_OP_STEP, 0, device=dev)
+        if self.fused:
             cat = lambda k: torch.cat([p[k] for p in pairs]).to(dev).contiguous()
             self.Px, self.Pw, self.Sx = cat("x"), cat("omega"), cat("x2")
             self.Sw = torch.cat([-p["omega2"] for p in pairs]).to(dev).contiguous()
@@ -104,7 +109,17 @@ class TrainStep:
                              self.grads, self.loss, self.n, self.eps, self.rhs_grad, self.scaler,
                              stream=stream)
 
+    def persistent_step(self, stream=None, status=None, timeout_ns=0, extra_arrivals=0):
+        api.octa_train_step_batched(self.scenes, self.Px, self.Pw, self.Sx, self.Sw, self.Ecat,
+                                    self.wcat, self.grads, self.groups, self.loss, self.scaler,
+                                    self.ws_step, self.n, self.eps, self.rhs_grad,
+                                    timeout_ns=timeout_ns, extra_arrivals=extra_arrivals,
+                                    status=status, stream=stream)
+
     def step(self, stream=None):
+        if self.persistent:
+            self.persistent_step(stream)
+            return
         if self.fused:
             self.fused_pass(stream)
         else:

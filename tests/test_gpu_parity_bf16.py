@@ -389,3 +389,66 @@ def test_fused_training_step_graph_and_scaler():
     assert st.skipped == 1 and st.scale == scale / 2
     assert torch.equal(a.states[0].master_t, before)
     assert torch.count_nonzero(a.states[0].grad_t).item() == 0
+
+
+# ------------------------------------------------------- persistent one-launch step
+
+def _update_err(a_state, b_state, t0):
+    da = a_state.master_t - t0
+    db = b_state.master_t - t0
+    return float(torch.linalg.norm(da - db) / torch.linalg.norm(db))
+
+
+@pytest.mark.parametrize("multi", [False, True])
+def test_persistent_step_matches_fused_plus_adam(multi):
+    """octa_train_step_batched (fused pass + grid barriers + Adam in one
+    cooperative launch) against octa_train_fused followed by adam_step, two
+    steps: same losses, scaler state and parameter updates."""
+    from paper_2606_08469_gb300 import api as A
+    from paper_2606_08469_gb300 import workloads as WL
+    if multi:
+        counts = [3000, 129, 20000, 64, 64, 64, 64, 64]
+        a, _ = WL.batched_train_step(counts=counts, fused=True)
+        b, _ = WL.batched_train_step(counts=counts, persistent=True)
+    else:
+        cfg = I.CONFIGS[2]
+        a, _ = WL.train_step_for(cfg, n_pairs=8192, fused=True)
+        b, _ = WL.train_step_for(cfg, n_pairs=8192, persistent=True)
+    t0 = [s.master_t.clone() for s in a.states]
+    for _ in range(2):
+        a.step()
+        b.step()
+        torch.cuda.synchronize()
+        torch.testing.assert_close(b.loss, a.loss, rtol=1e-6, atol=0)
+        sa, sb = A.read_scaler(a.scaler), A.read_scaler(b.scaler)
+        assert (sa.step, sa.skipped, sa.scale) == (sb.step, sb.skipped, sb.scale)
+        assert abs(sa.grad_norm - sb.grad_norm) <= 1e-5 * sa.grad_norm
+    for sa_, sb_, t in zip(a.states, b.states, t0):
+        assert _update_err(sb_, sa_, t) <= 1e-3
+        assert torch.count_nonzero(sb_.grad_t).item() == 0
+
+
+def test_persistent_step_barrier_timeout_reports_status():
+    """A grid barrier that waits for one CTA more than the grid runs out
+    after its 20 ms limit: the launch returns, OCTA_STATUS_TIMEOUT is set,
+    the optimiser is skipped, and the next step runs normally."""
+    from paper_2606_08469_gb300 import _lib as L
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[2]
+    b, _ = WL.train_step_for(cfg, n_pairs=4096, persistent=True)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    before = b.states[0].master_t.clone()
+    b.persistent_step(status=status, timeout_ns=20_000_000, extra_arrivals=1)
+    torch.cuda.synchronize()
+    assert int(status.item()) & L.OCTA_STATUS_TIMEOUT
+    assert torch.equal(b.states[0].master_t, before)       # Adam did not run
+    for s in b.states:                                      # the caller restarts the step
+        s.grad_t.zero_()
+        s.grad_w.zero_()
+    b.ws_step.zero_()
+    status.zero_()
+    b.persistent_step(status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert not torch.equal(b.states[0].master_t, before)
+    assert torch.isfinite(b.states[0].master_t).all()
