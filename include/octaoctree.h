@@ -304,6 +304,23 @@ int octa_train_step_batched(const octa_scene* scenes, int32_t n_scenes, const oc
                             const octa_step_options* options, void* workspace,
                             size_t workspace_bytes, int32_t* status, void* stream);
 
+/* ---- launch tuning ------------------------------------------------------ */
+/* Process-wide launch knobs read by later calls (an autotuner sets them).
+ * Zero in a field keeps the library's default.                            */
+typedef struct octa_tuning {
+  int32_t fwd_ctas_per_sm;     /* tensor-core forward: cap on resident CTAs
+                                  per SM (each CTA = one 128-query tile)   */
+  int32_t encode_ctas_per_sm;  /* octa_encode: cap on resident CTAs per SM */
+  int32_t engine_ctas_per_sm;  /* FP32 path: cap on resident CTAs per SM   */
+  int32_t fwd_order;           /* forward / encode / FP32 tiles: 1 = each
+                                  persistent CTA takes a contiguous chunk,
+                                  2 = interleaved (default)                */
+  int32_t train_order;         /* training / backward work items: as above */
+  int32_t reserved[3];
+} octa_tuning;
+int octa_set_tuning(const octa_tuning* t);   /* NULL restores the defaults */
+int octa_get_tuning(octa_tuning* t);
+
 /* ---- workspace sizing, errors ------------------------------------------ */
 #define OCTA_OP_LOSS 1
 #define OCTA_OP_ADAM 2

@@ -123,6 +123,12 @@ class octa_adam_cfg(C.Structure):
     _fields_ = [("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
 
 
+class octa_tuning(C.Structure):
+    _fields_ = [("fwd_ctas_per_sm", C.c_int32), ("encode_ctas_per_sm", C.c_int32),
+                ("engine_ctas_per_sm", C.c_int32), ("fwd_order", C.c_int32),
+                ("train_order", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
 class octa_step_options(C.Structure):
     _fields_ = [("barrier_timeout_ns", C.c_uint64), ("extra_barrier_arrivals", C.c_int32),
                 ("reserved", C.c_int32)]
@@ -155,6 +161,8 @@ _SIGNATURES = {
     "adam_step": (C.c_int, [C.POINTER(octa_param_group), C.c_int32, C.POINTER(octa_adam_cfg), _P,
                             _P, C.c_size_t, _P]),
     "octa_workspace_bytes": (C.c_size_t, [C.c_int32, C.c_int64]),
+    "octa_set_tuning": (C.c_int, [C.POINTER(octa_tuning)]),
+    "octa_get_tuning": (C.c_int, [C.POINTER(octa_tuning)]),
     "octa_last_error": (C.c_char_p, []),
     "octa_abi_version": (C.c_int32, []),
 }

@@ -405,7 +405,8 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
   Grads<S> g;
   if (S::BWD) g.zero();
   int cur = -1;
-  for (int64_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+  const WorkRange wr = work_range(p.n_tiles, p.order);
+  for (int64_t tile = wr.begin; tile < wr.end; tile += wr.step) {
     const int s = scene_of_tile(p, tile);
     const DevScene& sc = p.sc[s];
     __syncthreads();  // previous tile finished with shared memory

@@ -101,4 +101,20 @@ inline LaunchCache& launch_cache() {
   return c;
 }
 
+// Process-wide launch knobs (octa_set_tuning); zero fields mean "default".
+inline octa_tuning& tuning() {
+  static octa_tuning t{};
+  return t;
+}
+inline std::mutex& tuning_mutex() {
+  static std::mutex m;
+  return m;
+}
+inline octa_tuning tuning_snapshot() {
+  std::lock_guard<std::mutex> lock(tuning_mutex());
+  return tuning();
+}
+// Resident CTAs per SM after an optional cap (0 = no cap).
+inline int apply_cap(int per_sm, int cap) { return cap > 0 ? std::max(1, std::min(per_sm, cap)) : per_sm; }
+
 }  // namespace octa

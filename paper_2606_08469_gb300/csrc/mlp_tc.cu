@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(NT, 4) fwd_kernel(const __grid_constant__ Quer
   int cur = -1;
   bool failed = false;
 
-  for (int64_t tile = blockIdx.x; tile < p.n_tiles && !failed; tile += gridDim.x) {
+  const WorkRange wr = work_range(p.n_tiles, p.order);
+  for (int64_t tile = wr.begin; tile < wr.end && !failed; tile += wr.step) {
     const int s = scene_of_tile(p, tile);
     const DevScene& sc = p.sc[s];
     __syncthreads();
@@ -577,7 +578,8 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   const float lscale = TRAIN ? (p.scaler ? p.scaler->scale : 1.f) : 1.f;
   float* xch = reinterpret_cast<float*>(gbase + S::GR_XCH);  // radiance exchange (TRAIN)
 
-  for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+  const WorkRange wr = work_range(p.n_items, p.order);
+  for (int64_t item = wr.begin; item < wr.end; item += wr.step) {
     int s = 0;
     while (s + 1 < p.n_scenes && item >= p.item_begin[s + 1]) ++s;
     const DevScene& sc = p.sc[s];
@@ -834,8 +836,12 @@ int launch_fwd(const QueryParams& p, cudaStream_t stream) {
   int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, NT,
                               static_cast<int>(S::TMEM_COLS), &per_sm);
   if (rc) return rc;
+  const octa_tuning tu = tuning_snapshot();
+  per_sm = apply_cap(per_sm, tu.fwd_ctas_per_sm);
+  QueryParams pp = p;
+  pp.order = tu.fwd_order == 1 ? 1 : 0;
   const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * device_sm_count());
-  kern<<<static_cast<unsigned>(grid), NT, S::SMEM, stream>>>(p);
+  kern<<<static_cast<unsigned>(grid), NT, S::SMEM, stream>>>(pp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(OCTA_ECUDA, "tc fwd launch: %s", cudaGetErrorString(e));
   return OCTA_OK;
@@ -857,6 +863,7 @@ int launch_bwd(const QueryParams& p0, const AdamBlock* adam, cudaStream_t stream
   }
   p.item_begin[p.n_scenes] = items;
   p.n_items = items;
+  p.order = tuning_snapshot().train_order == 1 ? 1 : 0;
   if (items == 0 && !PERSIST) return OCTA_OK;
   auto kern = bwd_kernel<S, TT, TRAIN, PERSIST>;
   int per_sm = 0;

@@ -62,7 +62,22 @@ struct QueryParams {
   double* loss;  // [n_scenes], accumulated
   float eps;
   int32_t rhs_grad;
+  int32_t order;  // how persistent CTAs take work: 0 interleaved, 1 contiguous chunks
 };
+
+// Work units [0, n) of this CTA: interleaved (u = block + k * grid) or one
+// contiguous chunk per CTA (fewer scene switches in a multi-scene launch).
+struct WorkRange {
+  int64_t begin, end, step;
+};
+__device__ __forceinline__ WorkRange work_range(int64_t n, int order) {
+  if (order == 1) {
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b = int64_t(blockIdx.x) * chunk;
+    return WorkRange{b, b + chunk < n ? b + chunk : n, 1};
+  }
+  return WorkRange{int64_t(blockIdx.x), n, int64_t(gridDim.x)};
+}
 
 // Scene owning global tile t (tiles never straddle scenes).
 __device__ __forceinline__ int scene_of_tile(const QueryParams& p, int64_t t) {

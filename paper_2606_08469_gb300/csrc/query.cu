@@ -29,7 +29,8 @@ __global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ 
   extern __shared__ __align__(16) uint8_t stage[];
   const int q = threadIdx.x;
   OT* out = static_cast<OT*>(p.features);
-  for (int64_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+  const WorkRange wr = work_range(p.n_tiles, p.order);
+  for (int64_t tile = wr.begin; tile < wr.end; tile += wr.step) {
     const int s = scene_of_tile(p, tile);
     const DevScene& sc = p.sc[s];
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * ENC_NT;
@@ -80,12 +81,15 @@ namespace {
 
 // Persistent grid: as many CTAs as fit on the device, never more than tiles.
 template <class Kern>
-int launch_persistent(Kern kernel, size_t smem, const QueryParams& p, cudaStream_t stream,
-                      int threads) {
-  if (p.n_tiles == 0) return OCTA_OK;
+int launch_persistent(Kern kernel, size_t smem, const QueryParams& p0, cudaStream_t stream,
+                      int threads, int cap, int order) {
+  if (p0.n_tiles == 0) return OCTA_OK;
   int per_sm = 0;
   int rc = launch_cache().get(reinterpret_cast<const void*>(kernel), smem, threads, 0, &per_sm);
   if (rc) return rc;
+  per_sm = apply_cap(per_sm, cap);
+  QueryParams p = p0;
+  p.order = order == 1 ? 1 : 0;
   const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * device_sm_count());
   kernel<<<static_cast<unsigned>(grid), threads, smem, stream>>>(p);
   cudaError_t e = cudaGetLastError();
@@ -178,18 +182,18 @@ namespace {
 // ---------------------------------------------------------------------------
 // FP32 engine dispatch
 // ---------------------------------------------------------------------------
-struct EngineKey {
-  int F, WP, H, NH, tdt;
-};
-
 template <int F, int WP, int H, int NH, typename TT>
 int run_engine(const QueryParams& p, bool bwd, cudaStream_t stream) {
   if (bwd) {
     using S = f32::Shape<F, WP, H, NH, true>;
-    return launch_persistent(f32::engine_kernel<S, TT>, S::SMEM, p, stream, f32::NT);
+    const octa_tuning tu = tuning_snapshot();
+    return launch_persistent(f32::engine_kernel<S, TT>, S::SMEM, p, stream, f32::NT,
+                             tu.engine_ctas_per_sm, tu.train_order);
   }
   using S = f32::Shape<F, WP, H, NH, false>;
-  return launch_persistent(f32::engine_kernel<S, TT>, S::SMEM, p, stream, f32::NT);
+  const octa_tuning tu = tuning_snapshot();
+  return launch_persistent(f32::engine_kernel<S, TT>, S::SMEM, p, stream, f32::NT,
+                           tu.engine_ctas_per_sm, tu.fwd_order);
 }
 
 // Built shapes of the FP32 engine: (F, padded input width, hidden width,
@@ -265,9 +269,12 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
   static_assert(ENC_NT == QT, "tile size");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool f16 = tdt == OCTA_F16, bf = feat_dtype == OCTA_BF16;
-#define OCTA_ENC(F_, TT_, KP_)                                                              \
-  return bf ? launch_persistent(encode_kernel<F_, TT_, __nv_bfloat16, KP_>, smem, p, st, ENC_NT) \
-            : launch_persistent(encode_kernel<F_, TT_, float, KP_>, smem, p, st, ENC_NT);
+  const octa_tuning tu = tuning_snapshot();
+#define OCTA_ENC(F_, TT_, KP_)                                                                   \
+  return bf ? launch_persistent(encode_kernel<F_, TT_, __nv_bfloat16, KP_>, smem, p, st, ENC_NT, \
+                                tu.encode_ctas_per_sm, tu.fwd_order)                             \
+            : launch_persistent(encode_kernel<F_, TT_, float, KP_>, smem, p, st, ENC_NT,         \
+                                tu.encode_ctas_per_sm, tu.fwd_order);
 #define OCTA_ENC_KP(F_, TT_)      \
   if (kmax <= 10) {               \
     OCTA_ENC(F_, TT_, 10)         \
@@ -427,4 +434,26 @@ extern "C" int octa_train_step_batched(const octa_scene* scenes, int32_t n_scene
   cudaError_t e = cudaMemsetAsync(loss_dev, 0, sizeof(double) * n_scenes, st);
   if (e != cudaSuccess) return fail(OCTA_ECUDA, "clearing loss_dev: %s", cudaGetErrorString(e));
   return tc::train_step_persistent(scenes, n_scenes, p, a, st);
+}
+
+extern "C" int octa_set_tuning(const octa_tuning* t) {
+  clear_error();
+  std::lock_guard<std::mutex> lock(tuning_mutex());
+  if (!t) {
+    tuning() = octa_tuning{};
+    return OCTA_OK;
+  }
+  if (t->fwd_ctas_per_sm < 0 || t->encode_ctas_per_sm < 0 || t->engine_ctas_per_sm < 0 ||
+      t->fwd_order < 0 || t->fwd_order > 2 || t->train_order < 0 || t->train_order > 2)
+    return fail(OCTA_EINVAL, "tuning values out of range");
+  tuning() = *t;
+  return OCTA_OK;
+}
+
+extern "C" int octa_get_tuning(octa_tuning* t) {
+  clear_error();
+  if (!t) return fail(OCTA_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lock(tuning_mutex());
+  *t = tuning();
+  return OCTA_OK;
 }

@@ -1,0 +1,73 @@
+"""Launch knobs change how work is spread, never the results; the autotuner
+picks a setting and caches it."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2606_08469_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _reset():
+    from paper_2606_08469_gb300 import build
+    build.build()
+    from paper_2606_08469_gb300 import autotune as T
+    T.set_tuning(None)
+    yield
+    T.set_tuning(None)
+
+
+def test_forward_results_independent_of_knobs():
+    from paper_2606_08469_gb300 import api as A
+    from paper_2606_08469_gb300 import autotune as T
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[3]
+    sc, _ = WL.forward_scene(cfg)
+    x, w = I.uniform_queries(3, 50000)
+    X, W = WL.to_dev(x), WL.to_dev(w)
+    ref, _, _ = A.octa_query_fwd(sc, X, W)
+    for setting in ({"fwd_ctas_per_sm": 1}, {"fwd_ctas_per_sm": 2, "fwd_order": 1},
+                    {"fwd_order": 1}):
+        T.set_tuning(setting)
+        got, _, _ = A.octa_query_fwd(sc, X, W)
+        torch.testing.assert_close(got, ref, rtol=0, atol=0)
+
+
+def test_training_results_independent_of_order():
+    from paper_2606_08469_gb300 import autotune as T
+    from paper_2606_08469_gb300 import workloads as WL
+    counts = [3000, 129, 20000, 64, 64, 64, 64, 64]
+    a, _ = WL.batched_train_step(counts=counts, fused=True)
+    b, _ = WL.batched_train_step(counts=counts, fused=True)
+    a.fused_pass()
+    T.set_tuning({"train_order": 1})
+    b.fused_pass()
+    torch.cuda.synchronize()
+    torch.testing.assert_close(b.loss, a.loss, rtol=1e-6, atol=0)
+    for sa, sb in zip(a.states, b.states):
+        assert torch.linalg.norm(sa.grad_t - sb.grad_t) <= 1e-5 * torch.linalg.norm(sa.grad_t)
+
+
+def test_autotune_picks_and_caches(tmp_path):
+    from paper_2606_08469_gb300 import api as A
+    from paper_2606_08469_gb300 import autotune as T
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[3]
+    sc, _ = WL.forward_scene(cfg)
+    x, w = I.uniform_queries(4, 100000)
+    X, W = WL.to_dev(x), WL.to_dev(w)
+    rgb = torch.empty((len(x), 3), device="cuda")
+    fn = lambda: A.octa_query_fwd(sc, X, W, rgb=rgb)
+    cache = str(tmp_path / "tune.json")
+    best, rep = T.autotune(fn, {"fwd_ctas_per_sm": [2, 4], "fwd_order": [1, 2]}, "test-fwd", cache,
+                           reps=3)
+    assert len(rep["trials"]) == 4 and rep["best_ms"] == min(t["ms"] for t in rep["trials"])
+    assert T.get_tuning()["fwd_ctas_per_sm"] == best["fwd_ctas_per_sm"]
+    with open(cache) as f:
+        assert any(k.endswith("|test-fwd") for k in json.load(f))
+    best2, rep2 = T.autotune(fn, {"fwd_ctas_per_sm": [2, 4]}, "test-fwd", cache)
+    assert best2 == best and rep2["best_ms"] == rep["best_ms"]     # served from the cache

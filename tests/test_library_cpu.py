@@ -111,3 +111,16 @@ def test_query_validation_without_gpu(lib):
                              None, 0, None) == L.OCTA_EINVAL
     assert lib.octa_workspace_bytes(L.OCTA_OP_LOSS, 100) >= 8 * 1024
     assert lib.octa_workspace_bytes(99, 100) == 0
+
+
+def test_tuning_knobs_round_trip(lib):
+    from paper_2606_08469_gb300 import autotune as T
+    T.set_tuning({"fwd_ctas_per_sm": 3, "train_order": 1})
+    got = T.get_tuning()
+    assert got["fwd_ctas_per_sm"] == 3 and got["train_order"] == 1 and got["fwd_order"] == 0
+    from paper_2606_08469_gb300 import _lib as L
+    bad = L.octa_tuning()
+    bad.fwd_order = 7
+    assert lib.octa_set_tuning(C.byref(bad)) == L.OCTA_EINVAL
+    T.set_tuning(None)
+    assert all(v == 0 for v in T.get_tuning().values())
