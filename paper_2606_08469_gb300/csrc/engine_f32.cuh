@@ -38,9 +38,11 @@ struct Shape {
   static constexpr int MAXW = WP > H ? WP : H;
   // BWD keeps h, a_1..a_NH and delta_L; FWD ping-pongs two buffers
   static constexpr int ACT_ROWS = BWD ? (WP + NH * H + 4) : 2 * MAXW;
-  static constexpr size_t SMEM =
+  static constexpr size_t TREE_OFF =
       sizeof(float) * (size_t(WSM) + size_t(ACT_ROWS) * LDA) + sizeof(int) * KMAX * QT +
       sizeof(float) * 2 * QT;
+  static constexpr int TREE_NODES = 1280;  // staged octree, int2 per node
+  static constexpr size_t SMEM = TREE_OFF + 8 * size_t(TREE_NODES);
 };
 
 // ---------------------------------------------------------------------------
@@ -242,10 +244,13 @@ __device__ __forceinline__ void load_weights(const DevScene& sc, float* wsm) {
     dst[i] = i < 3 * S::H ? Wg[sc.w_offset[S::NH] + i] : 0.f;
 }
 
-// Phase 1: fold omega and walk the tree (one thread per query).
+// Phase 1: fold omega and walk the tree (one thread per query), reading node
+// records from the staged tree (global memory when tree is nullptr).  Level
+// l's cell is c >> (15 - l) with c = min(floor(x * 2^15), 2^15 - 1) per axis.
 template <int KMAX>
-__device__ __forceinline__ void locate_tile(const QueryParams& p, const DevScene& sc, int64_t q0,
-                                            int nq, int* node_sm, float* u_sm) {
+__device__ __forceinline__ void locate_tile(const QueryParams& p, const DevScene& sc,
+                                            const int2* tree, int64_t q0, int nq, int* node_sm,
+                                            float* u_sm) {
   const int q = threadIdx.x;
   if (q >= QT) return;
   const bool valid = q < nq;
@@ -263,28 +268,27 @@ __device__ __forceinline__ void locate_tile(const QueryParams& p, const DevScene
   octa_fold(w0, w1, w2, ux, uy);
   u_sm[q] = ux;
   u_sm[QT + q] = uy;
-  x0 = clamp01(x0);
-  x1 = clamp01(x1);
-  x2 = clamp01(x2);
+  const int cx = min(static_cast<int>(clamp01(x0) * 32768.f), 32767);
+  const int cy = min(static_cast<int>(clamp01(x1) * 32768.f), 32767);
+  const int cz = min(static_cast<int>(clamp01(x2) * 32768.f), 32767);
   int node = valid ? 0 : -1;
   node_sm[q] = node;
-  int cp0 = 0, cp1 = 0, cp2 = 0;
 #pragma unroll
   for (int l = 1; l < KMAX; ++l) {
-    if (l < sc.K) {
-      const int c0 = cell_coord(x0, l), c1 = cell_coord(x1, l), c2 = cell_coord(x2, l);
-      const int slot = (c0 - 2 * cp0) | ((c1 - 2 * cp1) << 1) | ((c2 - 2 * cp2) << 2);
-      if (node >= 0) {
-        int fc = __ldg(sc.first_child + node);
+    if (l < sc.K && node >= 0) {
+      const int sh = 15 - l;
+      const int slot = ((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2);
+      int fc;
+      if (tree) {
+        fc = tree[node].x;
+      } else {
+        fc = __ldg(sc.first_child + node);
         if (fc >= 0 && fc > sc.num_nodes - 8) {
           if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
           fc = -1;
         }
-        node = fc >= 0 ? fc + slot : -1;
       }
-      cp0 = c0;
-      cp1 = c1;
-      cp2 = c2;
+      node = fc >= 0 ? fc + slot : -1;
     } else {
       node = -1;
     }
@@ -297,21 +301,17 @@ __device__ __forceinline__ void locate_tile(const QueryParams& p, const DevScene
 }
 
 // Base texel of a node's map, or -1 if the map would leave the table.
-__device__ __forceinline__ int64_t map_base(const QueryParams& p, const DevScene& sc, int node,
-                                            int R) {
-  const int64_t mo = __ldg(sc.map_offset + node);
-  if (mo < 0 || mo + int64_t(R) * R > sc.num_texels) {
-    if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_MAP);
-    return -1;
-  }
-  return mo;
+__device__ __forceinline__ int64_t map_base(const QueryParams& p, const DevScene& sc,
+                                            const int2* tree, int node, int R) {
+  return checked_map_base(p, sc, tree ? tree[node].y : __ldg(sc.map_offset + node), R);
 }
 
 // Phase 2: one thread per (query, level) item for levels [0, nlev); writes
 // feature f of level l for query q to h[(l*F + f) * ld_feat + q * ld_q].
 template <int F, typename TT>
-__device__ __forceinline__ void gather_tile(const QueryParams& p, const DevScene& sc, int64_t q0,
-                                            int nq, int nlev, const int* node_sm,
+__device__ __forceinline__ void gather_tile(const QueryParams& p, const DevScene& sc,
+                                            const int2* tree, int64_t q0, int nq, int nlev,
+                                            const int* node_sm,
                                             const float* u_sm, float* h, int ld_feat, int ld_q) {
   for (int it = threadIdx.x; it < nlev * QT; it += NT) {
     const int l = it / QT, q = it % QT;
@@ -322,7 +322,7 @@ __device__ __forceinline__ void gather_tile(const QueryParams& p, const DevScene
     int64_t a4[4] = {-1, -1, -1, -1};
     if (node >= 0) {
       const int R = sc.R[l];
-      const int64_t mo = map_base(p, sc, node, R);
+      const int64_t mo = map_base(p, sc, tree, node, R);
       if (mo >= 0) {
         const Footprint fp = footprint(u_sm[q], u_sm[QT + q], R);
         float t[4][F];
@@ -363,14 +363,14 @@ __device__ __forceinline__ void gather_tile(const QueryParams& p, const DevScene
 // present level (float4 vector atomics).
 template <int KMAX, int F>
 __device__ __forceinline__ void scatter_tile(const QueryParams& p, const DevScene& sc,
-                                             const int* node_sm, const float* u_sm,
+                                             const int2* tree, const int* node_sm, const float* u_sm,
                                              const float* dh) {
   for (int it = threadIdx.x; it < KMAX * QT; it += NT) {
     const int l = it / QT, q = it % QT;
     const int node = node_sm[l * QT + q];
     if (node < 0) continue;
     const int R = sc.R[l];
-    const int64_t mo = map_base(p, sc, node, R);
+    const int64_t mo = map_base(p, sc, tree, node, R);
     if (mo < 0) continue;
     const Footprint fp = footprint(u_sm[q], u_sm[QT + q], R);
 #pragma unroll
@@ -397,6 +397,8 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
   float* act = wsm + S::WSM;
   int* node_sm = reinterpret_cast<int*>(act + S::ACT_ROWS * LDA);
   float* u_sm = reinterpret_cast<float*>(node_sm + S::KMAX * QT);
+  int2* tree_sm = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(smem) + S::TREE_OFF);
+  const int2* tree = nullptr;
   // activation buffers
   auto act_bwd = [&](int i) { return i == 0 ? act : act + (WP + (i - 1) * H) * LDA; };
   float* dL = act + (WP + NH * H) * LDA;  // delta_L (BWD)
@@ -416,14 +418,16 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
         g.zero();
       }
       load_weights<S>(sc, wsm);
+      tree = stage_tree(p, sc, tree_sm, S::TREE_NODES, threadIdx.x, NT);
       cur = s;
+      __syncthreads();
     }
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * QT;
     const int nq = static_cast<int>(sc.q_end - q0 < QT ? sc.q_end - q0 : int64_t(QT));
     float* h = S::BWD ? act_bwd(0) : buf[0];
-    locate_tile<S::KMAX>(p, sc, q0, nq, node_sm, u_sm);
+    locate_tile<S::KMAX>(p, sc, tree, q0, nq, node_sm, u_sm);
     __syncthreads();
-    gather_tile<S::F, TT>(p, sc, q0, nq, S::KMAX, node_sm, u_sm, h, LDA, 1);
+    gather_tile<S::F, TT>(p, sc, tree, q0, nq, S::KMAX, node_sm, u_sm, h, LDA, 1);
     __syncthreads();
 
     // ---- decoder forward (Eq. 13)
@@ -513,7 +517,7 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
         gemm_bwd_data<H, H, true>(wsm + H * WP + (i - 1) * H * H, act_bwd(i + 1), act_bwd(i));
       __syncthreads();
     }
-    scatter_tile<S::KMAX, S::F>(p, sc, node_sm, u_sm, act_bwd(0));
+    scatter_tile<S::KMAX, S::F>(p, sc, tree, node_sm, u_sm, act_bwd(0));
   }
   if (S::BWD && cur >= 0) g.flush(p.sc[cur]);
 }

@@ -1,7 +1,6 @@
 // Per-thread walk and gather of one query, shared by the tensor-core kernels
 // and the standalone encoding kernel.
 #pragma once
-#include "engine_f32.cuh"
 #include "octa_device.cuh"
 
 namespace octa {
@@ -16,22 +15,27 @@ __device__ __forceinline__ void fma_f16x2_f32(float& s0, float& s1, uint16_t w, 
 }
 
 // One query per thread: fold omega (Eq. 4, 5, canonical binary32), walk the
-// query's path down the octree (Section 3.4), load the map base of every
-// present level, then gather KP levels, two at a time (both levels' texel
-// loads in flight together; one at a time for 32-byte texels), handing the
-// F blended features of level l to store(l, v) (absent levels: zeros).
-// node_sm / u_sm (nullable, row stride nt) keep the path and the folded
-// direction for a later scatter; node_idx / texel_addr outputs of p are
-// written for query gq when requested.  F16W (FP16 tables only): blend with
-// the four weights rounded to FP16 and FP32 accumulation, for consumers that
-// round the features to BF16 anyway (the weight rounding, 2^-12 relative, is
-// 8x below that of the BF16 result).
+// query's path down the octree (Section 3.4) reading each node's record from
+// the staged tree (global memory when tree is nullptr), then gather KP
+// levels, two at a time (both levels' texel loads in flight together; one at
+// a time for 32-byte texels), handing the F blended features of level l to
+// store(l, v) (absent levels: zeros).  The cells of all levels come from one
+// integer per axis: with c = min(floor(x * 2^15), 2^15 - 1), level l's cell
+// is c >> (15 - l), since x * 2^l is exact in binary32 and the floor commutes
+// with the shift.  base_sm / u_sm (nullable, row stride nt) keep the map
+// base of every level (-1: absent) and the folded direction for a later
+// scatter; node_idx / texel_addr outputs of p are written for query gq when
+// requested.  F16W (FP16 tables only): blend with the four weights rounded
+// to FP16 and FP32 accumulation, for consumers that round the features to
+// BF16 anyway (the weight rounding, 2^-12 relative, is 8x below that of the
+// BF16 result).
 template <int F, typename TT, int KP, bool F16W = false, class Store>
 __device__ __forceinline__ void locate_gather_query(const QueryParams& p, const DevScene& sc,
-                                                    const float* __restrict__ xs,
+                                                    const int2* tree, const float* __restrict__ xs,
                                                     const float* __restrict__ ws, int64_t gq,
-                                                    bool valid, int* node_sm, float* u_sm, int q,
+                                                    bool valid, int* base_sm, float* u_sm, int q,
                                                     int nt, Store&& store) {
+  static_assert(KP <= 16, "levels");
   constexpr int WIN = TexelRaw<TT, F>::BYTES <= 16 ? 2 : 1;
   float x0 = 0.f, x1 = 0.f, x2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 1.f;
   if (valid) {
@@ -44,33 +48,39 @@ __device__ __forceinline__ void locate_gather_query(const QueryParams& p, const 
   }
   float ux, uy;
   octa_fold(w0, w1, w2, ux, uy);
-  x0 = clamp01(x0);
-  x1 = clamp01(x1);
-  x2 = clamp01(x2);
-  int node[KP];
-  node[0] = valid ? 0 : -1;
-  int cp0 = 0, cp1 = 0, cp2 = 0;
+  const int cx = min(static_cast<int>(clamp01(x0) * 32768.f), 32767);
+  const int cy = min(static_cast<int>(clamp01(x1) * 32768.f), 32767);
+  const int cz = min(static_cast<int>(clamp01(x2) * 32768.f), 32767);
+  int node[KP], mo[KP];
+  int nd = valid ? 0 : -1;
 #pragma unroll
-  for (int l = 1; l < KP; ++l) {
-    int nd = -1;
-    if (l < sc.K && node[l - 1] >= 0) {
-      const int c0 = cell_coord(x0, l), c1 = cell_coord(x1, l), c2 = cell_coord(x2, l);
-      const int slot = (c0 - 2 * cp0) | ((c1 - 2 * cp1) << 1) | ((c2 - 2 * cp2) << 2);
-      int fc = __ldg(sc.first_child + node[l - 1]);
-      if (fc >= 0 && fc > sc.num_nodes - 8) {
-        if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
-        fc = -1;
-      }
-      nd = fc >= 0 ? fc + slot : -1;
-      cp0 = c0;
-      cp1 = c1;
-      cp2 = c2;
-    }
+  for (int l = 0; l < KP; ++l) {
     node[l] = nd;
+    mo[l] = -1;
+    int fc = -1;
+    if (nd >= 0) {
+      int2 rec;
+      if (tree) {
+        rec = tree[nd];
+      } else {
+        rec = make_int2(__ldg(sc.first_child + nd), __ldg(sc.map_offset + nd));
+        if (rec.x >= 0 && rec.x > sc.num_nodes - 8) {
+          if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
+          rec.x = -1;
+        }
+      }
+      mo[l] = checked_map_base(p, sc, rec.y, sc.R[l]);
+      fc = rec.x;
+    }
+    if (l + 1 < KP) {
+      const int sh = 14 - l;  // level l + 1
+      const int slot = ((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2);
+      nd = (l + 1 < sc.K && fc >= 0) ? fc + slot : -1;
+    }
   }
-  if (node_sm) {
+  if (base_sm) {
 #pragma unroll
-    for (int l = 0; l < KP; ++l) node_sm[l * nt + q] = node[l];
+    for (int l = 0; l < KP; ++l) base_sm[l * nt + q] = mo[l];
     u_sm[q] = ux;
     u_sm[nt + q] = uy;
   }
@@ -80,10 +90,6 @@ __device__ __forceinline__ void locate_gather_query(const QueryParams& p, const 
       if (l < p.kmax_out) p.node_idx[gq * p.kmax_out + l] = node[l];
     for (int l = KP; l < p.kmax_out; ++l) p.node_idx[gq * p.kmax_out + l] = -1;
   }
-  int mo[KP];  // map base per level (texel index < 2^31), -1 when absent
-#pragma unroll
-  for (int l = 0; l < KP; ++l)
-    mo[l] = node[l] >= 0 ? static_cast<int>(f32::map_base(p, sc, node[l], sc.R[l])) : -1;
 #pragma unroll
   for (int l0 = 0; l0 < KP; l0 += WIN) {
     TexelRaw<TT, F> t[WIN][4];

@@ -45,10 +45,13 @@ inline int ctas_from_resources(const void* fn, size_t smem, int threads) {
 // allocate tensor memory (tmem_cols > 0) the count comes from the kernel's
 // registers and shared memory (the runtime's occupancy query reports one CTA
 // per SM for them) and is capped by the 512 tensor-memory columns of an SM.
-// Called once per kernel and device, outside any stream capture.
-inline int resident_ctas(const void* fn, size_t smem, int threads, int tmem_cols, int* out) {
+// Called once per kernel, device and shared-memory size, outside any stream
+// capture; attr_smem (>= smem) is the largest size this kernel is launched
+// with, which the dynamic shared-memory limit must keep allowing.
+inline int resident_ctas(const void* fn, size_t smem, size_t attr_smem, int threads, int tmem_cols,
+                         int* out) {
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+                                       static_cast<int>(attr_smem));
   if (e != cudaSuccess) return fail(OCTA_ECUDA, "cudaFuncSetAttribute(smem): %s", cudaGetErrorString(e));
   e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                            cudaSharedmemCarveoutMaxShared);
@@ -70,13 +73,17 @@ class LaunchCache {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu_);
-    for (int i = 0; i < n_; ++i)
-      if (e_[i].fn == fn && e_[i].dev == dev && e_[i].smem == smem) {
+    size_t attr = smem;
+    for (int i = 0; i < n_; ++i) {
+      if (e_[i].fn != fn || e_[i].dev != dev) continue;
+      if (e_[i].smem == smem) {
         *out = e_[i].per_sm;
         return OCTA_OK;
       }
+      attr = std::max(attr, e_[i].smem);
+    }
     int per_sm = 0;
-    int rc = resident_ctas(fn, smem, threads, tmem_cols, &per_sm);
+    int rc = resident_ctas(fn, smem, attr, threads, tmem_cols, &per_sm);
     if (rc) return rc;
     if (n_ < kMax) e_[n_++] = Entry{fn, dev, smem, per_sm};
     *out = per_sm;

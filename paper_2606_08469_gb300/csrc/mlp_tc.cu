@@ -35,6 +35,17 @@ namespace tc {
 constexpr int NT = 128;   // threads per CTA = queries per tile
 constexpr int NOUT = 16;  // padded output width of the last layer
 
+// Shared memory of an SM and the per-CTA reservation on this GPU family;
+// they size the staged octree so that it does not lower the residency the
+// rest of a kernel's layout allows (a wrong guess costs residency, never
+// correctness: the launcher measures what fits).
+constexpr int kSmemPerSM = 233472, kSmemPerCTAReserved = 1024;
+constexpr int tree_capacity(uint32_t used, int ctas_per_sm) {
+  const int room = kSmemPerSM / ctas_per_sm - kSmemPerCTAReserved - static_cast<int>(used);
+  const int n = room > 0 ? (room / 8) & ~15 : 0;
+  return n > 2048 ? 2048 : n;
+}
+
 template <int F_, int WP_, int H_, int NH_>
 struct Shape {
   static constexpr int F = F_, WP = WP_, H = H_, NH = NH_, NL = NH_ + 1;
@@ -49,10 +60,11 @@ struct Shape {
   static constexpr uint32_t NODE_BYTES = KPAD * NT * 4;
   static constexpr uint32_t U_BYTES = 2 * NT * 4;
   static constexpr uint32_t OFF_ACT = W_BYTES;
-  static constexpr uint32_t OFF_NODE = OFF_ACT + ACT_BYTES;
-  static constexpr uint32_t OFF_U = OFF_NODE + NODE_BYTES;
-  static constexpr uint32_t OFF_BAR = (OFF_U + U_BYTES + 15) & ~15u;
-  static constexpr size_t SMEM = OFF_BAR + 16;
+  static constexpr uint32_t OFF_BAR = (OFF_ACT + ACT_BYTES + 15) & ~15u;
+  // staged octree (int2 per node), as large as four CTAs per SM allow
+  static constexpr uint32_t OFF_TREE = OFF_BAR + 16;
+  static constexpr int TREE_NODES = tree_capacity(OFF_TREE, 4);
+  static constexpr size_t SMEM = OFF_TREE + 8u * TREE_NODES;
   static constexpr uint32_t TMEM_COLS = H <= 32 ? 32 : (H <= 64 ? 64 : 128);
   __host__ __device__ static constexpr uint32_t w_off(int layer) {
     return layer == 0 ? 0u : W0_BYTES + static_cast<uint32_t>(layer - 1) * WH_BYTES;
@@ -83,13 +95,13 @@ __device__ void load_weights_bf16(const DevScene& sc, uint8_t* smem) {
 // operand tile (canonical K-major, one 16-byte store per level for F = 8).
 template <class S, typename TT>
 __device__ __forceinline__ void locate_gather_bf16(const QueryParams& p, const DevScene& sc,
-                                                   const float* __restrict__ xs,
+                                                   const int2* tree, const float* __restrict__ xs,
                                                    const float* __restrict__ ws, int64_t gq,
-                                                   bool valid, uint8_t* act, int* node_sm,
+                                                   bool valid, uint8_t* act, int* base_sm,
                                                    float* u_sm, int q) {
   constexpr int F = S::F;
   locate_gather_query<F, TT, S::KPAD, true>(
-      p, sc, xs, ws, gq, valid, node_sm, u_sm, q, NT, [&](int l, const float (&v)[F]) {
+      p, sc, tree, xs, ws, gq, valid, base_sm, u_sm, q, NT, [&](int l, const float (&v)[F]) {
         uint8_t* dst = act + kmajor_offset(q, l * F, S::WP);
         if constexpr (F == 8) {
           uint4 o;
@@ -125,8 +137,8 @@ template <class S, typename TT>
 __global__ void __launch_bounds__(NT, 4) fwd_kernel(const __grid_constant__ QueryParams p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* act = smem + S::OFF_ACT;
-  int* node_sm = reinterpret_cast<int*>(smem + S::OFF_NODE);
-  float* u_sm = reinterpret_cast<float*>(smem + S::OFF_U);
+  int2* tree_sm = S::TREE_NODES > 0 ? reinterpret_cast<int2*>(smem + S::OFF_TREE) : nullptr;
+  const int2* tree = nullptr;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::OFF_BAR);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::OFF_BAR + 8);
   const uint32_t mbar = smem_addr(bar);
@@ -154,12 +166,14 @@ __global__ void __launch_bounds__(NT, 4) fwd_kernel(const __grid_constant__ Quer
     __syncthreads();
     if (s != cur) {
       load_weights_bf16<S>(sc, smem);
+      tree = stage_tree(p, sc, tree_sm, S::TREE_NODES, threadIdx.x, NT);
       cur = s;
+      __syncthreads();
     }
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * NT;
     const int nq = static_cast<int>(sc.q_end - q0 < NT ? sc.q_end - q0 : int64_t(NT));
-    locate_gather_bf16<S, TT>(p, sc, p.x, p.omega, q0 + threadIdx.x, int(threadIdx.x) < nq, act,
-                              nullptr, nullptr, threadIdx.x);
+    locate_gather_bf16<S, TT>(p, sc, tree, p.x, p.omega, q0 + threadIdx.x, int(threadIdx.x) < nq,
+                              act, nullptr, nullptr, threadIdx.x);
     fence_proxy_async();
     __syncthreads();
 
@@ -238,7 +252,7 @@ struct BShape : Shape<F_, WP_, H_, NH_> {
   static constexpr uint32_t H_TILE = NT * WP_ * 2;
   static constexpr uint32_t A_TILE = NT * H_ * 2;
   static constexpr uint32_t DL_TILE = NT * NOUT * 2;
-  // group region: h | a_1 .. a_NH | delta_L | slack | node | u.  MN-major
+  // group region: h | a_1 .. a_NH | delta_L | slack | map bases | u.  MN-major
   // reads with M = 128 rows run past a tile narrower than 128 features into
   // the next buffer; the slack keeps the last one inside the region.
   static constexpr uint32_t GR_DL = H_TILE + NH_ * A_TILE;
@@ -248,7 +262,9 @@ struct BShape : Shape<F_, WP_, H_, NH_> {
   static constexpr uint32_t GR_BYTES = (GR_XCH + 64 * 4 * 4 + 1023) & ~1023u;
   static constexpr uint32_t OFF_GROUP = (B::W_BYTES + 1023) & ~1023u;
   static constexpr uint32_t OFF_BAR = OFF_GROUP + G * GR_BYTES;
-  static constexpr size_t SMEM = OFF_BAR + 8 * G + 8;
+  static constexpr uint32_t OFF_TREE = (OFF_BAR + 8 * G + 8 + 15) & ~15u;
+  static constexpr int TREE_NODES = tree_capacity(OFF_TREE, 1);
+  static constexpr size_t SMEM = OFF_TREE + 8u * TREE_NODES;
   static constexpr int WORK = WP_ > H_ ? WP_ : H_;
   static constexpr int DW0 = G * WORK;
   static constexpr int DW_COLS = H_ * NH_ + NOUT;
@@ -536,8 +552,10 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   extern __shared__ __align__(1024) uint8_t smem[];
   const int g = threadIdx.x / NT, t = threadIdx.x % NT, warp = threadIdx.x >> 5;
   uint8_t* gbase = smem + S::OFF_GROUP + g * S::GR_BYTES;
-  int* node_sm = reinterpret_cast<int*>(gbase + S::GR_NODE);
+  int* base_sm = reinterpret_cast<int*>(gbase + S::GR_NODE);  // map base per level
   float* u_sm = reinterpret_cast<float*>(gbase + S::GR_U);
+  int2* tree_sm = S::TREE_NODES > 0 ? reinterpret_cast<int2*>(smem + S::OFF_TREE) : nullptr;
+  const int2* tree = nullptr;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::OFF_BAR);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::OFF_BAR + 8 * S::G);
   __shared__ int abort_flag;
@@ -604,6 +622,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
               (n < out && k < in) ? Wg[sc.w_offset[l] + n * in + k] : __float2bfloat16_rn(0.f);
         }
       }
+      tree = stage_tree(p, sc, tree_sm, S::TREE_NODES, threadIdx.x, S::NTB);
       cur = s;
       __syncthreads();
     }
@@ -616,8 +635,8 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
     const bool primary = !TRAIN || t < ROWS;
     const bool valid = row < nq;
     const int64_t gq = q0 + row;
-    locate_gather_bf16<S, TT>(p, sc, primary ? p.x : p.x2, primary ? p.omega : p.omega2, gq, valid,
-                              smem + S::off_act(g, 0), node_sm, u_sm, t);
+    locate_gather_bf16<S, TT>(p, sc, tree, primary ? p.x : p.x2, primary ? p.omega : p.omega2, gq,
+                              valid, smem + S::off_act(g, 0), base_sm, u_sm, t);
     fence_proxy_async();
     named_sync(gbar, NT);
 
@@ -784,12 +803,9 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
         tc_fence_before_sync();
 #pragma unroll
         for (int l = 0; l < S::KPAD; ++l) {
-          const int node = node_sm[l * NT + t];
-          if (node < 0) continue;
-          const int R = sc.R[l];
-          const int64_t mo = f32::map_base(p, sc, node, R);
+          const int64_t mo = base_sm[l * NT + t];
           if (mo < 0) continue;
-          const Footprint fp = footprint(u_sm[t], u_sm[NT + t], R);
+          const Footprint fp = footprint(u_sm[t], u_sm[NT + t], sc.R[l]);
 #pragma unroll
           for (int c4 = 0; c4 < S::F / 4; ++c4) {
             const float g0 = __uint_as_float(r[l * S::F + 4 * c4 + 0]);

@@ -63,6 +63,10 @@ struct QueryParams {
   float eps;
   int32_t rhs_grad;
   int32_t order;  // how persistent CTAs take work: 0 interleaved, 1 contiguous chunks
+  // staged octree of kernels with a run-time shared-memory layout: capacity
+  // in nodes (0: walk in global memory) and byte offset in dynamic memory
+  int32_t tree_cap;
+  int32_t tree_off;
 };
 
 // Work units [0, n) of this CTA: interleaved (u = block + k * grid) or one
@@ -173,13 +177,38 @@ __device__ __forceinline__ Footprint footprint(float ux, float uy, int R) {
   return f;
 }
 
-// Level-l cell coordinate of x in [0,1] (x * 2^l is exact in binary32).
-__device__ __forceinline__ int cell_coord(float x, int l) {
-  const int n = 1 << l;
-  return min(static_cast<int>(floorf(x * static_cast<float>(n))), n - 1);
+__device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
+
+// Node records {first_child, map_offset} of scene sc in shared memory for the
+// walk of Section 3.4: one int2 per node, first_child validated here (a child
+// block running past the node array is reported and cut).  Returns the staged
+// view, or nullptr when there is no room (tree larger than cap nodes); the
+// caller synchronises the CTA before the first walk.
+__device__ __forceinline__ const int2* stage_tree(const QueryParams& p, const DevScene& sc,
+                                                  int2* tree_sm, int cap, int tid, int nthr) {
+  if (tree_sm == nullptr || sc.num_nodes > cap) return nullptr;
+  for (int n = tid; n < sc.num_nodes; n += nthr) {
+    int fc = __ldg(sc.first_child + n);
+    if (fc >= 0 && fc > sc.num_nodes - 8) {
+      if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
+      fc = -1;
+    }
+    tree_sm[n] = make_int2(fc, __ldg(sc.map_offset + n));
+  }
+  return tree_sm;
 }
 
-__device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
+// Map base of a level-l node, or -1 (reported) when its R x R map runs past
+// the table.
+__device__ __forceinline__ int checked_map_base(const QueryParams& p, const DevScene& sc, int mo,
+                                                int R) {
+  if (mo < 0 || int64_t(mo) + int64_t(R) * R > sc.num_texels) {
+    if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_MAP);
+    return -1;
+  }
+  return mo;
+}
+
 
 // Loads of one texel's F features as FP32.
 template <typename TT, int F>

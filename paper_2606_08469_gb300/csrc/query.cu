@@ -29,10 +29,18 @@ __global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ 
   extern __shared__ __align__(16) uint8_t stage[];
   const int q = threadIdx.x;
   OT* out = static_cast<OT*>(p.features);
+  int2* tree_sm = p.tree_cap > 0 ? reinterpret_cast<int2*>(stage + p.tree_off) : nullptr;
+  const int2* tree = nullptr;
+  int cur = -1;
   const WorkRange wr = work_range(p.n_tiles, p.order);
   for (int64_t tile = wr.begin; tile < wr.end; tile += wr.step) {
     const int s = scene_of_tile(p, tile);
     const DevScene& sc = p.sc[s];
+    if (s != cur) {
+      __syncthreads();
+      tree = stage_tree(p, sc, tree_sm, p.tree_cap, q, ENC_NT);
+      cur = s;
+    }
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * ENC_NT;
     const int nq = static_cast<int>(sc.q_end - q0 < ENC_NT ? sc.q_end - q0 : int64_t(ENC_NT));
     const int W = sc.K * F;
@@ -40,7 +48,7 @@ __global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ 
     const int rb = (row_bytes + 15) & ~15;  // staging row stride
     __syncthreads();
     locate_gather_query<F, TT, KP, sizeof(OT) == 2>(
-        p, sc, p.x, p.omega, q0 + q, q < nq, nullptr, nullptr, q, ENC_NT,
+        p, sc, tree, p.x, p.omega, q0 + q, q < nq, nullptr, nullptr, q, ENC_NT,
         [&](int l, const float (&v)[F]) {
           if (l >= sc.K) return;
           uint8_t* dst = stage + q * rb + l * F * int(sizeof(OT));
@@ -264,7 +272,15 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
   p.kmax_out = kmax;
   p.status = status;
   const size_t ot = feat_dtype == OCTA_BF16 ? 2 : 4;
-  const size_t smem = size_t(ENC_NT) * ((size_t(kmax) * F * ot + 15) & ~size_t(15));
+  size_t smem = size_t(ENC_NT) * ((size_t(kmax) * F * ot + 15) & ~size_t(15));
+  // staged octree: the largest scene's nodes in granules of 256, at most 2048
+  int max_nodes = 0;
+  for (int s = 0; s < n_scenes; ++s) max_nodes = std::max(max_nodes, scenes[s].num_nodes);
+  if (max_nodes <= 2048) {
+    p.tree_cap = (max_nodes + 255) & ~255;
+    p.tree_off = static_cast<int32_t>(smem);
+    smem += size_t(p.tree_cap) * 8;
+  }
   // the encode kernel tiles ENC_NT queries; QT-sized tiles were counted above
   static_assert(ENC_NT == QT, "tile size");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
