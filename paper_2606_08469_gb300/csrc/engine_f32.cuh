@@ -249,28 +249,19 @@ __device__ __forceinline__ void load_weights(const DevScene& sc, float* wsm) {
 // l's cell is c >> (15 - l) with c = min(floor(x * 2^15), 2^15 - 1) per axis.
 template <int KMAX>
 __device__ __forceinline__ void locate_tile(const QueryParams& p, const DevScene& sc,
-                                            const int2* tree, int64_t q0, int nq, int* node_sm,
-                                            float* u_sm) {
+                                            const int2* tree, const QueryIn& in, int64_t q0,
+                                            int nq, int* node_sm, float* u_sm) {
   const int q = threadIdx.x;
   if (q >= QT) return;
   const bool valid = q < nq;
   const int64_t gq = q0 + q;
-  float x0 = 0.f, x1 = 0.f, x2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 1.f;
-  if (valid) {
-    x0 = p.x[3 * gq];
-    x1 = p.x[3 * gq + 1];
-    x2 = p.x[3 * gq + 2];
-    w0 = p.omega[3 * gq];
-    w1 = p.omega[3 * gq + 1];
-    w2 = p.omega[3 * gq + 2];
-  }
   float ux, uy;
-  octa_fold(w0, w1, w2, ux, uy);
+  octa_fold(in.w0, in.w1, in.w2, ux, uy);
   u_sm[q] = ux;
   u_sm[QT + q] = uy;
-  const int cx = min(static_cast<int>(clamp01(x0) * 32768.f), 32767);
-  const int cy = min(static_cast<int>(clamp01(x1) * 32768.f), 32767);
-  const int cz = min(static_cast<int>(clamp01(x2) * 32768.f), 32767);
+  const int cx = min(static_cast<int>(clamp01(in.x0) * 32768.f), 32767);
+  const int cy = min(static_cast<int>(clamp01(in.x1) * 32768.f), 32767);
+  const int cz = min(static_cast<int>(clamp01(in.x2) * 32768.f), 32767);
   int node = valid ? 0 : -1;
   node_sm[q] = node;
 #pragma unroll
@@ -408,9 +399,13 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
   if (S::BWD) g.zero();
   int cur = -1;
   const WorkRange wr = work_range(p.n_tiles, p.order);
+  const int qrow = threadIdx.x < QT ? int(threadIdx.x) : QT;  // locate threads only
+  QueryIn next = wr.begin < wr.end ? load_tile_query(p, wr.begin, qrow, QT) : QueryIn{};
   for (int64_t tile = wr.begin; tile < wr.end; tile += wr.step) {
     const int s = scene_of_tile(p, tile);
     const DevScene& sc = p.sc[s];
+    const QueryIn in = next;
+    if (tile + wr.step < wr.end) next = load_tile_query(p, tile + wr.step, qrow, QT);
     __syncthreads();  // previous tile finished with shared memory
     if (s != cur) {
       if (S::BWD && cur >= 0) {
@@ -425,7 +420,7 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * QT;
     const int nq = static_cast<int>(sc.q_end - q0 < QT ? sc.q_end - q0 : int64_t(QT));
     float* h = S::BWD ? act_bwd(0) : buf[0];
-    locate_tile<S::KMAX>(p, sc, tree, q0, nq, node_sm, u_sm);
+    locate_tile<S::KMAX>(p, sc, tree, in, q0, nq, node_sm, u_sm);
     __syncthreads();
     gather_tile<S::F, TT>(p, sc, tree, q0, nq, S::KMAX, node_sm, u_sm, h, LDA, 1);
     __syncthreads();

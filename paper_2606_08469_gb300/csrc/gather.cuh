@@ -31,26 +31,16 @@ __device__ __forceinline__ void fma_f16x2_f32(float& s0, float& s1, uint16_t w, 
 // BF16 result).
 template <int F, typename TT, int KP, bool F16W = false, class Store>
 __device__ __forceinline__ void locate_gather_query(const QueryParams& p, const DevScene& sc,
-                                                    const int2* tree, const float* __restrict__ xs,
-                                                    const float* __restrict__ ws, int64_t gq,
-                                                    bool valid, int* base_sm, float* u_sm, int q,
-                                                    int nt, Store&& store) {
+                                                    const int2* tree, const QueryIn& in,
+                                                    int64_t gq, bool valid, int* base_sm,
+                                                    float* u_sm, int q, int nt, Store&& store) {
   static_assert(KP <= 16, "levels");
   constexpr int WIN = TexelRaw<TT, F>::BYTES <= 16 ? 2 : 1;
-  float x0 = 0.f, x1 = 0.f, x2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 1.f;
-  if (valid) {
-    x0 = xs[3 * gq];
-    x1 = xs[3 * gq + 1];
-    x2 = xs[3 * gq + 2];
-    w0 = ws[3 * gq];
-    w1 = ws[3 * gq + 1];
-    w2 = ws[3 * gq + 2];
-  }
   float ux, uy;
-  octa_fold(w0, w1, w2, ux, uy);
-  const int cx = min(static_cast<int>(clamp01(x0) * 32768.f), 32767);
-  const int cy = min(static_cast<int>(clamp01(x1) * 32768.f), 32767);
-  const int cz = min(static_cast<int>(clamp01(x2) * 32768.f), 32767);
+  octa_fold(in.w0, in.w1, in.w2, ux, uy);
+  const int cx = min(static_cast<int>(clamp01(in.x0) * 32768.f), 32767);
+  const int cy = min(static_cast<int>(clamp01(in.x1) * 32768.f), 32767);
+  const int cz = min(static_cast<int>(clamp01(in.x2) * 32768.f), 32767);
   int node[KP], mo[KP];
   int nd = valid ? 0 : -1;
 #pragma unroll

@@ -95,13 +95,12 @@ __device__ void load_weights_bf16(const DevScene& sc, uint8_t* smem) {
 // operand tile (canonical K-major, one 16-byte store per level for F = 8).
 template <class S, typename TT>
 __device__ __forceinline__ void locate_gather_bf16(const QueryParams& p, const DevScene& sc,
-                                                   const int2* tree, const float* __restrict__ xs,
-                                                   const float* __restrict__ ws, int64_t gq,
+                                                   const int2* tree, const QueryIn& in, int64_t gq,
                                                    bool valid, uint8_t* act, int* base_sm,
                                                    float* u_sm, int q) {
   constexpr int F = S::F;
   locate_gather_query<F, TT, S::KPAD, true>(
-      p, sc, tree, xs, ws, gq, valid, base_sm, u_sm, q, NT, [&](int l, const float (&v)[F]) {
+      p, sc, tree, in, gq, valid, base_sm, u_sm, q, NT, [&](int l, const float (&v)[F]) {
         uint8_t* dst = act + kmajor_offset(q, l * F, S::WP);
         if constexpr (F == 8) {
           uint4 o;
@@ -160,9 +159,12 @@ __global__ void __launch_bounds__(NT, 4) fwd_kernel(const __grid_constant__ Quer
   bool failed = false;
 
   const WorkRange wr = work_range(p.n_tiles, p.order);
+  QueryIn next = wr.begin < wr.end ? load_tile_query(p, wr.begin, threadIdx.x, NT) : QueryIn{};
   for (int64_t tile = wr.begin; tile < wr.end && !failed; tile += wr.step) {
     const int s = scene_of_tile(p, tile);
     const DevScene& sc = p.sc[s];
+    const QueryIn in = next;
+    if (tile + wr.step < wr.end) next = load_tile_query(p, tile + wr.step, threadIdx.x, NT);
     __syncthreads();
     if (s != cur) {
       load_weights_bf16<S>(sc, smem);
@@ -172,8 +174,8 @@ __global__ void __launch_bounds__(NT, 4) fwd_kernel(const __grid_constant__ Quer
     }
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * NT;
     const int nq = static_cast<int>(sc.q_end - q0 < NT ? sc.q_end - q0 : int64_t(NT));
-    locate_gather_bf16<S, TT>(p, sc, tree, p.x, p.omega, q0 + threadIdx.x, int(threadIdx.x) < nq,
-                              act, nullptr, nullptr, threadIdx.x);
+    locate_gather_bf16<S, TT>(p, sc, tree, in, q0 + threadIdx.x, int(threadIdx.x) < nq, act,
+                              nullptr, nullptr, threadIdx.x);
     fence_proxy_async();
     __syncthreads();
 
@@ -596,11 +598,26 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   const float lscale = TRAIN ? (p.scaler ? p.scaler->scale : 1.f) : 1.f;
   float* xch = reinterpret_cast<float*>(gbase + S::GR_XCH);  // radiance exchange (TRAIN)
 
+  // query (pair) row of this thread in a tile, and which pair array it reads
+  const int row = TRAIN ? (t & (ROWS - 1)) : t;
+  const bool primary = !TRAIN || t < ROWS;
+  const float* xs = primary ? p.x : p.x2;
+  const float* ws = primary ? p.omega : p.omega2;
+  auto item_query = [&](int64_t item) {  // this thread's query of an item, prefetched
+    int s = 0;
+    while (s + 1 < p.n_scenes && item >= p.item_begin[s + 1]) ++s;
+    const DevScene& sc = p.sc[s];
+    const int64_t gq = sc.q_begin + (2 * (item - p.item_begin[s]) + g) * ROWS + row;
+    return load_query(xs, ws, gq, gq < sc.q_end);
+  };
   const WorkRange wr = work_range(p.n_items, p.order);
+  QueryIn next = wr.begin < wr.end ? item_query(wr.begin) : QueryIn{};
   for (int64_t item = wr.begin; item < wr.end; item += wr.step) {
     int s = 0;
     while (s + 1 < p.n_scenes && item >= p.item_begin[s + 1]) ++s;
     const DevScene& sc = p.sc[s];
+    const QueryIn in = next;
+    if (item + wr.step < wr.end) next = item_query(item + wr.step);
     tc_fence_before_sync();
     __syncthreads();
     if (abort_flag) break;
@@ -631,12 +648,10 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
     if (tile_s >= tiles_s) continue;  // odd tile count: this group idles
     const int64_t q0 = sc.q_begin + tile_s * ROWS;  // first query (pair) of the tile
     const int nq = static_cast<int>(sc.q_end - q0 < ROWS ? sc.q_end - q0 : int64_t(ROWS));
-    const int row = TRAIN ? (t & (ROWS - 1)) : t;   // query (pair) of this thread in the tile
-    const bool primary = !TRAIN || t < ROWS;
     const bool valid = row < nq;
     const int64_t gq = q0 + row;
-    locate_gather_bf16<S, TT>(p, sc, tree, primary ? p.x : p.x2, primary ? p.omega : p.omega2, gq,
-                              valid, smem + S::off_act(g, 0), base_sm, u_sm, t);
+    locate_gather_bf16<S, TT>(p, sc, tree, in, gq, valid, smem + S::off_act(g, 0), base_sm, u_sm,
+                              t);
     fence_proxy_async();
     named_sync(gbar, NT);
 

@@ -91,6 +91,34 @@ __device__ __forceinline__ int scene_of_tile(const QueryParams& p, int64_t t) {
   return s;
 }
 
+// Position and direction of one query, loaded a tile ahead of its walk so
+// that the HBM latency overlaps the previous tile's work.
+struct QueryIn {
+  float x0, x1, x2, w0, w1, w2;
+};
+__device__ __forceinline__ QueryIn load_query(const float* __restrict__ xs,
+                                              const float* __restrict__ ws, int64_t gq,
+                                              bool valid) {
+  QueryIn in{0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
+  if (valid) {
+    in.x0 = __ldcs(xs + 3 * gq);
+    in.x1 = __ldcs(xs + 3 * gq + 1);
+    in.x2 = __ldcs(xs + 3 * gq + 2);
+    in.w0 = __ldcs(ws + 3 * gq);
+    in.w1 = __ldcs(ws + 3 * gq + 1);
+    in.w2 = __ldcs(ws + 3 * gq + 2);
+  }
+  return in;
+}
+
+// Query row of one tile of tile_rows queries (persistent tile loops).
+__device__ __forceinline__ QueryIn load_tile_query(const QueryParams& p, int64_t tile, int row,
+                                                   int tile_rows) {
+  const DevScene& sc = p.sc[scene_of_tile(p, tile)];
+  const int64_t gq = sc.q_begin + (tile - sc.tile_begin) * tile_rows + row;
+  return load_query(p.x, p.omega, gq, row < tile_rows && gq < sc.q_end);
+}
+
 // Eq. 4 and Eq. 5 in the canonical binary32 order (one IEEE rounding per
 // operation, no contraction), so the integer texel coordinates agree
 // bit-exactly with any other implementation of the same sequence:

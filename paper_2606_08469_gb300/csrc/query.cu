@@ -33,9 +33,12 @@ __global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ 
   const int2* tree = nullptr;
   int cur = -1;
   const WorkRange wr = work_range(p.n_tiles, p.order);
+  QueryIn next = wr.begin < wr.end ? load_tile_query(p, wr.begin, q, ENC_NT) : QueryIn{};
   for (int64_t tile = wr.begin; tile < wr.end; tile += wr.step) {
     const int s = scene_of_tile(p, tile);
     const DevScene& sc = p.sc[s];
+    const QueryIn in = next;
+    if (tile + wr.step < wr.end) next = load_tile_query(p, tile + wr.step, q, ENC_NT);
     if (s != cur) {
       __syncthreads();
       tree = stage_tree(p, sc, tree_sm, p.tree_cap, q, ENC_NT);
@@ -48,7 +51,7 @@ __global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ 
     const int rb = (row_bytes + 15) & ~15;  // staging row stride
     __syncthreads();
     locate_gather_query<F, TT, KP, sizeof(OT) == 2>(
-        p, sc, tree, p.x, p.omega, q0 + q, q < nq, nullptr, nullptr, q, ENC_NT,
+        p, sc, tree, in, q0 + q, q < nq, nullptr, nullptr, q, ENC_NT,
         [&](int l, const float (&v)[F]) {
           if (l >= sc.K) return;
           uint8_t* dst = stage + q * rb + l * F * int(sizeof(OT));
