@@ -175,9 +175,10 @@ def bf16_vs_f32_leg(dev, flush, stream, steps, peaks):
                        "1048576 pairs = 2097152 queries, dynamic loss scaling"}
     W = cfg.widths
     fwd_flop = 2 * sum(a * b for a, b in zip(W[:-1], W[1:]))
-    for prec in ("bf16", "bf16_unfused", "f32"):
-        step, _ = WL.train_step_for(cfg, device=dev, precision="f32" if prec == "f32" else None,
-                                    fused=prec == "bf16", persistent=False)
+    for prec in ("bf16", "bf16_unfused", "f32", "f32_fused"):
+        step, _ = WL.train_step_for(cfg, device=dev,
+                                    precision="f32" if prec.startswith("f32") else None,
+                                    fused=prec in ("bf16", "f32_fused"), persistent=False)
         for _ in range(3):
             step.step()
         stream.synchronize()
@@ -199,6 +200,9 @@ def bf16_vs_f32_leg(dev, flush, stream, steps, peaks):
                 one.step()
             leg["one_launch_ms_per_step"] = round(_timed(one.step, steps, flush, stream), 4)
             del one
+        elif prec == "f32_fused":
+            leg["fused_pass_ms"] = round(_timed(step.fused_pass, steps, flush, stream), 4)
+            leg["path"] = "octa_train_fused on the FP32 engine + adam_step"
         else:
             step.forward()
             leg["fwd_ms"] = round(_timed(step.forward, steps, flush, stream), 4)
@@ -208,6 +212,7 @@ def bf16_vs_f32_leg(dev, flush, stream, steps, peaks):
         out[prec] = leg
         del step
     out["speedup_bf16_over_f32"] = round(out["bf16"]["Mq/s"] / out["f32"]["Mq/s"], 3)
+    out["speedup_bf16_over_f32_fused"] = round(out["bf16"]["Mq/s"] / out["f32_fused"]["Mq/s"], 3)
     return out
 
 
@@ -379,7 +384,10 @@ def run_ours(args):
     from paper_2606_08469_gb300 import workloads as WL
 
     cfg = I.CONFIGS[1]
-    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=args.pairs, device=dev)
+    # the FP32 training step: the engine's fused pass (forward, Eq. 14
+    # gradient, backward in one launch) and Adam with the loss scaler
+    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=args.pairs, device=dev,
+                                                             fused=True)
     n_q = 2 * pairs.n
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
@@ -394,7 +402,7 @@ def run_ours(args):
     barrier()
 
     # device-resident timed region: per step, flush L2 (outside the events),
-    # then time the whole step and, inside it, the backward kernel
+    # then time the whole step and, inside it, the fused training pass
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -408,10 +416,8 @@ def run_ours(args):
             flush.zero_()
             a, b, c, d = ev[k]
             a.record(stream)
-            step.forward()
-            step.loss_and_grad()
             c.record(stream)
-            step.backward()
+            step.fused_pass()
             d.record(stream)
             step.optimizer()
             b.record(stream)
@@ -423,7 +429,7 @@ def run_ours(args):
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    launches = 5 * args.steps  # fwd, residual_loss, bwd, adam norm, adam update
+    launches = 3 * args.steps  # fused pass, adam norm, adam update
 
     # forward-only rate (same queries), L2 flushed between launches
     fwd_ms = []
@@ -439,19 +445,17 @@ def run_ours(args):
 
     # end to end through the public API: pinned host inputs copied in every
     # step, the loss read back every step
-    host = {k: torch.from_numpy(v).pin_memory() for k, v in
-            {"X": step.X.cpu().numpy(), "Om": step.Om.cpu().numpy(), "E": step.E[0].cpu().numpy(),
-             "w": step.w[0].cpu().numpy()}.items()}
+    dev_in = {"Px": step.Px, "Pw": step.Pw, "Sx": step.Sx, "Sw": step.Sw, "E": step.Ecat,
+              "w": step.wcat}  # the pair arrays the fused pass reads
+    host = {k: t.cpu().pin_memory() for k, t in dev_in.items()}
     loss_host = torch.empty(1, dtype=torch.float64).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in host.values())
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        step.X.copy_(host["X"], non_blocking=True)
-        step.Om.copy_(host["Om"], non_blocking=True)
-        step.E[0].copy_(host["E"], non_blocking=True)
-        step.w[0].copy_(host["w"], non_blocking=True)
+        for k, t in dev_in.items():
+            t.copy_(host[k], non_blocking=True)
         step.step()
         loss_host.copy_(step.loss, non_blocking=True)
     e1.record(stream)
@@ -465,8 +469,9 @@ def run_ours(args):
     if rank == 0:
         peaks, src = _peaks()
         sc = api.read_scaler(step.scaler)
-        # dominant kernel: the FP32 backward (recomputed forward + backward),
-        # bound by FP32 FFMA issue; algorithmic flops at the real widths
+        # dominant kernel: the FP32 fused training pass (forward + backward of
+        # every query), bound by FP32 FFMA issue; algorithmic flops at the
+        # real widths
         W = cfg.widths
         fwd_flop = 2 * sum(a * b for a, b in zip(W[:-1], W[1:]))
         bwd_flop = 3 * fwd_flop
@@ -489,19 +494,21 @@ def run_ours(args):
             "data": "synthetic (seeded octree, features, MLP, surface samples; no scene assets)",
             "config": {"workload": "config[1] FP32 training step: depth-6 seeded octree "
                                    f"({tree.num_nodes} nodes, R 32..8, F=8 FP32), decoder 56-64-64-3, "
-                                   f"{pairs.n} pairs = {n_q} queries per step (fwd, Eq.14 loss, bwd, Adam)",
+                                   f"{pairs.n} pairs = {n_q} queries per step (fused fwd + Eq.14 "
+                                   "gradient + bwd, then Adam)",
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": f"replicas x{world}"},
             "fwd_only": {"value": round(world * n_q / (statistics.mean(fwd_ms) / 1e3) / 1e6, 3),
                          "unit": UNIT, "ms": round(statistics.mean(fwd_ms), 4)},
             "loss": float(step.loss.item()),
             "grad_norm": float(sc.grad_norm),
-            "roofline": {"bound": "alu", "kernel": "f32 engine backward (recompute + bwd + scatter)",
+            "roofline": {"bound": "alu", "kernel": "f32 engine fused training pass "
+                                                   "(fwd + Eq.14 gradient + bwd + scatter)",
                          "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                          "frac": round(achieved / peak, 4), "traffic": None,
                          "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {clk:.0f} MHz "
                                         f"({src} sm_max_mhz)",
-                         "bwd_ms": round(statistics.mean(bwd_ms), 4)},
+                         "pass_ms": round(statistics.mean(bwd_ms), 4)},
             "e2e": {"value": round(world * n_q * args.steps / (e2e_ms / 1e3) / 1e6, 3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
             "gpu_launches": launches,

@@ -238,7 +238,8 @@ typedef struct octa_pairs {
 } octa_pairs;
 
 /* octa_train_fused -- octa_query_fwd + residual_loss + octa_query_bwd of a
- * training batch in one launch (BF16 decoders on the tensor cores only).
+ * training batch in one launch: BF16 decoders on the tensor cores, FP32
+ * decoders on the FP32 engine (CUDA cores); all scenes share the dtype.
  * Every 64-pair tile runs the primary and secondary queries together, forms
  * the Eq. 14 gradient of each pair from its two radiances in the tile
  * (the target's dependence on the secondary query enters iff rhs_grad; the
@@ -246,7 +247,8 @@ typedef struct octa_pairs {
  * decoder (gradients of S * loss, S = scaler->scale or 1; accumulated into
  * grads as in octa_query_bwd).  loss_dev: device double [n_scenes], set to
  * each scene's mean r^2 over its pairs and channels (zeroed by the call;
- * FP64 partials, summed with atomics).  OCTA_EUNSUPPORTED for FP32 decoders.*/
+ * FP64 partials, summed with atomics).  OCTA_EUNSUPPORTED for scenes of
+ * mixed decoder dtypes.                                                    */
 int octa_train_fused(const octa_scene* scenes, int32_t n_scenes, const octa_pairs* pairs,
                      float eps, int32_t rhs_grad, const octa_scaler* scaler, double* loss_dev,
                      const octa_scene_grads* grads, int32_t* status, void* stream);

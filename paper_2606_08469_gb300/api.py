@@ -222,7 +222,8 @@ def octa_query_bwd(scenes, x, omega, d_rgb, grads, counts=None, status=None, str
 
 def octa_train_fused(scenes, x, omega, x2, omega2, E, w, grads, loss_out, counts=None, eps=1e-2,
                      rhs_grad=True, scaler=None, status=None, stream=None):
-    """Fused forward + Eq. 14 loss + backward over training pairs (BF16)."""
+    """Fused forward + Eq. 14 loss + backward over training pairs (BF16
+    decoders on the tensor cores, FP32 decoders on the FP32 engine)."""
     arr, ns = _scene_array(scenes)
     g = (L.octa_scene_grads * ns)(*[L.octa_scene_grads(dt.data_ptr(), dw.data_ptr())
                                     for dt, dw in grads])

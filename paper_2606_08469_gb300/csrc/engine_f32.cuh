@@ -380,8 +380,34 @@ __device__ __forceinline__ void scatter_tile(const QueryParams& p, const DevScen
   }
 }
 
-template <class S, typename TT>
+// Sum of every thread's FP64 loss partial, added once per CTA to loss as
+// a mean over 3 n_pairs elements (all threads of the CTA call it).
+__device__ __forceinline__ void flush_loss_f64(double& acc, double* loss, int64_t n_pairs) {
+  __shared__ double red[NT / 32];
+  double v = acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < NT / 32; ++i) t += red[i];
+    atomicAdd(loss, t / (3.0 * double(n_pairs)));
+  }
+  __syncthreads();
+  acc = 0.0;
+}
+
+// TRAIN (with BWD): the fused training pass.  A tile holds PR = QT / 2 pairs:
+// rows 0..PR-1 their primary queries (x, omega) and rows PR..QT-1 their
+// secondary queries (x2, omega2); after the forward the Eq. 14 gradient of
+// every pair is formed in the tile from the two radiances, and the backward
+// runs on it directly (only the loss value leaves the CTA, as FP64 partials).
+template <class S, typename TT, bool TRAIN = false>
 __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ QueryParams p) {
+  static_assert(!TRAIN || S::BWD, "the training pass runs the backward");
+  constexpr int PR = QT / 2;            // pairs per tile (TRAIN)
+  constexpr int ROWS = TRAIN ? PR : QT;  // work units (pairs or queries) per tile
   constexpr int H = S::H, WP = S::WP, NH = S::NH;
   extern __shared__ __align__(16) float smem[];
   float* wsm = smem;
@@ -398,29 +424,45 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
   Grads<S> g;
   if (S::BWD) g.zero();
   int cur = -1;
+  double loss_acc = 0.0;
+  const float lscale = TRAIN ? (p.scaler ? p.scaler->scale : 1.f) : 1.f;
+  // the locate threads' row in a tile and the array it reads (TRAIN:
+  // primaries in rows 0..PR-1, secondaries in PR..QT-1)
+  const int qrow = threadIdx.x < QT ? (TRAIN ? int(threadIdx.x) % PR : int(threadIdx.x)) : ROWS;
+  const bool primary = !TRAIN || threadIdx.x < PR;
+  const float* xs = primary ? p.x : p.x2;
+  const float* ws = primary ? p.omega : p.omega2;
+  auto tile_query = [&](int64_t tile) {
+    const DevScene& sc = p.sc[scene_of_tile(p, tile)];
+    const int64_t gq = sc.q_begin + (tile - sc.tile_begin) * ROWS + qrow;
+    return load_query(xs, ws, gq, qrow < ROWS && gq < sc.q_end);
+  };
   const WorkRange wr = work_range(p.n_tiles, p.order);
-  const int qrow = threadIdx.x < QT ? int(threadIdx.x) : QT;  // locate threads only
-  QueryIn next = wr.begin < wr.end ? load_tile_query(p, wr.begin, qrow, QT) : QueryIn{};
+  QueryIn next = wr.begin < wr.end ? tile_query(wr.begin) : QueryIn{};
   for (int64_t tile = wr.begin; tile < wr.end; tile += wr.step) {
     const int s = scene_of_tile(p, tile);
     const DevScene& sc = p.sc[s];
     const QueryIn in = next;
-    if (tile + wr.step < wr.end) next = load_tile_query(p, tile + wr.step, qrow, QT);
+    if (tile + wr.step < wr.end) next = tile_query(tile + wr.step);
     __syncthreads();  // previous tile finished with shared memory
     if (s != cur) {
       if (S::BWD && cur >= 0) {
         g.flush(p.sc[cur]);
         g.zero();
+        if (TRAIN) flush_loss_f64(loss_acc, p.loss + cur, p.sc[cur].q_end - p.sc[cur].q_begin);
       }
       load_weights<S>(sc, wsm);
       tree = stage_tree(p, sc, tree_sm, S::TREE_NODES, threadIdx.x, NT);
       cur = s;
       __syncthreads();
     }
-    const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * QT;
-    const int nq = static_cast<int>(sc.q_end - q0 < QT ? sc.q_end - q0 : int64_t(QT));
+    const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * ROWS;
+    const int nq = static_cast<int>(sc.q_end - q0 < ROWS ? sc.q_end - q0 : int64_t(ROWS));
     float* h = S::BWD ? act_bwd(0) : buf[0];
-    locate_tile<S::KMAX>(p, sc, tree, in, q0, nq, node_sm, u_sm);
+    if (TRAIN)  // rows of both halves are valid for the tile's nq pairs
+      locate_tile<S::KMAX>(p, sc, tree, in, q0, threadIdx.x < PR ? nq : PR + nq, node_sm, u_sm);
+    else
+      locate_tile<S::KMAX>(p, sc, tree, in, q0, nq, node_sm, u_sm);
     __syncthreads();
     gather_tile<S::F, TT>(p, sc, tree, q0, nq, S::KMAX, node_sm, u_sm, h, LDA, 1);
     __syncthreads();
@@ -465,6 +507,11 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
           p.rgb[3 * gq + 1] = r1;
           p.rgb[3 * gq + 2] = r2;
         }
+      } else if (TRAIN) {  // radiances, turned into delta_L below
+        dL[q] = r0;
+        dL[LDA + q] = r1;
+        dL[2 * LDA + q] = r2;
+        dL[3 * LDA + q] = 0.f;
       } else {
         float d0 = 0.f, d1 = 0.f, d2 = 0.f;
         if (q < nq) {
@@ -479,6 +526,34 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
       }
     }
     if (!S::BWD) continue;
+    if (TRAIN) {
+      // Eq. 14 with the one-sample target of Eq. 3, per pair and channel:
+      // T = E + w L_s, r = (L_p - T) / (L_p + T + eps) (normaliser detached),
+      // d/dL_p = S 2 r / (3 n den), d/dL_s = -w d/dL_p (rhs_grad); then
+      // delta_L = d/dL * L (the derivative of exp is exp).
+      __syncthreads();
+      if (threadIdx.x < PR) {
+        const int r = threadIdx.x;
+        const int64_t gp = q0 + r;
+        const float n3 = 3.f * static_cast<float>(sc.q_end - sc.q_begin);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float Lp = dL[c * LDA + r], Ls = dL[c * LDA + PR + r];
+          float dp = 0.f, ds = 0.f;
+          if (r < nq) {
+            const float ww = p.w[3 * gp + c];
+            const float T = p.E[3 * gp + c] + ww * Ls;
+            const float den = Lp + T + p.eps;
+            const float rr = (Lp - T) / den;
+            loss_acc += double(rr) * double(rr);
+            dp = 2.f * lscale * rr / (n3 * den);
+            ds = p.rhs_grad ? -dp * ww : 0.f;
+          }
+          dL[c * LDA + r] = dp * Lp;
+          dL[c * LDA + PR + r] = ds * Ls;
+        }
+      }
+    }
 
     // ---- backward
     __syncthreads();
@@ -515,6 +590,7 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
     scatter_tile<S::KMAX, S::F>(p, sc, tree, node_sm, u_sm, act_bwd(0));
   }
   if (S::BWD && cur >= 0) g.flush(p.sc[cur]);
+  if (TRAIN && cur >= 0) flush_loss_f64(loss_acc, p.loss + cur, p.sc[cur].q_end - p.sc[cur].q_begin);
 }
 
 }  // namespace f32

@@ -7,9 +7,9 @@
 #include <algorithm>
 #include <cstring>
 
-#include "engine_f32.cuh"
+#include "engine_path.h"
 #include "gather.cuh"
-#include "launch_util.h"
+#include "launch_persistent.cuh"
 #include "octa_internal.h"
 #include "tc_path.h"
 
@@ -89,24 +89,6 @@ __global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ 
 }
 
 namespace {
-
-// Persistent grid: as many CTAs as fit on the device, never more than tiles.
-template <class Kern>
-int launch_persistent(Kern kernel, size_t smem, const QueryParams& p0, cudaStream_t stream,
-                      int threads, int cap, int order) {
-  if (p0.n_tiles == 0) return OCTA_OK;
-  int per_sm = 0;
-  int rc = launch_cache().get(reinterpret_cast<const void*>(kernel), smem, threads, 0, &per_sm);
-  if (rc) return rc;
-  per_sm = apply_cap(per_sm, cap);
-  QueryParams p = p0;
-  p.order = order == 1 ? 1 : 0;
-  const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * device_sm_count());
-  kernel<<<static_cast<unsigned>(grid), threads, smem, stream>>>(p);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(OCTA_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
-  return OCTA_OK;
-}
 
 bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
 
@@ -188,60 +170,6 @@ int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_qu
   return OCTA_OK;
 }
 
-namespace {
-
-// ---------------------------------------------------------------------------
-// FP32 engine dispatch
-// ---------------------------------------------------------------------------
-template <int F, int WP, int H, int NH, typename TT>
-int run_engine(const QueryParams& p, bool bwd, cudaStream_t stream) {
-  if (bwd) {
-    using S = f32::Shape<F, WP, H, NH, true>;
-    const octa_tuning tu = tuning_snapshot();
-    return launch_persistent(f32::engine_kernel<S, TT>, S::SMEM, p, stream, f32::NT,
-                             tu.engine_ctas_per_sm, tu.train_order);
-  }
-  using S = f32::Shape<F, WP, H, NH, false>;
-  const octa_tuning tu = tuning_snapshot();
-  return launch_persistent(f32::engine_kernel<S, TT>, S::SMEM, p, stream, f32::NT,
-                           tu.engine_ctas_per_sm, tu.fwd_order);
-}
-
-// Built shapes of the FP32 engine: (F, padded input width, hidden width,
-// hidden layers) x table type.  A scene set uses the smallest padded width
-// that holds every scene's K*F.
-int dispatch_engine(const octa_scene* scenes, int n_scenes, const QueryParams& p, bool bwd,
-                    cudaStream_t stream) {
-  const octa_scene& c0 = scenes[0];
-  const int F = c0.F, L = c0.n_layers, H = c0.widths[1], tdt = c0.table_dtype;
-  int need = 0;
-  for (int s = 0; s < n_scenes; ++s) {
-    const octa_scene& c = scenes[s];
-    if (c.F != F || c.n_layers != L || c.table_dtype != tdt || c.weight_dtype != OCTA_F32)
-      return fail(OCTA_EUNSUPPORTED, "scenes of one call must share F, depth of the MLP and dtypes");
-    for (int i = 1; i < L; ++i)
-      if (c.widths[i] != H)
-        return fail(OCTA_EUNSUPPORTED, "FP32 path: hidden widths must all equal %d", H);
-    need = std::max(need, c.widths[0]);
-  }
-  const int NH = L - 1;
-  const bool f16 = tdt == OCTA_F16;
-#define OCTA_TRY(F_, WP_, H_, NH_)                                                      \
-  if (F == F_ && H == H_ && NH == NH_ && need <= WP_)                                   \
-    return f16 ? run_engine<F_, WP_, H_, NH_, __half>(p, bwd, stream)                  \
-               : run_engine<F_, WP_, H_, NH_, float>(p, bwd, stream);
-  OCTA_TRY(4, 24, 32, 2)
-  OCTA_TRY(8, 56, 64, 2)
-  OCTA_TRY(8, 72, 64, 2)
-  OCTA_TRY(8, 80, 64, 2)
-  OCTA_TRY(8, 72, 64, 3)
-  OCTA_TRY(8, 80, 64, 3)
-#undef OCTA_TRY
-  return fail(OCTA_EUNSUPPORTED,
-              "FP32 path: no built shape for F=%d, K*F=%d, hidden %d x %d", F, need, NH, H);
-}
-
-}  // namespace
 }  // namespace octa
 
 using namespace octa;
@@ -334,7 +262,7 @@ extern "C" int octa_query_fwd(const octa_scene* scenes, int32_t n_scenes, const 
   p.status = status;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (scenes[0].weight_dtype == OCTA_BF16) return tc::query_fwd(scenes, n_scenes, p, st);
-  return dispatch_engine(scenes, n_scenes, p, false, st);
+  return f32::dispatch(scenes, n_scenes, p, f32::Mode::kForward, st);
 }
 
 extern "C" int octa_query_bwd(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
@@ -350,7 +278,7 @@ extern "C" int octa_query_bwd(const octa_scene* scenes, int32_t n_scenes, const 
   p.status = status;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (scenes[0].weight_dtype == OCTA_BF16) return tc::query_bwd(scenes, n_scenes, p, st);
-  return dispatch_engine(scenes, n_scenes, p, true, st);
+  return f32::dispatch(scenes, n_scenes, p, f32::Mode::kBackward, st);
 }
 
 extern "C" int octa_train_fused(const octa_scene* scenes, int32_t n_scenes, const octa_pairs* pairs,
@@ -371,9 +299,10 @@ extern "C" int octa_train_fused(const octa_scene* scenes, int32_t n_scenes, cons
   QueryParams p;
   int rc = build_query_params(scenes, n_scenes, &q, grads, p);
   if (rc) return rc;
+  const bool bf16 = scenes[0].weight_dtype == OCTA_BF16;
   for (int s = 0; s < n_scenes; ++s)
-    if (scenes[s].weight_dtype != OCTA_BF16)
-      return fail(OCTA_EUNSUPPORTED, "octa_train_fused needs BF16 decoders (tensor-core path)");
+    if ((scenes[s].weight_dtype == OCTA_BF16) != bf16)
+      return fail(OCTA_EUNSUPPORTED, "scenes of one call must share the decoder dtype");
   p.x2 = pairs->x2;
   p.omega2 = pairs->omega2;
   p.E = pairs->E;
@@ -386,7 +315,8 @@ extern "C" int octa_train_fused(const octa_scene* scenes, int32_t n_scenes, cons
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(loss_dev, 0, sizeof(double) * n_scenes, st);
   if (e != cudaSuccess) return fail(OCTA_ECUDA, "clearing loss_dev: %s", cudaGetErrorString(e));
-  return tc::train_fused(scenes, n_scenes, p, st);
+  return bf16 ? tc::train_fused(scenes, n_scenes, p, st)
+              : f32::dispatch(scenes, n_scenes, p, f32::Mode::kTrain, st);
 }
 
 extern "C" int octa_train_step_batched(const octa_scene* scenes, int32_t n_scenes,

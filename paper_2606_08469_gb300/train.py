@@ -72,8 +72,8 @@ class TrainStep:
         self.eps, self.rhs_grad = eps, rhs_grad
         self.groups = [g for s in scene_states for g in s.groups(lr_tables, lr_mlp)]
         self.grads = [(s.grad_t, s.grad_w) for s in scene_states]
-        # fused mode (BF16 decoders): one octa_train_fused launch replaces
-        # forward + loss + backward; the pair arrays are kept per role
+        # fused mode: one octa_train_fused launch replaces forward + loss +
+        # backward; the pair arrays are kept per role
         # persistent mode: the fused pass and Adam in one cooperative launch
         self.persistent = persistent
         self.fused = fused or persistent

@@ -113,13 +113,15 @@ def _update_err(new_gpu, new_ref, old):
     return np.linalg.norm((new_gpu - old) - d_ref) / np.linalg.norm(d_ref)
 
 
-def test_train_step_matches_oracle():
+@pytest.mark.parametrize("fused", [False, True])
+def test_train_step_matches_oracle(fused):
     """Two full FP32 steps (fwd, loss, bwd, Adam + scaler) of config-1 shapes
-    on 4096 pairs vs the oracle's step."""
+    on 4096 pairs vs the oracle's step; fused = the one-launch training pass
+    of the FP32 engine in place of forward + residual_loss + backward."""
     from paper_2606_08469_gb300 import api as A
     from paper_2606_08469_gb300 import workloads as WL
     cfg = I.CONFIGS[1]
-    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=4096)
+    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=4096, fused=fused)
     ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
     st = _oracle_state(tables, weights)
     scaler = O.LossScaler()
@@ -196,3 +198,52 @@ def test_train_step_graph_replay_equals_eager():
     torch.testing.assert_close(a.loss, b.loss, rtol=1e-5, atol=0)
     ta, tb = a.states[0].master_t, b.states[0].master_t
     assert torch.linalg.norm(ta - tb) <= 1e-3 * torch.linalg.norm(ta - t0)
+
+
+def _grad_err(a, b):
+    """Largest normwise difference of the table and weight gradients."""
+    e = 0.0
+    for sa, sb in zip(a.states, b.states):
+        for ga, gb in ((sa.grad_t, sb.grad_t), (sa.grad_w, sb.grad_w)):
+            e = max(e, (torch.linalg.norm(ga - gb) / torch.linalg.norm(gb)).item())
+    return e
+
+
+@pytest.mark.parametrize("rhs_grad", [True, False])
+def test_fused_f32_pass_matches_unfused(rhs_grad):
+    """The FP32 engine's fused training pass (64-pair tiles, in-tile Eq. 14
+    gradient) against octa_query_fwd + residual_loss + octa_query_bwd on a
+    ragged batch (4097 pairs: a one-pair tail tile).  Both run the same FP32
+    arithmetic; only the atomics' summation order differs."""
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[1]
+    a, _ = WL.train_step_for(cfg, n_pairs=4097, rhs_grad=rhs_grad)
+    b, _ = WL.train_step_for(cfg, n_pairs=4097, rhs_grad=rhs_grad, fused=True)
+    a.forward()
+    a.loss_and_grad()
+    a.backward()
+    b.fused_pass()
+    torch.cuda.synchronize()
+    torch.testing.assert_close(b.loss, a.loss, rtol=1e-6, atol=0)
+    err = _grad_err(b, a)
+    print("fused vs unfused FP32 gradients", err)
+    assert err <= 1e-5
+
+
+def test_fused_f32_pass_batched_scenes():
+    """Eight scenes of uneven size (FP32 copies of the batched workload's
+    parameters) in one fused FP32 launch vs the unfused path, per scene."""
+    from paper_2606_08469_gb300 import workloads as WL
+    counts = [3000, 1, 64, 65, 700, 129, 5, 2048]
+    a, _ = WL.batched_train_step(counts=counts, precision="f32")
+    b, _ = WL.batched_train_step(counts=counts, precision="f32", fused=True)
+    a.forward()
+    a.loss_and_grad()
+    a.backward()
+    b.fused_pass()
+    torch.cuda.synchronize()
+    la, lb = a.loss.cpu().numpy(), b.loss.cpu().numpy()
+    np.testing.assert_allclose(lb, la, rtol=1e-6, atol=0)
+    for sa, sb in zip(a.states, b.states):
+        for ga, gb in ((sa.grad_t, sb.grad_t), (sa.grad_w, sb.grad_w)):
+            assert (torch.linalg.norm(gb - ga) / torch.linalg.norm(ga)).item() <= 1e-5
