@@ -239,7 +239,7 @@ def inference_leg(dev, flush, stream, steps, peaks):
                 fn()
             from paper_2606_08469_gb300 import autotune as T
             if prec == "bf16":
-                best, rep = T.autotune(fn, {"fwd_ctas_per_sm": [2, 3, 4], "fwd_order": [1, 2]},
+                best, rep = T.autotune(fn, {"fwd_threads_per_query": [1, 2], "fwd_order": [1, 2]},
                                        f"config3-forward-{w_}x{h_}", reps=5)
             g = _graph(fn, stream)
             g.replay()
@@ -248,7 +248,8 @@ def inference_leg(dev, flush, stream, steps, peaks):
                          "timing": "CUDA-graph replay"}
             if prec == "bf16":
                 res[prec]["autotune"] = {"best": best, "best_ms": rep["best_ms"],
-                                         "default_ms": rep["default_ms"], "gain": rep["gain"]}
+                                         "default_ms": rep["default_ms"], "gain": rep["gain"],
+                                         "trials": rep["trials"]}
             T.set_tuning(None)
             if prec == "bf16":
                 peak = float(peaks.get("bf16_tflops", 1886.6))

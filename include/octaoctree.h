@@ -318,7 +318,10 @@ typedef struct octa_tuning {
                                   persistent CTA takes a contiguous chunk,
                                   2 = interleaved (default)                */
   int32_t train_order;         /* training / backward work items: as above */
-  int32_t reserved[3];
+  int32_t fwd_threads_per_query; /* tensor-core forward: 1 (default) or 2
+                                  threads per query (256-thread CTAs, each
+                                  thread gathering half of the levels)     */
+  int32_t reserved[2];
 } octa_tuning;
 int octa_set_tuning(const octa_tuning* t);   /* NULL restores the defaults */
 int octa_get_tuning(octa_tuning* t);

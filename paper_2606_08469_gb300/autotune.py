@@ -20,7 +20,8 @@ import torch
 
 from . import _lib as L
 
-KNOBS = ("fwd_ctas_per_sm", "encode_ctas_per_sm", "engine_ctas_per_sm", "fwd_order", "train_order")
+KNOBS = ("fwd_ctas_per_sm", "encode_ctas_per_sm", "engine_ctas_per_sm", "fwd_order", "train_order",
+         "fwd_threads_per_query")
 
 
 def get_tuning():

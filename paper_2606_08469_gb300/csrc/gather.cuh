@@ -14,91 +14,114 @@ __device__ __forceinline__ void fma_f16x2_f32(float& s0, float& s1, uint16_t w, 
       : "r"(t), "h"(w));
 }
 
-// One query per thread: fold omega (Eq. 4, 5, canonical binary32), walk the
-// query's path down the octree (Section 3.4) reading each node's record from
-// the staged tree (global memory when tree is nullptr), then gather KP
-// levels, two at a time (both levels' texel loads in flight together; one at
-// a time for 32-byte texels), handing the F blended features of level l to
-// store(l, v) (absent levels: zeros).  The cells of all levels come from one
-// integer per axis: with c = min(floor(x * 2^15), 2^15 - 1), level l's cell
-// is c >> (15 - l), since x * 2^l is exact in binary32 and the floor commutes
-// with the shift.  base_sm / u_sm (nullable, row stride nt) keep the map
-// base of every level (-1: absent) and the folded direction for a later
-// scatter; node_idx / texel_addr outputs of p are written for query gq when
-// requested.  F16W (FP16 tables only): blend with the four weights rounded
-// to FP16 and FP32 accumulation, for consumers that round the features to
-// BF16 anyway (the weight rounding, 2^-12 relative, is 8x below that of the
-// BF16 result).
-template <int F, typename TT, int KP, bool F16W = false, class Store>
+// One query per TPQ threads: each folds omega (Eq. 4, 5, canonical
+// binary32) and walks the query's path down the octree (Section 3.4),
+// reading node records from the staged tree (global memory when tree is
+// nullptr); thread par (0 <= par < TPQ) then gathers the levels l with
+// l % TPQ == par, WIN of its levels at a time (their texel loads in flight
+// together; one at a time for 32-byte texels), handing the F blended
+// features of level l to store(l, v) (absent levels: zeros).  The cells of
+// all levels come from one integer per axis: with c = min(floor(x * 2^15),
+// 2^15 - 1), level l's cell is c >> (15 - l), since x * 2^l is exact in
+// binary32 and the floor commutes with the shift.  Windows stop at the
+// deepest path of the warp (all lanes of a warp share par and call this
+// converged); deeper levels only get zero features.  base_sm / u_sm
+// (nullable, row stride nt) keep the map base of the thread's levels (-1:
+// absent) and the folded direction for a later scatter; node_idx (thread
+// par 0) and texel_addr (the level's thread) outputs of p are written for
+// query gq when requested.  F16W (FP16 tables only): blend with the four
+// weights rounded to FP16 and FP32 accumulation, for consumers that round
+// the features to BF16 anyway (the weight rounding, 2^-12 relative, is 8x
+// below that of the BF16 result).
+template <int F, typename TT, int KP, bool F16W = false, int TPQ = 1, class Store>
 __device__ __forceinline__ void locate_gather_query(const QueryParams& p, const DevScene& sc,
                                                     const int2* tree, const QueryIn& in,
-                                                    int64_t gq, bool valid, int* base_sm,
+                                                    int64_t gq, bool valid, int par, int* base_sm,
                                                     float* u_sm, int q, int nt, Store&& store) {
   static_assert(KP <= 16, "levels");
-  constexpr int WIN = TexelRaw<TT, F>::BYTES <= 16 ? 2 : 1;
+  static_assert(TPQ == 1 || TPQ == 2, "threads per query");
+  // two levels per window for 16-byte texels at one thread per query; one
+  // when the levels are split over two threads (register budget)
+  constexpr int WIN = (TexelRaw<TT, F>::BYTES <= 16 && TPQ == 1) ? 2 : 1;
+  constexpr int KO = (KP + TPQ - 1) / TPQ;  // level slots of one thread
   float ux, uy;
   octa_fold(in.w0, in.w1, in.w2, ux, uy);
   const int cx = min(static_cast<int>(clamp01(in.x0) * 32768.f), 32767);
   const int cy = min(static_cast<int>(clamp01(in.x1) * 32768.f), 32767);
   const int cz = min(static_cast<int>(clamp01(in.x2) * 32768.f), 32767);
-  int node[KP], mo[KP];
+  const bool out_nodes = p.node_idx != nullptr && valid && par == 0;
+  int mo[KO];  // map base of level o * TPQ + par, -1 when absent
+#pragma unroll
+  for (int o = 0; o < KO; ++o) mo[o] = -1;
+  int depth = 0;  // levels on the query's path (0 for an invalid row)
   int nd = valid ? 0 : -1;
 #pragma unroll
   for (int l = 0; l < KP; ++l) {
-    node[l] = nd;
-    mo[l] = -1;
-    int fc = -1;
-    if (nd >= 0) {
-      int2 rec;
-      if (tree) {
-        rec = tree[nd];
-      } else {
-        rec = make_int2(__ldg(sc.first_child + nd), __ldg(sc.map_offset + nd));
-        if (rec.x >= 0 && rec.x > sc.num_nodes - 8) {
-          if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
-          rec.x = -1;
-        }
+    if (nd < 0) break;
+    depth = l + 1;
+    if (out_nodes && l < p.kmax_out) p.node_idx[gq * p.kmax_out + l] = nd;
+    int2 rec;
+    if (tree) {
+      rec = tree[nd];
+    } else {
+      rec = make_int2(__ldg(sc.first_child + nd), __ldg(sc.map_offset + nd));
+      if (rec.x >= 0 && rec.x > sc.num_nodes - 8) {
+        if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
+        rec.x = -1;
       }
-      mo[l] = checked_map_base(p, sc, rec.y, sc.R[l]);
-      fc = rec.x;
     }
-    if (l + 1 < KP) {
-      const int sh = 14 - l;  // level l + 1
-      const int slot = ((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2);
-      nd = (l + 1 < sc.K && fc >= 0) ? fc + slot : -1;
-    }
+    if (l % TPQ == par) mo[l / TPQ] = checked_map_base(p, sc, rec.y, sc.R[l]);
+    if (l + 1 >= KP || l + 1 >= sc.K || rec.x < 0) break;
+    const int sh = 14 - l;  // level l + 1
+    nd = rec.x + (((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2));
   }
+  if (out_nodes)
+    for (int l = depth; l < p.kmax_out; ++l) p.node_idx[gq * p.kmax_out + l] = -1;
   if (base_sm) {
 #pragma unroll
-    for (int l = 0; l < KP; ++l) base_sm[l * nt + q] = mo[l];
+    for (int o = 0; o < KO; ++o)
+      if (o * TPQ + par < KP) base_sm[(o * TPQ + par) * nt + q] = mo[o];
     u_sm[q] = ux;
     u_sm[nt + q] = uy;
   }
-  if (p.node_idx && valid) {
+  const int dw = __reduce_max_sync(0xffffffffu, depth);
+  auto addr_out = [&](int l, int4 a) {
+    if (p.texel_addr && valid && l < p.kmax_out)
+      *reinterpret_cast<int4*>(p.texel_addr + (gq * p.kmax_out + l) * 4) = a;
+  };
 #pragma unroll
-    for (int l = 0; l < KP; ++l)
-      if (l < p.kmax_out) p.node_idx[gq * p.kmax_out + l] = node[l];
-    for (int l = KP; l < p.kmax_out; ++l) p.node_idx[gq * p.kmax_out + l] = -1;
-  }
+  for (int o0 = 0; o0 < KO; o0 += WIN) {
+    if (o0 * TPQ >= dw) {  // warp-uniform: no lane has these levels
 #pragma unroll
-  for (int l0 = 0; l0 < KP; l0 += WIN) {
+      for (int o = o0; o < KO; ++o) {
+        const int l = o * TPQ + par;
+        if (l >= KP) continue;
+        float v[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) v[f] = 0.f;
+        store(l, v);
+        addr_out(l, make_int4(-1, -1, -1, -1));
+      }
+      break;
+    }
     TexelRaw<TT, F> t[WIN][4];
     Footprint fp[WIN];
 #pragma unroll
     for (int j = 0; j < WIN; ++j) {
-      const int l = l0 + j;
-      if (l < KP && mo[l] >= 0) {
-        fp[j] = footprint(ux, uy, sc.R[l]);
+      const int o = o0 + j;
+      if (o < KO && mo[o] >= 0) {
+        fp[j] = footprint(ux, uy, sc.R[o * TPQ + par]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) t[j][k].load(sc.tables, int64_t(mo[l]) + fp[j].idx[k]);
+        for (int k = 0; k < 4; ++k) t[j][k].load(sc.tables, int64_t(mo[o]) + fp[j].idx[k]);
       }
     }
 #pragma unroll
     for (int j = 0; j < WIN; ++j) {
-      const int l = l0 + j;
-      if (l >= KP) continue;
+      const int o = o0 + j;
+      const int l = o * TPQ + par;
+      if (o >= KO || l >= KP) continue;
       float v[F];
-      if (mo[l] >= 0) {
+      if (mo[o] >= 0) {
         if constexpr (F16W && sizeof(TT) == 2) {
           uint16_t w16[4];
 #pragma unroll
@@ -126,16 +149,14 @@ __device__ __forceinline__ void locate_gather_query(const QueryParams& p, const 
         for (int f = 0; f < F; ++f) v[f] = 0.f;
       }
       store(l, v);
-      if (p.texel_addr && valid && l < p.kmax_out) {
-        int4 a = make_int4(-1, -1, -1, -1);
-        if (mo[l] >= 0)
-          a = make_int4(mo[l] + fp[j].idx[0], mo[l] + fp[j].idx[1], mo[l] + fp[j].idx[2],
-                        mo[l] + fp[j].idx[3]);
-        *reinterpret_cast<int4*>(p.texel_addr + (gq * p.kmax_out + l) * 4) = a;
-      }
+      int4 a = make_int4(-1, -1, -1, -1);
+      if (mo[o] >= 0)
+        a = make_int4(mo[o] + fp[j].idx[0], mo[o] + fp[j].idx[1], mo[o] + fp[j].idx[2],
+                      mo[o] + fp[j].idx[3]);
+      addr_out(l, a);
     }
   }
-  if (p.texel_addr && valid)
+  if (p.texel_addr && valid && par == 0)
     for (int l = KP; l < p.kmax_out; ++l)
       *reinterpret_cast<int4*>(p.texel_addr + (gq * p.kmax_out + l) * 4) = make_int4(-1, -1, -1, -1);
 }

@@ -75,14 +75,14 @@ struct Shape {
 
 // Weights of one scene into shared memory, canonical K-major, zero padded.
 template <class S>
-__device__ void load_weights_bf16(const DevScene& sc, uint8_t* smem) {
+__device__ void load_weights_bf16(const DevScene& sc, uint8_t* smem, int nthreads = NT) {
   const __nv_bfloat16* Wg = static_cast<const __nv_bfloat16*>(sc.weights);
 #pragma unroll 1
   for (int l = 0; l < S::NL; ++l) {
     const int K = S::kdim(l), N = S::ndim(l);
     const int in = sc.widths[l], out = sc.widths[l + 1];
     __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(smem + S::w_off(l));
-    for (int i = threadIdx.x; i < N * K; i += NT) {
+    for (int i = threadIdx.x; i < N * K; i += nthreads) {
       const int n = i / K, k = i % K;
       const __nv_bfloat16 v =
           (n < out && k < in) ? Wg[sc.w_offset[l] + n * in + k] : __float2bfloat16_rn(0.f);
@@ -93,14 +93,14 @@ __device__ void load_weights_bf16(const DevScene& sc, uint8_t* smem) {
 
 // Locate and gather of one query per thread into its row of the layer-0
 // operand tile (canonical K-major, one 16-byte store per level for F = 8).
-template <class S, typename TT>
+template <class S, typename TT, int TPQ = 1>
 __device__ __forceinline__ void locate_gather_bf16(const QueryParams& p, const DevScene& sc,
                                                    const int2* tree, const QueryIn& in, int64_t gq,
-                                                   bool valid, uint8_t* act, int* base_sm,
+                                                   bool valid, int par, uint8_t* act, int* base_sm,
                                                    float* u_sm, int q) {
   constexpr int F = S::F;
-  locate_gather_query<F, TT, S::KPAD, true>(
-      p, sc, tree, in, gq, valid, base_sm, u_sm, q, NT, [&](int l, const float (&v)[F]) {
+  locate_gather_query<F, TT, S::KPAD, true, TPQ>(
+      p, sc, tree, in, gq, valid, par, base_sm, u_sm, q, NT, [&](int l, const float (&v)[F]) {
         uint8_t* dst = act + kmajor_offset(q, l * F, S::WP);
         if constexpr (F == 8) {
           uint4 o;
@@ -132,8 +132,16 @@ __device__ __forceinline__ void issue_layer(int layer, uint32_t act_sa, uint32_t
   mma_commit(mbar);
 }
 
-template <class S, typename TT>
-__global__ void __launch_bounds__(NT, 4) fwd_kernel(const __grid_constant__ QueryParams p) {
+// Forward of 128-query tiles: TPQ threads per query (thread par of a row
+// gathers the levels l with l % TPQ == par and, in the epilogues, the
+// column range par of the hidden layer), all of them waiting on the MMAs of
+// the tile; persistent over tiles.
+template <class S, typename TT, int TPQ>
+__global__ void __launch_bounds__(NT * TPQ, 4)
+    fwd_kernel(const __grid_constant__ QueryParams p) {
+  constexpr int NTF = NT * TPQ;         // threads per CTA
+  constexpr int HC = S::H / TPQ;        // hidden columns per thread
+  static_assert(HC % 16 == 0, "epilogue column split");
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* act = smem + S::OFF_ACT;
   int2* tree_sm = S::TREE_NODES > 0 ? reinterpret_cast<int2*>(smem + S::OFF_TREE) : nullptr;
@@ -143,6 +151,7 @@ __global__ void __launch_bounds__(NT, 4) fwd_kernel(const __grid_constant__ Quer
   const uint32_t mbar = smem_addr(bar);
   const uint32_t act_sa = smem_addr(act), w_sa = smem_addr(smem);
   const int warp = threadIdx.x >> 5;
+  const int q = threadIdx.x % NT, par = threadIdx.x / NT;  // row, level parity
 
   if (threadIdx.x == 0) mbar_init(mbar, 1);
   if (warp == 0) {
@@ -153,29 +162,29 @@ __global__ void __launch_bounds__(NT, 4) fwd_kernel(const __grid_constant__ Quer
   __syncthreads();
   tc_fence_after_sync();
   const uint32_t tmem = *tslot;
-  const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  // warp w reads the tensor-memory lanes of its subpartition w % 4
+  const uint32_t lane_base = tmem + (static_cast<uint32_t>((warp % 4) * 32) << 16);
   uint32_t phase = 0;
   int cur = -1;
   bool failed = false;
 
   const WorkRange wr = work_range(p.n_tiles, p.order);
-  QueryIn next = wr.begin < wr.end ? load_tile_query(p, wr.begin, threadIdx.x, NT) : QueryIn{};
+  QueryIn next = wr.begin < wr.end ? load_tile_query(p, wr.begin, q, NT) : QueryIn{};
   for (int64_t tile = wr.begin; tile < wr.end && !failed; tile += wr.step) {
     const int s = scene_of_tile(p, tile);
     const DevScene& sc = p.sc[s];
     const QueryIn in = next;
-    if (tile + wr.step < wr.end) next = load_tile_query(p, tile + wr.step, threadIdx.x, NT);
+    if (tile + wr.step < wr.end) next = load_tile_query(p, tile + wr.step, q, NT);
     __syncthreads();
     if (s != cur) {
-      load_weights_bf16<S>(sc, smem);
-      tree = stage_tree(p, sc, tree_sm, S::TREE_NODES, threadIdx.x, NT);
+      load_weights_bf16<S>(sc, smem, NTF);
+      tree = stage_tree(p, sc, tree_sm, S::TREE_NODES, threadIdx.x, NTF);
       cur = s;
       __syncthreads();
     }
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * NT;
     const int nq = static_cast<int>(sc.q_end - q0 < NT ? sc.q_end - q0 : int64_t(NT));
-    locate_gather_bf16<S, TT>(p, sc, tree, in, q0 + threadIdx.x, int(threadIdx.x) < nq, act,
-                              nullptr, nullptr, threadIdx.x);
+    locate_gather_bf16<S, TT, TPQ>(p, sc, tree, in, q0 + q, q < nq, par, act, nullptr, nullptr, q);
     fence_proxy_async();
     __syncthreads();
 
@@ -190,36 +199,37 @@ __global__ void __launch_bounds__(NT, 4) fwd_kernel(const __grid_constant__ Quer
       }
       tc_fence_after_sync();
       if (layer < S::NL - 1) {
-        uint32_t r[S::H];
+        const int c0 = par * HC;
+        uint32_t r[HC];
 #pragma unroll
-        for (int c = 0; c < S::H; c += 16)
-          tmem_ld16(lane_base + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
+        for (int c = 0; c < HC; c += 16)
+          tmem_ld16(lane_base + c0 + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
         tmem_wait_ld();
-        const int q = threadIdx.x;
 #pragma unroll
-        for (int c = 0; c < S::H; c += 8) {
+        for (int c = 0; c < HC; c += 8) {
           uint4 o;
-          o.x = pack_bf16x2(fmaxf(__uint_as_float(r[c + 0]), 0.f), fmaxf(__uint_as_float(r[c + 1]), 0.f));
-          o.y = pack_bf16x2(fmaxf(__uint_as_float(r[c + 2]), 0.f), fmaxf(__uint_as_float(r[c + 3]), 0.f));
-          o.z = pack_bf16x2(fmaxf(__uint_as_float(r[c + 4]), 0.f), fmaxf(__uint_as_float(r[c + 5]), 0.f));
-          o.w = pack_bf16x2(fmaxf(__uint_as_float(r[c + 6]), 0.f), fmaxf(__uint_as_float(r[c + 7]), 0.f));
-          *reinterpret_cast<uint4*>(act + kmajor_offset(q, c, S::H)) = o;
+          o.x = pack_relu_bf16x2(r[c + 0], r[c + 1]);
+          o.y = pack_relu_bf16x2(r[c + 2], r[c + 3]);
+          o.z = pack_relu_bf16x2(r[c + 4], r[c + 5]);
+          o.w = pack_relu_bf16x2(r[c + 6], r[c + 7]);
+          *reinterpret_cast<uint4*>(act + kmajor_offset(q, c0 + c, S::H)) = o;
         }
         fence_proxy_async();
         tc_fence_before_sync();
         __syncthreads();
       } else {
-        uint32_t r[16];
-        tmem_ld16(lane_base, r);
-        tmem_wait_ld();
-        tc_fence_before_sync();
-        const int q = threadIdx.x;
-        if (q < nq) {
-          const int64_t gq = q0 + q;
-          p.rgb[3 * gq] = expf(__uint_as_float(r[0]));
-          p.rgb[3 * gq + 1] = expf(__uint_as_float(r[1]));
-          p.rgb[3 * gq + 2] = expf(__uint_as_float(r[2]));
+        if (par == 0) {
+          uint32_t r[16];
+          tmem_ld16(lane_base, r);
+          tmem_wait_ld();
+          if (q < nq) {
+            const int64_t gq = q0 + q;
+            p.rgb[3 * gq] = expf(__uint_as_float(r[0]));
+            p.rgb[3 * gq + 1] = expf(__uint_as_float(r[1]));
+            p.rgb[3 * gq + 2] = expf(__uint_as_float(r[2]));
+          }
         }
+        tc_fence_before_sync();
       }
     }
   }
@@ -650,8 +660,8 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
     const int nq = static_cast<int>(sc.q_end - q0 < ROWS ? sc.q_end - q0 : int64_t(ROWS));
     const bool valid = row < nq;
     const int64_t gq = q0 + row;
-    locate_gather_bf16<S, TT>(p, sc, tree, in, gq, valid, smem + S::off_act(g, 0), base_sm, u_sm,
-                              t);
+    locate_gather_bf16<S, TT>(p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), base_sm,
+                              u_sm, t);
     fence_proxy_async();
     named_sync(gbar, NT);
 
@@ -677,10 +687,10 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
 #pragma unroll
         for (int c = 0; c < H; c += 8) {
           uint4 o;
-          o.x = pack_bf16x2(fmaxf(__uint_as_float(r[c + 0]), 0.f), fmaxf(__uint_as_float(r[c + 1]), 0.f));
-          o.y = pack_bf16x2(fmaxf(__uint_as_float(r[c + 2]), 0.f), fmaxf(__uint_as_float(r[c + 3]), 0.f));
-          o.z = pack_bf16x2(fmaxf(__uint_as_float(r[c + 4]), 0.f), fmaxf(__uint_as_float(r[c + 5]), 0.f));
-          o.w = pack_bf16x2(fmaxf(__uint_as_float(r[c + 6]), 0.f), fmaxf(__uint_as_float(r[c + 7]), 0.f));
+          o.x = pack_relu_bf16x2(r[c + 0], r[c + 1]);
+          o.y = pack_relu_bf16x2(r[c + 2], r[c + 3]);
+          o.z = pack_relu_bf16x2(r[c + 4], r[c + 5]);
+          o.w = pack_relu_bf16x2(r[c + 6], r[c + 7]);
           *reinterpret_cast<uint4*>(dst + kmajor_offset(t, c, H)) = o;
         }
       } else {
@@ -859,23 +869,29 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
 
 namespace {
 
-template <class S, typename TT>
-int launch_fwd(const QueryParams& p, cudaStream_t stream) {
-  if (p.n_tiles == 0) return OCTA_OK;
-  auto kern = fwd_kernel<S, TT>;
+template <class S, typename TT, int TPQ>
+int launch_fwd_tpq(const QueryParams& p, const octa_tuning& tu, cudaStream_t stream) {
+  auto kern = fwd_kernel<S, TT, TPQ>;
   int per_sm = 0;
-  int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, NT,
+  int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, NT * TPQ,
                               static_cast<int>(S::TMEM_COLS), &per_sm);
   if (rc) return rc;
-  const octa_tuning tu = tuning_snapshot();
   per_sm = apply_cap(per_sm, tu.fwd_ctas_per_sm);
   QueryParams pp = p;
   pp.order = tu.fwd_order == 1 ? 1 : 0;
   const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * device_sm_count());
-  kern<<<static_cast<unsigned>(grid), NT, S::SMEM, stream>>>(pp);
+  kern<<<static_cast<unsigned>(grid), NT * TPQ, S::SMEM, stream>>>(pp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(OCTA_ECUDA, "tc fwd launch: %s", cudaGetErrorString(e));
   return OCTA_OK;
+}
+
+template <class S, typename TT>
+int launch_fwd(const QueryParams& p, cudaStream_t stream) {
+  if (p.n_tiles == 0) return OCTA_OK;
+  const octa_tuning tu = tuning_snapshot();
+  return tu.fwd_threads_per_query == 2 ? launch_fwd_tpq<S, TT, 2>(p, tu, stream)
+                                       : launch_fwd_tpq<S, TT, 1>(p, tu, stream);
 }
 
 template <class S, typename TT, bool TRAIN, bool PERSIST>

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ 
     const int rb = (row_bytes + 15) & ~15;  // staging row stride
     __syncthreads();
     locate_gather_query<F, TT, KP, sizeof(OT) == 2>(
-        p, sc, tree, in, q0 + q, q < nq, nullptr, nullptr, q, ENC_NT,
+        p, sc, tree, in, q0 + q, q < nq, 0, nullptr, nullptr, q, ENC_NT,
         [&](int l, const float (&v)[F]) {
           if (l >= sc.K) return;
           uint8_t* dst = stage + q * rb + l * F * int(sizeof(OT));
@@ -393,7 +393,8 @@ extern "C" int octa_set_tuning(const octa_tuning* t) {
     return OCTA_OK;
   }
   if (t->fwd_ctas_per_sm < 0 || t->encode_ctas_per_sm < 0 || t->engine_ctas_per_sm < 0 ||
-      t->fwd_order < 0 || t->fwd_order > 2 || t->train_order < 0 || t->train_order > 2)
+      t->fwd_order < 0 || t->fwd_order > 2 || t->train_order < 0 || t->train_order > 2 ||
+      t->fwd_threads_per_query < 0 || t->fwd_threads_per_query > 2)
     return fail(OCTA_EINVAL, "tuning values out of range");
   tuning() = *t;
   return OCTA_OK;

@@ -184,5 +184,13 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return r;
 }
 
+// pack_bf16x2 of (max(lo, 0), max(hi, 0)): the ReLU folded into the
+// conversion (the .relu form clamps negative results to +0).
+__device__ __forceinline__ uint32_t pack_relu_bf16x2(uint32_t lo, uint32_t hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(__uint_as_float(hi)), "f"(__uint_as_float(lo)));
+  return r;
+}
+
 }  // namespace tc
 }  // namespace octa

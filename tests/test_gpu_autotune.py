@@ -29,12 +29,18 @@ def test_forward_results_independent_of_knobs():
     sc, _ = WL.forward_scene(cfg)
     x, w = I.uniform_queries(3, 50000)
     X, W = WL.to_dev(x), WL.to_dev(w)
-    ref, _, _ = A.octa_query_fwd(sc, X, W)
+    ref, rn, ra = A.octa_query_fwd(sc, X, W, want_nodes=True, want_addr=True)
+    counts = [777, len(x) - 777]              # two scenes, a ragged first tile
+    ref2, _, _ = A.octa_query_fwd([sc, sc], X, W, counts)
     for setting in ({"fwd_ctas_per_sm": 1}, {"fwd_ctas_per_sm": 2, "fwd_order": 1},
-                    {"fwd_order": 1}):
+                    {"fwd_order": 1}, {"fwd_threads_per_query": 2},
+                    {"fwd_threads_per_query": 2, "fwd_order": 1, "fwd_ctas_per_sm": 3}):
         T.set_tuning(setting)
-        got, _, _ = A.octa_query_fwd(sc, X, W)
+        got, gn, ga = A.octa_query_fwd(sc, X, W, want_nodes=True, want_addr=True)
         torch.testing.assert_close(got, ref, rtol=0, atol=0)
+        assert torch.equal(gn, rn) and torch.equal(ga, ra)
+        got2, _, _ = A.octa_query_fwd([sc, sc], X, W, counts)
+        torch.testing.assert_close(got2, ref2, rtol=0, atol=0)
 
 
 def test_training_results_independent_of_order():
