@@ -23,6 +23,20 @@ namespace octa {
 namespace f32 {
 
 constexpr int NT = 256;        // threads per CTA
+
+// Two independent binary32 fused multiply-adds in one instruction (the
+// packed FP32 pair form of sm_100 and later): d.x = a.x*b.x + c.x, d.y =
+// a.y*b.y + c.y, each rounded once, exactly as two fmaf calls.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long A, B, Cc, D;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(B) : "f"(b.x), "f"(b.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(Cc) : "f"(c.x), "f"(c.y));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D) : "l"(A), "l"(B), "l"(Cc));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(D));
+  return d;
+}
 constexpr int LDA = QT + 4;    // activation row stride (floats)
 
 template <int F_, int WP_, int H_, int NH_, bool BWD_>
@@ -38,10 +52,18 @@ struct Shape {
   static constexpr int MAXW = WP > H ? WP : H;
   // BWD keeps h, a_1..a_NH and delta_L; FWD ping-pongs two buffers
   static constexpr int ACT_ROWS = BWD ? (WP + NH * H + 4) : 2 * MAXW;
-  static constexpr size_t TREE_OFF =
-      sizeof(float) * (size_t(WSM) + size_t(ACT_ROWS) * LDA) + sizeof(int) * KMAX * QT +
-      sizeof(float) * 2 * QT;
   static constexpr int TREE_NODES = 1280;  // staged octree, int2 per node
+  static constexpr size_t bytes_before_tree(int wdup) {
+    return sizeof(float) * (size_t(WSM) * wdup + size_t(ACT_ROWS) * LDA) +
+           sizeof(int) * KMAX * QT + sizeof(float) * 2 * QT;
+  }
+  // the backward kernels keep every weight twice in a row (w, w) where the
+  // shared memory allows (one 16-byte broadcast load then yields two ready
+  // operand pairs of ffma2); 227 KB per CTA less 1 KB of static memory
+  static constexpr int WDUP =
+      BWD && bytes_before_tree(2) + 8 * size_t(TREE_NODES) <= 232448 - 1024 ? 2 : 1;
+  static constexpr bool DUP = WDUP == 2;
+  static constexpr size_t TREE_OFF = bytes_before_tree(WDUP);
   static constexpr size_t SMEM = TREE_OFF + 8 * size_t(TREE_NODES);
 };
 
@@ -52,13 +74,42 @@ struct Shape {
 // Y[m][q] = relu(sum_k W[m][k] X[k][q]);  W row-major [M][KD].
 // Warp w owns rows [w*M/8, (w+1)*M/8) (weight reads are warp-uniform
 // broadcasts); lane owns queries [4 lane, 4 lane + 4).
-template <int M, int KD>
+template <int M, int KD, bool DUP = false>
 __device__ __forceinline__ void gemm_fwd_relu(const float* __restrict__ W,
                                               const float* __restrict__ X,
                                               float* __restrict__ Y) {
   constexpr int TM = M / 8;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = warp * TM, q0 = lane * 4;
+  if constexpr (DUP) {  // W holds each weight twice; two query columns per ffma2
+    float2 lo[TM], hi[TM];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) lo[i] = hi[i] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int k = 0; k < KD; k += 4) {
+      float4 x[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) x[c] = *reinterpret_cast<const float4*>(X + (k + c) * LDA + q0);
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        const float4* wr = reinterpret_cast<const float4*>(W + 2 * ((m0 + i) * KD + k));
+        const float4 wa = wr[0], wb = wr[1];
+        const float2 w2[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w),
+                              make_float2(wb.x, wb.y), make_float2(wb.z, wb.w)};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          lo[i] = ffma2(w2[c], make_float2(x[c].x, x[c].y), lo[i]);
+          hi[i] = ffma2(w2[c], make_float2(x[c].z, x[c].w), hi[i]);
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+      *reinterpret_cast<float4*>(Y + (m0 + i) * LDA + q0) =
+          make_float4(fmaxf(lo[i].x, 0.f), fmaxf(lo[i].y, 0.f), fmaxf(hi[i].x, 0.f),
+                      fmaxf(hi[i].y, 0.f));
+    return;
+  }
   float acc[TM][4];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -97,7 +148,7 @@ __device__ __forceinline__ void gemm_fwd_relu(const float* __restrict__ W,
 // row-major [M][KD].  Rows k come in chunks of 4; chunk c goes to warp c % 8.
 // With MASK the result overwrites the activation it is masked with (each
 // element is read and written by the same thread).
-template <int M, int KD, bool MASK>
+template <int M, int KD, bool MASK, bool DUP = false>
 __device__ __forceinline__ void gemm_bwd_data(const float* __restrict__ W,
                                               const float* __restrict__ D, float* Y) {
   constexpr int NCH = KD / 4;
@@ -105,6 +156,53 @@ __device__ __forceinline__ void gemm_bwd_data(const float* __restrict__ W,
   static_assert(KD % 4 == 0, "KD");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q0 = lane * 4;
+  if constexpr (DUP) {  // W holds each weight twice; two query columns per ffma2
+    float2 lo[CPW][4], hi[CPW][4];
+#pragma unroll
+    for (int j = 0; j < CPW; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) lo[j][r] = hi[j][r] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int m = 0; m < M; ++m) {
+      const float4 d = *reinterpret_cast<const float4*>(D + m * LDA + q0);
+      const float2 dlo = make_float2(d.x, d.y), dhi = make_float2(d.z, d.w);
+#pragma unroll
+      for (int j = 0; j < CPW; ++j) {
+        const int ch = warp + 8 * j;
+        if (ch < NCH) {
+          const float4* wr = reinterpret_cast<const float4*>(W + 2 * (m * KD + 4 * ch));
+          const float4 wa = wr[0], wb = wr[1];
+          const float2 w2[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w),
+                                make_float2(wb.x, wb.y), make_float2(wb.z, wb.w)};
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            lo[j][r] = ffma2(w2[r], dlo, lo[j][r]);
+            hi[j][r] = ffma2(w2[r], dhi, hi[j][r]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < CPW; ++j) {
+      const int ch = warp + 8 * j;
+      if (ch < NCH) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          float* y = Y + (4 * ch + r) * LDA + q0;
+          float4 o = make_float4(lo[j][r].x, lo[j][r].y, hi[j][r].x, hi[j][r].y);
+          if (MASK) {
+            const float4 a = *reinterpret_cast<const float4*>(y);
+            o.x = a.x > 0.f ? o.x : 0.f;
+            o.y = a.y > 0.f ? o.y : 0.f;
+            o.z = a.z > 0.f ? o.z : 0.f;
+            o.w = a.w > 0.f ? o.w : 0.f;
+          }
+          *reinterpret_cast<float4*>(y) = o;
+        }
+      }
+    }
+    return;
+  }
   float acc[CPW][4][4];
 #pragma unroll
   for (int j = 0; j < CPW; ++j)
@@ -165,10 +263,17 @@ struct WGrad {
 #pragma unroll
       for (int c = 0; c < TKW; ++c) a[r][c] = 0.f;
   }
-  // a[r][c] += sum_q D[m_r][q] X[k_c][q]
+  // a[r][c] += sum_q D[m_r][q] X[k_c][q]: the tile's sum is kept as two
+  // partial sums over even and odd queries (one ffma2 per query pair) and
+  // folded into a once per tile.
   __device__ __forceinline__ void accumulate(const float* __restrict__ D,
                                              const float* __restrict__ X) {
     const int mb = threadIdx.x & 15, kb = threadIdx.x >> 4;
+    float2 t[TMW][TKW];
+#pragma unroll
+    for (int r = 0; r < TMW; ++r)
+#pragma unroll
+      for (int c = 0; c < TKW; ++c) t[r][c] = make_float2(0.f, 0.f);
 #pragma unroll 2
     for (int q = 0; q < QT; q += 4) {
       float4 d[TMW], x[TKW];
@@ -183,14 +288,14 @@ struct WGrad {
       for (int r = 0; r < TMW; ++r)
 #pragma unroll
         for (int c = 0; c < TKW; ++c) {
-          float s = a[r][c];
-          s = fmaf(d[r].x, x[c].x, s);
-          s = fmaf(d[r].y, x[c].y, s);
-          s = fmaf(d[r].z, x[c].z, s);
-          s = fmaf(d[r].w, x[c].w, s);
-          a[r][c] = s;
+          t[r][c] = ffma2(make_float2(d[r].x, d[r].y), make_float2(x[c].x, x[c].y), t[r][c]);
+          t[r][c] = ffma2(make_float2(d[r].z, d[r].w), make_float2(x[c].z, x[c].w), t[r][c]);
         }
     }
+#pragma unroll
+    for (int r = 0; r < TMW; ++r)
+#pragma unroll
+      for (int c = 0; c < TKW; ++c) a[r][c] += t[r][c].x + t[r][c].y;
   }
   // d_weights[off + m * in + k] += a (k < in only: padded columns are zero)
   __device__ __forceinline__ void flush(float* dW, int in) const {
@@ -229,19 +334,31 @@ struct Grads {
   }
 };
 
+// Weight element i of the padded layout (W_0 [H][WP], W_1.. [H][H], W_L
+// [4][H] with row 3 zero), stored once or, for the backward kernels, twice
+// in a row.
+template <class S>
+__device__ __forceinline__ void put_weight(float* wsm, int i, float v) {
+  if constexpr (S::WDUP == 2)
+    reinterpret_cast<float2*>(wsm)[i] = make_float2(v, v);
+  else
+    wsm[i] = v;
+}
+
 template <class S>
 __device__ __forceinline__ void load_weights(const DevScene& sc, float* wsm) {
   const float* Wg = static_cast<const float*>(sc.weights);
   const int in0 = sc.widths[0];
   for (int i = threadIdx.x; i < S::H * S::WP; i += NT) {
     const int m = i / S::WP, k = i % S::WP;
-    wsm[i] = k < in0 ? Wg[sc.w_offset[0] + m * in0 + k] : 0.f;
+    put_weight<S>(wsm, i, k < in0 ? Wg[sc.w_offset[0] + m * in0 + k] : 0.f);
   }
-  float* dst = wsm + S::H * S::WP;
+  int dst = S::H * S::WP;
   for (int l = 1; l < S::NH; ++l, dst += S::H * S::H)
-    for (int i = threadIdx.x; i < S::H * S::H; i += NT) dst[i] = Wg[sc.w_offset[l] + i];
+    for (int i = threadIdx.x; i < S::H * S::H; i += NT)
+      put_weight<S>(wsm, dst + i, Wg[sc.w_offset[l] + i]);
   for (int i = threadIdx.x; i < 4 * S::H; i += NT)
-    dst[i] = i < 3 * S::H ? Wg[sc.w_offset[S::NH] + i] : 0.f;
+    put_weight<S>(wsm, dst + i, i < 3 * S::H ? Wg[sc.w_offset[S::NH] + i] : 0.f);
 }
 
 // Phase 1: fold omega and walk the tree (one thread per query), reading node
@@ -411,7 +528,8 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
   constexpr int H = S::H, WP = S::WP, NH = S::NH;
   extern __shared__ __align__(16) float smem[];
   float* wsm = smem;
-  float* act = wsm + S::WSM;
+  float* act = wsm + S::WSM * S::WDUP;
+  constexpr int WD = S::WDUP;  // weight element i sits at wsm[WD * i]
   int* node_sm = reinterpret_cast<int*>(act + S::ACT_ROWS * LDA);
   float* u_sm = reinterpret_cast<float*>(node_sm + S::KMAX * QT);
   int2* tree_sm = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(smem) + S::TREE_OFF);
@@ -468,14 +586,15 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
     __syncthreads();
 
     // ---- decoder forward (Eq. 13)
-    const float* Wl = wsm + H * WP + (NH - 1) * H * H;  // last layer [4][H]
+    const float* Wl = wsm + WD * (H * WP + (NH - 1) * H * H);  // last layer [4][H]
     float* a_last;
     if (S::BWD) {
-      gemm_fwd_relu<H, WP>(wsm, act_bwd(0), act_bwd(1));
+      gemm_fwd_relu<H, WP, S::DUP>(wsm, act_bwd(0), act_bwd(1));
       __syncthreads();
 #pragma unroll
       for (int i = 1; i < NH; ++i) {
-        gemm_fwd_relu<H, H>(wsm + H * WP + (i - 1) * H * H, act_bwd(i), act_bwd(i + 1));
+        gemm_fwd_relu<H, H, S::DUP>(wsm + WD * (H * WP + (i - 1) * H * H), act_bwd(i),
+                                  act_bwd(i + 1));
         __syncthreads();
       }
       a_last = act_bwd(NH);
@@ -495,9 +614,9 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
 #pragma unroll 8
       for (int k = 0; k < H; ++k) {
         const float a = a_last[k * LDA + q];
-        z0 = fmaf(Wl[k], a, z0);
-        z1 = fmaf(Wl[H + k], a, z1);
-        z2 = fmaf(Wl[2 * H + k], a, z2);
+        z0 = fmaf(Wl[WD * k], a, z0);
+        z1 = fmaf(Wl[WD * (H + k)], a, z1);
+        z2 = fmaf(Wl[WD * (2 * H + k)], a, z2);
       }
       const float r0 = expf(z0), r1 = expf(z1), r2 = expf(z2);
       const int64_t gq = q0 + q;
@@ -572,7 +691,7 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
       g.wl = sacc;
     }
     __syncthreads();
-    gemm_bwd_data<3, H, true>(Wl, dL, act_bwd(NH));  // delta_NH in place
+    gemm_bwd_data<3, H, true, S::DUP>(Wl, dL, act_bwd(NH));  // delta_NH in place
     __syncthreads();
 #pragma unroll
     for (int i = NH - 1; i >= 0; --i) {
@@ -582,9 +701,10 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
         g.wh[i - 1].accumulate(act_bwd(i + 1), act_bwd(i));
       __syncthreads();
       if (i == 0)
-        gemm_bwd_data<H, WP, false>(wsm, act_bwd(1), act_bwd(0));  // dh
+        gemm_bwd_data<H, WP, false, S::DUP>(wsm, act_bwd(1), act_bwd(0));  // dh
       else
-        gemm_bwd_data<H, H, true>(wsm + H * WP + (i - 1) * H * H, act_bwd(i + 1), act_bwd(i));
+        gemm_bwd_data<H, H, true, S::DUP>(wsm + WD * (H * WP + (i - 1) * H * H), act_bwd(i + 1),
+                                        act_bwd(i));
       __syncthreads();
     }
     scatter_tile<S::KMAX, S::F>(p, sc, tree, node_sm, u_sm, act_bwd(0));

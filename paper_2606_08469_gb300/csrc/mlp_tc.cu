@@ -469,8 +469,8 @@ __device__ __noinline__ void persistent_adam(const AdamBlock& a, int32_t* status
   }
   __shared__ float bc[2];
   if (threadIdx.x == 0) {
-    bc[0] = skip ? 1.f : static_cast<float>(1.0 - pow(double(a.beta1), double(t_new)));
-    bc[1] = skip ? 1.f : static_cast<float>(1.0 - pow(double(a.beta2), double(t_new)));
+    bc[0] = skip ? 1.f : adam_bias_correction(a.beta1, t_new);
+    bc[1] = skip ? 1.f : adam_bias_correction(a.beta2, t_new);
   }
   __syncthreads();
   const float bc1 = bc[0], bc2 = bc[1];

@@ -207,6 +207,13 @@ __device__ __forceinline__ Footprint footprint(float ux, float uy, int R) {
 
 __device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
 
+// Adam's bias correction 1 - beta^t (Kingma and Ba 2015) in binary32 without
+// cancellation: beta^t = exp(t log(1 - (1 - beta))), so 1 - beta^t =
+// -expm1(t log1p(-(1 - beta))); 1 - beta is exact for beta in [1/2, 1).
+__device__ __forceinline__ float adam_bias_correction(float beta, int64_t t) {
+  return -expm1f(static_cast<float>(t) * log1pf(-(1.f - beta)));
+}
+
 // Node records {first_child, map_offset} of scene sc in shared memory for the
 // walk of Section 3.4: one int2 per node, first_child validated here (a child
 // block running past the node array is reported and cut).  Returns the staged

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "octa_device.cuh"
 #include "octa_internal.h"
 
 namespace octa {
@@ -142,8 +143,8 @@ __global__ void __launch_bounds__(kThreads) adam_norm_kernel(const __grid_consta
         s->scale *= 2.f;
         s->good_steps = 0;
       }
-      p.bias_corr[0] = static_cast<float>(1.0 - pow(double(p.beta1), double(s->step)));
-      p.bias_corr[1] = static_cast<float>(1.0 - pow(double(p.beta2), double(s->step)));
+      p.bias_corr[0] = adam_bias_correction(p.beta1, s->step);
+      p.bias_corr[1] = adam_bias_correction(p.beta2, s->step);
     }
   }
 }
