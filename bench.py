@@ -367,6 +367,29 @@ def batched_leg(dev, flush, stream, steps):
                          "gain": rep["gain"]}}
 
 
+LEGS = ("bf16_vs_f32", "inference", "small_forward", "encode", "batched")
+
+
+def run_legs(args, names):
+    """Only the named extra legs on one GPU (profiling captures of their
+    kernels); prints one JSON object with those legs."""
+    import torch
+    from paper_2606_08469_gb300 import build
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    peaks, _ = _peaks()
+    steps = max(3, args.steps)
+    fns = {"bf16_vs_f32": lambda: bf16_vs_f32_leg(dev, flush, stream, steps, peaks),
+           "inference": lambda: inference_leg(dev, flush, stream, steps, peaks),
+           "small_forward": lambda: small_forward_leg(dev, flush, stream, steps),
+           "encode": lambda: encode_leg(dev, flush, stream, steps, peaks),
+           "batched": lambda: batched_leg(dev, flush, stream, steps)}
+    print(json.dumps({n: fns[n]() for n in names}), flush=True)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -565,11 +588,20 @@ def main():
                     help="skip the BF16-vs-FP32 and inference legs (profiling captures)")
     ap.add_argument("--pairs", type=int, default=262144,
                     help="training pairs per step (smaller values only for profiling captures)")
+    ap.add_argument("--only", default=None,
+                    help="comma-separated extra legs to run alone, without the headline "
+                         f"(profiling captures): {', '.join(LEGS)}")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        names = [n for n in args.only.split(",") if n]
+        bad = [n for n in names if n not in LEGS]
+        if bad:
+            ap.error(f"unknown legs {bad}; choose from {LEGS}")
+        run_legs(args, names)
     else:
         run_ours(args)
 
