@@ -369,6 +369,12 @@ def batched_leg(dev, flush, stream, steps):
 
 LEGS = ("bf16_vs_f32", "inference", "small_forward", "encode", "batched")
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
+# launch (262,144 pairs) of the FP32 fused training pass, from one ncu
+# capture of the current kernel; to be re-taken (or set to None) whenever the
+# kernel changes.
+F32_PASS_DRAM_BYTES = 22922752 + 0
+
 
 def run_legs(args, names):
     """Only the named extra legs on one GPU (profiling captures of their
@@ -529,7 +535,9 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": "f32 engine fused training pass "
                                                    "(fwd + Eq.14 gradient + bwd + scatter)",
                          "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "frac": round(achieved / peak, 4),
+                         "traffic": F32_PASS_DRAM_BYTES if args.pairs == 262144 else None,
+                         "algorithmic_bytes": 72 * pairs.n + tables.size * 4 + sum(w.size for w in weights) * 4,
                          "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {clk:.0f} MHz "
                                         f"({src} sm_max_mhz)",
                          "pass_ms": round(statistics.mean(bwd_ms), 4)},
