@@ -342,29 +342,40 @@ def small_forward_leg(dev, flush, stream, steps):
 
 def batched_leg(dev, flush, stream, steps):
     """Config [4]: 8 octrees (depth 4..9) with their own BF16 decoders and
-    log-uniform pair counts, forward + loss + backward + Adam of all scenes,
-    replayed from one captured CUDA graph."""
+    log-uniform pair counts; the whole training step of all scenes (forward,
+    Eq. 14 gradient, backward, Adam with the loss scaler) as one persistent
+    cooperative launch captured in a CUDA graph; beside it the same step as
+    the fused pass + adam_step (two launches, one graph).  The persistent
+    kernels' work order is autotuned on this workload."""
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
     from paper_2606_08469_gb300 import autotune as T
     counts = I.batched_pair_counts()
-    step, _ = WL.batched_train_step(device=dev, fused=True)
-    for _ in range(3):
-        step.step()
-    # autotune the work order of the persistent kernels on this workload
-    best, rep = T.autotune(step.step, {"train_order": [1, 2], "fwd_order": [1, 2]},
-                           "config4-batched-step", reps=5)
-    g = _graph(step.step, stream)
-    g.replay()
-    t = _timed(g.replay, steps, flush, stream)
-    T.set_tuning(None)
     nq = 2 * sum(counts)
-    return {"workload": f"config[4] batched training step: 8 scenes (depth 4..9), pairs per scene {counts}, "
-                        "BF16 decoders 8L-64-64-3, FP16 tables, fused training pass over all scenes + Adam, "
-                        "captured in one CUDA graph",
-            "ms_per_step": round(t, 4), "Mq/s": round(nq / t / 1e3, 1), "queries": nq,
-            "autotune": {"best": best, "best_ms": rep["best_ms"], "default_ms": rep["default_ms"],
-                         "gain": rep["gain"]}}
+    out = {"workload": f"config[4] batched training step: 8 scenes (depth 4..9), pairs per scene {counts}, "
+                       "BF16 decoders 8L-64-64-3, FP16 tables, forward + Eq.14 gradient + backward + Adam of "
+                       "all scenes", "queries": nq}
+    for mode in ("one_launch", "two_launch"):
+        step, _ = WL.batched_train_step(device=dev, fused=True, persistent=mode == "one_launch")
+        for _ in range(3):
+            step.step()
+        best, rep = T.autotune(step.step, {"train_order": [1, 2], "fwd_order": [1, 2]},
+                               f"config4-batched-{mode}", reps=5)
+        g = _graph(step.step, stream)
+        g.replay()
+        t = _timed(g.replay, steps, flush, stream)
+        T.set_tuning(None)
+        leg = {"ms_per_step": round(t, 4), "Mq/s": round(nq / t / 1e3, 1),
+               "launches_per_step": 1 if mode == "one_launch" else 3,
+               "autotune": {"best": best, "best_ms": rep["best_ms"], "default_ms": rep["default_ms"],
+                            "gain": rep["gain"]}}
+        if mode == "one_launch":
+            out.update(leg)
+            out["path"] = "octa_train_step_batched (one cooperative launch), CUDA-graph replay"
+        else:
+            out["two_launch"] = dict(leg, path="octa_train_fused + adam_step, CUDA-graph replay")
+        del step
+    return out
 
 
 LEGS = ("bf16_vs_f32", "inference", "small_forward", "encode", "batched")

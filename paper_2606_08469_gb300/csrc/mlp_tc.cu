@@ -330,23 +330,30 @@ struct BwdParams {
 };
 
 // Grid-wide barrier of a cooperative launch: arrival counter plus a
-// generation word.  The wait is bounded by timeout_ns (globaltimer); on
-// timeout it returns false in every thread of the CTA.
+// generation word, with acquire/release ordering at GPU scope.  Thread 0 of
+// each CTA arrives after a CTA barrier (so the CTA's earlier writes precede
+// its release); the last arrival resets the counter and releases the next
+// generation; the others acquire-load the generation until it changes.  The
+// wait is bounded by timeout_ns (globaltimer); on timeout it returns false
+// in every thread of the CTA.  (A volatile spin with full fences in its
+// place made the compiler slow the whole fused pass down by half.)
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned expected, uint64_t timeout_ns) {
   __shared__ int ok_sm;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vbar = bar;
-    const unsigned gen = vbar[1];
-    __threadfence();
+    unsigned gen, old;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
     int ok = 1;
-    if (atomicAdd(bar, 1u) == expected - 1) {
-      bar[0] = 0;
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
+    if (old == expected - 1) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
     } else {
       const uint64_t t0 = globaltimer_ns();
-      while (vbar[1] == gen) {
+      for (;;) {
+        unsigned g;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+        if (g != gen) break;
         if (globaltimer_ns() - t0 > timeout_ns) {
           ok = 0;
           break;
@@ -354,7 +361,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned expected, u
         __nanosleep(256);
       }
     }
-    __threadfence();
     ok_sm = ok;
   }
   __syncthreads();
@@ -391,7 +397,7 @@ __device__ __forceinline__ void adam_elem(float& pm, float& m, float& v, float g
 // taken identically in every CTA (same partials, same summation order) from
 // the scaler state read after the first barrier, Adam with bias correction over this
 // CTA's slice (16-byte accesses where a group allows them), gradients zeroed.
-__device__ __noinline__ void persistent_adam(const AdamBlock& a, int32_t* status) {
+__device__ __forceinline__ void persistent_adam(const AdamBlock& a, int32_t* status) {
   const uint64_t tmo = a.timeout_ns;
   const unsigned expected = gridDim.x + static_cast<unsigned>(a.extra_arrivals);
   if (!grid_barrier(a.bar, expected, tmo)) {  // every gradient is in
@@ -419,11 +425,15 @@ __device__ __noinline__ void persistent_adam(const AdamBlock& a, int32_t* status
     if (a.vec4[gi]) {
       const float4* g4 = reinterpret_cast<const float4*>(G.grad);
       const int64_t n4 = G.n / 4;
-#pragma unroll 4
-      for (int64_t i = first; i < n4; i += stride) {
-        const float4 g = __ldcg(g4 + i);
-        const double x = g.x * inv_s, y = g.y * inv_s, z = g.z * inv_s, w = g.w * inv_s;
-        acc += x * x + y * y + z * z + w * w;
+      constexpr int UN = 8;  // loads in flight per thread
+      for (int64_t i0 = first; i0 < n4; i0 += UN * stride) {
+        float4 g[UN];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+          const int64_t i = i0 + u * stride;
+          g[u] = i < n4 ? __ldcg(g4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        acc += sum_sq4_batch(g, inv_s);
       }
       done = n4 * 4;
     }
@@ -485,12 +495,9 @@ __device__ __noinline__ void persistent_adam(const AdamBlock& a, int32_t* status
       float4* Gr = reinterpret_cast<float4*>(G.grad);
       float4* M = reinterpret_cast<float4*>(G.m);
       float4* V = reinterpret_cast<float4*>(G.v);
-#pragma unroll 2
-      for (int64_t i = first; i < n4; i += stride) {
-        const float4 g = __ldcg(Gr + i);
-        Gr[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (skip) continue;
-        float4 pm = P[i], m = M[i], v = V[i];
+      // two elements (float4) per iteration, all their loads issued before
+      // any store, so each thread keeps eight 16-byte loads in flight
+      auto finish = [&](int64_t i, float4 g, float4 pm, float4 m, float4 v) {
         adam_elem(pm.x, m.x, v.x, g.x * inv_s, lr, b1, b2, eps, bc1, bc2);
         adam_elem(pm.y, m.y, v.y, g.y * inv_s, lr, b1, b2, eps, bc1, bc2);
         adam_elem(pm.z, m.z, v.z, g.z * inv_s, lr, b1, b2, eps, bc1, bc2);
@@ -508,6 +515,28 @@ __device__ __noinline__ void persistent_adam(const AdamBlock& a, int32_t* status
             w[0] = __floats2bfloat162_rn(pm.x, pm.y);
             w[1] = __floats2bfloat162_rn(pm.z, pm.w);
           }
+        }
+      };
+      // UB elements per iteration, all their loads issued before any store
+      constexpr int UB = 4;
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int64_t i0 = first; i0 < n4; i0 += UB * stride) {
+        float4 g[UB], pm[UB], m[UB], v[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+          const int64_t i = i0 + u * stride;
+          const bool in = i < n4;
+          g[u] = in ? __ldcg(Gr + i) : z4;
+          pm[u] = in && !skip ? P[i] : z4;
+          m[u] = in && !skip ? M[i] : z4;
+          v[u] = in && !skip ? V[i] : z4;
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+          const int64_t i = i0 + u * stride;
+          if (i >= n4) break;
+          Gr[i] = z4;
+          if (!skip) finish(i, g[u], pm[u], m[u], v[u]);
         }
       }
       done = n4 * 4;

@@ -207,6 +207,37 @@ __device__ __forceinline__ Footprint footprint(float ux, float uy, int R) {
 
 __device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
 
+// Sum of squares of four unscaled gradient components for the gradient-norm
+// reductions: the products and their sum in binary32 (GB300's FP64 rate is a
+// small fraction of its FP32 rate), widened to FP64 once per four elements
+// for the accumulation; recomputed in FP64 when the binary32 sum is not
+// finite, so a finite gradient never reads as an overflow and a non-finite
+// one stays non-finite.
+__device__ __forceinline__ double sum_sq4(float4 g, float inv_s) {
+  const float x = g.x * inv_s, y = g.y * inv_s, z = g.z * inv_s, w = g.w * inv_s;
+  const float s = fmaf(x, x, fmaf(y, y, fmaf(z, z, w * w)));
+  if (fabsf(s) <= 3.4028235e38f) return static_cast<double>(s);
+  return double(x) * x + double(y) * y + double(z) * z + double(w) * w;
+}
+
+// Binary32 sum of squares of n unscaled float4 gradients, widened to FP64
+// once; recomputed in FP64 when the binary32 sum is not finite (same
+// guarantees as sum_sq4).
+template <int N>
+__device__ __forceinline__ double sum_sq4_batch(const float4 (&g)[N], float inv_s) {
+  float s = 0.f;
+#pragma unroll
+  for (int u = 0; u < N; ++u) {
+    const float x = g[u].x * inv_s, y = g[u].y * inv_s, z = g[u].z * inv_s, w = g[u].w * inv_s;
+    s = fmaf(x, x, fmaf(y, y, fmaf(z, z, fmaf(w, w, s))));
+  }
+  if (fabsf(s) <= 3.4028235e38f) return static_cast<double>(s);
+  double d = 0.0;
+#pragma unroll
+  for (int u = 0; u < N; ++u) d += sum_sq4(g[u], inv_s);
+  return d;
+}
+
 // Adam's bias correction 1 - beta^t (Kingma and Ba 2015) in binary32 without
 // cancellation: beta^t = exp(t log(1 - (1 - beta))), so 1 - beta^t =
 // -expm1(t log1p(-(1 - beta))); 1 - beta is exact for beta in [1/2, 1).

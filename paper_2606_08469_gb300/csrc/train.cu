@@ -115,10 +115,27 @@ __global__ void __launch_bounds__(kThreads) adam_norm_kernel(const __grid_consta
   const float inv_s = 1.f / p.scaler->scale;
   double acc = 0.0;
   const int64_t stride = int64_t(gridDim.x) * kThreads;
+  const int64_t first = int64_t(blockIdx.x) * kThreads + threadIdx.x;
   for (int gi = 0; gi < p.n_groups; ++gi) {
     const float* __restrict__ g = p.g[gi].grad;
     const int64_t n = p.g[gi].n;
-    for (int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x; i < n; i += stride) {
+    int64_t done = 0;
+    if (p.vec4[gi]) {  // four elements per load, squared and summed in FP32
+      const float4* __restrict__ g4 = reinterpret_cast<const float4*>(g);
+      const int64_t n4 = n / 4;
+      constexpr int UN = 4;  // loads in flight per thread
+      for (int64_t i0 = first; i0 < n4; i0 += UN * stride) {
+        float4 gv[UN];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+          const int64_t i = i0 + u * stride;
+          gv[u] = i < n4 ? g4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        acc += sum_sq4_batch(gv, inv_s);
+      }
+      done = n4 * 4;
+    }
+    for (int64_t i = done + first; i < n; i += stride) {
       const double v = double(g[i] * inv_s);
       acc += v * v;
     }
@@ -177,27 +194,43 @@ __global__ void __launch_bounds__(kThreads) adam_update_kernel(const __grid_cons
       float4* Gr = reinterpret_cast<float4*>(G.grad);
       float4* M = reinterpret_cast<float4*>(G.m);
       float4* V = reinterpret_cast<float4*>(G.v);
-      for (int64_t i = first; i < n4; i += stride) {
-        float4 g = Gr[i];
-        Gr[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (skip) continue;
-        float4 pm = P[i], m = M[i], v = V[i];
-        adam_one(pm.x, m.x, v.x, g.x * inv_s, lr, b1, b2, eps, bc1, bc2);
-        adam_one(pm.y, m.y, v.y, g.y * inv_s, lr, b1, b2, eps, bc1, bc2);
-        adam_one(pm.z, m.z, v.z, g.z * inv_s, lr, b1, b2, eps, bc1, bc2);
-        adam_one(pm.w, m.w, v.w, g.w * inv_s, lr, b1, b2, eps, bc1, bc2);
-        P[i] = pm;
-        M[i] = m;
-        V[i] = v;
-        if (G.work) {
-          if (G.work_dtype == OCTA_F16) {
-            __half2* w = reinterpret_cast<__half2*>(G.work) + 2 * i;
-            w[0] = __floats2half2_rn(pm.x, pm.y);
-            w[1] = __floats2half2_rn(pm.z, pm.w);
-          } else {
-            __nv_bfloat162* w = reinterpret_cast<__nv_bfloat162*>(G.work) + 2 * i;
-            w[0] = __floats2bfloat162_rn(pm.x, pm.y);
-            w[1] = __floats2bfloat162_rn(pm.z, pm.w);
+      // UB elements per iteration, all their loads issued before any store
+      constexpr int UB = 2;
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int64_t i0 = first; i0 < n4; i0 += UB * stride) {
+        float4 g[UB], pm[UB], m[UB], v[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+          const int64_t i = i0 + u * stride;
+          const bool in = i < n4;
+          g[u] = in ? Gr[i] : z4;
+          pm[u] = in && !skip ? P[i] : z4;
+          m[u] = in && !skip ? M[i] : z4;
+          v[u] = in && !skip ? V[i] : z4;
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+          const int64_t i = i0 + u * stride;
+          if (i >= n4) break;
+          Gr[i] = z4;
+          if (skip) continue;
+          adam_one(pm[u].x, m[u].x, v[u].x, g[u].x * inv_s, lr, b1, b2, eps, bc1, bc2);
+          adam_one(pm[u].y, m[u].y, v[u].y, g[u].y * inv_s, lr, b1, b2, eps, bc1, bc2);
+          adam_one(pm[u].z, m[u].z, v[u].z, g[u].z * inv_s, lr, b1, b2, eps, bc1, bc2);
+          adam_one(pm[u].w, m[u].w, v[u].w, g[u].w * inv_s, lr, b1, b2, eps, bc1, bc2);
+          P[i] = pm[u];
+          M[i] = m[u];
+          V[i] = v[u];
+          if (G.work) {
+            if (G.work_dtype == OCTA_F16) {
+              __half2* w = reinterpret_cast<__half2*>(G.work) + 2 * i;
+              w[0] = __floats2half2_rn(pm[u].x, pm[u].y);
+              w[1] = __floats2half2_rn(pm[u].z, pm[u].w);
+            } else {
+              __nv_bfloat162* w = reinterpret_cast<__nv_bfloat162*>(G.work) + 2 * i;
+              w[0] = __floats2bfloat162_rn(pm[u].x, pm[u].y);
+              w[1] = __floats2bfloat162_rn(pm[u].z, pm[u].w);
+            }
           }
         }
       }
@@ -309,7 +342,7 @@ extern "C" int adam_step(const octa_param_group* groups, int32_t n_groups,
   p.bias_corr = reinterpret_cast<float*>(static_cast<char*>(workspace) + kPartialBytes + 16);
   const int blocks = static_cast<int>(std::max<int64_t>(
       1, std::min<int64_t>({(total / 4 + kThreads - 1) / kThreads, int64_t(kMaxBlocks),
-                            4LL * sm_count()})));
+                            6LL * sm_count()})));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   adam_norm_kernel<<<blocks, kThreads, 0, st>>>(p);
   rc = launched("adam_step (norm)");
