@@ -655,6 +655,7 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
         const int r = threadIdx.x;
         const int64_t gp = q0 + r;
         const float n3 = 3.f * static_cast<float>(sc.q_end - sc.q_begin);
+        float r2 = 0.f;  // the pair's three r^2 in binary32, one FP64 add
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const float Lp = dL[c * LDA + r], Ls = dL[c * LDA + PR + r];
@@ -664,13 +665,14 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
             const float T = p.E[3 * gp + c] + ww * Ls;
             const float den = Lp + T + p.eps;
             const float rr = (Lp - T) / den;
-            loss_acc += double(rr) * double(rr);
+            r2 = fmaf(rr, rr, r2);
             dp = 2.f * lscale * rr / (n3 * den);
             ds = p.rhs_grad ? -dp * ww : 0.f;
           }
           dL[c * LDA + r] = dp * Lp;
           dL[c * LDA + PR + r] = ds * Ls;
         }
+        loss_acc += double(r2);
       }
     }
 

@@ -750,17 +750,18 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
             const float Ls[3] = {xch[4 * row], xch[4 * row + 1], xch[4 * row + 2]};
             const float Lp[3] = {L0, L1, L2};
             const float n3 = 3.f * static_cast<float>(sc.q_end - sc.q_begin);
-            float dp[3], ds[3];
+            float dp[3], ds[3], r2 = 0.f;  // the pair's three r^2 in binary32
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
               const float ww = p.w[3 * gq + c];
               const float T = p.E[3 * gq + c] + ww * Ls[c];
               const float den = Lp[c] + T + p.eps;
               const float rr = (Lp[c] - T) / den;
-              loss_acc += double(rr) * double(rr);
+              r2 = fmaf(rr, rr, r2);
               dp[c] = 2.f * lscale * rr / (n3 * den);
               ds[c] = p.rhs_grad ? -dp[c] * ww : 0.f;
             }
+            loss_acc += double(r2);  // one FP64 add per pair
             d0 = dp[0];
             d1 = dp[1];
             d2 = dp[2];
