@@ -378,6 +378,26 @@ def batched_leg(dev, flush, stream, steps):
     return out
 
 
+def max_over_ranks(value, device=None):
+    """The largest value over all ranks of the initialised process group (a
+    replicated job's time is its slowest rank's); the value itself on one
+    rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, steps, total_ms):
+    """Whole-job throughput in millions of units per second: every rank
+    processes units_per_rank per step, the job takes the slowest rank's
+    total_ms for steps steps."""
+    return world * units_per_rank * steps / (total_ms / 1e3) / 1e6
+
+
 LEGS = ("bf16_vs_f32", "inference", "small_forward", "encode", "batched")
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
@@ -465,11 +485,7 @@ def run_ours(args):
         barrier()
     step_ms = [e[0].elapsed_time(e[1]) for e in ev]
     bwd_ms = [e[2].elapsed_time(e[3]) for e in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     launches = 3 * args.steps  # fused pass, adam norm, adam update
 
     # forward-only rate (same queries), L2 flushed between launches
@@ -483,6 +499,7 @@ def run_ours(args):
         fwd_ms.append((a, b))
     torch.cuda.synchronize(dev)
     fwd_ms = [a.elapsed_time(b) for a, b in fwd_ms]
+    fwd_mean = max_over_ranks(statistics.mean(fwd_ms), dev)
 
     # end to end through the public API: pinned host inputs copied in every
     # step, the loss read back every step
@@ -501,11 +518,7 @@ def run_ours(args):
         loss_host.copy_(step.loss, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dev)
 
     if rank == 0:
         peaks, src = _peaks()
@@ -522,7 +535,7 @@ def run_ours(args):
         peak = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
         out = {
             "metric": METRIC,
-            "value": round(world * n_q * args.steps / (total_ms / 1e3) / 1e6, 3),
+            "value": round(job_rate(n_q, world, args.steps, total_ms), 3),
             "unit": UNIT,
             "n_gpus": world,
             "steps": args.steps,
@@ -539,8 +552,8 @@ def run_ours(args):
                                    "gradient + bwd, then Adam)",
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": f"replicas x{world}"},
-            "fwd_only": {"value": round(world * n_q / (statistics.mean(fwd_ms) / 1e3) / 1e6, 3),
-                         "unit": UNIT, "ms": round(statistics.mean(fwd_ms), 4)},
+            "fwd_only": {"value": round(job_rate(n_q, world, 1, fwd_mean), 3),
+                         "unit": UNIT, "ms": round(fwd_mean, 4)},
             "loss": float(step.loss.item()),
             "grad_norm": float(sc.grad_norm),
             "roofline": {"bound": "alu", "kernel": "f32 engine fused training pass "
@@ -552,7 +565,7 @@ def run_ours(args):
                          "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {clk:.0f} MHz "
                                         f"({src} sm_max_mhz)",
                          "pass_ms": round(statistics.mean(bwd_ms), 4)},
-            "e2e": {"value": round(world * n_q * args.steps / (e2e_ms / 1e3) / 1e6, 3), "unit": UNIT,
+            "e2e": {"value": round(job_rate(n_q, world, args.steps, e2e_ms), 3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
             "gpu_launches": launches,
             "clocks": clocks.summary(),
