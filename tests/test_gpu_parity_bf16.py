@@ -428,6 +428,38 @@ def test_persistent_step_matches_fused_plus_adam(multi):
         assert torch.count_nonzero(sb_.grad_t).item() == 0
 
 
+def test_persistent_step_graph_replay_equals_eager():
+    """The one-launch step captured in a CUDA graph (how the batched
+    configuration is timed) and replayed three times agrees with three eager
+    one-launch steps on the same start state: losses, scaler and the table
+    update."""
+    from paper_2606_08469_gb300 import api as A
+    from paper_2606_08469_gb300 import workloads as WL
+    counts = [3000, 129, 20000, 64, 64, 64, 64, 64]
+    a, _ = WL.batched_train_step(counts=counts, persistent=True)
+    b, _ = WL.batched_train_step(counts=counts, persistent=True)
+    a.step()                                   # eager first step on both sides
+    b.step()
+    torch.cuda.synchronize()
+    t0 = [s.master_t.clone() for s in a.states]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            b.step()
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(3):
+        a.step()
+        graph.replay()
+    torch.cuda.synchronize()
+    torch.testing.assert_close(b.loss, a.loss, rtol=1e-5, atol=0)
+    sa, sb = A.read_scaler(a.scaler), A.read_scaler(b.scaler)
+    assert (sa.step, sa.skipped, sa.scale) == (sb.step, sb.skipped, sb.scale) and sa.step == 4
+    for sa_, sb_, t in zip(a.states, b.states, t0):
+        assert _update_err(sb_, sa_, t) <= 1e-3
+
+
 def test_persistent_step_barrier_timeout_reports_status():
     """A grid barrier that waits for one CTA more than the grid runs out
     after its 20 ms limit: the launch returns, OCTA_STATUS_TIMEOUT is set,
