@@ -112,7 +112,7 @@ __device__ __forceinline__ void locate_gather_query(const QueryParams& p, const 
       if (o < KO && mo[o] >= 0) {
         fp[j] = footprint(ux, uy, sc.R[o * TPQ + par]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) t[j][k].load(sc.tables, int64_t(mo[o]) + fp[j].idx[k]);
+        for (int k = 0; k < 4; ++k) t[j][k].load(sc.tables, uint32_t(mo[o] + fp[j].idx[k]));
       }
     }
 #pragma unroll

@@ -265,10 +265,11 @@ __device__ __forceinline__ const int2* stage_tree(const QueryParams& p, const De
 }
 
 // Map base of a level-l node, or -1 (reported) when its R x R map runs past
-// the table.
+// the table (32-bit unsigned arithmetic: num_texels < 2^31 and R <= 4096, so
+// a negative base wraps to a value beyond any table and fails the test).
 __device__ __forceinline__ int checked_map_base(const QueryParams& p, const DevScene& sc, int mo,
                                                 int R) {
-  if (mo < 0 || int64_t(mo) + int64_t(R) * R > sc.num_texels) {
+  if (static_cast<uint32_t>(mo) + static_cast<uint32_t>(R * R) > static_cast<uint32_t>(sc.num_texels)) {
     if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_MAP);
     return -1;
   }
@@ -334,7 +335,9 @@ struct TexelRaw {
   static_assert(BYTES == 8 || BYTES == 16 || BYTES == 32, "texel size");
   static constexpr int WORDS = BYTES / 4;
   uint32_t w[WORDS];
-  __device__ __forceinline__ void load(const void* t, int64_t texel) {
+  // texel index < 2^31 (the table limit): 32-bit index arithmetic, one
+  // widening multiply-add for the address
+  __device__ __forceinline__ void load(const void* t, uint32_t texel) {
     if constexpr (BYTES == 8) {
       const uint2 a = __ldg(reinterpret_cast<const uint2*>(t) + texel);
       w[0] = a.x;
