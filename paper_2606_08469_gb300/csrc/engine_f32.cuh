@@ -48,7 +48,6 @@ struct Shape {
   static_assert(H % 16 == 0, "hidden width");
   // weights: W_0 [H][WP], W_1..W_{NH-1} [H][H], W_L [4][H] (row 3 zero)
   static constexpr int WSM = H * WP + (NH - 1) * H * H + 4 * H;
-  static constexpr int ACT0 = 0;
   static constexpr int MAXW = WP > H ? WP : H;
   // BWD keeps h, a_1..a_NH and delta_L; FWD ping-pongs two buffers
   static constexpr int ACT_ROWS = BWD ? (WP + NH * H + 4) : 2 * MAXW;
