@@ -85,6 +85,23 @@ class TrainStep:
             self.Sw = torch.cat([-p["omega2"] for p in pairs]).to(dev).contiguous()
             self.Ecat, self.wcat = cat("E"), cat("w")
 
+    PAIR_INPUTS = ("Px", "Pw", "Sx", "Sw", "Ecat", "wcat")
+
+    def pair_inputs(self):
+        """The device arrays the fused pass reads (primaries, secondaries,
+        emission, BSDF weight), by name."""
+        return {k: getattr(self, k) for k in self.PAIR_INPUTS}
+
+    def set_pair_inputs(self, arrays):
+        """Point the fused pass at other device arrays of the same shapes
+        (double-buffered input copies)."""
+        for k in self.PAIR_INPUTS:
+            t = arrays[k]
+            cur = getattr(self, k)
+            if t.shape != cur.shape or t.dtype != cur.dtype or t.device != cur.device:
+                raise ValueError(f"{k}: expected {tuple(cur.shape)} {cur.dtype} on {cur.device}")
+            setattr(self, k, t)
+
     def forward(self, stream=None):
         api.octa_query_fwd(self.scenes, self.X, self.Om, self.counts, rgb=self.rgb, stream=stream)
 

@@ -247,3 +247,24 @@ def test_fused_f32_pass_batched_scenes():
     for sa, sb in zip(a.states, b.states):
         for ga, gb in ((sa.grad_t, sb.grad_t), (sa.grad_w, sb.grad_w)):
             assert (torch.linalg.norm(gb - ga) / torch.linalg.norm(ga)).item() <= 1e-5
+
+
+def test_pair_inputs_can_be_swapped():
+    """A fused step reading a copy of its pair arrays (set_pair_inputs, as the
+    double-buffered end-to-end loop does) gives the same loss and gradients;
+    arrays of another shape are refused."""
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[1]
+    a, _ = WL.train_step_for(cfg, n_pairs=1000, fused=True)
+    b, _ = WL.train_step_for(cfg, n_pairs=1000, fused=True)
+    copies = {k: t.clone() for k, t in b.pair_inputs().items()}
+    b.set_pair_inputs(copies)
+    a.fused_pass()
+    b.fused_pass()
+    torch.cuda.synchronize()
+    torch.testing.assert_close(b.loss, a.loss, rtol=1e-6, atol=0)
+    assert torch.linalg.norm(b.states[0].grad_t - a.states[0].grad_t) <= \
+        1e-5 * torch.linalg.norm(a.states[0].grad_t)
+    bad = dict(copies, Px=copies["Px"][:-1])
+    with pytest.raises(ValueError):
+        b.set_pair_inputs(bad)
