@@ -235,6 +235,11 @@ typedef struct octa_pairs {
   const float* w;              /* device [n][3] f_r |n.omega'| / p(omega')  */
   int64_t n;
   int64_t scene_start[OCTA_MAX_SCENES + 1];
+  /* pairs that scene s's loss is a mean over (0: its own count).  A data-
+   * parallel rank holding a shard of a batch passes the whole batch's count,
+   * so that its loss and gradients are its shard's share of the batch's and
+   * the ranks' sums are the batch's.                                        */
+  int64_t norm_pairs[OCTA_MAX_SCENES];
 } octa_pairs;
 
 /* octa_train_fused -- octa_query_fwd + residual_loss + octa_query_bwd of a
@@ -246,9 +251,11 @@ typedef struct octa_pairs {
  * normaliser is detached), and back-propagates into the tables and the
  * decoder (gradients of S * loss, S = scaler->scale or 1; accumulated into
  * grads as in octa_query_bwd).  loss_dev: device double [n_scenes], set to
- * each scene's mean r^2 over its pairs and channels (zeroed by the call;
- * FP64 partials, summed with atomics).  OCTA_EUNSUPPORTED for scenes of
- * mixed decoder dtypes.                                                    */
+ * each scene's sum of r^2 over its pairs and channels divided by 3 x
+ * (pairs->norm_pairs[s], or the scene's own pair count when 0) (zeroed by
+ * the call; FP64 partials, summed with atomics); the gradients are of that
+ * same loss.  OCTA_EUNSUPPORTED for scenes of mixed decoder dtypes;
+ * OCTA_EINVAL for a negative norm_pairs.                                  */
 int octa_train_fused(const octa_scene* scenes, int32_t n_scenes, const octa_pairs* pairs,
                      float eps, int32_t rhs_grad, const octa_scaler* scaler, double* loss_dev,
                      const octa_scene_grads* grads, int32_t* status, void* stream);

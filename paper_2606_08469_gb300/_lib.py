@@ -71,6 +71,7 @@ class octa_queries(C.Structure):
         ("omega", C.c_void_p),
         ("n", C.c_int64),
         ("scene_start", C.c_int64 * (OCTA_MAX_SCENES + 1)),
+        ("norm_pairs", C.c_int64 * OCTA_MAX_SCENES),
     ]
 
 
@@ -88,6 +89,7 @@ class octa_pairs(C.Structure):
         ("w", C.c_void_p),
         ("n", C.c_int64),
         ("scene_start", C.c_int64 * (OCTA_MAX_SCENES + 1)),
+        ("norm_pairs", C.c_int64 * OCTA_MAX_SCENES),
     ]
 
 

@@ -220,8 +220,14 @@ def octa_query_bwd(scenes, x, omega, d_rgb, grads, counts=None, status=None, str
                                   _stream(stream)), "octa_query_bwd")
 
 
+def _set_norm(pr, norm_pairs):
+    if norm_pairs is not None:
+        for i, m in enumerate(norm_pairs):
+            pr.norm_pairs[i] = int(m)
+
+
 def octa_train_fused(scenes, x, omega, x2, omega2, E, w, grads, loss_out, counts=None, eps=1e-2,
-                     rhs_grad=True, scaler=None, status=None, stream=None):
+                     rhs_grad=True, scaler=None, status=None, stream=None, norm_pairs=None):
     """Fused forward + Eq. 14 loss + backward over training pairs (BF16
     decoders on the tensor cores, FP32 decoders on the FP32 engine)."""
     arr, ns = _scene_array(scenes)
@@ -237,6 +243,7 @@ def octa_train_fused(scenes, x, omega, x2, omega2, E, w, grads, loss_out, counts
     for i, c in enumerate(counts):
         acc += c
         pr.scene_start[i + 1] = acc
+    _set_norm(pr, norm_pairs)
     L.check(_lib().octa_train_fused(arr, ns, C.byref(pr), C.c_float(eps), int(bool(rhs_grad)),
                                     _ptr(scaler), _ptr(loss_out), g, _ptr(status), _stream(stream)),
             "octa_train_fused")
@@ -245,7 +252,7 @@ def octa_train_fused(scenes, x, omega, x2, omega2, E, w, grads, loss_out, counts
 def octa_train_step_batched(scenes, x, omega, x2, omega2, E, w, grads, groups, loss_out, scaler, ws,
                             counts=None, eps=1e-2, rhs_grad=True, beta1=0.9, beta2=0.999,
                             adam_eps=1e-8, timeout_ns=0, extra_arrivals=0, status=None,
-                            stream=None):
+                            stream=None, norm_pairs=None):
     """Whole training step (fused pass + Adam) in one persistent launch."""
     arr, ns = _scene_array(scenes)
     g = (L.octa_scene_grads * ns)(*[L.octa_scene_grads(dt.data_ptr(), dw.data_ptr())
@@ -261,6 +268,7 @@ def octa_train_step_batched(scenes, x, omega, x2, omega2, E, w, grads, groups, l
     for i, c in enumerate(counts):
         acc += c
         pr.scene_start[i + 1] = acc
+    _set_norm(pr, norm_pairs)
     opt = L.octa_step_options(timeout_ns, extra_arrivals, 0)
     cfg = L.octa_adam_cfg(beta1, beta2, adam_eps)
     L.check(_lib().octa_train_step_batched(arr, ns, C.byref(pr), g, pg, len(groups), C.c_float(eps),

@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
       if (S::BWD && cur >= 0) {
         g.flush(p.sc[cur]);
         g.zero();
-        if (TRAIN) flush_loss_f64(loss_acc, p.loss + cur, p.sc[cur].q_end - p.sc[cur].q_begin);
+        if (TRAIN) flush_loss_f64(loss_acc, p.loss + cur, p.sc[cur].norm_pairs);
       }
       load_weights<S>(sc, wsm);
       tree = stage_tree(p, sc, tree_sm, S::TREE_NODES, threadIdx.x, NT);
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
       if (threadIdx.x < PR) {
         const int r = threadIdx.x;
         const int64_t gp = q0 + r;
-        const float n3 = 3.f * static_cast<float>(sc.q_end - sc.q_begin);
+        const float n3 = 3.f * static_cast<float>(sc.norm_pairs);
         float r2 = 0.f;  // the pair's three r^2 in binary32, one FP64 add
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -711,7 +711,7 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
     scatter_tile<S::KMAX, S::F>(p, sc, tree, node_sm, u_sm, act_bwd(0));
   }
   if (S::BWD && cur >= 0) g.flush(p.sc[cur]);
-  if (TRAIN && cur >= 0) flush_loss_f64(loss_acc, p.loss + cur, p.sc[cur].q_end - p.sc[cur].q_begin);
+  if (TRAIN && cur >= 0) flush_loss_f64(loss_acc, p.loss + cur, p.sc[cur].norm_pairs);
 }
 
 }  // namespace f32

@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
       if (cur >= 0) {
         flush_weight_grads<S>(p.sc[cur], lane_addr, g == 0 ? 0 : NL / 2, g == 0 ? NL / 2 : NL);
         tc_fence_before_sync();
-        if (TRAIN) flush_loss(loss_acc, p.loss + cur, p.sc[cur].q_end - p.sc[cur].q_begin);
+        if (TRAIN) flush_loss(loss_acc, p.loss + cur, p.sc[cur].norm_pairs);
       }
       for (int l = 0; l < S::NL; ++l) {  // weights, all 256 threads
         const int K = S::kdim(l), N = S::ndim(l);
@@ -749,7 +749,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
           if (primary && valid) {
             const float Ls[3] = {xch[4 * row], xch[4 * row + 1], xch[4 * row + 2]};
             const float Lp[3] = {L0, L1, L2};
-            const float n3 = 3.f * static_cast<float>(sc.q_end - sc.q_begin);
+            const float n3 = 3.f * static_cast<float>(sc.norm_pairs);
             float dp[3], ds[3], r2 = 0.f;  // the pair's three r^2 in binary32
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -887,7 +887,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   tc_fence_after_sync();
   if (cur >= 0 && !abort_flag) {
     flush_weight_grads<S>(p.sc[cur], lane_addr, g == 0 ? 0 : NL / 2, g == 0 ? NL / 2 : NL);
-    if (TRAIN) flush_loss(loss_acc, p.loss + cur, p.sc[cur].q_end - p.sc[cur].q_begin);
+    if (TRAIN) flush_loss(loss_acc, p.loss + cur, p.sc[cur].norm_pairs);
   }
   tc_fence_before_sync();
   __syncthreads();

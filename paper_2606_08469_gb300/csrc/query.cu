@@ -161,6 +161,7 @@ int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_qu
     }
     d.q_begin = q->scene_start[s];
     d.q_end = q->scene_start[s + 1];
+    d.norm_pairs = d.q_end - d.q_begin;
     d.tile_begin = tiles;
     tiles += (d.q_end - d.q_begin + QT - 1) / QT;
   }
@@ -170,6 +171,16 @@ int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_qu
   return OCTA_OK;
 }
 
+
+// Loss normalisation of the training passes: pairs->norm_pairs[s] when set.
+int apply_norm_pairs(const octa_pairs* pairs, int n_scenes, QueryParams& p) {
+  for (int s = 0; s < n_scenes; ++s) {
+    const int64_t m = pairs->norm_pairs[s];
+    if (m < 0) return fail(OCTA_EINVAL, "norm_pairs[%d] < 0", s);
+    if (m > 0) p.sc[s].norm_pairs = m;
+  }
+  return OCTA_OK;
+}
 }  // namespace octa
 
 using namespace octa;
@@ -303,6 +314,8 @@ extern "C" int octa_train_fused(const octa_scene* scenes, int32_t n_scenes, cons
   for (int s = 0; s < n_scenes; ++s)
     if ((scenes[s].weight_dtype == OCTA_BF16) != bf16)
       return fail(OCTA_EUNSUPPORTED, "scenes of one call must share the decoder dtype");
+  rc = apply_norm_pairs(pairs, n_scenes, p);
+  if (rc) return rc;
   p.x2 = pairs->x2;
   p.omega2 = pairs->omega2;
   p.E = pairs->E;
@@ -348,6 +361,8 @@ extern "C" int octa_train_step_batched(const octa_scene* scenes, int32_t n_scene
   for (int s = 0; s < n_scenes; ++s)
     if (scenes[s].weight_dtype != OCTA_BF16)
       return fail(OCTA_EUNSUPPORTED, "the persistent step needs BF16 decoders");
+  rc = apply_norm_pairs(pairs, n_scenes, p);
+  if (rc) return rc;
   p.x2 = pairs->x2;
   p.omega2 = pairs->omega2;
   p.E = pairs->E;

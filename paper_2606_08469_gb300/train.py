@@ -46,7 +46,7 @@ class TrainStep:
 
     def __init__(self, scene_states, pairs, eps=1e-2, rhs_grad=True, lr_tables=1e-2, lr_mlp=1e-3,
                  scale=2.0 ** 15, growth_interval=2000, device="cuda", fused=False,
-                 persistent=False):
+                 persistent=False, norm_pairs=None):
         dev = torch.device(device)
         self.states = scene_states
         self.scenes = [s.scene for s in scene_states]
@@ -77,6 +77,11 @@ class TrainStep:
         # persistent mode: the fused pass and Adam in one cooperative launch
         self.persistent = persistent
         self.fused = fused or persistent
+        # pairs each scene's loss is a mean over (None: the scene's own pairs;
+        # a data-parallel shard passes the whole batch's counts)
+        self.norm_pairs = None if norm_pairs is None else [int(m) for m in norm_pairs]
+        if self.norm_pairs is not None and not self.fused:
+            raise ValueError("norm_pairs needs the fused training pass")
         if persistent:
             self.ws_step = api.workspace(L.OCTA_OP_STEP, 0, device=dev)
         if self.fused:
@@ -124,14 +129,14 @@ class TrainStep:
     def fused_pass(self, stream=None):
         api.octa_train_fused(self.scenes, self.Px, self.Pw, self.Sx, self.Sw, self.Ecat, self.wcat,
                              self.grads, self.loss, self.n, self.eps, self.rhs_grad, self.scaler,
-                             stream=stream)
+                             stream=stream, norm_pairs=self.norm_pairs)
 
     def persistent_step(self, stream=None, status=None, timeout_ns=0, extra_arrivals=0):
         api.octa_train_step_batched(self.scenes, self.Px, self.Pw, self.Sx, self.Sw, self.Ecat,
                                     self.wcat, self.grads, self.groups, self.loss, self.scaler,
                                     self.ws_step, self.n, self.eps, self.rhs_grad,
                                     timeout_ns=timeout_ns, extra_arrivals=extra_arrivals,
-                                    status=status, stream=stream)
+                                    status=status, stream=stream, norm_pairs=self.norm_pairs)
 
     def step(self, stream=None):
         if self.persistent:

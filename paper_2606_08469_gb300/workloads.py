@@ -49,6 +49,24 @@ def train_step_for(cfg, n_pairs=None, device="cuda", precision=None, **kw):
     return TrainStep([st], [pairs_on_device(pairs, device)], **kw), (tree, tables, weights, pairs)
 
 
+def data_parallel_train_step(cfg, rank, world, n_pairs=None, device="cuda", precision=None, **kw):
+    """Fused TrainStep of a data-parallel rank: the batch's seeded pairs,
+    this rank's contiguous shard, the loss normalised by the whole batch."""
+    from .dataparallel import shard_range
+    tree, tables, weights = host_params(cfg)
+    tdt, wdt = table_dtype(cfg), weight_dtype(cfg)
+    if precision == "f32":
+        tdt = wdt = torch.float32
+    st = SceneState(tree, tables, weights, tdt, wdt, device)
+    n = cfg.n if n_pairs is None else n_pairs
+    pairs = I.training_pairs(cfg.seed("queries"), n)
+    b, e = shard_range(n, rank, world)
+    shard = {k: torch.from_numpy(np.ascontiguousarray(getattr(pairs, k)[b:e])).to(device)
+             for k in ("x", "omega", "x2", "omega2", "E", "w")}
+    step = TrainStep([st], [shard], fused=True, norm_pairs=[n], device=device, **kw)
+    return step, (tree, tables, weights, pairs, (b, e))
+
+
 def batched_train_step(device="cuda", counts=None, precision=None, **kw):
     """TrainStep of the batched workload (8 scenes); counts overrides the
     per-scene pair counts."""
