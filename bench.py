@@ -297,6 +297,62 @@ def encode_leg(dev, flush, stream, steps, peaks):
                          "per_query": f"24 B in + {2 * W} B out, table {table_bytes} B once"}}
 
 
+def encode_stress_leg(dev, flush, stream, steps, peaks):
+    """The encoding alone with tables larger than L2: 2^20 uniform random
+    queries (x in the unit cube, omega on the sphere) on a dense octree of
+    depth 6 (299,593 nodes; R 64,64,32,32,16,16,8; F = 8 FP16: 26.8 M
+    texels, 430 MB), BF16 features out: every query has all 7 levels, and
+    the fine levels' texels are spread over the whole table, the gather's
+    HBM-bound regime.  Algorithmic bytes: 24 B in and 112 B out per query
+    plus every distinct texel the launch touches once (counted from the
+    kernel's texel addresses in an untimed run)."""
+    import torch
+    from paper_2606_08469_gb300 import api
+    from paper_2606_08469_gb300 import inputs as I
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[3]
+    R = [64, 64, 32, 32, 16, 16, 8]
+    tree = api.octree_build(cfg.seed("tree"), 6, 1.0, R)
+    g = torch.Generator(device=dev)
+    g.manual_seed(cfg.seed("tables"))
+    T = (torch.randn((tree.num_texels, cfg.F), generator=g, device=dev) * cfg.sigma).half()
+    mlp = I.make_mlp(cfg.seed("mlp"), [tree.num_levels * cfg.F, 64, 64, 3])
+    sc = api.Scene(tree, T, [WL.to_dev(w, dev).to(torch.bfloat16) for w in mlp], device=dev)
+    x, om = I.uniform_queries(cfg.seed("queries"), 1 << 20)
+    X, Om = WL.to_dev(x, dev), WL.to_dev(om, dev)
+    W = tree.num_levels * cfg.F
+    _, _, addr = api.octa_encode(sc, X, Om, feat_dtype=torch.bfloat16, want_addr=True)
+    distinct = int(torch.unique(addr[addr >= 0]).numel())
+    del addr
+    feat = torch.empty((len(x), W), dtype=torch.bfloat16, device=dev)
+    q = api._queries(X, Om, None)
+    arr, ns = api._scene_array(sc)
+    lib = api._lib()
+
+    def fn():
+        api.L.check(lib.octa_encode(arr, ns, api.C.byref(q), api._ptr(feat), api.L.OCTA_BF16, W,
+                                    None, None, None, api._stream()), "octa_encode")
+    for _ in range(3):
+        fn()
+    t = _timed(fn, steps, flush, stream)
+    texel_bytes = cfg.F * 2
+    alg = len(x) * (24 + 2 * W) + distinct * texel_bytes
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    ach = alg / (t / 1e3) / 1e9
+    out = {"workload": f"{len(x)} uniform random queries on a dense depth-6 octree ({tree.num_nodes} "
+                       f"nodes, {tree.num_texels} texels x {cfg.F} FP16 = "
+                       f"{tree.num_texels * texel_bytes >> 20} MiB > L2), encoding alone, {W} BF16 "
+                       "features out",
+           "ms": round(t, 4), "Mq/s": round(len(x) / t / 1e3, 1),
+           "distinct_texels": distinct,
+           "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(ach / peak, 4), "algorithmic_bytes": alg,
+                        "per_launch": f"{len(x)} x (24 B in + {2 * W} B out) + {distinct} distinct "
+                                      f"texels x {texel_bytes} B"}}
+    del T, sc
+    return out
+
+
 def _graph(fn, stream):
     """Capture fn (already run eagerly) into a CUDA graph on a side stream."""
     import torch
@@ -398,7 +454,7 @@ def job_rate(units_per_rank, world, steps, total_ms):
     return world * units_per_rank * steps / (total_ms / 1e3) / 1e6
 
 
-LEGS = ("bf16_vs_f32", "inference", "small_forward", "encode", "batched")
+LEGS = ("bf16_vs_f32", "inference", "small_forward", "encode", "encode_stress", "batched")
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
 # launch (262,144 pairs) of the FP32 fused training pass, from one ncu
@@ -423,6 +479,7 @@ def run_legs(args, names):
            "inference": lambda: inference_leg(dev, flush, stream, steps, peaks),
            "small_forward": lambda: small_forward_leg(dev, flush, stream, steps),
            "encode": lambda: encode_leg(dev, flush, stream, steps, peaks),
+           "encode_stress": lambda: encode_stress_leg(dev, flush, stream, steps, peaks),
            "batched": lambda: batched_leg(dev, flush, stream, steps)}
     print(json.dumps({n: fns[n]() for n in names}), flush=True)
 
@@ -597,6 +654,8 @@ def run_ours(args):
             out["inference"] = inference_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
             out["small_forward"] = small_forward_leg(dev, flush, stream, max(5, args.steps // 2))
             out["encode"] = encode_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
+            out["encode_stress"] = encode_stress_leg(dev, flush, stream, max(5, args.steps // 2),
+                                                     peaks)
             out["batched"] = batched_leg(dev, flush, stream, max(5, args.steps // 2))
         out["cpu_baseline"] = cpu_baseline() if not args.no_cpu else None
         print(json.dumps(out), flush=True)
