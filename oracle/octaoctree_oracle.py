@@ -17,6 +17,8 @@ fusion or reordering of its own:
   wrap              octahedral edge wrap of the texel grid (Section 3.3: the
                     map is continuous across the unfolded edges)
   encode_features   Eq. 10 in the single-cell, bilinear form + Eq. 11
+  encode_features_full  Eq. 10 as printed (eight cells, renormalised
+                    trilinear weights) with Eq. 6 (barycentric on vertex maps)
   mlp_forward       Eq. 13 (decoder; ReLU hidden layers, exp output)
   residual_loss     Eq. 14 with the Monte-Carlo target of Eq. 3 (M = 1)
   query_backward    derivative of Eq. 13, then of Eq. 10/11 w.r.t. the table
@@ -334,6 +336,195 @@ def encode_features(tree, tables, x, omega):
             h[:, l * F:(l + 1) * F] += wgt[:, l, k][:, None] * T[np.where(present, a, 0)] \
                 * present[:, None]
     return Encoding(h, node, addr, wgt)
+
+
+# ---------------------------------------------------------------------------
+# The full query (Section 3.3 Eq. 6, Section 3.4 Eq. 10): directional
+# features stored at map vertices and interpolated barycentrically over the
+# triangle holding the direction, spatial features blended over the eight
+# cells around x with trilinear weights renormalised over non-empty cells
+# ---------------------------------------------------------------------------
+
+def node_of_cell(tree, l, c):
+    """Node of the level-l cell c [N][3] (descent from the root along the
+    cell's ancestors), -1 where the cell is not in the octree."""
+    c = np.asarray(c, dtype=np.int64)
+    node = np.zeros(len(c), dtype=np.int64)
+    for m in range(1, l + 1):
+        b = (c >> (l - m)) & 1
+        slot = b[:, 0] | (b[:, 1] << 1) | (b[:, 2] << 2)
+        fc = np.where(node >= 0, tree.first_child[np.maximum(node, 0)], -1)
+        node = np.where(fc >= 0, fc + slot, -1)
+    return node
+
+
+def node_of_cell_bruteforce(tree, l, c):
+    """Scan every node of level l for cell c."""
+    c = np.asarray(c, dtype=np.int64)
+    out = np.full(len(c), -1, dtype=np.int64)
+    for n in range(tree.level_node_start[l], tree.level_node_start[l + 1]):
+        out[np.all(c == tree.node_coord[n], axis=1)] = n
+    return out
+
+
+def neighbour_cells(x, l):
+    """The eight level-l cells whose centres surround x, with standard
+    trilinear weights.  Cell k has centre (k + 1/2) / 2^l; the lower corner
+    cell is c0 = floor(p) with p = x 2^l - 1/2 evaluated in binary32 (the
+    integer decision is taken in the kernel's precision; x 2^l is exact and
+    the subtraction rounds at most once), the weights in FP64.  Neighbour j
+    is c0 + (j & 1, (j >> 1) & 1, j >> 2).  Returns cells [N][8][3], weights
+    [N][8] and whether each cell lies inside the cube [N][8]."""
+    f = np.float32
+    n = 1 << l
+    x32 = np.clip(np.asarray(x, dtype=np.float32), f(0.0), f(1.0))
+    p32 = x32 * f(n) - f(0.5)
+    c0 = np.floor(p32).astype(np.int64)
+    t = x32.astype(np.float64) * n - 0.5 - c0
+    cells = np.zeros((len(x32), 8, 3), dtype=np.int64)
+    wts = np.ones((len(x32), 8))
+    for j in range(8):
+        d = np.array([j & 1, (j >> 1) & 1, j >> 2])
+        cells[:, j, :] = c0 + d
+        for a in range(3):
+            wts[:, j] *= t[:, a] if d[a] else 1.0 - t[:, a]
+    inside = np.all((cells >= 0) & (cells < n), axis=2)
+    return cells, wts, inside
+
+
+def vertex_cell_f32(omega32, V):
+    """Grid cell (i0, j0) of a V x V vertex map (N = V - 1 cells a side;
+    vertex (i, j) sits at uv = (i, j) / N) and the fractions (fx, fy) inside
+    it, from the canonical binary32 sequence of corner_base_f32 with
+    p = uv * N (no half-texel shift): (i0, j0) = min(floor(p), N - 1),
+    f = p - (i0, j0) (exact in binary32).  Returns float32 fractions."""
+    f = np.float32
+    w = np.asarray(omega32, dtype=np.float32)
+    ax, ay, az = np.abs(w[:, 0]), np.abs(w[:, 1]), np.abs(w[:, 2])
+    s = (ax + ay) + az
+    ux = w[:, 0] / s
+    uy = w[:, 1] / s
+    one = f(1.0)
+    sx = np.where(ux >= 0, one, -one).astype(np.float32)
+    sy = np.where(uy >= 0, one, -one).astype(np.float32)
+    fx = (one - np.abs(uy)) * sx
+    fy = (one - np.abs(ux)) * sy
+    lower = w[:, 2] < 0
+    ux = np.where(lower, fx, ux).astype(np.float32)
+    uy = np.where(lower, fy, uy).astype(np.float32)
+    N = V - 1
+    px = (ux * f(0.5) + f(0.5)) * f(N)
+    py = (uy * f(0.5) + f(0.5)) * f(N)
+    i0 = np.minimum(np.floor(px), f(N - 1)).astype(np.int64)
+    j0 = np.minimum(np.floor(py), f(N - 1)).astype(np.int64)
+    return i0, j0, (px - i0.astype(np.float32)).astype(np.float32), \
+        (py - j0.astype(np.float32)).astype(np.float32)
+
+
+def vertex_triangle(i0, j0, fx32, fy32, N):
+    """The right isosceles triangle of cell (i0, j0) that holds the point,
+    as three vertex offsets (da, db) and the barycentric weights (Eq. 6).
+
+    Each octahedron face is tiled by the unfolded triangles, so a cell is
+    split along the diagonal parallel to its quadrant's face boundary
+    (|u_x| + |u_y| = 1): the anti-diagonal in the quadrants u_x, u_y of equal
+    sign, the main diagonal otherwise (N is even, so no cell straddles a
+    quadrant edge).  The side of the diagonal is decided in binary32
+    (fx + fy <= 1, or fy <= fx); the weights are those of the FP64
+    fractions.  Returns offsets [N][3][2] and weights [N][3]."""
+    f = np.float32
+    fx = fx32.astype(np.float64)
+    fy = fy32.astype(np.float64)
+    anti = (i0 >= N // 2) == (j0 >= N // 2)
+    a_lower = (fx32 + fy32) <= f(1.0)
+    m_lower = fy32 <= fx32
+    n = len(i0)
+    off = np.zeros((n, 3, 2), dtype=np.int64)
+    b = np.zeros((n, 3))
+    # anti-diagonal, lower-left triangle (0,0) (1,0) (0,1)
+    m = anti & a_lower
+    off[m] = [[0, 0], [1, 0], [0, 1]]
+    b[m] = np.stack([1 - fx - fy, fx, fy], 1)[m]
+    # anti-diagonal, upper-right triangle (1,1) (1,0) (0,1)
+    m = anti & ~a_lower
+    off[m] = [[1, 1], [1, 0], [0, 1]]
+    b[m] = np.stack([fx + fy - 1, 1 - fy, 1 - fx], 1)[m]
+    # main diagonal, lower-right triangle (0,0) (1,0) (1,1)
+    m = ~anti & m_lower
+    off[m] = [[0, 0], [1, 0], [1, 1]]
+    b[m] = np.stack([1 - fx, fx - fy, fy], 1)[m]
+    # main diagonal, upper-left triangle (0,0) (0,1) (1,1)
+    m = ~anti & ~m_lower
+    off[m] = [[0, 0], [0, 1], [1, 1]]
+    b[m] = np.stack([1 - fy, fy - fx, fx], 1)[m]
+    return off, b
+
+
+def canonical_vertex(i, j, N):
+    """One representative of each vertex of the unfolded map.  The fold of
+    Eq. 5 glues each edge of the square to itself mirrored: (N, j) and
+    (0, j) are the directions of (N, N - j) and (0, N - j), (i, N) and (i, 0)
+    those of (N - i, N) and (N - i, 0); the four corners are one direction.
+    Vertical edges first (j -> min(j, N - j)), then horizontal edges
+    (i -> min(i, N - i))."""
+    i = np.asarray(i, dtype=np.int64).copy()
+    j = np.asarray(j, dtype=np.int64).copy()
+    v = (i == 0) | (i == N)
+    j = np.where(v, np.minimum(j, N - j), j)
+    hz = (j == 0) | (j == N)
+    i = np.where(hz, np.minimum(i, N - i), i)
+    return i, j
+
+
+@dataclass
+class FullEncoding:
+    h: np.ndarray           # [N][K*F] FP64 features (Eq. 10 with Eq. 6, Eq. 11)
+    addr: np.ndarray        # [N][K][8][3] vertex entry per neighbour and vertex (-1 absent)
+    weight: np.ndarray      # [N][K][8][3] FP64 weight (renormalised trilinear x barycentric)
+
+
+def encode_features_full(tree, tables, x, omega):
+    """Eq. 10 as printed, with the directional lookup of Eq. 6 and without
+    the disparity shift (the same direction omega in all eight cells): per
+    level, the eight cells around x with trilinear weights renormalised over
+    the cells present in the octree (a level with none gives zero features),
+    in each the barycentric blend of the three vertex features of the
+    triangle holding omega on that node's V x V vertex map (V = R[l]);
+    levels concatenated (Eq. 11).  Vertex (i, j) of a node's map is entry
+    map_offset + j V + i of the canonical representative (i, j)."""
+    T = np.asarray(tables, dtype=np.float64)
+    F = T.shape[1]
+    n = len(x)
+    K = tree.num_levels
+    om32 = np.asarray(omega, dtype=np.float32)
+    h = np.zeros((n, K * F))
+    addr = np.full((n, K, 8, 3), -1, dtype=np.int64)
+    wgt = np.zeros((n, K, 8, 3))
+    for l in range(K):
+        V = int(tree.R[l])
+        N = V - 1
+        cells, wsp, inside = neighbour_cells(x, l)
+        nodes = np.full((n, 8), -1, dtype=np.int64)
+        for j in range(8):
+            nodes[:, j] = np.where(inside[:, j], node_of_cell(tree, l, np.clip(cells[:, j], 0, None)), -1)
+        present = nodes >= 0
+        wp = np.where(present, wsp, 0.0)
+        den = wp.sum(axis=1)
+        wn = np.where(den[:, None] > 0, wp / np.where(den > 0, den, 1.0)[:, None], 0.0)
+        i0, j0, fx32, fy32 = vertex_cell_f32(om32, V)
+        off, b = vertex_triangle(i0, j0, fx32, fy32, N)
+        for k in range(3):
+            vi, vj = canonical_vertex(i0 + off[:, k, 0], j0 + off[:, k, 1], N)
+            vidx = vj * V + vi
+            for j in range(8):
+                base = tree.map_offset[np.maximum(nodes[:, j], 0)]
+                a = np.where(present[:, j], base + vidx, -1)
+                w = wn[:, j] * b[:, k]
+                addr[:, l, j, k] = a
+                wgt[:, l, j, k] = np.where(present[:, j], w, 0.0)
+                h[:, l * F:(l + 1) * F] += (wgt[:, l, j, k][:, None] * T[np.maximum(a, 0)]
+                                            * present[:, j][:, None])
+    return FullEncoding(h, addr, wgt)
 
 
 # ---------------------------------------------------------------------------
