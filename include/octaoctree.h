@@ -121,7 +121,21 @@ typedef struct octa_scene {
   int32_t weight_dtype;        /* OCTA_F32 or OCTA_BF16                    */
   int32_t n_layers;            /* weight matrices L (2..OCTA_MAX_LAYERS)   */
   int32_t widths[OCTA_MAX_LAYERS + 1]; /* widths[0] = K*F, widths[L] = 3   */
+  int32_t query_form;          /* OCTA_FORM_CELL_BILINEAR or
+                                  OCTA_FORM_TRILINEAR_VERTEX (see below)   */
 } octa_scene;
+
+/* Query forms.  OCTA_FORM_CELL_BILINEAR: per level the cell that contains x
+ * and a bilinear blend of the 4 texels around the direction on its R x R
+ * texel-centred map.  OCTA_FORM_TRILINEAR_VERTEX (Eq. 10 with Eq. 6, without
+ * the disparity shift): per level the 8 cells around x with trilinear
+ * weights renormalised over the cells present in the octree, in each the
+ * barycentric blend of the 3 vertices of the triangle holding the direction
+ * on the node's R x R vertex map (R = 2^k + 1, k >= 1; mirrored vertices of
+ * the map's edges are one vertex).  Only octa_encode evaluates the second
+ * form; the other entry points return OCTA_EUNSUPPORTED for it.           */
+#define OCTA_FORM_CELL_BILINEAR 0
+#define OCTA_FORM_TRILINEAR_VERTEX 1
 
 /* Queries: scene s answers queries [scene_start[s], scene_start[s+1]).   */
 typedef struct octa_queries {
@@ -131,14 +145,17 @@ typedef struct octa_queries {
   int64_t scene_start[OCTA_MAX_SCENES + 1];
 } octa_queries;
 
-/* octa_encode -- the OctaOctree encoding alone (Eq. 10 single-cell bilinear
- * form, Eq. 11): features [n][W] with W = sum over scenes of nothing: each
- * query writes its own scene's K*F features into a row of row_stride
- * elements (row_stride >= K*F of every scene; unused tail left untouched).
- * feat_dtype OCTA_F32 or OCTA_BF16.  Absent levels write zeros.
- * node_idx: device [n][K_max] int32 or NULL (K_max = largest K of the
- * scenes, unused columns -1); texel_addr: device [n][K_max][4] int32 or NULL,
- * corner order k = a + 2b for corner (i0+a, j0+b), -1 where absent.      */
+/* octa_encode -- the OctaOctree encoding alone in the scenes' query form
+ * (all scenes of a call share it; Eq. 10 single-cell bilinear form or Eq. 10
+ * with Eq. 6, then Eq. 11): each query writes its own scene's K*F features
+ * into a row of row_stride elements (row_stride >= K*F of every scene;
+ * unused tail left untouched).  feat_dtype OCTA_F32 or OCTA_BF16.  Absent
+ * levels write zeros.  node_idx: device [n][K_max] int32 or NULL (K_max =
+ * largest K of the scenes, unused columns -1; cell form only).
+ * texel_addr: device int32 or NULL, -1 where absent: cell form [n][K_max][4]
+ * (corner k = a + 2b for corner (i0+a, j0+b)); trilinear vertex form
+ * [n][K_max][24] (neighbour j = 0..7, offset (j & 1, j >> 1 & 1, j >> 2)
+ * from the lower cell, times vertex k = 0..2: entry 3 j + k).             */
 int octa_encode(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
                 void* features, int32_t feat_dtype, int64_t row_stride,
                 int32_t* node_idx, int32_t* texel_addr, int32_t* status, void* stream);

@@ -30,6 +30,8 @@ OCTA_MAX_GROUPS = 16
 OCTA_F32 = 0
 OCTA_F16 = 1
 OCTA_BF16 = 2
+OCTA_FORM_CELL_BILINEAR = 0
+OCTA_FORM_TRILINEAR_VERTEX = 1
 
 OCTA_OP_LOSS = 1
 OCTA_OP_ADAM = 2
@@ -62,6 +64,7 @@ class octa_scene(C.Structure):
         ("weight_dtype", C.c_int32),
         ("n_layers", C.c_int32),
         ("widths", C.c_int32 * (OCTA_MAX_LAYERS + 1)),
+        ("query_form", C.c_int32),
     ]
 
 

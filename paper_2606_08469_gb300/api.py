@@ -104,8 +104,10 @@ class Scene:
     [out][in] (float32 or bfloat16), stored back to back.
     """
 
-    def __init__(self, tree: HostTree, tables, weights, device="cuda"):
+    def __init__(self, tree: HostTree, tables, weights, device="cuda",
+                 query_form=L.OCTA_FORM_CELL_BILINEAR):
         self.tree = tree
+        self.query_form = int(query_form)
         self.device = torch.device(device)
         self.first_child = torch.from_numpy(tree.first_child).to(self.device)
         self.map_offset = torch.from_numpy(tree.map_offset).to(self.device)
@@ -150,6 +152,7 @@ class Scene:
         s.n_layers = len(self.widths) - 1
         for i, w in enumerate(self.widths):
             s.widths[i] = w
+        s.query_form = self.query_form
         return s
 
 
@@ -186,7 +189,8 @@ def octa_encode(scenes, x, omega, counts=None, feat_dtype=torch.float32, want_no
     dev = x.device
     feat = torch.zeros((n, W), dtype=feat_dtype, device=dev)
     nodes = torch.empty((n, kmax), dtype=torch.int32, device=dev) if want_nodes else None
-    addr = torch.empty((n, kmax, 4), dtype=torch.int32, device=dev) if want_addr else None
+    per_level = 24 if sl[0].query_form == L.OCTA_FORM_TRILINEAR_VERTEX else 4
+    addr = torch.empty((n, kmax, per_level), dtype=torch.int32, device=dev) if want_addr else None
     q = _queries(x, omega, counts)
     L.check(_lib().octa_encode(arr, ns, C.byref(q), _ptr(feat), _DT[feat_dtype], W, _ptr(nodes),
                                _ptr(addr), _ptr(status), _stream(stream)), "octa_encode")

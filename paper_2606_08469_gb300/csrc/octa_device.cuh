@@ -25,6 +25,7 @@ struct DevScene {
   int64_t num_texels;
   int64_t q_begin, q_end;  // query range of this scene
   int64_t norm_pairs;      // training passes: pairs the loss is a mean over
+  int32_t query_form;      // OCTA_FORM_*
   int64_t tile_begin;      // first global tile of this scene
   int32_t num_nodes;
   int32_t K;

@@ -24,7 +24,7 @@ namespace octa {
 // output rows are packed), so the feature stream is written coalesced.
 constexpr int ENC_NT = 128;
 
-template <int F, typename TT, typename OT, int KP>
+template <int F, typename TT, typename OT, int KP, int FORM = OCTA_FORM_CELL_BILINEAR>
 __global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ QueryParams p) {
   extern __shared__ __align__(16) uint8_t stage[];
   const int q = threadIdx.x;
@@ -50,26 +50,29 @@ __global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ 
     const int row_bytes = W * int(sizeof(OT));
     const int rb = (row_bytes + 15) & ~15;  // staging row stride
     __syncthreads();
-    locate_gather_query<F, TT, KP, sizeof(OT) == 2>(
-        p, sc, tree, in, q0 + q, q < nq, 0, nullptr, nullptr, q, ENC_NT,
-        [&](int l, const float (&v)[F]) {
-          if (l >= sc.K) return;
-          uint8_t* dst = stage + q * rb + l * F * int(sizeof(OT));
-          if constexpr (sizeof(OT) == 2) {
-            uint32_t w[F / 2];
+    auto stage_row = [&](int l, const float (&v)[F]) {
+      if (l >= sc.K) return;
+      uint8_t* dst = stage + q * rb + l * F * int(sizeof(OT));
+      if constexpr (sizeof(OT) == 2) {
+        uint32_t w[F / 2];
 #pragma unroll
-            for (int i = 0; i < F / 2; ++i) w[i] = pack_bf16x2_rn(v[2 * i], v[2 * i + 1]);
-            if constexpr (F == 8)
-              *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-            else
-              *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
-          } else {
+        for (int i = 0; i < F / 2; ++i) w[i] = pack_bf16x2_rn(v[2 * i], v[2 * i + 1]);
+        if constexpr (F == 8)
+          *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+        else
+          *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+      } else {
 #pragma unroll
-            for (int i = 0; i < F / 4; ++i)
-              reinterpret_cast<float4*>(dst)[i] =
-                  make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-          }
-        });
+        for (int i = 0; i < F / 4; ++i)
+          reinterpret_cast<float4*>(dst)[i] =
+              make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+      }
+    };
+    if constexpr (FORM == OCTA_FORM_TRILINEAR_VERTEX)
+      gather_full_query<F, TT, KP>(p, sc, tree, in, q0 + q, q < nq, stage_row);
+    else
+      locate_gather_query<F, TT, KP, sizeof(OT) == 2>(p, sc, tree, in, q0 + q, q < nq, 0, nullptr,
+                                                       nullptr, q, ENC_NT, stage_row);
     __syncthreads();
     const bool packed = p.row_stride == W && rb == row_bytes &&
                         (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
@@ -96,7 +99,7 @@ bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u
 
 // Validates scenes + queries and fills the kernel parameter block.
 int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
-                       const octa_scene_grads* grads, QueryParams& p) {
+                       const octa_scene_grads* grads, QueryParams& p, bool full_form_ok = false) {
   std::memset(&p, 0, sizeof(p));
   if (!scenes || !q) return fail(OCTA_EINVAL, "scenes and queries must be non-NULL");
   if (n_scenes < 1 || n_scenes > OCTA_MAX_SCENES)
@@ -144,6 +147,20 @@ int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_qu
     d.K = c.num_levels;
     d.n_layers = c.n_layers;
     for (int l = 0; l < c.num_levels; ++l) d.R[l] = c.R[l];
+    d.query_form = c.query_form;
+    if (c.query_form != OCTA_FORM_CELL_BILINEAR && c.query_form != OCTA_FORM_TRILINEAR_VERTEX)
+      return fail(OCTA_EINVAL, "scene %d: unknown query_form %d", s, c.query_form);
+    if (c.query_form == OCTA_FORM_TRILINEAR_VERTEX) {
+      if (!full_form_ok)
+        return fail(OCTA_EUNSUPPORTED, "scene %d: the trilinear vertex form is evaluated by "
+                                       "octa_encode only", s);
+      for (int l = 0; l < c.num_levels; ++l) {
+        const int n = c.R[l] - 1;  // cells a side: a power of two >= 2
+        if (n < 2 || (n & (n - 1)))
+          return fail(OCTA_EINVAL, "scene %d: vertex map side R[%d] = %d is not 2^k + 1", s, l,
+                      c.R[l]);
+      }
+    }
     int off = 0;
     for (int i = 0; i <= c.n_layers; ++i) {
       if (c.widths[i] < 1) return fail(OCTA_EINVAL, "scene %d: width %d < 1", s, i);
@@ -191,9 +208,14 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
                            void* stream) {
   clear_error();
   QueryParams p;
-  int rc = build_query_params(scenes, n_scenes, q, nullptr, p);
+  int rc = build_query_params(scenes, n_scenes, q, nullptr, p, true);
   if (rc) return rc;
   if (q->n > 0 && !features) return fail(OCTA_EINVAL, "features must be non-NULL");
+  for (int s = 1; s < n_scenes; ++s)
+    if (scenes[s].query_form != scenes[0].query_form)
+      return fail(OCTA_EUNSUPPORTED, "scenes of one call must share the query form");
+  if (node_idx && scenes[0].query_form == OCTA_FORM_TRILINEAR_VERTEX)
+    return fail(OCTA_EINVAL, "node_idx is not defined for the trilinear vertex form");
   if (feat_dtype != OCTA_F32 && feat_dtype != OCTA_BF16)
     return fail(OCTA_EINVAL, "feature dtype must be F32 or BF16");
   int kmax = 0, F = scenes[0].F, tdt = scenes[0].table_dtype;
@@ -227,12 +249,18 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
   static_assert(ENC_NT == QT, "tile size");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool f16 = tdt == OCTA_F16, bf = feat_dtype == OCTA_BF16;
+  const bool full = scenes[0].query_form == OCTA_FORM_TRILINEAR_VERTEX;
   const octa_tuning tu = tuning_snapshot();
-#define OCTA_ENC(F_, TT_, KP_)                                                                   \
-  return bf ? launch_persistent(encode_kernel<F_, TT_, __nv_bfloat16, KP_>, smem, p, st, ENC_NT, \
-                                tu.encode_ctas_per_sm, tu.fwd_order)                             \
-            : launch_persistent(encode_kernel<F_, TT_, float, KP_>, smem, p, st, ENC_NT,         \
+#define OCTA_ENC_FORM(F_, TT_, KP_, FORM_)                                                       \
+  return bf ? launch_persistent(encode_kernel<F_, TT_, __nv_bfloat16, KP_, FORM_>, smem, p, st,  \
+                                ENC_NT, tu.encode_ctas_per_sm, tu.fwd_order)                     \
+            : launch_persistent(encode_kernel<F_, TT_, float, KP_, FORM_>, smem, p, st, ENC_NT,  \
                                 tu.encode_ctas_per_sm, tu.fwd_order);
+#define OCTA_ENC(F_, TT_, KP_)                                    \
+  if (full) {                                                     \
+    OCTA_ENC_FORM(F_, TT_, KP_, OCTA_FORM_TRILINEAR_VERTEX)       \
+  }                                                               \
+  OCTA_ENC_FORM(F_, TT_, KP_, OCTA_FORM_CELL_BILINEAR)
 #define OCTA_ENC_KP(F_, TT_)      \
   if (kmax <= 10) {               \
     OCTA_ENC(F_, TT_, 10)         \
@@ -252,6 +280,7 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
   OCTA_ENC_KP(8, float)
 #undef OCTA_ENC_KP
 #undef OCTA_ENC
+#undef OCTA_ENC_FORM
 }
 
 extern "C" int octa_query_fwd(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
