@@ -297,6 +297,50 @@ def encode_leg(dev, flush, stream, steps, peaks):
                          "per_query": f"24 B in + {2 * W} B out, table {table_bytes} B once"}}
 
 
+def encode_full_leg(dev, flush, stream, steps, peaks):
+    """The full query form (Eq. 10 eight-cell renormalised trilinear blend,
+    Eq. 6 barycentric interpolation on vertex maps) of config [3]'s 1280x720
+    G-buffer on its depth-8 octree with vertex maps of side 2^k + 1 (65, 65,
+    33, 33, 17, 17, 9, 9, 9), FP16 features, BF16 features out: 8 x 3 vertex
+    loads per level against the cell form's 4 texels."""
+    import torch
+    from paper_2606_08469_gb300 import _lib as L
+    from paper_2606_08469_gb300 import api
+    from paper_2606_08469_gb300 import inputs as I
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[3]
+    V = [r + 1 for r in cfg.R]
+    tree = api.octree_build(cfg.seed("tree"), cfg.max_depth, cfg.p_base, V)
+    T = WL.to_dev(I.make_tables(cfg.seed("tables"), tree.num_texels, cfg.F, cfg.sigma), dev).half()
+    mlp = I.make_mlp(cfg.seed("mlp"), [tree.num_levels * cfg.F, 64, 64, 3])
+    sc = api.Scene(tree, T, [WL.to_dev(w, dev).to(torch.bfloat16) for w in mlp], device=dev,
+                   query_form=L.OCTA_FORM_TRILINEAR_VERTEX)
+    x, om = I.gbuffer_queries(cfg.seed("queries"), 1280, 720)
+    X, Om = WL.to_dev(x, dev), WL.to_dev(om, dev)
+    W = tree.num_levels * cfg.F
+    feat = torch.empty((len(x), W), dtype=torch.bfloat16, device=dev)
+    q = api._queries(X, Om, None)
+    arr, ns = api._scene_array(sc)
+    lib = api._lib()
+
+    def fn():
+        api.L.check(lib.octa_encode(arr, ns, api.C.byref(q), api._ptr(feat), api.L.OCTA_BF16, W,
+                                    None, None, None, api._stream()), "octa_encode")
+    for _ in range(3):
+        fn()
+    t = _timed(fn, steps, flush, stream)
+    table_bytes = tree.num_texels * cfg.F * 2
+    alg = len(x) * (24 + 2 * W) + table_bytes
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    ach = alg / (t / 1e3) / 1e9
+    return {"workload": f"config[3] 1280x720 G-buffer, depth-8 octree with vertex maps {V}, FP16 "
+                        f"features ({tree.num_texels} entries), full query form, {W} BF16 features out",
+            "ms": round(t, 4), "Mq/s": round(len(x) / t / 1e3, 1),
+            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(ach / peak, 4), "algorithmic_bytes": alg,
+                         "per_query": f"24 B in + {2 * W} B out, table {table_bytes} B once"}}
+
+
 def encode_stress_leg(dev, flush, stream, steps, peaks):
     """The encoding alone with tables larger than L2: 2^20 uniform random
     queries (x in the unit cube, omega on the sphere) on a dense octree of
@@ -454,7 +498,8 @@ def job_rate(units_per_rank, world, steps, total_ms):
     return world * units_per_rank * steps / (total_ms / 1e3) / 1e6
 
 
-LEGS = ("bf16_vs_f32", "inference", "small_forward", "encode", "encode_stress", "batched")
+LEGS = ("bf16_vs_f32", "inference", "small_forward", "encode", "encode_full", "encode_stress",
+        "batched")
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
 # launch (262,144 pairs) of the FP32 fused training pass, from one ncu
@@ -479,6 +524,7 @@ def run_legs(args, names):
            "inference": lambda: inference_leg(dev, flush, stream, steps, peaks),
            "small_forward": lambda: small_forward_leg(dev, flush, stream, steps),
            "encode": lambda: encode_leg(dev, flush, stream, steps, peaks),
+           "encode_full": lambda: encode_full_leg(dev, flush, stream, steps, peaks),
            "encode_stress": lambda: encode_stress_leg(dev, flush, stream, steps, peaks),
            "batched": lambda: batched_leg(dev, flush, stream, steps)}
     print(json.dumps({n: fns[n]() for n in names}), flush=True)
@@ -654,6 +700,7 @@ def run_ours(args):
             out["inference"] = inference_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
             out["small_forward"] = small_forward_leg(dev, flush, stream, max(5, args.steps // 2))
             out["encode"] = encode_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
+            out["encode_full"] = encode_full_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
             out["encode_stress"] = encode_stress_leg(dev, flush, stream, max(5, args.steps // 2),
                                                      peaks)
             out["batched"] = batched_leg(dev, flush, stream, max(5, args.steps // 2))
