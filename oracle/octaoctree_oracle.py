@@ -545,10 +545,27 @@ def mlp_forward(weights, h):
     return np.exp(zs[-1]), zs, inputs
 
 
-def query_forward(tree, tables, weights, x, omega):
-    """L_hat(x, omega): encoding then decoder.  Returns (rgb, Encoding)."""
-    enc = encode_features(tree, tables, x, omega)
-    rgb, _, _ = mlp_forward(weights, enc.h)
+FORMS = ("cell", "full")
+
+
+def _encode(tree, tables, x, omega, form):
+    """Encoding in the query form: "cell" (encode_features) or "full"
+    (encode_features_full); returns (h, addr [N][K][n_entries],
+    weight [N][K][n_entries])."""
+    if form == "cell":
+        e = encode_features(tree, tables, x, omega)
+        return e, e.h, e.addr, e.weight
+    if form == "full":
+        e = encode_features_full(tree, tables, x, omega)
+        n, K = e.h.shape[0], tree.num_levels
+        return e, e.h, e.addr.reshape(n, K, 24), e.weight.reshape(n, K, 24)
+    raise ValueError(form)
+
+
+def query_forward(tree, tables, weights, x, omega, form="cell"):
+    """L_hat(x, omega): encoding then decoder.  Returns (rgb, encoding)."""
+    enc, h, _, _ = _encode(tree, tables, x, omega, form)
+    rgb, _, _ = mlp_forward(weights, h)
     return rgb, enc
 
 
@@ -578,18 +595,19 @@ def residual_loss(Lp, Ls, E, w, eps=1e-2, rhs_grad=True, scale=1.0):
     return loss, dLp, dLs
 
 
-def query_backward(tree, tables, weights, x, omega, d_rgb):
+def query_backward(tree, tables, weights, x, omega, d_rgb, form="cell"):
     """Gradients of sum(d_rgb * L_hat) w.r.t. the table and the weights.
 
     Decoder: delta_L = d_rgb * exp(z_L); dW_i = delta_i^T a_{i-1};
     delta_{i-1} = (delta_i W_i) * 1[z_{i-1} > 0]; dh = delta_1 W_1.
-    Encoding: each present corner k of level l receives weight_k * dh_l.
+    Encoding: each present entry k of level l (4 corners in the cell form,
+    8 cells x 3 vertices in the full form) receives weight_k * dh_l.
     """
     T = np.asarray(tables, dtype=np.float64)
     F = T.shape[1]
     K = tree.num_levels
-    enc = encode_features(tree, T, x, omega)
-    rgb, zs, inputs = mlp_forward(weights, enc.h)
+    _, h, addr, weight = _encode(tree, T, x, omega, form)
+    rgb, zs, inputs = mlp_forward(weights, h)
     Ws = [np.asarray(W, dtype=np.float64) for W in weights]
     delta = np.asarray(d_rgb, dtype=np.float64) * rgb
     dWs = [None] * len(Ws)
@@ -602,11 +620,11 @@ def query_backward(tree, tables, weights, x, omega, d_rgb):
             dh = g
     dT = np.zeros_like(T)
     for l in range(K):
-        for k in range(4):
-            a = enc.addr[:, l, k]
+        for k in range(addr.shape[2]):
+            a = addr[:, l, k]
             ok = a >= 0
             for f in range(F):
-                dT[:, f] += np.bincount(a[ok], weights=enc.weight[ok, l, k] * dh[ok, l * F + f],
+                dT[:, f] += np.bincount(a[ok], weights=weight[ok, l, k] * dh[ok, l * F + f],
                                         minlength=len(T))
     return dT, dWs, rgb
 

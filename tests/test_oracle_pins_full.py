@@ -170,3 +170,44 @@ def test_directional_features_are_continuous_on_the_sphere():
     h2 = O.encode_features_full(t, T, x, w2.astype(np.float32)).h
     lip = 4 * (V - 1) * np.abs(T).max() * 2
     assert np.max(np.abs(h1 - h2)) <= lip * 2e-6 + 1e-6
+
+
+def test_full_form_backward_matches_central_differences():
+    """d/dtheta of sum(d_rgb . L_hat) in the full form: the oracle's analytic
+    table and weight gradients against central differences (FP64)."""
+    t = O.build_tree(41, 2, 0.8, [5, 3, 3])
+    F = 2
+    rng = np.random.default_rng(42)
+    T = rng.normal(scale=0.3, size=(t.num_texels, F))
+    Ws = [W.astype(np.float64) * 1.5 for W in I.make_mlp(43, [t.num_levels * F, 8, 3])]
+    x, w = I.uniform_queries(44, 40)
+    d = rng.normal(size=(len(x), 3))
+    dT, dWs, _ = O.query_backward(t, T, Ws, x, w, d, form="full")
+
+    def f(T_, Ws_):
+        rgb, _ = O.query_forward(t, T_, Ws_, x, w, form="full")
+        return float(np.sum(d * rgb))
+
+    h = 1e-6
+    touched = np.argwhere(np.abs(dT) > 0)
+    pick = touched[rng.choice(len(touched), size=min(60, len(touched)), replace=False)]
+    fd, an = [], []
+    for (r, c) in pick:
+        Tp, Tm = T.copy(), T.copy()
+        Tp[r, c] += h
+        Tm[r, c] -= h
+        fd.append((f(Tp, Ws) - f(Tm, Ws)) / (2 * h))
+        an.append(dT[r, c])
+    for i, W in enumerate(Ws):
+        for idx in zip(*np.unravel_index(rng.choice(W.size, size=min(20, W.size), replace=False),
+                                         W.shape)):
+            Wp = [w_.copy() for w_ in Ws]
+            Wm = [w_.copy() for w_ in Ws]
+            Wp[i][idx] += h
+            Wm[i][idx] -= h
+            fd.append((f(T, Wp) - f(T, Wm)) / (2 * h))
+            an.append(dWs[i][idx])
+    fd, an = np.array(fd), np.array(an)
+    assert np.linalg.norm(fd - an) <= 1e-6 * np.linalg.norm(an)
+    # an untouched entry has zero gradient
+    assert np.count_nonzero(dT) < dT.size
