@@ -207,7 +207,8 @@ def octa_query_fwd(scenes, x, omega, counts=None, want_nodes=False, want_addr=Fa
     if rgb is None:
         rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
     nodes = torch.empty((n, kmax), dtype=torch.int32, device=dev) if want_nodes else None
-    addr = torch.empty((n, kmax, 4), dtype=torch.int32, device=dev) if want_addr else None
+    per_level = 24 if sl[0].query_form == L.OCTA_FORM_TRILINEAR_VERTEX else 4
+    addr = torch.empty((n, kmax, per_level), dtype=torch.int32, device=dev) if want_addr else None
     q = _queries(x, omega, counts)
     L.check(_lib().octa_query_fwd(arr, ns, C.byref(q), _ptr(rgb), _ptr(nodes), _ptr(addr),
                                   _ptr(status), _stream(stream)), "octa_query_fwd")

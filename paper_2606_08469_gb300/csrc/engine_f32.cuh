@@ -363,10 +363,14 @@ __device__ __forceinline__ void load_weights(const DevScene& sc, float* wsm) {
 // Phase 1: fold omega and walk the tree (one thread per query), reading node
 // records from the staged tree (global memory when tree is nullptr).  Level
 // l's cell is c >> (15 - l) with c = min(floor(x * 2^15), 2^15 - 1) per axis.
+// In the trilinear vertex form (Eq. 10) every level needs eight cells, so the
+// walk is left to the (query, level) items: rows 0-2 of node_sm then hold the
+// clamped position (as floats) and row 3 the query's validity (0 / -1).
 template <int KMAX>
 __device__ __forceinline__ void locate_tile(const QueryParams& p, const DevScene& sc,
                                             const int2* tree, const QueryIn& in, int64_t q0,
                                             int nq, int* node_sm, float* u_sm) {
+  static_assert(KMAX >= 4, "the full form keeps positions and validity in four rows");
   const int q = threadIdx.x;
   if (q >= QT) return;
   const bool valid = q < nq;
@@ -375,6 +379,14 @@ __device__ __forceinline__ void locate_tile(const QueryParams& p, const DevScene
   octa_fold(in.w0, in.w1, in.w2, ux, uy);
   u_sm[q] = ux;
   u_sm[QT + q] = uy;
+  if (sc.query_form == OCTA_FORM_TRILINEAR_VERTEX) {  // the items look up their own cells
+    float* xs = reinterpret_cast<float*>(node_sm);    // [3][QT] positions (KMAX >= 3 rows)
+    xs[q] = clamp01(in.x0);
+    xs[QT + q] = clamp01(in.x1);
+    xs[2 * QT + q] = clamp01(in.x2);
+    node_sm[3 * QT + q] = valid ? 0 : -1;             // validity of the query
+    return;
+  }
   const int cx = min(static_cast<int>(clamp01(in.x0) * 32768.f), 32767);
   const int cy = min(static_cast<int>(clamp01(in.x1) * 32768.f), 32767);
   const int cz = min(static_cast<int>(clamp01(in.x2) * 32768.f), 32767);
@@ -414,12 +426,57 @@ __device__ __forceinline__ int64_t map_base(const QueryParams& p, const DevScene
 }
 
 // Phase 2: one thread per (query, level) item for levels [0, nlev); writes
-// feature f of level l for query q to h[(l*F + f) * ld_feat + q * ld_q].
+// feature f of level l for query q to h[(l*F + f) * ld_feat + q * ld_q].  In
+// the trilinear vertex form the item blends the 8 x 3 vertex features of
+// full_form_level (Eq. 6, 10; texel_addr rows of 24 entries a level).
 template <int F, typename TT>
 __device__ __forceinline__ void gather_tile(const QueryParams& p, const DevScene& sc,
                                             const int2* tree, int64_t q0, int nq, int nlev,
                                             const int* node_sm,
                                             const float* u_sm, float* h, int ld_feat, int ld_q) {
+  if (sc.query_form == OCTA_FORM_TRILINEAR_VERTEX) {
+    const float* xsm = reinterpret_cast<const float*>(node_sm);
+    for (int it = threadIdx.x; it < nlev * QT; it += NT) {
+      const int l = it / QT, q = it % QT;
+      float v[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) v[f] = 0.f;
+      const bool on = node_sm[3 * QT + q] >= 0 && l < sc.K;
+      int32_t* aout = (p.texel_addr && q < nq && l < p.kmax_out)
+                          ? p.texel_addr + ((q0 + q) * p.kmax_out + l) * 24 : nullptr;
+      if (on) {
+        const float xs[3] = {xsm[q], xsm[QT + q], xsm[2 * QT + q]};
+        FullLevel fl;
+        full_form_level(p, sc, tree, xs, u_sm[q], u_sm[QT + q], l, fl);
+        for (int j = 0; j < 8; ++j) {
+          if (fl.base[j] < 0) {
+            if (aout)
+              for (int k = 0; k < 3; ++k) aout[3 * j + k] = -1;
+            continue;
+          }
+          for (int k = 0; k < 3; ++k) {
+            float t[F];
+            TexelLoad<TT, F>::load(sc.tables, int64_t(fl.base[j] + fl.vidx[k]), t);
+            const float w = fl.wn[j] * fl.b[k];
+#pragma unroll
+            for (int f = 0; f < F; ++f) v[f] = fmaf(w, t[f], v[f]);
+            if (aout) aout[3 * j + k] = fl.base[j] + fl.vidx[k];
+          }
+        }
+      } else if (aout) {
+        for (int k = 0; k < 24; ++k) aout[k] = -1;
+      }
+#pragma unroll
+      for (int f = 0; f < F; ++f) h[(l * F + f) * ld_feat + q * ld_q] = v[f];
+    }
+    if (p.texel_addr && p.kmax_out > nlev)
+      for (int it = threadIdx.x; it < (p.kmax_out - nlev) * QT; it += NT) {
+        const int l = nlev + it / QT, q = it % QT;
+        if (q < nq)
+          for (int k = 0; k < 24; ++k) p.texel_addr[((q0 + q) * p.kmax_out + l) * 24 + k] = -1;
+      }
+    return;
+  }
   for (int it = threadIdx.x; it < nlev * QT; it += NT) {
     const int l = it / QT, q = it % QT;
     const int node = node_sm[l * QT + q];
@@ -467,11 +524,38 @@ __device__ __forceinline__ void gather_tile(const QueryParams& p, const DevScene
 }
 
 // Phase 4 (BWD): d_tables[texel] += w_k * dh_l for the 4 corners of every
-// present level (float4 vector atomics).
+// present level (float4 vector atomics); in the trilinear vertex form for the
+// 24 vertices of a level, weight = renormalised cell weight x barycentric.
 template <int KMAX, int F>
 __device__ __forceinline__ void scatter_tile(const QueryParams& p, const DevScene& sc,
                                              const int2* tree, const int* node_sm, const float* u_sm,
                                              const float* dh) {
+  if (sc.query_form == OCTA_FORM_TRILINEAR_VERTEX) {
+    const float* xsm = reinterpret_cast<const float*>(node_sm);
+    for (int it = threadIdx.x; it < KMAX * QT; it += NT) {
+      const int l = it / QT, q = it % QT;
+      if (node_sm[3 * QT + q] < 0 || l >= sc.K) continue;
+      const float xs[3] = {xsm[q], xsm[QT + q], xsm[2 * QT + q]};
+      FullLevel fl;
+      full_form_level(p, sc, tree, xs, u_sm[q], u_sm[QT + q], l, fl);
+      for (int c = 0; c < F / 4; ++c) {
+        const float g0 = dh[(l * F + 4 * c + 0) * LDA + q];
+        const float g1 = dh[(l * F + 4 * c + 1) * LDA + q];
+        const float g2 = dh[(l * F + 4 * c + 2) * LDA + q];
+        const float g3 = dh[(l * F + 4 * c + 3) * LDA + q];
+        for (int j = 0; j < 8; ++j) {
+          if (fl.base[j] < 0) continue;
+          for (int k = 0; k < 3; ++k) {
+            const float w = fl.wn[j] * fl.b[k];
+            float4* dst =
+                reinterpret_cast<float4*>(sc.d_tables + int64_t(fl.base[j] + fl.vidx[k]) * F) + c;
+            atomicAdd(dst, make_float4(w * g0, w * g1, w * g2, w * g3));
+          }
+        }
+      }
+    }
+    return;
+  }
   for (int it = threadIdx.x; it < KMAX * QT; it += NT) {
     const int l = it / QT, q = it % QT;
     const int node = node_sm[l * QT + q];

@@ -161,23 +161,10 @@ __device__ __forceinline__ void locate_gather_query(const QueryParams& p, const 
       *reinterpret_cast<int4*>(p.texel_addr + (gq * p.kmax_out + l) * 4) = make_int4(-1, -1, -1, -1);
 }
 
-// The full query form (Eq. 10 with the directional lookup of Eq. 6, the
-// same direction in every cell): one query per thread.  Per level l:
-//   direction  the canonical binary32 fold, p = uv N on the V x V vertex
-//              map (N = V - 1, vertex (i, j) at uv = (i, j) / N), the grid
-//              cell (i0, j0) = min(floor(p), N - 1) and the triangle of it
-//              holding p: cells split along the diagonal parallel to their
-//              quadrant's face edge (anti-diagonal where u_x and u_y share a
-//              sign), the side decided in binary32 (fx + fy <= 1, fy <= fx);
-//              barycentric weights of the three vertices; mirrored vertices
-//              of the map's edges folded onto one representative;
-//   space      the eight cells around x: c0 = floor(x 2^l - 1/2) (binary32),
-//              neighbour j = c0 + (j & 1, j >> 1 & 1, j >> 2), trilinear
-//              weights, each cell looked up by a descent from the root, the
-//              weights renormalised over the cells present (none: zeros);
-// then the 8 x 3 vertex features blended into the level's F features,
-// handed to store(l, v).  texel_addr (when requested) receives the 24
-// entries of each level (neighbour-major, -1 where absent).
+// The full query form of one query per thread (encoding kernel): per level
+// full_form_level, then the 8 x 3 vertex features blended into the level's F
+// features, handed to store(l, v).  texel_addr (when requested) receives the
+// 24 entries of each level (neighbour-major, -1 where absent).
 template <int F, typename TT, int KP, class Store>
 __device__ __forceinline__ void gather_full_query(const QueryParams& p, const DevScene& sc,
                                                   const int2* tree, const QueryIn& in, int64_t gq,
@@ -185,15 +172,6 @@ __device__ __forceinline__ void gather_full_query(const QueryParams& p, const De
   float ux, uy;
   octa_fold(in.w0, in.w1, in.w2, ux, uy);
   const float xs[3] = {clamp01(in.x0), clamp01(in.x1), clamp01(in.x2)};
-  auto child = [&](int nd) {  // validated first_child of a node
-    if (tree) return tree[nd].x;
-    int fc = __ldg(sc.first_child + nd);
-    if (fc >= 0 && fc > sc.num_nodes - 8) {
-      if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
-      fc = -1;
-    }
-    return fc;
-  };
 #pragma unroll 1
   for (int l = 0; l < KP; ++l) {
     float v[F];
@@ -207,96 +185,24 @@ __device__ __forceinline__ void gather_full_query(const QueryParams& p, const De
       store(l, v);
       continue;
     }
-    const int V = sc.R[l], N = V - 1;
-    // ---- direction: vertex cell, triangle, barycentric weights (Eq. 6)
-    const float fN = static_cast<float>(N);
-    const float px = __fmul_rn(__fadd_rn(__fmul_rn(ux, 0.5f), 0.5f), fN);
-    const float py = __fmul_rn(__fadd_rn(__fmul_rn(uy, 0.5f), 0.5f), fN);
-    const int i0 = min(max(static_cast<int>(floorf(px)), 0), N - 1);
-    const int j0 = min(max(static_cast<int>(floorf(py)), 0), N - 1);
-    const float fx = __fsub_rn(px, static_cast<float>(i0));
-    const float fy = __fsub_rn(py, static_cast<float>(j0));
-    int oi[3], oj[3];
-    float b[3];
-    if ((i0 >= N / 2) == (j0 >= N / 2)) {  // anti-diagonal split
-      if (__fadd_rn(fx, fy) <= 1.f) {
-        oi[0] = 0, oj[0] = 0, oi[1] = 1, oj[1] = 0, oi[2] = 0, oj[2] = 1;
-        b[0] = 1.f - fx - fy, b[1] = fx, b[2] = fy;
-      } else {
-        oi[0] = 1, oj[0] = 1, oi[1] = 1, oj[1] = 0, oi[2] = 0, oj[2] = 1;
-        b[0] = fx + fy - 1.f, b[1] = 1.f - fy, b[2] = 1.f - fx;
-      }
-    } else {  // main-diagonal split
-      if (fy <= fx) {
-        oi[0] = 0, oj[0] = 0, oi[1] = 1, oj[1] = 0, oi[2] = 1, oj[2] = 1;
-        b[0] = 1.f - fx, b[1] = fx - fy, b[2] = fy;
-      } else {
-        oi[0] = 0, oj[0] = 0, oi[1] = 0, oj[1] = 1, oi[2] = 1, oj[2] = 1;
-        b[0] = 1.f - fy, b[1] = fy - fx, b[2] = fx;
-      }
-    }
-    int vidx[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      int vi = i0 + oi[k], vj = j0 + oj[k];
-      if (vi == 0 || vi == N) vj = min(vj, N - vj);  // the fold glues each edge to itself
-      if (vj == 0 || vj == N) vi = min(vi, N - vi);
-      vidx[k] = vj * V + vi;
-    }
-    // ---- space: the eight cells around x, renormalised trilinear weights (Eq. 10)
-    const int n = 1 << l;
-    const float fn = static_cast<float>(n);
-    int c0[3];
-    float t[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float pa = __fsub_rn(__fmul_rn(xs[a], fn), 0.5f);
-      const float fl = floorf(pa);
-      c0[a] = static_cast<int>(fl);
-      t[a] = __fsub_rn(pa, fl);
-    }
-    int base[8];
-    float wsp[8], wsum = 0.f;
+    FullLevel fl;
+    full_form_level(p, sc, tree, xs, ux, uy, l, fl);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int c[3] = {c0[0] + (j & 1), c0[1] + ((j >> 1) & 1), c0[2] + (j >> 2)};
-      base[j] = -1;
-      wsp[j] = 0.f;
-      if (c[0] < 0 || c[1] < 0 || c[2] < 0 || c[0] >= n || c[1] >= n || c[2] >= n) continue;
-      int nd = 0;
-      for (int m = 1; m <= l && nd >= 0; ++m) {
-        const int sh = l - m;
-        const int fc = child(nd);
-        nd = fc >= 0 ? fc + (((c[0] >> sh) & 1) | (((c[1] >> sh) & 1) << 1) | (((c[2] >> sh) & 1) << 2))
-                     : -1;
-      }
-      if (nd < 0) continue;
-      const int mo = checked_map_base(p, sc, tree ? tree[nd].y : __ldg(sc.map_offset + nd), V);
-      if (mo < 0) continue;
-      base[j] = mo;
-      wsp[j] = ((j & 1) ? t[0] : 1.f - t[0]) * (((j >> 1) & 1) ? t[1] : 1.f - t[1]) *
-               ((j >> 2) ? t[2] : 1.f - t[2]);
-      wsum += wsp[j];
-    }
-    const float inv = wsum > 0.f ? 1.f / wsum : 0.f;
-    // ---- the 24 vertex features
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (base[j] < 0) {
+      if (fl.base[j] < 0) {
         if (aout)
           for (int k = 0; k < 3; ++k) aout[3 * j + k] = -1;
         continue;
       }
-      const float wj = wsp[j] * inv;
       TexelRaw<TT, F> tx[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) tx[k].load(sc.tables, uint32_t(base[j] + vidx[k]));
+      for (int k = 0; k < 3; ++k) tx[k].load(sc.tables, uint32_t(fl.base[j] + fl.vidx[k]));
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const float w = wj * b[k];
+        const float w = fl.wn[j] * fl.b[k];
 #pragma unroll
         for (int f = 0; f < F; ++f) v[f] = fmaf(w, tx[k].get(f), v[f]);
-        if (aout) aout[3 * j + k] = base[j] + vidx[k];
+        if (aout) aout[3 * j + k] = fl.base[j] + fl.vidx[k];
       }
     }
     store(l, v);

@@ -278,6 +278,112 @@ __device__ __forceinline__ int checked_map_base(const QueryParams& p, const DevS
   return mo;
 }
 
+// One level of the full query form (Eq. 10 with the directional lookup of
+// Eq. 6, the same direction in every cell):
+//   direction  the folded direction (ux, uy), p = uv N on the V x V vertex
+//              map (N = V - 1, vertex (i, j) at uv = (i, j) / N), the grid
+//              cell (i0, j0) = min(floor(p), N - 1) and the triangle of it
+//              holding p: cells split along the diagonal parallel to their
+//              quadrant's face edge (anti-diagonal where u_x and u_y share a
+//              sign), the side decided in binary32 (fx + fy <= 1, fy <= fx);
+//              barycentric weights b of the three vertices, whose entries
+//              vidx fold mirrored vertices of the map's edges onto one;
+//   space      the eight cells around x: c0 = floor(x 2^l - 1/2) (binary32),
+//              neighbour j = c0 + (j & 1, j >> 1 & 1, j >> 2), trilinear
+//              weights, each cell found by a descent from the root, the
+//              weights renormalised over the cells present (base[j] = their
+//              map base, -1 for absent cells; all weights 0 when none is).
+struct FullLevel {
+  int base[8];
+  float wn[8];
+  int vidx[3];
+  float b[3];
+};
+
+__device__ __forceinline__ void full_form_level(const QueryParams& p, const DevScene& sc,
+                                                const int2* tree, const float (&xs)[3], float ux,
+                                                float uy, int l, FullLevel& o) {
+  const int V = sc.R[l], N = V - 1;
+  const float fN = static_cast<float>(N);
+  const float px = __fmul_rn(__fadd_rn(__fmul_rn(ux, 0.5f), 0.5f), fN);
+  const float py = __fmul_rn(__fadd_rn(__fmul_rn(uy, 0.5f), 0.5f), fN);
+  const int i0 = min(max(static_cast<int>(floorf(px)), 0), N - 1);
+  const int j0 = min(max(static_cast<int>(floorf(py)), 0), N - 1);
+  const float fx = __fsub_rn(px, static_cast<float>(i0));
+  const float fy = __fsub_rn(py, static_cast<float>(j0));
+  int oi[3], oj[3];
+  if ((i0 >= N / 2) == (j0 >= N / 2)) {  // anti-diagonal split
+    if (__fadd_rn(fx, fy) <= 1.f) {
+      oi[0] = 0, oj[0] = 0, oi[1] = 1, oj[1] = 0, oi[2] = 0, oj[2] = 1;
+      o.b[0] = 1.f - fx - fy, o.b[1] = fx, o.b[2] = fy;
+    } else {
+      oi[0] = 1, oj[0] = 1, oi[1] = 1, oj[1] = 0, oi[2] = 0, oj[2] = 1;
+      o.b[0] = fx + fy - 1.f, o.b[1] = 1.f - fy, o.b[2] = 1.f - fx;
+    }
+  } else {  // main-diagonal split
+    if (fy <= fx) {
+      oi[0] = 0, oj[0] = 0, oi[1] = 1, oj[1] = 0, oi[2] = 1, oj[2] = 1;
+      o.b[0] = 1.f - fx, o.b[1] = fx - fy, o.b[2] = fy;
+    } else {
+      oi[0] = 0, oj[0] = 0, oi[1] = 0, oj[1] = 1, oi[2] = 1, oj[2] = 1;
+      o.b[0] = 1.f - fy, o.b[1] = fy - fx, o.b[2] = fx;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    int vi = i0 + oi[k], vj = j0 + oj[k];
+    if (vi == 0 || vi == N) vj = min(vj, N - vj);  // the fold glues each edge to itself
+    if (vj == 0 || vj == N) vi = min(vi, N - vi);
+    o.vidx[k] = vj * V + vi;
+  }
+  const int n = 1 << l;
+  const float fn = static_cast<float>(n);
+  int c0[3];
+  float t[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float pa = __fsub_rn(__fmul_rn(xs[a], fn), 0.5f);
+    const float fl = floorf(pa);
+    c0[a] = static_cast<int>(fl);
+    t[a] = __fsub_rn(pa, fl);
+  }
+  float wsum = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int c[3] = {c0[0] + (j & 1), c0[1] + ((j >> 1) & 1), c0[2] + (j >> 2)};
+    o.base[j] = -1;
+    o.wn[j] = 0.f;
+    if (c[0] < 0 || c[1] < 0 || c[2] < 0 || c[0] >= n || c[1] >= n || c[2] >= n) continue;
+    int nd = 0;
+    for (int m = 1; m <= l && nd >= 0; ++m) {
+      const int sh = l - m;
+      int fc;
+      if (tree) {
+        fc = tree[nd].x;
+      } else {
+        fc = __ldg(sc.first_child + nd);
+        if (fc >= 0 && fc > sc.num_nodes - 8) {
+          if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
+          fc = -1;
+        }
+      }
+      nd = fc >= 0 ? fc + (((c[0] >> sh) & 1) | (((c[1] >> sh) & 1) << 1) | (((c[2] >> sh) & 1) << 2))
+                   : -1;
+    }
+    if (nd < 0) continue;
+    const int mo = checked_map_base(p, sc, tree ? tree[nd].y : __ldg(sc.map_offset + nd), V);
+    if (mo < 0) continue;
+    o.base[j] = mo;
+    o.wn[j] = ((j & 1) ? t[0] : 1.f - t[0]) * (((j >> 1) & 1) ? t[1] : 1.f - t[1]) *
+              ((j >> 2) ? t[2] : 1.f - t[2]);
+    wsum += o.wn[j];
+  }
+  const float inv = wsum > 0.f ? 1.f / wsum : 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) o.wn[j] *= inv;
+}
+
+
 
 // Loads of one texel's F features as FP32.
 template <typename TT, int F>

@@ -98,8 +98,11 @@ bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u
 }  // namespace
 
 // Validates scenes + queries and fills the kernel parameter block.
+// full_form: where the trilinear vertex form is accepted (the encoding for
+// any decoder; the query and training passes for FP32 decoders).
+enum FullForm { kFullNo = 0, kFullFp32 = 1, kFullAny = 2 };
 int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
-                       const octa_scene_grads* grads, QueryParams& p, bool full_form_ok = false) {
+                       const octa_scene_grads* grads, QueryParams& p, int full_form = kFullNo) {
   std::memset(&p, 0, sizeof(p));
   if (!scenes || !q) return fail(OCTA_EINVAL, "scenes and queries must be non-NULL");
   if (n_scenes < 1 || n_scenes > OCTA_MAX_SCENES)
@@ -151,9 +154,9 @@ int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_qu
     if (c.query_form != OCTA_FORM_CELL_BILINEAR && c.query_form != OCTA_FORM_TRILINEAR_VERTEX)
       return fail(OCTA_EINVAL, "scene %d: unknown query_form %d", s, c.query_form);
     if (c.query_form == OCTA_FORM_TRILINEAR_VERTEX) {
-      if (!full_form_ok)
+      if (full_form == kFullNo || (full_form == kFullFp32 && c.weight_dtype != OCTA_F32))
         return fail(OCTA_EUNSUPPORTED, "scene %d: the trilinear vertex form is evaluated by "
-                                       "octa_encode only", s);
+                                       "octa_encode and the FP32 decoder passes only", s);
       for (int l = 0; l < c.num_levels; ++l) {
         const int n = c.R[l] - 1;  // cells a side: a power of two >= 2
         if (n < 2 || (n & (n - 1)))
@@ -202,20 +205,30 @@ int apply_norm_pairs(const octa_pairs* pairs, int n_scenes, QueryParams& p) {
 
 using namespace octa;
 
+namespace {
+// One query form per call (texel_addr's row layout depends on it); node_idx
+// has no meaning in the trilinear vertex form (eight cells per level).
+int check_one_form(const octa_scene* scenes, int32_t n_scenes, const int32_t* node_idx) {
+  for (int s = 1; s < n_scenes; ++s)
+    if (scenes[s].query_form != scenes[0].query_form)
+      return fail(OCTA_EUNSUPPORTED, "scenes of one call must share the query form");
+  if (node_idx && scenes[0].query_form == OCTA_FORM_TRILINEAR_VERTEX)
+    return fail(OCTA_EINVAL, "node_idx is not defined for the trilinear vertex form");
+  return 0;
+}
+}  // namespace
+
 extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
                            void* features, int32_t feat_dtype, int64_t row_stride,
                            int32_t* node_idx, int32_t* texel_addr, int32_t* status,
                            void* stream) {
   clear_error();
   QueryParams p;
-  int rc = build_query_params(scenes, n_scenes, q, nullptr, p, true);
+  int rc = build_query_params(scenes, n_scenes, q, nullptr, p, kFullAny);
   if (rc) return rc;
   if (q->n > 0 && !features) return fail(OCTA_EINVAL, "features must be non-NULL");
-  for (int s = 1; s < n_scenes; ++s)
-    if (scenes[s].query_form != scenes[0].query_form)
-      return fail(OCTA_EUNSUPPORTED, "scenes of one call must share the query form");
-  if (node_idx && scenes[0].query_form == OCTA_FORM_TRILINEAR_VERTEX)
-    return fail(OCTA_EINVAL, "node_idx is not defined for the trilinear vertex form");
+  rc = check_one_form(scenes, n_scenes, node_idx);
+  if (rc) return rc;
   if (feat_dtype != OCTA_F32 && feat_dtype != OCTA_BF16)
     return fail(OCTA_EINVAL, "feature dtype must be F32 or BF16");
   int kmax = 0, F = scenes[0].F, tdt = scenes[0].table_dtype;
@@ -288,7 +301,9 @@ extern "C" int octa_query_fwd(const octa_scene* scenes, int32_t n_scenes, const 
                               int32_t* status, void* stream) {
   clear_error();
   QueryParams p;
-  int rc = build_query_params(scenes, n_scenes, q, nullptr, p);
+  int rc = build_query_params(scenes, n_scenes, q, nullptr, p, kFullFp32);
+  if (rc) return rc;
+  rc = check_one_form(scenes, n_scenes, node_idx);
   if (rc) return rc;
   if (q->n > 0 && !rgb) return fail(OCTA_EINVAL, "rgb must be non-NULL");
   if (texel_addr && (reinterpret_cast<uintptr_t>(texel_addr) & 15u))
@@ -311,7 +326,7 @@ extern "C" int octa_query_bwd(const octa_scene* scenes, int32_t n_scenes, const 
   clear_error();
   if (!grads) return fail(OCTA_EINVAL, "grads must be non-NULL");
   QueryParams p;
-  int rc = build_query_params(scenes, n_scenes, q, grads, p);
+  int rc = build_query_params(scenes, n_scenes, q, grads, p, kFullFp32);
   if (rc) return rc;
   if (q->n > 0 && !d_rgb) return fail(OCTA_EINVAL, "d_rgb must be non-NULL");
   p.d_rgb = d_rgb;
@@ -337,7 +352,7 @@ extern "C" int octa_train_fused(const octa_scene* scenes, int32_t n_scenes, cons
   q.n = pairs->n;
   for (int s = 0; s <= OCTA_MAX_SCENES; ++s) q.scene_start[s] = pairs->scene_start[s];
   QueryParams p;
-  int rc = build_query_params(scenes, n_scenes, &q, grads, p);
+  int rc = build_query_params(scenes, n_scenes, &q, grads, p, kFullFp32);
   if (rc) return rc;
   const bool bf16 = scenes[0].weight_dtype == OCTA_BF16;
   for (int s = 0; s < n_scenes; ++s)

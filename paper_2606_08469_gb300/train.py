@@ -17,7 +17,7 @@ from . import api
 class SceneState:
     """Master parameters, gradients, Adam moments and working copies of one scene."""
 
-    def __init__(self, tree, tables, weights, table_dtype, weight_dtype, device):
+    def __init__(self, tree, tables, weights, table_dtype, weight_dtype, device, query_form=0):
         dev = torch.device(device)
         self.master_t = torch.as_tensor(tables, dtype=torch.float32).to(dev).contiguous()
         self.master_w = torch.cat([torch.as_tensor(W, dtype=torch.float32).reshape(-1)
@@ -32,7 +32,7 @@ class SceneState:
         self.work_w = None if weight_dtype == torch.float32 else self.master_w.to(weight_dtype)
         shaped = [torch.empty(W.shape) for W in weights]
         self.scene = api.Scene(tree, self.work_t if self.work_t is not None else self.master_t,
-                               shaped, device=dev)
+                               shaped, device=dev, query_form=query_form)
         self.scene.set_weights_flat(self.work_w if self.work_w is not None else self.master_w)
 
     def groups(self, lr_tables, lr_mlp):

@@ -20,10 +20,13 @@ def weight_dtype(cfg):
     return _TORCH_DT[cfg.weight_dtype]
 
 
-def host_params(cfg, tree_seed=None, tables_seed=None, mlp_seed=None):
-    """Host tree (library builder) plus FP32 master tables and weights."""
+def host_params(cfg, tree_seed=None, tables_seed=None, mlp_seed=None, vertex_maps=False):
+    """Host tree (library builder) plus FP32 master tables and weights.
+    vertex_maps: maps of side R + 1 (vertices of an R-cell grid, for the
+    trilinear vertex query form) in place of R x R texel maps."""
+    R = [r + 1 for r in cfg.R] if vertex_maps else cfg.R
     tree = api.octree_build(cfg.seed("tree") if tree_seed is None else tree_seed, cfg.max_depth,
-                            cfg.p_base, cfg.R)
+                            cfg.p_base, R)
     tables = I.make_tables(cfg.seed("tables") if tables_seed is None else tables_seed,
                            tree.num_texels, cfg.F, cfg.sigma)
     widths = [tree.num_levels * cfg.F] + list(cfg.widths[1:])
@@ -36,14 +39,18 @@ def pairs_on_device(pairs, device="cuda"):
             for k in ("x", "omega", "x2", "omega2", "E", "w")}
 
 
-def train_step_for(cfg, n_pairs=None, device="cuda", precision=None, **kw):
+def train_step_for(cfg, n_pairs=None, device="cuda", precision=None, query_form=None, **kw):
     """TrainStep of a 'pairs' workload.  precision='f32' forces the FP32 path
-    on the same shapes (FP32 tables and weights)."""
-    tree, tables, weights = host_params(cfg)
+    on the same shapes (FP32 tables and weights); query_form='full' queries
+    the trilinear vertex form on vertex maps of side R + 1."""
+    full = query_form == "full"
+    tree, tables, weights = host_params(cfg, vertex_maps=full)
     tdt, wdt = table_dtype(cfg), weight_dtype(cfg)
     if precision == "f32":
         tdt = wdt = torch.float32
-    st = SceneState(tree, tables, weights, tdt, wdt, device)
+    st = SceneState(tree, tables, weights, tdt, wdt, device,
+                    query_form=api.L.OCTA_FORM_TRILINEAR_VERTEX if full else
+                    api.L.OCTA_FORM_CELL_BILINEAR)
     n = cfg.n if n_pairs is None else n_pairs
     pairs = I.training_pairs(cfg.seed("queries"), n)
     return TrainStep([st], [pairs_on_device(pairs, device)], **kw), (tree, tables, weights, pairs)

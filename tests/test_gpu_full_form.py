@@ -1,7 +1,8 @@
-"""The full query form on the GPU (octa_encode with OCTA_FORM_TRILINEAR_VERTEX:
-Eq. 10 eight-cell renormalised trilinear blend with Eq. 6 barycentric
-interpolation on vertex maps) against the FP64 oracle: the 24 vertex entries
-per level bit-exact, features within the binary32 bound of a 24-term blend."""
+"""The full query form on the GPU (OCTA_FORM_TRILINEAR_VERTEX: Eq. 10
+eight-cell renormalised trilinear blend with Eq. 6 barycentric interpolation
+on vertex maps) against the FP64 oracle: the 24 vertex entries per level
+bit-exact, features within the binary32 bound of a 24-term blend; the FP32
+decoder's forward, backward and fused training pass in the same form."""
 import numpy as np
 import pytest
 import torch
@@ -116,6 +117,135 @@ def test_full_form_argument_errors():
     tree = A.octree_build(5, 2, 0.6, [5, 3, 3])
     sc = _scene(tree, I.make_tables(1, tree.num_texels, 4, 0.3))
     with pytest.raises(L.OctaError):
-        A.octa_query_fwd(sc, dev(x), dev(w))             # the decoder path takes the cell form only
-    with pytest.raises(L.OctaError):
         A.octa_encode(sc, dev(x), dev(w), want_nodes=True)
+    with pytest.raises(L.OctaError):
+        A.octa_query_fwd(sc, dev(x), dev(w), want_nodes=True)
+    weights = [dev(W).to(torch.bfloat16) for W in I.make_mlp(1, [12, 32, 32, 3])]
+    sb = A.Scene(tree, sc.tables, weights, device=DEV, query_form=L.OCTA_FORM_TRILINEAR_VERTEX)
+    with pytest.raises(L.OctaError):                      # BF16 decoders: cell form only
+        A.octa_query_fwd(sb, dev(x), dev(w))
+    A.octa_encode(sb, dev(x), dev(w))                     # the encoding takes either decoder
+
+
+# ------------------------------------------- FP32 decoder passes (FP32 engine)
+
+def _decoder_scene(seed, depth, V, F, hidden, tdt=torch.float32, wscale=1.5):
+    from paper_2606_08469_gb300 import _lib as L
+    from paper_2606_08469_gb300 import api as A
+    tree = A.octree_build(seed, depth, 0.6, V)
+    ot = O.build_tree(seed, depth, 0.6, V)
+    tables = I.make_tables(seed + 1, tree.num_texels, F, 0.3)
+    if tdt == torch.float16:
+        tables = tables.astype(np.float16).astype(np.float32)   # the values the GPU reads
+    weights = [W * np.float32(wscale) for W in I.make_mlp(seed + 2, [(depth + 1) * F] + hidden + [3])]
+    sc = A.Scene(tree, dev(tables).to(tdt).contiguous(), [dev(W) for W in weights], device=DEV,
+                 query_form=L.OCTA_FORM_TRILINEAR_VERTEX)
+    return sc, ot, tables, weights
+
+
+def _rgb_tol(ot, tables, weights, x, w):
+    """|rgb_gpu / rgb - 1| bound: the absolute error of z, at most c * u *
+    z_abs with z_abs the decoder run on |W| and on the blend of |tables|
+    (the 24 blend weights are non-negative, so that blend bounds the
+    features' rounding as well); c = 16 as for the cell form, floor 1e-5."""
+    habs = O.encode_features_full(ot, np.abs(tables), x, w).h
+    _, zs, _ = O.mlp_forward([np.abs(W) for W in weights], habs)
+    return np.maximum(1e-5, 16 * U32 * zs[-1])
+
+
+def _normwise(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+FP32_SCENES = [
+    (1300, 4, [9, 9, 5, 5, 3], 4, [32, 32], torch.float32),
+    (1301, 5, [17, 17, 9, 9, 5, 3], 8, [64, 64], torch.float16),
+    (1302, 6, [9, 9, 9, 5, 5, 3, 3], 8, [64, 64, 64], torch.float32),
+]
+WSCALE = {1300: 1.5, 1301: 1.5, 1302: 0.5}   # three hidden layers: keep z_abs moderate
+
+
+@pytest.mark.parametrize("seed,depth,V,F,hidden,tdt", FP32_SCENES)
+def test_full_form_query_fwd_matches_oracle(seed, depth, V, F, hidden, tdt):
+    """octa_query_fwd on an FP32 decoder in the full form: radiance within
+    the FP32 bound, the 24 entries of every level bit-exact, on a ragged
+    batch (several 128-query tiles and a tail)."""
+    from paper_2606_08469_gb300 import api as A
+    sc, ot, tables, weights = _decoder_scene(seed, depth, V, F, hidden, tdt, WSCALE[seed])
+    x, w = I.uniform_queries(seed + 3, 3001)
+    rgb, _, addr = A.octa_query_fwd(sc, dev(x), dev(w), want_addr=True)
+    ref, enc = O.query_forward(ot, tables, weights, x, w, form="full")
+    np.testing.assert_array_equal(addr.cpu().numpy(), enc.addr.reshape(len(x), depth + 1, 24))
+    err = np.abs(rgb.cpu().numpy() - ref) / ref
+    assert np.all(err <= _rgb_tol(ot, tables, weights, x, w)), err.max()
+
+
+@pytest.mark.parametrize("seed,depth,V,F,hidden,tdt", FP32_SCENES[:2])
+def test_full_form_query_bwd_matches_oracle(seed, depth, V, F, hidden, tdt):
+    """octa_query_bwd in the full form: the 24 entries of a level each
+    receive (renormalised cell weight x barycentric) x dh; table and weight
+    gradients to 1e-5 normwise against the FP64 oracle."""
+    from paper_2606_08469_gb300 import api as A
+    sc, ot, tables, weights = _decoder_scene(seed, depth, V, F, hidden, tdt)
+    x, w = I.uniform_queries(seed + 4, 4000)
+    d_rgb = np.random.default_rng(seed).normal(size=(len(x), 3)).astype(np.float32)
+    dT = torch.zeros((sc.tree.num_texels, F), device=DEV)
+    dW = torch.zeros(sc.weights.shape, device=DEV)
+    A.octa_query_bwd(sc, dev(x), dev(w), dev(d_rgb), [(dT, dW)])
+    rT, rWs, _ = O.query_backward(ot, tables, weights, x, w, d_rgb, form="full")
+    assert _normwise(dT.cpu().numpy(), rT) <= 1e-5
+    gw = dW.cpu().numpy()
+    for (off, o, i), rW in zip(sc.weight_slices(), rWs):
+        assert _normwise(gw[off:off + o * i].reshape(o, i), rW) <= 1e-5
+
+
+@pytest.mark.parametrize("rhs_grad", [True, False])
+def test_full_form_fused_training_matches_oracle(rhs_grad):
+    """octa_train_fused (FP32 engine, 64-pair tiles) in the full form: the
+    Eq. 14 loss to 1e-5 and the gradients of both queries of every pair to
+    1e-5 normwise, against the oracle's residual_loss and query_backward on
+    the same pairs (1,001 pairs: a ragged tail tile)."""
+    from paper_2606_08469_gb300 import api as A
+    seed, depth, V, F, hidden, tdt = FP32_SCENES[1]
+    sc, ot, tables, weights = _decoder_scene(seed, depth, V, F, hidden, tdt)
+    pr = I.training_pairs(seed + 5, 1001)
+    dT = torch.zeros((sc.tree.num_texels, F), device=DEV)
+    dW = torch.zeros(sc.weights.shape, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+    A.octa_train_fused(sc, dev(pr.x), dev(pr.omega), dev(pr.x2), dev(-pr.omega2), dev(pr.E),
+                       dev(pr.w), [(dT, dW)], loss, rhs_grad=rhs_grad)
+    N = len(pr.x)
+    X = np.concatenate([pr.x, pr.x2])
+    Om = np.concatenate([pr.omega, -pr.omega2])
+    rgb, _ = O.query_forward(ot, tables, weights, X, Om, form="full")
+    ref_loss, dLp, dLs = O.residual_loss(rgb[:N], rgb[N:], pr.E, pr.w, 1e-2, rhs_grad)
+    assert abs(loss.item() - ref_loss) <= 1e-5 * ref_loss
+    rT, rWs, _ = O.query_backward(ot, tables, weights, X, Om, np.concatenate([dLp, dLs]),
+                                  form="full")
+    assert _normwise(dT.cpu().numpy(), rT) <= 1e-5
+    gw = dW.cpu().numpy()
+    for (off, o, i), rW in zip(sc.weight_slices(), rWs):
+        assert _normwise(gw[off:off + o * i].reshape(o, i), rW) <= 1e-5
+
+
+def test_full_form_train_step_fused_matches_unfused():
+    """The training step of the headline workload's shapes (FP32, 2,049
+    pairs) in the full form: the fused pass against octa_query_fwd +
+    residual_loss + octa_query_bwd, then one Adam step each."""
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[1]
+    a, _ = WL.train_step_for(cfg, n_pairs=2049, precision="f32", query_form="full")
+    b, _ = WL.train_step_for(cfg, n_pairs=2049, precision="f32", query_form="full", fused=True)
+    a.forward()
+    a.loss_and_grad()
+    a.backward()
+    b.fused_pass()
+    torch.cuda.synchronize()
+    torch.testing.assert_close(b.loss, a.loss, rtol=1e-6, atol=0)
+    for sa, sb in zip(a.states, b.states):
+        for ga, gb in ((sa.grad_t, sb.grad_t), (sa.grad_w, sb.grad_w)):
+            assert (torch.linalg.norm(gb - ga) / torch.linalg.norm(ga)).item() <= 1e-5
+    a.step()
+    b.step()
+    torch.cuda.synchronize()
+    assert np.isfinite(a.loss.item()) and np.isfinite(b.loss.item())
