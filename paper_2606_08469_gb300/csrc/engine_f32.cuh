@@ -448,18 +448,22 @@ __device__ __forceinline__ void gather_tile(const QueryParams& p, const DevScene
         const float xs[3] = {xsm[q], xsm[QT + q], xsm[2 * QT + q]};
         FullLevel fl;
         full_form_level(p, sc, tree, xs, u_sm[q], u_sm[QT + q], l, fl);
+#pragma unroll
         for (int j = 0; j < 8; ++j) {
           if (fl.base[j] < 0) {
             if (aout)
               for (int k = 0; k < 3; ++k) aout[3 * j + k] = -1;
             continue;
           }
+          float t[3][F];
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+            TexelLoad<TT, F>::load(sc.tables, int64_t(fl.base[j] + fl.vidx[k]), t[k]);
+#pragma unroll
           for (int k = 0; k < 3; ++k) {
-            float t[F];
-            TexelLoad<TT, F>::load(sc.tables, int64_t(fl.base[j] + fl.vidx[k]), t);
             const float w = fl.wn[j] * fl.b[k];
 #pragma unroll
-            for (int f = 0; f < F; ++f) v[f] = fmaf(w, t[f], v[f]);
+            for (int f = 0; f < F; ++f) v[f] = fmaf(w, t[k][f], v[f]);
             if (aout) aout[3 * j + k] = fl.base[j] + fl.vidx[k];
           }
         }

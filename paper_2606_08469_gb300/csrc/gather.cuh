@@ -162,9 +162,10 @@ __device__ __forceinline__ void locate_gather_query(const QueryParams& p, const 
 }
 
 // The full query form of one query per thread (encoding kernel): per level
-// full_form_level, then the 8 x 3 vertex features blended into the level's F
-// features, handed to store(l, v).  texel_addr (when requested) receives the
-// 24 entries of each level (neighbour-major, -1 where absent).
+// the eight cells' nodes (carried from the level above by full_descend), the
+// triangle of the vertex map, then the 8 x 3 vertex features blended into the
+// level's F features, handed to store(l, v).  texel_addr (when requested)
+// receives the 24 entries of each level (neighbour-major, -1 where absent).
 template <int F, typename TT, int KP, class Store>
 __device__ __forceinline__ void gather_full_query(const QueryParams& p, const DevScene& sc,
                                                   const int2* tree, const QueryIn& in, int64_t gq,
@@ -172,6 +173,8 @@ __device__ __forceinline__ void gather_full_query(const QueryParams& p, const De
   float ux, uy;
   octa_fold(in.w0, in.w1, in.w2, ux, uy);
   const float xs[3] = {clamp01(in.x0), clamp01(in.x1), clamp01(in.x2)};
+  int nd[8];
+  int pc[3] = {0, 0, 0};
 #pragma unroll 1
   for (int l = 0; l < KP; ++l) {
     float v[F];
@@ -186,7 +189,21 @@ __device__ __forceinline__ void gather_full_query(const QueryParams& p, const De
       continue;
     }
     FullLevel fl;
-    full_form_level(p, sc, tree, xs, ux, uy, l, fl);
+    full_vertex(ux, uy, sc.R[l], fl);
+    int c0[3];
+    float t[3];
+    full_cells(xs, l, c0, t);
+    if (l == 0) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)  // the root is the one cell of level 0
+        nd[j] = (c0[0] + (j & 1) == 0 && c0[1] + ((j >> 1) & 1) == 0 && c0[2] + (j >> 2) == 0)
+                    ? 0 : -1;
+    } else {
+      full_descend(p, sc, tree, pc, c0, l, nd);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) pc[a] = c0[a];
+    full_finish(p, sc, tree, nd, t, sc.R[l], fl);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       if (fl.base[j] < 0) {

@@ -300,10 +300,10 @@ struct FullLevel {
   float b[3];
 };
 
-__device__ __forceinline__ void full_form_level(const QueryParams& p, const DevScene& sc,
-                                                const int2* tree, const float (&xs)[3], float ux,
-                                                float uy, int l, FullLevel& o) {
-  const int V = sc.R[l], N = V - 1;
+// Direction part of one level: the triangle of the vertex map holding u and
+// its barycentric weights (vidx, b of o).
+__device__ __forceinline__ void full_vertex(float ux, float uy, int V, FullLevel& o) {
+  const int N = V - 1;
   const float fN = static_cast<float>(N);
   const float px = __fmul_rn(__fadd_rn(__fmul_rn(ux, 0.5f), 0.5f), fN);
   const float py = __fmul_rn(__fadd_rn(__fmul_rn(uy, 0.5f), 0.5f), fN);
@@ -336,10 +336,13 @@ __device__ __forceinline__ void full_form_level(const QueryParams& p, const DevS
     if (vj == 0 || vj == N) vi = min(vi, N - vi);
     o.vidx[k] = vj * V + vi;
   }
-  const int n = 1 << l;
-  const float fn = static_cast<float>(n);
-  int c0[3];
-  float t[3];
+}
+
+// Spatial part of one level: the lower cell c0 = floor(x 2^l - 1/2) per axis
+// (binary32) and the fractions t.
+__device__ __forceinline__ void full_cells(const float (&xs)[3], int l, int (&c0)[3],
+                                           float (&t)[3]) {
+  const float fn = static_cast<float>(1 << l);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const float pa = __fsub_rn(__fmul_rn(xs[a], fn), 0.5f);
@@ -347,31 +350,33 @@ __device__ __forceinline__ void full_form_level(const QueryParams& p, const DevS
     c0[a] = static_cast<int>(fl);
     t[a] = __fsub_rn(pa, fl);
   }
+}
+
+// First child of node nd (staged tree, else global memory with the child
+// range check), -1 for a leaf.
+__device__ __forceinline__ int full_first_child(const QueryParams& p, const DevScene& sc,
+                                                const int2* tree, int nd) {
+  if (tree) return tree[nd].x;
+  int fc = __ldg(sc.first_child + nd);
+  if (fc >= 0 && fc > sc.num_nodes - 8) {
+    if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
+    fc = -1;
+  }
+  return fc;
+}
+
+// Map bases and renormalised trilinear weights of the eight cells whose
+// nodes are nd (-1: absent or outside the cube).
+__device__ __forceinline__ void full_finish(const QueryParams& p, const DevScene& sc,
+                                            const int2* tree, const int (&nd)[8],
+                                            const float (&t)[3], int V, FullLevel& o) {
   float wsum = 0.f;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const int c[3] = {c0[0] + (j & 1), c0[1] + ((j >> 1) & 1), c0[2] + (j >> 2)};
     o.base[j] = -1;
     o.wn[j] = 0.f;
-    if (c[0] < 0 || c[1] < 0 || c[2] < 0 || c[0] >= n || c[1] >= n || c[2] >= n) continue;
-    int nd = 0;
-    for (int m = 1; m <= l && nd >= 0; ++m) {
-      const int sh = l - m;
-      int fc;
-      if (tree) {
-        fc = tree[nd].x;
-      } else {
-        fc = __ldg(sc.first_child + nd);
-        if (fc >= 0 && fc > sc.num_nodes - 8) {
-          if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
-          fc = -1;
-        }
-      }
-      nd = fc >= 0 ? fc + (((c[0] >> sh) & 1) | (((c[1] >> sh) & 1) << 1) | (((c[2] >> sh) & 1) << 2))
-                   : -1;
-    }
-    if (nd < 0) continue;
-    const int mo = checked_map_base(p, sc, tree ? tree[nd].y : __ldg(sc.map_offset + nd), V);
+    if (nd[j] < 0) continue;
+    const int mo = checked_map_base(p, sc, tree ? tree[nd[j]].y : __ldg(sc.map_offset + nd[j]), V);
     if (mo < 0) continue;
     o.base[j] = mo;
     o.wn[j] = ((j & 1) ? t[0] : 1.f - t[0]) * (((j >> 1) & 1) ? t[1] : 1.f - t[1]) *
@@ -383,7 +388,64 @@ __device__ __forceinline__ void full_form_level(const QueryParams& p, const DevS
   for (int j = 0; j < 8; ++j) o.wn[j] *= inv;
 }
 
+// One level from scratch: the eight descents from the root advance
+// together, one level per step (eight independent node reads in flight).
+__device__ __forceinline__ void full_form_level(const QueryParams& p, const DevScene& sc,
+                                                const int2* tree, const float (&xs)[3], float ux,
+                                                float uy, int l, FullLevel& o) {
+  const int V = sc.R[l];
+  full_vertex(ux, uy, V, o);
+  int c0[3];
+  float t[3];
+  full_cells(xs, l, c0, t);
+  const int n = 1 << l;
+  int nd[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int cx = c0[0] + (j & 1), cy = c0[1] + ((j >> 1) & 1), cz = c0[2] + (j >> 2);
+    nd[j] = (cx < 0 || cy < 0 || cz < 0 || cx >= n || cy >= n || cz >= n) ? -1 : 0;
+  }
+  for (int m = 1; m <= l; ++m) {
+    const int sh = l - m;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (nd[j] < 0) continue;
+      const int fc = full_first_child(p, sc, tree, nd[j]);
+      const int slot = (((c0[0] + (j & 1)) >> sh) & 1) | ((((c0[1] + ((j >> 1) & 1)) >> sh) & 1) << 1) |
+                       ((((c0[2] + (j >> 2)) >> sh) & 1) << 2);
+      nd[j] = fc >= 0 ? fc + slot : -1;
+    }
+  }
+  full_finish(p, sc, tree, nd, t, V, o);
+}
 
+// Level-to-level step of the eight cells' nodes: nd holds the nodes of level
+// l - 1's cells (lower cell pc), and on return those of level l's (lower
+// cell c0).  The parent of a level-l cell c is c >> 1, and since
+// floor(x 2^l - 1/2) >> 1 and (floor(x 2^l - 1/2) + 1) >> 1 both lie in
+// {pc, pc + 1} per axis, every parent is one of level l - 1's eight cells.
+__device__ __forceinline__ void full_descend(const QueryParams& p, const DevScene& sc,
+                                             const int2* tree, const int (&pc)[3],
+                                             const int (&c0)[3], int l, int (&nd)[8]) {
+  const int n = 1 << l;
+  int par[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) par[j] = nd[j];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int cx = c0[0] + (j & 1), cy = c0[1] + ((j >> 1) & 1), cz = c0[2] + (j >> 2);
+    if (cx < 0 || cy < 0 || cz < 0 || cx >= n || cy >= n || cz >= n) {
+      nd[j] = -1;
+      continue;
+    }
+    const int pj = ((cx >> 1) - pc[0]) | (((cy >> 1) - pc[1]) << 1) | (((cz >> 1) - pc[2]) << 2);
+    int pn = par[0];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) pn = pj == i ? par[i] : pn;
+    const int fc = pn >= 0 ? full_first_child(p, sc, tree, pn) : -1;
+    nd[j] = fc >= 0 ? fc + ((cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2)) : -1;
+  }
+}
 
 // Loads of one texel's F features as FP32.
 template <typename TT, int F>
