@@ -132,8 +132,10 @@ typedef struct octa_scene {
  * weights renormalised over the cells present in the octree, in each the
  * barycentric blend of the 3 vertices of the triangle holding the direction
  * on the node's R x R vertex map (R = 2^k + 1, k >= 1; mirrored vertices of
- * the map's edges are one vertex).  Only octa_encode evaluates the second
- * form; the other entry points return OCTA_EUNSUPPORTED for it.           */
+ * the map's edges are one vertex).  octa_encode evaluates the second form
+ * for any decoder; octa_query_fwd, octa_query_bwd and octa_train_fused for
+ * FP32 decoders (weight_dtype F32).  With BF16 decoders, and in
+ * octa_train_step_batched, it returns OCTA_EUNSUPPORTED.                  */
 #define OCTA_FORM_CELL_BILINEAR 0
 #define OCTA_FORM_TRILINEAR_VERTEX 1
 
@@ -162,7 +164,8 @@ int octa_encode(const octa_scene* scenes, int32_t n_scenes, const octa_queries* 
 
 /* octa_query_fwd -- L_hat(x, omega) = exp(W_L relu(... relu(W_1 h))) per
  * query (Eq. 13), h the encoding above.  rgb: device [n][3] float32.
- * node_idx / texel_addr / status as in octa_encode (nullable).
+ * node_idx / texel_addr / status as in octa_encode (nullable; the scenes
+ * of a call share one query form, node_idx only in the cell form).
  * The FP32 path (weight_dtype F32) runs on the CUDA cores in FP32; the
  * BF16 path runs the decoder on the tcgen05 tensor cores (BF16 operands,
  * FP32 accumulation in tensor memory).                                     */
@@ -180,7 +183,9 @@ typedef struct octa_scene_grads {
  * the feature tables and the decoder weights.  Recomputes the forward pass
  * (no activations are kept between calls), back-propagates through the
  * decoder (exp, ReLU masks 1[z > 0]) and scatter-adds weight_k * dh_l into
- * the four texels each present level read.  ACCUMULATES (+=) into
+ * the entries each present level read (4 texels in the cell form; in the
+ * trilinear vertex form 24 vertices, weight = renormalised cell weight x
+ * barycentric weight).  ACCUMULATES (+=) into
  * grads[s].d_tables / d_weights, which the caller zeroes (adam_step zeroes
  * them after each update).  d_rgb: device [n][3] float32.                 */
 int octa_query_bwd(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
