@@ -21,6 +21,12 @@ fusion or reordering of its own:
                     trilinear weights) with Eq. 6 (barycentric on vertex maps)
   mlp_forward       Eq. 13 (decoder; ReLU hidden layers, exp output)
   residual_loss     Eq. 14 with the Monte-Carlo target of Eq. 3 (M = 1)
+  residual_loss_multi  Eq. 14 with Eq. 3's M-sample target
+  trace_rays_f32    Eq. 2's first intersection x'(omega_i) with the synthetic
+                    scene (planes, spheres, the box's inner walls), every
+                    decision in binary32 in a fixed operation order
+  quarter_schedule  Section 4: halve the LHS count and double M after each
+                    quarter of the schedule
   query_backward    derivative of Eq. 13, then of Eq. 10/11 w.r.t. the table
   adam_update       Kingma & Ba (2015), with bias correction
   LossScaler        dynamic loss scaling, Micikevicius et al. (2018)
@@ -720,3 +726,117 @@ def train_step(tree, state, pairs, scaler=None, eps=1e-2, rhs_grad=True,
             state.weights[i], state.m_w[i], state.v_w[i] = adam_update(
                 state.weights[i], dWs[i], state.m_w[i], state.v_w[i], t, lr_mlp)
     return loss, float(np.sqrt(sq)), skipped
+
+
+# ---------------------------------------------------------------------------
+# The paper's training regime: M RHS samples per LHS sample (Eq. 3), the
+# quarter schedule (Section 4) and the secondary hits x'(omega_i) (Eq. 2)
+# ---------------------------------------------------------------------------
+
+def rhs_target(E, w, Ls):
+    """Eq. 3: T = E + (1/M) sum_m w_m * L_hat(x'^m, -omega_i^m), with
+    w_m = f_r |n . omega_i^m| / p(omega_i^m).  E [N][3]; w, Ls [N][M][3]."""
+    E = np.asarray(E, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    Ls = np.asarray(Ls, dtype=np.float64)
+    M = w.shape[1]
+    return E + np.sum(w * Ls, axis=1) / M
+
+
+def residual_loss_multi(Lp, Ls, E, w, eps=1e-2, rhs_grad=True, scale=1.0):
+    """Eq. 14 against the M-sample target of Eq. 3.  Lp, E [N][3]; Ls, w
+    [N][M][3].  The normaliser is detached; with rhs_grad the gradient flows
+    into every secondary radiance through T (dT/dLs_m = w_m / M), without it
+    the target is detached as Eq. 14 prints.  Returns (loss, dLp [N][3],
+    dLs [N][M][3]), gradients of scale * loss; loss = mean over 3N."""
+    Lp = np.asarray(Lp, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    M = w.shape[1]
+    T = rhs_target(E, w, Ls)
+    den = Lp + T + eps
+    r = (Lp - T) / den
+    n = Lp.size
+    loss = float(np.sum(r * r) / n)
+    dLp = scale * 2.0 * r / (n * den)
+    if rhs_grad:
+        dLs = -(dLp[:, None, :] * w) / M
+    else:
+        dLs = np.zeros(w.shape)
+    return loss, dLp, dLs
+
+
+def quarter_schedule(step, total_steps, n0, m0, quarters=4):
+    """(LHS samples, M) of a 0-based step: after every quarter of the
+    schedule the LHS count halves and M doubles (Section 4)."""
+    q = min(quarters - 1, (quarters * step) // total_steps)
+    return n0 >> q, m0 << q
+
+
+def _dot3_f32(a, b):
+    """((a0 b0 + a1 b1) + a2 b2) in binary32, one rounding per operation."""
+    f = np.float32
+    return ((a[..., 0] * b[..., 0]).astype(f) + (a[..., 1] * b[..., 1]).astype(f)).astype(f) + \
+        (a[..., 2] * b[..., 2]).astype(f)
+
+
+def trace_rays_f32(planes, spheres, o, d, t_min):
+    """First intersection of each ray o + t d (t > t_min) with the scene, in
+    binary32 with one rounding per operation in the order written here, so
+    the hit primitive, t and the point are fixed bit for bit.
+
+    planes [P][13]: point p, unit normal n, tangents t1, t2, half-size h
+    (the square patch |(x - p).t1| <= h, |(x - p).t2| <= h; inf: unbounded);
+    spheres [S][4]: centre c, radius r; then the box's six inner walls
+    (x_a = 0, x_a = 1 for a = 0, 1, 2).  Primitive ids: planes 0..P-1,
+    spheres P..P+S-1, walls P+S + 2a + (wall == 1).  Tests run planes,
+    spheres, walls in index order and replace the best hit only on a strictly
+    smaller t.  Plane: t = ((p - o).n) / (d.n).  Sphere (|d| = 1 assumed):
+    b = (o - c).d, disc = b^2 - ((o - c).(o - c) - r^2), t = -b - sqrt(disc)
+    if that exceeds t_min, else -b + sqrt(disc).  Wall: t = (w - o_a) / d_a.
+    The hit point is o + t d per component.  Returns (t [n], prim [n] int32,
+    -1 and t = inf for a miss; hit [n][3]).
+    """
+    f = np.float32
+    o = np.asarray(o, dtype=f)
+    d = np.asarray(d, dtype=f)
+    planes = np.asarray(planes, dtype=f).reshape(-1, 13)
+    spheres = np.asarray(spheres, dtype=f).reshape(-1, 4)
+    tmin = f(t_min)
+    n = len(o)
+    best = np.full(n, np.inf, dtype=f)
+    prim = np.full(n, -1, dtype=np.int32)
+    P, S = len(planes), len(spheres)
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        for k in range(P):
+            pk, nk, t1, t2, h = planes[k, 0:3], planes[k, 3:6], planes[k, 6:9], planes[k, 9:12], planes[k, 12]
+            den = _dot3_f32(d, nk[None, :])
+            num = _dot3_f32((pk[None, :] - o).astype(f), nk[None, :])
+            t = (num / den).astype(f)
+            hit = (o + (t[:, None] * d).astype(f)).astype(f)
+            rel = (hit - pk[None, :]).astype(f)
+            a = _dot3_f32(rel, t1[None, :])
+            b = _dot3_f32(rel, t2[None, :])
+            ok = (den != 0) & (t > tmin) & (t < best) & (np.abs(a) <= h) & (np.abs(b) <= h)
+            best = np.where(ok, t, best)
+            prim = np.where(ok, k, prim).astype(np.int32)
+        for s_ in range(S):
+            c, r = spheres[s_, 0:3], spheres[s_, 3]
+            oc = (o - c[None, :]).astype(f)
+            bq = _dot3_f32(oc, d)
+            cq = (_dot3_f32(oc, oc) - (r * r).astype(f)).astype(f)
+            disc = ((bq * bq).astype(f) - cq).astype(f)
+            sq = np.sqrt(np.maximum(disc, f(0))).astype(f)
+            t0 = (-bq - sq).astype(f)
+            t1v = (-bq + sq).astype(f)
+            t = np.where(t0 > tmin, t0, t1v).astype(f)
+            ok = (disc >= 0) & (t > tmin) & (t < best)
+            best = np.where(ok, t, best)
+            prim = np.where(ok, P + s_, prim).astype(np.int32)
+        for a in range(3):
+            for wi, wall in enumerate((f(0), f(1))):
+                t = ((wall - o[:, a]).astype(f) / d[:, a]).astype(f)
+                ok = (t > tmin) & (t < best)
+                best = np.where(ok, t, best)
+                prim = np.where(ok, P + S + 2 * a + wi, prim).astype(np.int32)
+        hit = (o + (best[:, None] * d).astype(f)).astype(f)
+    return best, prim, hit

@@ -189,6 +189,22 @@ def sample_surface_points(g, prims, n):
     return x, nrm
 
 
+def unit_vectors(g, n):
+    """Uniform directions on S^2 (float64 [n][3])."""
+    return _unit_vectors(g, n)
+
+
+def scene_arrays(prims):
+    """The scene as the ray caster takes it: planes [P][13] float32 (point,
+    unit normal, the two tangents of the patch frame, half-size; inf for an
+    unbounded plane) and spheres [S][4] float32 (centre, radius)."""
+    t1, t2 = _tangent_frame(prims.plane_n)
+    planes = np.concatenate([prims.plane_p, prims.plane_n, t1, t2, prims.plane_half[:, None]],
+                            axis=1).astype(np.float32)
+    spheres = np.concatenate([prims.sphere_c, prims.sphere_r[:, None]], axis=1).astype(np.float32)
+    return np.ascontiguousarray(planes), np.ascontiguousarray(spheres)
+
+
 def hemisphere_directions(g, nrm):
     """Uniform directions on the hemisphere about each normal."""
     w = _unit_vectors(g, len(nrm))
