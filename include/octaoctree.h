@@ -244,6 +244,56 @@ int residual_loss_static(const float* L_p, const float* L_s, const float* E, con
                          const octa_scaler* scaler, double* loss_dev, float* dL_p, float* dL_s,
                          void* stream);
 
+/* ---- the training regime of Section 4: M RHS samples per LHS sample ---- */
+
+/* residual_loss_multi -- Eq. 14 against Eq. 3's M-sample target:
+ * T = E + (1/M) sum_m w_m * L_s,m  (M = n_samples >= 1),
+ * r = (L_p - T) / (L_p + T + eps), loss = sum(r^2) / (3 n_pairs) (FP64
+ * reduction, deterministic for a given launch shape),
+ * dL_p = S * 2 r / (3 n (L_p + T + eps)) and, if rhs_grad,
+ * dL_s,m = -dL_p * w_m / M (the gradient through the target into every
+ * secondary radiance; the normaliser stays detached).  Without rhs_grad the
+ * target is detached as Eq. 14 prints and dL_s (nullable) gets zeros.
+ * S = scaler->scale or 1 when scaler is NULL.  L_p, E, dL_p: device
+ * [n_pairs][3] float32; L_s, w, dL_s: device [n_pairs][M][3] float32 (the M
+ * samples of a pair contiguous).  loss_dev: device double.  Workspace:
+ * octa_workspace_bytes(OCTA_OP_LOSS, n_pairs).  M = 1 gives residual_loss's
+ * values (the loss to FP64 rounding).                                     */
+int residual_loss_multi(const float* L_p, const float* L_s, const float* E, const float* w,
+                        int64_t n_pairs, int32_t n_samples, float eps, int32_t rhs_grad,
+                        const octa_scaler* scaler, double* loss_dev, float* dL_p, float* dL_s,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
+/* The synthetic scene that secondary rays hit (Eq. 2): planes (square
+ * patches |(x - p).t1| <= h, |(x - p).t2| <= h, or unbounded with h = inf),
+ * spheres, and always the six inner walls of the unit box.              */
+#define OCTA_MAX_PRIMS 64
+typedef struct octa_prims {
+  const float* planes;         /* device [n_planes][13]: point p(3), unit    */
+                               /* normal n(3), tangents t1(3), t2(3), h     */
+  const float* spheres;        /* device [n_spheres][4]: centre(3), radius  */
+  int32_t n_planes;            /* 0..OCTA_MAX_PRIMS                         */
+  int32_t n_spheres;           /* 0..OCTA_MAX_PRIMS                         */
+} octa_prims;
+
+/* octa_trace_rays -- x'(omega_i) of Eq. 2: the first intersection with t >
+ * t_min of ray i, origin[i / rays_per_origin] + t dir[i], with the scene.
+ * Every decision is taken in binary32 with one rounding per operation in a
+ * fixed order (plane: t = ((p - o).n) / (d.n), hit on the patch; sphere
+ * with |d| = 1: b = (o - c).d, disc = b^2 - ((o - c).(o - c) - r^2),
+ * t = -b - sqrt(disc) if that exceeds t_min, else -b + sqrt(disc); wall
+ * a at w: t = (w - o_a) / d_a; dot products ((x0 y0 + x1 y1) + x2 y2);
+ * planes, spheres, then walls x0, x1, y0, y1, z0, z1, each replacing the
+ * best hit only on a strictly smaller t), so results are bit-reproducible.
+ * Outputs (device, n_rays rows): hit [n][3] = o + t d per component
+ * (required); query_dir [n][3] = -dir, the secondary query's direction
+ * (nullable); prim [n] int32 = planes 0..P-1, spheres P..P+S-1, walls
+ * P+S+2a+(w == 1), -1 for a miss (nullable); t [n] (nullable, inf for a
+ * miss).  origin / dir: device float32 [.][3].  rays_per_origin >= 1.     */
+int octa_trace_rays(const octa_prims* prims, const float* origin, int32_t rays_per_origin,
+                    const float* dir, int64_t n_rays, float t_min, float* hit,
+                    float* query_dir, int32_t* prim, float* t, void* stream);
+
 /* Training pairs: pair i of scene s (scene_start[s] <= i < scene_start[s+1])
  * is the primary query (x[i], omega[i]) and the secondary query
  * (x2[i], omega2[i]); omega2 is the secondary query's direction itself,

@@ -140,6 +140,14 @@ class octa_step_options(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+OCTA_MAX_PRIMS = 64
+
+
+class octa_prims(C.Structure):
+    _fields_ = [("planes", C.c_void_p), ("spheres", C.c_void_p), ("n_planes", C.c_int32),
+                ("n_spheres", C.c_int32)]
+
+
 # Every symbol the header declares, with its ctypes signature.
 _P = C.c_void_p
 _SIGNATURES = {
@@ -164,6 +172,10 @@ _SIGNATURES = {
                                 _P, C.c_size_t, _P]),
     "residual_loss_static": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_float, C.c_int32, _P, _P,
                                        _P, _P, _P]),
+    "residual_loss_multi": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int32, C.c_float, C.c_int32,
+                                      _P, _P, _P, _P, _P, C.c_size_t, _P]),
+    "octa_trace_rays": (C.c_int, [C.POINTER(octa_prims), _P, C.c_int32, _P, C.c_int64, C.c_float,
+                                  _P, _P, _P, _P, _P]),
     "adam_step": (C.c_int, [C.POINTER(octa_param_group), C.c_int32, C.POINTER(octa_adam_cfg), _P,
                             _P, C.c_size_t, _P]),
     "octa_workspace_bytes": (C.c_size_t, [C.c_int32, C.c_int64]),

@@ -318,6 +318,57 @@ def residual_loss(Lp, Ls, E, w, dLp, dLs, loss_out, ws, eps=1e-2, rhs_grad=True,
             "residual_loss")
 
 
+def residual_loss_multi(Lp, Ls, E, w, dLp, dLs, loss_out, ws, eps=1e-2, rhs_grad=True,
+                        scaler=None, stream=None):
+    """Eq. 14 against Eq. 3's M-sample target: Lp, E, dLp [N][3]; Ls, w, dLs
+    [N][M][3] (dLs may be None without rhs_grad)."""
+    n, M = int(w.shape[0]), int(w.shape[1])
+    L.check(_lib().residual_loss_multi(_ptr(Lp), _ptr(Ls), _ptr(E), _ptr(w), n, M, C.c_float(eps),
+                                       int(bool(rhs_grad)), _ptr(scaler), _ptr(loss_out),
+                                       _ptr(dLp), _ptr(dLs), _ptr(ws), ws.numel(),
+                                       _stream(stream)),
+            "residual_loss_multi")
+
+
+class Prims:
+    """The synthetic scene on the device for octa_trace_rays: planes [P][13]
+    and spheres [S][4] float32 (see inputs.scene_arrays)."""
+
+    def __init__(self, planes, spheres, device="cuda"):
+        dev = torch.device(device)
+        self.planes = torch.as_tensor(planes, dtype=torch.float32).reshape(-1, 13).to(dev).contiguous()
+        self.spheres = torch.as_tensor(spheres, dtype=torch.float32).reshape(-1, 4).to(dev).contiguous()
+
+    def as_c(self):
+        p = L.octa_prims()
+        p.planes = self.planes.data_ptr() if self.planes.numel() else None
+        p.spheres = self.spheres.data_ptr() if self.spheres.numel() else None
+        p.n_planes = int(self.planes.shape[0])
+        p.n_spheres = int(self.spheres.shape[0])
+        return p
+
+
+def octa_trace_rays(prims, origin, direction, rays_per_origin=1, t_min=1e-4, hit=None,
+                    query_dir=None, want_prim=False, want_t=False, stream=None):
+    """x'(omega_i) of Eq. 2 for every ray (origin[i // rays_per_origin],
+    direction[i]); returns (hit, query_dir, prim, t), the last three None
+    unless asked for (query_dir: pass a buffer or True)."""
+    n = int(direction.shape[0])
+    dev = direction.device
+    if hit is None:
+        hit = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    if query_dir is True:
+        query_dir = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    prim = torch.empty(n, dtype=torch.int32, device=dev) if want_prim else None
+    t = torch.empty(n, dtype=torch.float32, device=dev) if want_t else None
+    pc = prims.as_c()
+    L.check(_lib().octa_trace_rays(C.byref(pc), _ptr(origin), int(rays_per_origin),
+                                   _ptr(direction), n, C.c_float(t_min), _ptr(hit),
+                                   _ptr(query_dir), _ptr(prim), _ptr(t), _stream(stream)),
+            "octa_trace_rays")
+    return hit, query_dir, prim, t
+
+
 @dataclass
 class ParamGroup:
     param: torch.Tensor

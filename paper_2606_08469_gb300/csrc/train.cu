@@ -97,6 +97,76 @@ __global__ void __launch_bounds__(kThreads) residual_loss_kernel(
   if (last_block_total(bsum, partials, counter, &total, red)) *loss_dev = total / double(n3);
 }
 
+// Eq. 14 against Eq. 3's M-sample target, one warp per pair: the pair's 3M
+// secondary radiances and weights are read coalesced (lane j takes elements
+// j, j + 32, ... of the pair's [M][3] block), each lane sums w * L_s per
+// channel in FP32 with two partial sums, and the warp reduces the three
+// channel sums by shuffles; the gradients of the secondaries are written
+// back by the lanes that read them.
+__global__ void __launch_bounds__(kThreads) residual_loss_multi_kernel(
+    const float* __restrict__ Lp, const float* __restrict__ Ls, const float* __restrict__ E,
+    const float* __restrict__ w, int64_t n_pairs, int M, float eps, int rhs_grad,
+    const octa_scaler* __restrict__ scaler, double* loss_dev, float* __restrict__ dLp,
+    float* __restrict__ dLs, double* partials, unsigned* counter) {
+  __shared__ double red[kThreads / 32];
+  const float S = scaler ? scaler->scale : 1.f;
+  const float gscale = 2.f * S / static_cast<float>(3 * n_pairs);
+  const float invM = 1.f / static_cast<float>(M);
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = int64_t(gridDim.x) * (kThreads / 32);
+  const int per = 3 * M;  // elements of a pair
+  double acc = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); i < n_pairs;
+       i += warps) {
+    const float* ls = Ls + i * per;
+    const float* ww = w + i * per;
+    float s0[3] = {0.f, 0.f, 0.f}, s1[3] = {0.f, 0.f, 0.f};
+    int e = lane, c = lane % 3;  // element and its channel
+    bool odd = false;
+    for (; e < per; e += 32, c = (c + 2) % 3) {  // 32 = 2 (mod 3)
+      const float v = __ldg(ww + e) * __ldcs(ls + e);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {  // registers only: no indexing by c
+        const float add = c == k ? v : 0.f;
+        if (odd)
+          s1[k] += add;
+        else
+          s0[k] += add;
+      }
+      odd = !odd;
+    }
+    float T[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float v = s0[k] + s1[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      T[k] = E[3 * i + k] + v * invM;
+    }
+    float g[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float lp = Lp[3 * i + k];
+      const float den = lp + T[k] + eps;
+      const float r = (lp - T[k]) / den;
+      if (lane == 0) acc += double(r) * double(r);
+      g[k] = gscale * r / den;
+    }
+    auto pick = [&](int k) { return k == 0 ? g[0] : (k == 1 ? g[1] : g[2]); };
+    if (lane < 3) dLp[3 * i + lane] = pick(lane);
+    if (dLs) {
+      float* dls = dLs + i * per;
+      c = lane % 3;
+      for (e = lane; e < per; e += 32, c = (c + 2) % 3)
+        dls[e] = rhs_grad ? -pick(c) * ww[e] * invM : 0.f;
+    }
+  }
+  const double bsum = block_sum(acc, red);
+  double total;
+  if (last_block_total(bsum, partials, counter, &total, red))
+    *loss_dev = total / double(3 * n_pairs);
+}
+
 struct AdamParams {
   octa_param_group g[OCTA_MAX_GROUPS];
   int32_t vec4[OCTA_MAX_GROUPS];  // group may use 16-byte vector accesses
@@ -303,6 +373,32 @@ extern "C" int residual_loss(const float* L_p, const float* L_s, const float* E,
   residual_loss_kernel<<<blocks, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       L_p, L_s, E, w, n3, eps, rhs_grad, scaler, loss_dev, dL_p, dL_s, partials, counter);
   return launched("residual_loss");
+}
+
+extern "C" int residual_loss_multi(const float* L_p, const float* L_s, const float* E,
+                                   const float* w, int64_t n_pairs, int32_t n_samples, float eps,
+                                   int32_t rhs_grad, const octa_scaler* scaler, double* loss_dev,
+                                   float* dL_p, float* dL_s, void* workspace,
+                                   size_t workspace_bytes, void* stream) {
+  clear_error();
+  if (n_pairs < 1) return fail(OCTA_EINVAL, "n_pairs must be >= 1");
+  if (n_samples < 1) return fail(OCTA_EINVAL, "n_samples must be >= 1");
+  if (n_pairs > (int64_t(1) << 40) / n_samples) return fail(OCTA_ERANGE, "n_pairs * n_samples too large");
+  if (!L_p || !L_s || !E || !w || !loss_dev || !dL_p)
+    return fail(OCTA_EINVAL, "NULL array argument");
+  if (rhs_grad && !dL_s) return fail(OCTA_EINVAL, "dL_s must be non-NULL when rhs_grad");
+  if (!(eps > 0.f)) return fail(OCTA_EINVAL, "eps must be > 0");
+  int rc = check_workspace(workspace, workspace_bytes);
+  if (rc) return rc;
+  constexpr int kWarps = kThreads / 32;
+  const int blocks = static_cast<int>(std::min<int64_t>(
+      {(n_pairs + kWarps - 1) / kWarps, int64_t(kMaxBlocks), 4LL * sm_count()}));
+  double* partials = static_cast<double*>(workspace);
+  unsigned* counter = reinterpret_cast<unsigned*>(static_cast<char*>(workspace) + kPartialBytes);
+  residual_loss_multi_kernel<<<blocks, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      L_p, L_s, E, w, n_pairs, n_samples, eps, rhs_grad, scaler, loss_dev, dL_p, dL_s, partials,
+      counter);
+  return launched("residual_loss_multi");
 }
 
 extern "C" int adam_step(const octa_param_group* groups, int32_t n_groups,

@@ -245,6 +245,45 @@ def training_pairs(seed, n, n_planes=8, n_spheres=8):
     return TrainingPairs(f32(x), f32(om), f32(x2), f32(om2), f32(E), f32(w))
 
 
+@dataclass
+class TrainingSamples:
+    """LHS samples with M sampled incident directions each (Eq. 3); the
+    secondary positions x'^m come from ray casting the scene (Eq. 2)."""
+    x: np.ndarray        # [n][3] float32, LHS position on a primitive
+    omega: np.ndarray    # [n][3] float32, outgoing direction
+    E: np.ndarray        # [n][3] float32, emitted radiance
+    omega_i: np.ndarray  # [n][M][3] float32, incident directions (hemisphere about the normal)
+    w: np.ndarray        # [n][M][3] float32, f_r |n.omega_i| / p(omega_i)
+    planes: np.ndarray   # scene_arrays(prims)
+    spheres: np.ndarray
+
+    @property
+    def n(self):
+        return len(self.x)
+
+    @property
+    def M(self):
+        return self.omega_i.shape[1]
+
+
+def training_samples(seed, n, M, n_planes=8, n_spheres=8):
+    """The training batch of Section 4's regime: n LHS samples as in
+    training_pairs (16 unbounded planes and spheres, omega on the hemisphere,
+    5% emissive points), each with M incident directions drawn uniformly on
+    the hemisphere about the point's normal and U[0,1]^3 weights."""
+    g = rng(seed)
+    prims = make_primitives(g, n_planes, n_spheres)
+    x, nrm = sample_surface_points(g, prims, n)
+    om = hemisphere_directions(g, nrm)
+    emissive = g.random(n) < 0.05
+    E = g.random((n, 3)) * emissive[:, None]
+    oi = hemisphere_directions(g, np.repeat(nrm, M, axis=0)).reshape(n, M, 3)
+    w = g.random((n, M, 3))
+    planes, spheres = scene_arrays(prims)
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    return TrainingSamples(f32(x), f32(om), f32(E), f32(oi), f32(w), planes, spheres)
+
+
 # ---------------------------------------------------------------------------
 # G-buffer for the real-time inference workload
 # ---------------------------------------------------------------------------

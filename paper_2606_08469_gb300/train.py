@@ -149,3 +149,86 @@ class TrainStep:
             self.loss_and_grad(stream)
             self.backward(stream)
         self.optimizer(stream)
+
+
+def quarter_schedule(step, total_steps, n0, m0, quarters=4):
+    """(LHS samples, RHS samples M) of 0-based step `step` of `total_steps`:
+    the LHS count halves and M doubles after every quarter (Section 4)."""
+    if total_steps < 1 or step < 0:
+        raise ValueError("need total_steps >= 1 and step >= 0")
+    q = min(quarters - 1, (quarters * step) // total_steps)
+    return n0 >> q, m0 << q
+
+
+class MultiSampleStep:
+    """Training step of Section 4's regime on one scene: every LHS sample
+    (x, omega) is supervised by Eq. 3's target over M RHS samples.
+
+    Per step, all through the C ABI: octa_trace_rays finds the secondary
+    hits x'^m of the N*M sampled directions (Eq. 2) and writes them, with
+    the query directions -omega_i^m, after the N primaries; one
+    octa_query_fwd evaluates the N + N*M queries; residual_loss_multi forms
+    the target and Eq. 14; octa_query_bwd back-propagates the primaries
+    (and, with rhs_grad, the secondaries); adam_step updates.
+    samples: dict of device tensors x [N][3], omega [N][3], E [N][3],
+    omega_i [N][M][3], w [N][M][3]; prims: api.Prims of the scene."""
+
+    def __init__(self, state, prims, samples, eps=1e-2, rhs_grad=False, lr_tables=1e-2,
+                 lr_mlp=1e-3, scale=2.0 ** 15, growth_interval=2000, t_min=1e-4, device="cuda"):
+        dev = torch.device(device)
+        self.state, self.scene, self.prims = state, state.scene, prims
+        N, M = int(samples["omega_i"].shape[0]), int(samples["omega_i"].shape[1])
+        self.N, self.M = N, M
+        total = N + N * M
+        self.X = torch.empty((total, 3), dtype=torch.float32, device=dev)
+        self.Om = torch.empty((total, 3), dtype=torch.float32, device=dev)
+        self.X[:N].copy_(samples["x"])
+        self.Om[:N].copy_(samples["omega"])
+        self.dirs = samples["omega_i"].reshape(N * M, 3).to(dev).contiguous()
+        self.E = samples["E"].to(dev).contiguous()
+        self.w = samples["w"].to(dev).contiguous()
+        self.rgb = torch.empty((total, 3), dtype=torch.float32, device=dev)
+        self.d_rgb = torch.zeros((total, 3), dtype=torch.float32, device=dev)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.scaler = api.make_scaler(scale, growth_interval, device=dev)
+        self.ws_loss = api.workspace(L.OCTA_OP_LOSS, N, device=dev)
+        self.ws_adam = api.workspace(L.OCTA_OP_ADAM, 0, device=dev)
+        self.eps, self.rhs_grad, self.t_min = eps, rhs_grad, t_min
+        self.groups = state.groups(lr_tables, lr_mlp)
+        self.grads = [(state.grad_t, state.grad_w)]
+
+    @property
+    def queries_per_step(self):
+        return self.N * (1 + self.M)
+
+    def trace(self, stream=None):
+        N = self.N
+        api.octa_trace_rays(self.prims, self.X[:N], self.dirs, self.M, self.t_min,
+                            hit=self.X[N:], query_dir=self.Om[N:], stream=stream)
+
+    def forward(self, stream=None):
+        api.octa_query_fwd(self.scene, self.X, self.Om, rgb=self.rgb, stream=stream)
+
+    def loss_and_grad(self, stream=None):
+        N, M = self.N, self.M
+        api.residual_loss_multi(self.rgb[:N], self.rgb[N:].view(N, M, 3), self.E, self.w,
+                                self.d_rgb[:N], self.d_rgb[N:].view(N, M, 3), self.loss,
+                                self.ws_loss, self.eps, self.rhs_grad, self.scaler, stream=stream)
+
+    def backward(self, stream=None):
+        if self.rhs_grad:
+            api.octa_query_bwd(self.scene, self.X, self.Om, self.d_rgb, self.grads, stream=stream)
+        else:  # the target is detached: only the primaries carry gradient
+            N = self.N
+            api.octa_query_bwd(self.scene, self.X[:N], self.Om[:N], self.d_rgb[:N], self.grads,
+                               stream=stream)
+
+    def optimizer(self, stream=None):
+        api.adam_step(self.groups, self.scaler, self.ws_adam, stream=stream)
+
+    def step(self, stream=None):
+        self.trace(stream)
+        self.forward(stream)
+        self.loss_and_grad(stream)
+        self.backward(stream)
+        self.optimizer(stream)

@@ -7,7 +7,7 @@ import torch
 
 from . import api
 from . import inputs as I
-from .train import SceneState, TrainStep
+from .train import MultiSampleStep, SceneState, TrainStep
 
 _TORCH_DT = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
 
@@ -120,3 +120,19 @@ def queries_for(cfg, n=None):
 
 def to_dev(a, device="cuda"):
     return torch.from_numpy(np.ascontiguousarray(a)).to(device)
+
+
+def multi_sample_step_for(cfg, n, M, device="cuda", precision=None, seed=None, **kw):
+    """MultiSampleStep of a 'pairs' workload's scene parameters on n LHS
+    samples with M RHS samples each (training_samples batch; secondary hits
+    ray cast on the device every step)."""
+    tree, tables, weights = host_params(cfg)
+    tdt, wdt = table_dtype(cfg), weight_dtype(cfg)
+    if precision == "f32":
+        tdt = wdt = torch.float32
+    st = SceneState(tree, tables, weights, tdt, wdt, device)
+    smp = I.training_samples(cfg.seed("queries") if seed is None else seed, n, M)
+    dev = torch.device(device)
+    arrays = {k: torch.from_numpy(getattr(smp, k)).to(dev) for k in ("x", "omega", "E", "omega_i", "w")}
+    prims = api.Prims(smp.planes, smp.spheres, device=dev)
+    return MultiSampleStep(st, prims, arrays, device=device, **kw), (tree, tables, weights, smp)

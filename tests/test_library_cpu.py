@@ -42,7 +42,8 @@ def test_struct_sizes_match_header(lib):
     """The ctypes mirrors have the C layout (checked through a sizing call)."""
     from paper_2606_08469_gb300 import _lib as L
     assert C.sizeof(L.octa_tree_desc) == 4 + 4 + 8 + 4 * 16 + 4 * 17 + 4 + 8 * 17
-    assert lib.octa_abi_version() == 3
+    assert lib.octa_abi_version() == 4
+    assert C.sizeof(L.octa_prims) == 8 + 8 + 4 + 4
     assert C.sizeof(L.octa_pairs) == 6 * 8 + 8 + 8 * 17 + 8 * 16
 
 

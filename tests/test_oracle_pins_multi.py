@@ -215,3 +215,13 @@ def test_trace_matches_brute_force_march():
         assert abs(float(t[i]) - tm) <= 1e-5 * max(1.0, tm), (i, t[i], tm)
         np.testing.assert_allclose(hit[i], o[i] + t[i] * d[i], rtol=0, atol=1e-6)
     assert checked >= 120
+
+
+def test_host_quarter_schedule_matches_oracle():
+    """The library's host-side schedule against the oracle's."""
+    from paper_2606_08469_gb300.train import quarter_schedule
+    for total in (1, 3, 4, 10, 100, 20000):
+        for s in sorted({0, 1, total // 4, total // 2, total - 1, max(0, total - 2)}):
+            assert quarter_schedule(s, total, 65536, 32) == O.quarter_schedule(s, total, 65536, 32)
+    with pytest.raises(ValueError):
+        quarter_schedule(0, 0, 1, 1)
