@@ -365,6 +365,38 @@ def train_full_leg(dev, flush, stream, steps):
     return out
 
 
+def multi_rhs_leg(dev, flush, stream, steps):
+    """Section 4's training regime on config [2]'s scene (depth-8 octree,
+    FP16 tables, BF16 decoder 72-64-64-64-3): LHS samples with M RHS samples
+    each, the quarter schedule from 65,536 LHS x M = 32 to 8,192 x 256
+    (2,162,688 down to 2,105,344 queries a step).  A step: octa_trace_rays
+    (secondary hits of the N*M sampled directions), one forward over all
+    queries, residual_loss_multi, the backward of the primaries (the target
+    detached, as Eq. 14 prints), Adam."""
+    from paper_2606_08469_gb300 import inputs as I
+    from paper_2606_08469_gb300 import workloads as WL
+    from paper_2606_08469_gb300.train import quarter_schedule
+    cfg = I.CONFIGS[2]
+    out = {"workload": "config[2] scene, BF16 decoder; quarter schedule 65536 x 32 -> 8192 x 256, "
+                       "secondary hits ray cast each step, target detached"}
+    for q in range(4):
+        n, M = quarter_schedule(q, 4, 65536, 32)
+        step, _ = WL.multi_sample_step_for(cfg, n, M, device=dev)
+        for _ in range(3):
+            step.step()
+        stream.synchronize()
+        t = _timed(step.step, steps, flush, stream)
+        nq = step.queries_per_step
+        leg = {"lhs": n, "M": M, "queries": nq, "ms_per_step": round(t, 4),
+               "Mq/s": round(nq / t / 1e3, 1), "loss": float(step.loss.item())}
+        for part in ("trace", "forward", "loss_and_grad", "backward", "optimizer"):
+            leg[part + "_ms"] = round(_timed(getattr(step, part), steps, flush, stream), 4)
+        leg["trace_Grays/s"] = round(n * M / leg["trace_ms"] / 1e6, 2)
+        out[f"quarter{q}"] = leg
+        del step
+    return out
+
+
 def encode_stress_leg(dev, flush, stream, steps, peaks):
     """The encoding alone with tables larger than L2: 2^20 uniform random
     queries (x in the unit cube, omega on the sphere) on a dense octree of
@@ -523,7 +555,7 @@ def job_rate(units_per_rank, world, steps, total_ms):
 
 
 LEGS = ("bf16_vs_f32", "inference", "small_forward", "encode", "encode_full", "encode_stress",
-        "train_full", "batched")
+        "train_full", "multi_rhs", "batched")
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
 # launch (262,144 pairs) of the FP32 fused training pass, from one ncu
@@ -551,6 +583,7 @@ def run_legs(args, names):
            "encode_full": lambda: encode_full_leg(dev, flush, stream, steps, peaks),
            "encode_stress": lambda: encode_stress_leg(dev, flush, stream, steps, peaks),
            "train_full": lambda: train_full_leg(dev, flush, stream, steps),
+           "multi_rhs": lambda: multi_rhs_leg(dev, flush, stream, steps),
            "batched": lambda: batched_leg(dev, flush, stream, steps)}
     print(json.dumps({n: fns[n]() for n in names}), flush=True)
 
@@ -729,6 +762,7 @@ def run_ours(args):
             out["encode_stress"] = encode_stress_leg(dev, flush, stream, max(5, args.steps // 2),
                                                      peaks)
             out["train_full"] = train_full_leg(dev, flush, stream, max(5, args.steps // 2))
+            out["multi_rhs"] = multi_rhs_leg(dev, flush, stream, max(5, args.steps // 2))
             out["batched"] = batched_leg(dev, flush, stream, max(5, args.steps // 2))
         out["cpu_baseline"] = cpu_baseline() if not args.no_cpu else None
         print(json.dumps(out), flush=True)
