@@ -284,6 +284,11 @@ def encode_leg(dev, flush, stream, steps, peaks):
     for _ in range(3):
         fn()
     t = _timed(fn, steps, flush, stream)
+    rgb = torch.empty((len(x), 3), dtype=torch.float32, device=dev)
+    fwd = lambda: api.octa_query_fwd(sc, X, Om, rgb=rgb)
+    for _ in range(3):
+        fwd()
+    t_fwd = _timed(fwd, steps, flush, stream)
     table_bytes = tree.num_texels * cfg.F * 2
     alg = len(x) * (24 + 2 * W) + table_bytes
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -329,6 +334,11 @@ def encode_full_leg(dev, flush, stream, steps, peaks):
     for _ in range(3):
         fn()
     t = _timed(fn, steps, flush, stream)
+    rgb = torch.empty((len(x), 3), dtype=torch.float32, device=dev)
+    fwd = lambda: api.octa_query_fwd(sc, X, Om, rgb=rgb)
+    for _ in range(3):
+        fwd()
+    t_fwd = _timed(fwd, steps, flush, stream)
     table_bytes = tree.num_texels * cfg.F * 2
     alg = len(x) * (24 + 2 * W) + table_bytes
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -338,7 +348,9 @@ def encode_full_leg(dev, flush, stream, steps, peaks):
             "ms": round(t, 4), "Mq/s": round(len(x) / t / 1e3, 1),
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(ach / peak, 4), "algorithmic_bytes": alg,
-                         "per_query": f"24 B in + {2 * W} B out, table {table_bytes} B once"}}
+                         "per_query": f"24 B in + {2 * W} B out, table {table_bytes} B once"},
+            "tc_forward_ms": round(t_fwd, 4),
+            "tc_forward": "octa_query_fwd in the full form, BF16 decoder 72-64-64-3 on the tensor cores"}
 
 
 def train_full_leg(dev, flush, stream, steps):

@@ -92,30 +92,37 @@ __device__ void load_weights_bf16(const DevScene& sc, uint8_t* smem, int nthread
 }
 
 // Locate and gather of one query per thread into its row of the layer-0
-// operand tile (canonical K-major, one 16-byte store per level for F = 8).
-template <class S, typename TT, int TPQ = 1>
+// operand tile (canonical K-major, one 16-byte store per level for F = 8);
+// FULL: the trilinear vertex form (Eq. 10 with Eq. 6, one thread a query).
+template <class S, typename TT, int TPQ = 1, bool FULL = false>
 __device__ __forceinline__ void locate_gather_bf16(const QueryParams& p, const DevScene& sc,
                                                    const int2* tree, const QueryIn& in, int64_t gq,
                                                    bool valid, int par, uint8_t* act, int* base_sm,
                                                    float* u_sm, int q) {
   constexpr int F = S::F;
-  locate_gather_query<F, TT, S::KPAD, true, TPQ>(
-      p, sc, tree, in, gq, valid, par, base_sm, u_sm, q, NT, [&](int l, const float (&v)[F]) {
-        uint8_t* dst = act + kmajor_offset(q, l * F, S::WP);
-        if constexpr (F == 8) {
-          uint4 o;
-          o.x = pack_bf16x2(v[0], v[1]);
-          o.y = pack_bf16x2(v[2], v[3]);
-          o.z = pack_bf16x2(v[4], v[5]);
-          o.w = pack_bf16x2(v[6], v[7]);
-          *reinterpret_cast<uint4*>(dst) = o;
-        } else {
-          uint2 o;
-          o.x = pack_bf16x2(v[0], v[1]);
-          o.y = pack_bf16x2(v[2], v[3]);
-          *reinterpret_cast<uint2*>(dst) = o;
-        }
-      });
+  auto store = [&](int l, const float (&v)[F]) {
+    uint8_t* dst = act + kmajor_offset(q, l * F, S::WP);
+    if constexpr (F == 8) {
+      uint4 o;
+      o.x = pack_bf16x2(v[0], v[1]);
+      o.y = pack_bf16x2(v[2], v[3]);
+      o.z = pack_bf16x2(v[4], v[5]);
+      o.w = pack_bf16x2(v[6], v[7]);
+      *reinterpret_cast<uint4*>(dst) = o;
+    } else {
+      uint2 o;
+      o.x = pack_bf16x2(v[0], v[1]);
+      o.y = pack_bf16x2(v[2], v[3]);
+      *reinterpret_cast<uint2*>(dst) = o;
+    }
+  };
+  if constexpr (FULL) {
+    static_assert(TPQ == 1, "the full form gathers one query per thread");
+    gather_full_query<F, TT, S::KPAD>(p, sc, tree, in, gq, valid, store);
+  } else {
+    locate_gather_query<F, TT, S::KPAD, true, TPQ>(p, sc, tree, in, gq, valid, par, base_sm, u_sm,
+                                                   q, NT, store);
+  }
 }
 
 // Issue the MMAs of one layer (single thread) and commit to the mbarrier.
@@ -136,7 +143,7 @@ __device__ __forceinline__ void issue_layer(int layer, uint32_t act_sa, uint32_t
 // gathers the levels l with l % TPQ == par and, in the epilogues, the
 // column range par of the hidden layer), all of them waiting on the MMAs of
 // the tile; persistent over tiles.
-template <class S, typename TT, int TPQ>
+template <class S, typename TT, int TPQ, bool FULL = false>
 __global__ void __launch_bounds__(NT * TPQ, 4)
     fwd_kernel(const __grid_constant__ QueryParams p) {
   constexpr int NTF = NT * TPQ;         // threads per CTA
@@ -184,7 +191,8 @@ __global__ void __launch_bounds__(NT * TPQ, 4)
     }
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * NT;
     const int nq = static_cast<int>(sc.q_end - q0 < NT ? sc.q_end - q0 : int64_t(NT));
-    locate_gather_bf16<S, TT, TPQ>(p, sc, tree, in, q0 + q, q < nq, par, act, nullptr, nullptr, q);
+    locate_gather_bf16<S, TT, TPQ, FULL>(p, sc, tree, in, q0 + q, q < nq, par, act, nullptr,
+                                         nullptr, q);
     fence_proxy_async();
     __syncthreads();
 
@@ -899,9 +907,9 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
 
 namespace {
 
-template <class S, typename TT, int TPQ>
+template <class S, typename TT, int TPQ, bool FULL = false>
 int launch_fwd_tpq(const QueryParams& p, const octa_tuning& tu, cudaStream_t stream) {
-  auto kern = fwd_kernel<S, TT, TPQ>;
+  auto kern = fwd_kernel<S, TT, TPQ, FULL>;
   int per_sm = 0;
   int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, NT * TPQ,
                               static_cast<int>(S::TMEM_COLS), &per_sm);
@@ -920,6 +928,8 @@ template <class S, typename TT>
 int launch_fwd(const QueryParams& p, cudaStream_t stream) {
   if (p.n_tiles == 0) return OCTA_OK;
   const octa_tuning tu = tuning_snapshot();
+  if (p.sc[0].query_form == OCTA_FORM_TRILINEAR_VERTEX)  // all scenes of a call share it
+    return launch_fwd_tpq<S, TT, 1, true>(p, tu, stream);
   return tu.fwd_threads_per_query == 2 ? launch_fwd_tpq<S, TT, 2>(p, tu, stream)
                                        : launch_fwd_tpq<S, TT, 1>(p, tu, stream);
 }

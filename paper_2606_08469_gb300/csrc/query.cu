@@ -98,8 +98,9 @@ bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u
 }  // namespace
 
 // Validates scenes + queries and fills the kernel parameter block.
-// full_form: where the trilinear vertex form is accepted (the encoding for
-// any decoder; the query and training passes for FP32 decoders).
+// full_form: where the trilinear vertex form is accepted (the encoding and
+// the forward for any decoder; the backward and training passes for FP32
+// decoders).
 enum FullForm { kFullNo = 0, kFullFp32 = 1, kFullAny = 2 };
 int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
                        const octa_scene_grads* grads, QueryParams& p, int full_form = kFullNo) {
@@ -155,8 +156,8 @@ int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_qu
       return fail(OCTA_EINVAL, "scene %d: unknown query_form %d", s, c.query_form);
     if (c.query_form == OCTA_FORM_TRILINEAR_VERTEX) {
       if (full_form == kFullNo || (full_form == kFullFp32 && c.weight_dtype != OCTA_F32))
-        return fail(OCTA_EUNSUPPORTED, "scene %d: the trilinear vertex form is evaluated by "
-                                       "octa_encode and the FP32 decoder passes only", s);
+        return fail(OCTA_EUNSUPPORTED, "scene %d: the trilinear vertex form: backward and "
+                                       "training passes need FP32 decoders", s);
       for (int l = 0; l < c.num_levels; ++l) {
         const int n = c.R[l] - 1;  // cells a side: a power of two >= 2
         if (n < 2 || (n & (n - 1)))
@@ -301,7 +302,7 @@ extern "C" int octa_query_fwd(const octa_scene* scenes, int32_t n_scenes, const 
                               int32_t* status, void* stream) {
   clear_error();
   QueryParams p;
-  int rc = build_query_params(scenes, n_scenes, q, nullptr, p, kFullFp32);
+  int rc = build_query_params(scenes, n_scenes, q, nullptr, p, kFullAny);
   if (rc) return rc;
   rc = check_one_form(scenes, n_scenes, node_idx);
   if (rc) return rc;

@@ -122,9 +122,12 @@ def test_full_form_argument_errors():
         A.octa_query_fwd(sc, dev(x), dev(w), want_nodes=True)
     weights = [dev(W).to(torch.bfloat16) for W in I.make_mlp(1, [12, 32, 32, 3])]
     sb = A.Scene(tree, sc.tables, weights, device=DEV, query_form=L.OCTA_FORM_TRILINEAR_VERTEX)
-    with pytest.raises(L.OctaError):                      # BF16 decoders: cell form only
-        A.octa_query_fwd(sb, dev(x), dev(w))
-    A.octa_encode(sb, dev(x), dev(w))                     # the encoding takes either decoder
+    A.octa_encode(sb, dev(x), dev(w))                     # the encoding and the forward take
+    A.octa_query_fwd(sb, dev(x), dev(w))                  # either decoder
+    dT = torch.zeros((tree.num_texels, 4), device=DEV)
+    dW = torch.zeros(sb.weights.shape, device=DEV)
+    with pytest.raises(L.OctaError):                      # BF16 backward: cell form only
+        A.octa_query_bwd(sb, dev(x), dev(w), torch.ones((10, 3), device=DEV), [(dT, dW)])
 
 
 # ------------------------------------------- FP32 decoder passes (FP32 engine)
@@ -249,3 +252,30 @@ def test_full_form_train_step_fused_matches_unfused():
     b.step()
     torch.cuda.synchronize()
     assert np.isfinite(a.loss.item()) and np.isfinite(b.loss.item())
+
+
+@pytest.mark.parametrize("tdt", [torch.float16, torch.float32])
+def test_full_form_tensor_core_forward(tdt):
+    """The tcgen05 forward (BF16 decoder 48-64-64-3) in the full form on a
+    ragged batch: the 24 entries of every level bit-exact, radiance within
+    the BF16 path's 1e-2 normwise bound against the FP64 oracle run on the
+    FP32 master weights (features and weights rounded to BF16 on the GPU)."""
+    from paper_2606_08469_gb300 import _lib as L
+    from paper_2606_08469_gb300 import api as A
+    seed, depth, V, F = 1301, 5, [17, 17, 9, 9, 5, 3], 8
+    tree = A.octree_build(seed, depth, 0.6, V)
+    ot = O.build_tree(seed, depth, 0.6, V)
+    tables = I.make_tables(seed + 1, tree.num_texels, F, 0.3)
+    if tdt == torch.float16:
+        tables = tables.astype(np.float16).astype(np.float32)
+    weights = I.make_mlp(seed + 2, [(depth + 1) * F, 64, 64, 3])
+    sc = A.Scene(tree, dev(tables).to(tdt).contiguous(),
+                 [dev(W).to(torch.bfloat16) for W in weights], device=DEV,
+                 query_form=L.OCTA_FORM_TRILINEAR_VERTEX)
+    x, w = I.uniform_queries(seed + 3, 3001)
+    rgb, _, addr = A.octa_query_fwd(sc, dev(x), dev(w), want_addr=True)
+    ref, enc = O.query_forward(ot, tables, weights, x, w, form="full")
+    np.testing.assert_array_equal(addr.cpu().numpy(), enc.addr.reshape(len(x), depth + 1, 24))
+    err = np.linalg.norm(rgb.cpu().numpy() - ref) / np.linalg.norm(ref)
+    print("BF16 full-form forward, normwise error", err)
+    assert err <= 1e-2
