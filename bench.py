@@ -354,26 +354,33 @@ def encode_full_leg(dev, flush, stream, steps, peaks):
 
 
 def train_full_leg(dev, flush, stream, steps):
-    """The headline workload (config [1], 262,144 pairs, FP32) trained in the
-    full query form: the FP32 engine's fused pass + Adam on vertex maps of
-    side R + 1 (33, 33, 17, 17, 9, 9, 9), against the same step in the cell
-    form; 8 x 3 vertex loads (and scatters) per level against 4."""
+    """Training in the full query form on vertex maps of side R + 1 against
+    the same step in the cell form (8 x 3 vertex loads and scatters per level
+    against 4): the headline workload (config [1], 262,144 pairs, the FP32
+    engine's fused pass + Adam) and config [2] (1,048,576 pairs, the BF16
+    tensor-core fused pass + Adam)."""
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[1]
     out = {"workload": "config[1] training step, FP32, 262144 pairs = 524288 queries, fused FP32 "
+                       "pass + Adam; config[2] training step, BF16, 1048576 pairs, fused tensor-core "
                        "pass + Adam: trilinear vertex form vs cell form"}
-    for form in ("cell", "full"):
-        step, _ = WL.train_step_for(cfg, device=dev, precision="f32", fused=True, query_form=form)
-        for _ in range(3):
-            step.step()
-        stream.synchronize()
-        t = _timed(step.step, steps, flush, stream)
-        t_pass = _timed(step.fused_pass, steps, flush, stream)
-        out[form] = {"ms_per_step": round(t, 4), "fused_pass_ms": round(t_pass, 4),
-                     "Mq/s": round(2 * cfg.n / t / 1e3, 2), "loss": float(step.loss.item())}
-        del step
-    out["full_over_cell_time"] = round(out["full"]["ms_per_step"] / out["cell"]["ms_per_step"], 3)
+    for ci, prec in ((1, "f32"), (2, None)):
+        cfg = I.CONFIGS[ci]
+        tag = "f32_cfg1" if prec else "bf16_cfg2"
+        for form in ("cell", "full"):
+            step, _ = WL.train_step_for(cfg, device=dev, precision=prec, fused=True,
+                                        query_form=form)
+            for _ in range(3):
+                step.step()
+            stream.synchronize()
+            t = _timed(step.step, steps, flush, stream)
+            t_pass = _timed(step.fused_pass, steps, flush, stream)
+            out[f"{tag}_{form}"] = {"ms_per_step": round(t, 4), "fused_pass_ms": round(t_pass, 4),
+                                    "Mq/s": round(2 * cfg.n / t / 1e3, 2),
+                                    "loss": float(step.loss.item())}
+            del step
+        out[f"{tag}_full_over_cell_time"] = round(
+            out[f"{tag}_full"]["ms_per_step"] / out[f"{tag}_cell"]["ms_per_step"], 3)
     return out
 
 

@@ -161,33 +161,20 @@ __device__ __forceinline__ void locate_gather_query(const QueryParams& p, const 
       *reinterpret_cast<int4*>(p.texel_addr + (gq * p.kmax_out + l) * 4) = make_int4(-1, -1, -1, -1);
 }
 
-// The full query form of one query per thread (encoding kernel): per level
-// the eight cells' nodes (carried from the level above by full_descend), the
-// triangle of the vertex map, then the 8 x 3 vertex features blended into the
-// level's F features, handed to store(l, v).  texel_addr (when requested)
-// receives the 24 entries of each level (neighbour-major, -1 where absent).
-template <int F, typename TT, int KP, class Store>
-__device__ __forceinline__ void gather_full_query(const QueryParams& p, const DevScene& sc,
-                                                  const int2* tree, const QueryIn& in, int64_t gq,
-                                                  bool valid, Store&& store) {
-  float ux, uy;
-  octa_fold(in.w0, in.w1, in.w2, ux, uy);
-  const float xs[3] = {clamp01(in.x0), clamp01(in.x1), clamp01(in.x2)};
+// The levels 0 .. min(K, KP) - 1 of one query in the full form, the eight
+// cells' nodes carried from each level to the next (full_descend): per level
+// the triangle of the vertex map and the cells' map bases and renormalised
+// weights, handed to fn(l, fl).  UNROLL unrolls the level loop (fn may then
+// index register arrays by l).
+template <int KP, bool UNROLL, class Fn>
+__device__ __forceinline__ void visit_full_levels(const QueryParams& p, const DevScene& sc,
+                                                  const int2* tree, const float (&xs)[3], float ux,
+                                                  float uy, Fn&& fn) {
   int nd[8];
   int pc[3] = {0, 0, 0};
-#pragma unroll 1
+#pragma unroll(UNROLL ? KP : 1)
   for (int l = 0; l < KP; ++l) {
-    float v[F];
-#pragma unroll
-    for (int f = 0; f < F; ++f) v[f] = 0.f;
-    int32_t* aout = (p.texel_addr && valid && l < p.kmax_out)
-                        ? p.texel_addr + (gq * p.kmax_out + l) * 24 : nullptr;
-    if (!valid || l >= sc.K) {
-      if (aout)
-        for (int k = 0; k < 24; ++k) aout[k] = -1;
-      store(l, v);
-      continue;
-    }
+    if (l >= sc.K) break;
     FullLevel fl;
     full_vertex(ux, uy, sc.R[l], fl);
     int c0[3];
@@ -204,27 +191,63 @@ __device__ __forceinline__ void gather_full_query(const QueryParams& p, const De
 #pragma unroll
     for (int a = 0; a < 3; ++a) pc[a] = c0[a];
     full_finish(p, sc, tree, nd, t, sc.R[l], fl);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (fl.base[j] < 0) {
-        if (aout)
-          for (int k = 0; k < 3; ++k) aout[3 * j + k] = -1;
-        continue;
-      }
-      TexelRaw<TT, F> tx[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) tx[k].load(sc.tables, uint32_t(fl.base[j] + fl.vidx[k]));
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float w = fl.wn[j] * fl.b[k];
-#pragma unroll
-        for (int f = 0; f < F; ++f) v[f] = fmaf(w, tx[k].get(f), v[f]);
-        if (aout) aout[3 * j + k] = fl.base[j] + fl.vidx[k];
-      }
-    }
-    store(l, v);
+    fn(l, fl);
   }
-  if (p.texel_addr && valid)
+}
+
+// The full query form of one query per thread (encoding and tensor-core
+// kernels): the 8 x 3 vertex features of each level blended into its F
+// features, handed to store(l, v) for every l < KP (zeros for absent levels
+// and levels beyond the scene's K).  texel_addr (when requested) receives
+// the 24 entries of each level (neighbour-major, -1 where absent).
+template <int F, typename TT, int KP, class Store>
+__device__ __forceinline__ void gather_full_query(const QueryParams& p, const DevScene& sc,
+                                                  const int2* tree, const QueryIn& in, int64_t gq,
+                                                  bool valid, Store&& store) {
+  float ux, uy;
+  octa_fold(in.w0, in.w1, in.w2, ux, uy);
+  const float xs[3] = {clamp01(in.x0), clamp01(in.x1), clamp01(in.x2)};
+  const bool want_addr = p.texel_addr != nullptr && valid;
+  int done = 0;  // levels handed over
+  if (valid) {
+    visit_full_levels<KP, false>(p, sc, tree, xs, ux, uy, [&](int l, const FullLevel& fl) {
+      float v[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) v[f] = 0.f;
+      int32_t* aout = (want_addr && l < p.kmax_out) ? p.texel_addr + (gq * p.kmax_out + l) * 24
+                                                    : nullptr;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (fl.base[j] < 0) {
+          if (aout)
+            for (int k = 0; k < 3; ++k) aout[3 * j + k] = -1;
+          continue;
+        }
+        TexelRaw<TT, F> tx[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tx[k].load(sc.tables, uint32_t(fl.base[j] + fl.vidx[k]));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float w = fl.wn[j] * fl.b[k];
+#pragma unroll
+          for (int f = 0; f < F; ++f) v[f] = fmaf(w, tx[k].get(f), v[f]);
+          if (aout) aout[3 * j + k] = fl.base[j] + fl.vidx[k];
+        }
+      }
+      store(l, v);
+      done = l + 1;
+    });
+  }
+#pragma unroll 1
+  for (int l = done; l < KP; ++l) {
+    float v[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) v[f] = 0.f;
+    store(l, v);
+    if (want_addr && l < p.kmax_out)
+      for (int k = 0; k < 24; ++k) p.texel_addr[(gq * p.kmax_out + l) * 24 + k] = -1;
+  }
+  if (want_addr)
     for (int l = KP; l < p.kmax_out; ++l)
       for (int k = 0; k < 24; ++k) p.texel_addr[(gq * p.kmax_out + l) * 24 + k] = -1;
 }

@@ -697,8 +697,14 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
     const int nq = static_cast<int>(sc.q_end - q0 < ROWS ? sc.q_end - q0 : int64_t(ROWS));
     const bool valid = row < nq;
     const int64_t gq = q0 + row;
-    locate_gather_bf16<S, TT>(p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), base_sm,
-                              u_sm, t);
+    const bool full = sc.query_form == OCTA_FORM_TRILINEAR_VERTEX;  // uniform over the CTA
+    const QueryIn& qry = in;  // the layer loops below reuse the name in
+    if (full)
+      locate_gather_bf16<S, TT, 1, true>(p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0),
+                                         nullptr, nullptr, t);
+    else
+      locate_gather_bf16<S, TT>(p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), base_sm,
+                                u_sm, t);
     fence_proxy_async();
     named_sync(gbar, NT);
 
@@ -864,22 +870,55 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
           tmem_ld16(lane_work + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
         tmem_wait_ld();
         tc_fence_before_sync();
+        if (full) {  // the 24 vertices of each level (Eq. 10 with Eq. 6)
+          if (valid) {
+            // dh by level from a thread-local copy (the level loop stays rolled)
+            float dh[S::WP];
 #pragma unroll
-        for (int l = 0; l < S::KPAD; ++l) {
-          const int64_t mo = base_sm[l * NT + t];
-          if (mo < 0) continue;
-          const Footprint fp = footprint(u_sm[t], u_sm[NT + t], sc.R[l]);
+            for (int c = 0; c < S::WP; ++c) dh[c] = __uint_as_float(r[c]);
+            float ux, uy;
+            octa_fold(qry.w0, qry.w1, qry.w2, ux, uy);
+            const float xs[3] = {clamp01(qry.x0), clamp01(qry.x1), clamp01(qry.x2)};
+            visit_full_levels<S::KPAD, false>(p, sc, tree, xs, ux, uy,
+                                              [&](int l, const FullLevel& fl) {
 #pragma unroll
-          for (int c4 = 0; c4 < S::F / 4; ++c4) {
-            const float g0 = __uint_as_float(r[l * S::F + 4 * c4 + 0]);
-            const float g1 = __uint_as_float(r[l * S::F + 4 * c4 + 1]);
-            const float g2 = __uint_as_float(r[l * S::F + 4 * c4 + 2]);
-            const float g3 = __uint_as_float(r[l * S::F + 4 * c4 + 3]);
+              for (int c4 = 0; c4 < S::F / 4; ++c4) {
+                const float g0 = dh[l * S::F + 4 * c4 + 0];
+                const float g1 = dh[l * S::F + 4 * c4 + 1];
+                const float g2 = dh[l * S::F + 4 * c4 + 2];
+                const float g3 = dh[l * S::F + 4 * c4 + 3];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const float w = fp.w[k];
-              float4* dst = reinterpret_cast<float4*>(sc.d_tables + (mo + fp.idx[k]) * S::F) + c4;
-              atomicAdd(dst, make_float4(w * g0, w * g1, w * g2, w * g3));
+                for (int j = 0; j < 8; ++j) {
+                  if (fl.base[j] < 0) continue;
+#pragma unroll
+                  for (int k = 0; k < 3; ++k) {
+                    const float w = fl.wn[j] * fl.b[k];
+                    float4* dst = reinterpret_cast<float4*>(
+                                      sc.d_tables + int64_t(fl.base[j] + fl.vidx[k]) * S::F) + c4;
+                    atomicAdd(dst, make_float4(w * g0, w * g1, w * g2, w * g3));
+                  }
+                }
+              }
+            });
+          }
+        } else {
+#pragma unroll
+          for (int l = 0; l < S::KPAD; ++l) {
+            const int64_t mo = base_sm[l * NT + t];
+            if (mo < 0) continue;
+            const Footprint fp = footprint(u_sm[t], u_sm[NT + t], sc.R[l]);
+#pragma unroll
+            for (int c4 = 0; c4 < S::F / 4; ++c4) {
+              const float g0 = __uint_as_float(r[l * S::F + 4 * c4 + 0]);
+              const float g1 = __uint_as_float(r[l * S::F + 4 * c4 + 1]);
+              const float g2 = __uint_as_float(r[l * S::F + 4 * c4 + 2]);
+              const float g3 = __uint_as_float(r[l * S::F + 4 * c4 + 3]);
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const float w = fp.w[k];
+                float4* dst = reinterpret_cast<float4*>(sc.d_tables + (mo + fp.idx[k]) * S::F) + c4;
+                atomicAdd(dst, make_float4(w * g0, w * g1, w * g2, w * g3));
+              }
             }
           }
         }

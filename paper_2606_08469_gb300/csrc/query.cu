@@ -98,12 +98,8 @@ bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u
 }  // namespace
 
 // Validates scenes + queries and fills the kernel parameter block.
-// full_form: where the trilinear vertex form is accepted (the encoding and
-// the forward for any decoder; the backward and training passes for FP32
-// decoders).
-enum FullForm { kFullNo = 0, kFullFp32 = 1, kFullAny = 2 };
 int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
-                       const octa_scene_grads* grads, QueryParams& p, int full_form = kFullNo) {
+                       const octa_scene_grads* grads, QueryParams& p) {
   std::memset(&p, 0, sizeof(p));
   if (!scenes || !q) return fail(OCTA_EINVAL, "scenes and queries must be non-NULL");
   if (n_scenes < 1 || n_scenes > OCTA_MAX_SCENES)
@@ -155,9 +151,6 @@ int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_qu
     if (c.query_form != OCTA_FORM_CELL_BILINEAR && c.query_form != OCTA_FORM_TRILINEAR_VERTEX)
       return fail(OCTA_EINVAL, "scene %d: unknown query_form %d", s, c.query_form);
     if (c.query_form == OCTA_FORM_TRILINEAR_VERTEX) {
-      if (full_form == kFullNo || (full_form == kFullFp32 && c.weight_dtype != OCTA_F32))
-        return fail(OCTA_EUNSUPPORTED, "scene %d: the trilinear vertex form: backward and "
-                                       "training passes need FP32 decoders", s);
       for (int l = 0; l < c.num_levels; ++l) {
         const int n = c.R[l] - 1;  // cells a side: a power of two >= 2
         if (n < 2 || (n & (n - 1)))
@@ -225,7 +218,7 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
                            void* stream) {
   clear_error();
   QueryParams p;
-  int rc = build_query_params(scenes, n_scenes, q, nullptr, p, kFullAny);
+  int rc = build_query_params(scenes, n_scenes, q, nullptr, p);
   if (rc) return rc;
   if (q->n > 0 && !features) return fail(OCTA_EINVAL, "features must be non-NULL");
   rc = check_one_form(scenes, n_scenes, node_idx);
@@ -302,7 +295,7 @@ extern "C" int octa_query_fwd(const octa_scene* scenes, int32_t n_scenes, const 
                               int32_t* status, void* stream) {
   clear_error();
   QueryParams p;
-  int rc = build_query_params(scenes, n_scenes, q, nullptr, p, kFullAny);
+  int rc = build_query_params(scenes, n_scenes, q, nullptr, p);
   if (rc) return rc;
   rc = check_one_form(scenes, n_scenes, node_idx);
   if (rc) return rc;
@@ -327,7 +320,7 @@ extern "C" int octa_query_bwd(const octa_scene* scenes, int32_t n_scenes, const 
   clear_error();
   if (!grads) return fail(OCTA_EINVAL, "grads must be non-NULL");
   QueryParams p;
-  int rc = build_query_params(scenes, n_scenes, q, grads, p, kFullFp32);
+  int rc = build_query_params(scenes, n_scenes, q, grads, p);
   if (rc) return rc;
   if (q->n > 0 && !d_rgb) return fail(OCTA_EINVAL, "d_rgb must be non-NULL");
   p.d_rgb = d_rgb;
@@ -353,7 +346,7 @@ extern "C" int octa_train_fused(const octa_scene* scenes, int32_t n_scenes, cons
   q.n = pairs->n;
   for (int s = 0; s <= OCTA_MAX_SCENES; ++s) q.scene_start[s] = pairs->scene_start[s];
   QueryParams p;
-  int rc = build_query_params(scenes, n_scenes, &q, grads, p, kFullFp32);
+  int rc = build_query_params(scenes, n_scenes, &q, grads, p);
   if (rc) return rc;
   const bool bf16 = scenes[0].weight_dtype == OCTA_BF16;
   for (int s = 0; s < n_scenes; ++s)

@@ -124,10 +124,10 @@ def test_full_form_argument_errors():
     sb = A.Scene(tree, sc.tables, weights, device=DEV, query_form=L.OCTA_FORM_TRILINEAR_VERTEX)
     A.octa_encode(sb, dev(x), dev(w))                     # the encoding and the forward take
     A.octa_query_fwd(sb, dev(x), dev(w))                  # either decoder
-    dT = torch.zeros((tree.num_texels, 4), device=DEV)
-    dW = torch.zeros(sb.weights.shape, device=DEV)
-    with pytest.raises(L.OctaError):                      # BF16 backward: cell form only
-        A.octa_query_bwd(sb, dev(x), dev(w), torch.ones((10, 3), device=DEV), [(dT, dW)])
+    cell = A.Scene(tree, sc.tables, [dev(W) for W in I.make_mlp(1, [12, 16, 3])], device=DEV)
+    two = [sc, cell]                                      # forms mixed in one call
+    with pytest.raises(L.OctaError):
+        A.octa_query_fwd(two, dev(np.concatenate([x, x])), dev(np.concatenate([w, w])), [10, 10])
 
 
 # ------------------------------------------- FP32 decoder passes (FP32 engine)
@@ -279,3 +279,88 @@ def test_full_form_tensor_core_forward(tdt):
     err = np.linalg.norm(rgb.cpu().numpy() - ref) / np.linalg.norm(ref)
     print("BF16 full-form forward, normwise error", err)
     assert err <= 1e-2
+
+
+# ------------------------------------ BF16 tensor-core backward / training
+
+def _mask_fraction(weights, h):
+    """Fraction of hidden pre-activations within the BF16 forward error bound
+    2^-7 sum |w||a| of zero (their ReLU masks may differ from FP64's)."""
+    a = np.asarray(h, np.float64)
+    flags = []
+    for W in [np.asarray(W, np.float64) for W in weights][:-1]:
+        z = a @ W.T
+        flags.append((np.abs(z) < 2.0 ** -7 * (np.abs(a) @ np.abs(W).T)).ravel())
+        a = np.maximum(z, 0.0)
+    return float(np.mean(np.concatenate(flags)))
+
+
+def test_full_form_bf16_backward_vs_oracle():
+    """octa_query_bwd on a BF16 decoder in the full form against the FP64
+    oracle on the quantised parameters: the last layer's dW (no ReLU mask)
+    to 1e-2, the other tensors to 3 sqrt(f) + 1e-2 with f the fraction of
+    pre-activations whose mask BF16 may flip (the bound of the cell form's
+    BF16 backward tests)."""
+    from paper_2606_08469_gb300 import _lib as L
+    from paper_2606_08469_gb300 import api as A
+    seed, depth, V, F = 1311, 5, [17, 17, 9, 9, 5, 3], 8
+    tree = A.octree_build(seed, depth, 0.6, V)
+    ot = O.build_tree(seed, depth, 0.6, V)
+    tq = I.make_tables(seed + 1, tree.num_texels, F, 0.3).astype(np.float16).astype(np.float32)
+    weights = [W * np.float32(1.5) for W in I.make_mlp(seed + 2, [(depth + 1) * F, 64, 64, 3])]
+    Wb = [dev(W).to(torch.bfloat16) for W in weights]
+    wq = [W.float().cpu().numpy() for W in Wb]
+    sc = A.Scene(tree, dev(tq).half().contiguous(), Wb, device=DEV,
+                 query_form=L.OCTA_FORM_TRILINEAR_VERTEX)
+    x, w = I.uniform_queries(seed + 3, 6000)
+    d_rgb = np.random.default_rng(seed).normal(size=(len(x), 3)).astype(np.float32)
+    dT = torch.zeros((tree.num_texels, F), device=DEV)
+    dW = torch.zeros(sc.weights.shape, device=DEV)
+    A.octa_query_bwd(sc, dev(x), dev(w), dev(d_rgb), [(dT, dW)])
+    rT, rWs, _ = O.query_backward(ot, tq, wq, x, w, d_rgb, form="full")
+    frac = _mask_fraction(wq, O.encode_features_full(ot, tq, x, w).h)
+    errs = [_normwise(dT.cpu().numpy(), rT)]
+    gw = dW.cpu().numpy()
+    for (off, o, i), rW in zip(sc.weight_slices(), rWs):
+        errs.append(_normwise(gw[off:off + o * i].reshape(o, i), rW))
+    print("BF16 full-form backward errors", [round(e, 5) for e in errs], "mask fraction", frac)
+    assert errs[-1] <= 1e-2
+    assert max(errs[:-1]) <= 3.0 * np.sqrt(frac) + 1e-2
+
+
+def test_full_form_bf16_fused_and_one_launch_training():
+    """Config [2]'s shapes (BF16 decoder, FP16 tables) on vertex maps of side
+    R + 1 in the full form, 4,097 pairs: the fused training pass against the
+    unfused forward + loss + backward (same arithmetic up to the atomics'
+    order), its loss against the FP64 oracle (1e-2), and the one-launch
+    step against the fused pass followed by Adam."""
+    from paper_2606_08469_gb300 import api as A
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.CONFIGS[2]
+    a, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=4097, query_form="full")
+    b, _ = WL.train_step_for(cfg, n_pairs=4097, query_form="full", fused=True)
+    a.forward()
+    a.loss_and_grad()
+    a.backward()
+    b.fused_pass()
+    torch.cuda.synchronize()
+    assert abs(a.loss.item() - b.loss.item()) <= 1e-6 * a.loss.item()
+    for sa, sb in zip(a.states, b.states):
+        for ga, gb in ((sa.grad_t, sb.grad_t), (sa.grad_w, sb.grad_w)):
+            assert (torch.linalg.norm(ga - gb) / torch.linalg.norm(gb)).item() <= 1e-4
+    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, [r + 1 for r in cfg.R])
+    N = pairs.n
+    X = np.concatenate([pairs.x, pairs.x2])
+    Om = np.concatenate([pairs.omega, -pairs.omega2])
+    rgb, _ = O.query_forward(ot, tables, weights, X, Om, form="full")
+    loss, _, _ = O.residual_loss(rgb[:N], rgb[N:], pairs.E, pairs.w)
+    assert abs(b.loss.item() - loss) <= 1e-2 * loss
+    c, _ = WL.train_step_for(cfg, n_pairs=4097, query_form="full", fused=True)
+    d, _ = WL.train_step_for(cfg, n_pairs=4097, query_form="full", persistent=True)
+    for _ in range(2):
+        c.step()
+        d.step()
+        torch.cuda.synchronize()
+        torch.testing.assert_close(d.loss, c.loss, rtol=1e-6, atol=0)
+        sc_, sd_ = A.read_scaler(c.scaler), A.read_scaler(d.scaler)
+        assert (sc_.step, sc_.skipped) == (sd_.step, sd_.skipped)
