@@ -132,10 +132,8 @@ typedef struct octa_scene {
  * weights renormalised over the cells present in the octree, in each the
  * barycentric blend of the 3 vertices of the triangle holding the direction
  * on the node's R x R vertex map (R = 2^k + 1, k >= 1; mirrored vertices of
- * the map's edges are one vertex).  octa_encode and octa_query_fwd evaluate
- * the second form for any decoder; octa_query_bwd and octa_train_fused for
- * FP32 decoders (weight_dtype F32).  Their BF16 path, and
- * octa_train_step_batched, return OCTA_EUNSUPPORTED for it.               */
+ * the map's edges are one vertex).  Every query and training entry point
+ * evaluates either form, for FP32 and BF16 decoders.                      */
 #define OCTA_FORM_CELL_BILINEAR 0
 #define OCTA_FORM_TRILINEAR_VERTEX 1
 
