@@ -19,6 +19,8 @@ fusion or reordering of its own:
   encode_features   Eq. 10 in the single-cell, bilinear form + Eq. 11
   encode_features_full  Eq. 10 as printed (eight cells, renormalised
                     trilinear weights) with Eq. 6 (barycentric on vertex maps)
+  encode_features_shifted  the same with Eq. 7-9's disparity-shifted
+                    direction per cell (reflect_f32, shifted_direction_f32)
   mlp_forward       Eq. 13 (decoder; ReLU hidden layers, exp output)
   residual_loss     Eq. 14 with the Monte-Carlo target of Eq. 3 (M = 1)
   residual_loss_multi  Eq. 14 with Eq. 3's M-sample target
@@ -530,6 +532,80 @@ def encode_features_full(tree, tables, x, omega):
                 wgt[:, l, j, k] = np.where(present[:, j], w, 0.0)
                 h[:, l * F:(l + 1) * F] += (wgt[:, l, j, k][:, None] * T[np.maximum(a, 0)]
                                             * present[:, j][:, None])
+    return FullEncoding(h, addr, wgt)
+
+
+def reflect_f32(omega, normal):
+    """The mirror reflection direction omega_r of Eq. 7 in binary32, one
+    rounding per operation: omega and n normalised (v / sqrt(v.v)), then
+    omega_r = (2 (n.omega)) n - omega per component; dot products
+    ((a0 b0 + a1 b1) + a2 b2)."""
+    f = np.float32
+
+    def dot(a, b):
+        return ((a[:, 0] * b[:, 0]).astype(f) + (a[:, 1] * b[:, 1]).astype(f)).astype(f) + \
+            (a[:, 2] * b[:, 2]).astype(f)
+
+    def unit(v):
+        v = np.asarray(v, dtype=f)
+        return (v / np.sqrt(dot(v, v)).astype(f)[:, None]).astype(f)
+    w = unit(omega)
+    n = unit(normal)
+    d2 = (f(2) * dot(n, w)).astype(f)
+    return ((d2[:, None] * n).astype(f) - w).astype(f)
+
+
+def shifted_direction_f32(x, omega_r, disparity, cells, l):
+    """Eq. 9's direction in the cell with integer coordinates `cells` [N][3]
+    at level l, in binary32 with one rounding per operation:
+    v = (x - c) d + omega_r per component, c = (cell + 1/2) 2^-l (exact).
+    The normalisation of Eq. 9 is left out: the octahedral map of Eq. 4
+    divides by the L1 norm, so v and v / |v| fold to the same point."""
+    f = np.float32
+    x32 = np.clip(np.asarray(x, dtype=f), f(0), f(1))
+    c = ((cells.astype(f) + f(0.5)) * f(2.0 ** -l)).astype(f)
+    d = np.asarray(disparity, dtype=f)[:, None]
+    return (((x32 - c).astype(f) * d).astype(f) + np.asarray(omega_r, dtype=f)).astype(f)
+
+
+def encode_features_shifted(tree, tables, x, omega, normal, disparity):
+    """Eq. 10 with the disparity-shifted lookup of Eq. 7-9 and Eq. 6: as
+    encode_features_full, but cell j of level l looks its vertex map up in
+    the direction of y - c_j, y = x + omega_r / d (Eq. 8), i.e. of
+    (x - c_j) d + omega_r (Eq. 9), with omega_r the reflection of omega
+    about the normal (Eq. 7) and d the given disparity per query.  d = 0
+    looks every cell up at omega_r."""
+    T = np.asarray(tables, dtype=np.float64)
+    F = T.shape[1]
+    n = len(x)
+    K = tree.num_levels
+    om_r = reflect_f32(omega, normal)
+    h = np.zeros((n, K * F))
+    addr = np.full((n, K, 8, 3), -1, dtype=np.int64)
+    wgt = np.zeros((n, K, 8, 3))
+    for l in range(K):
+        V = int(tree.R[l])
+        N = V - 1
+        cells, wsp, inside = neighbour_cells(x, l)
+        nodes = np.full((n, 8), -1, dtype=np.int64)
+        for j in range(8):
+            nodes[:, j] = np.where(inside[:, j], node_of_cell(tree, l, np.clip(cells[:, j], 0, None)), -1)
+        present = nodes >= 0
+        wp = np.where(present, wsp, 0.0)
+        den = wp.sum(axis=1)
+        wn = np.where(den[:, None] > 0, wp / np.where(den > 0, den, 1.0)[:, None], 0.0)
+        for j in range(8):
+            v = shifted_direction_f32(x, om_r, disparity, cells[:, j], l)
+            i0, j0, fx32, fy32 = vertex_cell_f32(v, V)
+            off, b = vertex_triangle(i0, j0, fx32, fy32, N)
+            base = tree.map_offset[np.maximum(nodes[:, j], 0)]
+            for k in range(3):
+                vi, vj = canonical_vertex(i0 + off[:, k, 0], j0 + off[:, k, 1], N)
+                a = np.where(present[:, j], base + vj * V + vi, -1)
+                w = np.where(present[:, j], wn[:, j] * b[:, k], 0.0)
+                addr[:, l, j, k] = a
+                wgt[:, l, j, k] = w
+                h[:, l * F:(l + 1) * F] += w[:, None] * T[np.maximum(a, 0)] * present[:, j][:, None]
     return FullEncoding(h, addr, wgt)
 
 
