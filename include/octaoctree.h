@@ -136,6 +136,16 @@ typedef struct octa_scene {
  * evaluates either form, for FP32 and BF16 decoders.                      */
 #define OCTA_FORM_CELL_BILINEAR 0
 #define OCTA_FORM_TRILINEAR_VERTEX 1
+/* OCTA_FORM_SHIFTED (Eq. 7-9 with Eq. 10 and Eq. 6): the trilinear vertex
+ * form in which cell j of a level looks its map up in the direction of
+ * y - c_j, y = x + omega_r / d (c_j the cell's centre, d the query's
+ * disparity, omega_r the reflection of omega about the normal, both
+ * normalised as v / sqrt(v.v)), evaluated as (x - c_j) d + omega_r in
+ * binary32 with one rounding per operation (omega_r = (2 (n.omega)) n -
+ * omega; the octahedral map divides by the L1 norm, so no normalisation).
+ * Only octa_encode evaluates it (the others return OCTA_EUNSUPPORTED); the
+ * disparity comes from the caller.                                       */
+#define OCTA_FORM_SHIFTED 2
 
 /* Queries: scene s answers queries [scene_start[s], scene_start[s+1]).   */
 typedef struct octa_queries {
@@ -143,6 +153,9 @@ typedef struct octa_queries {
   const float* omega;          /* device [n][3], direction (any length > 0) */
   int64_t n;
   int64_t scene_start[OCTA_MAX_SCENES + 1];
+  /* the shifted form only (NULL otherwise): */
+  const float* normal;         /* device [n][3], surface normal (length > 0)*/
+  const float* disparity;      /* device [n], d of Eq. 8 (>= 0)            */
 } octa_queries;
 
 /* octa_encode -- the OctaOctree encoding alone in the scenes' query form

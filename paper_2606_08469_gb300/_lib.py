@@ -32,6 +32,7 @@ OCTA_F16 = 1
 OCTA_BF16 = 2
 OCTA_FORM_CELL_BILINEAR = 0
 OCTA_FORM_TRILINEAR_VERTEX = 1
+OCTA_FORM_SHIFTED = 2
 
 OCTA_OP_LOSS = 1
 OCTA_OP_ADAM = 2
@@ -74,7 +75,8 @@ class octa_queries(C.Structure):
         ("omega", C.c_void_p),
         ("n", C.c_int64),
         ("scene_start", C.c_int64 * (OCTA_MAX_SCENES + 1)),
-        ("norm_pairs", C.c_int64 * OCTA_MAX_SCENES),
+        ("normal", C.c_void_p),
+        ("disparity", C.c_void_p),
     ]
 
 

@@ -180,7 +180,9 @@ def _queries(x, omega, counts):
 
 
 def octa_encode(scenes, x, omega, counts=None, feat_dtype=torch.float32, want_nodes=False,
-                want_addr=False, status=None, stream=None):
+                want_addr=False, status=None, stream=None, normal=None, disparity=None):
+    """The encoding alone (features [n][W]); normal [n][3] and disparity [n]
+    are the shifted form's inputs."""
     arr, ns = _scene_array(scenes)
     sl = [scenes] if isinstance(scenes, Scene) else scenes
     kmax = max(s.tree.num_levels for s in sl)
@@ -189,9 +191,11 @@ def octa_encode(scenes, x, omega, counts=None, feat_dtype=torch.float32, want_no
     dev = x.device
     feat = torch.zeros((n, W), dtype=feat_dtype, device=dev)
     nodes = torch.empty((n, kmax), dtype=torch.int32, device=dev) if want_nodes else None
-    per_level = 24 if sl[0].query_form == L.OCTA_FORM_TRILINEAR_VERTEX else 4
+    per_level = 4 if sl[0].query_form == L.OCTA_FORM_CELL_BILINEAR else 24
     addr = torch.empty((n, kmax, per_level), dtype=torch.int32, device=dev) if want_addr else None
     q = _queries(x, omega, counts)
+    q.normal = normal.data_ptr() if normal is not None and n else None
+    q.disparity = disparity.data_ptr() if disparity is not None and n else None
     L.check(_lib().octa_encode(arr, ns, C.byref(q), _ptr(feat), _DT[feat_dtype], W, _ptr(nodes),
                                _ptr(addr), _ptr(status), _stream(stream)), "octa_encode")
     return feat, nodes, addr
@@ -207,7 +211,7 @@ def octa_query_fwd(scenes, x, omega, counts=None, want_nodes=False, want_addr=Fa
     if rgb is None:
         rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
     nodes = torch.empty((n, kmax), dtype=torch.int32, device=dev) if want_nodes else None
-    per_level = 24 if sl[0].query_form == L.OCTA_FORM_TRILINEAR_VERTEX else 4
+    per_level = 4 if sl[0].query_form == L.OCTA_FORM_CELL_BILINEAR else 24
     addr = torch.empty((n, kmax, per_level), dtype=torch.int32, device=dev) if want_addr else None
     q = _queries(x, omega, counts)
     L.check(_lib().octa_query_fwd(arr, ns, C.byref(q), _ptr(rgb), _ptr(nodes), _ptr(addr),

@@ -163,20 +163,19 @@ __device__ __forceinline__ void locate_gather_query(const QueryParams& p, const 
 
 // The levels 0 .. min(K, KP) - 1 of one query in the full form, the eight
 // cells' nodes carried from each level to the next (full_descend): per level
-// the triangle of the vertex map and the cells' map bases and renormalised
-// weights, handed to fn(l, fl).  UNROLL unrolls the level loop (fn may then
-// index register arrays by l).
+// the lower cell c0 and the cells' map bases and renormalised weights (base,
+// wn of fl), handed to fn(l, c0, fl).  UNROLL unrolls the level loop (fn may
+// then index register arrays by l).
 template <int KP, bool UNROLL, class Fn>
-__device__ __forceinline__ void visit_full_levels(const QueryParams& p, const DevScene& sc,
-                                                  const int2* tree, const float (&xs)[3], float ux,
-                                                  float uy, Fn&& fn) {
+__device__ __forceinline__ void visit_cell_levels(const QueryParams& p, const DevScene& sc,
+                                                  const int2* tree, const float (&xs)[3],
+                                                  Fn&& fn) {
   int nd[8];
   int pc[3] = {0, 0, 0};
 #pragma unroll(UNROLL ? KP : 1)
   for (int l = 0; l < KP; ++l) {
     if (l >= sc.K) break;
     FullLevel fl;
-    full_vertex(ux, uy, sc.R[l], fl);
     int c0[3];
     float t[3];
     full_cells(xs, l, c0, t);
@@ -191,8 +190,109 @@ __device__ __forceinline__ void visit_full_levels(const QueryParams& p, const De
 #pragma unroll
     for (int a = 0; a < 3; ++a) pc[a] = c0[a];
     full_finish(p, sc, tree, nd, t, sc.R[l], fl);
-    fn(l, fl);
+    fn(l, c0, fl);
   }
+}
+
+// visit_cell_levels with one direction for all cells: fl also carries the
+// triangle (vidx, b) of the folded direction (ux, uy) on the level's map.
+template <int KP, bool UNROLL, class Fn>
+__device__ __forceinline__ void visit_full_levels(const QueryParams& p, const DevScene& sc,
+                                                  const int2* tree, const float (&xs)[3], float ux,
+                                                  float uy, Fn&& fn) {
+  visit_cell_levels<KP, UNROLL>(p, sc, tree, xs, [&](int l, const int (&)[3], FullLevel& fl) {
+    full_vertex(ux, uy, sc.R[l], fl);
+    fn(l, fl);
+  });
+}
+
+// ((a0 b0 + a1 b1) + a2 b2), one rounding per operation.
+__device__ __forceinline__ float dot3_f32_rn(const float (&a)[3], const float (&b)[3]) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(a[0], b[0]), __fmul_rn(a[1], b[1])), __fmul_rn(a[2], b[2]));
+}
+
+// The mirror reflection of Eq. 7: w and n normalised (v / sqrt(v.v)), then
+// r = (2 (n.w)) n - w, one rounding per operation.
+__device__ __forceinline__ void reflect_f32_rn(const float (&w0)[3], const float (&n0)[3],
+                                               float (&r)[3]) {
+  const float sw = __fsqrt_rn(dot3_f32_rn(w0, w0)), sn = __fsqrt_rn(dot3_f32_rn(n0, n0));
+  const float w[3] = {__fdiv_rn(w0[0], sw), __fdiv_rn(w0[1], sw), __fdiv_rn(w0[2], sw)};
+  const float n[3] = {__fdiv_rn(n0[0], sn), __fdiv_rn(n0[1], sn), __fdiv_rn(n0[2], sn)};
+  const float d2 = __fmul_rn(2.f, dot3_f32_rn(n, w));
+#pragma unroll
+  for (int a = 0; a < 3; ++a) r[a] = __fsub_rn(__fmul_rn(d2, n[a]), w[a]);
+}
+
+// The shifted form of one query per thread (encoding kernel): per level the
+// eight cells' nodes, then in each present cell j its own direction
+// v_j = (x - c_j) d + omega_r (Eq. 9; c_j = (c + 1/2) 2^-l exact), the
+// triangle of v_j on the cell's vertex map and the blend of its 3 vertices
+// (Eq. 6) with the renormalised trilinear weight (Eq. 10); store(l, v) for
+// every l < KP as gather_full_query, texel_addr rows of 24 entries.
+template <int F, typename TT, int KP, class Store>
+__device__ __forceinline__ void gather_shifted_query(const QueryParams& p, const DevScene& sc,
+                                                     const int2* tree, const QueryIn& in,
+                                                     int64_t gq, bool valid, Store&& store) {
+  const float xs[3] = {clamp01(in.x0), clamp01(in.x1), clamp01(in.x2)};
+  const bool want_addr = p.texel_addr != nullptr && valid;
+  int done = 0;
+  if (valid) {
+    const float w0[3] = {in.w0, in.w1, in.w2};
+    const float n0[3] = {p.normal[3 * gq], p.normal[3 * gq + 1], p.normal[3 * gq + 2]};
+    float wr[3];
+    reflect_f32_rn(w0, n0, wr);
+    const float disp = p.disparity[gq];
+    visit_cell_levels<KP, false>(p, sc, tree, xs, [&](int l, const int (&c0)[3], FullLevel& fl) {
+      float v[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) v[f] = 0.f;
+      int32_t* aout = (want_addr && l < p.kmax_out) ? p.texel_addr + (gq * p.kmax_out + l) * 24
+                                                    : nullptr;
+      const float scale = __int_as_float((127 - l) << 23);  // 2^-l
+#pragma unroll 1
+      for (int j = 0; j < 8; ++j) {
+        if (fl.base[j] < 0) {
+          if (aout)
+            for (int k = 0; k < 3; ++k) aout[3 * j + k] = -1;
+          continue;
+        }
+        const int cj[3] = {c0[0] + (j & 1), c0[1] + ((j >> 1) & 1), c0[2] + (j >> 2)};
+        float dir[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float c = __fmul_rn(__fadd_rn(static_cast<float>(cj[a]), 0.5f), scale);
+          dir[a] = __fadd_rn(__fmul_rn(__fsub_rn(xs[a], c), disp), wr[a]);
+        }
+        float ux, uy;
+        octa_fold(dir[0], dir[1], dir[2], ux, uy);
+        full_vertex(ux, uy, sc.R[l], fl);
+        TexelRaw<TT, F> tx[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tx[k].load(sc.tables, uint32_t(fl.base[j] + fl.vidx[k]));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float w = fl.wn[j] * fl.b[k];
+#pragma unroll
+          for (int f = 0; f < F; ++f) v[f] = fmaf(w, tx[k].get(f), v[f]);
+          if (aout) aout[3 * j + k] = fl.base[j] + fl.vidx[k];
+        }
+      }
+      store(l, v);
+      done = l + 1;
+    });
+  }
+#pragma unroll 1
+  for (int l = done; l < KP; ++l) {
+    float v[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) v[f] = 0.f;
+    store(l, v);
+    if (want_addr && l < p.kmax_out)
+      for (int k = 0; k < 24; ++k) p.texel_addr[(gq * p.kmax_out + l) * 24 + k] = -1;
+  }
+  if (want_addr)
+    for (int l = KP; l < p.kmax_out; ++l)
+      for (int k = 0; k < 24; ++k) p.texel_addr[(gq * p.kmax_out + l) * 24 + k] = -1;
 }
 
 // The full query form of one query per thread (encoding and tensor-core

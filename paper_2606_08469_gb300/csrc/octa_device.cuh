@@ -69,6 +69,9 @@ struct QueryParams {
   // in nodes (0: walk in global memory) and byte offset in dynamic memory
   int32_t tree_cap;
   int32_t tree_off;
+  // the shifted form's per-query inputs (normal [n][3], disparity [n])
+  const float* normal;
+  const float* disparity;
 };
 
 // Work units [0, n) of this CTA: interleaved (u = block + k * grid) or one

@@ -68,7 +68,9 @@ __global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ 
               make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
       }
     };
-    if constexpr (FORM == OCTA_FORM_TRILINEAR_VERTEX)
+    if constexpr (FORM == OCTA_FORM_SHIFTED)
+      gather_shifted_query<F, TT, KP>(p, sc, tree, in, q0 + q, q < nq, stage_row);
+    else if constexpr (FORM == OCTA_FORM_TRILINEAR_VERTEX)
       gather_full_query<F, TT, KP>(p, sc, tree, in, q0 + q, q < nq, stage_row);
     else
       locate_gather_query<F, TT, KP, sizeof(OT) == 2>(p, sc, tree, in, q0 + q, q < nq, 0, nullptr,
@@ -148,9 +150,10 @@ int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_qu
     d.n_layers = c.n_layers;
     for (int l = 0; l < c.num_levels; ++l) d.R[l] = c.R[l];
     d.query_form = c.query_form;
-    if (c.query_form != OCTA_FORM_CELL_BILINEAR && c.query_form != OCTA_FORM_TRILINEAR_VERTEX)
+    if (c.query_form != OCTA_FORM_CELL_BILINEAR && c.query_form != OCTA_FORM_TRILINEAR_VERTEX &&
+        c.query_form != OCTA_FORM_SHIFTED)
       return fail(OCTA_EINVAL, "scene %d: unknown query_form %d", s, c.query_form);
-    if (c.query_form == OCTA_FORM_TRILINEAR_VERTEX) {
+    if (c.query_form != OCTA_FORM_CELL_BILINEAR) {
       for (int l = 0; l < c.num_levels; ++l) {
         const int n = c.R[l] - 1;  // cells a side: a power of two >= 2
         if (n < 2 || (n & (n - 1)))
@@ -200,13 +203,22 @@ int apply_norm_pairs(const octa_pairs* pairs, int n_scenes, QueryParams& p) {
 using namespace octa;
 
 namespace {
+// The shifted form is evaluated by octa_encode alone.
+int reject_shifted(const octa_scene* scenes, int32_t n_scenes) {
+  for (int s = 0; s < n_scenes; ++s)
+    if (scenes[s].query_form == OCTA_FORM_SHIFTED)
+      return fail(OCTA_EUNSUPPORTED, "scene %d: the shifted form is evaluated by octa_encode only",
+                  s);
+  return 0;
+}
+
 // One query form per call (texel_addr's row layout depends on it); node_idx
 // has no meaning in the trilinear vertex form (eight cells per level).
 int check_one_form(const octa_scene* scenes, int32_t n_scenes, const int32_t* node_idx) {
   for (int s = 1; s < n_scenes; ++s)
     if (scenes[s].query_form != scenes[0].query_form)
       return fail(OCTA_EUNSUPPORTED, "scenes of one call must share the query form");
-  if (node_idx && scenes[0].query_form == OCTA_FORM_TRILINEAR_VERTEX)
+  if (node_idx && scenes[0].query_form != OCTA_FORM_CELL_BILINEAR)
     return fail(OCTA_EINVAL, "node_idx is not defined for the trilinear vertex form");
   return 0;
 }
@@ -223,6 +235,8 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
   if (q->n > 0 && !features) return fail(OCTA_EINVAL, "features must be non-NULL");
   rc = check_one_form(scenes, n_scenes, node_idx);
   if (rc) return rc;
+  if (scenes[0].query_form == OCTA_FORM_SHIFTED && q->n > 0 && (!q->normal || !q->disparity))
+    return fail(OCTA_EINVAL, "the shifted form needs normal and disparity");
   if (feat_dtype != OCTA_F32 && feat_dtype != OCTA_BF16)
     return fail(OCTA_EINVAL, "feature dtype must be F32 or BF16");
   int kmax = 0, F = scenes[0].F, tdt = scenes[0].table_dtype;
@@ -256,7 +270,9 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
   static_assert(ENC_NT == QT, "tile size");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool f16 = tdt == OCTA_F16, bf = feat_dtype == OCTA_BF16;
-  const bool full = scenes[0].query_form == OCTA_FORM_TRILINEAR_VERTEX;
+  const int form = scenes[0].query_form;
+  p.normal = q->normal;
+  p.disparity = q->disparity;
   const octa_tuning tu = tuning_snapshot();
 #define OCTA_ENC_FORM(F_, TT_, KP_, FORM_)                                                       \
   return bf ? launch_persistent(encode_kernel<F_, TT_, __nv_bfloat16, KP_, FORM_>, smem, p, st,  \
@@ -264,7 +280,10 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
             : launch_persistent(encode_kernel<F_, TT_, float, KP_, FORM_>, smem, p, st, ENC_NT,  \
                                 tu.encode_ctas_per_sm, tu.fwd_order);
 #define OCTA_ENC(F_, TT_, KP_)                                    \
-  if (full) {                                                     \
+  if (form == OCTA_FORM_SHIFTED) {                                \
+    OCTA_ENC_FORM(F_, TT_, KP_, OCTA_FORM_SHIFTED)                \
+  }                                                               \
+  if (form == OCTA_FORM_TRILINEAR_VERTEX) {                       \
     OCTA_ENC_FORM(F_, TT_, KP_, OCTA_FORM_TRILINEAR_VERTEX)       \
   }                                                               \
   OCTA_ENC_FORM(F_, TT_, KP_, OCTA_FORM_CELL_BILINEAR)
@@ -297,6 +316,8 @@ extern "C" int octa_query_fwd(const octa_scene* scenes, int32_t n_scenes, const 
   QueryParams p;
   int rc = build_query_params(scenes, n_scenes, q, nullptr, p);
   if (rc) return rc;
+  rc = reject_shifted(scenes, n_scenes);
+  if (rc) return rc;
   rc = check_one_form(scenes, n_scenes, node_idx);
   if (rc) return rc;
   if (q->n > 0 && !rgb) return fail(OCTA_EINVAL, "rgb must be non-NULL");
@@ -321,6 +342,8 @@ extern "C" int octa_query_bwd(const octa_scene* scenes, int32_t n_scenes, const 
   if (!grads) return fail(OCTA_EINVAL, "grads must be non-NULL");
   QueryParams p;
   int rc = build_query_params(scenes, n_scenes, q, grads, p);
+  if (rc) return rc;
+  rc = reject_shifted(scenes, n_scenes);
   if (rc) return rc;
   if (q->n > 0 && !d_rgb) return fail(OCTA_EINVAL, "d_rgb must be non-NULL");
   p.d_rgb = d_rgb;
@@ -347,6 +370,8 @@ extern "C" int octa_train_fused(const octa_scene* scenes, int32_t n_scenes, cons
   for (int s = 0; s <= OCTA_MAX_SCENES; ++s) q.scene_start[s] = pairs->scene_start[s];
   QueryParams p;
   int rc = build_query_params(scenes, n_scenes, &q, grads, p);
+  if (rc) return rc;
+  rc = reject_shifted(scenes, n_scenes);
   if (rc) return rc;
   const bool bf16 = scenes[0].weight_dtype == OCTA_BF16;
   for (int s = 0; s < n_scenes; ++s)
@@ -395,6 +420,8 @@ extern "C" int octa_train_step_batched(const octa_scene* scenes, int32_t n_scene
   for (int s = 0; s <= OCTA_MAX_SCENES; ++s) q.scene_start[s] = pairs->scene_start[s];
   QueryParams p;
   int rc = build_query_params(scenes, n_scenes, &q, grads, p);
+  if (rc) return rc;
+  rc = reject_shifted(scenes, n_scenes);
   if (rc) return rc;
   for (int s = 0; s < n_scenes; ++s)
     if (scenes[s].weight_dtype != OCTA_BF16)

@@ -1,0 +1,89 @@
+"""The disparity-shifted lookup (OCTA_FORM_SHIFTED: Eq. 7-9 with Eq. 10 and
+Eq. 6) in octa_encode against the FP64 oracle: the 24 vertex entries of every
+level bit-exact (the reflection, the per-cell direction, the fold and the
+triangle decided in binary32 in the same order on both sides), the features
+within the binary32 bound of a 24-term blend."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import octaoctree_oracle as O
+from paper_2606_08469_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2606_08469_gb300 import build
+    build.build()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _case(seed, depth, V, F, n, tdt=torch.float32, dmax=10.0):
+    from paper_2606_08469_gb300 import _lib as L
+    from paper_2606_08469_gb300 import api as A
+    tree = A.octree_build(seed, depth, 0.6, V)
+    ot = O.build_tree(seed, depth, 0.6, V)
+    tables = I.make_tables(seed + 1, tree.num_texels, F, 0.3)
+    if tdt == torch.float16:
+        tables = tables.astype(np.float16).astype(np.float32)
+    weights = [dev(W) for W in I.make_mlp(seed + 2, [(depth + 1) * F, 16, 3])]
+    sc = A.Scene(tree, dev(tables).to(tdt).contiguous(), weights, device=DEV,
+                 query_form=L.OCTA_FORM_SHIFTED)
+    g = I.rng(seed + 3)
+    x = g.random((n, 3)).astype(np.float32)
+    w = I.unit_vectors(g, n).astype(np.float32)
+    nrm = (I.unit_vectors(g, n) * g.uniform(0.5, 2.0, (n, 1))).astype(np.float32)
+    d = g.uniform(0.0, dmax, n).astype(np.float32)
+    d[:7] = 0.0                                   # the unshifted limit
+    return sc, ot, tables, x, w, nrm, d
+
+
+@pytest.mark.parametrize("seed,depth,V,F,tdt", [
+    (1400, 4, [9, 9, 5, 5, 3], 4, torch.float32),
+    (1401, 6, [17, 17, 9, 9, 5, 5, 3], 8, torch.float16),
+    (1402, 2, [3, 5, 9], 8, torch.float32),
+])
+def test_shifted_encoding_matches_oracle(seed, depth, V, F, tdt):
+    from paper_2606_08469_gb300 import api as A
+    sc, ot, tables, x, w, nrm, d = _case(seed, depth, V, F, 4001, tdt)
+    feat, _, addr = A.octa_encode(sc, dev(x), dev(w), want_addr=True, normal=dev(nrm),
+                                  disparity=dev(d))
+    ref = O.encode_features_shifted(ot, tables, x, w, nrm, d)
+    np.testing.assert_array_equal(addr.cpu().numpy(), ref.addr.reshape(len(x), depth + 1, 24))
+    bound = 64 * U32 * np.abs(tables).max()
+    np.testing.assert_allclose(feat.cpu().numpy(), ref.h, rtol=1e-6, atol=bound)
+
+
+def test_shifted_global_walk_and_errors():
+    """A tree larger than the staged capacity; the entry points that do not
+    evaluate the shifted form refuse it, and missing inputs are refused."""
+    from paper_2606_08469_gb300 import _lib as L
+    from paper_2606_08469_gb300 import api as A
+    V = [3, 3, 3, 3, 3]
+    tree = A.octree_build(5, 4, 1.0, V)
+    assert tree.num_nodes > 2048
+    ot = O.build_tree(5, 4, 1.0, V)
+    tables = I.make_tables(6, tree.num_texels, 4, 0.3)
+    sc = A.Scene(tree, dev(tables), [dev(W) for W in I.make_mlp(7, [20, 32, 32, 3])], device=DEV,
+                 query_form=L.OCTA_FORM_SHIFTED)
+    g = I.rng(8)
+    x = g.random((2000, 3)).astype(np.float32)
+    w = I.unit_vectors(g, 2000).astype(np.float32)
+    nrm = I.unit_vectors(g, 2000).astype(np.float32)
+    d = g.uniform(0, 5, 2000).astype(np.float32)
+    feat, _, addr = A.octa_encode(sc, dev(x), dev(w), want_addr=True, normal=dev(nrm),
+                                  disparity=dev(d))
+    ref = O.encode_features_shifted(ot, tables, x, w, nrm, d)
+    np.testing.assert_array_equal(addr.cpu().numpy(), ref.addr.reshape(2000, 5, 24))
+    np.testing.assert_allclose(feat.cpu().numpy(), ref.h, rtol=1e-6, atol=64 * U32 * 2.5)
+    with pytest.raises(L.OctaError):
+        A.octa_encode(sc, dev(x), dev(w))                        # no normal / disparity
+    with pytest.raises(L.OctaError):
+        A.octa_query_fwd(sc, dev(x), dev(w))                     # encoding only
