@@ -159,15 +159,16 @@ typedef struct octa_queries {
 } octa_queries;
 
 /* octa_encode -- the OctaOctree encoding alone in the scenes' query form
- * (all scenes of a call share it; Eq. 10 single-cell bilinear form or Eq. 10
- * with Eq. 6, then Eq. 11): each query writes its own scene's K*F features
+ * (all scenes of a call share it; Eq. 10 single-cell bilinear form, Eq. 10
+ * with Eq. 6, or the shifted form of Eq. 7-9 with q->normal and
+ * q->disparity; then Eq. 11): each query writes its own scene's K*F features
  * into a row of row_stride elements (row_stride >= K*F of every scene;
  * unused tail left untouched).  feat_dtype OCTA_F32 or OCTA_BF16.  Absent
  * levels write zeros.  node_idx: device [n][K_max] int32 or NULL (K_max =
  * largest K of the scenes, unused columns -1; cell form only).
  * texel_addr: device int32 or NULL, -1 where absent: cell form [n][K_max][4]
- * (corner k = a + 2b for corner (i0+a, j0+b)); trilinear vertex form
- * [n][K_max][24] (neighbour j = 0..7, offset (j & 1, j >> 1 & 1, j >> 2)
+ * (corner k = a + 2b for corner (i0+a, j0+b)); trilinear vertex and
+ * shifted forms [n][K_max][24] (neighbour j = 0..7, offset (j & 1, j >> 1 & 1, j >> 2)
  * from the lower cell, times vertex k = 0..2: entry 3 j + k).             */
 int octa_encode(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
                 void* features, int32_t feat_dtype, int64_t row_stride,
