@@ -13,6 +13,7 @@ namespace {
 
 constexpr int kTraceThreads = 256;
 constexpr int kPlaneFloats = 13;
+constexpr int kPlaneStride = 16;  // shared-memory row of a plane: four float4
 constexpr int kSphereFloats = 4;
 
 // ((a0 b0 + a1 b1) + a2 b2), one rounding per operation (no contraction).
@@ -29,9 +30,14 @@ __global__ void __launch_bounds__(kTraceThreads) trace_kernel(
     int n_spheres, const float* __restrict__ origin, int rays_per_origin,
     const float* __restrict__ dir, int64_t n_rays, float t_min, float* __restrict__ hit,
     float* __restrict__ query_dir, int32_t* __restrict__ prim_out, float* __restrict__ t_out) {
-  __shared__ float pl[OCTA_MAX_PRIMS * kPlaneFloats];
-  __shared__ float sp[OCTA_MAX_PRIMS * kSphereFloats];
-  for (int i = threadIdx.x; i < n_planes * kPlaneFloats; i += blockDim.x) pl[i] = planes_g[i];
+  __shared__ float4 pl4[OCTA_MAX_PRIMS * kPlaneStride / 4];
+  __shared__ float4 sp4[OCTA_MAX_PRIMS];
+  float* pl = reinterpret_cast<float*>(pl4);
+  float* sp = reinterpret_cast<float*>(sp4);
+  for (int i = threadIdx.x; i < n_planes * kPlaneStride; i += blockDim.x) {
+    const int k = i / kPlaneStride, e = i % kPlaneStride;
+    pl[i] = e < kPlaneFloats ? planes_g[k * kPlaneFloats + e] : 0.f;
+  }
   for (int i = threadIdx.x; i < n_spheres * kSphereFloats; i += blockDim.x) sp[i] = spheres_g[i];
   __syncthreads();
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -41,33 +47,41 @@ __global__ void __launch_bounds__(kTraceThreads) trace_kernel(
     const float d0 = __ldcs(dir + 3 * i), d1 = __ldcs(dir + 3 * i + 1), d2 = __ldcs(dir + 3 * i + 2);
     float best = INFINITY;
     int best_id = -1;
+    // Only the decisions' values are fixed; work whose outcome cannot
+    // change the hit is skipped (a patch test beyond t's range, an unbounded
+    // plane's patch test, a square root of a negative discriminant).
     for (int k = 0; k < n_planes; ++k) {
-      const float* q = pl + k * kPlaneFloats;
-      const float den = dot3_rn(d0, d1, d2, q[3], q[4], q[5]);
-      const float num = dot3_rn(__fsub_rn(q[0], o0), __fsub_rn(q[1], o1), __fsub_rn(q[2], o2),
-                                q[3], q[4], q[5]);
+      const float4 qa = pl4[k * 4], qb = pl4[k * 4 + 1];  // p, n.x | n.yz, t1.xy
+      const float den = dot3_rn(d0, d1, d2, qa.w, qb.x, qb.y);
+      if (den == 0.f) continue;
+      const float num = dot3_rn(__fsub_rn(qa.x, o0), __fsub_rn(qa.y, o1), __fsub_rn(qa.z, o2),
+                                qa.w, qb.x, qb.y);
       const float t = __fdiv_rn(num, den);
-      const float r0 = __fsub_rn(__fadd_rn(o0, __fmul_rn(t, d0)), q[0]);
-      const float r1 = __fsub_rn(__fadd_rn(o1, __fmul_rn(t, d1)), q[1]);
-      const float r2 = __fsub_rn(__fadd_rn(o2, __fmul_rn(t, d2)), q[2]);
-      const float a = dot3_rn(r0, r1, r2, q[6], q[7], q[8]);
-      const float b = dot3_rn(r0, r1, r2, q[9], q[10], q[11]);
-      if (den != 0.f && t > t_min && t < best && fabsf(a) <= q[12] && fabsf(b) <= q[12]) {
-        best = t;
-        best_id = k;
+      if (!(t > t_min && t < best)) continue;
+      const float4 qc = pl4[k * 4 + 2], qd = pl4[k * 4 + 3];  // t1.z, t2 | h
+      if (qd.x != INFINITY) {  // a patch: the hit must lie on it
+        const float r0 = __fsub_rn(__fadd_rn(o0, __fmul_rn(t, d0)), qa.x);
+        const float r1 = __fsub_rn(__fadd_rn(o1, __fmul_rn(t, d1)), qa.y);
+        const float r2 = __fsub_rn(__fadd_rn(o2, __fmul_rn(t, d2)), qa.z);
+        const float a = dot3_rn(r0, r1, r2, qb.z, qb.w, qc.x);
+        const float b = dot3_rn(r0, r1, r2, qc.y, qc.z, qc.w);
+        if (!(fabsf(a) <= qd.x && fabsf(b) <= qd.x)) continue;
       }
+      best = t;
+      best_id = k;
     }
     for (int s = 0; s < n_spheres; ++s) {
-      const float* q = sp + s * kSphereFloats;
-      const float c0 = __fsub_rn(o0, q[0]), c1 = __fsub_rn(o1, q[1]), c2 = __fsub_rn(o2, q[2]);
+      const float4 q = sp4[s];
+      const float c0 = __fsub_rn(o0, q.x), c1 = __fsub_rn(o1, q.y), c2 = __fsub_rn(o2, q.z);
       const float bq = dot3_rn(c0, c1, c2, d0, d1, d2);
-      const float cq = __fsub_rn(dot3_rn(c0, c1, c2, c0, c1, c2), __fmul_rn(q[3], q[3]));
+      const float cq = __fsub_rn(dot3_rn(c0, c1, c2, c0, c1, c2), __fmul_rn(q.w, q.w));
       const float disc = __fsub_rn(__fmul_rn(bq, bq), cq);
-      const float sq = __fsqrt_rn(fmaxf(disc, 0.f));
+      if (!(disc >= 0.f)) continue;
+      const float sq = __fsqrt_rn(disc);
       const float t0 = __fsub_rn(-bq, sq);
       const float t1 = __fadd_rn(-bq, sq);
       const float t = t0 > t_min ? t0 : t1;
-      if (disc >= 0.f && t > t_min && t < best) {
+      if (t > t_min && t < best) {
         best = t;
         best_id = n_planes + s;
       }
