@@ -284,28 +284,6 @@ def encode_leg(dev, flush, stream, steps, peaks):
     for _ in range(3):
         fn()
     t = _timed(fn, steps, flush, stream)
-    rgb = torch.empty((len(x), 3), dtype=torch.float32, device=dev)
-    fwd = lambda: api.octa_query_fwd(sc, X, Om, rgb=rgb)
-    for _ in range(3):
-        fwd()
-    t_fwd = _timed(fwd, steps, flush, stream)
-    # the shifted form (Eq. 7-9) on the same frame: seeded normals and
-    # disparities in [0, 10]
-    g = I.rng(cfg.seed("queries") + 77)
-    nrm = WL.to_dev(I.unit_vectors(g, len(x)).astype(np.float32), dev)
-    disp = WL.to_dev(g.uniform(0.0, 10.0, len(x)).astype(np.float32), dev)
-    ss = api.Scene(tree, T, [WL.to_dev(w, dev).to(torch.bfloat16) for w in mlp], device=dev,
-                   query_form=L.OCTA_FORM_SHIFTED)
-    arr_s, ns_s = api._scene_array(ss)
-    qs = api._queries(X, Om, None)
-    qs.normal, qs.disparity = nrm.data_ptr(), disp.data_ptr()
-
-    def fn_shift():
-        api.L.check(lib.octa_encode(arr_s, ns_s, api.C.byref(qs), api._ptr(feat), api.L.OCTA_BF16,
-                                    W, None, None, None, api._stream()), "octa_encode")
-    for _ in range(3):
-        fn_shift()
-    t_shift = _timed(fn_shift, steps, flush, stream)
     table_bytes = tree.num_texels * cfg.F * 2
     alg = len(x) * (24 + 2 * W) + table_bytes
     peak = float(peaks.get("hbm_gbs", 6800.0))

@@ -412,7 +412,9 @@ typedef struct octa_tuning {
   int32_t fwd_threads_per_query; /* tensor-core forward: 1 (default) or 2
                                   threads per query (256-thread CTAs, each
                                   thread gathering half of the levels)     */
-  int32_t reserved[2];
+  int32_t encode_threads_per_query; /* octa_encode, cell form: 1 (default)
+                                  or 2, as fwd_threads_per_query           */
+  int32_t reserved;
 } octa_tuning;
 int octa_set_tuning(const octa_tuning* t);   /* NULL restores the defaults */
 int octa_get_tuning(octa_tuning* t);

@@ -134,7 +134,7 @@ class octa_tuning(C.Structure):
     _fields_ = [("fwd_ctas_per_sm", C.c_int32), ("encode_ctas_per_sm", C.c_int32),
                 ("engine_ctas_per_sm", C.c_int32), ("fwd_order", C.c_int32),
                 ("train_order", C.c_int32), ("fwd_threads_per_query", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("encode_threads_per_query", C.c_int32), ("reserved", C.c_int32)]
 
 
 class octa_step_options(C.Structure):

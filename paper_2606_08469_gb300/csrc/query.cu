@@ -24,10 +24,13 @@ namespace octa {
 // output rows are packed), so the feature stream is written coalesced.
 constexpr int ENC_NT = 128;
 
-template <int F, typename TT, typename OT, int KP, int FORM = OCTA_FORM_CELL_BILINEAR>
-__global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ QueryParams p) {
+template <int F, typename TT, typename OT, int KP, int FORM = OCTA_FORM_CELL_BILINEAR,
+          int TPQ = 1>
+__global__ void __launch_bounds__(ENC_NT * TPQ) encode_kernel(const __grid_constant__ QueryParams p) {
+  static_assert(TPQ == 1 || FORM == OCTA_FORM_CELL_BILINEAR, "threads per query: cell form");
+  constexpr int NTH = ENC_NT * TPQ;  // TPQ threads per query, thread par gathers levels l % TPQ
   extern __shared__ __align__(16) uint8_t stage[];
-  const int q = threadIdx.x;
+  const int q = threadIdx.x % ENC_NT, par = threadIdx.x / ENC_NT;
   OT* out = static_cast<OT*>(p.features);
   int2* tree_sm = p.tree_cap > 0 ? reinterpret_cast<int2*>(stage + p.tree_off) : nullptr;
   const int2* tree = nullptr;
@@ -41,7 +44,7 @@ __global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ 
     if (tile + wr.step < wr.end) next = load_tile_query(p, tile + wr.step, q, ENC_NT);
     if (s != cur) {
       __syncthreads();
-      tree = stage_tree(p, sc, tree_sm, p.tree_cap, q, ENC_NT);
+      tree = stage_tree(p, sc, tree_sm, p.tree_cap, threadIdx.x, NTH);
       cur = s;
     }
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * ENC_NT;
@@ -73,8 +76,8 @@ __global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ 
     else if constexpr (FORM == OCTA_FORM_TRILINEAR_VERTEX)
       gather_full_query<F, TT, KP>(p, sc, tree, in, q0 + q, q < nq, stage_row);
     else
-      locate_gather_query<F, TT, KP, sizeof(OT) == 2>(p, sc, tree, in, q0 + q, q < nq, 0, nullptr,
-                                                       nullptr, q, ENC_NT, stage_row);
+      locate_gather_query<F, TT, KP, sizeof(OT) == 2, TPQ>(p, sc, tree, in, q0 + q, q < nq, par,
+                                                            nullptr, nullptr, q, ENC_NT, stage_row);
     __syncthreads();
     const bool packed = p.row_stride == W && rb == row_bytes &&
                         (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
@@ -82,9 +85,9 @@ __global__ void __launch_bounds__(ENC_NT) encode_kernel(const __grid_constant__ 
       const int chunks = nq * row_bytes / 16;
       uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(out + q0 * W));
       const uint4* src = reinterpret_cast<const uint4*>(stage);
-      for (int c = q; c < chunks; c += ENC_NT) dst[c] = src[c];
+      for (int c = threadIdx.x; c < chunks; c += NTH) dst[c] = src[c];
     } else {
-      for (int i = q; i < nq * W; i += ENC_NT) {
+      for (int i = threadIdx.x; i < nq * W; i += NTH) {
         const int r = i / W, k = i % W;
         out[(q0 + r) * p.row_stride + k] =
             *reinterpret_cast<const OT*>(stage + r * rb + k * int(sizeof(OT)));
@@ -286,6 +289,13 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
   if (form == OCTA_FORM_TRILINEAR_VERTEX) {                       \
     OCTA_ENC_FORM(F_, TT_, KP_, OCTA_FORM_TRILINEAR_VERTEX)       \
   }                                                               \
+  if (tu.encode_threads_per_query == 2) {                         \
+    return bf ? launch_persistent(                                \
+                    encode_kernel<F_, TT_, __nv_bfloat16, KP_, OCTA_FORM_CELL_BILINEAR, 2>, \
+                    smem, p, st, 2 * ENC_NT, tu.encode_ctas_per_sm, tu.fwd_order)           \
+              : launch_persistent(encode_kernel<F_, TT_, float, KP_, OCTA_FORM_CELL_BILINEAR, 2>, \
+                                  smem, p, st, 2 * ENC_NT, tu.encode_ctas_per_sm, tu.fwd_order); \
+  }                                                               \
   OCTA_ENC_FORM(F_, TT_, KP_, OCTA_FORM_CELL_BILINEAR)
 #define OCTA_ENC_KP(F_, TT_)      \
   if (kmax <= 10) {               \
@@ -474,7 +484,8 @@ extern "C" int octa_set_tuning(const octa_tuning* t) {
   }
   if (t->fwd_ctas_per_sm < 0 || t->encode_ctas_per_sm < 0 || t->engine_ctas_per_sm < 0 ||
       t->fwd_order < 0 || t->fwd_order > 2 || t->train_order < 0 || t->train_order > 2 ||
-      t->fwd_threads_per_query < 0 || t->fwd_threads_per_query > 2)
+      t->fwd_threads_per_query < 0 || t->fwd_threads_per_query > 2 ||
+      t->encode_threads_per_query < 0 || t->encode_threads_per_query > 2)
     return fail(OCTA_EINVAL, "tuning values out of range");
   tuning() = *t;
   return OCTA_OK;
