@@ -364,3 +364,34 @@ def test_full_form_bf16_fused_and_one_launch_training():
         torch.testing.assert_close(d.loss, c.loss, rtol=1e-6, atol=0)
         sc_, sd_ = A.read_scaler(c.scaler), A.read_scaler(d.scaler)
         assert (sc_.step, sc_.skipped) == (sd_.step, sd_.skipped)
+
+
+def test_full_form_config3_frame_samples():
+    """The full-form legs' configuration at full size: config [3]'s 1280x720
+    G-buffer on its depth-8 octree with vertex maps 65 ... 9, FP16 tables.
+    On 2,000 sampled queries: the 24 entries of every level bit-exact, the
+    BF16 features within BF16 rounding of the oracle's, the tensor-core
+    forward within the BF16 path's 1e-2 normwise bound."""
+    from paper_2606_08469_gb300 import _lib as L
+    from paper_2606_08469_gb300 import api as A
+    cfg = I.CONFIGS[3]
+    V = [r + 1 for r in cfg.R]
+    tree = A.octree_build(cfg.seed("tree"), cfg.max_depth, cfg.p_base, V)
+    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, V)
+    tables = I.make_tables(cfg.seed("tables"), tree.num_texels, cfg.F, cfg.sigma)
+    tq = tables.astype(np.float16).astype(np.float32)
+    mlp = I.make_mlp(cfg.seed("mlp"), [tree.num_levels * cfg.F, 64, 64, 3])
+    sc = A.Scene(tree, dev(tq).half().contiguous(), [dev(W).to(torch.bfloat16) for W in mlp],
+                 device=DEV, query_form=L.OCTA_FORM_TRILINEAR_VERTEX)
+    x, om = I.gbuffer_queries(cfg.seed("queries"), 1280, 720)
+    feat, _, addr = A.octa_encode(sc, dev(x), dev(om), feat_dtype=torch.bfloat16, want_addr=True)
+    rgb, _, _ = A.octa_query_fwd(sc, dev(x), dev(om))
+    rows = np.random.default_rng(4).choice(len(x), 2000, replace=False)
+    ref = O.encode_features_full(ot, tq, x[rows], om[rows])
+    K = tree.num_levels
+    np.testing.assert_array_equal(addr.cpu().numpy()[rows], ref.addr.reshape(len(rows), K, 24))
+    np.testing.assert_allclose(feat.float().cpu().numpy()[rows], ref.h, rtol=2 ** -8,
+                               atol=64 * U32 * np.abs(tq).max())
+    r_ref, _ = O.query_forward(ot, tq, mlp, x[rows], om[rows], form="full")
+    got = rgb.cpu().numpy()[rows]
+    assert np.linalg.norm(got - r_ref) <= 1e-2 * np.linalg.norm(r_ref)
