@@ -21,6 +21,9 @@ fusion or reordering of its own:
                     trilinear weights) with Eq. 6 (barycentric on vertex maps)
   encode_features_shifted  the same with Eq. 7-9's disparity-shifted
                     direction per cell (reflect_f32, shifted_direction_f32)
+  hash_encode, disparity  the predictor g_psi of Eq. 7 (Section 3.5): a
+                    multiresolution hash encoding of x (Mueller et al. 2022)
+                    and a bias-free ReLU MLP on [encoding, omega_r], exp out
   mlp_forward       Eq. 13 (decoder; ReLU hidden layers, exp output)
   residual_loss     Eq. 14 with the Monte-Carlo target of Eq. 3 (M = 1)
   residual_loss_multi  Eq. 14 with Eq. 3's M-sample target
@@ -916,3 +919,73 @@ def trace_rays_f32(planes, spheres, o, d, t_min):
                 prim = np.where(ok, P + S + 2 * a + wi, prim).astype(np.int32)
         hit = (o + (best[:, None] * d).astype(f)).astype(f)
     return best, prim, hit
+
+
+# ---------------------------------------------------------------------------
+# The disparity predictor g_psi (Eq. 7, Section 3.5): a multiresolution hash
+# encoding (Mueller, Evans, Schied & Keller 2022, written from its published
+# definition) and a tiny MLP
+# ---------------------------------------------------------------------------
+
+HASH_PRIMES = (1, 2654435761, 805459861)
+
+
+def hash_resolutions(levels, n_min, n_max):
+    """Per-level grid resolution N_l = floor(n_min b^l), b = (n_max /
+    n_min)^(1 / (levels - 1)), in FP64."""
+    if levels == 1:
+        return [int(n_min)]
+    b = np.exp((np.log(n_max) - np.log(n_min)) / (levels - 1))
+    return [int(np.floor(n_min * b ** l)) for l in range(levels)]
+
+
+def hash_index(i, j, k, res, T):
+    """Entry of grid vertex (i, j, k) in a level's table of T entries: the
+    dense index i + j (N + 1) + k (N + 1)^2 when the (N + 1)^3 vertices fit,
+    else the spatial hash (i pi_1 xor j pi_2 xor k pi_3) mod T over 32-bit
+    unsigned integers."""
+    side = res + 1
+    i = np.asarray(i, dtype=np.uint64)
+    j = np.asarray(j, dtype=np.uint64)
+    k = np.asarray(k, dtype=np.uint64)
+    if side ** 3 <= T:
+        return (i + j * side + k * side * side).astype(np.int64)
+    m = np.uint64(0xFFFFFFFF)
+    h = ((i * np.uint64(HASH_PRIMES[0])) & m) ^ ((j * np.uint64(HASH_PRIMES[1])) & m) ^ \
+        ((k * np.uint64(HASH_PRIMES[2])) & m)
+    return (h % np.uint64(T)).astype(np.int64)
+
+
+def hash_encode(table, res, x):
+    """The multiresolution hash encoding of positions x [N][3] in [0, 1]:
+    per level l, p = x N_l (binary32), the cell i0 = min(floor(p), N_l - 1)
+    per axis, f = p - i0, and the trilinear blend (FP64 weights) of the
+    features of the cell's eight vertices; levels concatenated.  table
+    [L][T][F].  Returns [N][L F]."""
+    tab = np.asarray(table, dtype=np.float64)
+    L, T, F = tab.shape
+    x32 = np.clip(np.asarray(x, dtype=np.float32), np.float32(0), np.float32(1))
+    out = np.zeros((len(x32), L * F))
+    for l in range(L):
+        N = int(res[l])
+        p = x32 * np.float32(N)
+        i0 = np.minimum(np.floor(p), np.float32(N - 1)).astype(np.int64)
+        f = p.astype(np.float64) - i0
+        for c in range(8):
+            d = np.array([c & 1, (c >> 1) & 1, c >> 2])
+            idx = hash_index(i0[:, 0] + d[0], i0[:, 1] + d[1], i0[:, 2] + d[2], N, T)
+            w = np.ones(len(x32))
+            for a in range(3):
+                w *= f[:, a] if d[a] else 1.0 - f[:, a]
+            out[:, l * F:(l + 1) * F] += w[:, None] * tab[l][idx]
+    return out
+
+
+def disparity(table, res, weights, x, omega, normal):
+    """d = g_psi(x, omega_r) (Eq. 7): the decoder-like MLP (bias-free, ReLU
+    hidden, exp output, so d > 0) on [hash_encode(x), omega_r], omega_r from
+    reflect_f32.  Returns d [N] (FP64)."""
+    om_r = reflect_f32(omega, normal).astype(np.float64)
+    inp = np.concatenate([hash_encode(table, res, x), om_r], axis=1)
+    out, _, _ = mlp_forward(weights, inp)
+    return out[:, 0]

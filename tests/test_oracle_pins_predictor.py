@@ -1,0 +1,81 @@
+"""Pins of the oracle's disparity predictor g_psi (CPU only): the level
+resolutions' geometric progression, the hash index's structure (a bijection
+in the dense regime; xor-separable with pi_1 = 1 in the hashed one), exact
+reproduction of a linear field by the trilinear encoding, and a hand-built
+MLP whose output is exp(omega_r . e_z)."""
+import numpy as np
+import pytest
+
+from oracle import octaoctree_oracle as O
+from paper_2606_08469_gb300 import inputs as I
+
+
+def test_resolutions():
+    r = O.hash_resolutions(8, 16, 512)
+    assert r[0] == 16 and r[-1] == 512
+    ratios = [b / a for a, b in zip(r[:-1], r[1:])]
+    assert all(1.5 < q < 1.75 for q in ratios)        # b = 32^(1/7) = 1.64, floored
+    assert O.hash_resolutions(1, 16, 512) == [16]
+
+
+def test_hash_index_structure():
+    # dense: every vertex of a 9^3 grid gets its own entry in [0, 729)
+    g = np.stack(np.meshgrid(np.arange(9), np.arange(9), np.arange(9), indexing="ij"), -1).reshape(-1, 3)
+    d = O.hash_index(g[:, 0], g[:, 1], g[:, 2], 8, 4096)
+    assert sorted(d.tolist()) == list(range(729))
+    # hashed (40^3 > T): the first prime is 1 and the hash xor-separates
+    T = 1 << 12
+    rng = np.random.default_rng(1)
+    i, j, k = (rng.integers(0, 40, 500) for _ in range(3))
+    h = O.hash_index(i, j, k, 39, T)
+    z = np.zeros_like(i)
+    assert np.all(O.hash_index(i, z, z, 39, T) == i % T)
+    assert np.all(h == O.hash_index(i, z, z, 39, T) ^ O.hash_index(z, j, z, 39, T)
+                  ^ O.hash_index(z, z, k, 39, T))
+    assert np.all((h >= 0) & (h < T)) and O.hash_index(0, 0, 0, 39, T) == 0
+    assert len(np.unique(h)) > 400                     # the primes spread the vertices
+
+
+@pytest.mark.parametrize("x_edge", [False, True])
+def test_encoding_reproduces_a_linear_field(x_edge):
+    """Dense levels whose entries hold a linear function of the vertex
+    coordinates: the trilinear blend returns that function at p = x N_l."""
+    res = [4, 7, 13]
+    T = 14 ** 3
+    F = 2
+    coef = np.array([[0.5, -1.0, 2.0, 0.25], [1.5, 0.75, -0.5, -1.0]])
+    table = np.zeros((len(res), T, F))
+    for l, N in enumerate(res):
+        g = np.stack(np.meshgrid(np.arange(N + 1), np.arange(N + 1), np.arange(N + 1),
+                                 indexing="ij"), -1).reshape(-1, 3)
+        idx = O.hash_index(g[:, 0], g[:, 1], g[:, 2], N, T)
+        for f in range(F):
+            table[l, idx, f] = g @ coef[f, :3] + coef[f, 3] * (l + 1)
+    x = I.rng(3).random((300, 3)).astype(np.float32)
+    if x_edge:
+        x[:50] = np.float32(1.0)
+        x[50:100, 0] = np.float32(0.0)
+    enc = O.hash_encode(table, res, x)
+    for l, N in enumerate(res):
+        p = (x * np.float32(N)).astype(np.float64)
+        for f in range(F):
+            want = p @ coef[f, :3] + coef[f, 3] * (l + 1)
+            np.testing.assert_allclose(enc[:, l * F + f], want, rtol=1e-12, atol=1e-12)
+
+
+def test_predictor_hand_mlp():
+    """W1 routes omega_r's z component into two ReLU units (+z, -z), W2 is
+    the identity, W3 = (1, -1): z = omega_r . e_z and d = exp(z)."""
+    res = [4, 8]
+    table = I.rng(4).normal(size=(2, 64, 2))
+    W1 = np.zeros((2, 2 * 2 + 3))
+    W1[0, 6], W1[1, 6] = 1.0, -1.0
+    W2 = np.eye(2)
+    W3 = np.array([[1.0, -1.0]])
+    g = I.rng(5)
+    x = g.random((200, 3)).astype(np.float32)
+    w = I.unit_vectors(g, 200).astype(np.float32)
+    n = I.unit_vectors(g, 200).astype(np.float32)
+    d = O.disparity(table, res, [W1, W2, W3], x, w, n)
+    r = O.reflect_f32(w, n).astype(np.float64)
+    np.testing.assert_allclose(d, np.exp(r[:, 2]), rtol=1e-14)
