@@ -352,6 +352,16 @@ def encode_full_leg(dev, flush, stream, steps, peaks):
     for _ in range(3):
         fn_shift()
     t_shift = _timed(fn_shift, steps, flush, stream)
+    # the disparity predictor g_psi that produces d (8 hash levels of 2^16
+    # entries, resolutions 16 .. 512, MLP 19-64-64-1)
+    res = [int(np.floor(16 * (512 / 16) ** (l / 7))) for l in range(8)]
+    ptab = g.uniform(-0.1, 0.1, (8, 1 << 16, 2)).astype(np.float32)
+    pred = api.Predictor(ptab, res, I.make_mlp(cfg.seed("mlp") + 5, [19, 64, 64, 1]), device=dev)
+    dout = torch.empty(len(x), dtype=torch.float32, device=dev)
+    fn_pred = lambda: api.octa_disparity(pred, X, Om, nrm, out=dout)
+    for _ in range(3):
+        fn_pred()
+    t_pred = _timed(fn_pred, steps, flush, stream)
     table_bytes = tree.num_texels * cfg.F * 2
     alg = len(x) * (24 + 2 * W) + table_bytes
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -363,6 +373,7 @@ def encode_full_leg(dev, flush, stream, steps, peaks):
                          "frac": round(ach / peak, 4), "algorithmic_bytes": alg,
                          "per_query": f"24 B in + {2 * W} B out, table {table_bytes} B once"},
             "shifted_encode_ms": round(t_shift, 4),
+            "predictor_ms": round(t_pred, 4),
             "shifted": "octa_encode in the disparity-shifted form (one direction per cell)",
             "tc_forward_ms": round(t_fwd, 4),
             "tc_forward": "octa_query_fwd in the full form, BF16 decoder 72-64-64-3 on the tensor cores"}

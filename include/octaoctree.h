@@ -256,6 +256,34 @@ int residual_loss_static(const float* L_p, const float* L_s, const float* E, con
                          const octa_scaler* scaler, double* loss_dev, float* dL_p, float* dL_s,
                          void* stream);
 
+/* ---- the disparity predictor g_psi (Eq. 7, Section 3.5) ---------------- */
+
+/* g_psi: a multiresolution hash encoding of x -- level l's grid has res[l]
+ * cells a side; p = x res[l] in binary32 (x clamped to [0,1]), cell
+ * i0 = min(floor(p), res[l] - 1) per axis, trilinear weights of p - i0;
+ * vertex (i, j, k) is entry i + j (N+1) + k (N+1)^2 of the level's table
+ * when (N+1)^3 <= T, else (i * 1 ^ j * 2654435761 ^ k * 805459861) mod T in
+ * 32-bit unsigned arithmetic (Mueller et al. 2022) -- concatenated with
+ * omega_r (the reflection of omega about the normal, as in the shifted
+ * form), into a bias-free MLP (2 levels + 3) -> 64 -> 64 -> 1 with ReLU
+ * hidden layers and an exp output, so the disparity d is positive.       */
+#define OCTA_PRED_HIDDEN 64
+#define OCTA_PRED_MAX_LEVELS 16
+typedef struct octa_predictor {
+  const float* table;          /* device [levels][2^log2_T][2] float32     */
+  const float* weights;        /* device W1 [64][2 levels + 3], W2 [64][64],*/
+                               /* W3 [1][64], row-major, back to back      */
+  int32_t levels;              /* 1..OCTA_PRED_MAX_LEVELS                  */
+  int32_t log2_T;              /* 4..24                                    */
+  int32_t res[OCTA_PRED_MAX_LEVELS]; /* cells a side per level, 1..65535  */
+} octa_predictor;
+
+/* octa_disparity -- d = g_psi(x, omega_r) for queries q (x, omega and
+ * normal; scene_start is not used).  disparity: device [n] float32, the
+ * shifted form's input.                                                   */
+int octa_disparity(const octa_predictor* pred, const octa_queries* q, float* disparity,
+                   void* stream);
+
 /* ---- the training regime of Section 4: M RHS samples per LHS sample ---- */
 
 /* residual_loss_multi -- Eq. 14 against Eq. 3's M-sample target:

@@ -143,6 +143,13 @@ class octa_step_options(C.Structure):
 
 
 OCTA_MAX_PRIMS = 64
+OCTA_PRED_HIDDEN = 64
+OCTA_PRED_MAX_LEVELS = 16
+
+
+class octa_predictor(C.Structure):
+    _fields_ = [("table", C.c_void_p), ("weights", C.c_void_p), ("levels", C.c_int32),
+                ("log2_T", C.c_int32), ("res", C.c_int32 * OCTA_PRED_MAX_LEVELS)]
 
 
 class octa_prims(C.Structure):
@@ -178,6 +185,7 @@ _SIGNATURES = {
                                       _P, _P, _P, _P, _P, C.c_size_t, _P]),
     "octa_trace_rays": (C.c_int, [C.POINTER(octa_prims), _P, C.c_int32, _P, C.c_int64, C.c_float,
                                   _P, _P, _P, _P, _P]),
+    "octa_disparity": (C.c_int, [C.POINTER(octa_predictor), C.POINTER(octa_queries), _P, _P]),
     "adam_step": (C.c_int, [C.POINTER(octa_param_group), C.c_int32, C.POINTER(octa_adam_cfg), _P,
                             _P, C.c_size_t, _P]),
     "octa_workspace_bytes": (C.c_size_t, [C.c_int32, C.c_int64]),

@@ -373,6 +373,44 @@ def octa_trace_rays(prims, origin, direction, rays_per_origin=1, t_min=1e-4, hit
     return hit, query_dir, prim, t
 
 
+class Predictor:
+    """The disparity predictor g_psi on the device: hash tables [L][T][2]
+    float32 (T a power of two), per-level resolutions, and the MLP
+    W1 [64][2L+3], W2 [64][64], W3 [1][64] float32."""
+
+    def __init__(self, table, res, weights, device="cuda"):
+        dev = torch.device(device)
+        self.table = torch.as_tensor(table, dtype=torch.float32).to(dev).contiguous()
+        L_, T, F = self.table.shape
+        assert F == 2 and T & (T - 1) == 0 and len(res) == L_
+        self.res = [int(r) for r in res]
+        self.weights = torch.cat([torch.as_tensor(W, dtype=torch.float32).reshape(-1)
+                                  for W in weights]).to(dev).contiguous()
+
+    def as_c(self):
+        p = L.octa_predictor()
+        p.table = self.table.data_ptr()
+        p.weights = self.weights.data_ptr()
+        p.levels = len(self.res)
+        p.log2_T = int(self.table.shape[1]).bit_length() - 1
+        for i, r in enumerate(self.res):
+            p.res[i] = r
+        return p
+
+
+def octa_disparity(pred, x, omega, normal, out=None, stream=None):
+    """d = g_psi(x, omega_r) per query (Eq. 7)."""
+    n = int(x.shape[0])
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=x.device)
+    q = _queries(x, omega, None)
+    q.normal = normal.data_ptr() if n else None
+    pc = pred.as_c()
+    L.check(_lib().octa_disparity(C.byref(pc), C.byref(q), _ptr(out), _stream(stream)),
+            "octa_disparity")
+    return out
+
+
 @dataclass
 class ParamGroup:
     param: torch.Tensor

@@ -1,0 +1,174 @@
+// The disparity predictor g_psi of Eq. 7 (Section 3.5): a multiresolution
+// hash encoding of the position and a tiny MLP on [encoding, omega_r].
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "gather.cuh"
+#include "octa_internal.h"
+
+namespace octa {
+namespace {
+
+constexpr int kPredThreads = 128;
+constexpr int kH = OCTA_PRED_HIDDEN;
+constexpr int kMaxIn = 2 * OCTA_PRED_MAX_LEVELS + 3;  // widest MLP input
+
+struct PredParams {
+  const float* table;
+  const float* weights;
+  const float* x;
+  const float* omega;
+  const float* normal;
+  float* disparity;
+  int64_t n;
+  int32_t levels;
+  uint32_t tmask;                  // T - 1
+  int32_t res[OCTA_PRED_MAX_LEVELS];
+  int32_t dense[OCTA_PRED_MAX_LEVELS];  // (res + 1)^3 <= T
+};
+
+// Entry of grid vertex (i, j, k) of a level (dense index or spatial hash).
+__device__ __forceinline__ uint32_t vertex_entry(uint32_t i, uint32_t j, uint32_t k, uint32_t side,
+                                                 bool dense, uint32_t tmask) {
+  if (dense) return i + side * (j + side * k);
+  return (i ^ (j * 2654435761u) ^ (k * 805459861u)) & tmask;
+}
+
+// One thread per query; the MLP's weights live in shared memory with W1's
+// rows padded to kMaxIn columns (zeros past the encoding's width), so every
+// loop has a compile-time trip count.
+__global__ void __launch_bounds__(kPredThreads) disparity_kernel(const __grid_constant__ PredParams p) {
+  __shared__ float w1[kH * kMaxIn];
+  __shared__ float w2[kH * kH];
+  __shared__ float w3[kH];
+  const int in_w = 2 * p.levels + 3;
+  for (int i = threadIdx.x; i < kH * kMaxIn; i += blockDim.x) {
+    const int o = i / kMaxIn, c = i % kMaxIn;
+    w1[i] = c < in_w ? p.weights[o * in_w + c] : 0.f;
+  }
+  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) w2[i] = p.weights[kH * in_w + i];
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) w3[i] = p.weights[kH * in_w + kH * kH + i];
+  __syncthreads();
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < p.n; q += stride) {
+    const float xs[3] = {clamp01(p.x[3 * q]), clamp01(p.x[3 * q + 1]), clamp01(p.x[3 * q + 2])};
+    float in[kMaxIn];
+#pragma unroll
+    for (int c = 0; c < kMaxIn; ++c) in[c] = 0.f;
+#pragma unroll
+    for (int l = 0; l < OCTA_PRED_MAX_LEVELS; ++l) {
+      if (l >= p.levels) break;
+      const int N = p.res[l];
+      const float fN = static_cast<float>(N);
+      int i0[3];
+      float f[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float pa = __fmul_rn(xs[a], fN);
+        i0[a] = min(static_cast<int>(floorf(pa)), N - 1);
+        f[a] = __fsub_rn(pa, static_cast<float>(i0[a]));
+      }
+      const float2* tab = reinterpret_cast<const float2*>(p.table) + size_t(l) * (p.tmask + 1u);
+      const bool dense = p.dense[l] != 0;
+      float2 t[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        t[c] = __ldg(tab + vertex_entry(i0[0] + (c & 1), i0[1] + ((c >> 1) & 1), i0[2] + (c >> 2),
+                                        N + 1, dense, p.tmask));
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float w = ((c & 1) ? f[0] : 1.f - f[0]) * (((c >> 1) & 1) ? f[1] : 1.f - f[1]) *
+                        ((c >> 2) ? f[2] : 1.f - f[2]);
+        s0 = fmaf(w, t[c].x, s0);
+        s1 = fmaf(w, t[c].y, s1);
+      }
+      in[2 * l] = s0;
+      in[2 * l + 1] = s1;
+    }
+    const float w0[3] = {p.omega[3 * q], p.omega[3 * q + 1], p.omega[3 * q + 2]};
+    const float n0[3] = {p.normal[3 * q], p.normal[3 * q + 1], p.normal[3 * q + 2]};
+    float wr[3];
+    reflect_f32_rn(w0, n0, wr);
+    // omega_r follows the encoding: columns 2 L .. 2 L + 2 of W1
+#pragma unroll
+    for (int l = 0; l <= OCTA_PRED_MAX_LEVELS; ++l)
+      if (l == p.levels) {
+        in[2 * l] = wr[0];
+        in[2 * l + 1] = wr[1];
+        in[2 * l + 2] = wr[2];
+      }
+    float h1[kH];
+#pragma unroll
+    for (int o = 0; o < kH; ++o) {
+      float s = 0.f;
+#pragma unroll
+      for (int c = 0; c < kMaxIn; ++c) s = fmaf(w1[o * kMaxIn + c], in[c], s);
+      h1[o] = fmaxf(s, 0.f);
+    }
+    float z = 0.f;
+#pragma unroll 4
+    for (int o = 0; o < kH; ++o) {
+      float s = 0.f;
+#pragma unroll
+      for (int c = 0; c < kH; ++c) s = fmaf(w2[o * kH + c], h1[c], s);
+      z = fmaf(w3[o], fmaxf(s, 0.f), z);
+    }
+    p.disparity[q] = expf(z);
+  }
+}
+
+int sm_count_here() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 148;
+}
+
+}  // namespace
+}  // namespace octa
+
+using namespace octa;
+
+extern "C" int octa_disparity(const octa_predictor* pred, const octa_queries* q, float* disparity,
+                              void* stream) {
+  clear_error();
+  if (!pred || !q) return fail(OCTA_EINVAL, "pred and q must be non-NULL");
+  if (pred->levels < 1 || pred->levels > OCTA_PRED_MAX_LEVELS)
+    return fail(OCTA_ERANGE, "predictor levels %d outside [1, %d]", pred->levels,
+                OCTA_PRED_MAX_LEVELS);
+  if (pred->log2_T < 4 || pred->log2_T > 24)
+    return fail(OCTA_ERANGE, "predictor log2_T %d outside [4, 24]", pred->log2_T);
+  if (!pred->table || !pred->weights) return fail(OCTA_EINVAL, "NULL predictor table or weights");
+  if (reinterpret_cast<uintptr_t>(pred->table) & 7u)
+    return fail(OCTA_EINVAL, "predictor table not 8-byte aligned");
+  if (q->n < 0) return fail(OCTA_EINVAL, "negative query count");
+  if (q->n == 0) return OCTA_OK;
+  if (!q->x || !q->omega || !q->normal || !disparity)
+    return fail(OCTA_EINVAL, "x, omega, normal and disparity must be non-NULL");
+  PredParams p{};
+  p.table = pred->table;
+  p.weights = pred->weights;
+  p.x = q->x;
+  p.omega = q->omega;
+  p.normal = q->normal;
+  p.disparity = disparity;
+  p.n = q->n;
+  p.levels = pred->levels;
+  const int64_t T = int64_t(1) << pred->log2_T;
+  p.tmask = static_cast<uint32_t>(T - 1);
+  for (int l = 0; l < pred->levels; ++l) {
+    const int N = pred->res[l];
+    if (N < 1 || N > 65535) return fail(OCTA_ERANGE, "predictor res[%d] = %d outside [1, 65535]", l, N);
+    p.res[l] = N;
+    const int64_t side = N + 1;
+    p.dense[l] = side * side * side <= T ? 1 : 0;
+  }
+  const int64_t want = (q->n + kPredThreads - 1) / kPredThreads;
+  const int blocks = static_cast<int>(std::min<int64_t>(want, 8LL * sm_count_here()));
+  disparity_kernel<<<blocks, kPredThreads, 0, static_cast<cudaStream_t>(stream)>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "octa_disparity: %s", cudaGetErrorString(e));
+  return OCTA_OK;
+}
