@@ -633,24 +633,39 @@ def mlp_forward(weights, h):
 FORMS = ("cell", "full")
 
 
-def _encode(tree, tables, x, omega, form):
-    """Encoding in the query form: "cell" (encode_features) or "full"
-    (encode_features_full); returns (h, addr [N][K][n_entries],
+def _encode(tree, tables, x, omega, form, normal=None, disparity=None):
+    """Encoding in the query form: "cell" (encode_features), "full"
+    (encode_features_full) or "shifted" (encode_features_shifted, with the
+    normal and disparity); returns (h, addr [N][K][n_entries],
     weight [N][K][n_entries])."""
     if form == "cell":
         e = encode_features(tree, tables, x, omega)
         return e, e.h, e.addr, e.weight
-    if form == "full":
-        e = encode_features_full(tree, tables, x, omega)
+    if form in ("full", "shifted"):
+        if form == "full":
+            e = encode_features_full(tree, tables, x, omega)
+        else:
+            e = encode_features_shifted(tree, tables, x, omega, normal, disparity)
         n, K = e.h.shape[0], tree.num_levels
         return e, e.h, e.addr.reshape(n, K, 24), e.weight.reshape(n, K, 24)
     raise ValueError(form)
 
 
-def query_forward(tree, tables, weights, x, omega, form="cell"):
-    """L_hat(x, omega): encoding then decoder.  Returns (rgb, encoding)."""
-    enc, h, _, _ = _encode(tree, tables, x, omega, form)
-    rgb, _, _ = mlp_forward(weights, h)
+def decoder_input(h, attrs):
+    """Eq. 12: the decoder sees [h, g], the per-query surface attributes g
+    (position, reflection direction, normal, albedo, roughness in the paper)
+    appended after the K F features; attrs None: h alone."""
+    if attrs is None:
+        return h
+    return np.concatenate([h, np.asarray(attrs, dtype=np.float64)], axis=1)
+
+
+def query_forward(tree, tables, weights, x, omega, form="cell", normal=None, disparity=None,
+                  attrs=None):
+    """L_hat(x, omega) = f_phi(h, g) (Eq. 13): encoding, the attributes of
+    Eq. 12 when given, then decoder.  Returns (rgb, encoding)."""
+    enc, h, _, _ = _encode(tree, tables, x, omega, form, normal, disparity)
+    rgb, _, _ = mlp_forward(weights, decoder_input(h, attrs))
     return rgb, enc
 
 
@@ -680,7 +695,7 @@ def residual_loss(Lp, Ls, E, w, eps=1e-2, rhs_grad=True, scale=1.0):
     return loss, dLp, dLs
 
 
-def query_backward(tree, tables, weights, x, omega, d_rgb, form="cell"):
+def query_backward(tree, tables, weights, x, omega, d_rgb, form="cell", attrs=None):
     """Gradients of sum(d_rgb * L_hat) w.r.t. the table and the weights.
 
     Decoder: delta_L = d_rgb * exp(z_L); dW_i = delta_i^T a_{i-1};
@@ -692,7 +707,7 @@ def query_backward(tree, tables, weights, x, omega, d_rgb, form="cell"):
     F = T.shape[1]
     K = tree.num_levels
     _, h, addr, weight = _encode(tree, T, x, omega, form)
-    rgb, zs, inputs = mlp_forward(weights, h)
+    rgb, zs, inputs = mlp_forward(weights, decoder_input(h, attrs))
     Ws = [np.asarray(W, dtype=np.float64) for W in weights]
     delta = np.asarray(d_rgb, dtype=np.float64) * rgb
     dWs = [None] * len(Ws)

@@ -79,3 +79,26 @@ def test_predictor_hand_mlp():
     d = O.disparity(table, res, [W1, W2, W3], x, w, n)
     r = O.reflect_f32(w, n).astype(np.float64)
     np.testing.assert_allclose(d, np.exp(r[:, 2]), rtol=1e-14)
+
+
+def test_decoder_attributes():
+    """Eq. 12: attributes behind zero columns of W1 change nothing; with an
+    all-zero table the hand decoder returns exp(g_0) in the first channel."""
+    ot = O.build_tree(61, 2, 1.0, [4, 4, 4])
+    g = I.rng(62)
+    x = g.random((100, 3)).astype(np.float32)
+    w = I.unit_vectors(g, 100).astype(np.float32)
+    tables = I.make_tables(63, ot.num_texels, 4, 0.5)
+    W = I.make_mlp(64, [12, 16, 16, 3])
+    attrs = g.normal(size=(100, 13))
+    W1z = np.concatenate([W[0], np.zeros((16, 13))], axis=1)
+    a, _ = O.query_forward(ot, tables, [W1z, W[1], W[2]], x, w, attrs=attrs)
+    b, _ = O.query_forward(ot, tables, W, x, w)
+    np.testing.assert_array_equal(a, b)
+    W1 = np.zeros((2, 25))
+    W1[0, 12], W1[1, 12] = 1.0, -1.0
+    W3 = np.zeros((3, 2))
+    W3[0] = [1.0, -1.0]
+    rgb, _ = O.query_forward(ot, np.zeros_like(tables), [W1, np.eye(2), W3], x, w, attrs=attrs)
+    np.testing.assert_allclose(rgb[:, 0], np.exp(attrs[:, 0]), rtol=1e-15)
+    np.testing.assert_array_equal(rgb[:, 1:], 1.0)
