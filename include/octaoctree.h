@@ -143,8 +143,9 @@ typedef struct octa_scene {
  * normalised as v / sqrt(v.v)), evaluated as (x - c_j) d + omega_r in
  * binary32 with one rounding per operation (omega_r = (2 (n.omega)) n -
  * omega; the octahedral map divides by the L1 norm, so no normalisation).
- * Only octa_encode evaluates it (the others return OCTA_EUNSUPPORTED); the
- * disparity comes from the caller.                                       */
+ * octa_encode and, for BF16 decoders, octa_query_fwd evaluate it (the
+ * other entry points return OCTA_EUNSUPPORTED); the disparity comes from
+ * the caller (octa_disparity computes it with the predictor g_psi).      */
 #define OCTA_FORM_SHIFTED 2
 
 /* Queries: scene s answers queries [scene_start[s], scene_start[s+1]).   */
@@ -156,7 +157,15 @@ typedef struct octa_queries {
   /* the shifted form only (NULL otherwise): */
   const float* normal;         /* device [n][3], surface normal (length > 0)*/
   const float* disparity;      /* device [n], d of Eq. 8 (>= 0)            */
+  /* Eq. 12's surface attributes g, appended to the decoder input after the
+   * K*F features (widths[0] = K*F + n_attrs); the paper's g is position,
+   * reflection direction, normal, albedo and roughness (13 values).  Read
+   * by octa_query_fwd and octa_query_bwd; NULL / 0 for none.              */
+  const float* attrs;          /* device [n][n_attrs]                       */
+  int32_t n_attrs;             /* 0..OCTA_MAX_ATTRS                         */
+  int32_t reserved_q;
 } octa_queries;
+#define OCTA_MAX_ATTRS 16
 
 /* octa_encode -- the OctaOctree encoding alone in the scenes' query form
  * (all scenes of a call share it; Eq. 10 single-cell bilinear form, Eq. 10

@@ -77,6 +77,9 @@ class octa_queries(C.Structure):
         ("scene_start", C.c_int64 * (OCTA_MAX_SCENES + 1)),
         ("normal", C.c_void_p),
         ("disparity", C.c_void_p),
+        ("attrs", C.c_void_p),
+        ("n_attrs", C.c_int32),
+        ("reserved_q", C.c_int32),
     ]
 
 

@@ -201,8 +201,17 @@ def octa_encode(scenes, x, omega, counts=None, feat_dtype=torch.float32, want_no
     return feat, nodes, addr
 
 
+def _set_extras(q, n, normal=None, disparity=None, attrs=None):
+    """The shifted form's normal / disparity and Eq. 12's attributes."""
+    q.normal = normal.data_ptr() if normal is not None and n else None
+    q.disparity = disparity.data_ptr() if disparity is not None and n else None
+    if attrs is not None:
+        q.attrs = attrs.data_ptr() if n else None
+        q.n_attrs = int(attrs.shape[1])
+
+
 def octa_query_fwd(scenes, x, omega, counts=None, want_nodes=False, want_addr=False, rgb=None,
-                   status=None, stream=None):
+                   status=None, stream=None, normal=None, disparity=None, attrs=None):
     arr, ns = _scene_array(scenes)
     sl = [scenes] if isinstance(scenes, Scene) else scenes
     kmax = max(s.tree.num_levels for s in sl)
@@ -214,17 +223,20 @@ def octa_query_fwd(scenes, x, omega, counts=None, want_nodes=False, want_addr=Fa
     per_level = 4 if sl[0].query_form == L.OCTA_FORM_CELL_BILINEAR else 24
     addr = torch.empty((n, kmax, per_level), dtype=torch.int32, device=dev) if want_addr else None
     q = _queries(x, omega, counts)
+    _set_extras(q, n, normal, disparity, attrs)
     L.check(_lib().octa_query_fwd(arr, ns, C.byref(q), _ptr(rgb), _ptr(nodes), _ptr(addr),
                                   _ptr(status), _stream(stream)), "octa_query_fwd")
     return rgb, nodes, addr
 
 
-def octa_query_bwd(scenes, x, omega, d_rgb, grads, counts=None, status=None, stream=None):
+def octa_query_bwd(scenes, x, omega, d_rgb, grads, counts=None, status=None, stream=None,
+                   attrs=None):
     """grads: list of (d_tables fp32, d_weights fp32) per scene; accumulated."""
     arr, ns = _scene_array(scenes)
     g = (L.octa_scene_grads * ns)(*[L.octa_scene_grads(dt.data_ptr(), dw.data_ptr())
                                     for dt, dw in grads])
     q = _queries(x, omega, counts)
+    _set_extras(q, int(x.shape[0]), attrs=attrs)
     L.check(_lib().octa_query_bwd(arr, ns, C.byref(q), _ptr(d_rgb), g, _ptr(status),
                                   _stream(stream)), "octa_query_bwd")
 

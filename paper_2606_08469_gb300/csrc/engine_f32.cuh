@@ -426,7 +426,8 @@ __device__ __forceinline__ int64_t map_base(const QueryParams& p, const DevScene
 }
 
 // Phase 2: one thread per (query, level) item for levels [0, nlev); writes
-// feature f of level l for query q to h[(l*F + f) * ld_feat + q * ld_q].  In
+// feature f of level l for query q to h[(l*F + f) * ld_feat + q * ld_q]
+// (levels past the scene's K: Eq. 12's attributes, else zeros).  In
 // the trilinear vertex form the item blends the 8 x 3 vertex features of
 // full_form_level (Eq. 6, 10; texel_addr rows of 24 entries a level).
 template <int F, typename TT>
@@ -467,8 +468,10 @@ __device__ __forceinline__ void gather_tile(const QueryParams& p, const DevScene
             if (aout) aout[3 * j + k] = fl.base[j] + fl.vidx[k];
           }
         }
-      } else if (aout) {
-        for (int k = 0; k < 24; ++k) aout[k] = -1;
+      } else {
+        if (aout)
+          for (int k = 0; k < 24; ++k) aout[k] = -1;
+        if (p.n_attrs > 0 && l >= sc.K) attr_columns<F>(p, sc.K, l, q0 + q, q < nq, v);
       }
 #pragma unroll
       for (int f = 0; f < F; ++f) h[(l * F + f) * ld_feat + q * ld_q] = v[f];
@@ -508,6 +511,8 @@ __device__ __forceinline__ void gather_tile(const QueryParams& p, const DevScene
           v[f] = s;
         }
       }
+    } else if (p.n_attrs > 0 && l >= sc.K) {  // Eq. 12's attributes past the features
+      attr_columns<F>(p, sc.K, l, q0 + q, q < nq, v);
     }
 #pragma unroll
     for (int f = 0; f < F; ++f) h[(l * F + f) * ld_feat + q * ld_q] = v[f];

@@ -93,14 +93,20 @@ __device__ void load_weights_bf16(const DevScene& sc, uint8_t* smem, int nthread
 
 // Locate and gather of one query per thread into its row of the layer-0
 // operand tile (canonical K-major, one 16-byte store per level for F = 8);
-// FULL: the trilinear vertex form (Eq. 10 with Eq. 6, one thread a query).
-template <class S, typename TT, int TPQ = 1, bool FULL = false>
+// FORM: the query form (the trilinear vertex and shifted forms gather one
+// query per thread).  Columns past the K levels take Eq. 12's attributes.
+template <class S, typename TT, int TPQ = 1, int FORM = OCTA_FORM_CELL_BILINEAR>
 __device__ __forceinline__ void locate_gather_bf16(const QueryParams& p, const DevScene& sc,
                                                    const int2* tree, const QueryIn& in, int64_t gq,
                                                    bool valid, int par, uint8_t* act, int* base_sm,
                                                    float* u_sm, int q) {
   constexpr int F = S::F;
-  auto store = [&](int l, const float (&v)[F]) {
+  auto store = [&](int l, const float (&v0)[F]) {
+    float v[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) v[f] = v0[f];
+    if constexpr (TPQ == 1)  // the host runs one thread a query when attributes are given
+      if (p.n_attrs > 0 && l >= sc.K) attr_columns<F>(p, sc.K, l, gq, valid, v);
     uint8_t* dst = act + kmajor_offset(q, l * F, S::WP);
     if constexpr (F == 8) {
       uint4 o;
@@ -116,7 +122,10 @@ __device__ __forceinline__ void locate_gather_bf16(const QueryParams& p, const D
       *reinterpret_cast<uint2*>(dst) = o;
     }
   };
-  if constexpr (FULL) {
+  if constexpr (FORM == OCTA_FORM_SHIFTED) {
+    static_assert(TPQ == 1, "the shifted form gathers one query per thread");
+    gather_shifted_query<F, TT, S::KPAD>(p, sc, tree, in, gq, valid, store);
+  } else if constexpr (FORM == OCTA_FORM_TRILINEAR_VERTEX) {
     static_assert(TPQ == 1, "the full form gathers one query per thread");
     gather_full_query<F, TT, S::KPAD>(p, sc, tree, in, gq, valid, store);
   } else {
@@ -143,7 +152,7 @@ __device__ __forceinline__ void issue_layer(int layer, uint32_t act_sa, uint32_t
 // gathers the levels l with l % TPQ == par and, in the epilogues, the
 // column range par of the hidden layer), all of them waiting on the MMAs of
 // the tile; persistent over tiles.
-template <class S, typename TT, int TPQ, bool FULL = false>
+template <class S, typename TT, int TPQ, int FORM = OCTA_FORM_CELL_BILINEAR>
 __global__ void __launch_bounds__(NT * TPQ, 4)
     fwd_kernel(const __grid_constant__ QueryParams p) {
   constexpr int NTF = NT * TPQ;         // threads per CTA
@@ -191,7 +200,7 @@ __global__ void __launch_bounds__(NT * TPQ, 4)
     }
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * NT;
     const int nq = static_cast<int>(sc.q_end - q0 < NT ? sc.q_end - q0 : int64_t(NT));
-    locate_gather_bf16<S, TT, TPQ, FULL>(p, sc, tree, in, q0 + q, q < nq, par, act, nullptr,
+    locate_gather_bf16<S, TT, TPQ, FORM>(p, sc, tree, in, q0 + q, q < nq, par, act, nullptr,
                                          nullptr, q);
     fence_proxy_async();
     __syncthreads();
@@ -700,8 +709,8 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
     const bool full = sc.query_form == OCTA_FORM_TRILINEAR_VERTEX;  // uniform over the CTA
     const QueryIn& qry = in;  // the layer loops below reuse the name in
     if (full)
-      locate_gather_bf16<S, TT, 1, true>(p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0),
-                                         nullptr, nullptr, t);
+      locate_gather_bf16<S, TT, 1, OCTA_FORM_TRILINEAR_VERTEX>(
+          p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), nullptr, nullptr, t);
     else
       locate_gather_bf16<S, TT>(p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), base_sm,
                                 u_sm, t);
@@ -946,9 +955,9 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
 
 namespace {
 
-template <class S, typename TT, int TPQ, bool FULL = false>
+template <class S, typename TT, int TPQ, int FORM = OCTA_FORM_CELL_BILINEAR>
 int launch_fwd_tpq(const QueryParams& p, const octa_tuning& tu, cudaStream_t stream) {
-  auto kern = fwd_kernel<S, TT, TPQ, FULL>;
+  auto kern = fwd_kernel<S, TT, TPQ, FORM>;
   int per_sm = 0;
   int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, NT * TPQ,
                               static_cast<int>(S::TMEM_COLS), &per_sm);
@@ -968,9 +977,11 @@ int launch_fwd(const QueryParams& p, cudaStream_t stream) {
   if (p.n_tiles == 0) return OCTA_OK;
   const octa_tuning tu = tuning_snapshot();
   if (p.sc[0].query_form == OCTA_FORM_TRILINEAR_VERTEX)  // all scenes of a call share it
-    return launch_fwd_tpq<S, TT, 1, true>(p, tu, stream);
-  return tu.fwd_threads_per_query == 2 ? launch_fwd_tpq<S, TT, 2>(p, tu, stream)
-                                       : launch_fwd_tpq<S, TT, 1>(p, tu, stream);
+    return launch_fwd_tpq<S, TT, 1, OCTA_FORM_TRILINEAR_VERTEX>(p, tu, stream);
+  if (p.sc[0].query_form == OCTA_FORM_SHIFTED)
+    return launch_fwd_tpq<S, TT, 1, OCTA_FORM_SHIFTED>(p, tu, stream);
+  return tu.fwd_threads_per_query == 2 && p.n_attrs == 0 ? launch_fwd_tpq<S, TT, 2>(p, tu, stream)
+                                                         : launch_fwd_tpq<S, TT, 1>(p, tu, stream);
 }
 
 template <class S, typename TT, bool TRAIN, bool PERSIST>
@@ -1090,6 +1101,7 @@ int query_fwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cuda
   OCTA_TC_TRY(8, 64, 64, 2)
   OCTA_TC_TRY(8, 80, 64, 2)
   OCTA_TC_TRY(8, 80, 64, 3)
+  OCTA_TC_TRY(8, 96, 64, 2)  // K*F + Eq. 12's attributes
 #undef OCTA_TC_TRY
   return fail(OCTA_EUNSUPPORTED, "BF16 path: no built shape for F=%d, K*F=%d, hidden %d x %d", F,
               need, NH, H);

@@ -72,7 +72,22 @@ struct QueryParams {
   // the shifted form's per-query inputs (normal [n][3], disparity [n])
   const float* normal;
   const float* disparity;
+  // Eq. 12's attributes [n][n_attrs], decoder input columns K*F .. K*F+n_attrs-1
+  const float* attrs;
+  int32_t n_attrs;
 };
+
+// Decoder-input columns of level l >= K (past the features): Eq. 12's
+// attributes of query gq where they fall, else zeros.
+template <int F>
+__device__ __forceinline__ void attr_columns(const QueryParams& p, int K, int l, int64_t gq,
+                                             bool valid, float (&v)[F]) {
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    const int c = (l - K) * F + f;
+    v[f] = (valid && c < p.n_attrs) ? p.attrs[gq * p.n_attrs + c] : 0.f;
+  }
+}
 
 // Work units [0, n) of this CTA: interleaved (u = block + k * grid) or one
 // contiguous chunk per CTA (fewer scene switches in a multi-scene launch).

@@ -110,10 +110,15 @@ int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_qu
   if (n_scenes < 1 || n_scenes > OCTA_MAX_SCENES)
     return fail(OCTA_ERANGE, "n_scenes %d outside [1, %d]", n_scenes, OCTA_MAX_SCENES);
   if (q->n < 0) return fail(OCTA_EINVAL, "negative query count");
+  if (q->n_attrs < 0 || q->n_attrs > OCTA_MAX_ATTRS)
+    return fail(OCTA_ERANGE, "n_attrs %d outside [0, %d]", q->n_attrs, OCTA_MAX_ATTRS);
+  if (q->n_attrs > 0 && q->n > 0 && !q->attrs) return fail(OCTA_EINVAL, "attrs must be non-NULL");
   if (q->n > 0 && (!q->x || !q->omega)) return fail(OCTA_EINVAL, "x / omega must be non-NULL");
   if (q->scene_start[0] != 0 || q->scene_start[n_scenes] != q->n)
     return fail(OCTA_EINVAL, "scene_start must run from 0 to n");
   p.n_scenes = n_scenes;
+  p.attrs = q->n_attrs > 0 ? q->attrs : nullptr;
+  p.n_attrs = q->n_attrs;
   int64_t tiles = 0;
   for (int s = 0; s < n_scenes; ++s) {
     const octa_scene& c = scenes[s];
@@ -136,8 +141,8 @@ int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_qu
     if (c.n_layers < 2 || c.n_layers > OCTA_MAX_LAYERS)
       return fail(OCTA_ERANGE, "scene %d: n_layers %d outside [2, %d]", s, c.n_layers,
                   OCTA_MAX_LAYERS);
-    if (c.widths[0] != c.num_levels * c.F)
-      return fail(OCTA_EINVAL, "scene %d: widths[0] must equal K*F", s);
+    if (c.widths[0] != c.num_levels * c.F + q->n_attrs)
+      return fail(OCTA_EINVAL, "scene %d: widths[0] must equal K*F + n_attrs", s);
     if (c.widths[c.n_layers] != 3) return fail(OCTA_EINVAL, "scene %d: output width must be 3", s);
     if (!aligned16(c.tables)) return fail(OCTA_EINVAL, "scene %d: tables not 16-byte aligned", s);
     for (int l = 0; l < c.num_levels; ++l)
@@ -326,8 +331,12 @@ extern "C" int octa_query_fwd(const octa_scene* scenes, int32_t n_scenes, const 
   QueryParams p;
   int rc = build_query_params(scenes, n_scenes, q, nullptr, p);
   if (rc) return rc;
-  rc = reject_shifted(scenes, n_scenes);
-  if (rc) return rc;
+  if (scenes[0].query_form == OCTA_FORM_SHIFTED) {  // the tensor-core forward only
+    if (scenes[0].weight_dtype != OCTA_BF16)
+      return fail(OCTA_EUNSUPPORTED, "the shifted form's forward needs BF16 decoders");
+    if (q->n > 0 && (!q->normal || !q->disparity))
+      return fail(OCTA_EINVAL, "the shifted form needs normal and disparity");
+  }
   rc = check_one_form(scenes, n_scenes, node_idx);
   if (rc) return rc;
   if (q->n > 0 && !rgb) return fail(OCTA_EINVAL, "rgb must be non-NULL");
@@ -340,6 +349,8 @@ extern "C" int octa_query_fwd(const octa_scene* scenes, int32_t n_scenes, const 
   p.texel_addr = texel_addr;
   p.kmax_out = kmax;
   p.status = status;
+  p.normal = q->normal;
+  p.disparity = q->disparity;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (scenes[0].weight_dtype == OCTA_BF16) return tc::query_fwd(scenes, n_scenes, p, st);
   return f32::dispatch(scenes, n_scenes, p, f32::Mode::kForward, st);

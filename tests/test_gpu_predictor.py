@@ -103,3 +103,69 @@ def test_predictor_errors():
         L.check(A._lib().octa_disparity(A.C.byref(bad), A.C.byref(q),
                                         A._ptr(torch.empty(10, device=DEV)), A._stream()), "d")
     assert A.octa_disparity(pred, dev(x)[:0], dev(w)[:0], dev(nrm)[:0]).numel() == 0
+
+
+def _attrs(x, w, nrm, seed):
+    """Eq. 12's g: position, reflection direction, normal, albedo, roughness."""
+    g = I.rng(seed)
+    n = nrm / np.linalg.norm(nrm, axis=1, keepdims=True)
+    return np.concatenate([x, O.reflect_f32(w, nrm), n, g.random((len(x), 3)),
+                           g.uniform(0.05, 0.6, (len(x), 1))], axis=1).astype(np.float32)
+
+
+def test_full_inference_path_tensor_cores():
+    """The paper's inference: d = g_psi(x, omega_r) (octa_disparity), then
+    octa_query_fwd in the shifted form on a BF16 decoder whose input is
+    [h, g] (K F = 72 features + 13 attributes, the 96-wide operand): the 24
+    entries of every level bit-exact given the GPU's d, radiance within the
+    BF16 path's 1e-2 normwise bound against the FP64 oracle."""
+    from paper_2606_08469_gb300 import _lib as L
+    from paper_2606_08469_gb300 import api as A
+    table, res, pw = _predictor(1000, 8, 16, 16, 512)
+    pred = A.Predictor(table, res, pw, device=DEV)
+    V = [65, 65, 33, 33, 17, 17, 9, 9, 9]
+    tree = A.octree_build(1001, 8, 0.6, V)
+    ot = O.build_tree(1001, 8, 0.6, V)
+    tables = I.make_tables(1002, tree.num_texels, 8, 0.3).astype(np.float16).astype(np.float32)
+    weights = I.make_mlp(1003, [72 + 13, 64, 64, 3])
+    sc = A.Scene(tree, dev(tables).half().contiguous(), [dev(W).to(torch.bfloat16) for W in weights],
+                 device=DEV, query_form=L.OCTA_FORM_SHIFTED)
+    x, w, nrm = _queries(1004, 3001)
+    g = _attrs(x, w, nrm, 1005)
+    X, Wd, Nd, G = dev(x), dev(w), dev(nrm), dev(g)
+    d = A.octa_disparity(pred, X, Wd, Nd)
+    rgb, _, addr = A.octa_query_fwd(sc, X, Wd, want_addr=True, normal=Nd, disparity=d, attrs=G)
+    dd = d.cpu().numpy()
+    ref, enc = O.query_forward(ot, tables, weights, x, w, form="shifted", normal=nrm,
+                               disparity=dd, attrs=g)
+    np.testing.assert_array_equal(addr.cpu().numpy(), enc.addr.reshape(len(x), 9, 24))
+    err = np.linalg.norm(rgb.cpu().numpy() - ref) / np.linalg.norm(ref)
+    print("full inference path, BF16 normwise error", err)
+    assert err <= 1e-2
+
+
+def test_attributes_fp32_forward_and_backward():
+    """Eq. 12 on the FP32 engine (cell form, K F = 56 + 13 attributes in the
+    72-wide shape): radiance to 1e-5 and table / weight gradients (the
+    attributes' W1 columns included) to 1e-5 normwise against the oracle."""
+    from paper_2606_08469_gb300 import api as A
+    cfg = I.CONFIGS[1]
+    tree = A.octree_build(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    tables = I.make_tables(1101, tree.num_texels, 8, 0.3)
+    weights = I.make_mlp(1102, [56 + 13, 64, 64, 3])
+    sc = A.Scene(tree, dev(tables), [dev(W) for W in weights], device=DEV)
+    x, w, nrm = _queries(1103, 4097)
+    g = _attrs(x, w, nrm, 1104)
+    rgb, _, _ = A.octa_query_fwd(sc, dev(x), dev(w), attrs=dev(g))
+    ref, _ = O.query_forward(ot, tables, weights, x, w, attrs=g)
+    assert np.max(np.abs(rgb.cpu().numpy() / ref - 1)) <= 1e-5
+    d_rgb = np.random.default_rng(5).normal(size=(len(x), 3)).astype(np.float32)
+    dT = torch.zeros((tree.num_texels, 8), device=DEV)
+    dW = torch.zeros(sc.weights.shape, device=DEV)
+    A.octa_query_bwd(sc, dev(x), dev(w), dev(d_rgb), [(dT, dW)], attrs=dev(g))
+    rT, rWs, _ = O.query_backward(ot, tables, weights, x, w, d_rgb, attrs=g)
+    assert np.linalg.norm(dT.cpu().numpy() - rT) <= 1e-5 * np.linalg.norm(rT)
+    gw = dW.cpu().numpy()
+    for (off, o, i), rW in zip(sc.weight_slices(), rWs):
+        assert np.linalg.norm(gw[off:off + o * i].reshape(o, i) - rW) <= 1e-5 * np.linalg.norm(rW)

@@ -44,7 +44,7 @@ def test_struct_sizes_match_header(lib):
     assert C.sizeof(L.octa_tree_desc) == 4 + 4 + 8 + 4 * 16 + 4 * 17 + 4 + 8 * 17
     assert lib.octa_abi_version() == 4
     assert C.sizeof(L.octa_prims) == 8 + 8 + 4 + 4
-    assert C.sizeof(L.octa_queries) == 8 + 8 + 8 + 8 * 17 + 8 + 8
+    assert C.sizeof(L.octa_queries) == 8 + 8 + 8 + 8 * 17 + 8 + 8 + 8 + 4 + 4
     assert C.sizeof(L.octa_predictor) == 8 + 8 + 4 + 4 + 4 * 16
     assert C.sizeof(L.octa_pairs) == 6 * 8 + 8 + 8 * 17 + 8 * 16
 
