@@ -13,6 +13,7 @@ namespace {
 constexpr int kPredThreads = 128;
 constexpr int kH = OCTA_PRED_HIDDEN;
 constexpr int kMaxIn = 2 * OCTA_PRED_MAX_LEVELS + 3;  // widest MLP input
+constexpr int kW1Row = (kMaxIn + 3) / 4 * 4;           // W1 row in shared memory (float4s)
 
 struct PredParams {
   const float* table;
@@ -36,15 +37,16 @@ __device__ __forceinline__ uint32_t vertex_entry(uint32_t i, uint32_t j, uint32_
 }
 
 // One thread per query; the MLP's weights live in shared memory with W1's
-// rows padded to kMaxIn columns (zeros past the encoding's width), so every
-// loop has a compile-time trip count.
-__global__ void __launch_bounds__(kPredThreads) disparity_kernel(const __grid_constant__ PredParams p) {
-  __shared__ float w1[kH * kMaxIn];
-  __shared__ float w2[kH * kH];
-  __shared__ float w3[kH];
+// rows padded to kW1Row columns (zeros past the encoding's width), so every
+// loop has a compile-time trip count, and are read as float4 (one shared
+// load per four FMAs; all threads of a warp read the same address).
+__global__ void __launch_bounds__(kPredThreads, 3) disparity_kernel(const __grid_constant__ PredParams p) {
+  __shared__ __align__(16) float w1[kH * kW1Row];
+  __shared__ __align__(16) float w2[kH * kH];
+  __shared__ __align__(16) float w3[kH];
   const int in_w = 2 * p.levels + 3;
-  for (int i = threadIdx.x; i < kH * kMaxIn; i += blockDim.x) {
-    const int o = i / kMaxIn, c = i % kMaxIn;
+  for (int i = threadIdx.x; i < kH * kW1Row; i += blockDim.x) {
+    const int o = i / kW1Row, c = i % kW1Row;
     w1[i] = c < in_w ? p.weights[o * in_w + c] : 0.f;
   }
   for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) w2[i] = p.weights[kH * in_w + i];
@@ -53,9 +55,9 @@ __global__ void __launch_bounds__(kPredThreads) disparity_kernel(const __grid_co
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < p.n; q += stride) {
     const float xs[3] = {clamp01(p.x[3 * q]), clamp01(p.x[3 * q + 1]), clamp01(p.x[3 * q + 2])};
-    float in[kMaxIn];
+    float in[kW1Row];
 #pragma unroll
-    for (int c = 0; c < kMaxIn; ++c) in[c] = 0.f;
+    for (int c = 0; c < kW1Row; ++c) in[c] = 0.f;
 #pragma unroll
     for (int l = 0; l < OCTA_PRED_MAX_LEVELS; ++l) {
       if (l >= p.levels) break;
@@ -99,21 +101,42 @@ __global__ void __launch_bounds__(kPredThreads) disparity_kernel(const __grid_co
         in[2 * l + 1] = wr[1];
         in[2 * l + 2] = wr[2];
       }
+    // four outputs at a time: four independent FMA chains per thread
     float h1[kH];
 #pragma unroll
-    for (int o = 0; o < kH; ++o) {
-      float s = 0.f;
+    for (int o = 0; o < kH; o += 4) {
+      float s[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int c = 0; c < kMaxIn; ++c) s = fmaf(w1[o * kMaxIn + c], in[c], s);
-      h1[o] = fmaxf(s, 0.f);
+      for (int c = 0; c < kW1Row / 4; ++c) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const float4 w = reinterpret_cast<const float4*>(w1 + (o + r) * kW1Row)[c];
+          s[r] = fmaf(w.x, in[4 * c], s[r]);
+          s[r] = fmaf(w.y, in[4 * c + 1], s[r]);
+          s[r] = fmaf(w.z, in[4 * c + 2], s[r]);
+          s[r] = fmaf(w.w, in[4 * c + 3], s[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) h1[o + r] = fmaxf(s[r], 0.f);
     }
     float z = 0.f;
-#pragma unroll 4
-    for (int o = 0; o < kH; ++o) {
-      float s = 0.f;
+#pragma unroll 1
+    for (int o = 0; o < kH; o += 4) {
+      float s[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int c = 0; c < kH; ++c) s = fmaf(w2[o * kH + c], h1[c], s);
-      z = fmaf(w3[o], fmaxf(s, 0.f), z);
+      for (int c = 0; c < kH / 4; ++c) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const float4 w = reinterpret_cast<const float4*>(w2 + (o + r) * kH)[c];
+          s[r] = fmaf(w.x, h1[4 * c], s[r]);
+          s[r] = fmaf(w.y, h1[4 * c + 1], s[r]);
+          s[r] = fmaf(w.z, h1[4 * c + 2], s[r]);
+          s[r] = fmaf(w.w, h1[4 * c + 3], s[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) z = fmaf(w3[o + r], fmaxf(s[r], 0.f), z);
     }
     p.disparity[q] = expf(z);
   }
