@@ -1,6 +1,6 @@
 """Benchmark of the OctaOctree training step (and forward) on GB300.
 
-Default workload: the FP32 training step of config [1] -- a depth-6 octree
+Default workload: the FP32 training step of train_f32 -- a depth-6 octree
 (R = 32,32,16,16,8,8,8, F = 8 FP32 features), decoder 56-64-64-3, 262,144
 training pairs = 524,288 queries per step (a primary and a secondary query
 per pair): forward, Eq. 14 residual loss, backward with recompute and
@@ -108,11 +108,11 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 def oracle_step_rate(n_pairs, repeats=1):
-    """Mq/s of the FP64 oracle training step on n_pairs pairs of config [1]."""
+    """Mq/s of the FP64 oracle training step on n_pairs pairs of train_f32."""
     import numpy as np
     from oracle import octaoctree_oracle as O
     from paper_2606_08469_gb300 import inputs as I
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     tree = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
     tables = I.make_tables(cfg.seed("tables"), tree.num_texels, cfg.F, cfg.sigma)
     W = I.make_mlp(cfg.seed("mlp"), cfg.widths)
@@ -165,13 +165,13 @@ def _timed(fn, n, flush, stream):
 
 
 def bf16_vs_f32_leg(dev, flush, stream, steps, peaks):
-    """Config [2] training step (1,048,576 pairs, depth-8 tree, decoder
+    """train_bf16 training step (1,048,576 pairs, depth-8 tree, decoder
     72-64-64-64-3): BF16 tensor-core path vs the FP32 path on the same shapes."""
     from paper_2606_08469_gb300 import api
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[2]
-    out = {"workload": "config[2] training step: depth-8 octree, R 64..8, F=8, decoder 72-64-64-64-3, "
+    cfg = I.WORKLOADS["train_bf16"]
+    out = {"workload": "train_bf16 training step: depth-8 octree, R 64..8, F=8, decoder 72-64-64-64-3, "
                        "1048576 pairs = 2097152 queries, dynamic loss scaling"}
     W = cfg.widths
     fwd_flop = 2 * sum(a * b for a, b in zip(W[:-1], W[1:]))
@@ -217,16 +217,16 @@ def bf16_vs_f32_leg(dev, flush, stream, steps, peaks):
 
 
 def inference_leg(dev, flush, stream, steps, peaks):
-    """Config [3]: one query per pixel of a synthetic G-buffer, BF16 decoder
+    """gbuffer_frame: one query per pixel of a synthetic G-buffer, BF16 decoder
     72-64-64-3 on the tensor cores (FP32 path for comparison)."""
     import torch
     from paper_2606_08469_gb300 import api
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[3]
+    cfg = I.WORKLOADS["gbuffer_frame"]
     W = cfg.widths
     fwd_flop = 2 * sum(a * b for a, b in zip(W[:-1], W[1:]))
-    out = {"workload": "config[3] inference: depth-8 octree, FP16 features, BF16 decoder 72-64-64-3"}
+    out = {"workload": "gbuffer_frame inference: depth-8 octree, FP16 features, BF16 decoder 72-64-64-3"}
     for (w_, h_) in ((1280, 720), (1024, 1024)):
         x, om = I.gbuffer_queries(cfg.seed("queries"), w_, h_)
         X, Om = WL.to_dev(x, dev), WL.to_dev(om, dev)
@@ -262,13 +262,13 @@ def inference_leg(dev, flush, stream, steps, peaks):
 
 def encode_leg(dev, flush, stream, steps, peaks):
     """The OctaOctree encoding alone (fold, walk, bilinear gather of every
-    level, concatenation) for config [3]'s 1280x720 queries, BF16 features
+    level, concatenation) for gbuffer_frame's 1280x720 queries, BF16 features
     out: bound by the HBM stream of positions/directions in and features out."""
     import torch
     from paper_2606_08469_gb300 import api
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[3]
+    cfg = I.WORKLOADS["gbuffer_frame"]
     sc, (tree, _, _) = WL.forward_scene(cfg, device=dev)
     x, om = I.gbuffer_queries(cfg.seed("queries"), 1280, 720)
     X, Om = WL.to_dev(x, dev), WL.to_dev(om, dev)
@@ -288,7 +288,7 @@ def encode_leg(dev, flush, stream, steps, peaks):
     alg = len(x) * (24 + 2 * W) + table_bytes
     peak = float(peaks.get("hbm_gbs", 6800.0))
     ach = alg / (t / 1e3) / 1e9
-    return {"workload": f"config[3] encoding alone: {len(x)} queries, depth-8 octree, FP16 table, "
+    return {"workload": f"gbuffer_frame encoding alone: {len(x)} queries, depth-8 octree, FP16 table, "
                         f"{W} BF16 features per query out",
             "ms": round(t, 4), "Mq/s": round(len(x) / t / 1e3, 1),
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
@@ -299,7 +299,7 @@ def encode_leg(dev, flush, stream, steps, peaks):
 
 def encode_full_leg(dev, flush, stream, steps, peaks):
     """The full query form (Eq. 10 eight-cell renormalised trilinear blend,
-    Eq. 6 barycentric interpolation on vertex maps) of config [3]'s 1280x720
+    Eq. 6 barycentric interpolation on vertex maps) of gbuffer_frame's 1280x720
     G-buffer on its depth-8 octree with vertex maps of side 2^k + 1 (65, 65,
     33, 33, 17, 17, 9, 9, 9), FP16 features, BF16 features out: 8 x 3 vertex
     loads per level against the cell form's 4 texels."""
@@ -309,7 +309,7 @@ def encode_full_leg(dev, flush, stream, steps, peaks):
     from paper_2606_08469_gb300 import api
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[3]
+    cfg = I.WORKLOADS["gbuffer_frame"]
     V = [r + 1 for r in cfg.R]
     tree = api.octree_build(cfg.seed("tree"), cfg.max_depth, cfg.p_base, V)
     T = WL.to_dev(I.make_tables(cfg.seed("tables"), tree.num_texels, cfg.F, cfg.sigma), dev).half()
@@ -366,7 +366,7 @@ def encode_full_leg(dev, flush, stream, steps, peaks):
     alg = len(x) * (24 + 2 * W) + table_bytes
     peak = float(peaks.get("hbm_gbs", 6800.0))
     ach = alg / (t / 1e3) / 1e9
-    return {"workload": f"config[3] 1280x720 G-buffer, depth-8 octree with vertex maps {V}, FP16 "
+    return {"workload": f"gbuffer_frame 1280x720 G-buffer, depth-8 octree with vertex maps {V}, FP16 "
                         f"features ({tree.num_texels} entries), full query form, {W} BF16 features out",
             "ms": round(t, 4), "Mq/s": round(len(x) / t / 1e3, 1),
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
@@ -382,16 +382,16 @@ def encode_full_leg(dev, flush, stream, steps, peaks):
 def train_full_leg(dev, flush, stream, steps):
     """Training in the full query form on vertex maps of side R + 1 against
     the same step in the cell form (8 x 3 vertex loads and scatters per level
-    against 4): the headline workload (config [1], 262,144 pairs, the FP32
-    engine's fused pass + Adam) and config [2] (1,048,576 pairs, the BF16
+    against 4): the headline workload (train_f32, 262,144 pairs, the FP32
+    engine's fused pass + Adam) and train_bf16 (1,048,576 pairs, the BF16
     tensor-core fused pass + Adam)."""
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
-    out = {"workload": "config[1] training step, FP32, 262144 pairs = 524288 queries, fused FP32 "
-                       "pass + Adam; config[2] training step, BF16, 1048576 pairs, fused tensor-core "
+    out = {"workload": "train_f32 training step, FP32, 262144 pairs = 524288 queries, fused FP32 "
+                       "pass + Adam; train_bf16 training step, BF16, 1048576 pairs, fused tensor-core "
                        "pass + Adam: trilinear vertex form vs cell form"}
     for ci, prec in ((1, "f32"), (2, None)):
-        cfg = I.CONFIGS[ci]
+        cfg = I.WORKLOADS[ci]
         tag = "f32_cfg1" if prec else "bf16_cfg2"
         for form in ("cell", "full"):
             step, _ = WL.train_step_for(cfg, device=dev, precision=prec, fused=True,
@@ -411,7 +411,7 @@ def train_full_leg(dev, flush, stream, steps):
 
 
 def multi_rhs_leg(dev, flush, stream, steps):
-    """Section 4's training regime on config [2]'s scene (depth-8 octree,
+    """Section 4's training regime on train_bf16's scene (depth-8 octree,
     FP16 tables, BF16 decoder 72-64-64-64-3): LHS samples with M RHS samples
     each, the quarter schedule from 65,536 LHS x M = 32 to 8,192 x 256
     (2,162,688 down to 2,105,344 queries a step).  A step: octa_trace_rays
@@ -421,8 +421,8 @@ def multi_rhs_leg(dev, flush, stream, steps):
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
     from paper_2606_08469_gb300.train import quarter_schedule
-    cfg = I.CONFIGS[2]
-    out = {"workload": "config[2] scene, BF16 decoder; quarter schedule 65536 x 32 -> 8192 x 256, "
+    cfg = I.WORKLOADS["train_bf16"]
+    out = {"workload": "train_bf16 scene, BF16 decoder; quarter schedule 65536 x 32 -> 8192 x 256, "
                        "secondary hits ray cast each step, target detached"}
     for q in range(4):
         n, M = quarter_schedule(q, 4, 65536, 32)
@@ -443,7 +443,7 @@ def multi_rhs_leg(dev, flush, stream, steps):
 
 
 def full_inference_leg(dev, flush, stream, steps):
-    """The paper's whole inference per frame on config [3]'s G-buffer frames:
+    """The paper's whole inference per frame on gbuffer_frame's G-buffer frames:
     d = g_psi(x, omega_r) (octa_disparity: 8 hash levels of 2^16 entries,
     MLP 19-64-64-1), then octa_query_fwd in the disparity-shifted form
     (Eq. 7-9 with Eq. 10 and Eq. 6, vertex maps 65 ... 9) on a BF16 decoder
@@ -455,7 +455,7 @@ def full_inference_leg(dev, flush, stream, steps):
     from paper_2606_08469_gb300 import api
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[3]
+    cfg = I.WORKLOADS["gbuffer_frame"]
     V = [r + 1 for r in cfg.R]
     tree = api.octree_build(cfg.seed("tree"), cfg.max_depth, cfg.p_base, V)
     T = WL.to_dev(I.make_tables(cfg.seed("tables"), tree.num_texels, cfg.F, cfg.sigma), dev).half()
@@ -466,7 +466,7 @@ def full_inference_leg(dev, flush, stream, steps):
     res = [int(np.floor(16 * (512 / 16) ** (l / 7))) for l in range(8)]
     pred = api.Predictor(g.uniform(-0.1, 0.1, (8, 1 << 16, 2)).astype(np.float32), res,
                          I.make_mlp(cfg.seed("mlp") + 5, [19, 64, 64, 1]), device=dev)
-    out = {"workload": "config[3] frames, full method: predictor g_psi + shifted lookup + decoder "
+    out = {"workload": "gbuffer_frame frames, full method: predictor g_psi + shifted lookup + decoder "
                        "on [h, g] (13 attributes), BF16 decoder 85-64-64-3, FP16 vertex tables",
            "paper_context": "the paper reports 10-20 ms per frame on an RTX 3090 for its whole "
                             "renderer (G-buffer included, decoder 4x128): another machine and "
@@ -506,7 +506,7 @@ def encode_stress_leg(dev, flush, stream, steps, peaks):
     from paper_2606_08469_gb300 import api
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[3]
+    cfg = I.WORKLOADS["gbuffer_frame"]
     R = [64, 64, 32, 32, 16, 16, 8]
     tree = api.octree_build(cfg.seed("tree"), 6, 1.0, R)
     g = torch.Generator(device=dev)
@@ -563,13 +563,13 @@ def _graph(fn, stream):
 
 
 def small_forward_leg(dev, flush, stream, steps):
-    """Config [0]: 16,384 queries, depth-4 tree, F=4 FP32, decoder 20-32-32-3
+    """forward_small: 16,384 queries, depth-4 tree, F=4 FP32, decoder 20-32-32-3
     (FP32 path), replayed from a CUDA graph."""
     import torch
     from paper_2606_08469_gb300 import api
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[0]
+    cfg = I.WORKLOADS["forward_small"]
     sc, _ = WL.forward_scene(cfg, device=dev)
     x, om = WL.queries_for(cfg)
     X, Om = WL.to_dev(x, dev), WL.to_dev(om, dev)
@@ -587,13 +587,13 @@ def small_forward_leg(dev, flush, stream, steps):
     g = _graph(fn, stream)
     g.replay()
     t = _timed(g.replay, steps, flush, stream)
-    return {"workload": "config[0] forward: 16384 queries, depth-4 octree, F=4 FP32, decoder 20-32-32-3, "
+    return {"workload": "forward_small forward: 16384 queries, depth-4 octree, F=4 FP32, decoder 20-32-32-3, "
                         "node indices and texel addresses written, CUDA-graph replay",
             "ms": round(t, 5), "Mq/s": round(len(x) / t / 1e3, 1)}
 
 
 def batched_leg(dev, flush, stream, steps):
-    """Config [4]: 8 octrees (depth 4..9) with their own BF16 decoders and
+    """batched: 8 octrees (depth 4..9) with their own BF16 decoders and
     log-uniform pair counts; the whole training step of all scenes (forward,
     Eq. 14 gradient, backward, Adam with the loss scaler) as one persistent
     cooperative launch captured in a CUDA graph; beside it the same step as
@@ -604,7 +604,7 @@ def batched_leg(dev, flush, stream, steps):
     from paper_2606_08469_gb300 import autotune as T
     counts = I.batched_pair_counts()
     nq = 2 * sum(counts)
-    out = {"workload": f"config[4] batched training step: 8 scenes (depth 4..9), pairs per scene {counts}, "
+    out = {"workload": f"batched training step: 8 scenes (depth 4..9), pairs per scene {counts}, "
                        "BF16 decoders 8L-64-64-3, FP16 tables, forward + Eq.14 gradient + backward + Adam of "
                        "all scenes", "queries": nq}
     for mode in ("one_launch", "two_launch"):
@@ -702,7 +702,7 @@ def run_ours(args):
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
 
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     # the FP32 training step: the engine's fused pass (forward, Eq. 14
     # gradient, backward in one launch) and Adam with the loss scaler
     step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=args.pairs, device=dev,
@@ -826,7 +826,7 @@ def run_ours(args):
             "vs_baseline": None,
             "dtype": "f32",
             "data": "synthetic (seeded octree, features, MLP, surface samples; no scene assets)",
-            "config": {"workload": "config[1] FP32 training step: depth-6 seeded octree "
+            "config": {"workload": "train_f32 FP32 training step: depth-6 seeded octree "
                                    f"({tree.num_nodes} nodes, R 32..8, F=8 FP32), decoder 56-64-64-3, "
                                    f"{pairs.n} pairs = {n_q} queries per step (fused fwd + Eq.14 "
                                    "gradient + bwd, then Adam)",
@@ -883,7 +883,7 @@ def run_reference(args):
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(1e3 * t / args.steps, 2), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "config[1] training step, FP64 oracle on a bounded sample of "
+           "config": {"workload": "train_f32 training step, FP64 oracle on a bounded sample of "
                                   f"{n_pairs} of the 262144 pairs per step"},
            "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"{n_pairs} pairs ({2 * n_pairs} queries) per step"},

@@ -55,16 +55,22 @@ class Config:
         return base + self.index
 
 
-CONFIGS = {
-    0: Config(0, 4, 0.6, [16, 16, 8, 8, 8], 4, "f32", 0.1, [20, 32, 32, 3], "f32",
+# The workloads by name (their index only seeds the generators):
+# forward_small  16,384 uniform queries on a depth-4 tree, FP32 decoder 20-32-32-3
+# train_f32      262,144 training pairs on a depth-6 tree, FP32 decoder 56-64-64-3
+# train_bf16     1,048,576 pairs on a depth-8 tree, FP16 tables, BF16 72-64-64-64-3
+# gbuffer_frame  a 1280x720 G-buffer frame on a depth-8 tree, BF16 72-64-64-3
+# batched        eight scenes of depth 4..9, log-uniform pair counts, BF16 80-64-64-3
+WORKLOADS = {
+    "forward_small": Config(0, 4, 0.6, [16, 16, 8, 8, 8], 4, "f32", 0.1, [20, 32, 32, 3], "f32",
               16384, "uniform"),
-    1: Config(1, 6, 0.6, [32, 32, 16, 16, 8, 8, 8], 8, "f32", 0.01, [56, 64, 64, 3], "f32",
+    "train_f32": Config(1, 6, 0.6, [32, 32, 16, 16, 8, 8, 8], 8, "f32", 0.01, [56, 64, 64, 3], "f32",
               262144, "pairs"),
-    2: Config(2, 8, 0.6, R_DEEP[:9], 8, "f16", 0.01, [72, 64, 64, 64, 3], "bf16",
+    "train_bf16": Config(2, 8, 0.6, R_DEEP[:9], 8, "f16", 0.01, [72, 64, 64, 64, 3], "bf16",
               1048576, "pairs", loss_scaling=True),
-    3: Config(3, 8, 0.6, R_DEEP[:9], 8, "f16", 0.01, [72, 64, 64, 3], "bf16",
+    "gbuffer_frame": Config(3, 8, 0.6, R_DEEP[:9], 8, "f16", 0.01, [72, 64, 64, 3], "bf16",
               1280 * 720, "gbuffer", extra={"width": 1280, "height": 720}),
-    4: Config(4, 9, 0.6, R_DEEP, 8, "f16", 0.01, [80, 64, 64, 3], "bf16",
+    "batched": Config(4, 9, 0.6, R_DEEP, 8, "f16", 0.01, [80, 64, 64, 3], "bf16",
               0, "batched", loss_scaling=True,
               extra={"depths": [4, 5, 6, 7, 8, 8, 9, 9], "log2_min": 16, "log2_max": 21}),
 }
@@ -405,14 +411,14 @@ def gbuffer_queries(seed, width, height, n_planes=16, n_spheres=16, fov_deg=60.0
 # batched workload
 # ---------------------------------------------------------------------------
 
-def batched_pair_counts(cfg=CONFIGS[4]):
+def batched_pair_counts(cfg=WORKLOADS["batched"]):
     """Per-scene pair counts floor(2^U[16,21]) (log-uniform)."""
     g = rng(4499)
     e = g.uniform(cfg.extra["log2_min"], cfg.extra["log2_max"], size=len(cfg.extra["depths"]))
     return [int(math.floor(2.0 ** v)) for v in e]
 
 
-def batched_scene_config(s, cfg=CONFIGS[4]):
+def batched_scene_config(s, cfg=WORKLOADS["batched"]):
     """Per-scene configuration of the batched workload (scene s)."""
     depth = cfg.extra["depths"][s]
     K = depth + 1

@@ -77,7 +77,7 @@ def data_parallel_train_step(cfg, rank, world, n_pairs=None, device="cuda", prec
 def batched_train_step(device="cuda", counts=None, precision=None, **kw):
     """TrainStep of the batched workload (8 scenes); counts overrides the
     per-scene pair counts."""
-    cfg = I.CONFIGS[4]
+    cfg = I.WORKLOADS["batched"]
     counts = I.batched_pair_counts(cfg) if counts is None else counts
     states, plist, host = [], [], []
     for s, n in enumerate(counts):

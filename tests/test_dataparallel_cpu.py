@@ -25,7 +25,7 @@ def _free_port():
 def _problem():
     from oracle import octaoctree_oracle as O
     from paper_2606_08469_gb300 import inputs as I
-    cfg = I.CONFIGS[0]
+    cfg = I.WORKLOADS["forward_small"]
     ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
     tables = I.make_tables(cfg.seed("tables"), ot.num_texels, cfg.F, 0.3)
     weights = I.make_mlp(cfg.seed("mlp"), [ot.num_levels * cfg.F, 32, 32, 3])

@@ -25,7 +25,7 @@ def test_forward_results_independent_of_knobs():
     from paper_2606_08469_gb300 import api as A
     from paper_2606_08469_gb300 import autotune as T
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[3]
+    cfg = I.WORKLOADS["gbuffer_frame"]
     sc, _ = WL.forward_scene(cfg)
     x, w = I.uniform_queries(3, 50000)
     X, W = WL.to_dev(x), WL.to_dev(w)
@@ -62,7 +62,7 @@ def test_autotune_picks_and_caches(tmp_path):
     from paper_2606_08469_gb300 import api as A
     from paper_2606_08469_gb300 import autotune as T
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[3]
+    cfg = I.WORKLOADS["gbuffer_frame"]
     sc, _ = WL.forward_scene(cfg)
     x, w = I.uniform_queries(4, 100000)
     X, W = WL.to_dev(x), WL.to_dev(w)

@@ -24,7 +24,7 @@ def _rel(a, b):
 @pytest.mark.parametrize("which,precision,tol", [(1, "f32", 1e-5), (2, None, 1e-5)])
 def test_shard_passes_sum_to_the_batch_pass(which, precision, tol):
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[which]
+    cfg = I.WORKLOADS[which]
     n, world = 3001, 3
     full, _ = WL.train_step_for(cfg, n_pairs=n, precision=precision, fused=True)
     full.fused_pass()
@@ -45,7 +45,7 @@ def test_data_parallel_step_single_rank_is_the_fused_step():
     """Without a process group DataParallelStep is the fused step itself."""
     from paper_2606_08469_gb300 import dataparallel as D
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     a, _ = WL.train_step_for(cfg, n_pairs=2048, fused=True)
     b, _ = WL.data_parallel_train_step(cfg, 0, 1, n_pairs=2048)
     dp = D.DataParallelStep(b)

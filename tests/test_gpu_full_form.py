@@ -236,7 +236,7 @@ def test_full_form_train_step_fused_matches_unfused():
     pairs) in the full form: the fused pass against octa_query_fwd +
     residual_loss + octa_query_bwd, then one Adam step each."""
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     a, _ = WL.train_step_for(cfg, n_pairs=2049, precision="f32", query_form="full")
     b, _ = WL.train_step_for(cfg, n_pairs=2049, precision="f32", query_form="full", fused=True)
     a.forward()
@@ -329,14 +329,14 @@ def test_full_form_bf16_backward_vs_oracle():
 
 
 def test_full_form_bf16_fused_and_one_launch_training():
-    """Config [2]'s shapes (BF16 decoder, FP16 tables) on vertex maps of side
+    """train_bf16's shapes (BF16 decoder, FP16 tables) on vertex maps of side
     R + 1 in the full form, 4,097 pairs: the fused training pass against the
     unfused forward + loss + backward (same arithmetic up to the atomics'
     order), its loss against the FP64 oracle (1e-2), and the one-launch
     step against the fused pass followed by Adam."""
     from paper_2606_08469_gb300 import api as A
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[2]
+    cfg = I.WORKLOADS["train_bf16"]
     a, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=4097, query_form="full")
     b, _ = WL.train_step_for(cfg, n_pairs=4097, query_form="full", fused=True)
     a.forward()
@@ -367,14 +367,14 @@ def test_full_form_bf16_fused_and_one_launch_training():
 
 
 def test_full_form_config3_frame_samples():
-    """The full-form legs' configuration at full size: config [3]'s 1280x720
+    """The full-form legs' configuration at full size: gbuffer_frame's 1280x720
     G-buffer on its depth-8 octree with vertex maps 65 ... 9, FP16 tables.
     On 2,000 sampled queries: the 24 entries of every level bit-exact, the
     BF16 features within BF16 rounding of the oracle's, the tensor-core
     forward within the BF16 path's 1e-2 normwise bound."""
     from paper_2606_08469_gb300 import _lib as L
     from paper_2606_08469_gb300 import api as A
-    cfg = I.CONFIGS[3]
+    cfg = I.WORKLOADS["gbuffer_frame"]
     V = [r + 1 for r in cfg.R]
     tree = A.octree_build(cfg.seed("tree"), cfg.max_depth, cfg.p_base, V)
     ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, V)

@@ -141,12 +141,12 @@ def test_loss_multi_with_one_sample_equals_residual_loss():
 
 @pytest.mark.parametrize("rhs_grad", [False, True])
 def test_multi_sample_step_gradients_match_oracle(rhs_grad):
-    """One M-sample training step of the FP32 configuration-[1] scene (300
+    """One M-sample training step of the FP32 train_f32 scene (300
     LHS samples, M = 8): the traced secondaries are the oracle's bit for bit,
     and the table / decoder gradients (before Adam) agree with the oracle's
     FP64 forward, M-sample loss and backward to 1e-5 normwise."""
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     step, (tree, tables, weights, smp) = WL.multi_sample_step_for(
         cfg, 300, 8, device=DEV, precision="f32", rhs_grad=rhs_grad, scale=1.0,
         growth_interval=0)
@@ -180,13 +180,13 @@ def test_multi_sample_step_gradients_match_oracle(rhs_grad):
 
 
 def test_full_size_quarter0_samples():
-    """The bench's first quarter at full size (config [2]'s scene and BF16
+    """The bench's first quarter at full size (train_bf16's scene and BF16
     decoder, 65,536 LHS samples x M = 32): 2,000 sampled secondary hits
     bit-exact against the oracle's tracer, the loss equal to the oracle's
     M-sample loss evaluated on the GPU's radiances (FP64, 1e-6), and 300
     sampled radiances within the BF16 path's 1e-2 normwise bound."""
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[2]
+    cfg = I.WORKLOADS["train_bf16"]
     step, (tree, tables, weights, smp) = WL.multi_sample_step_for(cfg, 65536, 32, device=DEV)
     step.trace()
     step.forward()

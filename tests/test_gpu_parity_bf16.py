@@ -78,11 +78,11 @@ def check_forward(sc, ot, tables, weights, tq, wq, x, w, counts=None):
 
 
 def test_bf16_forward_config3_gbuffer_sample():
-    """Config [3]: 1280x720 G-buffer queries, depth-8 tree, FP16 features,
+    """gbuffer_frame: 1280x720 G-buffer queries, depth-8 tree, FP16 features,
     decoder 72-64-64-3 in BF16; all queries on the GPU, a 65,536-query
     sample (every 14th pixel) against the oracle."""
     from paper_2606_08469_gb300 import api as A
-    cfg = I.CONFIGS[3]
+    cfg = I.WORKLOADS["gbuffer_frame"]
     sc, ot, tables, weights, tq, wq = make_bf16_scene(cfg.seed("tree"), 8, cfg.R, 8, cfg.sigma,
                                                       [64, 64], tseed=cfg.seed("tables"),
                                                       wseed=cfg.seed("mlp"))
@@ -100,11 +100,11 @@ def test_bf16_forward_shapes(shape, n):
     """Every built decoder shape, features drawn wide (sigma 0.3, weights x2)
     so that the decoder is far from linear, ragged batch sizes."""
     if shape == "cfg0":
-        cfg, hidden, F = I.CONFIGS[0], [32, 32], 4
+        cfg, hidden, F = I.WORKLOADS["forward_small"], [32, 32], 4
     elif shape == "cfg1":
-        cfg, hidden, F = I.CONFIGS[1], [64, 64], 8
+        cfg, hidden, F = I.WORKLOADS["train_f32"], [64, 64], 8
     else:
-        cfg, hidden, F = I.CONFIGS[2], [64, 64, 64], 8
+        cfg, hidden, F = I.WORKLOADS["train_bf16"], [64, 64, 64], 8
     sc, ot, tables, weights, tq, wq = make_bf16_scene(cfg.seed("tree"), cfg.max_depth, cfg.R, F,
                                                       0.3, hidden, wscale=2.0)
     x, w = I.uniform_queries(500 + n, n)
@@ -112,7 +112,7 @@ def test_bf16_forward_shapes(shape, n):
 
 
 def test_bf16_forward_fp32_tables():
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     sc, ot, tables, weights, tq, wq = make_bf16_scene(cfg.seed("tree"), cfg.max_depth, cfg.R, 8,
                                                       0.3, [64, 64], wscale=2.0, tdt=torch.float32)
     x, w = I.uniform_queries(61, 3000)
@@ -150,10 +150,10 @@ def test_bf16_forward_batched_scenes():
 
 def _bwd_case(shape):
     if shape == "cfg0":
-        return I.CONFIGS[0], [32, 32], 4
+        return I.WORKLOADS["forward_small"], [32, 32], 4
     if shape == "cfg1":
-        return I.CONFIGS[1], [64, 64], 8
-    return I.CONFIGS[2], [64, 64, 64], 8
+        return I.WORKLOADS["train_f32"], [64, 64], 8
+    return I.WORKLOADS["train_bf16"], [64, 64, 64], 8
 
 
 def _mask_margin(weights, h):
@@ -211,11 +211,11 @@ def test_bf16_backward_vs_oracle(shape):
 
 
 def test_bf16_backward_config2_inputs():
-    """Gradients of one config-[2] step (its own inputs: sigma 0.01, Xavier
+    """Gradients of one train_bf16 step (its own inputs: sigma 0.01, Xavier
     weights, 4096 pairs, loss scale 2^15) per tensor against the FP64 oracle
     on the quantised parameters."""
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[2]
+    cfg = I.WORKLOADS["train_bf16"]
     step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=4096)
     step.forward()
     step.loss_and_grad()
@@ -245,12 +245,12 @@ def test_bf16_backward_config2_inputs():
 
 
 def test_bf16_train_step_config2_shapes():
-    """Config [2] shapes (depth 8, FP16 tables, 72-64-64-64-3 BF16, dynamic
+    """train_bf16 shapes (depth 8, FP16 tables, 72-64-64-64-3 BF16, dynamic
     loss scaling) on 8192 pairs: loss, gradient norm and update vs the FP64
     oracle step on the FP32 masters."""
     from paper_2606_08469_gb300 import api as A
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[2]
+    cfg = I.WORKLOADS["train_bf16"]
     step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=8192)
     ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
     T = tables.astype(np.float64)
@@ -317,10 +317,10 @@ def _grads_close(a_states, b_states, tol):
 @pytest.mark.parametrize("rhs_grad", [True, False])
 def test_fused_training_pass_matches_unfused(rhs_grad):
     """octa_train_fused vs octa_query_fwd + residual_loss + octa_query_bwd on
-    config-[2] shapes (4,097 pairs: a ragged last tile): same loss, same
+    train_bf16 shapes (4,097 pairs: a ragged last tile): same loss, same
     gradients up to the order of the FP32 atomics; loss vs the FP64 oracle."""
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[2]
+    cfg = I.WORKLOADS["train_bf16"]
     a, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=4097, rhs_grad=rhs_grad)
     b, _ = WL.train_step_for(cfg, n_pairs=4097, rhs_grad=rhs_grad, fused=True)
     a.forward()
@@ -360,7 +360,7 @@ def test_fused_training_step_graph_and_scaler():
     with eager fused steps; a host-injected overflow skips and halves."""
     from paper_2606_08469_gb300 import api as A
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[2]
+    cfg = I.WORKLOADS["train_bf16"]
     a, _ = WL.train_step_for(cfg, n_pairs=8192, fused=True)
     b, _ = WL.train_step_for(cfg, n_pairs=8192, fused=True)
     a.step()
@@ -411,7 +411,7 @@ def test_persistent_step_matches_fused_plus_adam(multi):
         a, _ = WL.batched_train_step(counts=counts, fused=True)
         b, _ = WL.batched_train_step(counts=counts, persistent=True)
     else:
-        cfg = I.CONFIGS[2]
+        cfg = I.WORKLOADS["train_bf16"]
         a, _ = WL.train_step_for(cfg, n_pairs=8192, fused=True)
         b, _ = WL.train_step_for(cfg, n_pairs=8192, persistent=True)
     t0 = [s.master_t.clone() for s in a.states]
@@ -469,7 +469,7 @@ def test_persistent_step_barrier_timeout_reports_status():
     the optimiser is skipped, and the next step runs normally."""
     from paper_2606_08469_gb300 import _lib as L
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[2]
+    cfg = I.WORKLOADS["train_bf16"]
     b, _ = WL.train_step_for(cfg, n_pairs=4096, persistent=True)
     status = torch.zeros(1, dtype=torch.int32, device=DEV)
     before = b.states[0].master_t.clone()

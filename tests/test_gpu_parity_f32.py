@@ -85,7 +85,7 @@ def normwise(a, b):
 @pytest.mark.parametrize("sigma,wscale", [(0.1, 1.0), (0.6, 3.0)])
 def test_forward_config0_full(sigma, wscale):
     """16384 queries, depth-4 tree, R = 16,16,8,8,8, F = 4, 20-32-32-3."""
-    cfg = I.CONFIGS[0]
+    cfg = I.WORKLOADS["forward_small"]
     sc, ot, tables, weights = make_scene(cfg.seed("tree"), 4, cfg.R, 4, sigma, [32, 32],
                                          wscale=wscale, tseed=cfg.seed("tables"),
                                          wseed=cfg.seed("mlp"))
@@ -102,7 +102,7 @@ def test_forward_config0_full(sigma, wscale):
 
 
 def test_encode_features_match_oracle():
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     sc, ot, tables, weights = make_scene(cfg.seed("tree"), 6, cfg.R, 8, 0.3, [64, 64])
     pairs = I.training_pairs(cfg.seed("queries"), 5000)
     feat, nodes, addr = api().octa_encode(sc, dev(pairs.x), dev(pairs.omega), want_nodes=True,
@@ -163,7 +163,7 @@ def _edge_queries():
 
 @pytest.mark.parametrize("n", [1, 127, 129, 300, 4097])
 def test_forward_ragged_and_edges(n):
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     sc, ot, tables, weights = make_scene(cfg.seed("tree"), 6, cfg.R, 8, 0.3, [64, 64], wscale=2.0)
     xe, we = _edge_queries()
     x, w = I.uniform_queries(77 + n, n)
@@ -177,7 +177,7 @@ def test_forward_ragged_and_edges(n):
 
 
 def test_forward_empty_batch_is_a_no_op():
-    cfg = I.CONFIGS[0]
+    cfg = I.WORKLOADS["forward_small"]
     sc, _, _, _ = make_scene(cfg.seed("tree"), 4, cfg.R, 4, 0.1, [32, 32])
     x = torch.empty((0, 3), device=DEV)
     rgb, _, _ = api().octa_query_fwd(sc, x, x)
@@ -205,7 +205,7 @@ def test_forward_hand_tree_absent_levels():
 
 
 def test_forward_fp16_tables_fp32_decoder():
-    cfg = I.CONFIGS[2]
+    cfg = I.WORKLOADS["train_bf16"]
     sc, ot, tables, weights = make_scene(cfg.seed("tree"), 8, cfg.R, 8, 0.3, [64, 64, 64],
                                          tdt=torch.float16, wscale=2.0)
     x, w = I.uniform_queries(21, 6000)
@@ -246,7 +246,7 @@ def test_malformed_tree_reports_status():
 
 @pytest.mark.parametrize("which", [0, 1])
 def test_backward_matches_oracle(which):
-    cfg = I.CONFIGS[which]
+    cfg = I.WORKLOADS[which]
     hidden = [32, 32] if which == 0 else [64, 64]
     sc, ot, tables, weights = make_scene(cfg.seed("tree"), cfg.max_depth, cfg.R, cfg.F, 0.3,
                                          hidden, wscale=1.5)
@@ -266,7 +266,7 @@ def test_backward_fd_subset_config1():
     """GPU gradient of the Eq. 14 loss on 64 pairs of the config-1 workload vs
     central differences (FP64 oracle) of the frozen-normaliser surrogate."""
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=64, scale=1.0,
                                                              growth_interval=0)
     step.forward()
@@ -353,7 +353,7 @@ def test_batched_scenes_match_oracle():
 
 def test_autograd_function():
     A = api()
-    cfg = I.CONFIGS[0]
+    cfg = I.WORKLOADS["forward_small"]
     sc, ot, tables, weights = make_scene(cfg.seed("tree"), 4, cfg.R, 4, 0.3, [32, 32])
     x, w = I.uniform_queries(55, 2048)
     T = sc.tables.clone().requires_grad_(True)

@@ -149,7 +149,7 @@ def test_attributes_fp32_forward_and_backward():
     72-wide shape): radiance to 1e-5 and table / weight gradients (the
     attributes' W1 columns included) to 1e-5 normwise against the oracle."""
     from paper_2606_08469_gb300 import api as A
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     tree = A.octree_build(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
     ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
     tables = I.make_tables(1101, tree.num_texels, 8, 0.3)

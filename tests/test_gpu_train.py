@@ -120,7 +120,7 @@ def test_train_step_matches_oracle(fused):
     of the FP32 engine in place of forward + residual_loss + backward."""
     from paper_2606_08469_gb300 import api as A
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=4096, fused=fused)
     ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
     st = _oracle_state(tables, weights)
@@ -152,7 +152,7 @@ def test_train_step_full_config1_loss_and_samples():
     """The full 262,144-pair config-1 step on the GPU: the forward on sampled
     queries and the loss value of the whole batch vs the oracle."""
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     step, (tree, tables, weights, pairs) = WL.train_step_for(cfg)
     step.forward()
     step.loss_and_grad()
@@ -176,7 +176,7 @@ def test_train_step_full_config1_loss_and_samples():
 
 def test_train_step_graph_replay_equals_eager():
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     a, host = WL.train_step_for(cfg, n_pairs=8192)
     b, _ = WL.train_step_for(cfg, n_pairs=8192)
     t0 = torch.from_numpy(host[1]).to(DEV)
@@ -216,7 +216,7 @@ def test_fused_f32_pass_matches_unfused(rhs_grad):
     ragged batch (4097 pairs: a one-pair tail tile).  Both run the same FP32
     arithmetic; only the atomics' summation order differs."""
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     a, _ = WL.train_step_for(cfg, n_pairs=4097, rhs_grad=rhs_grad)
     b, _ = WL.train_step_for(cfg, n_pairs=4097, rhs_grad=rhs_grad, fused=True)
     a.forward()
@@ -254,7 +254,7 @@ def test_pair_inputs_can_be_swapped():
     double-buffered end-to-end loop does) gives the same loss and gradients;
     arrays of another shape are refused."""
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.CONFIGS[1]
+    cfg = I.WORKLOADS["train_f32"]
     a, _ = WL.train_step_for(cfg, n_pairs=1000, fused=True)
     b, _ = WL.train_step_for(cfg, n_pairs=1000, fused=True)
     copies = {k: t.clone() for k, t in b.pair_inputs().items()}
