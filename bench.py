@@ -466,7 +466,7 @@ def full_inference_leg(dev, flush, stream, steps):
     res = [int(np.floor(16 * (512 / 16) ** (l / 7))) for l in range(8)]
     pred = api.Predictor(g.uniform(-0.1, 0.1, (8, 1 << 16, 2)).astype(np.float32), res,
                          I.make_mlp(cfg.seed("mlp") + 5, [19, 64, 64, 1]), device=dev)
-    out = {"workload": "gbuffer_frame frames, full method: predictor g_psi + shifted lookup + decoder "
+    out = {"workload": "gbuffer_frame G-buffer frames (1280x720, 1024x1024), full method: predictor g_psi + shifted lookup + decoder "
                        "on [h, g] (13 attributes), BF16 decoder 85-64-64-3, FP16 vertex tables",
            "paper_context": "the paper reports 10-20 ms per frame on an RTX 3090 for its whole "
                             "renderer (G-buffer included, decoder 4x128): another machine and "
