@@ -390,7 +390,7 @@ def train_full_leg(dev, flush, stream, steps):
     out = {"workload": "train_f32 training step, FP32, 262144 pairs = 524288 queries, fused FP32 "
                        "pass + Adam; train_bf16 training step, BF16, 1048576 pairs, fused tensor-core "
                        "pass + Adam: trilinear vertex form vs cell form"}
-    for ci, prec in ((1, "f32"), (2, None)):
+    for ci, prec in (("train_f32", "f32"), ("train_bf16", None)):
         cfg = I.WORKLOADS[ci]
         tag = "f32_cfg1" if prec else "bf16_cfg2"
         for form in ("cell", "full"):

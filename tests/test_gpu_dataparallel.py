@@ -21,7 +21,8 @@ def _rel(a, b):
     return (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
 
 
-@pytest.mark.parametrize("which,precision,tol", [(1, "f32", 1e-5), (2, None, 1e-5)])
+@pytest.mark.parametrize("which,precision,tol", [("train_f32", "f32", 1e-5),
+                                                  ("train_bf16", None, 1e-5)])
 def test_shard_passes_sum_to_the_batch_pass(which, precision, tol):
     from paper_2606_08469_gb300 import workloads as WL
     cfg = I.WORKLOADS[which]

@@ -244,13 +244,13 @@ def test_malformed_tree_reports_status():
 
 # ----------------------------------------------------------------- backward
 
-@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("which", ["forward_small", "train_f32"])
 def test_backward_matches_oracle(which):
     cfg = I.WORKLOADS[which]
-    hidden = [32, 32] if which == 0 else [64, 64]
+    hidden = [32, 32] if which == "forward_small" else [64, 64]
     sc, ot, tables, weights = make_scene(cfg.seed("tree"), cfg.max_depth, cfg.R, cfg.F, 0.3,
                                          hidden, wscale=1.5)
-    x, w = I.uniform_queries(31 + which, 12000)
+    x, w = I.uniform_queries(31 + cfg.index, 12000)
     d_rgb = np.random.default_rng(5).normal(size=(len(x), 3)).astype(np.float32)
     dT = torch.zeros(sc.tables.shape, device=DEV)
     dW = torch.zeros(sc.weights.shape, device=DEV)
