@@ -94,14 +94,14 @@ def test_bf16_forward_config3_gbuffer_sample():
     check_forward(sc, ot, tables, weights, tq, wq, x[idx[:8192]], w[idx[:8192]])
 
 
-@pytest.mark.parametrize("shape", ["cfg0", "cfg1", "cfg2"])
+@pytest.mark.parametrize("shape", ["forward_small", "train_f32", "train_bf16"])
 @pytest.mark.parametrize("n", [1, 129, 5000])
 def test_bf16_forward_shapes(shape, n):
     """Every built decoder shape, features drawn wide (sigma 0.3, weights x2)
     so that the decoder is far from linear, ragged batch sizes."""
-    if shape == "cfg0":
+    if shape == "forward_small":
         cfg, hidden, F = I.WORKLOADS["forward_small"], [32, 32], 4
-    elif shape == "cfg1":
+    elif shape == "train_f32":
         cfg, hidden, F = I.WORKLOADS["train_f32"], [64, 64], 8
     else:
         cfg, hidden, F = I.WORKLOADS["train_bf16"], [64, 64, 64], 8
@@ -149,9 +149,9 @@ def test_bf16_forward_batched_scenes():
 # ----------------------------------------------------------------- backward
 
 def _bwd_case(shape):
-    if shape == "cfg0":
+    if shape == "forward_small":
         return I.WORKLOADS["forward_small"], [32, 32], 4
-    if shape == "cfg1":
+    if shape == "train_f32":
         return I.WORKLOADS["train_f32"], [64, 64], 8
     return I.WORKLOADS["train_bf16"], [64, 64, 64], 8
 
@@ -171,7 +171,7 @@ def _mask_margin(weights, h):
     return margins
 
 
-@pytest.mark.parametrize("shape", ["cfg0", "cfg1", "cfg2"])
+@pytest.mark.parametrize("shape", ["forward_small", "train_f32", "train_bf16"])
 def test_bf16_backward_vs_oracle(shape):
     """Table and weight gradients of the tensor-core backward against the
     FP64 oracle on the quantised parameters (arithmetic of BF16 operands)
