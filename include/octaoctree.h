@@ -143,9 +143,10 @@ typedef struct octa_scene {
  * normalised as v / sqrt(v.v)), evaluated as (x - c_j) d + omega_r in
  * binary32 with one rounding per operation (omega_r = (2 (n.omega)) n -
  * omega; the octahedral map divides by the L1 norm, so no normalisation).
- * octa_encode and, for BF16 decoders, octa_query_fwd evaluate it (the
- * other entry points return OCTA_EUNSUPPORTED); the disparity comes from
- * the caller (octa_disparity computes it with the predictor g_psi).      */
+ * octa_encode and, for BF16 decoders, octa_query_fwd and octa_query_bwd
+ * evaluate it (the other entry points return OCTA_EUNSUPPORTED); the
+ * disparity comes from the caller (octa_disparity computes it with the
+ * predictor g_psi) and receives no gradient.                             */
 #define OCTA_FORM_SHIFTED 2
 
 /* Queries: scene s answers queries [scene_start[s], scene_start[s+1]).   */

@@ -695,7 +695,8 @@ def residual_loss(Lp, Ls, E, w, eps=1e-2, rhs_grad=True, scale=1.0):
     return loss, dLp, dLs
 
 
-def query_backward(tree, tables, weights, x, omega, d_rgb, form="cell", attrs=None):
+def query_backward(tree, tables, weights, x, omega, d_rgb, form="cell", attrs=None, normal=None,
+                   disparity=None):
     """Gradients of sum(d_rgb * L_hat) w.r.t. the table and the weights.
 
     Decoder: delta_L = d_rgb * exp(z_L); dW_i = delta_i^T a_{i-1};
@@ -706,7 +707,7 @@ def query_backward(tree, tables, weights, x, omega, d_rgb, form="cell", attrs=No
     T = np.asarray(tables, dtype=np.float64)
     F = T.shape[1]
     K = tree.num_levels
-    _, h, addr, weight = _encode(tree, T, x, omega, form)
+    _, h, addr, weight = _encode(tree, T, x, omega, form, normal, disparity)
     rgb, zs, inputs = mlp_forward(weights, decoder_input(h, attrs))
     Ws = [np.asarray(W, dtype=np.float64) for W in weights]
     delta = np.asarray(d_rgb, dtype=np.float64) * rgb

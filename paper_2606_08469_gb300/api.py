@@ -230,13 +230,13 @@ def octa_query_fwd(scenes, x, omega, counts=None, want_nodes=False, want_addr=Fa
 
 
 def octa_query_bwd(scenes, x, omega, d_rgb, grads, counts=None, status=None, stream=None,
-                   attrs=None):
+                   attrs=None, normal=None, disparity=None):
     """grads: list of (d_tables fp32, d_weights fp32) per scene; accumulated."""
     arr, ns = _scene_array(scenes)
     g = (L.octa_scene_grads * ns)(*[L.octa_scene_grads(dt.data_ptr(), dw.data_ptr())
                                     for dt, dw in grads])
     q = _queries(x, omega, counts)
-    _set_extras(q, int(x.shape[0]), attrs=attrs)
+    _set_extras(q, int(x.shape[0]), normal, disparity, attrs)
     L.check(_lib().octa_query_bwd(arr, ns, C.byref(q), _ptr(d_rgb), g, _ptr(status),
                                   _stream(stream)), "octa_query_bwd")
 

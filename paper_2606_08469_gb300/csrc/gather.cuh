@@ -223,6 +223,25 @@ __device__ __forceinline__ void reflect_f32_rn(const float (&w0)[3], const float
   for (int a = 0; a < 3; ++a) r[a] = __fsub_rn(__fmul_rn(d2, n[a]), w[a]);
 }
 
+// Cell j's triangle in the shifted form: the direction v_j = (x - c_j) d +
+// omega_r (Eq. 9; c_j = (c0 + offset_j + 1/2) 2^-l, exact), folded, and its
+// triangle and barycentric weights on the level's vertex map (vidx, b of fl).
+__device__ __forceinline__ void shifted_cell_vertex(const DevScene& sc, const float (&xs)[3],
+                                                    const float (&wr)[3], float disp, int l,
+                                                    const int (&c0)[3], int j, FullLevel& fl) {
+  const float scale = __int_as_float((127 - l) << 23);  // 2^-l
+  const int cj[3] = {c0[0] + (j & 1), c0[1] + ((j >> 1) & 1), c0[2] + (j >> 2)};
+  float dir[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float c = __fmul_rn(__fadd_rn(static_cast<float>(cj[a]), 0.5f), scale);
+    dir[a] = __fadd_rn(__fmul_rn(__fsub_rn(xs[a], c), disp), wr[a]);
+  }
+  float ux, uy;
+  octa_fold(dir[0], dir[1], dir[2], ux, uy);
+  full_vertex(ux, uy, sc.R[l], fl);
+}
+
 // The shifted form of one query per thread (encoding kernel): per level the
 // eight cells' nodes, then in each present cell j its own direction
 // v_j = (x - c_j) d + omega_r (Eq. 9; c_j = (c + 1/2) 2^-l exact), the
@@ -248,7 +267,6 @@ __device__ __forceinline__ void gather_shifted_query(const QueryParams& p, const
       for (int f = 0; f < F; ++f) v[f] = 0.f;
       int32_t* aout = (want_addr && l < p.kmax_out) ? p.texel_addr + (gq * p.kmax_out + l) * 24
                                                     : nullptr;
-      const float scale = __int_as_float((127 - l) << 23);  // 2^-l
 #pragma unroll 1
       for (int j = 0; j < 8; ++j) {
         if (fl.base[j] < 0) {
@@ -256,16 +274,7 @@ __device__ __forceinline__ void gather_shifted_query(const QueryParams& p, const
             for (int k = 0; k < 3; ++k) aout[3 * j + k] = -1;
           continue;
         }
-        const int cj[3] = {c0[0] + (j & 1), c0[1] + ((j >> 1) & 1), c0[2] + (j >> 2)};
-        float dir[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const float c = __fmul_rn(__fadd_rn(static_cast<float>(cj[a]), 0.5f), scale);
-          dir[a] = __fadd_rn(__fmul_rn(__fsub_rn(xs[a], c), disp), wr[a]);
-        }
-        float ux, uy;
-        octa_fold(dir[0], dir[1], dir[2], ux, uy);
-        full_vertex(ux, uy, sc.R[l], fl);
+        shifted_cell_vertex(sc, xs, wr, disp, l, c0, j, fl);
         TexelRaw<TT, F> tx[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) tx[k].load(sc.tables, uint32_t(fl.base[j] + fl.vidx[k]));

@@ -707,9 +707,13 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
     const bool valid = row < nq;
     const int64_t gq = q0 + row;
     const bool full = sc.query_form == OCTA_FORM_TRILINEAR_VERTEX;  // uniform over the CTA
+    const bool shifted = sc.query_form == OCTA_FORM_SHIFTED;
     const QueryIn& qry = in;  // the layer loops below reuse the name in
     if (full)
       locate_gather_bf16<S, TT, 1, OCTA_FORM_TRILINEAR_VERTEX>(
+          p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), nullptr, nullptr, t);
+    else if (shifted)
+      locate_gather_bf16<S, TT, 1, OCTA_FORM_SHIFTED>(
           p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), nullptr, nullptr, t);
     else
       locate_gather_bf16<S, TT>(p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), base_sm,
@@ -879,12 +883,15 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
           tmem_ld16(lane_work + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
         tmem_wait_ld();
         tc_fence_before_sync();
+        // full and shifted forms: dh by level from a thread-local copy (their
+        // level loops stay rolled)
+        float dh[S::WP];
+        if (full || shifted) {
+#pragma unroll
+          for (int c = 0; c < S::WP; ++c) dh[c] = __uint_as_float(r[c]);
+        }
         if (full) {  // the 24 vertices of each level (Eq. 10 with Eq. 6)
           if (valid) {
-            // dh by level from a thread-local copy (the level loop stays rolled)
-            float dh[S::WP];
-#pragma unroll
-            for (int c = 0; c < S::WP; ++c) dh[c] = __uint_as_float(r[c]);
             float ux, uy;
             octa_fold(qry.w0, qry.w1, qry.w2, ux, uy);
             const float xs[3] = {clamp01(qry.x0), clamp01(qry.x1), clamp01(qry.x2)};
@@ -899,6 +906,37 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                   if (fl.base[j] < 0) continue;
+#pragma unroll
+                  for (int k = 0; k < 3; ++k) {
+                    const float w = fl.wn[j] * fl.b[k];
+                    float4* dst = reinterpret_cast<float4*>(
+                                      sc.d_tables + int64_t(fl.base[j] + fl.vidx[k]) * S::F) + c4;
+                    atomicAdd(dst, make_float4(w * g0, w * g1, w * g2, w * g3));
+                  }
+                }
+              }
+            });
+          }
+        } else if (shifted) {  // each cell's own triangle (Eq. 7-9 with Eq. 6, 10)
+          if (valid) {
+            const float xs[3] = {clamp01(qry.x0), clamp01(qry.x1), clamp01(qry.x2)};
+            const float w0[3] = {qry.w0, qry.w1, qry.w2};
+            const float n0[3] = {p.normal[3 * gq], p.normal[3 * gq + 1], p.normal[3 * gq + 2]};
+            float wr[3];
+            reflect_f32_rn(w0, n0, wr);
+            const float disp = p.disparity[gq];
+            visit_cell_levels<S::KPAD, false>(p, sc, tree, xs,
+                                              [&](int l, const int (&c0)[3], FullLevel& fl) {
+#pragma unroll 1
+              for (int j = 0; j < 8; ++j) {
+                if (fl.base[j] < 0) continue;
+                shifted_cell_vertex(sc, xs, wr, disp, l, c0, j, fl);
+#pragma unroll
+                for (int c4 = 0; c4 < S::F / 4; ++c4) {
+                  const float g0 = dh[l * S::F + 4 * c4 + 0];
+                  const float g1 = dh[l * S::F + 4 * c4 + 1];
+                  const float g2 = dh[l * S::F + 4 * c4 + 2];
+                  const float g3 = dh[l * S::F + 4 * c4 + 3];
 #pragma unroll
                   for (int k = 0; k < 3; ++k) {
                     const float w = fl.wn[j] * fl.b[k];

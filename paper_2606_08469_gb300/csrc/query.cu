@@ -364,11 +364,19 @@ extern "C" int octa_query_bwd(const octa_scene* scenes, int32_t n_scenes, const 
   QueryParams p;
   int rc = build_query_params(scenes, n_scenes, q, grads, p);
   if (rc) return rc;
-  rc = reject_shifted(scenes, n_scenes);
+  if (scenes[0].query_form == OCTA_FORM_SHIFTED) {  // the tensor-core backward only
+    if (scenes[0].weight_dtype != OCTA_BF16)
+      return fail(OCTA_EUNSUPPORTED, "the shifted form's backward needs BF16 decoders");
+    if (q->n > 0 && (!q->normal || !q->disparity))
+      return fail(OCTA_EINVAL, "the shifted form needs normal and disparity");
+  }
+  rc = check_one_form(scenes, n_scenes, nullptr);
   if (rc) return rc;
   if (q->n > 0 && !d_rgb) return fail(OCTA_EINVAL, "d_rgb must be non-NULL");
   p.d_rgb = d_rgb;
   p.status = status;
+  p.normal = q->normal;
+  p.disparity = q->disparity;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (scenes[0].weight_dtype == OCTA_BF16) return tc::query_bwd(scenes, n_scenes, p, st);
   return f32::dispatch(scenes, n_scenes, p, f32::Mode::kBackward, st);

@@ -86,4 +86,48 @@ def test_shifted_global_walk_and_errors():
     with pytest.raises(L.OctaError):
         A.octa_encode(sc, dev(x), dev(w))                        # no normal / disparity
     with pytest.raises(L.OctaError):
-        A.octa_query_fwd(sc, dev(x), dev(w))                     # encoding only
+        A.octa_query_fwd(sc, dev(x), dev(w))                     # FP32 decoder: encoding only
+
+
+def test_shifted_bf16_backward_vs_oracle():
+    """octa_query_bwd in the shifted form on a BF16 decoder (the disparity
+    given, no gradient to it): table and weight gradients against the FP64
+    oracle on the quantised parameters with the BF16 path's ReLU-mask bound
+    (the last layer's dW to 1e-2, the rest to 3 sqrt(f) + 1e-2)."""
+    from paper_2606_08469_gb300 import _lib as L
+    from paper_2606_08469_gb300 import api as A
+    seed, depth, V, F = 1450, 5, [17, 17, 9, 9, 5, 3], 8
+    tree = A.octree_build(seed, depth, 0.6, V)
+    ot = O.build_tree(seed, depth, 0.6, V)
+    tq = I.make_tables(seed + 1, tree.num_texels, F, 0.3).astype(np.float16).astype(np.float32)
+    weights = [W * np.float32(1.5) for W in I.make_mlp(seed + 2, [(depth + 1) * F, 64, 64, 3])]
+    Wb = [dev(W).to(torch.bfloat16) for W in weights]
+    wq = [W.float().cpu().numpy() for W in Wb]
+    sc = A.Scene(tree, dev(tq).half().contiguous(), Wb, device=DEV, query_form=L.OCTA_FORM_SHIFTED)
+    g = I.rng(seed + 3)
+    n = 6000
+    x = g.random((n, 3)).astype(np.float32)
+    w = I.unit_vectors(g, n).astype(np.float32)
+    nrm = I.unit_vectors(g, n).astype(np.float32)
+    d = g.uniform(0, 8, n).astype(np.float32)
+    d_rgb = g.normal(size=(n, 3)).astype(np.float32)
+    dT = torch.zeros((tree.num_texels, F), device=DEV)
+    dW = torch.zeros(sc.weights.shape, device=DEV)
+    A.octa_query_bwd(sc, dev(x), dev(w), dev(d_rgb), [(dT, dW)], normal=dev(nrm), disparity=dev(d))
+    rT, rWs, _ = O.query_backward(ot, tq, wq, x, w, d_rgb, form="shifted", normal=nrm, disparity=d)
+    h = O.encode_features_shifted(ot, tq, x, w, nrm, d).h
+    a = h
+    flags = []
+    for W in [np.asarray(W, np.float64) for W in wq][:-1]:
+        z = a @ W.T
+        flags.append((np.abs(z) < 2.0 ** -7 * (np.abs(a) @ np.abs(W).T)).ravel())
+        a = np.maximum(z, 0.0)
+    frac = float(np.mean(np.concatenate(flags)))
+    nw = lambda u, v: np.linalg.norm(u - v) / np.linalg.norm(v)
+    errs = [nw(dT.cpu().numpy(), rT)]
+    gw = dW.cpu().numpy()
+    for (off, o, i), rW in zip(sc.weight_slices(), rWs):
+        errs.append(nw(gw[off:off + o * i].reshape(o, i), rW))
+    print("BF16 shifted backward errors", [round(e, 5) for e in errs], "mask fraction", frac)
+    assert errs[-1] <= 1e-2
+    assert max(errs[:-1]) <= 3.0 * np.sqrt(frac) + 1e-2

@@ -104,3 +104,41 @@ def test_each_cell_looks_up_its_own_direction():
     assert checked > 2000
     full = O.encode_features_full(ot, tables, x, O.reflect_f32(w, nrm))
     assert np.mean(enc.addr != full.addr) > 0.1
+
+
+def test_shifted_backward_by_central_differences():
+    """Table and weight gradients of sum(d_rgb . L_hat) in the shifted form
+    against central differences of the forward (the disparity fixed; step
+    1e-6, so the differences carry ~1e-6 relative rounding of sum's size)."""
+    ot, tables = _tree_and_tables(71, 2, [5, 5, 3])
+    g = I.rng(72)
+    n = 40
+    x = g.random((n, 3)).astype(np.float32)
+    w = I.unit_vectors(g, n).astype(np.float32)
+    nrm = I.unit_vectors(g, n).astype(np.float32)
+    d = g.uniform(0.5, 5.0, n).astype(np.float32)
+    weights = [W.astype(np.float64) * 2 for W in I.make_mlp(73, [12, 16, 16, 3])]
+    d_rgb = g.normal(size=(n, 3))
+    T = tables.astype(np.float64)
+
+    def f(T_, Ws_):
+        rgb, _ = O.query_forward(ot, T_, Ws_, x, w, form="shifted", normal=nrm, disparity=d)
+        return float(np.sum(d_rgb * rgb))
+    dT, dWs, _ = O.query_backward(ot, T, weights, x, w, d_rgb, form="shifted", normal=nrm,
+                                  disparity=d)
+    h = 1e-6
+    touched = np.nonzero(np.abs(dT).sum(1) > 0)[0]
+    for r in g.choice(touched, 10, replace=False):
+        c = int(g.integers(4))
+        P, Q = T.copy(), T.copy()
+        P[r, c] += h
+        Q[r, c] -= h
+        assert dT[r, c] == pytest.approx((f(P, weights) - f(Q, weights)) / (2 * h), rel=1e-5,
+                                         abs=1e-8)
+    for i in range(3):
+        a, b = int(g.integers(weights[i].shape[0])), int(g.integers(weights[i].shape[1]))
+        P = [W.copy() for W in weights]
+        Q = [W.copy() for W in weights]
+        P[i][a, b] += h
+        Q[i][a, b] -= h
+        assert dWs[i][a, b] == pytest.approx((f(T, P) - f(T, Q)) / (2 * h), rel=1e-5, abs=1e-8)
