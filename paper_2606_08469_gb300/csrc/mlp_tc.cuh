@@ -16,6 +16,11 @@
 //            last layer (N padded to 16) ends in exp().
 // Several CTAs share an SM (64 tensor-memory columns each), so one CTA's
 // gather overlaps another's MMAs.
+//
+// The kernels and launchers live in this header; mlp_tc_fwd.cu, mlp_tc_bwd.cu
+// and mlp_tc_step.cu each define one group of entry points (OCTA_TC_FWD,
+// OCTA_TC_BWD, OCTA_TC_STEP), so the three groups compile in parallel.
+#pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -1104,6 +1109,7 @@ int dispatch_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, c
               need, NH, H);
 }
 
+#ifdef OCTA_TC_BWD
 int query_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
   return dispatch_bwd<false, false>(scenes, n_scenes, p, nullptr, stream);
 }
@@ -1111,12 +1117,16 @@ int query_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cuda
 int train_fused(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
   return dispatch_bwd<true, false>(scenes, n_scenes, p, nullptr, stream);
 }
+#endif  // OCTA_TC_BWD
 
+#ifdef OCTA_TC_STEP
 int train_step_persistent(const octa_scene* scenes, int n_scenes, const QueryParams& p,
                           const AdamBlock& adam, cudaStream_t stream) {
   return dispatch_bwd<true, true>(scenes, n_scenes, p, &adam, stream);
 }
+#endif  // OCTA_TC_STEP
 
+#ifdef OCTA_TC_FWD
 int query_fwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
   const octa_scene& c0 = scenes[0];
   const int F = c0.F, L = c0.n_layers, H = c0.widths[1], tdt = c0.table_dtype;
@@ -1144,6 +1154,7 @@ int query_fwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cuda
   return fail(OCTA_EUNSUPPORTED, "BF16 path: no built shape for F=%d, K*F=%d, hidden %d x %d", F,
               need, NH, H);
 }
+#endif  // OCTA_TC_FWD
 
 }  // namespace tc
 }  // namespace octa
