@@ -445,7 +445,8 @@ def multi_rhs_leg(dev, flush, stream, steps):
 def full_inference_leg(dev, flush, stream, steps):
     """The paper's whole inference per frame on gbuffer_frame's G-buffer frames:
     d = g_psi(x, omega_r) (octa_disparity: 8 hash levels of 2^16 entries,
-    MLP 19-64-64-1), then octa_query_fwd in the disparity-shifted form
+    MLP 19-64-64-1 on the tensor cores; the FP32 CUDA-core predictor timed
+    beside it), then octa_query_fwd in the disparity-shifted form
     (Eq. 7-9 with Eq. 10 and Eq. 6, vertex maps 65 ... 9) on a BF16 decoder
     whose input is [h, g] (Eq. 12: 72 features + 13 surface attributes),
     85-64-64-3 on the tensor cores."""
@@ -464,8 +465,10 @@ def full_inference_leg(dev, flush, stream, steps):
                    query_form=L.OCTA_FORM_SHIFTED)
     g = I.rng(cfg.seed("queries") + 91)
     res = [int(np.floor(16 * (512 / 16) ** (l / 7))) for l in range(8)]
-    pred = api.Predictor(g.uniform(-0.1, 0.1, (8, 1 << 16, 2)).astype(np.float32), res,
-                         I.make_mlp(cfg.seed("mlp") + 5, [19, 64, 64, 1]), device=dev)
+    ptab = g.uniform(-0.1, 0.1, (8, 1 << 16, 2)).astype(np.float32)
+    pmlp = I.make_mlp(cfg.seed("mlp") + 5, [19, 64, 64, 1])
+    pred = api.Predictor(ptab, res, pmlp, device=dev, tensor_cores=True)
+    pred32 = api.Predictor(ptab, res, pmlp, device=dev)
     out = {"workload": "gbuffer_frame G-buffer frames (1280x720, 1024x1024), full method: predictor g_psi + shifted lookup + decoder "
                        "on [h, g] (13 attributes), BF16 decoder 85-64-64-3, FP16 vertex tables",
            "paper_context": "the paper reports 10-20 ms per frame on an RTX 3090 for its whole "
@@ -488,7 +491,9 @@ def full_inference_leg(dev, flush, stream, steps):
             frame()
         t = _timed(frame, steps, flush, stream)
         t_p = _timed(lambda: api.octa_disparity(pred, X, Om, N_, out=d), steps, flush, stream)
+        t_p32 = _timed(lambda: api.octa_disparity(pred32, X, Om, N_, out=d), steps, flush, stream)
         out[f"{wdt}x{hgt}"] = {"ms_per_frame": round(t, 4), "predictor_ms": round(t_p, 4),
+                               "predictor_fp32_ms": round(t_p32, 4),
                                "Mq/s": round(n / t / 1e3, 1)}
     return out
 

@@ -283,6 +283,11 @@ typedef struct octa_predictor {
   const float* table;          /* device [levels][2^log2_T][2] float32     */
   const float* weights;        /* device W1 [64][2 levels + 3], W2 [64][64],*/
                                /* W3 [1][64], row-major, back to back      */
+  const void* weights_bf16;    /* NULL: the MLP runs in FP32 on the CUDA
+                                  cores; else the same weights in BF16 and
+                                  the MLP runs on the tcgen05 tensor cores
+                                  (BF16 operands, FP32 accumulation; levels
+                                  <= 14)                                  */
   int32_t levels;              /* 1..OCTA_PRED_MAX_LEVELS                  */
   int32_t log2_T;              /* 4..24                                    */
   int32_t res[OCTA_PRED_MAX_LEVELS]; /* cells a side per level, 1..65535  */

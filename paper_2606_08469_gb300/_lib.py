@@ -151,8 +151,9 @@ OCTA_PRED_MAX_LEVELS = 16
 
 
 class octa_predictor(C.Structure):
-    _fields_ = [("table", C.c_void_p), ("weights", C.c_void_p), ("levels", C.c_int32),
-                ("log2_T", C.c_int32), ("res", C.c_int32 * OCTA_PRED_MAX_LEVELS)]
+    _fields_ = [("table", C.c_void_p), ("weights", C.c_void_p), ("weights_bf16", C.c_void_p),
+                ("levels", C.c_int32), ("log2_T", C.c_int32),
+                ("res", C.c_int32 * OCTA_PRED_MAX_LEVELS)]
 
 
 class octa_prims(C.Structure):

@@ -390,7 +390,7 @@ class Predictor:
     float32 (T a power of two), per-level resolutions, and the MLP
     W1 [64][2L+3], W2 [64][64], W3 [1][64] float32."""
 
-    def __init__(self, table, res, weights, device="cuda"):
+    def __init__(self, table, res, weights, device="cuda", tensor_cores=False):
         dev = torch.device(device)
         self.table = torch.as_tensor(table, dtype=torch.float32).to(dev).contiguous()
         L_, T, F = self.table.shape
@@ -398,11 +398,14 @@ class Predictor:
         self.res = [int(r) for r in res]
         self.weights = torch.cat([torch.as_tensor(W, dtype=torch.float32).reshape(-1)
                                   for W in weights]).to(dev).contiguous()
+        # tensor_cores: the MLP in BF16 on the tcgen05 path
+        self.weights_bf16 = self.weights.to(torch.bfloat16).contiguous() if tensor_cores else None
 
     def as_c(self):
         p = L.octa_predictor()
         p.table = self.table.data_ptr()
         p.weights = self.weights.data_ptr()
+        p.weights_bf16 = self.weights_bf16.data_ptr() if self.weights_bf16 is not None else None
         p.levels = len(self.res)
         p.log2_T = int(self.table.shape[1]).bit_length() - 1
         for i, r in enumerate(self.res):

@@ -223,6 +223,41 @@ __device__ __forceinline__ void reflect_f32_rn(const float (&w0)[3], const float
   for (int a = 0; a < 3; ++a) r[a] = __fsub_rn(__fmul_rn(d2, n[a]), w[a]);
 }
 
+// One level of g_psi's hash encoding at x (Mueller et al. 2022): p = x N in
+// binary32, cell i0 = min(floor(p), N - 1) per axis, the trilinear blend of
+// the 2 features of the cell's 8 vertices; vertex (i, j, k) is entry
+// i + (N+1) (j + (N+1) k) of a dense level, else (i ^ j pi_2 ^ k pi_3) mod T.
+__device__ __forceinline__ float2 hash_level(const float2* __restrict__ tab, const float (&xs)[3],
+                                             int N, bool dense, uint32_t tmask) {
+  const float fN = static_cast<float>(N);
+  int i0[3];
+  float f[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float pa = __fmul_rn(xs[a], fN);
+    i0[a] = min(static_cast<int>(floorf(pa)), N - 1);
+    f[a] = __fsub_rn(pa, static_cast<float>(i0[a]));
+  }
+  const uint32_t side = static_cast<uint32_t>(N + 1);
+  float2 t[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const uint32_t i = i0[0] + (c & 1), j = i0[1] + ((c >> 1) & 1), k = i0[2] + (c >> 2);
+    const uint32_t e = dense ? i + side * (j + side * k)
+                             : (i ^ (j * 2654435761u) ^ (k * 805459861u)) & tmask;
+    t[c] = __ldg(tab + e);
+  }
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float w = ((c & 1) ? f[0] : 1.f - f[0]) * (((c >> 1) & 1) ? f[1] : 1.f - f[1]) *
+                    ((c >> 2) ? f[2] : 1.f - f[2]);
+    s0 = fmaf(w, t[c].x, s0);
+    s1 = fmaf(w, t[c].y, s1);
+  }
+  return make_float2(s0, s1);
+}
+
 // Cell j's triangle in the shifted form: the direction v_j = (x - c_j) d +
 // omega_r (Eq. 9; c_j = (c0 + offset_j + 1/2) 2^-l, exact), folded, and its
 // triangle and barycentric weights on the level's vertex map (vidx, b of fl).

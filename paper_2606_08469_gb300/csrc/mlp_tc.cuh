@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "engine_f32.cuh"
 #include "gather.cuh"
@@ -139,6 +140,53 @@ __device__ __forceinline__ void locate_gather_bf16(const QueryParams& p, const D
   }
 }
 
+// The forward kernel's form that runs the disparity predictor g_psi: its
+// input row (hash encoding, omega_r) replaces the octree gather and the
+// single output is d = exp(z).
+constexpr int FORM_PREDICTOR = 100;
+
+// g_psi's input row of one query (Eq. 7, Section 3.5) into the layer-0
+// operand tile: 2 hash features a level, then omega_r; zeros to WP.
+template <class S>
+__device__ __forceinline__ void predictor_gather(const QueryParams& p, const QueryIn& in,
+                                                 int64_t gq, bool valid, uint8_t* act, int q) {
+  static_assert(S::WP >= 2 * 14 + 3, "the tensor-core predictor takes up to 14 levels");
+  float v[S::WP];
+#pragma unroll
+  for (int c = 0; c < S::WP; ++c) v[c] = 0.f;
+  if (valid) {
+    const float xs[3] = {clamp01(in.x0), clamp01(in.x1), clamp01(in.x2)};
+#pragma unroll
+    for (int l = 0; l < 14; ++l) {
+      if (l >= p.pred_levels) break;
+      const float2* tab = reinterpret_cast<const float2*>(p.pred_table) + size_t(l) * (p.pred_tmask + 1u);
+      const float2 e = hash_level(tab, xs, p.pred_res[l], p.pred_dense[l] != 0, p.pred_tmask);
+      v[2 * l] = e.x;
+      v[2 * l + 1] = e.y;
+    }
+    const float w0[3] = {in.w0, in.w1, in.w2};
+    const float n0[3] = {p.normal[3 * gq], p.normal[3 * gq + 1], p.normal[3 * gq + 2]};
+    float wr[3];
+    reflect_f32_rn(w0, n0, wr);
+#pragma unroll
+    for (int l = 1; l <= 14; ++l)
+      if (l == p.pred_levels) {
+        v[2 * l] = wr[0];
+        v[2 * l + 1] = wr[1];
+        v[2 * l + 2] = wr[2];
+      }
+  }
+#pragma unroll
+  for (int c = 0; c < S::WP; c += 8) {
+    uint4 o;
+    o.x = pack_bf16x2(v[c + 0], v[c + 1]);
+    o.y = pack_bf16x2(v[c + 2], v[c + 3]);
+    o.z = pack_bf16x2(v[c + 4], v[c + 5]);
+    o.w = pack_bf16x2(v[c + 6], v[c + 7]);
+    *reinterpret_cast<uint4*>(act + kmajor_offset(q, c, S::WP)) = o;
+  }
+}
+
 // Issue the MMAs of one layer (single thread) and commit to the mbarrier.
 template <class S>
 __device__ __forceinline__ void issue_layer(int layer, uint32_t act_sa, uint32_t w_sa, uint32_t tmem,
@@ -199,14 +247,18 @@ __global__ void __launch_bounds__(NT * TPQ, 4)
     __syncthreads();
     if (s != cur) {
       load_weights_bf16<S>(sc, smem, NTF);
-      tree = stage_tree(p, sc, tree_sm, S::TREE_NODES, threadIdx.x, NTF);
+      if constexpr (FORM != FORM_PREDICTOR)
+        tree = stage_tree(p, sc, tree_sm, S::TREE_NODES, threadIdx.x, NTF);
       cur = s;
       __syncthreads();
     }
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * NT;
     const int nq = static_cast<int>(sc.q_end - q0 < NT ? sc.q_end - q0 : int64_t(NT));
-    locate_gather_bf16<S, TT, TPQ, FORM>(p, sc, tree, in, q0 + q, q < nq, par, act, nullptr,
-                                         nullptr, q);
+    if constexpr (FORM == FORM_PREDICTOR)
+      predictor_gather<S>(p, in, q0 + q, q < nq, act, q);
+    else
+      locate_gather_bf16<S, TT, TPQ, FORM>(p, sc, tree, in, q0 + q, q < nq, par, act, nullptr,
+                                           nullptr, q);
     fence_proxy_async();
     __syncthreads();
 
@@ -246,9 +298,13 @@ __global__ void __launch_bounds__(NT * TPQ, 4)
           tmem_wait_ld();
           if (q < nq) {
             const int64_t gq = q0 + q;
-            p.rgb[3 * gq] = expf(__uint_as_float(r[0]));
-            p.rgb[3 * gq + 1] = expf(__uint_as_float(r[1]));
-            p.rgb[3 * gq + 2] = expf(__uint_as_float(r[2]));
+            if constexpr (FORM == FORM_PREDICTOR) {
+              p.disparity_out[gq] = expf(__uint_as_float(r[0]));
+            } else {
+              p.rgb[3 * gq] = expf(__uint_as_float(r[0]));
+              p.rgb[3 * gq + 1] = expf(__uint_as_float(r[1]));
+              p.rgb[3 * gq + 2] = expf(__uint_as_float(r[2]));
+            }
           }
         }
         tc_fence_before_sync();
@@ -1127,6 +1183,47 @@ int train_step_persistent(const octa_scene* scenes, int n_scenes, const QueryPar
 #endif  // OCTA_TC_STEP
 
 #ifdef OCTA_TC_FWD
+int predictor_fwd(const octa_predictor* pred, const octa_queries* q, float* disparity,
+                  cudaStream_t stream) {
+  QueryParams p;
+  std::memset(&p, 0, sizeof(p));
+  const int L = pred->levels;
+  DevScene& d = p.sc[0];
+  d.weights = pred->weights_bf16;
+  d.n_layers = 3;
+  d.K = 1;
+  d.widths[0] = 2 * L + 3;
+  d.widths[1] = OCTA_PRED_HIDDEN;
+  d.widths[2] = OCTA_PRED_HIDDEN;
+  d.widths[3] = 1;
+  int off = 0;
+  for (int i = 0; i <= 3; ++i) {
+    d.w_offset[i] = off;
+    if (i < 3) off += d.widths[i] * d.widths[i + 1];
+  }
+  d.q_begin = 0;
+  d.q_end = q->n;
+  d.tile_begin = 0;
+  p.n_scenes = 1;
+  p.n_tiles = (q->n + NT - 1) / NT;
+  p.x = q->x;
+  p.omega = q->omega;
+  p.normal = q->normal;
+  p.pred_table = pred->table;
+  p.pred_levels = L;
+  const int64_t T = int64_t(1) << pred->log2_T;
+  p.pred_tmask = static_cast<uint32_t>(T - 1);
+  for (int l = 0; l < L; ++l) {
+    p.pred_res[l] = pred->res[l];
+    const int64_t side = pred->res[l] + 1;
+    p.pred_dense[l] = side * side * side <= T ? 1 : 0;
+  }
+  p.disparity_out = disparity;
+  if (p.n_tiles == 0) return OCTA_OK;
+  return launch_fwd_tpq<Shape<8, 32, 64, 2>, __half, 1, FORM_PREDICTOR>(p, tuning_snapshot(),
+                                                                          stream);
+}
+
 int query_fwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
   const octa_scene& c0 = scenes[0];
   const int F = c0.F, L = c0.n_layers, H = c0.widths[1], tdt = c0.table_dtype;

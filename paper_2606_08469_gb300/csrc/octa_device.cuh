@@ -75,6 +75,14 @@ struct QueryParams {
   // Eq. 12's attributes [n][n_attrs], decoder input columns K*F .. K*F+n_attrs-1
   const float* attrs;
   int32_t n_attrs;
+  // the predictor g_psi on the tensor-core path: hash tables, levels, and the
+  // disparity it writes
+  const float* pred_table;
+  uint32_t pred_tmask;
+  int32_t pred_levels;
+  int32_t pred_res[OCTA_PRED_MAX_LEVELS];
+  int32_t pred_dense[OCTA_PRED_MAX_LEVELS];
+  float* disparity_out;
 };
 
 // Decoder-input columns of level l >= K (past the features): Eq. 12's

@@ -6,6 +6,7 @@
 
 #include "gather.cuh"
 #include "octa_internal.h"
+#include "tc_path.h"
 
 namespace octa {
 namespace {
@@ -28,13 +29,6 @@ struct PredParams {
   int32_t res[OCTA_PRED_MAX_LEVELS];
   int32_t dense[OCTA_PRED_MAX_LEVELS];  // (res + 1)^3 <= T
 };
-
-// Entry of grid vertex (i, j, k) of a level (dense index or spatial hash).
-__device__ __forceinline__ uint32_t vertex_entry(uint32_t i, uint32_t j, uint32_t k, uint32_t side,
-                                                 bool dense, uint32_t tmask) {
-  if (dense) return i + side * (j + side * k);
-  return (i ^ (j * 2654435761u) ^ (k * 805459861u)) & tmask;
-}
 
 // One thread per query; the MLP's weights live in shared memory with W1's
 // rows padded to kW1Row columns (zeros past the encoding's width), so every
@@ -61,31 +55,9 @@ __global__ void __launch_bounds__(kPredThreads, 3) disparity_kernel(const __grid
 #pragma unroll
     for (int l = 0; l < OCTA_PRED_MAX_LEVELS; ++l) {
       if (l >= p.levels) break;
-      const int N = p.res[l];
-      const float fN = static_cast<float>(N);
-      int i0[3];
-      float f[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float pa = __fmul_rn(xs[a], fN);
-        i0[a] = min(static_cast<int>(floorf(pa)), N - 1);
-        f[a] = __fsub_rn(pa, static_cast<float>(i0[a]));
-      }
       const float2* tab = reinterpret_cast<const float2*>(p.table) + size_t(l) * (p.tmask + 1u);
-      const bool dense = p.dense[l] != 0;
-      float2 t[8];
-#pragma unroll
-      for (int c = 0; c < 8; ++c)
-        t[c] = __ldg(tab + vertex_entry(i0[0] + (c & 1), i0[1] + ((c >> 1) & 1), i0[2] + (c >> 2),
-                                        N + 1, dense, p.tmask));
-      float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const float w = ((c & 1) ? f[0] : 1.f - f[0]) * (((c >> 1) & 1) ? f[1] : 1.f - f[1]) *
-                        ((c >> 2) ? f[2] : 1.f - f[2]);
-        s0 = fmaf(w, t[c].x, s0);
-        s1 = fmaf(w, t[c].y, s1);
-      }
+      const float2 e = hash_level(tab, xs, p.res[l], p.dense[l] != 0, p.tmask);
+      const float s0 = e.x, s1 = e.y;
       in[2 * l] = s0;
       in[2 * l + 1] = s1;
     }
@@ -170,6 +142,14 @@ extern "C" int octa_disparity(const octa_predictor* pred, const octa_queries* q,
   if (q->n == 0) return OCTA_OK;
   if (!q->x || !q->omega || !q->normal || !disparity)
     return fail(OCTA_EINVAL, "x, omega, normal and disparity must be non-NULL");
+  if (pred->weights_bf16) {  // the MLP on the tensor cores
+    if (pred->levels > 14)
+      return fail(OCTA_ERANGE, "the tensor-core predictor takes at most 14 levels");
+    for (int l = 0; l < pred->levels; ++l)
+      if (pred->res[l] < 1 || pred->res[l] > 65535)
+        return fail(OCTA_ERANGE, "predictor res[%d] = %d outside [1, 65535]", l, pred->res[l]);
+    return tc::predictor_fwd(pred, q, disparity, static_cast<cudaStream_t>(stream));
+  }
   PredParams p{};
   p.table = pred->table;
   p.weights = pred->weights;

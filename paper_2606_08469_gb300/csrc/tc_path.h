@@ -24,6 +24,10 @@ struct AdamBlock {
 
 
 int query_fwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream);
+// The disparity predictor g_psi with its MLP on the tensor cores (BF16
+// weights_bf16, FP32 accumulation); the caller has validated pred and q.
+int predictor_fwd(const octa_predictor* pred, const octa_queries* q, float* disparity,
+                  cudaStream_t stream);
 int query_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream);
 int train_fused(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream);
 int train_step_persistent(const octa_scene* scenes, int n_scenes, const QueryParams& p,

@@ -169,3 +169,27 @@ def test_attributes_fp32_forward_and_backward():
     gw = dW.cpu().numpy()
     for (off, o, i), rW in zip(sc.weight_slices(), rWs):
         assert np.linalg.norm(gw[off:off + o * i].reshape(o, i) - rW) <= 1e-5 * np.linalg.norm(rW)
+
+
+@pytest.mark.parametrize("levels,log2_T", [(8, 16), (14, 12)])
+def test_disparity_tensor_cores(levels, log2_T):
+    """g_psi's MLP on the tcgen05 path (BF16 inputs and weights, FP32
+    accumulation) against the FP64 oracle on the FP32 master weights: the
+    BF16 path's 1e-2 normwise bound, and per query |d / d_ref - 1| = |dz|
+    within the BF16 rounding of inputs and weights, 2^-6 z_abs + 1e-3 (z_abs
+    the MLP on |W| and |input|); the ragged tail of a 20,001-query batch
+    included."""
+    from paper_2606_08469_gb300 import api as A
+    table, res, weights = _predictor(640 + levels, levels, log2_T, 16, 512)
+    x, w, nrm = _queries(740 + levels, 20001)
+    pred = A.Predictor(table, res, weights, device=DEV, tensor_cores=True)
+    d = A.octa_disparity(pred, dev(x), dev(w), dev(nrm)).cpu().numpy()
+    ref = O.disparity(table, res, weights, x, w, nrm)
+    inp = np.concatenate([O.hash_encode(table, res, x),
+                          O.reflect_f32(w, nrm).astype(np.float64)], axis=1)
+    _, zs, _ = O.mlp_forward([np.abs(W) for W in weights], np.abs(inp))
+    err = np.abs(d / ref - 1)
+    tol = 2.0 ** -6 * zs[-1][:, 0] + 1e-3
+    print("tensor-core predictor: max |d/d_ref - 1|", err.max(), "median tol", np.median(tol))
+    assert np.all(err <= tol)
+    assert np.linalg.norm(d - ref) <= 1e-2 * np.linalg.norm(ref)   # the BF16 path's binding bound

@@ -45,7 +45,7 @@ def test_struct_sizes_match_header(lib):
     assert lib.octa_abi_version() == 4
     assert C.sizeof(L.octa_prims) == 8 + 8 + 4 + 4
     assert C.sizeof(L.octa_queries) == 8 + 8 + 8 + 8 * 17 + 8 + 8 + 8 + 4 + 4
-    assert C.sizeof(L.octa_predictor) == 8 + 8 + 4 + 4 + 4 * 16
+    assert C.sizeof(L.octa_predictor) == 8 + 8 + 8 + 4 + 4 + 4 * 16
     assert C.sizeof(L.octa_pairs) == 6 * 8 + 8 + 8 * 17 + 8 * 16
 
 
