@@ -663,7 +663,9 @@ __device__ __forceinline__ void flush_loss(double& acc, double* loss, int64_t n_
 // radiances (only the loss value leaves the CTA, as FP64 partials).
 // PERSIST (with TRAIN, cooperative launch): after the fused pass the same
 // launch applies Adam to every parameter group (persistent_adam).
-template <class S, typename TT, bool TRAIN, bool PERSIST = false>
+// FORMS: the kernel also serves the full and shifted query forms (scenes in
+// the cell form alone launch the FORMS = false instance, free of their code).
+template <class S, typename TT, bool TRAIN, bool PERSIST = false, bool FORMS = true>
 __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ BwdParams bp) {
   const QueryParams& p = bp.p;
   constexpr int H = S::H, NL = S::NL;
@@ -767,8 +769,8 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
     const int nq = static_cast<int>(sc.q_end - q0 < ROWS ? sc.q_end - q0 : int64_t(ROWS));
     const bool valid = row < nq;
     const int64_t gq = q0 + row;
-    const bool full = sc.query_form == OCTA_FORM_TRILINEAR_VERTEX;  // uniform over the CTA
-    const bool shifted = sc.query_form == OCTA_FORM_SHIFTED;
+    const bool full = FORMS && sc.query_form == OCTA_FORM_TRILINEAR_VERTEX;  // uniform over the CTA
+    const bool shifted = FORMS && sc.query_form == OCTA_FORM_SHIFTED;
     const QueryIn& qry = in;  // the layer loops below reuse the name in
     if (full)
       locate_gather_bf16<S, TT, 1, OCTA_FORM_TRILINEAR_VERTEX>(
@@ -1083,7 +1085,7 @@ int launch_fwd(const QueryParams& p, cudaStream_t stream) {
                                                          : launch_fwd_tpq<S, TT, 1>(p, tu, stream);
 }
 
-template <class S, typename TT, bool TRAIN, bool PERSIST>
+template <class S, typename TT, bool TRAIN, bool PERSIST, bool FORMS>
 int launch_bwd(const QueryParams& p0, const AdamBlock* adam, cudaStream_t stream) {
   if (p0.n_tiles == 0 && !PERSIST) return OCTA_OK;
   constexpr int ROWS = TRAIN ? NT / 2 : NT;
@@ -1101,7 +1103,7 @@ int launch_bwd(const QueryParams& p0, const AdamBlock* adam, cudaStream_t stream
   p.n_items = items;
   p.order = tuning_snapshot().train_order == 1 ? 1 : 0;
   if (items == 0 && !PERSIST) return OCTA_OK;
-  auto kern = bwd_kernel<S, TT, TRAIN, PERSIST>;
+  auto kern = bwd_kernel<S, TT, TRAIN, PERSIST, FORMS>;
   int per_sm = 0;
   int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, S::NTB,
                               static_cast<int>(S::TMEM_COLS), &per_sm);
@@ -1152,10 +1154,18 @@ int dispatch_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, c
   bool f16;
   int rc = select_shape(scenes, n_scenes, &F, &need, &H, &NH, &f16);
   if (rc) return rc;
+  bool forms = false;  // any scene in the full or shifted form
+  for (int s = 0; s < n_scenes; ++s) forms = forms || scenes[s].query_form != OCTA_FORM_CELL_BILINEAR;
 #define OCTA_TC_TRY(F_, WP_, H_, NH_)                                                        \
   if (F == F_ && H == H_ && NH == NH_ && need <= WP_)                                        \
-    return f16 ? launch_bwd<BShape<F_, WP_, H_, NH_>, __half, TRAIN, PERSIST>(p, adam, stream) \
-               : launch_bwd<BShape<F_, WP_, H_, NH_>, float, TRAIN, PERSIST>(p, adam, stream);
+    return forms ? (f16 ? launch_bwd<BShape<F_, WP_, H_, NH_>, __half, TRAIN, PERSIST, true>(     \
+                              p, adam, stream)                                                   \
+                        : launch_bwd<BShape<F_, WP_, H_, NH_>, float, TRAIN, PERSIST, true>(      \
+                              p, adam, stream))                                                  \
+                 : (f16 ? launch_bwd<BShape<F_, WP_, H_, NH_>, __half, TRAIN, PERSIST, false>(    \
+                              p, adam, stream)                                                   \
+                        : launch_bwd<BShape<F_, WP_, H_, NH_>, float, TRAIN, PERSIST, false>(     \
+                              p, adam, stream));
   OCTA_TC_TRY(4, 32, 32, 2)
   OCTA_TC_TRY(8, 64, 64, 2)
   OCTA_TC_TRY(8, 80, 64, 2)
