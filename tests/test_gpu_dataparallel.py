@@ -50,12 +50,15 @@ def test_data_parallel_step_single_rank_is_the_fused_step():
     a, _ = WL.train_step_for(cfg, n_pairs=2048, fused=True)
     b, _ = WL.data_parallel_train_step(cfg, 0, 1, n_pairs=2048)
     dp = D.DataParallelStep(b)
+    t0 = a.states[0].master_t.clone()
     for _ in range(2):
         a.step()
         dp.step()
     torch.cuda.synchronize()
     torch.testing.assert_close(b.loss, a.loss, rtol=1e-6, atol=0)
-    assert torch.linalg.norm(b.states[0].master_t - a.states[0].master_t) <= \
-        1e-6 * torch.linalg.norm(a.states[0].master_t)
+    # the updates agree normwise: an Adam update is about lr sign(g), and
+    # components whose g lies within the atomics' FP32 rounding of 0 may flip
+    ua, ub = a.states[0].master_t - t0, b.states[0].master_t - t0
+    assert torch.linalg.norm(ub - ua) <= 1e-3 * torch.linalg.norm(ua)
     with pytest.raises(ValueError):
         D.DataParallelStep(a)                     # no norm_pairs: not a shard step
