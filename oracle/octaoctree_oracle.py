@@ -24,6 +24,9 @@ fusion or reordering of its own:
   hash_encode, disparity  the predictor g_psi of Eq. 7 (Section 3.5): a
                     multiresolution hash encoding of x (Mueller et al. 2022)
                     and a bias-free ReLU MLP on [encoding, omega_r], exp out
+  shifted_features_d_gradient, disparity_backward  training g_psi: the
+                    features' derivative with respect to d and g_psi's
+                    gradients
   mlp_forward       Eq. 13 (decoder; ReLU hidden layers, exp output)
   residual_loss     Eq. 14 with the Monte-Carlo target of Eq. 3 (M = 1)
   residual_loss_multi  Eq. 14 with Eq. 3's M-sample target
@@ -1005,3 +1008,118 @@ def disparity(table, res, weights, x, omega, normal):
     inp = np.concatenate([hash_encode(table, res, x), om_r], axis=1)
     out, _, _ = mlp_forward(weights, inp)
     return out[:, 0]
+
+
+# ---------------------------------------------------------------------------
+# Training g_psi through the shifted lookup (Eq. 7-9): the derivative of the
+# features with respect to the disparity, and g_psi's backward
+# ---------------------------------------------------------------------------
+
+def _fold_jacobian(v):
+    """d(u_x, u_y)/dv of the octahedral map of Eq. 4/5 at v [N][3] (FP64,
+    the branch chosen by the sign of v_z as the binary32 fold chooses it):
+    upper, u = (v_x, v_y) / s with s = |v_x| + |v_y| + |v_z|, so
+    du_x/dv = (e_x - u_x sgn(v)) / s; lower, u = ((1 - |b|) sgn(a),
+    (1 - |a|) sgn(b)) of the upper (a, b), so du_x/dv = -sgn(a) sgn(b) db/dv
+    and du_y/dv = -sgn(a) sgn(b) da/dv.  Returns [N][2][3]."""
+    v = np.asarray(v, dtype=np.float64)
+    s = np.abs(v).sum(axis=1)
+    sg = np.where(v >= 0, 1.0, -1.0)
+    a = v[:, 0] / s
+    b = v[:, 1] / s
+    da = (np.array([1.0, 0, 0])[None, :] - a[:, None] * sg) / s[:, None]
+    db = (np.array([0, 1.0, 0])[None, :] - b[:, None] * sg) / s[:, None]
+    sa = np.where(a >= 0, 1.0, -1.0)
+    sb = np.where(b >= 0, 1.0, -1.0)
+    lower = (v[:, 2] < 0)[:, None]
+    dux = np.where(lower, -(sa * sb)[:, None] * db, da)
+    duy = np.where(lower, -(sa * sb)[:, None] * da, db)
+    return np.stack([dux, duy], axis=1)
+
+
+def _barycentric_gradient(i0, j0, fx32, fy32, N):
+    """d b_k / d(f_x, f_y) of vertex_triangle's weights: constant per
+    triangle.  Returns [N][3][2]."""
+    f = np.float32
+    anti = (i0 >= N // 2) == (j0 >= N // 2)
+    a_lower = (fx32 + fy32) <= f(1.0)
+    m_lower = fy32 <= fx32
+    g = np.zeros((len(i0), 3, 2))
+    g[anti & a_lower] = [[-1, -1], [1, 0], [0, 1]]
+    g[anti & ~a_lower] = [[1, 1], [0, -1], [-1, 0]]
+    g[~anti & m_lower] = [[-1, 0], [1, -1], [0, 1]]
+    g[~anti & ~m_lower] = [[0, -1], [-1, 1], [1, 0]]
+    return g
+
+
+def shifted_features_d_gradient(tree, tables, x, omega, normal, disparity):
+    """dh/dd [N][K F] of encode_features_shifted: per level and cell j,
+    sum_k wn_j (db_jk/dd) t_jk with db/dd = db/df (N/2) du/dv (x - c_j), the
+    triangle and cells as the binary32 lookup decides them."""
+    T = np.asarray(tables, dtype=np.float64)
+    F = T.shape[1]
+    n = len(x)
+    K = tree.num_levels
+    om_r = reflect_f32(omega, normal)
+    x32 = np.clip(np.asarray(x, dtype=np.float32), np.float32(0), np.float32(1))
+    enc = encode_features_shifted(tree, tables, x, omega, normal, disparity)
+    out = np.zeros((n, K * F))
+    for l in range(K):
+        V = int(tree.R[l])
+        N = V - 1
+        cells, _, _ = neighbour_cells(x, l)
+        for j in range(8):
+            v = shifted_direction_f32(x, om_r, disparity, cells[:, j], l)
+            i0, j0, fx32, fy32 = vertex_cell_f32(v, V)
+            gb = _barycentric_gradient(i0, j0, fx32, fy32, N)          # [n][3][2]
+            J = _fold_jacobian(v) * (N / 2.0)                          # d(px, py)/dv
+            c = (cells[:, j] + 0.5) / 2.0 ** l
+            dv = x32.astype(np.float64) - c                            # dv/dd
+            dp = np.einsum("nab,nb->na", J, dv)                        # d(px, py)/dd
+            dbk = np.einsum("nka,na->nk", gb, dp)                      # [n][3]
+            # the cell's renormalised weight wn_j: its entries' weights
+            # wn_j b_k summed over the triangle's vertices (sum_k b_k = 1)
+            wcell = enc.weight[:, l, j, :].sum(axis=1)
+            for k in range(3):
+                a = enc.addr[:, l, j, k]
+                ok = a >= 0
+                out[ok, l * F:(l + 1) * F] += (wcell[ok] * dbk[ok, k])[:, None] * T[a[ok]]
+    return out
+
+
+def disparity_backward(table, res, weights, x, omega, normal, d_disp):
+    """Gradients of sum_q d_disp[q] d_q (d = g_psi(x, omega_r)) with respect
+    to the hash tables [L][T][2] and the MLP weights: dz = d_disp d (exp),
+    the bias-free ReLU MLP's backward, and each level's feature gradient
+    scattered to its cell's 8 vertices with the trilinear weights."""
+    tab = np.asarray(table, dtype=np.float64)
+    L, T, Fh = tab.shape
+    om_r = reflect_f32(omega, normal).astype(np.float64)
+    inp = np.concatenate([hash_encode(table, res, x), om_r], axis=1)
+    out, zs, inputs = mlp_forward(weights, inp)
+    Ws = [np.asarray(W, dtype=np.float64) for W in weights]
+    delta = np.asarray(d_disp, dtype=np.float64)[:, None] * out
+    dWs = [None] * len(Ws)
+    for i in range(len(Ws) - 1, -1, -1):
+        dWs[i] = delta.T @ inputs[i]
+        g = delta @ Ws[i]
+        if i > 0:
+            delta = g * (zs[i - 1] > 0)
+        else:
+            d_in = g
+    dtab = np.zeros_like(tab)
+    x32 = np.clip(np.asarray(x, dtype=np.float32), np.float32(0), np.float32(1))
+    for l in range(L):
+        N = int(res[l])
+        p = x32 * np.float32(N)
+        i0 = np.minimum(np.floor(p), np.float32(N - 1)).astype(np.int64)
+        f = p.astype(np.float64) - i0
+        for c in range(8):
+            dd = np.array([c & 1, (c >> 1) & 1, c >> 2])
+            idx = hash_index(i0[:, 0] + dd[0], i0[:, 1] + dd[1], i0[:, 2] + dd[2], N, T)
+            w = np.ones(len(x32))
+            for a in range(3):
+                w *= f[:, a] if dd[a] else 1.0 - f[:, a]
+            for k in range(Fh):
+                dtab[l, :, k] += np.bincount(idx, weights=w * d_in[:, l * Fh + k], minlength=T)
+    return dtab, dWs

@@ -102,3 +102,64 @@ def test_decoder_attributes():
     rgb, _ = O.query_forward(ot, np.zeros_like(tables), [W1, np.eye(2), W3], x, w, attrs=attrs)
     np.testing.assert_allclose(rgb[:, 0], np.exp(attrs[:, 0]), rtol=1e-15)
     np.testing.assert_array_equal(rgb[:, 1:], 1.0)
+
+
+def test_shifted_features_derivative_in_d():
+    """dh/dd of the shifted lookup against central differences in d (step
+    1e-3 d, queries whose binary32 decisions change across the step left
+    out; the binary32 fractions bound the differences' accuracy to ~1e-3)."""
+    ot = O.build_tree(81, 3, 0.8, [17, 9, 9, 5])
+    tables = I.make_tables(82, ot.num_texels, 4, 0.5)
+    g = I.rng(83)
+    n = 300
+    x = g.random((n, 3)).astype(np.float32)
+    w = I.unit_vectors(g, n).astype(np.float32)
+    nrm = I.unit_vectors(g, n).astype(np.float32)
+    d = g.uniform(0.5, 4.0, n).astype(np.float32)
+    an = O.shifted_features_d_gradient(ot, tables, x, w, nrm, d)
+    dp = (d * np.float32(1.001)).astype(np.float32)
+    dm = (d * np.float32(0.999)).astype(np.float32)
+    ep = O.encode_features_shifted(ot, tables, x, w, nrm, dp)
+    em = O.encode_features_shifted(ot, tables, x, w, nrm, dm)
+    e0 = O.encode_features_shifted(ot, tables, x, w, nrm, d)
+    same = np.all((ep.addr == e0.addr) & (em.addr == e0.addr), axis=(1, 2, 3))
+    assert same.sum() > n // 3
+    fd = (ep.h - em.h) / (dp.astype(np.float64) - dm.astype(np.float64))[:, None]
+    a, f = an[same], fd[same]
+    assert np.linalg.norm(a - f) <= 3e-3 * np.linalg.norm(f)
+    assert np.linalg.norm(f) > 0
+
+
+def test_predictor_backward_by_central_differences():
+    """g_psi's table and weight gradients of sum_q c_q d_q against central
+    differences (FP64; the encoding is linear in the table)."""
+    table, res = None, [4, 9]
+    rng = np.random.default_rng(84)
+    table = rng.uniform(-0.3, 0.3, (2, 64, 2))
+    weights = [W.astype(np.float64) * 1.5 for W in I.make_mlp(85, [7, 16, 16, 1])]
+    g = I.rng(86)
+    n = 50
+    x = g.random((n, 3)).astype(np.float32)
+    w = I.unit_vectors(g, n).astype(np.float32)
+    nrm = I.unit_vectors(g, n).astype(np.float32)
+    c = rng.normal(size=n)
+
+    def f(tab, Ws):
+        return float(np.sum(c * O.disparity(tab, res, Ws, x, w, nrm)))
+    dtab, dWs = O.disparity_backward(table, res, weights, x, w, nrm, c)
+    h = 1e-6
+    touched = np.argwhere(np.abs(dtab) > 0)
+    for (l, e, k) in touched[rng.choice(len(touched), 12, replace=False)]:
+        P, Q = table.copy(), table.copy()
+        P[l, e, k] += h
+        Q[l, e, k] -= h
+        assert dtab[l, e, k] == pytest.approx((f(P, weights) - f(Q, weights)) / (2 * h), rel=1e-5,
+                                              abs=1e-9)
+    for i in range(3):
+        a, b = int(rng.integers(weights[i].shape[0])), int(rng.integers(weights[i].shape[1]))
+        P = [W.copy() for W in weights]
+        Q = [W.copy() for W in weights]
+        P[i][a, b] += h
+        Q[i][a, b] -= h
+        assert dWs[i][a, b] == pytest.approx((f(table, P) - f(table, Q)) / (2 * h), rel=1e-5,
+                                             abs=1e-9)
