@@ -146,6 +146,7 @@ class octa_step_options(C.Structure):
 
 
 OCTA_MAX_PRIMS = 64
+OCTA_MAX_ATTRS = 16
 OCTA_PRED_HIDDEN = 64
 OCTA_PRED_MAX_LEVELS = 16
 

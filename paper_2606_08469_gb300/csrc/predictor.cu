@@ -135,6 +135,8 @@ extern "C" int octa_disparity(const octa_predictor* pred, const octa_queries* q,
                 OCTA_PRED_MAX_LEVELS);
   if (pred->log2_T < 4 || pred->log2_T > 24)
     return fail(OCTA_ERANGE, "predictor log2_T %d outside [4, 24]", pred->log2_T);
+  if (pred->weights_bf16 && pred->levels > 14)
+    return fail(OCTA_ERANGE, "the tensor-core predictor takes at most 14 levels");
   if (!pred->table || !pred->weights) return fail(OCTA_EINVAL, "NULL predictor table or weights");
   if (reinterpret_cast<uintptr_t>(pred->table) & 7u)
     return fail(OCTA_EINVAL, "predictor table not 8-byte aligned");
@@ -143,8 +145,6 @@ extern "C" int octa_disparity(const octa_predictor* pred, const octa_queries* q,
   if (!q->x || !q->omega || !q->normal || !disparity)
     return fail(OCTA_EINVAL, "x, omega, normal and disparity must be non-NULL");
   if (pred->weights_bf16) {  // the MLP on the tensor cores
-    if (pred->levels > 14)
-      return fail(OCTA_ERANGE, "the tensor-core predictor takes at most 14 levels");
     for (int l = 0; l < pred->levels; ++l)
       if (pred->res[l] < 1 || pred->res[l] > 65535)
         return fail(OCTA_ERANGE, "predictor res[%d] = %d outside [1, 65535]", l, pred->res[l]);

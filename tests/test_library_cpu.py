@@ -128,3 +128,59 @@ def test_tuning_knobs_round_trip(lib):
     assert lib.octa_set_tuning(C.byref(bad)) == L.OCTA_EINVAL
     T.set_tuning(None)
     assert all(v == 0 for v in T.get_tuning().values())
+
+
+def test_training_regime_and_predictor_validation_without_gpu(lib):
+    """The tracer's, the M-sample loss's and the predictor's argument checks
+    run on the host before any launch (no device needed)."""
+    from paper_2606_08469_gb300 import _lib as L
+    # tracer: NULL scene, too many primitives, rays_per_origin < 1, t_min < 0
+    assert lib.octa_trace_rays(None, None, 1, None, 0, C.c_float(1e-4), None, None, None, None,
+                               None) == L.OCTA_EINVAL
+    pr = L.octa_prims()
+    pr.n_planes = L.OCTA_MAX_PRIMS + 1
+    assert lib.octa_trace_rays(C.byref(pr), None, 1, None, 0, C.c_float(1e-4), None, None, None,
+                               None, None) == L.OCTA_ERANGE
+    pr.n_planes = 0
+    assert lib.octa_trace_rays(C.byref(pr), None, 0, None, 0, C.c_float(1e-4), None, None, None,
+                               None, None) == L.OCTA_EINVAL
+    assert lib.octa_trace_rays(C.byref(pr), None, 1, None, 0, C.c_float(-1.0), None, None, None,
+                               None, None) == L.OCTA_EINVAL
+    assert lib.octa_trace_rays(C.byref(pr), None, 1, None, 0, C.c_float(1e-4), None, None, None,
+                               None, None) == L.OCTA_OK                     # empty batch
+    pr.n_spheres = 2                                                       # NULL sphere array
+    assert lib.octa_trace_rays(C.byref(pr), None, 1, None, 0, C.c_float(1e-4), None, None, None,
+                               None, None) == L.OCTA_EINVAL
+    # M-sample loss: no pairs, no samples, NULL arrays
+    assert lib.residual_loss_multi(None, None, None, None, 0, 4, C.c_float(0.01), 0, None, None,
+                                   None, None, None, 0, None) == L.OCTA_EINVAL
+    assert lib.residual_loss_multi(None, None, None, None, 10, 0, C.c_float(0.01), 0, None, None,
+                                   None, None, None, 0, None) == L.OCTA_EINVAL
+    assert lib.residual_loss_multi(None, None, None, None, 10, 4, C.c_float(0.01), 0, None, None,
+                                   None, None, None, 0, None) == L.OCTA_EINVAL
+    # predictor: levels, table size, NULL arrays, the tensor-core level limit
+    p = L.octa_predictor()
+    q = L.octa_queries()
+    q.n = 0
+    p.levels = 0
+    assert lib.octa_disparity(C.byref(p), C.byref(q), None, None) == L.OCTA_ERANGE
+    p.levels, p.log2_T = 2, 30
+    assert lib.octa_disparity(C.byref(p), C.byref(q), None, None) == L.OCTA_ERANGE
+    p.log2_T = 12
+    assert lib.octa_disparity(C.byref(p), C.byref(q), None, None) == L.OCTA_EINVAL
+    p.table = p.weights = 64                     # never dereferenced: n = 0
+    assert lib.octa_disparity(C.byref(p), C.byref(q), None, None) == L.OCTA_OK
+    p.levels, p.weights_bf16 = 15, 64
+    q.n = 5
+    assert lib.octa_disparity(C.byref(p), C.byref(q), None, None) == L.OCTA_ERANGE
+
+
+def test_query_attribute_and_form_validation_without_gpu(lib):
+    """Eq. 12's attribute count and the query forms are validated on the host."""
+    from paper_2606_08469_gb300 import _lib as L
+    q = L.octa_queries()
+    q.n = 0
+    q.n_attrs = L.OCTA_MAX_ATTRS + 1
+    s = L.octa_scene()
+    assert lib.octa_query_fwd(C.byref(s), 1, C.byref(q), None, None, None, None, None) == L.OCTA_ERANGE
+    assert b"n_attrs" in lib.octa_last_error()
