@@ -1,17 +1,21 @@
 """Benchmark of the OctaOctree training step (and forward) on GB300.
 
-Default workload: the FP32 training step of train_f32 -- a depth-6 octree
-(R = 32,32,16,16,8,8,8, F = 8 FP32 features), decoder 56-64-64-3, 262,144
-training pairs = 524,288 queries per step (a primary and a secondary query
-per pair): forward, Eq. 14 residual loss, backward with recompute and
-scatter-add, Adam with dynamic loss scaling.  Prints one JSON line.
+Default workload (the headline): the BF16 training step of train_bf16 -- a
+depth-8 octree (R = 64,64,32,32,16,16,8,8,8, F = 8 FP16 features), BF16
+decoder 72-64-64-64-3 on the tcgen05 tensor cores with FP32 accumulation,
+1,048,576 training pairs = 2,097,152 queries per step (a primary and a
+secondary query per pair): the fused pass (forward, Eq. 14 residual
+gradient, backward with recompute and scatter-add in one launch), then Adam
+with dynamic loss scaling.  The same inputs on the FP32 path, the error of
+the BF16 step against the FP64 oracle and the other workloads are extra keys
+of the one JSON line printed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun (N > 1) every rank runs an independent replica of the step on
 its own GPU (the step shards by independent pairs; weak scaling), timing is
 the max over ranks.  --impl reference times the FP64 CPU oracle on a bounded
-sample of the same workload on the host cores.
+sample of the same workload on all host cores.
 """
 from __future__ import annotations
 
@@ -104,22 +108,33 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU baseline: the oracle on a bounded sample (fresh single-threaded process)
+# CPU baseline: the FP64 oracle on a bounded sample of the headline workload
 # ---------------------------------------------------------------------------
 
-def oracle_step_rate(n_pairs, repeats=1):
-    """Mq/s of the FP64 oracle training step on n_pairs pairs of train_f32."""
+HEADLINE = "train_bf16"
+
+
+def _oracle_problem(cfg_name):
     import numpy as np
     from oracle import octaoctree_oracle as O
     from paper_2606_08469_gb300 import inputs as I
-    cfg = I.WORKLOADS["train_f32"]
+    cfg = I.WORKLOADS[cfg_name]
     tree = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
     tables = I.make_tables(cfg.seed("tables"), tree.num_texels, cfg.F, cfg.sigma)
     W = I.make_mlp(cfg.seed("mlp"), cfg.widths)
+    return cfg, tree, tables.astype(np.float64), [w.astype(np.float64) for w in W]
+
+
+def oracle_step_rate(n_pairs, repeats=1, cfg_name=HEADLINE):
+    """Seconds per FP64 oracle training step (forward, Eq. 14, backward,
+    Adam with the loss scaler) on n_pairs pairs of the named workload."""
+    import numpy as np
+    from oracle import octaoctree_oracle as O
+    from paper_2606_08469_gb300 import inputs as I
+    cfg, tree, tables, W = _oracle_problem(cfg_name)
     pairs = I.training_pairs(cfg.seed("queries"), n_pairs)
-    st = O.TrainState(tables.astype(np.float64), [w.astype(np.float64) for w in W],
-                      np.zeros(tables.shape), np.zeros(tables.shape), [np.zeros(w.shape) for w in W],
-                      [np.zeros(w.shape) for w in W])
+    st = O.TrainState(tables, W, np.zeros(tables.shape), np.zeros(tables.shape),
+                      [np.zeros(w.shape) for w in W], [np.zeros(w.shape) for w in W])
     sc = O.LossScaler()
     times = []
     for _ in range(repeats):
@@ -129,20 +144,112 @@ def oracle_step_rate(n_pairs, repeats=1):
     return times
 
 
-def cpu_baseline(n_pairs=65536, repeats=2):
+_POOL_STATE = {}
+
+
+def _pool_init(cfg_name, n_pairs):
+    import os as _os
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        _os.environ[k] = "1"
+    from paper_2606_08469_gb300 import inputs as I
+    cfg, tree, tables, W = _oracle_problem(cfg_name)
+    _POOL_STATE.update(tree=tree, tables=tables, W=W,
+                       pairs=I.training_pairs(cfg.seed("queries"), n_pairs))
+
+
+def _pool_shard(bounds):
+    """Forward, Eq. 14 and backward of one pair shard (FP64 oracle); returns
+    the shard's sum of r^2 and its gradients' squared norm."""
+    import numpy as np
+    from oracle import octaoctree_oracle as O
+    b, e = bounds
+    P = _POOL_STATE["pairs"]
+    tree, T, W = _POOL_STATE["tree"], _POOL_STATE["tables"], _POOL_STATE["W"]
+    X = np.concatenate([P.x[b:e], P.x2[b:e]])
+    Om = np.concatenate([P.omega[b:e], -P.omega2[b:e]])
+    n = e - b
+    rgb, _ = O.query_forward(tree, T, W, X, Om)
+    loss, dLp, dLs = O.residual_loss(rgb[:n], rgb[n:], P.E[b:e], P.w[b:e])
+    gT, gW, _ = O.query_backward(tree, T, W, X, Om, np.concatenate([dLp, dLs]))
+    return loss * n, float(np.sum(gT ** 2) + sum(np.sum(g ** 2) for g in gW))
+
+
+class OraclePool:
+    """The FP64 oracle's training pass on all host cores: a process pool
+    (spawn start, so no worker inherits a CUDA context), one contiguous pair
+    shard per worker per step.  Each worker runs forward, Eq. 14 and backward
+    on its shard; the cross-worker gradient sum and Adam are not included."""
+
+    def __init__(self, n_pairs, cfg_name=HEADLINE, workers=None):
+        import multiprocessing as mp
+        self.workers = workers or os.cpu_count() or 1
+        self.n_pairs = n_pairs
+        self.pool = mp.get_context("spawn").Pool(self.workers, initializer=_pool_init,
+                                                 initargs=(cfg_name, n_pairs))
+        w = self.workers
+        self.shards = [(n_pairs * i // w, n_pairs * (i + 1) // w) for i in range(w)]
+
+    def step(self):
+        return self.pool.map(_pool_shard, self.shards, chunksize=1)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(n_single=16384, n_all_per_core=16384, repeats=2):
+    """The oracle timed on the host: one thread on a full training step
+    (fresh process, BLAS pinned to one thread) and all cores on the
+    training pass (OraclePool), both on seeded pairs of the headline
+    workload."""
+    import platform
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     out = subprocess.run([sys.executable, os.path.abspath(__file__), "--_oracle-sample",
-                          str(n_pairs), str(repeats)], env=env, capture_output=True, text=True,
+                          str(n_single), str(repeats)], env=env, capture_output=True, text=True,
                          timeout=900)
+    cores = os.cpu_count() or 1
+    host = f"{cores} x {_cpu_model()} ({platform.machine()})"
     if out.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": f"failed: {out.stderr.strip()[-200:]}"}
-    times = json.loads(out.stdout.strip().splitlines()[-1])
-    t = min(times)
-    return {"value": 2 * n_pairs / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle, one training step on {n_pairs} of the 262144 pairs "
-                      f"({2 * n_pairs} queries), best of {repeats}: {t:.2f} s, single thread"}
+    t1 = min(json.loads(out.stdout.strip().splitlines()[-1]))
+    single = 2 * n_single / t1 / 1e6
+    res = {"value": single, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"FP64 numpy oracle, one {HEADLINE} training step (fwd, Eq.14, bwd, Adam) on "
+                     f"{n_single} of its 1048576 pairs ({2 * n_single} queries), best of {repeats}: "
+                     f"{t1:.2f} s, single thread; host {host}"}
+    try:
+        n_all = n_all_per_core * cores
+        pool = OraclePool(n_all, workers=cores)
+        pool.step()                                   # warm-up (worker start, imports)
+        ts = []
+        for _ in range(repeats):
+            t0 = time.perf_counter()
+            pool.step()
+            ts.append(time.perf_counter() - t0)
+        pool.close()
+        ta = min(ts)
+        res["all_cores"] = {"value": 2 * n_all / ta / 1e6, "unit": UNIT, "cores": cores,
+                            "sample": f"{n_all} pairs ({2 * n_all} queries), {cores} spawned "
+                                      f"processes x {n_all_per_core} pairs, fwd + Eq.14 + bwd per "
+                                      f"shard (no cross-process gradient sum, no Adam), best of "
+                                      f"{repeats}: {ta:.2f} s"}
+    except Exception as e:  # the single-thread figure stands without it
+        res["all_cores"] = {"value": None, "sample": f"failed: {e!r}"[:200]}
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -164,21 +271,23 @@ def _timed(fn, n, flush, stream):
     return statistics.median(a.elapsed_time(b) for a, b in evs)
 
 
-def bf16_vs_f32_leg(dev, flush, stream, steps, peaks):
-    """train_bf16 training step (1,048,576 pairs, depth-8 tree, decoder
-    72-64-64-64-3): BF16 tensor-core path vs the FP32 path on the same shapes."""
+def bf16_vs_f32_leg(dev, flush, stream, steps, peaks, bf16_value):
+    """The headline workload (train_bf16: 1,048,576 pairs, depth-8 tree,
+    decoder 72-64-64-64-3) on the other paths, same inputs: the FP32 path
+    (FP32 tables and weights on the CUDA-core engine) unfused and fused, the
+    BF16 unfused path, and the BF16 one-launch step.  bf16_value: the
+    headline's Mq/s (the BF16 fused pass + Adam)."""
     from paper_2606_08469_gb300 import api
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
-    cfg = I.WORKLOADS["train_bf16"]
-    out = {"workload": "train_bf16 training step: depth-8 octree, R 64..8, F=8, decoder 72-64-64-64-3, "
-                       "1048576 pairs = 2097152 queries, dynamic loss scaling"}
-    W = cfg.widths
-    fwd_flop = 2 * sum(a * b for a, b in zip(W[:-1], W[1:]))
-    for prec in ("bf16", "bf16_unfused", "f32", "f32_fused"):
-        step, _ = WL.train_step_for(cfg, device=dev,
-                                    precision="f32" if prec.startswith("f32") else None,
-                                    fused=prec in ("bf16", "f32_fused"), persistent=False)
+    cfg = I.WORKLOADS[HEADLINE]
+    out = {"workload": f"{HEADLINE} training step: depth-8 octree, R 64..8, F=8, decoder "
+                       "72-64-64-64-3, 1048576 pairs = 2097152 queries, dynamic loss scaling",
+           "bf16": {"Mq/s": bf16_value, "path": "octa_train_fused (tensor cores) + adam_step "
+                                               "(the headline value)"}}
+    for prec in ("f32", "f32_fused", "bf16_unfused"):
+        step, _ = WL.train_step_for(cfg, device=dev, precision="f32" if prec.startswith("f32") else None,
+                                    fused=prec == "f32_fused")
         for _ in range(3):
             step.step()
         stream.synchronize()
@@ -187,20 +296,7 @@ def bf16_vs_f32_leg(dev, flush, stream, steps, peaks):
         sc = api.read_scaler(step.scaler)
         leg = {"Mq/s": round(nq / t_step / 1e3, 2), "ms_per_step": round(t_step, 4),
                "loss": float(step.loss.item()), "loss_scale": float(sc.scale)}
-        if prec == "bf16":
-            t_pass = _timed(step.fused_pass, steps, flush, stream)
-            peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
-            ach = 3 * fwd_flop * nq / (t_pass / 1e3) / 1e12
-            leg["fused_pass_ms"] = round(t_pass, 4)
-            leg["roofline_fused_pass"] = {"bound": "tensor", "achieved": round(ach, 2), "peak": peak,
-                                          "unit": "TFLOP/s", "frac": round(ach / peak, 5)}
-            leg["path"] = "octa_train_fused (forward + Eq.14 gradient + backward, one launch) + adam_step"
-            one, _ = WL.train_step_for(cfg, device=dev, persistent=True)
-            for _ in range(3):
-                one.step()
-            leg["one_launch_ms_per_step"] = round(_timed(one.step, steps, flush, stream), 4)
-            del one
-        elif prec == "f32_fused":
+        if prec == "f32_fused":
             leg["fused_pass_ms"] = round(_timed(step.fused_pass, steps, flush, stream), 4)
             leg["path"] = "octa_train_fused on the FP32 engine + adam_step"
         else:
@@ -211,9 +307,57 @@ def bf16_vs_f32_leg(dev, flush, stream, steps, peaks):
             leg["path"] = "octa_query_fwd + residual_loss + octa_query_bwd + adam_step"
         out[prec] = leg
         del step
-    out["speedup_bf16_over_f32"] = round(out["bf16"]["Mq/s"] / out["f32"]["Mq/s"], 3)
-    out["speedup_bf16_over_f32_fused"] = round(out["bf16"]["Mq/s"] / out["f32_fused"]["Mq/s"], 3)
+    one, _ = WL.train_step_for(cfg, device=dev, persistent=True)
+    for _ in range(3):
+        one.step()
+    t1 = _timed(one.step, steps, flush, stream)
+    out["bf16_one_launch"] = {"ms_per_step": round(t1, 4), "Mq/s": round(2 * cfg.n / t1 / 1e3, 2),
+                              "path": "octa_train_step_batched (fused pass + Adam, one launch)"}
+    del one
+    out["speedup_bf16_over_f32"] = round(bf16_value / out["f32"]["Mq/s"], 3)
+    out["speedup_bf16_over_f32_fused"] = round(bf16_value / out["f32_fused"]["Mq/s"], 3)
     return out
+
+
+def train_f32_leg(dev, flush, stream, steps, peaks):
+    """train_f32: the FP32 training step (depth-6 tree, R 32..8, F = 8 FP32,
+    decoder 56-64-64-3, 262,144 pairs = 524,288 queries): the FP32 engine's
+    fused pass + Adam, its roofline against the FP32 FFMA peak."""
+    from paper_2606_08469_gb300 import inputs as I
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.WORKLOADS["train_f32"]
+    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, device=dev, fused=True)
+    for _ in range(3):
+        step.step()
+    stream.synchronize()
+    t_step = _timed(step.step, steps, flush, stream)
+    t_pass = _timed(step.fused_pass, steps, flush, stream)
+    t_fwd = _timed(step.forward, steps, flush, stream)
+    nq = 2 * pairs.n
+    fwd_flop = _fwd_flop(cfg.widths)
+    achieved = 3 * fwd_flop * nq / (t_pass / 1e3) / 1e12
+    peak, peak_src = _f32_peak(peaks)
+    out = {"workload": f"train_f32 FP32 training step: depth-6 octree ({tree.num_nodes} nodes, R 32..8, "
+                       f"F=8 FP32), decoder 56-64-64-3, {pairs.n} pairs = {nq} queries, fused pass + Adam",
+           "Mq/s": round(nq / t_step / 1e3, 2), "ms_per_step": round(t_step, 4),
+           "fwd_only_Mq/s": round(nq / t_fwd / 1e3, 2),
+           "loss": float(step.loss.item()),
+           "roofline": {"bound": "alu", "kernel": "f32 engine fused training pass",
+                        "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                        "frac": round(achieved / peak, 4), "traffic": F32_PASS_DRAM_BYTES,
+                        "pass_ms": round(t_pass, 4), "peak_source": peak_src}}
+    del step
+    return out
+
+
+def _f32_peak(peaks):
+    """FP32 FFMA peak: the measured microbenchmark figure when one is on
+    record, else 152 SMs x 128 lanes x 2 flop at the maximum SM clock."""
+    if "f32_ffma_tflops" in peaks:
+        return float(peaks["f32_ffma_tflops"]), "measured FFMA microbenchmark"
+    clk = float(peaks.get("sm_max_mhz", 2070.0))
+    return SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12, \
+        f"152 SMs x 128 FP32 lanes x 2 flop x {clk:.0f} MHz (unit counts)"
 
 
 def inference_leg(dev, flush, stream, steps, peaks):
@@ -659,10 +803,10 @@ LEGS = ("bf16_vs_f32", "inference", "small_forward", "encode", "encode_full", "e
         "train_full", "multi_rhs", "full_inference", "batched")
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
-# launch (262,144 pairs) of the FP32 fused training pass, from one ncu
-# capture of the current kernel; to be re-taken (or set to None) whenever the
-# kernel changes.
-F32_PASS_DRAM_BYTES = 22944768 + 0
+# launch of each fused training pass, from one ncu capture of the current
+# kernel; None until taken, and reset to None whenever the kernel changes.
+F32_PASS_DRAM_BYTES = 22944768   # train_f32, 262,144 pairs, FP32 engine
+BF16_PASS_DRAM_BYTES = None      # train_bf16, 1,048,576 pairs, tcgen05 kernel
 
 
 def run_legs(args, names):
@@ -690,50 +834,22 @@ def run_legs(args, names):
     print(json.dumps({n: fns[n]() for n in names}), flush=True)
 
 
-def run_ours(args):
+def measure_step(step, nq, dev, stream, flush, args, barrier, pass_name="fused_pass"):
+    """Device time of K training steps (fused pass + Adam) after W warm-up
+    steps, L2 flushed before each step outside the events, the fused pass
+    timed inside each step by its own events; then the same K steps end to
+    end through the public API with every step's pair inputs copied in from
+    pinned host memory (double-buffered on a copy stream) and the loss read
+    back.  Returns (step ms list, pass ms list, e2e ms, h2d bytes, clocks)."""
     import torch
-    import torch.distributed as dist
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
-    from paper_2606_08469_gb300 import build
-    build.build()
-    from paper_2606_08469_gb300 import api
-    from paper_2606_08469_gb300 import inputs as I
-    from paper_2606_08469_gb300 import workloads as WL
-
-    cfg = I.WORKLOADS["train_f32"]
-    # the FP32 training step: the engine's fused pass (forward, Eq. 14
-    # gradient, backward in one launch) and Adam with the loss scaler
-    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=args.pairs, device=dev,
-                                                             fused=True)
-    n_q = 2 * pairs.n
-    stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-
     for _ in range(args.warmup):
         step.step()
     barrier()
-
-    # device-resident timed region: per step, flush L2 (outside the events),
-    # then time the whole step and, inside it, the fused training pass
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(args.steps)]
     try:
         smi_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
-        smi_id = str(local)
+        smi_id = str(dev.index or 0)
     with ClockSampler(smi_id) as clocks:
         barrier()
         for k in range(args.steps):
@@ -741,37 +857,18 @@ def run_ours(args):
             a, b, c, d = ev[k]
             a.record(stream)
             c.record(stream)
-            step.fused_pass()
+            getattr(step, pass_name)()
             d.record(stream)
             step.optimizer()
             b.record(stream)
         barrier()
     step_ms = [e[0].elapsed_time(e[1]) for e in ev]
-    bwd_ms = [e[2].elapsed_time(e[3]) for e in ev]
-    total_ms = max_over_ranks(sum(step_ms), dev)
-    launches = 3 * args.steps  # fused pass, adam norm, adam update
+    pass_ms = [e[2].elapsed_time(e[3]) for e in ev]
 
-    # forward-only rate (same queries), L2 flushed between launches
-    fwd_ms = []
-    for _ in range(max(3, args.steps)):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step.forward()
-        b.record(stream)
-        fwd_ms.append((a, b))
-    torch.cuda.synchronize(dev)
-    fwd_ms = [a.elapsed_time(b) for a, b in fwd_ms]
-    fwd_mean = max_over_ranks(statistics.mean(fwd_ms), dev)
-
-    # end to end through the public API: every step's pair inputs copied in
-    # from pinned host memory and the loss read back; the copies of step k+1
-    # run on a second stream into the other of two input buffers while step
-    # k computes (events order each buffer's reuse)
     dev_in = step.pair_inputs()
     host = {k: t.cpu().pin_memory() for k, t in dev_in.items()}
     bufs = [dev_in, {k: torch.empty_like(t) for k, t in dev_in.items()}]
-    loss_host = torch.empty(1, dtype=torch.float64).pin_memory()
+    loss_host = torch.empty(step.loss.numel(), dtype=torch.float64).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in host.values())
     copy_stream = torch.cuda.Stream(dev)
     ready = [torch.cuda.Event(), torch.cuda.Event()]
@@ -803,21 +900,124 @@ def run_ours(args):
     e1.record(stream)
     barrier()
     step.set_pair_inputs(dev_in)
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dev)
+    return step_ms, pass_ms, e0.elapsed_time(e1), h2d, 8 * step.loss.numel(), clocks.summary()
+
+
+def _fwd_flop(widths):
+    return 2 * sum(a * b for a, b in zip(widths[:-1], widths[1:]))
+
+
+def headline_error(dev, n_pairs=65536, n_sample=32768):
+    """Error of the headline BF16 step against the FP64 oracle: radiance on a
+    seeded sample of the full batch's queries (normwise, against the FP32
+    masters: the binding end-to-end figure; and against the quantised FP16 /
+    BF16 parameters: the arithmetic alone), and the loss and every gradient
+    tensor of a fused pass over n_pairs seeded pairs of the same workload."""
+    import numpy as np
+    import torch
+    from oracle import octaoctree_oracle as O
+    from paper_2606_08469_gb300 import inputs as I
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.WORKLOADS[HEADLINE]
+    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=n_pairs, device=dev,
+                                                             fused=True)
+    step.fused_pass()
+    step.forward()
+    torch.cuda.synchronize(dev)
+    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    tq = tables.astype(np.float16).astype(np.float64)
+    wq = [torch.from_numpy(w).to(torch.bfloat16).double().numpy() for w in weights]
+    N = pairs.n
+    X = np.concatenate([pairs.x, pairs.x2])
+    Om = np.concatenate([pairs.omega, -pairs.omega2])
+    idx = np.sort(np.random.default_rng(11).choice(2 * N, min(n_sample, 2 * N), replace=False))
+    rgb = step.rgb.cpu().numpy()[idx]
+    nw = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    ref, _ = O.query_forward(ot, tables, weights, X[idx], Om[idx])
+    refq, _ = O.query_forward(ot, tq, wq, X[idx], Om[idx])
+    from paper_2606_08469_gb300 import api
+    S = float(api.read_scaler(step.scaler).scale)
+    gT = step.states[0].grad_t.cpu().numpy() / S
+    gW = step.states[0].grad_w.cpu().numpy() / S
+    out = {"radiance_vs_fp64_masters": round(nw(rgb, ref), 6),
+           "radiance_vs_fp64_quantised": round(nw(rgb, refq), 6),
+           "radiance_sample": f"{len(idx)} seeded queries of a {N}-pair batch"}
+    for name, (T_, W_) in (("quantised", (tq, wq)), ("masters", (tables, weights))):
+        rgb_o, _ = O.query_forward(ot, T_, W_, X, Om)
+        loss, dLp, dLs = O.residual_loss(rgb_o[:N], rgb_o[N:], pairs.E, pairs.w)
+        rT, rWs, _ = O.query_backward(ot, T_, W_, X, Om, np.concatenate([dLp, dLs]))
+        errs = [nw(gT, rT)]
+        off = 0
+        for rW in rWs:
+            errs.append(nw(gW[off:off + rW.size].reshape(rW.shape), rW))
+            off += rW.size
+        out[f"gradients_vs_fp64_{name}"] = {"tables": round(errs[0], 6),
+                                            "weights": [round(e, 6) for e in errs[1:]]}
+        out[f"loss_rel_vs_fp64_{name}"] = round(abs(step.loss.item() - loss) / loss, 8)
+    out["gradient_batch"] = f"fused pass over {N} seeded pairs of {HEADLINE}, loss scale 2^15"
+    out["bound"] = ("radiance <= 1e-2 normwise vs the FP32 masters; gradients: last layer <= 1e-2, "
+                    "ReLU-masked tensors within 3 sqrt(f) + 1e-2, f the fraction of pre-activations "
+                    "within the BF16 forward error of zero")
+    del step
+    return out
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2606_08469_gb300 import build
+    build.build()
+    from paper_2606_08469_gb300 import api
+    from paper_2606_08469_gb300 import inputs as I
+    from paper_2606_08469_gb300 import workloads as WL
+
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    cfg = I.WORKLOADS[HEADLINE]
+    # the BF16 training step: the tensor-core fused pass (forward, Eq. 14
+    # gradient, backward, scatter in one launch) and Adam with the loss scaler
+    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=args.pairs, device=dev,
+                                                             fused=True)
+    n_q = 2 * pairs.n
+    step_ms, pass_ms, e2e_ms, h2d, d2h, clocks = measure_step(step, n_q, dev, stream, flush, args,
+                                                             barrier)
+    total_ms = max_over_ranks(sum(step_ms), dev)
+    e2e_ms = max_over_ranks(e2e_ms, dev)
+    launches = 3 * args.steps  # fused pass, adam norm, adam update
+
+    # forward-only rate of the same queries (tensor-core forward), L2 flushed
+    fwd = []
+    for _ in range(max(3, args.steps)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step.forward()
+        b.record(stream)
+        fwd.append((a, b))
+    torch.cuda.synchronize(dev)
+    fwd_mean = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in fwd), dev)
 
     if rank == 0:
         peaks, src = _peaks()
         sc = api.read_scaler(step.scaler)
-        # dominant kernel: the FP32 fused training pass (forward + backward of
-        # every query), bound by FP32 FFMA issue; algorithmic flops at the
-        # real widths
-        W = cfg.widths
-        fwd_flop = 2 * sum(a * b for a, b in zip(W[:-1], W[1:]))
-        bwd_flop = 3 * fwd_flop
-        bwd_s = statistics.mean(bwd_ms) / 1e3
-        achieved = bwd_flop * n_q / bwd_s / 1e12
-        clk = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+        fwd_flop = _fwd_flop(cfg.widths)
+        pass_s = statistics.mean(pass_ms) / 1e3
+        achieved = 3 * fwd_flop * n_q / pass_s / 1e12
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
         out = {
             "metric": METRIC,
             "value": round(job_rate(n_q, world, args.steps, total_ms), 3),
@@ -829,44 +1029,50 @@ def run_ours(args):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32",
+            "dtype": "bf16",
             "data": "synthetic (seeded octree, features, MLP, surface samples; no scene assets)",
-            "config": {"workload": "train_f32 FP32 training step: depth-6 seeded octree "
-                                   f"({tree.num_nodes} nodes, R 32..8, F=8 FP32), decoder 56-64-64-3, "
+            "config": {"workload": f"{HEADLINE} BF16 training step: depth-8 seeded octree "
+                                   f"({tree.num_nodes} nodes, R 64..8, F=8 FP16 features), BF16 "
+                                   "decoder 72-64-64-64-3 on the tensor cores (FP32 accumulation), "
                                    f"{pairs.n} pairs = {n_q} queries per step (fused fwd + Eq.14 "
-                                   "gradient + bwd, then Adam)",
+                                   "gradient + bwd + scatter, then Adam with dynamic loss scaling)",
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": f"replicas x{world}"},
             "fwd_only": {"value": round(job_rate(n_q, world, 1, fwd_mean), 3),
                          "unit": UNIT, "ms": round(fwd_mean, 4)},
             "loss": float(step.loss.item()),
             "grad_norm": float(sc.grad_norm),
-            "roofline": {"bound": "alu", "kernel": "f32 engine fused training pass "
-                                                   "(fwd + Eq.14 gradient + bwd + scatter)",
-                         "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+            "roofline": {"bound": "tensor", "kernel": "tcgen05 fused training pass (fwd + Eq.14 "
+                                                      "gradient + bwd + scatter)",
+                         "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
                          "frac": round(achieved / peak, 4),
-                         "traffic": F32_PASS_DRAM_BYTES if args.pairs == 262144 else None,
-                         "algorithmic_bytes": 72 * pairs.n + tables.size * 4 + sum(w.size for w in weights) * 4,
-                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {clk:.0f} MHz "
-                                        f"({src} sm_max_mhz)",
-                         "pass_ms": round(statistics.mean(bwd_ms), 4)},
+                         "traffic": BF16_PASS_DRAM_BYTES if args.pairs == cfg.n else None,
+                         "algorithmic_flop": 3 * fwd_flop * n_q,
+                         "per_query": f"3 x {fwd_flop} flop (forward, and the backward's two "
+                                      "GEMMs per layer) at the real widths",
+                         "peak_source": f"{src} bf16_tflops_sustained (cuBLAS, seconds-long loop)",
+                         "pass_ms": round(statistics.mean(pass_ms), 4)},
             "e2e": {"value": round(job_rate(n_q, world, args.steps, e2e_ms), 3), "unit": UNIT,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
-            "clocks": clocks.summary(),
+            "clocks": clocks,
         }
+        del step
+        extra_steps = max(5, args.steps // 2)
         if not args.no_extra:
-            out["bf16_vs_f32"] = bf16_vs_f32_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
-            out["inference"] = inference_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
-            out["small_forward"] = small_forward_leg(dev, flush, stream, max(5, args.steps // 2))
-            out["encode"] = encode_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
-            out["encode_full"] = encode_full_leg(dev, flush, stream, max(5, args.steps // 2), peaks)
-            out["encode_stress"] = encode_stress_leg(dev, flush, stream, max(5, args.steps // 2),
-                                                     peaks)
-            out["train_full"] = train_full_leg(dev, flush, stream, max(5, args.steps // 2))
-            out["multi_rhs"] = multi_rhs_leg(dev, flush, stream, max(5, args.steps // 2))
-            out["full_inference"] = full_inference_leg(dev, flush, stream, max(5, args.steps // 2))
-            out["batched"] = batched_leg(dev, flush, stream, max(5, args.steps // 2))
+            out["bf16_vs_f32"] = bf16_vs_f32_leg(dev, flush, stream, extra_steps, peaks,
+                                                 out["value"])
+            out["error_vs_fp64"] = headline_error(dev)
+            out["train_f32"] = train_f32_leg(dev, flush, stream, extra_steps, peaks)
+            out["inference"] = inference_leg(dev, flush, stream, extra_steps, peaks)
+            out["small_forward"] = small_forward_leg(dev, flush, stream, extra_steps)
+            out["encode"] = encode_leg(dev, flush, stream, extra_steps, peaks)
+            out["encode_full"] = encode_full_leg(dev, flush, stream, extra_steps, peaks)
+            out["encode_stress"] = encode_stress_leg(dev, flush, stream, extra_steps, peaks)
+            out["train_full"] = train_full_leg(dev, flush, stream, extra_steps)
+            out["multi_rhs"] = multi_rhs_leg(dev, flush, stream, extra_steps)
+            out["full_inference"] = full_inference_leg(dev, flush, stream, extra_steps)
+            out["batched"] = batched_leg(dev, flush, stream, extra_steps)
         out["cpu_baseline"] = cpu_baseline() if not args.no_cpu else None
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -875,23 +1081,36 @@ def run_ours(args):
 
 
 def run_reference(args):
+    """The oracle as the reference arm: every step is the FP64 training pass
+    (forward, Eq. 14, backward) of a bounded sample of the headline workload's
+    pairs, sharded over all host cores (OraclePool)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n_pairs = 8192
-    times = oracle_step_rate(n_pairs, repeats=args.warmup + args.steps)
+    cores = os.cpu_count() or 1
+    per_core = 16384       # the oracle's scatter has a fixed cost per call: large shards
+    n_pairs = per_core * cores
+    pool = OraclePool(n_pairs, workers=cores)
+    pool.step()                                       # worker start-up and imports
+    times = []
+    for _ in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        pool.step()
+        times.append(time.perf_counter() - t0)
+    pool.close()
     t = sum(times[args.warmup:])
     v = 2 * n_pairs * args.steps / t / 1e6
-    cores = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
+    sample = (f"{n_pairs} pairs ({2 * n_pairs} queries) of {HEADLINE} per step, {cores} spawned "
+              f"processes x {per_core} pairs: FP64 fwd + Eq.14 + bwd per shard (no cross-process "
+              f"gradient sum, no Adam); host {cores} x {_cpu_model()}")
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT,
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(1e3 * t / args.steps, 2), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "train_f32 training step, FP64 oracle on a bounded sample of "
-                                  f"{n_pairs} of the 262144 pairs per step"},
+           "config": {"workload": f"{HEADLINE} training pass, FP64 oracle on a bounded sample"},
            "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"{n_pairs} pairs ({2 * n_pairs} queries) per step"},
+                            "sample": sample},
            "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -909,7 +1128,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the BF16-vs-FP32 and inference legs (profiling captures)")
-    ap.add_argument("--pairs", type=int, default=262144,
+    ap.add_argument("--pairs", type=int, default=1048576,
                     help="training pairs per step (smaller values only for profiling captures)")
     ap.add_argument("--only", default=None,
                     help="comma-separated extra legs to run alone, without the headline "

@@ -253,7 +253,9 @@ int residual_loss(const float* L_p, const float* L_s, const float* E, const floa
  * the process exits.  The call allocates nothing and calls no allocating
  * routine.  Limits: n_pairs <= 2,796,202 (the partial slots of the fixed
  * array); larger batches return OCTA_ERANGE with a message -- use
- * residual_loss with a workspace for them.  The first call on a device looks
+ * residual_loss with a workspace for them.  The current device's index must
+ * be below 64 (the library keeps the array's address for devices 0..63);
+ * a higher index returns OCTA_ERANGE.  The first call on a device looks
  * the array's device address up (cudaGetSymbolAddress) for that device, so
  * make that first call before any stream capture.  Every call shares the one
  * array: each call clears its counter on `stream` before the kernel, and
@@ -431,8 +433,9 @@ typedef struct octa_step_options {
  * alias the grad buffers of the groups that hold scene s's parameters and
  * start zeroed (every step leaves them zeroed).  Every barrier wait is
  * bounded; on timeout OCTA_STATUS_TIMEOUT is set in *status and the step is
- * incomplete.  Workspace: octa_workspace_bytes(OCTA_OP_STEP, 0), zero-filled
- * before its first use.  BF16 decoders only.                              */
+ * incomplete; the call clears the barrier words of the workspace on `stream`
+ * before its launch, so the next call starts from a consistent state.
+ * Workspace: octa_workspace_bytes(OCTA_OP_STEP, 0).  BF16 decoders only.  */
 int octa_train_step_batched(const octa_scene* scenes, int32_t n_scenes, const octa_pairs* pairs,
                             const octa_scene_grads* grads, const octa_param_group* groups,
                             int32_t n_groups, float eps, int32_t rhs_grad,

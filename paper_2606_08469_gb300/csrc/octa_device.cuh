@@ -292,12 +292,15 @@ __device__ __forceinline__ const int2* stage_tree(const QueryParams& p, const De
   return tree_sm;
 }
 
-// Map base of a level-l node, or -1 (reported) when its R x R map runs past
-// the table (32-bit unsigned arithmetic: num_texels < 2^31 and R <= 4096, so
-// a negative base wraps to a value beyond any table and fails the test).
+// Map base of a level-l node, or -1 (reported) when its R x R map starts
+// before the table or runs past its end.  mo < 0 is rejected on its own: in
+// 32-bit unsigned arithmetic a base in [-R^2, -1] would wrap the sum back
+// into range.  With 0 <= mo < 2^31, R <= 4096 and num_texels < 2^31 the
+// unsigned sum cannot wrap.
 __device__ __forceinline__ int checked_map_base(const QueryParams& p, const DevScene& sc, int mo,
                                                 int R) {
-  if (static_cast<uint32_t>(mo) + static_cast<uint32_t>(R * R) > static_cast<uint32_t>(sc.num_texels)) {
+  if (mo < 0 ||
+      static_cast<uint32_t>(mo) + static_cast<uint32_t>(R * R) > static_cast<uint32_t>(sc.num_texels)) {
     if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_MAP);
     return -1;
   }

@@ -491,6 +491,11 @@ extern "C" int octa_train_step_batched(const octa_scene* scenes, int32_t n_scene
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(loss_dev, 0, sizeof(double) * n_scenes, st);
   if (e != cudaSuccess) return fail(OCTA_ECUDA, "clearing loss_dev: %s", cudaGetErrorString(e));
+  // the barrier's arrival counter and generation word start at zero on every
+  // call, so a step that timed out (arrivals left behind) does not make the
+  // next step's barriers miscount
+  e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return fail(OCTA_ECUDA, "clearing the barrier: %s", cudaGetErrorString(e));
   return tc::train_step_persistent(scenes, n_scenes, p, a, st);
 }
 

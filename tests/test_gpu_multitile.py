@@ -1,0 +1,224 @@
+"""Gradient parity at sizes where every persistent CTA runs several tiles.
+
+The training and backward kernels are persistent: a CTA (or, in the tensor-
+core kernels, each of its two 128-thread groups) processes tile after tile,
+keeping the decoder's weight gradient on chip across its tiles (FP32 engine:
+registers with the per-tile even/odd fold; tensor-core kernels: dW^T
+accumulators in tensor memory, flushed when the scene changes and at the
+end) and prefetching the next tile's inputs.  The tests here run every such
+kernel at batch sizes of at least three tiles per resident tile slot (152
+SMs; one FP32 CTA or two tensor-core groups per SM) and compare the table and
+decoder gradients, before Adam, with the FP64 oracle's query_backward of the
+Eq. 14 loss (one-sample target of Eq. 3), normwise per tensor.
+
+Bounds: FP32 1e-5 normwise per tensor.  BF16 (quantised parameters, i.e.
+the arithmetic alone): the last layer's dW at 1e-2 (no ReLU mask), every
+other tensor at 3 sqrt(f) + 1e-2 with f the oracle's fraction of hidden
+pre-activations within the BF16 forward error of zero (a mask there may flip,
+changing one delta element by 100%)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import octaoctree_oracle as O
+from paper_2606_08469_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+SMS = 152
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2606_08469_gb300 import build
+    build.build()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def normwise(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def bf16_round(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy()
+
+
+def quantised(tables, weights):
+    """The parameters as the BF16 path reads them, widened exactly to FP64."""
+    return (tables.astype(np.float16).astype(np.float64),
+            [bf16_round(W).astype(np.float64) for W in weights])
+
+
+def ambiguous_fraction(weights, h):
+    """Fraction of hidden pre-activations z with |z| below the BF16 forward
+    error bound 2^-7 sum |w||a| of that element."""
+    a = np.asarray(h, np.float64)
+    flags = []
+    for W in weights[:-1]:
+        W = np.asarray(W, np.float64)
+        z = a @ W.T
+        flags.append((np.abs(z) < 2.0 ** -7 * (np.abs(a) @ np.abs(W).T)).ravel())
+        a = np.maximum(z, 0.0)
+    return float(np.mean(np.concatenate(flags)))
+
+
+def oracle_pair_grads(ot, tables, weights, pairs, rhs_grad=True):
+    """Loss, table gradient and per-layer weight gradients of the Eq. 14 loss
+    of a pair batch (FP64 oracle), and the features of its queries."""
+    N = pairs.n
+    X = np.concatenate([pairs.x, pairs.x2])
+    Om = np.concatenate([pairs.omega, -pairs.omega2])
+    rgb, enc = O.query_forward(ot, tables, weights, X, Om)
+    loss, dLp, dLs = O.residual_loss(rgb[:N], rgb[N:], pairs.E, pairs.w, rhs_grad=rhs_grad)
+    rT, rWs, _ = O.query_backward(ot, tables, weights, X, Om, np.concatenate([dLp, dLs]))
+    return loss, rT, rWs, enc.h
+
+
+def tensor_errors(gT, gW, rT, rWs):
+    errs = [normwise(gT, rT)]
+    off = 0
+    for rW in rWs:
+        errs.append(normwise(gW[off:off + rW.size].reshape(rW.shape), rW))
+        off += rW.size
+    return errs
+
+
+def assert_bf16_errors(errs, frac, what):
+    bound = 3.0 * np.sqrt(frac) + 1e-2
+    print(what, "ambiguous-mask fraction", round(frac, 5), "errors", [round(e, 5) for e in errs],
+          "bound", round(bound, 4))
+    assert errs[-1] <= 1e-2, errs
+    assert max(errs) <= bound, (errs, bound)
+
+
+def test_f32_fused_pass_full_config1_gradients():
+    """The headline FP32 pass (train_f32: 262,144 pairs, 4,096 64-pair tiles,
+    about 27 tiles per CTA) at its full size: loss and every gradient tensor
+    before Adam against the FP64 oracle at 1e-5."""
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.WORKLOADS["train_f32"]
+    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, fused=True)
+    assert pairs.n == 262144 and pairs.n // 64 >= 3 * SMS
+    step.fused_pass()
+    torch.cuda.synchronize()
+    S = 2.0 ** 15
+    gT = step.states[0].grad_t.cpu().numpy() / S
+    gW = step.states[0].grad_w.cpu().numpy() / S
+    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    loss, rT, rWs, _ = oracle_pair_grads(ot, tables, weights, pairs)
+    assert abs(step.loss.item() - loss) <= 1e-5 * loss
+    errs = tensor_errors(gT, gW, rT, rWs)
+    print("train_f32 full-size fused gradients vs FP64", [f"{e:.2e}" for e in errs])
+    assert max(errs) <= 1e-5, errs
+
+
+def test_f32_backward_multitile():
+    """octa_query_bwd on the FP32 engine (128-query tiles, one CTA per SM)
+    with 100,003 queries: 782 tiles, five or six per CTA, a ragged last one."""
+    from paper_2606_08469_gb300 import api as A
+    cfg = I.WORKLOADS["train_f32"]
+    tree = A.octree_build(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    tables = I.make_tables(cfg.seed("tables"), tree.num_texels, cfg.F, 0.3)
+    weights = [W * np.float32(1.5) for W in I.make_mlp(cfg.seed("mlp"), [56, 64, 64, 3])]
+    sc = A.Scene(tree, dev(tables), [dev(W) for W in weights], device=DEV)
+    x, w = I.uniform_queries(77, 100003)
+    assert len(x) // 128 >= 3 * SMS
+    d_rgb = np.random.default_rng(78).normal(size=(len(x), 3)).astype(np.float32)
+    dT = torch.zeros(sc.tables.shape, device=DEV)
+    dW = torch.zeros(sc.weights.shape, device=DEV)
+    A.octa_query_bwd(sc, dev(x), dev(w), dev(d_rgb), [(dT, dW)])
+    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    rT, rWs, _ = O.query_backward(ot, tables, weights, x, w, d_rgb)
+    errs = tensor_errors(dT.cpu().numpy(), dW.cpu().numpy(), rT, rWs)
+    print("FP32 backward, 782 tiles", [f"{e:.2e}" for e in errs])
+    assert max(errs) <= 1e-5, errs
+
+
+def test_bf16_fused_pass_config2_multitile():
+    """The train_bf16 fused pass (FP16 tables, BF16 72-64-64-64-3 decoder,
+    loss scale 2^15) on 262,144 of its pairs: 4,096 tiles on 304 group slots,
+    about 13 tiles per slot.  Gradients against the FP64 oracle on the
+    quantised parameters (arithmetic) and the loss on the FP32 masters."""
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.WORKLOADS["train_bf16"]
+    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=262144, fused=True)
+    assert pairs.n // 64 >= 3 * 2 * SMS
+    step.fused_pass()
+    torch.cuda.synchronize()
+    S = 2.0 ** 15
+    gT = step.states[0].grad_t.cpu().numpy() / S
+    gW = step.states[0].grad_w.cpu().numpy() / S
+    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    tq, wq = quantised(tables, weights)
+    loss_q, rT, rWs, h = oracle_pair_grads(ot, tq, wq, pairs)
+    assert abs(step.loss.item() - loss_q) <= 1e-2 * loss_q
+    frac = ambiguous_fraction(wq, h)
+    assert_bf16_errors(tensor_errors(gT, gW, rT, rWs), frac, "train_bf16 262,144 pairs")
+
+
+def test_bf16_backward_multitile():
+    """octa_query_bwd on the tensor cores (two 128-query groups per CTA) with
+    131,071 queries: 1,024 tiles on 304 group slots, a ragged last tile; wide
+    inputs (sigma 0.3, weights x1.5) so that the decoder is far from linear."""
+    from paper_2606_08469_gb300 import api as A
+    cfg = I.WORKLOADS["train_bf16"]
+    tree = A.octree_build(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    tables = I.make_tables(cfg.seed("tables"), tree.num_texels, cfg.F, 0.3)
+    weights = [W * np.float32(1.5) for W in I.make_mlp(cfg.seed("mlp"), [72, 64, 64, 64, 3])]
+    sc = A.Scene(tree, dev(tables).to(torch.float16).contiguous(),
+                 [dev(W).to(torch.bfloat16) for W in weights], device=DEV)
+    x, w = I.uniform_queries(79, 131071)
+    assert len(x) // 128 >= 3 * 2 * SMS
+    d_rgb = np.random.default_rng(80).normal(size=(len(x), 3)).astype(np.float32)
+    dT = torch.zeros(sc.tables.shape, device=DEV)
+    dW = torch.zeros(sc.weights.shape, device=DEV)
+    A.octa_query_bwd(sc, dev(x), dev(w), dev(d_rgb), [(dT, dW)])
+    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    tq, wq = quantised(tables, weights)
+    rT, rWs, _ = O.query_backward(ot, tq, wq, x, w, d_rgb)
+    frac = ambiguous_fraction(wq, O.encode_features(ot, tq, x, w).h)
+    assert_bf16_errors(tensor_errors(dT.cpu().numpy(), dW.cpu().numpy(), rT, rWs), frac,
+                       "BF16 backward, 1,024 tiles")
+
+
+# per-scene pair counts of the batched workload's eight scenes, each at least
+# 160 work items (two 64-pair tiles an item), so that with the interleaved
+# order every CTA of the 152-CTA persistent grid runs items of several scenes
+BATCHED_COUNTS = [20500, 21001, 23003, 20807, 24000, 20480, 22222, 25001]
+
+
+def test_persistent_batched_step_gradients():
+    """The one-launch batched step (fused pass, grid barriers, FP64 norm,
+    Adam) over the batched workload's eight scenes (depth 4..9, one BF16
+    decoder each) at BATCHED_COUNTS pairs: every CTA crosses scene
+    boundaries, flushing its dW^T accumulators and loss partials each time.
+    The first Adam step leaves m = (1 - beta1) g, so each scene's unscaled
+    gradient is read back from the first moment and compared per tensor with
+    the FP64 oracle on the quantised parameters; the losses and the step's
+    FP64 gradient norm are compared too."""
+    from paper_2606_08469_gb300 import api as A
+    from paper_2606_08469_gb300 import workloads as WL
+    assert min(BATCHED_COUNTS) // 128 >= SMS
+    step, host = WL.batched_train_step(counts=BATCHED_COUNTS, persistent=True)
+    step.step()
+    torch.cuda.synchronize()
+    sc = A.read_scaler(step.scaler)
+    assert sc.skipped == 0 and sc.step == 1
+    one_minus_b1 = np.float32(1.0) - np.float32(0.9)
+    sq = 0.0
+    losses = step.loss.cpu().numpy()
+    for s, (tree, tables, weights, pairs) in enumerate(host):
+        cfg_s = I.batched_scene_config(s)
+        ot = O.build_tree(I.batched_seed(s, "tree"), cfg_s.max_depth, cfg_s.p_base, cfg_s.R)
+        tq, wq = quantised(tables, weights)
+        loss_q, rT, rWs, h = oracle_pair_grads(ot, tq, wq, pairs)
+        assert abs(losses[s] - loss_q) <= 1e-2 * loss_q, (s, losses[s], loss_q)
+        gT = step.states[s].m_t.cpu().numpy() / one_minus_b1
+        gW = step.states[s].m_w.cpu().numpy() / one_minus_b1
+        assert_bf16_errors(tensor_errors(gT, gW, rT, rWs), ambiguous_fraction(wq, h),
+                           f"one-launch step, scene {s} (depth {cfg_s.max_depth})")
+        sq += float(np.sum(rT ** 2)) + sum(float(np.sum(W ** 2)) for W in rWs)
+    assert abs(sc.grad_norm - np.sqrt(sq)) <= 5e-2 * np.sqrt(sq), (sc.grad_norm, np.sqrt(sq))

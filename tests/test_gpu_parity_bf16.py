@@ -480,7 +480,8 @@ def test_persistent_step_barrier_timeout_reports_status():
     for s in b.states:                                      # the caller restarts the step
         s.grad_t.zero_()
         s.grad_w.zero_()
-    b.ws_step.zero_()
+    # the workspace is not re-zeroed by hand: the call clears the barrier
+    # words that the timed-out waits left behind
     status.zero_()
     b.persistent_step(status=status)
     torch.cuda.synchronize()

@@ -242,6 +242,36 @@ def test_malformed_tree_reports_status():
     assert int(status.item()) & 2
 
 
+
+@pytest.mark.parametrize("form", ["cell", "full"])
+@pytest.mark.parametrize("bad", [-1, -16])
+def test_negative_map_offset_reports_status(form, bad):
+    """A map base before the table start (negative offset, including ones
+    whose unsigned sum with R^2 lands back inside the table) is flagged as
+    OCTA_STATUS_BAD_MAP and never read: the encoding (shared gather) and the
+    FP32 engine's forward both treat the level as absent."""
+    from paper_2606_08469_gb300 import _lib as L
+    A = api()
+    R = [4, 4, 4] if form == "cell" else [5, 5, 5]
+    qf = L.OCTA_FORM_CELL_BILINEAR if form == "cell" else L.OCTA_FORM_TRILINEAR_VERTEX
+    tree = A.octree_build(3, 2, 1.0, R)
+    tables = I.make_tables(1, tree.num_texels, 4, 0.1)
+    weights = I.make_mlp(2, [12, 32, 32, 3])
+    tree.map_offset[:] = tree.map_offset.copy()
+    tree.map_offset[0] = bad          # the root's map would start before the table
+    sc = A.Scene(tree, dev(tables), [dev(W) for W in weights], device=DEV, query_form=qf)
+    x, w = I.uniform_queries(4, 500)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    feat, _, _ = A.octa_encode(sc, dev(x), dev(w), status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) & 2
+    assert torch.isfinite(feat).all() and (feat[:, :4] == 0).all()   # level 0 absent
+    status.zero_()
+    rgb, _, _ = A.octa_query_fwd(sc, dev(x), dev(w), status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) & 2
+    assert torch.isfinite(rgb).all()
+
 # ----------------------------------------------------------------- backward
 
 @pytest.mark.parametrize("which", ["forward_small", "train_f32"])
