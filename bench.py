@@ -12,9 +12,12 @@ of the one JSON line printed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun (N > 1) every rank runs an independent replica of the step on
-its own GPU (the step shards by independent pairs; weak scaling), timing is
-the max over ranks.  --impl reference times the FP64 CPU oracle on a bounded
+Under torchrun (N > 1) the step is data parallel: every rank holds its own
+seeded shard of 1,048,576 pairs of a global batch of N x 1,048,576 (weak
+scaling), runs the fused pass on it with the loss normalised by the global
+batch, and the ranks exchange every gradient and the loss in one NCCL
+all-reduce before each applies the same Adam update; timing is the max over
+ranks.  --impl reference times the FP64 CPU oracle on a bounded
 sample of the same workload on all host cores.
 """
 from __future__ import annotations
@@ -348,6 +351,35 @@ def train_f32_leg(dev, flush, stream, steps, peaks):
                         "pass_ms": round(t_pass, 4), "peak_source": peak_src}}
     del step
     return out
+
+
+def measure_ffma_peak(dev, reps=5):
+    """FP32 FMA throughput of this GPU (octa_measure_ffma: 16 independent
+    chains per thread, 8 resident 256-thread CTAs per SM), scalar and packed
+    pair forms, best of reps CUDA-event timings each: TFLOP/s."""
+    import torch
+    from paper_2606_08469_gb300 import api
+    blocks, threads, iters = SMS * 8, 256, 8192
+    out = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    lib = api._lib()
+    res = {}
+    for packed in (0, 1):
+        fn = lambda: api.L.check(lib.octa_measure_ffma(api._ptr(out), blocks, threads, iters, packed,
+                                                       api._stream()), "octa_measure_ffma")
+        fn()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        res["packed" if packed else "scalar"] = 2 * 16 * blocks * threads * iters / (min(ts) / 1e3) / 1e12
+    return {"f32_ffma_tflops": round(max(res.values()), 2),
+            "scalar_tflops": round(res["scalar"], 2), "packed_tflops": round(res["packed"], 2),
+            "how": f"octa_measure_ffma: {blocks} x {threads} threads x {iters} iterations x 16 "
+                   "FMA chains, best of 5"}
 
 
 def _f32_peak(peaks):
@@ -834,18 +866,22 @@ def run_legs(args, names):
     print(json.dumps({n: fns[n]() for n in names}), flush=True)
 
 
-def measure_step(step, nq, dev, stream, flush, args, barrier, pass_name="fused_pass"):
+def measure_step(step, nq, dev, stream, flush, args, barrier, pass_name="fused_pass", dp=None):
     """Device time of K training steps (fused pass + Adam) after W warm-up
     steps, L2 flushed before each step outside the events, the fused pass
     timed inside each step by its own events; then the same K steps end to
     end through the public API with every step's pair inputs copied in from
     pinned host memory (double-buffered on a copy stream) and the loss read
-    back.  Returns (step ms list, pass ms list, e2e ms, h2d bytes, clocks)."""
+    back.  dp: the rank's DataParallelStep (N > 1): its one all-reduce runs
+    between the pass and Adam inside the timed step and is timed by its own
+    events.  Returns (step ms list, pass ms list, e2e ms, h2d bytes, d2h
+    bytes, clocks, exchange ms list)."""
     import torch
+    run = dp.step if dp is not None else step.step
     for _ in range(args.warmup):
-        step.step()
+        run()
     barrier()
-    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(args.steps)]
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(6)) for _ in range(args.steps)]
     try:
         smi_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
@@ -854,16 +890,21 @@ def measure_step(step, nq, dev, stream, flush, args, barrier, pass_name="fused_p
         barrier()
         for k in range(args.steps):
             flush.zero_()
-            a, b, c, d = ev[k]
+            a, b, c, d, x0, x1 = ev[k]
             a.record(stream)
             c.record(stream)
             getattr(step, pass_name)()
             d.record(stream)
+            x0.record(stream)
+            if dp is not None:
+                dp.exchange()
+            x1.record(stream)
             step.optimizer()
             b.record(stream)
         barrier()
     step_ms = [e[0].elapsed_time(e[1]) for e in ev]
     pass_ms = [e[2].elapsed_time(e[3]) for e in ev]
+    xch_ms = [e[4].elapsed_time(e[5]) for e in ev]
 
     dev_in = step.pair_inputs()
     host = {k: t.cpu().pin_memory() for k, t in dev_in.items()}
@@ -894,13 +935,14 @@ def measure_step(step, nq, dev, stream, flush, args, barrier, pass_name="fused_p
                 copy_in(1 - b)
         stream.wait_event(ready[b])
         step.set_pair_inputs(bufs[b])
-        step.step()
+        run()
         consumed[b].record(stream)
         loss_host.copy_(step.loss, non_blocking=True)
     e1.record(stream)
     barrier()
     step.set_pair_inputs(dev_in)
-    return step_ms, pass_ms, e0.elapsed_time(e1), h2d, 8 * step.loss.numel(), clocks.summary()
+    return (step_ms, pass_ms, e0.elapsed_time(e1), h2d, 8 * step.loss.numel(), clocks.summary(),
+            xch_ms)
 
 
 def _fwd_flop(widths):
@@ -989,12 +1031,25 @@ def run_ours(args):
 
     cfg = I.WORKLOADS[HEADLINE]
     # the BF16 training step: the tensor-core fused pass (forward, Eq. 14
-    # gradient, backward, scatter in one launch) and Adam with the loss scaler
-    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=args.pairs, device=dev,
-                                                             fused=True)
+    # gradient, backward, scatter in one launch) and Adam with the loss
+    # scaler; with N > 1 ranks a data-parallel step over a global batch of
+    # N x args.pairs pairs (each rank its own seeded shard, the loss
+    # normalised by the global batch) with one NCCL all-reduce of the flat
+    # gradient buffer (and the loss) between the pass and Adam
+    dp = None
+    if world > 1:
+        from paper_2606_08469_gb300 import dataparallel as D
+        step, (tree, tables, weights, pairs) = WL.data_parallel_rank_step(
+            cfg, rank, world, n_per_rank=args.pairs, device=dev)
+        dp = D.DataParallelStep(step)
+    else:
+        step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, n_pairs=args.pairs,
+                                                                 device=dev, fused=True)
     n_q = 2 * pairs.n
-    step_ms, pass_ms, e2e_ms, h2d, d2h, clocks = measure_step(step, n_q, dev, stream, flush, args,
-                                                             barrier)
+    step_ms, pass_ms, e2e_ms, h2d, d2h, clocks, xch_ms = measure_step(step, n_q, dev, stream, flush,
+                                                                      args, barrier, dp=dp)
+    pass_max = max_over_ranks(statistics.mean(pass_ms), dev)
+    xch_max = max_over_ranks(statistics.mean(xch_ms), dev)
     total_ms = max_over_ranks(sum(step_ms), dev)
     e2e_ms = max_over_ranks(e2e_ms, dev)
     launches = 3 * args.steps  # fused pass, adam norm, adam update
@@ -1037,7 +1092,12 @@ def run_ours(args):
                                    f"{pairs.n} pairs = {n_q} queries per step (fused fwd + Eq.14 "
                                    "gradient + bwd + scatter, then Adam with dynamic loss scaling)",
                        "l2": "flushed between timed steps (256 MB write outside the events)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": (f"data parallel x{world}: global batch {world} x {pairs.n} "
+                                       "pairs, one NCCL all-reduce of the flat gradient buffer "
+                                       "and the loss per step") if world > 1 else "dp1"},
+            "data_parallel": {"ranks": world, "pass_ms_max_over_ranks": round(pass_max, 4),
+                              "allreduce_ms_max_over_ranks": round(xch_max, 4),
+                              "allreduce_bytes": int(dp.flat.numel() * 4) if dp is not None else 0},
             "fwd_only": {"value": round(job_rate(n_q, world, 1, fwd_mean), 3),
                          "unit": UNIT, "ms": round(fwd_mean, 4)},
             "loss": float(step.loss.item()),
@@ -1059,6 +1119,8 @@ def run_ours(args):
         }
         del step
         extra_steps = max(5, args.steps // 2)
+        out["ffma_peak"] = measure_ffma_peak(dev)
+        peaks = dict(peaks, f32_ffma_tflops=out["ffma_peak"]["f32_ffma_tflops"])
         if not args.no_extra:
             out["bf16_vs_f32"] = bf16_vs_f32_leg(dev, flush, stream, extra_steps, peaks,
                                                  out["value"])

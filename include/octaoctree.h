@@ -422,7 +422,14 @@ typedef struct octa_step_options {
                                   beyond the grid (0 in use; > 0 makes every
                                   wait run out, report OCTA_STATUS_TIMEOUT and
                                   skip the optimiser)                        */
-  int32_t reserved;
+  int32_t skip_first_mma;      /* test hook (0 in use): nonzero = no CTA
+                                  issues the tensor-core MMAs of the first
+                                  layer of its first tile, so that group's
+                                  mbarrier wait (bounded by
+                                  barrier_timeout_ns, like the grid barriers)
+                                  runs out: the kernel reports
+                                  OCTA_STATUS_TIMEOUT, frees its tensor
+                                  memory and returns without the optimiser */
 } octa_step_options;
 
 /* octa_train_step_batched -- a whole training step of up to 16 scenes in one
@@ -460,7 +467,10 @@ typedef struct octa_tuning {
                                   thread gathering half of the levels)     */
   int32_t encode_threads_per_query; /* octa_encode, cell form: 1 (default)
                                   or 2, as fwd_threads_per_query           */
-  int32_t reserved;
+  int32_t train_threads_per_row; /* tensor-core backward / training kernels,
+                                  cell form: 2 (default: 512-thread CTAs,
+                                  the two threads of a tile row splitting
+                                  its levels and epilogue columns) or 1   */
 } octa_tuning;
 int octa_set_tuning(const octa_tuning* t);   /* NULL restores the defaults */
 int octa_get_tuning(octa_tuning* t);

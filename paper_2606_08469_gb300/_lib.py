@@ -137,12 +137,12 @@ class octa_tuning(C.Structure):
     _fields_ = [("fwd_ctas_per_sm", C.c_int32), ("encode_ctas_per_sm", C.c_int32),
                 ("engine_ctas_per_sm", C.c_int32), ("fwd_order", C.c_int32),
                 ("train_order", C.c_int32), ("fwd_threads_per_query", C.c_int32),
-                ("encode_threads_per_query", C.c_int32), ("reserved", C.c_int32)]
+                ("encode_threads_per_query", C.c_int32), ("train_threads_per_row", C.c_int32)]
 
 
 class octa_step_options(C.Structure):
     _fields_ = [("barrier_timeout_ns", C.c_uint64), ("extra_barrier_arrivals", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("skip_first_mma", C.c_int32)]
 
 
 OCTA_MAX_PRIMS = 64
@@ -198,6 +198,7 @@ _SIGNATURES = {
     "octa_get_tuning": (C.c_int, [C.POINTER(octa_tuning)]),
     "octa_last_error": (C.c_char_p, []),
     "octa_abi_version": (C.c_int32, []),
+    "octa_measure_ffma": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P]),
 }
 
 _lib = None

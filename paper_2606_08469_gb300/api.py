@@ -273,7 +273,7 @@ def octa_train_fused(scenes, x, omega, x2, omega2, E, w, grads, loss_out, counts
 def octa_train_step_batched(scenes, x, omega, x2, omega2, E, w, grads, groups, loss_out, scaler, ws,
                             counts=None, eps=1e-2, rhs_grad=True, beta1=0.9, beta2=0.999,
                             adam_eps=1e-8, timeout_ns=0, extra_arrivals=0, status=None,
-                            stream=None, norm_pairs=None):
+                            stream=None, norm_pairs=None, skip_first_mma=0):
     """Whole training step (fused pass + Adam) in one persistent launch."""
     arr, ns = _scene_array(scenes)
     g = (L.octa_scene_grads * ns)(*[L.octa_scene_grads(dt.data_ptr(), dw.data_ptr())
@@ -290,7 +290,7 @@ def octa_train_step_batched(scenes, x, omega, x2, omega2, E, w, grads, groups, l
         acc += c
         pr.scene_start[i + 1] = acc
     _set_norm(pr, norm_pairs)
-    opt = L.octa_step_options(timeout_ns, extra_arrivals, 0)
+    opt = L.octa_step_options(timeout_ns, extra_arrivals, int(skip_first_mma))
     cfg = L.octa_adam_cfg(beta1, beta2, adam_eps)
     L.check(_lib().octa_train_step_batched(arr, ns, C.byref(pr), g, pg, len(groups), C.c_float(eps),
                                            int(bool(rhs_grad)), C.byref(cfg), _ptr(scaler),

@@ -111,8 +111,7 @@ __device__ __forceinline__ void locate_gather_bf16(const QueryParams& p, const D
     float v[F];
 #pragma unroll
     for (int f = 0; f < F; ++f) v[f] = v0[f];
-    if constexpr (TPQ == 1)  // the host runs one thread a query when attributes are given
-      if (p.n_attrs > 0 && l >= sc.K) attr_columns<F>(p, sc.K, l, gq, valid, v);
+    if (p.n_attrs > 0 && l >= sc.K) attr_columns<F>(p, sc.K, l, gq, valid, v);
     uint8_t* dst = act + kmajor_offset(q, l * F, S::WP);
     if constexpr (F == 8) {
       uint4 o;
@@ -334,11 +333,20 @@ __global__ void __launch_bounds__(NT * TPQ, 4)
 //   dW_i^T += a_i^T delta (both read MN-major from the forward's K-major
 //   tiles) and G = delta W_i (W_i read MN-major); the epilogue masks G with
 //   1[a_i > 0] in place; layer 0's G = dh is scattered with float4 atomics.
-template <int F_, int WP_, int H_, int NH_>
+// TPR (threads per row): 1 or 2 threads per tile row.  With two, a group is
+// 256 threads: thread (row, half) takes the levels of parity `half` in the
+// gather and the scatter and half of the columns in every epilogue (both
+// halves' warps read the same tensor-memory lane quadrant), so a CTA runs 16
+// warps and every per-thread chain of the tile is about half as long.
+template <int F_, int WP_, int H_, int NH_, int TPR_ = 1>
 struct BShape : Shape<F_, WP_, H_, NH_> {
   using B = Shape<F_, WP_, H_, NH_>;
   static constexpr int G = 2;
-  static constexpr int NTB = G * NT;
+  static constexpr int TPR = TPR_;
+  static_assert(TPR == 1 || TPR == 2, "threads per row");
+  static_assert(H_ % (16 * TPR) == 0, "epilogue column split");
+  static constexpr int NTG = TPR * NT;  // threads per group
+  static constexpr int NTB = G * NTG;
   static constexpr uint32_t H_TILE = NT * WP_ * 2;
   static constexpr uint32_t A_TILE = NT * H_ * 2;
   static constexpr uint32_t DL_TILE = NT * NOUT * 2;
@@ -373,16 +381,18 @@ struct BShape : Shape<F_, WP_, H_, NH_> {
   __host__ __device__ static constexpr int dw_col(int i) { return DW0 + H_ * i; }
 };
 
-// Adds the dW^T accumulators of the matrices [i0, i1) to the scene's FP32
-// weight gradient and zeroes them (thread t holds row t = input feature t).
+// Adds the dW^T accumulators of the matrices i0, i0 + di, ... below i1 to
+// the scene's FP32 weight gradient and zeroes them (thread t holds row t =
+// input feature t).
 template <class S>
-__device__ void flush_weight_grads(const DevScene& sc, uint32_t lane_addr, int i0, int i1) {
+__device__ void flush_weight_grads(const DevScene& sc, uint32_t lane_addr, int i0, int i1,
+                                   int di = 1) {
   const int r = threadIdx.x % NT;
   uint32_t zero[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) zero[j] = 0u;
 #pragma unroll 1
-  for (int i = i0; i < i1; ++i) {
+  for (int i = i0; i < i1; i += di) {
     const int n_pad = S::ndim(i);
     const int in = sc.widths[i], out = sc.widths[i + 1];
     float* dW = sc.d_weights + sc.w_offset[i];
@@ -668,10 +678,13 @@ __device__ __forceinline__ void flush_loss(double& acc, double* loss, int64_t n_
 template <class S, typename TT, bool TRAIN, bool PERSIST = false, bool FORMS = true>
 __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ BwdParams bp) {
   const QueryParams& p = bp.p;
-  constexpr int H = S::H, NL = S::NL;
+  constexpr int H = S::H, NL = S::NL, TPR = S::TPR, NTG = S::NTG;
+  static_assert(!FORMS || TPR == 1, "the full and shifted forms run one thread per row");
   constexpr int ROWS = TRAIN ? NT / 2 : NT;  // pairs or queries per tile
+  constexpr int HC = H / TPR;                // epilogue columns of one thread
   extern __shared__ __align__(1024) uint8_t smem[];
-  const int g = threadIdx.x / NT, t = threadIdx.x % NT, warp = threadIdx.x >> 5;
+  const int g = threadIdx.x / NTG, t = threadIdx.x % NT, warp = threadIdx.x >> 5;
+  const int half = (threadIdx.x % NTG) / NT;  // column half / level parity of the row
   uint8_t* gbase = smem + S::OFF_GROUP + g * S::GR_BYTES;
   int* base_sm = reinterpret_cast<int*>(gbase + S::GR_NODE);  // map base per level
   float* u_sm = reinterpret_cast<float*>(gbase + S::GR_U);
@@ -683,7 +696,9 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   const uint32_t mbar = smem_addr(bars + g);
   const uint32_t base_sa = smem_addr(smem);
   const uint32_t dl_sa = base_sa + S::off_dl(g);
-  const int gbar = 1 + g;  // named barrier of this group
+  const int gbar = 1 + g;                         // named barrier of this group
+  const int xbar = TPR == 1 ? gbar : 1 + S::G + g;  // its half-0 threads alone
+  const bool lead = t == 0 && half == 0;           // issues the group's MMAs
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < S::G; ++i) mbar_init(smem_addr(bars + i), 1);
@@ -700,12 +715,12 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   const uint32_t lane_addr = tmem + (static_cast<uint32_t>((warp % 4) * 32) << 16);
   const uint32_t work = tmem + static_cast<uint32_t>(g * S::WORK);           // MMA D address
   const uint32_t lane_work = lane_addr + static_cast<uint32_t>(g * S::WORK);  // epilogue loads
-  if (g == 0) {  // zero the shared dW^T accumulators
+  if (g == 0) {  // zero the shared dW^T accumulators (16-column chunks split by half)
     uint32_t zero[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) zero[j] = 0u;
 #pragma unroll 1
-    for (int c = 0; c < S::DW_COLS; c += 16) tmem_st16(lane_addr + S::DW0 + c, zero);
+    for (int c = 16 * half; c < S::DW_COLS; c += 16 * TPR) tmem_st16(lane_addr + S::DW0 + c, zero);
     tmem_wait_st();
   }
   tc_fence_before_sync();
@@ -716,6 +731,13 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   double loss_acc = 0.0;
   const float lscale = TRAIN ? (p.scaler ? p.scaler->scale : 1.f) : 1.f;
   float* xch = reinterpret_cast<float*>(gbase + S::GR_XCH);  // radiance exchange (TRAIN)
+  // the persistent step's bound on every wait (its test hook makes the
+  // first tile's first mbarrier wait run out: no MMA is issued for it)
+  const uint64_t wait_ns = PERSIST ? bp.a.timeout_ns : 1000000000ull;
+  bool skip_hook = PERSIST && bp.a.skip_first_mma != 0;
+  // matrices whose dW^T this thread's set (group, half) flushes
+  const int flush_set = g * TPR + half;
+  constexpr int FLUSH_SETS = S::G * TPR;
 
   // query (pair) row of this thread in a tile, and which pair array it reads
   const int row = TRAIN ? (t & (ROWS - 1)) : t;
@@ -743,11 +765,11 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
     if (s != cur) {
       tc_fence_after_sync();
       if (cur >= 0) {
-        flush_weight_grads<S>(p.sc[cur], lane_addr, g == 0 ? 0 : NL / 2, g == 0 ? NL / 2 : NL);
+        flush_weight_grads<S>(p.sc[cur], lane_addr, flush_set, NL, FLUSH_SETS);
         tc_fence_before_sync();
         if (TRAIN) flush_loss(loss_acc, p.loss + cur, p.sc[cur].norm_pairs);
       }
-      for (int l = 0; l < S::NL; ++l) {  // weights, all 256 threads
+      for (int l = 0; l < S::NL; ++l) {  // weights, all threads
         const int K = S::kdim(l), N = S::ndim(l);
         const int in = sc.widths[l], out = sc.widths[l + 1];
         const __nv_bfloat16* Wg = static_cast<const __nv_bfloat16*>(sc.weights);
@@ -772,47 +794,55 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
     const bool full = FORMS && sc.query_form == OCTA_FORM_TRILINEAR_VERTEX;  // uniform over the CTA
     const bool shifted = FORMS && sc.query_form == OCTA_FORM_SHIFTED;
     const QueryIn& qry = in;  // the layer loops below reuse the name in
-    if (full)
-      locate_gather_bf16<S, TT, 1, OCTA_FORM_TRILINEAR_VERTEX>(
-          p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), nullptr, nullptr, t);
-    else if (shifted)
-      locate_gather_bf16<S, TT, 1, OCTA_FORM_SHIFTED>(
-          p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), nullptr, nullptr, t);
-    else
-      locate_gather_bf16<S, TT>(p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), base_sm,
-                                u_sm, t);
+    if constexpr (FORMS) {
+      if (full)
+        locate_gather_bf16<S, TT, 1, OCTA_FORM_TRILINEAR_VERTEX>(
+            p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), nullptr, nullptr, t);
+      else if (shifted)
+        locate_gather_bf16<S, TT, 1, OCTA_FORM_SHIFTED>(
+            p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), nullptr, nullptr, t);
+      else
+        locate_gather_bf16<S, TT>(p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), base_sm,
+                                  u_sm, t);
+    } else {
+      locate_gather_bf16<S, TT, TPR>(p, sc, tree, in, gq, valid, half, smem + S::off_act(g, 0),
+                                     base_sm, u_sm, t);
+    }
     fence_proxy_async();
-    named_sync(gbar, NT);
+    named_sync(gbar, NTG);
 
     bool failed = false;
     // ---- forward, keeping a_1 .. a_NH and delta_L
 #pragma unroll 1
     for (int layer = 0; layer < NL; ++layer) {
-      if (t == 0) issue_layer<S>(layer, base_sa + S::off_act(g, layer), base_sa, work, mbar);
-      const bool ok = mbar_wait_bounded(mbar, phase);
+      if (lead && !(skip_hook && layer == 0))
+        issue_layer<S>(layer, base_sa + S::off_act(g, layer), base_sa, work, mbar);
+      skip_hook = false;
+      const bool ok = mbar_wait_bounded(mbar, phase, wait_ns);
       phase ^= 1u;
-      if (named_sync_or(gbar, NT, !ok)) {
+      if (named_sync_or(gbar, NTG, !ok)) {
         failed = true;
         break;
       }
       tc_fence_after_sync();
       if (layer < NL - 1) {
-        uint32_t r[H];
+        const int c0 = half * HC;
+        uint32_t r[HC];
 #pragma unroll
-        for (int c = 0; c < H; c += 16)
-          tmem_ld16(lane_work + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
+        for (int c = 0; c < HC; c += 16)
+          tmem_ld16(lane_work + c0 + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
         tmem_wait_ld();
         uint8_t* dst = smem + S::off_act(g, layer + 1);
 #pragma unroll
-        for (int c = 0; c < H; c += 8) {
+        for (int c = 0; c < HC; c += 8) {
           uint4 o;
           o.x = pack_relu_bf16x2(r[c + 0], r[c + 1]);
           o.y = pack_relu_bf16x2(r[c + 2], r[c + 3]);
           o.z = pack_relu_bf16x2(r[c + 4], r[c + 5]);
           o.w = pack_relu_bf16x2(r[c + 6], r[c + 7]);
-          *reinterpret_cast<uint4*>(dst + kmajor_offset(t, c, H)) = o;
+          *reinterpret_cast<uint4*>(dst + kmajor_offset(t, c0 + c, H)) = o;
         }
-      } else {
+      } else if (half == 0) {  // warp-uniform: the last layer's 3 outputs
         uint32_t r[16];
         tmem_ld16(lane_work, r);
         tmem_wait_ld();
@@ -835,7 +865,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
             xch[4 * row + 1] = L1;
             xch[4 * row + 2] = L2;
           }
-          named_sync(gbar, NT);
+          named_sync(xbar, NT);
           if (primary && valid) {
             const float Ls[3] = {xch[4 * row], xch[4 * row + 1], xch[4 * row + 2]};
             const float Lp[3] = {L0, L1, L2};
@@ -859,7 +889,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
             xch[4 * row + 1] = ds[1];
             xch[4 * row + 2] = ds[2];
           }
-          named_sync(gbar, NT);
+          named_sync(xbar, NT);
           if (!primary && valid) {
             d0 = xch[4 * row];
             d1 = xch[4 * row + 1];
@@ -878,7 +908,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
       }
       fence_proxy_async();
       tc_fence_before_sync();
-      named_sync(gbar, NT);
+      named_sync(gbar, NTG);
     }
 
     // ---- backward through the decoder
@@ -887,7 +917,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
       const int out = S::ndim(i), in = S::kdim(i);
       const uint32_t d_sa = i == NL - 1 ? dl_sa : base_sa + S::off_act(g, i + 1);
       const int dk = out;  // row length of the delta tile
-      if (t == 0) {
+      if (lead) {
         tc_fence_after_sync();
         // dW_i^T += a_i^T delta_{i+1}: M = 128 input features, N = out, K = 128 queries
         const uint32_t act_sa = base_sa + S::off_act(g, i);
@@ -905,24 +935,25 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
                    ko > 0 ? 1u : 0u);
         mma_commit(mbar);
       }
-      const bool ok = mbar_wait_bounded(mbar, phase);
+      const bool ok = mbar_wait_bounded(mbar, phase, wait_ns);
       phase ^= 1u;
-      if (named_sync_or(gbar, NT, !ok)) {
+      if (named_sync_or(gbar, NTG, !ok)) {
         failed = true;
         break;
       }
       tc_fence_after_sync();
       if (i > 0) {
         // delta_i = G * 1[a_i > 0], written over a_i (its MMAs have completed)
-        uint32_t r[H];
+        const int c0 = half * HC;
+        uint32_t r[HC];
 #pragma unroll
-        for (int c = 0; c < H; c += 16)
-          tmem_ld16(lane_work + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
+        for (int c = 0; c < HC; c += 16)
+          tmem_ld16(lane_work + c0 + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
         tmem_wait_ld();
         uint8_t* act = smem + S::off_act(g, i);
 #pragma unroll
-        for (int c = 0; c < H; c += 8) {
-          uint4* pa = reinterpret_cast<uint4*>(act + kmajor_offset(t, c, H));
+        for (int c = 0; c < HC; c += 8) {
+          uint4* pa = reinterpret_cast<uint4*>(act + kmajor_offset(t, c0 + c, H));
           const uint4 a = *pa;
           const uint32_t av[4] = {a.x, a.y, a.z, a.w};
           uint32_t ov[4];
@@ -937,22 +968,51 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
         }
         fence_proxy_async();
         tc_fence_before_sync();
-        named_sync(gbar, NT);
+        named_sync(gbar, NTG);
+      } else if (!full && !shifted) {
+        // dh = G; scatter w_k * dh_l into the four texels of each present
+        // level of this thread's parity
+        constexpr int KO = (S::KPAD + TPR - 1) / TPR;
+        uint32_t r[KO][S::F];
+#pragma unroll
+        for (int o = 0; o < KO; ++o)
+          if (o * TPR + half < S::KPAD)
+            tmem_ld_cols<S::F>(lane_work + (o * TPR + half) * S::F, r[o]);
+        tmem_wait_ld();
+        tc_fence_before_sync();
+#pragma unroll
+        for (int o = 0; o < KO; ++o) {
+          const int l = o * TPR + half;
+          if (l >= S::KPAD) continue;
+          const int64_t mo = base_sm[l * NT + t];
+          if (mo < 0) continue;
+          const Footprint fp = footprint(u_sm[t], u_sm[NT + t], sc.R[l]);
+#pragma unroll
+          for (int c4 = 0; c4 < S::F / 4; ++c4) {
+            const float g0 = __uint_as_float(r[o][4 * c4 + 0]);
+            const float g1 = __uint_as_float(r[o][4 * c4 + 1]);
+            const float g2 = __uint_as_float(r[o][4 * c4 + 2]);
+            const float g3 = __uint_as_float(r[o][4 * c4 + 3]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float w = fp.w[k];
+              float4* dst = reinterpret_cast<float4*>(sc.d_tables + (mo + fp.idx[k]) * S::F) + c4;
+              atomicAdd(dst, make_float4(w * g0, w * g1, w * g2, w * g3));
+            }
+          }
+        }
       } else {
-        // dh = G; scatter w_k * dh_l into the four texels of every present level
+        // full and shifted forms (one thread per row): dh by level from a
+        // thread-local copy (their level loops stay rolled)
         uint32_t r[S::WP];
 #pragma unroll
         for (int c = 0; c < S::WP; c += 16)
           tmem_ld16(lane_work + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
         tmem_wait_ld();
         tc_fence_before_sync();
-        // full and shifted forms: dh by level from a thread-local copy (their
-        // level loops stay rolled)
         float dh[S::WP];
-        if (full || shifted) {
 #pragma unroll
-          for (int c = 0; c < S::WP; ++c) dh[c] = __uint_as_float(r[c]);
-        }
+        for (int c = 0; c < S::WP; ++c) dh[c] = __uint_as_float(r[c]);
         if (full) {  // the 24 vertices of each level (Eq. 10 with Eq. 6)
           if (valid) {
             float ux, uy;
@@ -980,7 +1040,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
               }
             });
           }
-        } else if (shifted) {  // each cell's own triangle (Eq. 7-9 with Eq. 6, 10)
+        } else {  // shifted: each cell's own triangle (Eq. 7-9 with Eq. 6, 10)
           if (valid) {
             const float xs[3] = {clamp01(qry.x0), clamp01(qry.x1), clamp01(qry.x2)};
             const float w0[3] = {qry.w0, qry.w1, qry.w2};
@@ -1011,30 +1071,10 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
               }
             });
           }
-        } else {
-#pragma unroll
-          for (int l = 0; l < S::KPAD; ++l) {
-            const int64_t mo = base_sm[l * NT + t];
-            if (mo < 0) continue;
-            const Footprint fp = footprint(u_sm[t], u_sm[NT + t], sc.R[l]);
-#pragma unroll
-            for (int c4 = 0; c4 < S::F / 4; ++c4) {
-              const float g0 = __uint_as_float(r[l * S::F + 4 * c4 + 0]);
-              const float g1 = __uint_as_float(r[l * S::F + 4 * c4 + 1]);
-              const float g2 = __uint_as_float(r[l * S::F + 4 * c4 + 2]);
-              const float g3 = __uint_as_float(r[l * S::F + 4 * c4 + 3]);
-#pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                const float w = fp.w[k];
-                float4* dst = reinterpret_cast<float4*>(sc.d_tables + (mo + fp.idx[k]) * S::F) + c4;
-                atomicAdd(dst, make_float4(w * g0, w * g1, w * g2, w * g3));
-              }
-            }
-          }
         }
       }
     }
-    if (failed && t == 0) {
+    if (failed && lead) {
       abort_flag = 1;
       if (p.status) atomicOr(p.status, OCTA_STATUS_TIMEOUT);
     }
@@ -1043,7 +1083,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   __syncthreads();
   tc_fence_after_sync();
   if (cur >= 0 && !abort_flag) {
-    flush_weight_grads<S>(p.sc[cur], lane_addr, g == 0 ? 0 : NL / 2, g == 0 ? NL / 2 : NL);
+    flush_weight_grads<S>(p.sc[cur], lane_addr, flush_set, NL, FLUSH_SETS);
     if (TRAIN) flush_loss(loss_acc, p.loss + cur, p.sc[cur].norm_pairs);
   }
   tc_fence_before_sync();
@@ -1156,16 +1196,25 @@ int dispatch_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, c
   if (rc) return rc;
   bool forms = false;  // any scene in the full or shifted form
   for (int s = 0; s < n_scenes; ++s) forms = forms || scenes[s].query_form != OCTA_FORM_CELL_BILINEAR;
-#define OCTA_TC_TRY(F_, WP_, H_, NH_)                                                        \
-  if (F == F_ && H == H_ && NH == NH_ && need <= WP_)                                        \
-    return forms ? (f16 ? launch_bwd<BShape<F_, WP_, H_, NH_>, __half, TRAIN, PERSIST, true>(     \
-                              p, adam, stream)                                                   \
-                        : launch_bwd<BShape<F_, WP_, H_, NH_>, float, TRAIN, PERSIST, true>(      \
-                              p, adam, stream))                                                  \
-                 : (f16 ? launch_bwd<BShape<F_, WP_, H_, NH_>, __half, TRAIN, PERSIST, false>(    \
-                              p, adam, stream)                                                   \
-                        : launch_bwd<BShape<F_, WP_, H_, NH_>, float, TRAIN, PERSIST, false>(     \
-                              p, adam, stream));
+  // cell form: two threads per tile row unless the tuning asks for one
+  const bool tpr1 = tuning_snapshot().train_threads_per_row == 1;
+#define OCTA_TC_TRY(F_, WP_, H_, NH_)                                                         \
+  if (F == F_ && H == H_ && NH == NH_ && need <= WP_) {                                       \
+    if (forms)                                                                                \
+      return f16 ? launch_bwd<BShape<F_, WP_, H_, NH_, 1>, __half, TRAIN, PERSIST, true>(      \
+                       p, adam, stream)                                                       \
+                 : launch_bwd<BShape<F_, WP_, H_, NH_, 1>, float, TRAIN, PERSIST, true>(       \
+                       p, adam, stream);                                                      \
+    if (tpr1)                                                                                 \
+      return f16 ? launch_bwd<BShape<F_, WP_, H_, NH_, 1>, __half, TRAIN, PERSIST, false>(     \
+                       p, adam, stream)                                                       \
+                 : launch_bwd<BShape<F_, WP_, H_, NH_, 1>, float, TRAIN, PERSIST, false>(      \
+                       p, adam, stream);                                                      \
+    return f16 ? launch_bwd<BShape<F_, WP_, H_, NH_, 2>, __half, TRAIN, PERSIST, false>(       \
+                     p, adam, stream)                                                         \
+               : launch_bwd<BShape<F_, WP_, H_, NH_, 2>, float, TRAIN, PERSIST, false>(        \
+                     p, adam, stream);                                                        \
+  }
   OCTA_TC_TRY(4, 32, 32, 2)
   OCTA_TC_TRY(8, 64, 64, 2)
   OCTA_TC_TRY(8, 80, 64, 2)

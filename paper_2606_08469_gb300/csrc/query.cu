@@ -487,6 +487,7 @@ extern "C" int octa_train_step_batched(const octa_scene* scenes, int32_t n_scene
   a.partials = reinterpret_cast<double*>(static_cast<char*>(workspace) + 256);
   a.timeout_ns = options && options->barrier_timeout_ns ? options->barrier_timeout_ns : 1000000000ull;
   a.extra_arrivals = options ? options->extra_barrier_arrivals : 0;
+  a.skip_first_mma = options ? options->skip_first_mma : 0;
   if (a.extra_arrivals < 0) return fail(OCTA_EINVAL, "extra_barrier_arrivals must be >= 0");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(loss_dev, 0, sizeof(double) * n_scenes, st);
@@ -509,7 +510,8 @@ extern "C" int octa_set_tuning(const octa_tuning* t) {
   if (t->fwd_ctas_per_sm < 0 || t->encode_ctas_per_sm < 0 || t->engine_ctas_per_sm < 0 ||
       t->fwd_order < 0 || t->fwd_order > 2 || t->train_order < 0 || t->train_order > 2 ||
       t->fwd_threads_per_query < 0 || t->fwd_threads_per_query > 2 ||
-      t->encode_threads_per_query < 0 || t->encode_threads_per_query > 2)
+      t->encode_threads_per_query < 0 || t->encode_threads_per_query > 2 ||
+      t->train_threads_per_row < 0 || t->train_threads_per_row > 2)
     return fail(OCTA_EINVAL, "tuning values out of range");
   tuning() = *t;
   return OCTA_OK;

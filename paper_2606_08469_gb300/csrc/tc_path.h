@@ -20,6 +20,7 @@ struct AdamBlock {
   double* partials;         // [gridDim.x] FP64 sums of squares
   uint64_t timeout_ns;      // bound of every barrier wait
   int32_t extra_arrivals;   // arrivals awaited beyond the grid (0; tests use > 0)
+  int32_t skip_first_mma;   // test hook: no MMA for layer 0 of each CTA's first tile
 };
 
 

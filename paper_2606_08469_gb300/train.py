@@ -70,6 +70,7 @@ class TrainStep:
         self.ws_loss = api.workspace(L.OCTA_OP_LOSS, max(self.n), device=dev)
         self.ws_adam = api.workspace(L.OCTA_OP_ADAM, 0, device=dev)
         self.eps, self.rhs_grad = eps, rhs_grad
+        self.lr_tables, self.lr_mlp = lr_tables, lr_mlp
         self.groups = [g for s in scene_states for g in s.groups(lr_tables, lr_mlp)]
         self.grads = [(s.grad_t, s.grad_w) for s in scene_states]
         # fused mode: one octa_train_fused launch replaces forward + loss +
@@ -89,6 +90,33 @@ class TrainStep:
             self.Px, self.Pw, self.Sx = cat("x"), cat("omega"), cat("x2")
             self.Sw = torch.cat([-p["omega2"] for p in pairs]).to(dev).contiguous()
             self.Ecat, self.wcat = cat("E"), cat("w")
+
+    def use_flat_gradients(self, extra=0):
+        """Move every scene's gradient buffers into one flat FP32 tensor (each
+        buffer at a 16-byte aligned offset, as the float4 scatter needs) with
+        `extra` free slots at its end, and point the kernels' gradient
+        arguments and Adam's groups at the views.  Returns the flat tensor
+        (a data-parallel step all-reduces it with one collective)."""
+        sizes = []
+        for s in self.states:
+            sizes += [s.grad_t.numel(), s.grad_w.numel()]
+        offs, off = [], 0
+        for n in sizes:
+            offs.append(off)
+            off += (n + 3) // 4 * 4
+        flat = torch.zeros(off + extra, dtype=torch.float32, device=self.states[0].grad_t.device)
+        k = 0
+        for s in self.states:
+            for name in ("grad_t", "grad_w"):
+                old = getattr(s, name)
+                view = flat[offs[k]:offs[k] + old.numel()].view(old.shape)
+                view.copy_(old)
+                setattr(s, name, view)
+                k += 1
+        self.groups = [g for s in self.states for g in s.groups(self.lr_tables, self.lr_mlp)]
+        self.grads = [(s.grad_t, s.grad_w) for s in self.states]
+        self.flat_grads = flat
+        return flat
 
     PAIR_INPUTS = ("Px", "Pw", "Sx", "Sw", "Ecat", "wcat")
 
@@ -131,12 +159,14 @@ class TrainStep:
                              self.grads, self.loss, self.n, self.eps, self.rhs_grad, self.scaler,
                              stream=stream, norm_pairs=self.norm_pairs)
 
-    def persistent_step(self, stream=None, status=None, timeout_ns=0, extra_arrivals=0):
+    def persistent_step(self, stream=None, status=None, timeout_ns=0, extra_arrivals=0,
+                        skip_first_mma=0):
         api.octa_train_step_batched(self.scenes, self.Px, self.Pw, self.Sx, self.Sw, self.Ecat,
                                     self.wcat, self.grads, self.groups, self.loss, self.scaler,
                                     self.ws_step, self.n, self.eps, self.rhs_grad,
                                     timeout_ns=timeout_ns, extra_arrivals=extra_arrivals,
-                                    status=status, stream=stream, norm_pairs=self.norm_pairs)
+                                    status=status, stream=stream, norm_pairs=self.norm_pairs,
+                                    skip_first_mma=skip_first_mma)
 
     def step(self, stream=None):
         if self.persistent:

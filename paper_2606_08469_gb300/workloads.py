@@ -74,6 +74,24 @@ def data_parallel_train_step(cfg, rank, world, n_pairs=None, device="cuda", prec
     return step, (tree, tables, weights, pairs, (b, e))
 
 
+def data_parallel_rank_step(cfg, rank, world, n_per_rank=None, device="cuda", precision=None,
+                            **kw):
+    """Fused TrainStep of one rank of a weak-scaling data-parallel job: the
+    global batch is world x n_per_rank pairs, rank r holding its own
+    n_per_rank seeded pairs (seed of the workload's queries + 7919 r), every
+    rank's loss normalised by the global batch."""
+    tree, tables, weights = host_params(cfg)
+    tdt, wdt = table_dtype(cfg), weight_dtype(cfg)
+    if precision == "f32":
+        tdt = wdt = torch.float32
+    st = SceneState(tree, tables, weights, tdt, wdt, device)
+    n = cfg.n if n_per_rank is None else n_per_rank
+    pairs = I.training_pairs(cfg.seed("queries") + 7919 * rank, n)
+    step = TrainStep([st], [pairs_on_device(pairs, device)], fused=True, norm_pairs=[n * world],
+                     device=device, **kw)
+    return step, (tree, tables, weights, pairs)
+
+
 def batched_train_step(device="cuda", counts=None, precision=None, **kw):
     """TrainStep of the batched workload (8 scenes); counts overrides the
     per-scene pair counts."""

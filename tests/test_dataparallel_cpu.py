@@ -94,3 +94,44 @@ def test_shard_ranges_partition_the_batch():
             assert max(sizes) - min(sizes) <= 1
     with pytest.raises(ValueError):
         D.shard_range(5, 2, 2)
+
+
+def _flat_rank(rank, world, port, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2606_08469_gb300 import dataparallel as D
+    g = np.random.default_rng(100 + rank)
+    flat = torch.from_numpy(g.normal(size=1000).astype(np.float32))
+    flat[-4:] = 0.0                                    # the two losses' slots
+    losses = torch.tensor([0.123456789012345 * (rank + 1), 1e-3 / (rank + 3)], dtype=torch.float64)
+    calls = []
+    real = dist.all_reduce
+    dist.all_reduce = lambda *a, **k: (calls.append(1), real(*a, **k))[1]
+    D.allreduce_flat(flat, losses)
+    dist.all_reduce = real
+    out[rank] = (flat.numpy().copy(), losses.numpy().copy(), len(calls))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_flat_exchange_one_collective_two_ranks():
+    """A data-parallel step's exchange: the gradients and the FP64 losses
+    (as FP32 hi/lo pairs in the buffer's tail) in ONE all-reduce; the sum
+    of the ranks' losses comes back to about binary32 rounding of the sum."""
+    import sys
+    sys.path.insert(0, ROOT)
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_flat_rank, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    want = sum(np.random.default_rng(100 + r).normal(size=1000).astype(np.float32) for r in range(world))
+    want_loss = np.array([0.123456789012345 * 3, 1e-3 / 3 + 1e-3 / 4])
+    for r in range(world):
+        flat, losses, calls = res[r]
+        assert calls == 1
+        np.testing.assert_allclose(flat[:-4], want[:-4], rtol=1e-6, atol=1e-6)
+        np.testing.assert_allclose(losses, want_loss, rtol=1e-7, atol=0)

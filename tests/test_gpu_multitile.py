@@ -11,17 +11,28 @@ SMs; one FP32 CTA or two tensor-core groups per SM) and compare the table and
 decoder gradients, before Adam, with the FP64 oracle's query_backward of the
 Eq. 14 loss (one-sample target of Eq. 3), normwise per tensor.
 
-Bounds: FP32 1e-5 normwise per tensor.  BF16 (quantised parameters, i.e.
-the arithmetic alone): the last layer's dW at 1e-2 (no ReLU mask), every
-other tensor at 3 sqrt(f) + 1e-2 with f the oracle's fraction of hidden
-pre-activations within the BF16 forward error of zero (a mask there may flip,
-changing one delta element by 100%)."""
+A ReLU mask is an integer that floating point decides: where a hidden
+pre-activation z lies within the evaluation's rounding error of zero, the
+FP32 kernel and the FP64 oracle may take opposite sides, and that one delta
+element then differs by 100%.  At a quarter of a million pairs there are
+dozens of such elements (about 5e-5 of all pre-activations lie within
+2^-16 sum|w||a| of zero), enough to move the table gradient by ~1e-4 on
+their own.  The FP32 tests therefore give no gradient to a query whose FP64
+forward has such a pre-activation (backward: its d_rgb row is zero; training
+pass: its pair's target is set to its own FP64 radiance, E = L_p and w = 0,
+so its residual is zero to rounding), computed by the oracle alone, and hold
+every tensor to 1e-5 normwise.  BF16 (quantised parameters, i.e. the
+arithmetic alone): the last layer's dW at 1e-2 (no ReLU mask), every other
+tensor at 3 sqrt(f) + 1e-2 with f the oracle's fraction of hidden
+pre-activations within the BF16 forward error of zero (there most queries
+have one, so the bound absorbs the flips instead)."""
 import numpy as np
 import pytest
 import torch
 
 from oracle import octaoctree_oracle as O
 from paper_2606_08469_gb300 import inputs as I
+from oracle_helpers import ambiguous_queries, unambiguous_pairs
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
@@ -97,27 +108,62 @@ def assert_bf16_errors(errs, frac, what):
 def test_f32_fused_pass_full_config1_gradients():
     """The headline FP32 pass (train_f32: 262,144 pairs, 4,096 64-pair tiles,
     about 27 tiles per CTA) at its full size: loss and every gradient tensor
-    before Adam against the FP64 oracle at 1e-5."""
+    before Adam against the FP64 oracle at 1e-5, the pairs with an ambiguous
+    ReLU mask given a zero residual (module docstring)."""
     from paper_2606_08469_gb300 import workloads as WL
+    from paper_2606_08469_gb300.train import SceneState, TrainStep
     cfg = I.WORKLOADS["train_f32"]
-    step, (tree, tables, weights, pairs) = WL.train_step_for(cfg, fused=True)
-    assert pairs.n == 262144 and pairs.n // 64 >= 3 * SMS
+    tree, tables, weights = WL.host_params(cfg)
+    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    pairs, n_bad = unambiguous_pairs(ot, tables, weights, I.training_pairs(cfg.seed("queries"), cfg.n))
+    assert pairs.n == 262144 and pairs.n // 64 >= 3 * SMS and n_bad < pairs.n // 20
+    st = SceneState(tree, tables, weights, torch.float32, torch.float32, DEV)
+    step = TrainStep([st], [WL.pairs_on_device(pairs, DEV)], fused=True)
     step.fused_pass()
     torch.cuda.synchronize()
     S = 2.0 ** 15
     gT = step.states[0].grad_t.cpu().numpy() / S
     gW = step.states[0].grad_w.cpu().numpy() / S
-    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
     loss, rT, rWs, _ = oracle_pair_grads(ot, tables, weights, pairs)
     assert abs(step.loss.item() - loss) <= 1e-5 * loss
     errs = tensor_errors(gT, gW, rT, rWs)
-    print("train_f32 full-size fused gradients vs FP64", [f"{e:.2e}" for e in errs])
+    print(f"train_f32 full-size fused gradients vs FP64 ({n_bad} pairs zeroed)",
+          [f"{e:.2e}" for e in errs])
     assert max(errs) <= 1e-5, errs
+
+
+def test_f32_fused_pass_full_equals_shard_sum():
+    """The same full-size pass against the sum of 64 passes over its 4,096-
+    pair shards (each at most one tile per CTA, every one normalised by the
+    whole batch): the per-query FP32 arithmetic is the same in both, so they
+    differ only by the order of the FP32 atomics, whatever the masks."""
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.WORKLOADS["train_f32"]
+    full, _ = WL.train_step_for(cfg, fused=True)
+    full.fused_pass()
+    world = cfg.n // 4096
+    gT = torch.zeros_like(full.states[0].grad_t)
+    gW = torch.zeros_like(full.states[0].grad_w)
+    loss = 0.0
+    for r in range(world):
+        st, _ = WL.data_parallel_train_step(cfg, r, world)
+        st.fused_pass()
+        gT += st.states[0].grad_t
+        gW += st.states[0].grad_w
+        loss += st.loss.item()
+        del st
+    torch.cuda.synchronize()
+    e = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+    print("full pass vs shard sum: loss", abs(full.loss.item() - loss) / loss, "tables",
+          e(full.states[0].grad_t, gT), "weights", e(full.states[0].grad_w, gW))
+    assert abs(full.loss.item() - loss) <= 1e-6 * loss
+    assert e(full.states[0].grad_t, gT) <= 1e-5 and e(full.states[0].grad_w, gW) <= 1e-5
 
 
 def test_f32_backward_multitile():
     """octa_query_bwd on the FP32 engine (128-query tiles, one CTA per SM)
-    with 100,003 queries: 782 tiles, five or six per CTA, a ragged last one."""
+    with 100,003 queries: 782 tiles, five or six per CTA, a ragged last one;
+    queries with an ambiguous ReLU mask get a zero d_rgb row."""
     from paper_2606_08469_gb300 import api as A
     cfg = I.WORKLOADS["train_f32"]
     tree = A.octree_build(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
@@ -126,14 +172,16 @@ def test_f32_backward_multitile():
     sc = A.Scene(tree, dev(tables), [dev(W) for W in weights], device=DEV)
     x, w = I.uniform_queries(77, 100003)
     assert len(x) // 128 >= 3 * SMS
+    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
+    amb, _ = ambiguous_queries(ot, tables, weights, x, w)
     d_rgb = np.random.default_rng(78).normal(size=(len(x), 3)).astype(np.float32)
+    d_rgb[amb] = 0.0
     dT = torch.zeros(sc.tables.shape, device=DEV)
     dW = torch.zeros(sc.weights.shape, device=DEV)
     A.octa_query_bwd(sc, dev(x), dev(w), dev(d_rgb), [(dT, dW)])
-    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, cfg.R)
     rT, rWs, _ = O.query_backward(ot, tables, weights, x, w, d_rgb)
     errs = tensor_errors(dT.cpu().numpy(), dW.cpu().numpy(), rT, rWs)
-    print("FP32 backward, 782 tiles", [f"{e:.2e}" for e in errs])
+    print(f"FP32 backward, 782 tiles ({int(amb.sum())} queries zeroed)", [f"{e:.2e}" for e in errs])
     assert max(errs) <= 1e-5, errs
 
 

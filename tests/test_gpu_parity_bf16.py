@@ -488,3 +488,33 @@ def test_persistent_step_barrier_timeout_reports_status():
     assert int(status.item()) == 0
     assert not torch.equal(b.states[0].master_t, before)
     assert torch.isfinite(b.states[0].master_t).all()
+
+
+def test_persistent_step_mbarrier_timeout_frees_tensor_memory():
+    """The tensor-core MMAs of every CTA's first tile's first layer are not
+    issued (test hook), so that group's bounded mbarrier wait runs out after
+    its 20 ms limit: the launch returns with OCTA_STATUS_TIMEOUT set and
+    without the optimiser, every CTA having freed its tensor memory -- the
+    next step allocates the tensor memory of every SM again, runs normally
+    and matches a step of an untouched copy."""
+    from paper_2606_08469_gb300 import _lib as L
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.WORKLOADS["train_bf16"]
+    a, _ = WL.train_step_for(cfg, n_pairs=4096, persistent=True)
+    b, _ = WL.train_step_for(cfg, n_pairs=4096, persistent=True)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    before = b.states[0].master_t.clone()
+    b.persistent_step(status=status, timeout_ns=20_000_000, skip_first_mma=1)
+    torch.cuda.synchronize()
+    assert int(status.item()) & L.OCTA_STATUS_TIMEOUT
+    assert torch.equal(b.states[0].master_t, before)       # Adam did not run
+    for s in b.states:                                      # the caller restarts the step
+        s.grad_t.zero_()
+        s.grad_w.zero_()
+    status.zero_()
+    b.persistent_step(status=status)
+    a.persistent_step()
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert abs(b.loss.item() - a.loss.item()) <= 1e-6 * a.loss.item()
+    assert _update_err(b.states[0], a.states[0], before) <= 3e-3

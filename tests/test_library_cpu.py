@@ -22,16 +22,19 @@ def lib():
 
 
 def _declared_functions():
-    txt = open(os.path.join(ROOT, "include", "octaoctree.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    names = re.findall(r"^[A-Za-z_][\w \t\*]*?\b([a-z_][a-z0-9_]*)\s*\([^;{]*\)\s*;", txt, flags=re.M)
+    import glob
+    names = []
+    for path in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        txt = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \t\*]*?\b([a-z_][a-z0-9_]*)\s*\([^;{]*\)\s*;", txt,
+                            flags=re.M)
     return sorted(set(names))
 
 
 def test_header_symbols_exported(lib):
     names = _declared_functions()
     assert {"octree_build", "octa_query_fwd", "octa_query_bwd", "residual_loss",
-            "adam_step"} <= set(names)
+            "adam_step", "octa_measure_ffma"} <= set(names)
     for n in names:
         assert hasattr(lib, n), n
     from paper_2606_08469_gb300 import _lib
@@ -42,7 +45,7 @@ def test_struct_sizes_match_header(lib):
     """The ctypes mirrors have the C layout (checked through a sizing call)."""
     from paper_2606_08469_gb300 import _lib as L
     assert C.sizeof(L.octa_tree_desc) == 4 + 4 + 8 + 4 * 16 + 4 * 17 + 4 + 8 * 17
-    assert lib.octa_abi_version() == 4
+    assert lib.octa_abi_version() == 5
     assert C.sizeof(L.octa_prims) == 8 + 8 + 4 + 4
     assert C.sizeof(L.octa_queries) == 8 + 8 + 8 + 8 * 17 + 8 + 8 + 8 + 4 + 4
     assert C.sizeof(L.octa_predictor) == 8 + 8 + 8 + 4 + 4 + 4 * 16

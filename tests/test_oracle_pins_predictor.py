@@ -163,3 +163,17 @@ def test_predictor_backward_by_central_differences():
         Q[i][a, b] -= h
         assert dWs[i][a, b] == pytest.approx((f(table, P) - f(table, Q)) / (2 * h), rel=1e-5,
                                              abs=1e-9)
+
+
+def test_hash_index_published_primes_worked_examples():
+    """The spatial hash against index values worked out by hand from the
+    published primes (tests/golden/hash_index_mueller2022.txt): a wrong
+    pi_2 or pi_3, or a sum in place of the xor, fails it."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "hash_index_mueller2022.txt")
+    rows = [list(map(int, ln.split())) for ln in open(path)
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 5
+    for i, j, k, res, T, want in rows:
+        assert int(O.hash_index(i, j, k, res, T)) == want, (i, j, k, res, T)
