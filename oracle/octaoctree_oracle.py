@@ -27,6 +27,10 @@ fusion or reordering of its own:
   shifted_features_d_gradient, disparity_backward  training g_psi: the
                     features' derivative with respect to d and g_psi's
                     gradients
+  disparity_gradient  dL/dd of a query through the shifted lookup (Eq. 7-9)
+  shifted_train_gradients  a whole training step's gradients in the shifted
+                    form with the predicted disparity (Eq. 7-9, 14; Section
+                    3.3: d learnt only through the radiance objective)
   mlp_forward       Eq. 13 (decoder; ReLU hidden layers, exp output)
   residual_loss     Eq. 14 with the Monte-Carlo target of Eq. 3 (M = 1)
   residual_loss_multi  Eq. 14 with Eq. 3's M-sample target
@@ -699,13 +703,15 @@ def residual_loss(Lp, Ls, E, w, eps=1e-2, rhs_grad=True, scale=1.0):
 
 
 def query_backward(tree, tables, weights, x, omega, d_rgb, form="cell", attrs=None, normal=None,
-                   disparity=None):
+                   disparity=None, return_dh=False):
     """Gradients of sum(d_rgb * L_hat) w.r.t. the table and the weights.
 
     Decoder: delta_L = d_rgb * exp(z_L); dW_i = delta_i^T a_{i-1};
     delta_{i-1} = (delta_i W_i) * 1[z_{i-1} > 0]; dh = delta_1 W_1.
     Encoding: each present entry k of level l (4 corners in the cell form,
     8 cells x 3 vertices in the full form) receives weight_k * dh_l.
+    Returns (dT, dWs, rgb), and the decoder-input gradient dh [N][width]
+    as a fourth value when return_dh.
     """
     T = np.asarray(tables, dtype=np.float64)
     F = T.shape[1]
@@ -730,6 +736,8 @@ def query_backward(tree, tables, weights, x, omega, d_rgb, form="cell", attrs=No
             for f in range(F):
                 dT[:, f] += np.bincount(a[ok], weights=weight[ok, l, k] * dh[ok, l * F + f],
                                         minlength=len(T))
+    if return_dh:
+        return dT, dWs, rgb, dh
     return dT, dWs, rgb
 
 
@@ -1123,3 +1131,50 @@ def disparity_backward(table, res, weights, x, omega, normal, d_disp):
             for k in range(Fh):
                 dtab[l, :, k] += np.bincount(idx, weights=w * d_in[:, l * Fh + k], minlength=T)
     return dtab, dWs
+
+
+def disparity_gradient(tree, tables, weights, x, omega, normal, disparity, d_rgb, attrs=None):
+    """d/dd_q of sum(d_rgb * L_hat) in the shifted form (Eq. 7-9) for every
+    query q: the decoder's input gradient dh (Eq. 13 back-propagated, as in
+    query_backward) dotted with the query's feature derivative dh/dd
+    (shifted_features_d_gradient); the attributes of Eq. 12 do not depend
+    on d.  The lookup takes d in binary32.  Returns [N] (FP64)."""
+    d32 = np.asarray(disparity, dtype=np.float32)
+    _, _, _, dh = query_backward(tree, tables, weights, x, omega, d_rgb, form="shifted",
+                                 attrs=attrs, normal=normal, disparity=d32, return_dh=True)
+    dhdd = shifted_features_d_gradient(tree, tables, x, omega, normal, d32)
+    return np.sum(dh[:, :dhdd.shape[1]] * dhdd, axis=1)
+
+
+def shifted_train_gradients(tree, tables, weights, predictor, pairs, normal, normal2, eps=1e-2,
+                            rhs_grad=True, scale=1.0, attrs=None):
+    """The gradients of one training step of the paper's full model, before
+    the optimiser: every primary query (x, omega) and secondary query
+    (x', -omega') predicts its disparity d = g_psi(x, omega_r) (Eq. 7; omega_r
+    the reflection about that point's normal), reads the features with the
+    disparity-shifted lookup (Eq. 8-9 with Eq. 6, 10; d rounded to binary32,
+    the precision the lookup decides in) and is decoded (Eq. 13, with the
+    attributes of Eq. 12 when given as [2N][n_attrs], primaries first);
+    Eq. 14 against the one-sample target of Eq. 3 gives the loss.  The
+    disparity is trained only through this objective (Section 3.3): each
+    query's dL/dd (disparity_gradient) back-propagates through g_psi
+    (disparity_backward).  predictor = (hash table [L][T][2], res, weights).
+    Gradients are of scale * loss.  Returns (loss, dT, dWs, d_table, d_Ws_psi,
+    dL/dd [2N], d [2N])."""
+    table, res, pw = predictor
+    n = len(pairs.x)
+    X = np.concatenate([pairs.x, pairs.x2])
+    Om = np.concatenate([pairs.omega, -pairs.omega2])
+    Nr = np.concatenate([normal, normal2])
+    d = disparity(table, res, pw, X, Om, Nr)
+    d32 = d.astype(np.float32)
+    rgb, _ = query_forward(tree, tables, weights, X, Om, form="shifted", normal=Nr,
+                           disparity=d32, attrs=attrs)
+    loss, dLp, dLs = residual_loss(rgb[:n], rgb[n:], pairs.E, pairs.w, eps, rhs_grad, scale)
+    d_rgb = np.concatenate([dLp, dLs])
+    dT, dWs, _, dh = query_backward(tree, tables, weights, X, Om, d_rgb, form="shifted",
+                                    attrs=attrs, normal=Nr, disparity=d32, return_dh=True)
+    dhdd = shifted_features_d_gradient(tree, tables, X, Om, Nr, d32)
+    dd = np.sum(dh[:, :dhdd.shape[1]] * dhdd, axis=1)
+    dtab, dWp = disparity_backward(table, res, pw, X, Om, Nr, dd)
+    return loss, dT, dWs, dtab, dWp, dd, d

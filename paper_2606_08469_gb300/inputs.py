@@ -238,17 +238,34 @@ def training_pairs(seed, n, n_planes=8, n_spheres=8):
     """Training batch: 16 planes/spheres in the unit cube, omega on the
     hemisphere about the normal, omega' uniform, 5% emissive points and a
     U[0,1]^3 BSDF*cos/pdf weight."""
+    return training_pairs_with_normals(seed, n, n_planes, n_spheres)[0]
+
+
+def training_pairs_with_normals(seed, n, n_planes=8, n_spheres=8):
+    """training_pairs (the same draws, so the same pairs) and the surface
+    normals at x and at x' (float32 [n][3] each), which the disparity-
+    shifted lookup reflects its query directions about."""
     g = rng(seed)
     prims = make_primitives(g, n_planes, n_spheres)
     x, nrm = sample_surface_points(g, prims, n)
     om = hemisphere_directions(g, nrm)
-    x2, _ = sample_surface_points(g, prims, n)
+    x2, nrm2 = sample_surface_points(g, prims, n)
     om2 = _unit_vectors(g, n)
     emissive = g.random(n) < 0.05
     E = g.random((n, 3)) * emissive[:, None]
     w = g.random((n, 3))
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
-    return TrainingPairs(f32(x), f32(om), f32(x2), f32(om2), f32(E), f32(w))
+    return TrainingPairs(f32(x), f32(om), f32(x2), f32(om2), f32(E), f32(w)), f32(nrm), f32(nrm2)
+
+
+def predictor_params(seed, levels=8, log2_T=16, table_scale=1e-1):
+    """Parameters of the disparity predictor g_psi: hash tables
+    [levels][2^log2_T][2] uniform in [-table_scale, table_scale] and
+    Xavier-uniform weights of the bias-free MLP (2 levels + 3) -> 64 -> 64
+    -> 1.  The per-level grid resolutions are the caller's."""
+    g = rng(seed)
+    table = g.uniform(-table_scale, table_scale, (levels, 1 << log2_T, 2)).astype(np.float32)
+    return table, make_mlp(seed + 1, [2 * levels + 3, 64, 64, 1])
 
 
 @dataclass
