@@ -143,10 +143,14 @@ typedef struct octa_scene {
  * normalised as v / sqrt(v.v)), evaluated as (x - c_j) d + omega_r in
  * binary32 with one rounding per operation (omega_r = (2 (n.omega)) n -
  * omega; the octahedral map divides by the L1 norm, so no normalisation).
- * octa_encode and, for BF16 decoders, octa_query_fwd and octa_query_bwd
- * evaluate it (the other entry points return OCTA_EUNSUPPORTED); the
- * disparity comes from the caller (octa_disparity computes it with the
- * predictor g_psi) and receives no gradient.                             */
+ * octa_encode, octa_query_fwd, octa_query_bwd and octa_train_fused
+ * evaluate it (FP32 decoders: F = 8; octa_train_step_batched returns
+ * OCTA_EUNSUPPORTED); the disparity comes from the caller (octa_disparity
+ * computes it with the predictor g_psi).  The backward passes can also
+ * return each query's dL/dd (d_disparity), the derivative through every
+ * cell's shifted direction, the octahedral fold and the triangle's
+ * barycentric weights; octa_disparity_bwd carries it into g_psi, which
+ * the paper trains only through the radiance objective (Section 3.3).    */
 #define OCTA_FORM_SHIFTED 2
 
 /* Queries: scene s answers queries [scene_start[s], scene_start[s+1]).   */
@@ -165,6 +169,10 @@ typedef struct octa_queries {
   const float* attrs;          /* device [n][n_attrs]                       */
   int32_t n_attrs;             /* 0..OCTA_MAX_ATTRS                         */
   int32_t reserved_q;
+  /* octa_query_bwd in the shifted form: written with dL/dd of every query,
+   * the gradient (of the same loss as the table and weight gradients)
+   * with respect to its disparity; NULL: not computed.                    */
+  float* d_disparity;          /* device [n]                                */
 } octa_queries;
 #define OCTA_MAX_ATTRS 16
 
@@ -301,6 +309,19 @@ typedef struct octa_predictor {
 int octa_disparity(const octa_predictor* pred, const octa_queries* q, float* disparity,
                    void* stream);
 
+/* octa_disparity_bwd -- g_psi's backward (Section 3.3: d is trained through
+ * the radiance objective alone): the gradients of sum_q d_disp[q] d_q with
+ * respect to the hash tables and the MLP weights.  Recomputes the forward in
+ * FP32 on the CUDA cores (pred->weights; weights_bf16 is not read), back-
+ * propagates through exp (dd/dz = d) and the ReLU layers, and scatter-adds
+ * each level's two feature gradients into its cell's eight vertices with the
+ * trilinear weights (float2 atomics).  ACCUMULATES (+=) into d_table
+ * (device float32, layout of pred->table, 8-byte aligned) and d_weights
+ * (device float32, layout of pred->weights), which the caller zeroes.
+ * d_disp: device [n] float32 (the shifted backward's d_disparity).        */
+int octa_disparity_bwd(const octa_predictor* pred, const octa_queries* q, const float* d_disp,
+                       float* d_table, float* d_weights, void* stream);
+
 /* ---- the training regime of Section 4: M RHS samples per LHS sample ---- */
 
 /* residual_loss_multi -- Eq. 14 against Eq. 3's M-sample target:
@@ -369,6 +390,16 @@ typedef struct octa_pairs {
    * so that its loss and gradients are its shard's share of the batch's and
    * the ranks' sums are the batch's.                                        */
   int64_t norm_pairs[OCTA_MAX_SCENES];
+  /* the shifted form only (NULL otherwise): the primary and secondary
+   * queries' normals [n][3] and disparities [n], and (nullable) outputs
+   * d_disparity / d_disparity2 [n] written with each query's dL/dd (the
+   * gradient of S * loss, as the table and weight gradients).             */
+  const float* normal;
+  const float* normal2;
+  const float* disparity;
+  const float* disparity2;
+  float* d_disparity;
+  float* d_disparity2;
 } octa_pairs;
 
 /* octa_train_fused -- octa_query_fwd + residual_loss + octa_query_bwd of a

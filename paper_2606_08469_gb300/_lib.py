@@ -80,6 +80,7 @@ class octa_queries(C.Structure):
         ("attrs", C.c_void_p),
         ("n_attrs", C.c_int32),
         ("reserved_q", C.c_int32),
+        ("d_disparity", C.c_void_p),
     ]
 
 
@@ -98,6 +99,12 @@ class octa_pairs(C.Structure):
         ("n", C.c_int64),
         ("scene_start", C.c_int64 * (OCTA_MAX_SCENES + 1)),
         ("norm_pairs", C.c_int64 * OCTA_MAX_SCENES),
+        ("normal", C.c_void_p),
+        ("normal2", C.c_void_p),
+        ("disparity", C.c_void_p),
+        ("disparity2", C.c_void_p),
+        ("d_disparity", C.c_void_p),
+        ("d_disparity2", C.c_void_p),
     ]
 
 
@@ -191,6 +198,8 @@ _SIGNATURES = {
     "octa_trace_rays": (C.c_int, [C.POINTER(octa_prims), _P, C.c_int32, _P, C.c_int64, C.c_float,
                                   _P, _P, _P, _P, _P]),
     "octa_disparity": (C.c_int, [C.POINTER(octa_predictor), C.POINTER(octa_queries), _P, _P]),
+    "octa_disparity_bwd": (C.c_int, [C.POINTER(octa_predictor), C.POINTER(octa_queries), _P, _P,
+                                     _P, _P]),
     "adam_step": (C.c_int, [C.POINTER(octa_param_group), C.c_int32, C.POINTER(octa_adam_cfg), _P,
                             _P, C.c_size_t, _P]),
     "octa_workspace_bytes": (C.c_size_t, [C.c_int32, C.c_int64]),

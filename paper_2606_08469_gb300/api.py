@@ -230,13 +230,16 @@ def octa_query_fwd(scenes, x, omega, counts=None, want_nodes=False, want_addr=Fa
 
 
 def octa_query_bwd(scenes, x, omega, d_rgb, grads, counts=None, status=None, stream=None,
-                   attrs=None, normal=None, disparity=None):
-    """grads: list of (d_tables fp32, d_weights fp32) per scene; accumulated."""
+                   attrs=None, normal=None, disparity=None, d_disparity=None):
+    """grads: list of (d_tables fp32, d_weights fp32) per scene; accumulated.
+    d_disparity [n] (shifted form, optional) receives dL/dd per query."""
     arr, ns = _scene_array(scenes)
     g = (L.octa_scene_grads * ns)(*[L.octa_scene_grads(dt.data_ptr(), dw.data_ptr())
                                     for dt, dw in grads])
+    n = int(x.shape[0])
     q = _queries(x, omega, counts)
-    _set_extras(q, int(x.shape[0]), normal, disparity, attrs)
+    _set_extras(q, n, normal, disparity, attrs)
+    q.d_disparity = d_disparity.data_ptr() if d_disparity is not None and n else None
     L.check(_lib().octa_query_bwd(arr, ns, C.byref(q), _ptr(d_rgb), g, _ptr(status),
                                   _stream(stream)), "octa_query_bwd")
 
@@ -247,10 +250,22 @@ def _set_norm(pr, norm_pairs):
             pr.norm_pairs[i] = int(m)
 
 
+def _set_shift(pr, n, shift):
+    """The shifted form's pair inputs and outputs: shift = (normal, normal2,
+    disparity, disparity2, d_disparity or None, d_disparity2 or None)."""
+    if shift is None:
+        return
+    names = ("normal", "normal2", "disparity", "disparity2", "d_disparity", "d_disparity2")
+    for nm, t in zip(names, shift):
+        setattr(pr, nm, t.data_ptr() if t is not None and n else None)
+
+
 def octa_train_fused(scenes, x, omega, x2, omega2, E, w, grads, loss_out, counts=None, eps=1e-2,
-                     rhs_grad=True, scaler=None, status=None, stream=None, norm_pairs=None):
+                     rhs_grad=True, scaler=None, status=None, stream=None, norm_pairs=None,
+                     shift=None):
     """Fused forward + Eq. 14 loss + backward over training pairs (BF16
-    decoders on the tensor cores, FP32 decoders on the FP32 engine)."""
+    decoders on the tensor cores, FP32 decoders on the FP32 engine); shift:
+    the shifted form's tensors (_set_shift)."""
     arr, ns = _scene_array(scenes)
     g = (L.octa_scene_grads * ns)(*[L.octa_scene_grads(dt.data_ptr(), dw.data_ptr())
                                     for dt, dw in grads])
@@ -265,6 +280,7 @@ def octa_train_fused(scenes, x, omega, x2, omega2, E, w, grads, loss_out, counts
         acc += c
         pr.scene_start[i + 1] = acc
     _set_norm(pr, norm_pairs)
+    _set_shift(pr, n, shift)
     L.check(_lib().octa_train_fused(arr, ns, C.byref(pr), C.c_float(eps), int(bool(rhs_grad)),
                                     _ptr(scaler), _ptr(loss_out), g, _ptr(status), _stream(stream)),
             "octa_train_fused")
@@ -424,6 +440,17 @@ def octa_disparity(pred, x, omega, normal, out=None, stream=None):
     L.check(_lib().octa_disparity(C.byref(pc), C.byref(q), _ptr(out), _stream(stream)),
             "octa_disparity")
     return out
+
+
+def octa_disparity_bwd(pred, x, omega, normal, d_disp, d_table, d_weights, stream=None):
+    """g_psi's backward: accumulates the gradients of sum_q d_disp[q] d_q into
+    d_table (layout of pred.table) and d_weights (layout of pred.weights)."""
+    n = int(x.shape[0])
+    q = _queries(x, omega, None)
+    q.normal = normal.data_ptr() if n else None
+    pc = pred.as_c()
+    L.check(_lib().octa_disparity_bwd(C.byref(pc), C.byref(q), _ptr(d_disp), _ptr(d_table),
+                                      _ptr(d_weights), _stream(stream)), "octa_disparity_bwd")
 
 
 @dataclass

@@ -17,7 +17,7 @@
 // LDA = QT + 4 floats, so every GEMM operand read is a 16-byte vector and
 // rows of neighbouring features fall into different banks.
 #pragma once
-#include "octa_device.cuh"
+#include "gather.cuh"
 
 namespace octa {
 namespace f32 {
@@ -365,28 +365,51 @@ __device__ __forceinline__ void load_weights(const DevScene& sc, float* wsm) {
 // l's cell is c >> (15 - l) with c = min(floor(x * 2^15), 2^15 - 1) per axis.
 // In the trilinear vertex form (Eq. 10) every level needs eight cells, so the
 // walk is left to the (query, level) items: rows 0-2 of node_sm then hold the
-// clamped position (as floats) and row 3 the query's validity (0 / -1).
-template <int KMAX>
+// clamped position (as floats) and row 3 the query's validity (0 / -1).  The
+// shifted form (Eq. 7-9) also keeps omega_r (rows 4-5 of node_sm and row 0
+// of u_sm) and the disparity (row 1 of u_sm), read from nrm / dsp at index
+// gqs, the query's row of those arrays.
+template <int KMAX, bool SHIFT>
 __device__ __forceinline__ void locate_tile(const QueryParams& p, const DevScene& sc,
                                             const int2* tree, const QueryIn& in, int64_t q0,
-                                            int nq, int* node_sm, float* u_sm) {
-  static_assert(KMAX >= 4, "the full form keeps positions and validity in four rows");
+                                            int nq, int* node_sm, float* u_sm,
+                                            const float* nrm = nullptr, const float* dsp = nullptr,
+                                            int64_t gqs = 0) {
+  static_assert(KMAX >= 6, "the shifted form keeps positions, validity and omega_r in six rows");
   const int q = threadIdx.x;
   if (q >= QT) return;
   const bool valid = q < nq;
   const int64_t gq = q0 + q;
+  if (sc.query_form != OCTA_FORM_CELL_BILINEAR) {  // the items look up their own cells
+    float* xs = reinterpret_cast<float*>(node_sm);  // [3][QT] positions
+    xs[q] = clamp01(in.x0);
+    xs[QT + q] = clamp01(in.x1);
+    xs[2 * QT + q] = clamp01(in.x2);
+    node_sm[3 * QT + q] = valid ? 0 : -1;           // validity of the query
+    if (SHIFT && sc.query_form == OCTA_FORM_SHIFTED) {
+      float wr[3] = {0.f, 0.f, 1.f}, disp = 0.f;
+      if (valid) {
+        const float w0[3] = {in.w0, in.w1, in.w2};
+        const float n0[3] = {nrm[3 * gqs], nrm[3 * gqs + 1], nrm[3 * gqs + 2]};
+        reflect_f32_rn(w0, n0, wr);
+        disp = dsp[gqs];
+      }
+      xs[4 * QT + q] = wr[0];
+      xs[5 * QT + q] = wr[1];
+      u_sm[q] = wr[2];
+      u_sm[QT + q] = disp;
+      return;
+    }
+    float ux, uy;
+    octa_fold(in.w0, in.w1, in.w2, ux, uy);
+    u_sm[q] = ux;
+    u_sm[QT + q] = uy;
+    return;
+  }
   float ux, uy;
   octa_fold(in.w0, in.w1, in.w2, ux, uy);
   u_sm[q] = ux;
   u_sm[QT + q] = uy;
-  if (sc.query_form == OCTA_FORM_TRILINEAR_VERTEX) {  // the items look up their own cells
-    float* xs = reinterpret_cast<float*>(node_sm);    // [3][QT] positions (KMAX >= 3 rows)
-    xs[q] = clamp01(in.x0);
-    xs[QT + q] = clamp01(in.x1);
-    xs[2 * QT + q] = clamp01(in.x2);
-    node_sm[3 * QT + q] = valid ? 0 : -1;             // validity of the query
-    return;
-  }
   const int cx = min(static_cast<int>(clamp01(in.x0) * 32768.f), 32767);
   const int cy = min(static_cast<int>(clamp01(in.x1) * 32768.f), 32767);
   const int cz = min(static_cast<int>(clamp01(in.x2) * 32768.f), 32767);
@@ -430,13 +453,14 @@ __device__ __forceinline__ int64_t map_base(const QueryParams& p, const DevScene
 // (levels past the scene's K: Eq. 12's attributes, else zeros).  In
 // the trilinear vertex form the item blends the 8 x 3 vertex features of
 // full_form_level (Eq. 6, 10; texel_addr rows of 24 entries a level).
-template <int F, typename TT>
+template <int F, typename TT, bool SHIFT>
 __device__ __forceinline__ void gather_tile(const QueryParams& p, const DevScene& sc,
                                             const int2* tree, int64_t q0, int nq, int nlev,
                                             const int* node_sm,
                                             const float* u_sm, float* h, int ld_feat, int ld_q) {
-  if (sc.query_form == OCTA_FORM_TRILINEAR_VERTEX) {
+  if (sc.query_form != OCTA_FORM_CELL_BILINEAR) {
     const float* xsm = reinterpret_cast<const float*>(node_sm);
+    const bool shifted = SHIFT && sc.query_form == OCTA_FORM_SHIFTED;
     for (int it = threadIdx.x; it < nlev * QT; it += NT) {
       const int l = it / QT, q = it % QT;
       float v[F];
@@ -447,8 +471,14 @@ __device__ __forceinline__ void gather_tile(const QueryParams& p, const DevScene
                           ? p.texel_addr + ((q0 + q) * p.kmax_out + l) * 24 : nullptr;
       if (on) {
         const float xs[3] = {xsm[q], xsm[QT + q], xsm[2 * QT + q]};
+        const float wr[3] = {xsm[4 * QT + q], xsm[5 * QT + q], u_sm[q]};
+        const float disp = u_sm[QT + q];
         FullLevel fl;
-        full_form_level(p, sc, tree, xs, u_sm[q], u_sm[QT + q], l, fl);
+        int c0[3];
+        if (shifted)
+          cells_form_level(p, sc, tree, xs, l, c0, fl);
+        else
+          full_form_level(p, sc, tree, xs, u_sm[q], u_sm[QT + q], l, fl);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           if (fl.base[j] < 0) {
@@ -456,6 +486,7 @@ __device__ __forceinline__ void gather_tile(const QueryParams& p, const DevScene
               for (int k = 0; k < 3; ++k) aout[3 * j + k] = -1;
             continue;
           }
+          if (shifted) shifted_cell_vertex(sc, xs, wr, disp, l, c0, j, fl);
           float t[3][F];
 #pragma unroll
           for (int k = 0; k < 3; ++k)
@@ -535,10 +566,13 @@ __device__ __forceinline__ void gather_tile(const QueryParams& p, const DevScene
 // Phase 4 (BWD): d_tables[texel] += w_k * dh_l for the 4 corners of every
 // present level (float4 vector atomics); in the trilinear vertex form for the
 // 24 vertices of a level, weight = renormalised cell weight x barycentric.
-template <int KMAX, int F>
+// In the shifted form with dd_sm non-NULL, every item also adds its level's
+// share of dL/dd, sum over cells and vertices of wn_j (d b_k / d d)
+// <t_jk, dh_l>, into dd_sm[q] (shared memory, zeroed by the caller).
+template <int KMAX, int F, typename TT, bool SHIFT>
 __device__ __forceinline__ void scatter_tile(const QueryParams& p, const DevScene& sc,
                                              const int2* tree, const int* node_sm, const float* u_sm,
-                                             const float* dh) {
+                                             const float* dh, float* dd_sm = nullptr) {
   if (sc.query_form == OCTA_FORM_TRILINEAR_VERTEX) {
     const float* xsm = reinterpret_cast<const float*>(node_sm);
     for (int it = threadIdx.x; it < KMAX * QT; it += NT) {
@@ -562,6 +596,52 @@ __device__ __forceinline__ void scatter_tile(const QueryParams& p, const DevScen
           }
         }
       }
+    }
+    return;
+  }
+  if (SHIFT && sc.query_form == OCTA_FORM_SHIFTED) {
+    const float* xsm = reinterpret_cast<const float*>(node_sm);
+    for (int it = threadIdx.x; it < KMAX * QT; it += NT) {
+      const int l = it / QT, q = it % QT;
+      if (node_sm[3 * QT + q] < 0 || l >= sc.K) continue;
+      const float xs[3] = {xsm[q], xsm[QT + q], xsm[2 * QT + q]};
+      const float wr[3] = {xsm[4 * QT + q], xsm[5 * QT + q], u_sm[q]};
+      const float disp = u_sm[QT + q];
+      float g[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) g[f] = dh[(l * F + f) * LDA + q];
+      FullLevel fl;
+      int c0[3];
+      cells_form_level(p, sc, tree, xs, l, c0, fl);
+      float dd = 0.f;
+#pragma unroll 1
+      for (int j = 0; j < 8; ++j) {
+        if (fl.base[j] < 0) continue;
+        float db[3];
+        if (dd_sm)
+          shifted_cell_vertex_dd(sc, xs, wr, disp, l, c0, j, fl, db);
+        else
+          shifted_cell_vertex(sc, xs, wr, disp, l, c0, j, fl);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float w = fl.wn[j] * fl.b[k];
+          const int64_t e = int64_t(fl.base[j] + fl.vidx[k]);
+#pragma unroll
+          for (int c = 0; c < F / 4; ++c)
+            atomicAdd(reinterpret_cast<float4*>(sc.d_tables + e * F) + c,
+                      make_float4(w * g[4 * c], w * g[4 * c + 1], w * g[4 * c + 2],
+                                  w * g[4 * c + 3]));
+          if (dd_sm) {
+            float t[F];
+            TexelLoad<TT, F>::load(sc.tables, e, t);
+            float dot = 0.f;
+#pragma unroll
+            for (int f = 0; f < F; ++f) dot = fmaf(t[f], g[f], dot);
+            dd = fmaf(fl.wn[j] * db[k], dot, dd);
+          }
+        }
+      }
+      if (dd_sm) atomicAdd(dd_sm + q, dd);
     }
     return;
   }
@@ -612,7 +692,7 @@ __device__ __forceinline__ void flush_loss_f64(double& acc, double* loss, int64_
 // secondary queries (x2, omega2); after the forward the Eq. 14 gradient of
 // every pair is formed in the tile from the two radiances, and the backward
 // runs on it directly (only the loss value leaves the CTA, as FP64 partials).
-template <class S, typename TT, bool TRAIN = false>
+template <class S, typename TT, bool TRAIN = false, bool SHIFT = false>
 __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ QueryParams p) {
   static_assert(!TRAIN || S::BWD, "the training pass runs the backward");
   constexpr int PR = QT / 2;            // pairs per tile (TRAIN)
@@ -642,6 +722,10 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
   const bool primary = !TRAIN || threadIdx.x < PR;
   const float* xs = primary ? p.x : p.x2;
   const float* ws = primary ? p.omega : p.omega2;
+  const float* nrm = primary ? p.normal : p.normal2;  // the shifted form's inputs
+  const float* dsp = primary ? p.disparity : p.disparity2;
+  float* d_dsp = primary ? p.d_disparity : p.d_disparity2;  // its dL/dd out (nullable)
+  __shared__ float dd_sm[QT];
   auto tile_query = [&](int64_t tile) {
     const DevScene& sc = p.sc[scene_of_tile(p, tile)];
     const int64_t gq = sc.q_begin + (tile - sc.tile_begin) * ROWS + qrow;
@@ -669,12 +753,16 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * ROWS;
     const int nq = static_cast<int>(sc.q_end - q0 < ROWS ? sc.q_end - q0 : int64_t(ROWS));
     float* h = S::BWD ? act_bwd(0) : buf[0];
+    const bool want_dd = SHIFT && S::BWD && sc.query_form == OCTA_FORM_SHIFTED &&
+                         (p.d_disparity || p.d_disparity2);
+    if (want_dd && threadIdx.x < QT) dd_sm[threadIdx.x] = 0.f;
     if (TRAIN)  // rows of both halves are valid for the tile's nq pairs
-      locate_tile<S::KMAX>(p, sc, tree, in, q0, threadIdx.x < PR ? nq : PR + nq, node_sm, u_sm);
+      locate_tile<S::KMAX, SHIFT>(p, sc, tree, in, q0, threadIdx.x < PR ? nq : PR + nq, node_sm, u_sm,
+                           nrm, dsp, q0 + qrow);
     else
-      locate_tile<S::KMAX>(p, sc, tree, in, q0, nq, node_sm, u_sm);
+      locate_tile<S::KMAX, SHIFT>(p, sc, tree, in, q0, nq, node_sm, u_sm, nrm, dsp, q0 + qrow);
     __syncthreads();
-    gather_tile<S::F, TT>(p, sc, tree, q0, nq, S::KMAX, node_sm, u_sm, h, LDA, 1);
+    gather_tile<S::F, TT, SHIFT>(p, sc, tree, q0, nq, S::KMAX, node_sm, u_sm, h, LDA, 1);
     __syncthreads();
 
     // ---- decoder forward (Eq. 13)
@@ -801,7 +889,12 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
                                         act_bwd(i));
       __syncthreads();
     }
-    scatter_tile<S::KMAX, S::F>(p, sc, tree, node_sm, u_sm, act_bwd(0));
+    scatter_tile<S::KMAX, S::F, TT, SHIFT>(p, sc, tree, node_sm, u_sm, act_bwd(0),
+                                    want_dd ? dd_sm : nullptr);
+    if (want_dd) {  // the shifted form's dL/dd of the tile's queries
+      __syncthreads();
+      if (threadIdx.x < QT && d_dsp && qrow < nq) d_dsp[q0 + qrow] = dd_sm[threadIdx.x];
+    }
   }
   if (S::BWD && cur >= 0) g.flush(p.sc[cur]);
   if (TRAIN && cur >= 0) flush_loss_f64(loss_acc, p.loss + cur, p.sc[cur].norm_pairs);

@@ -16,6 +16,9 @@ enum class Mode {
 // Picks the built shape for the scenes' widths and launches the engine.
 int dispatch(const octa_scene* scenes, int n_scenes, const QueryParams& p, Mode mode,
              cudaStream_t stream);
+// The same for scenes in the shifted form (its own instances).
+int dispatch_shifted(const octa_scene* scenes, int n_scenes, const QueryParams& p, Mode mode,
+                     cudaStream_t stream);
 
 }  // namespace f32
 }  // namespace octa

@@ -258,23 +258,80 @@ __device__ __forceinline__ float2 hash_level(const float2* __restrict__ tab, con
   return make_float2(s0, s1);
 }
 
-// Cell j's triangle in the shifted form: the direction v_j = (x - c_j) d +
-// omega_r (Eq. 9; c_j = (c0 + offset_j + 1/2) 2^-l, exact), folded, and its
+// Cell j's shifted direction v_j = (x - c_j) d + omega_r (Eq. 9; c_j =
+// (c0 + offset_j + 1/2) 2^-l, exact) and e = x - c_j, one rounding per
+// operation.
+__device__ __forceinline__ void shifted_dir(const float (&xs)[3], const float (&wr)[3], float disp,
+                                            int l, const int (&c0)[3], int j, float (&dir)[3],
+                                            float (&e)[3]) {
+  const float scale = __int_as_float((127 - l) << 23);  // 2^-l
+  const int cj[3] = {c0[0] + (j & 1), c0[1] + ((j >> 1) & 1), c0[2] + (j >> 2)};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float c = __fmul_rn(__fadd_rn(static_cast<float>(cj[a]), 0.5f), scale);
+    e[a] = __fsub_rn(xs[a], c);
+    dir[a] = __fadd_rn(__fmul_rn(e[a], disp), wr[a]);
+  }
+}
+
+// Cell j's triangle in the shifted form: the direction v_j, folded, and its
 // triangle and barycentric weights on the level's vertex map (vidx, b of fl).
 __device__ __forceinline__ void shifted_cell_vertex(const DevScene& sc, const float (&xs)[3],
                                                     const float (&wr)[3], float disp, int l,
                                                     const int (&c0)[3], int j, FullLevel& fl) {
-  const float scale = __int_as_float((127 - l) << 23);  // 2^-l
-  const int cj[3] = {c0[0] + (j & 1), c0[1] + ((j >> 1) & 1), c0[2] + (j >> 2)};
-  float dir[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float c = __fmul_rn(__fadd_rn(static_cast<float>(cj[a]), 0.5f), scale);
-    dir[a] = __fadd_rn(__fmul_rn(__fsub_rn(xs[a], c), disp), wr[a]);
-  }
+  float dir[3], e[3];
+  shifted_dir(xs, wr, disp, l, c0, j, dir, e);
   float ux, uy;
   octa_fold(dir[0], dir[1], dir[2], ux, uy);
   full_vertex(ux, uy, sc.R[l], fl);
+}
+
+// shifted_cell_vertex, and the derivative of its barycentric weights in the
+// disparity (Eq. 9 differentiated on the triangle the lookup chose):
+// dv/dd = x - c_j; the octahedral map u = (v_x, v_y) / |v|_1 (Eq. 4) has
+// du_a/dv = (e_a - u_a sgn(v)) / |v|_1, and the fold of Eq. 5 (v_z < 0)
+// turns (u_x, u_y) into ((1 - |u_y|) sgn u_x, (1 - |u_x|) sgn u_y), whose
+// derivatives are those of (u_y, u_x) times -sgn(u_x) sgn(u_y); the map
+// position is p = (u / 2 + 1 / 2) N, and each triangle's weights are
+// affine in p's fractions (full_vertex) with the constant gradients used
+// below.  db[k] = d b_k / d d, in binary32.
+__device__ __forceinline__ void shifted_cell_vertex_dd(const DevScene& sc, const float (&xs)[3],
+                                                       const float (&wr)[3], float disp, int l,
+                                                       const int (&c0)[3], int j, FullLevel& fl,
+                                                       float (&db)[3]) {
+  float dir[3], e[3];
+  shifted_dir(xs, wr, disp, l, c0, j, dir, e);
+  float ux, uy;
+  octa_fold(dir[0], dir[1], dir[2], ux, uy);
+  full_vertex(ux, uy, sc.R[l], fl);
+  const float s = fabsf(dir[0]) + fabsf(dir[1]) + fabsf(dir[2]);
+  const float is = s > 0.f ? 1.f / s : 0.f;
+  const float a = dir[0] * is, b = dir[1] * is;
+  const float g = (dir[0] >= 0.f ? e[0] : -e[0]) + (dir[1] >= 0.f ? e[1] : -e[1]) +
+                  (dir[2] >= 0.f ? e[2] : -e[2]);
+  float dux = (e[0] - a * g) * is, duy = (e[1] - b * g) * is;
+  if (dir[2] < 0.f) {  // the fold: swapped rows, factor -sgn(a) sgn(b)
+    const float m = ((a >= 0.f) == (b >= 0.f)) ? -1.f : 1.f;
+    const float t = dux;
+    dux = m * duy;
+    duy = m * t;
+  }
+  const float hN = 0.5f * static_cast<float>(sc.R[l] - 1);
+  const float px = hN * dux, py = hN * duy;
+  switch (fl.tri) {
+    case 0:  // b = (1 - fx - fy, fx, fy)
+      db[0] = -px - py, db[1] = px, db[2] = py;
+      break;
+    case 1:  // b = (fx + fy - 1, 1 - fy, 1 - fx)
+      db[0] = px + py, db[1] = -py, db[2] = -px;
+      break;
+    case 2:  // b = (1 - fx, fx - fy, fy)
+      db[0] = -px, db[1] = px - py, db[2] = py;
+      break;
+    default:  // b = (1 - fy, fy - fx, fx)
+      db[0] = -py, db[1] = py - px, db[2] = px;
+      break;
+  }
 }
 
 // The shifted form of one query per thread (encoding kernel): per level the
@@ -283,19 +340,21 @@ __device__ __forceinline__ void shifted_cell_vertex(const DevScene& sc, const fl
 // triangle of v_j on the cell's vertex map and the blend of its 3 vertices
 // (Eq. 6) with the renormalised trilinear weight (Eq. 10); store(l, v) for
 // every l < KP as gather_full_query, texel_addr rows of 24 entries.
+// nrm / disp: the normal and disparity arrays query gq indexes.
 template <int F, typename TT, int KP, class Store>
 __device__ __forceinline__ void gather_shifted_query(const QueryParams& p, const DevScene& sc,
                                                      const int2* tree, const QueryIn& in,
-                                                     int64_t gq, bool valid, Store&& store) {
+                                                     int64_t gq, bool valid, const float* nrm,
+                                                     const float* disparity, Store&& store) {
   const float xs[3] = {clamp01(in.x0), clamp01(in.x1), clamp01(in.x2)};
   const bool want_addr = p.texel_addr != nullptr && valid;
   int done = 0;
   if (valid) {
     const float w0[3] = {in.w0, in.w1, in.w2};
-    const float n0[3] = {p.normal[3 * gq], p.normal[3 * gq + 1], p.normal[3 * gq + 2]};
+    const float n0[3] = {nrm[3 * gq], nrm[3 * gq + 1], nrm[3 * gq + 2]};
     float wr[3];
     reflect_f32_rn(w0, n0, wr);
-    const float disp = p.disparity[gq];
+    const float disp = disparity[gq];
     visit_cell_levels<KP, false>(p, sc, tree, xs, [&](int l, const int (&c0)[3], FullLevel& fl) {
       float v[F];
 #pragma unroll

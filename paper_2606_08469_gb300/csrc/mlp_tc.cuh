@@ -101,11 +101,13 @@ __device__ void load_weights_bf16(const DevScene& sc, uint8_t* smem, int nthread
 // operand tile (canonical K-major, one 16-byte store per level for F = 8);
 // FORM: the query form (the trilinear vertex and shifted forms gather one
 // query per thread).  Columns past the K levels take Eq. 12's attributes.
+// nrm / disp: the shifted form's normal and disparity arrays of query gq.
 template <class S, typename TT, int TPQ = 1, int FORM = OCTA_FORM_CELL_BILINEAR>
 __device__ __forceinline__ void locate_gather_bf16(const QueryParams& p, const DevScene& sc,
                                                    const int2* tree, const QueryIn& in, int64_t gq,
                                                    bool valid, int par, uint8_t* act, int* base_sm,
-                                                   float* u_sm, int q) {
+                                                   float* u_sm, int q, const float* nrm = nullptr,
+                                                   const float* disp = nullptr) {
   constexpr int F = S::F;
   auto store = [&](int l, const float (&v0)[F]) {
     float v[F];
@@ -129,7 +131,7 @@ __device__ __forceinline__ void locate_gather_bf16(const QueryParams& p, const D
   };
   if constexpr (FORM == OCTA_FORM_SHIFTED) {
     static_assert(TPQ == 1, "the shifted form gathers one query per thread");
-    gather_shifted_query<F, TT, S::KPAD>(p, sc, tree, in, gq, valid, store);
+    gather_shifted_query<F, TT, S::KPAD>(p, sc, tree, in, gq, valid, nrm, disp, store);
   } else if constexpr (FORM == OCTA_FORM_TRILINEAR_VERTEX) {
     static_assert(TPQ == 1, "the full form gathers one query per thread");
     gather_full_query<F, TT, S::KPAD>(p, sc, tree, in, gq, valid, store);
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(NT * TPQ, 4)
       predictor_gather<S>(p, in, q0 + q, q < nq, act, q);
     else
       locate_gather_bf16<S, TT, TPQ, FORM>(p, sc, tree, in, q0 + q, q < nq, par, act, nullptr,
-                                           nullptr, q);
+                                           nullptr, q, p.normal, p.disparity);
     fence_proxy_async();
     __syncthreads();
 
@@ -744,6 +746,9 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   const bool primary = !TRAIN || t < ROWS;
   const float* xs = primary ? p.x : p.x2;
   const float* ws = primary ? p.omega : p.omega2;
+  const float* nrm = primary ? p.normal : p.normal2;  // the shifted form's inputs
+  const float* dsp = primary ? p.disparity : p.disparity2;
+  float* d_dsp = primary ? p.d_disparity : p.d_disparity2;  // its dL/dd out (nullable)
   auto item_query = [&](int64_t item) {  // this thread's query of an item, prefetched
     int s = 0;
     while (s + 1 < p.n_scenes && item >= p.item_begin[s + 1]) ++s;
@@ -800,7 +805,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
             p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), nullptr, nullptr, t);
       else if (shifted)
         locate_gather_bf16<S, TT, 1, OCTA_FORM_SHIFTED>(
-            p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), nullptr, nullptr, t);
+            p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), nullptr, nullptr, t, nrm, dsp);
       else
         locate_gather_bf16<S, TT>(p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), base_sm,
                                   u_sm, t);
@@ -1044,16 +1049,23 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
           if (valid) {
             const float xs[3] = {clamp01(qry.x0), clamp01(qry.x1), clamp01(qry.x2)};
             const float w0[3] = {qry.w0, qry.w1, qry.w2};
-            const float n0[3] = {p.normal[3 * gq], p.normal[3 * gq + 1], p.normal[3 * gq + 2]};
+            const float n0[3] = {nrm[3 * gq], nrm[3 * gq + 1], nrm[3 * gq + 2]};
             float wr[3];
             reflect_f32_rn(w0, n0, wr);
-            const float disp = p.disparity[gq];
+            const float disp = dsp[gq];
+            // dL/dd = sum over levels, cells and vertices of
+            // wn_j (d b_k / d d) <t_jk, dh_l> (the texels read again)
+            float dd = 0.f;
             visit_cell_levels<S::KPAD, false>(p, sc, tree, xs,
                                               [&](int l, const int (&c0)[3], FullLevel& fl) {
 #pragma unroll 1
               for (int j = 0; j < 8; ++j) {
                 if (fl.base[j] < 0) continue;
-                shifted_cell_vertex(sc, xs, wr, disp, l, c0, j, fl);
+                float db[3];
+                if (d_dsp)
+                  shifted_cell_vertex_dd(sc, xs, wr, disp, l, c0, j, fl, db);
+                else
+                  shifted_cell_vertex(sc, xs, wr, disp, l, c0, j, fl);
 #pragma unroll
                 for (int c4 = 0; c4 < S::F / 4; ++c4) {
                   const float g0 = dh[l * S::F + 4 * c4 + 0];
@@ -1068,8 +1080,20 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
                     atomicAdd(dst, make_float4(w * g0, w * g1, w * g2, w * g3));
                   }
                 }
+                if (d_dsp) {
+#pragma unroll
+                  for (int k = 0; k < 3; ++k) {
+                    TexelRaw<TT, S::F> tx;
+                    tx.load(sc.tables, uint32_t(fl.base[j] + fl.vidx[k]));
+                    float dot = 0.f;
+#pragma unroll
+                    for (int f = 0; f < S::F; ++f) dot = fmaf(tx.get(f), dh[l * S::F + f], dot);
+                    dd = fmaf(fl.wn[j] * db[k], dot, dd);
+                  }
+                }
               }
             });
+            if (d_dsp) d_dsp[gq] = dd;
           }
         }
       }

@@ -69,9 +69,17 @@ struct QueryParams {
   // in nodes (0: walk in global memory) and byte offset in dynamic memory
   int32_t tree_cap;
   int32_t tree_off;
-  // the shifted form's per-query inputs (normal [n][3], disparity [n])
+  // the shifted form's per-query inputs (normal [n][3], disparity [n]); in
+  // the fused training pass those of the primaries, the secondaries' in
+  // normal2 / disparity2
   const float* normal;
   const float* disparity;
+  const float* normal2;
+  const float* disparity2;
+  // the shifted form's backward: dL/dd per query (nullable), the fused
+  // training pass's secondaries in d_disparity2
+  float* d_disparity;
+  float* d_disparity2;
   // Eq. 12's attributes [n][n_attrs], decoder input columns K*F .. K*F+n_attrs-1
   const float* attrs;
   int32_t n_attrs;
@@ -327,6 +335,7 @@ struct FullLevel {
   float wn[8];
   int vidx[3];
   float b[3];
+  int tri;  // which of the four triangle shapes holds the point (see full_vertex)
 };
 
 // Direction part of one level: the triangle of the vertex map holding u and
@@ -341,21 +350,27 @@ __device__ __forceinline__ void full_vertex(float ux, float uy, int V, FullLevel
   const float fx = __fsub_rn(px, static_cast<float>(i0));
   const float fy = __fsub_rn(py, static_cast<float>(j0));
   int oi[3], oj[3];
+  // tri: 0 / 1 the lower-left / upper-right triangle of an anti-diagonal
+  // split, 2 / 3 the lower-right / upper-left one of a main-diagonal split
   if ((i0 >= N / 2) == (j0 >= N / 2)) {  // anti-diagonal split
     if (__fadd_rn(fx, fy) <= 1.f) {
       oi[0] = 0, oj[0] = 0, oi[1] = 1, oj[1] = 0, oi[2] = 0, oj[2] = 1;
       o.b[0] = 1.f - fx - fy, o.b[1] = fx, o.b[2] = fy;
+      o.tri = 0;
     } else {
       oi[0] = 1, oj[0] = 1, oi[1] = 1, oj[1] = 0, oi[2] = 0, oj[2] = 1;
       o.b[0] = fx + fy - 1.f, o.b[1] = 1.f - fy, o.b[2] = 1.f - fx;
+      o.tri = 1;
     }
   } else {  // main-diagonal split
     if (fy <= fx) {
       oi[0] = 0, oj[0] = 0, oi[1] = 1, oj[1] = 0, oi[2] = 1, oj[2] = 1;
       o.b[0] = 1.f - fx, o.b[1] = fx - fy, o.b[2] = fy;
+      o.tri = 2;
     } else {
       oi[0] = 0, oj[0] = 0, oi[1] = 0, oj[1] = 1, oi[2] = 1, oj[2] = 1;
       o.b[0] = 1.f - fy, o.b[1] = fy - fx, o.b[2] = fx;
+      o.tri = 3;
     }
   }
 #pragma unroll
@@ -417,14 +432,13 @@ __device__ __forceinline__ void full_finish(const QueryParams& p, const DevScene
   for (int j = 0; j < 8; ++j) o.wn[j] *= inv;
 }
 
-// One level from scratch: the eight descents from the root advance
+// Spatial part of one level from scratch (the cells' map bases and weights
+// of o, the lower cell in c0): the eight descents from the root advance
 // together, one level per step (eight independent node reads in flight).
-__device__ __forceinline__ void full_form_level(const QueryParams& p, const DevScene& sc,
-                                                const int2* tree, const float (&xs)[3], float ux,
-                                                float uy, int l, FullLevel& o) {
+__device__ __forceinline__ void cells_form_level(const QueryParams& p, const DevScene& sc,
+                                                 const int2* tree, const float (&xs)[3], int l,
+                                                 int (&c0)[3], FullLevel& o) {
   const int V = sc.R[l];
-  full_vertex(ux, uy, V, o);
-  int c0[3];
   float t[3];
   full_cells(xs, l, c0, t);
   const int n = 1 << l;
@@ -446,6 +460,16 @@ __device__ __forceinline__ void full_form_level(const QueryParams& p, const DevS
     }
   }
   full_finish(p, sc, tree, nd, t, V, o);
+}
+
+// One level of the full form from scratch: the direction's triangle and the
+// eight cells.
+__device__ __forceinline__ void full_form_level(const QueryParams& p, const DevScene& sc,
+                                                const int2* tree, const float (&xs)[3], float ux,
+                                                float uy, int l, FullLevel& o) {
+  full_vertex(ux, uy, sc.R[l], o);
+  int c0[3];
+  cells_form_level(p, sc, tree, xs, l, c0, o);
 }
 
 // Level-to-level step of the eight cells' nodes: nd holds the nodes of level

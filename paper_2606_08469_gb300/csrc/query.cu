@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(ENC_NT * TPQ) encode_kernel(const __grid_const
       }
     };
     if constexpr (FORM == OCTA_FORM_SHIFTED)
-      gather_shifted_query<F, TT, KP>(p, sc, tree, in, q0 + q, q < nq, stage_row);
+      gather_shifted_query<F, TT, KP>(p, sc, tree, in, q0 + q, q < nq, p.normal, p.disparity,
+                                      stage_row);
     else if constexpr (FORM == OCTA_FORM_TRILINEAR_VERTEX)
       gather_full_query<F, TT, KP>(p, sc, tree, in, q0 + q, q < nq, stage_row);
     else
@@ -211,12 +212,12 @@ int apply_norm_pairs(const octa_pairs* pairs, int n_scenes, QueryParams& p) {
 using namespace octa;
 
 namespace {
-// The shifted form is evaluated by octa_encode alone.
+// The one-launch step does not evaluate the shifted form.
 int reject_shifted(const octa_scene* scenes, int32_t n_scenes) {
   for (int s = 0; s < n_scenes; ++s)
     if (scenes[s].query_form == OCTA_FORM_SHIFTED)
-      return fail(OCTA_EUNSUPPORTED, "scene %d: the shifted form is evaluated by octa_encode only",
-                  s);
+      return fail(OCTA_EUNSUPPORTED,
+                  "scene %d: the one-launch step does not evaluate the shifted form", s);
   return 0;
 }
 
@@ -331,12 +332,8 @@ extern "C" int octa_query_fwd(const octa_scene* scenes, int32_t n_scenes, const 
   QueryParams p;
   int rc = build_query_params(scenes, n_scenes, q, nullptr, p);
   if (rc) return rc;
-  if (scenes[0].query_form == OCTA_FORM_SHIFTED) {  // the tensor-core forward only
-    if (scenes[0].weight_dtype != OCTA_BF16)
-      return fail(OCTA_EUNSUPPORTED, "the shifted form's forward needs BF16 decoders");
-    if (q->n > 0 && (!q->normal || !q->disparity))
-      return fail(OCTA_EINVAL, "the shifted form needs normal and disparity");
-  }
+  if (scenes[0].query_form == OCTA_FORM_SHIFTED && q->n > 0 && (!q->normal || !q->disparity))
+    return fail(OCTA_EINVAL, "the shifted form needs normal and disparity");
   rc = check_one_form(scenes, n_scenes, node_idx);
   if (rc) return rc;
   if (q->n > 0 && !rgb) return fail(OCTA_EINVAL, "rgb must be non-NULL");
@@ -364,12 +361,11 @@ extern "C" int octa_query_bwd(const octa_scene* scenes, int32_t n_scenes, const 
   QueryParams p;
   int rc = build_query_params(scenes, n_scenes, q, grads, p);
   if (rc) return rc;
-  if (scenes[0].query_form == OCTA_FORM_SHIFTED) {  // the tensor-core backward only
-    if (scenes[0].weight_dtype != OCTA_BF16)
-      return fail(OCTA_EUNSUPPORTED, "the shifted form's backward needs BF16 decoders");
-    if (q->n > 0 && (!q->normal || !q->disparity))
-      return fail(OCTA_EINVAL, "the shifted form needs normal and disparity");
-  }
+  const bool shifted = scenes[0].query_form == OCTA_FORM_SHIFTED;
+  if (shifted && q->n > 0 && (!q->normal || !q->disparity))
+    return fail(OCTA_EINVAL, "the shifted form needs normal and disparity");
+  if (q->d_disparity && !shifted)
+    return fail(OCTA_EINVAL, "d_disparity is defined for the shifted form only");
   rc = check_one_form(scenes, n_scenes, nullptr);
   if (rc) return rc;
   if (q->n > 0 && !d_rgb) return fail(OCTA_EINVAL, "d_rgb must be non-NULL");
@@ -377,6 +373,7 @@ extern "C" int octa_query_bwd(const octa_scene* scenes, int32_t n_scenes, const 
   p.status = status;
   p.normal = q->normal;
   p.disparity = q->disparity;
+  p.d_disparity = q->d_disparity;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (scenes[0].weight_dtype == OCTA_BF16) return tc::query_bwd(scenes, n_scenes, p, st);
   return f32::dispatch(scenes, n_scenes, p, f32::Mode::kBackward, st);
@@ -400,8 +397,22 @@ extern "C" int octa_train_fused(const octa_scene* scenes, int32_t n_scenes, cons
   QueryParams p;
   int rc = build_query_params(scenes, n_scenes, &q, grads, p);
   if (rc) return rc;
-  rc = reject_shifted(scenes, n_scenes);
+  rc = check_one_form(scenes, n_scenes, nullptr);
   if (rc) return rc;
+  const bool shifted = scenes[0].query_form == OCTA_FORM_SHIFTED;
+  if (shifted && pairs->n > 0 &&
+      (!pairs->normal || !pairs->normal2 || !pairs->disparity || !pairs->disparity2))
+    return fail(OCTA_EINVAL, "the shifted form needs both queries' normals and disparities");
+  if ((pairs->d_disparity || pairs->d_disparity2) && !shifted)
+    return fail(OCTA_EINVAL, "d_disparity is defined for the shifted form only");
+  if (shifted) {
+    p.normal = pairs->normal;
+    p.normal2 = pairs->normal2;
+    p.disparity = pairs->disparity;
+    p.disparity2 = pairs->disparity2;
+    p.d_disparity = pairs->d_disparity;
+    p.d_disparity2 = pairs->d_disparity2;
+  }
   const bool bf16 = scenes[0].weight_dtype == OCTA_BF16;
   for (int s = 0; s < n_scenes; ++s)
     if ((scenes[s].weight_dtype == OCTA_BF16) != bf16)

@@ -62,8 +62,9 @@ def test_shifted_encoding_matches_oracle(seed, depth, V, F, tdt):
 
 
 def test_shifted_global_walk_and_errors():
-    """A tree larger than the staged capacity; the entry points that do not
-    evaluate the shifted form refuse it, and missing inputs are refused."""
+    """A tree larger than the staged capacity; missing inputs are refused, so
+    are the FP32 engine's F = 4 shapes (the shifted form is built for F = 8)
+    and the one-launch step."""
     from paper_2606_08469_gb300 import _lib as L
     from paper_2606_08469_gb300 import api as A
     V = [3, 3, 3, 3, 3]
@@ -86,7 +87,10 @@ def test_shifted_global_walk_and_errors():
     with pytest.raises(L.OctaError):
         A.octa_encode(sc, dev(x), dev(w))                        # no normal / disparity
     with pytest.raises(L.OctaError):
-        A.octa_query_fwd(sc, dev(x), dev(w))                     # FP32 decoder: encoding only
+        A.octa_query_fwd(sc, dev(x), dev(w))                     # no normal / disparity
+    with pytest.raises(L.OctaError) as e:                        # FP32 engine, F = 4
+        A.octa_query_fwd(sc, dev(x), dev(w), normal=dev(nrm), disparity=dev(d))
+    assert e.value.code == L.OCTA_EUNSUPPORTED
 
 
 def test_shifted_bf16_backward_vs_oracle():
