@@ -586,6 +586,36 @@ def train_full_leg(dev, flush, stream, steps):
     return out
 
 
+def shifted_train_leg(dev, flush, stream, steps):
+    """The paper's full model trained on the GPU (Eq. 7-9, 14; Section 3.3:
+    g_psi learnt through the radiance objective alone): per step octa_disparity
+    (8 hash levels of 2^16 entries, MLP 19-64-64-1) for every primary and
+    secondary query, the fused pass in the disparity-shifted form (vertex maps
+    of side R + 1) with each query's dL/dd, g_psi's backward
+    (octa_disparity_bwd, FP32) and Adam over the four parameter groups: on
+    train_bf16's workload (1,048,576 pairs, FP16 tables, BF16 decoder
+    72-64-64-64-3 on the tensor cores, the predictor's MLP on the tensor
+    cores) and train_f32's (262,144 pairs, FP32 on the CUDA cores)."""
+    from paper_2606_08469_gb300 import inputs as I
+    from paper_2606_08469_gb300 import workloads as WL
+    out = {"workload": "shifted-form training step (predictor g_psi, shifted lookup, decoder, "
+                       "Eq. 14, g_psi backward, Adam over tables, decoder, hash tables and g_psi)"}
+    for ci, prec in (("train_bf16", None), ("train_f32", "f32")):
+        cfg = I.WORKLOADS[ci]
+        step, _ = WL.shifted_train_step_for(cfg, device=dev, precision=prec)
+        for _ in range(3):
+            step.step()
+        stream.synchronize()
+        t = _timed(step.step, steps, flush, stream)
+        leg = {"pairs": cfg.n, "queries": 2 * cfg.n, "ms_per_step": round(t, 4),
+               "Mq/s": round(2 * cfg.n / t / 1e3, 2), "loss": float(step.loss.item())}
+        for part in ("predict", "fused_pass", "predictor_backward", "optimizer"):
+            leg[part + "_ms"] = round(_timed(getattr(step, part), steps, flush, stream), 4)
+        out[ci] = leg
+        del step
+    return out
+
+
 def multi_rhs_leg(dev, flush, stream, steps):
     """Section 4's training regime on train_bf16's scene (depth-8 octree,
     FP16 tables, BF16 decoder 72-64-64-64-3): LHS samples with M RHS samples
@@ -832,7 +862,7 @@ def job_rate(units_per_rank, world, steps, total_ms):
 
 
 LEGS = ("bf16_vs_f32", "inference", "small_forward", "encode", "encode_full", "encode_stress",
-        "train_full", "multi_rhs", "full_inference", "batched")
+        "train_full", "multi_rhs", "shifted_train", "full_inference", "batched")
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
 # launch of each fused training pass, from one ncu capture of the current
@@ -861,6 +891,7 @@ def run_legs(args, names):
            "encode_stress": lambda: encode_stress_leg(dev, flush, stream, steps, peaks),
            "train_full": lambda: train_full_leg(dev, flush, stream, steps),
            "multi_rhs": lambda: multi_rhs_leg(dev, flush, stream, steps),
+           "shifted_train": lambda: shifted_train_leg(dev, flush, stream, steps),
            "full_inference": lambda: full_inference_leg(dev, flush, stream, steps),
            "batched": lambda: batched_leg(dev, flush, stream, steps)}
     print(json.dumps({n: fns[n]() for n in names}), flush=True)
@@ -1133,6 +1164,7 @@ def run_ours(args):
             out["encode_stress"] = encode_stress_leg(dev, flush, stream, extra_steps, peaks)
             out["train_full"] = train_full_leg(dev, flush, stream, extra_steps)
             out["multi_rhs"] = multi_rhs_leg(dev, flush, stream, extra_steps)
+            out["shifted_train"] = shifted_train_leg(dev, flush, stream, extra_steps)
             out["full_inference"] = full_inference_leg(dev, flush, stream, extra_steps)
             out["batched"] = batched_leg(dev, flush, stream, extra_steps)
         out["cpu_baseline"] = cpu_baseline() if not args.no_cpu else None

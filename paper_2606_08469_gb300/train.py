@@ -262,3 +262,89 @@ class MultiSampleStep:
         self.loss_and_grad(stream)
         self.backward(stream)
         self.optimizer(stream)
+
+
+class PredictorState:
+    """Master parameters, gradients and Adam moments of the disparity
+    predictor g_psi (hash tables [L][T][2] and its MLP), FP32; with
+    tensor_cores its forward runs on the tcgen05 path from a BF16 working
+    copy of the weights that Adam refreshes."""
+
+    def __init__(self, table, res, weights, device, tensor_cores=False):
+        self.pred = api.Predictor(table, res, weights, device=device, tensor_cores=tensor_cores)
+        self.grad_t = torch.zeros_like(self.pred.table)
+        self.grad_w = torch.zeros_like(self.pred.weights)
+        self.m_t = torch.zeros_like(self.pred.table)
+        self.v_t = torch.zeros_like(self.pred.table)
+        self.m_w = torch.zeros_like(self.pred.weights)
+        self.v_w = torch.zeros_like(self.pred.weights)
+
+    def groups(self, lr_table, lr_mlp):
+        flat = lambda t: t.reshape(-1)
+        return [api.ParamGroup(flat(self.pred.table), flat(self.grad_t), flat(self.m_t),
+                               flat(self.v_t), lr_table),
+                api.ParamGroup(self.pred.weights, self.grad_w, self.m_w, self.v_w, lr_mlp,
+                               self.pred.weights_bf16)]
+
+
+class ShiftedTrainStep:
+    """A training step of the paper's full model on one scene (Eq. 7-9,
+    Eq. 14; Section 3.3: the disparity is learnt only through the radiance
+    objective).  Per step, all through the C ABI on the caller's stream:
+    octa_disparity predicts d = g_psi(x, omega_r) for the N primaries and N
+    secondaries in one launch; octa_train_fused runs the shifted lookup, the
+    decoder, the Eq. 14 gradient and the backward of every pair and returns
+    each query's dL/dd; octa_disparity_bwd carries dL/dd into g_psi's hash
+    tables and weights; adam_step updates the four parameter groups (tables,
+    decoder, hash tables, g_psi's MLP).  The scene state must be in the
+    shifted form; pairs: dict of device tensors x, omega, x2, omega2, E, w
+    (omega2 the sampled incident direction omega') and normal, normal2."""
+
+    def __init__(self, state, pred_state, pairs, eps=1e-2, rhs_grad=True, lr_tables=1e-2,
+                 lr_mlp=1e-3, lr_hash=1e-2, lr_pred=1e-3, scale=2.0 ** 15, growth_interval=2000,
+                 device="cuda"):
+        dev = torch.device(device)
+        self.state, self.pred_state = state, pred_state
+        self.scene = state.scene
+        n = int(pairs["x"].shape[0])
+        self.n = n
+        cat = lambda a, b: torch.cat([a, b]).to(dev).contiguous()
+        self.X = cat(pairs["x"], pairs["x2"])
+        self.Om = cat(pairs["omega"], -pairs["omega2"])
+        self.Nr = cat(pairs["normal"], pairs["normal2"])
+        self.E = pairs["E"].to(dev).contiguous()
+        self.w = pairs["w"].to(dev).contiguous()
+        self.D = torch.empty(2 * n, dtype=torch.float32, device=dev)
+        self.dD = torch.zeros(2 * n, dtype=torch.float32, device=dev)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.scaler = api.make_scaler(scale, growth_interval, device=dev)
+        self.ws_adam = api.workspace(L.OCTA_OP_ADAM, 0, device=dev)
+        self.eps, self.rhs_grad = eps, rhs_grad
+        self.groups = state.groups(lr_tables, lr_mlp) + pred_state.groups(lr_hash, lr_pred)
+        self.grads = [(state.grad_t, state.grad_w)]
+
+    def predict(self, stream=None):
+        api.octa_disparity(self.pred_state.pred, self.X, self.Om, self.Nr, out=self.D,
+                           stream=stream)
+
+    def fused_pass(self, stream=None):
+        n = self.n
+        api.octa_train_fused(self.scene, self.X[:n], self.Om[:n], self.X[n:], self.Om[n:],
+                             self.E, self.w, self.grads, self.loss, None, self.eps, self.rhs_grad,
+                             self.scaler, stream=stream,
+                             shift=(self.Nr[:n], self.Nr[n:], self.D[:n], self.D[n:],
+                                    self.dD[:n], self.dD[n:]))
+
+    def predictor_backward(self, stream=None):
+        ps = self.pred_state
+        api.octa_disparity_bwd(ps.pred, self.X, self.Om, self.Nr, self.dD, ps.grad_t, ps.grad_w,
+                               stream=stream)
+
+    def optimizer(self, stream=None):
+        api.adam_step(self.groups, self.scaler, self.ws_adam, stream=stream)
+
+    def step(self, stream=None):
+        self.predict(stream)
+        self.fused_pass(stream)
+        self.predictor_backward(stream)
+        self.optimizer(stream)

@@ -7,7 +7,7 @@ import torch
 
 from . import api
 from . import inputs as I
-from .train import MultiSampleStep, SceneState, TrainStep
+from .train import MultiSampleStep, PredictorState, SceneState, ShiftedTrainStep, TrainStep
 
 _TORCH_DT = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
 
@@ -154,3 +154,32 @@ def multi_sample_step_for(cfg, n, M, device="cuda", precision=None, seed=None, *
     arrays = {k: torch.from_numpy(getattr(smp, k)).to(dev) for k in ("x", "omega", "E", "omega_i", "w")}
     prims = api.Prims(smp.planes, smp.spheres, device=dev)
     return MultiSampleStep(st, prims, arrays, device=device, **kw), (tree, tables, weights, smp)
+
+
+# the disparity predictor of the shifted-form workloads: 8 hash levels of
+# 2^16 entries, resolutions 16 ... 512 on a geometric progression
+PREDICTOR_LEVELS = 8
+PREDICTOR_LOG2_T = 16
+PREDICTOR_RES = [int(np.floor(16 * (512 / 16) ** (l / 7))) for l in range(PREDICTOR_LEVELS)]
+
+
+def shifted_train_step_for(cfg, n_pairs=None, device="cuda", precision=None, attrs=0, **kw):
+    """ShiftedTrainStep of a 'pairs' workload: the paper's full model on the
+    workload's tree with vertex maps of side R + 1 (the shifted form), the
+    workload's table and decoder precisions (precision='f32': FP32), and
+    the predictor above (FP32 MLP; on the tensor cores when the decoder is
+    BF16)."""
+    tree, tables, weights = host_params(cfg, vertex_maps=True)
+    tdt, wdt = table_dtype(cfg), weight_dtype(cfg)
+    if precision == "f32":
+        tdt = wdt = torch.float32
+    st = SceneState(tree, tables, weights, tdt, wdt, device, query_form=api.L.OCTA_FORM_SHIFTED)
+    ptab, pw = I.predictor_params(cfg.seed("mlp") + 7, PREDICTOR_LEVELS, PREDICTOR_LOG2_T)
+    ps = PredictorState(ptab, PREDICTOR_RES, pw, device, tensor_cores=wdt == torch.bfloat16)
+    n = cfg.n if n_pairs is None else n_pairs
+    pairs, n1, n2 = I.training_pairs_with_normals(cfg.seed("queries"), n)
+    arrays = pairs_on_device(pairs, device)
+    arrays["normal"] = to_dev(n1, device)
+    arrays["normal2"] = to_dev(n2, device)
+    return ShiftedTrainStep(st, ps, arrays, device=device, **kw), \
+        (tree, tables, weights, (ptab, PREDICTOR_RES, pw), pairs, n1, n2)

@@ -368,3 +368,52 @@ def test_shifted_whole_step_fp32():
         # compare the updates normwise
         upd, ref_upd = got - p0, want - p0
         assert normwise(upd, ref_upd) <= 1e-3, normwise(upd, ref_upd)
+
+
+def test_shifted_train_step_wrapper_and_graph():
+    """train.ShiftedTrainStep (g_psi forward, fused shifted pass, g_psi
+    backward, Adam over four groups) on train_f32's scene with vertex maps:
+    its gradients before Adam against the oracle's shifted_train_gradients
+    (1e-3 normwise: no pairs are neutralised here, the strict comparison is
+    test_shifted_whole_step_fp32), and a CUDA-graph replay of three steps
+    against three eager steps of a second, identical instance."""
+    from paper_2606_08469_gb300 import inputs as I
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.WORKLOADS["train_f32"]
+    a, (tree, tables, weights, pred, pairs, n1, n2) = WL.shifted_train_step_for(
+        cfg, n_pairs=4096, device=DEV, precision="f32")
+    ot = O.build_tree(cfg.seed("tree"), cfg.max_depth, cfg.p_base, [r + 1 for r in cfg.R])
+    a.predict()
+    a.fused_pass()
+    a.predictor_backward()
+    torch.cuda.synchronize()
+    S = 2.0 ** 15
+    rl, rT, rWs, rtab, rWp, _, _ = O.shifted_train_gradients(ot, tables, weights, pred, pairs,
+                                                             n1, n2, scale=S)
+    assert abs(a.loss.item() - rl) <= 1e-5 * rl
+    errs = [normwise(a.state.grad_t.cpu().numpy(), rT),
+            max(weight_errors(a.state.grad_w.cpu().numpy(), rWs)),
+            normwise(a.pred_state.grad_t.cpu().numpy(), rtab),
+            max(weight_errors(a.pred_state.grad_w.cpu().numpy(), rWp))]
+    print("ShiftedTrainStep gradients vs FP64", [f"{e:.2e}" for e in errs])
+    assert max(errs) <= 1e-3
+    a.optimizer()
+    for _ in range(2):
+        a.step()
+    b, _ = WL.shifted_train_step_for(cfg, n_pairs=4096, device=DEV, precision="f32")
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        b.step(stream)                       # eager warm-up: step 1
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            b.step(stream)
+        g.replay()                           # steps 2, 3
+        g.replay()
+    stream.synchronize()
+    torch.cuda.synchronize()
+    e = lambda u, v: float(torch.linalg.norm(u - v) / torch.linalg.norm(v))
+    for u, v in ((a.state.master_t, b.state.master_t), (a.state.master_w, b.state.master_w),
+                 (a.pred_state.pred.table, b.pred_state.pred.table),
+                 (a.pred_state.pred.weights, b.pred_state.pred.weights)):
+        assert e(u, v) <= 1e-6, e(u, v)
