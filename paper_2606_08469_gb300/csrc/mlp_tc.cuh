@@ -756,6 +756,14 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
     const int64_t gq = sc.q_begin + (2 * (item - p.item_begin[s]) + g) * ROWS + row;
     return load_query(xs, ws, gq, gq < sc.q_end);
   };
+  // The two groups run half a tile apart: group 1 starts its first tile of
+  // a scene when group 0 has finished that tile's forward, so that one
+  // group's gather and scatter (memory) overlap the other's decoder
+  // (tensor cores).  Beyond that they synchronise only at scene changes and
+  // at the end; after an abort both keep stepping through the items without
+  // work, so every barrier sees both groups.
+  constexpr int SKEW_BAR = 1 + 2 * S::G;
+  bool skew_pending = false;
   const WorkRange wr = work_range(p.n_items, p.order);
   QueryIn next = wr.begin < wr.end ? item_query(wr.begin) : QueryIn{};
   for (int64_t item = wr.begin; item < wr.end; item += wr.step) {
@@ -764,12 +772,11 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
     const DevScene& sc = p.sc[s];
     const QueryIn in = next;
     if (item + wr.step < wr.end) next = item_query(item + wr.step);
-    tc_fence_before_sync();
-    __syncthreads();
-    if (abort_flag) break;
     if (s != cur) {
+      tc_fence_before_sync();
+      __syncthreads();  // both groups are done with the previous scene
       tc_fence_after_sync();
-      if (cur >= 0) {
+      if (cur >= 0 && !abort_flag) {
         flush_weight_grads<S>(p.sc[cur], lane_addr, flush_set, NL, FLUSH_SETS);
         tc_fence_before_sync();
         if (TRAIN) flush_loss(loss_acc, p.loss + cur, p.sc[cur].norm_pairs);
@@ -788,6 +795,21 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
       tree = stage_tree(p, sc, tree_sm, S::TREE_NODES, threadIdx.x, S::NTB);
       cur = s;
       __syncthreads();
+      skew_pending = true;
+    }
+    if (abort_flag) {  // keep the skew barrier's count, skip the work
+      if (skew_pending) {
+        if (g == 0)
+          named_arrive(SKEW_BAR, S::NTB);
+        else
+          named_sync(SKEW_BAR, S::NTB);
+        skew_pending = false;
+      }
+      continue;
+    }
+    if (g == 1 && skew_pending) {  // group 0's first tile of the scene is past its forward
+      named_sync(SKEW_BAR, S::NTB);
+      skew_pending = false;
     }
     const int64_t tiles_s = (sc.q_end - sc.q_begin + ROWS - 1) / ROWS;
     const int64_t tile_s = 2 * (item - p.item_begin[s]) + g;
@@ -814,6 +836,25 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
                                      base_sm, u_sm, t);
     }
     fence_proxy_async();
+    // the loss epilogue's per-pair inputs (E, w) or the backward's d_rgb,
+    // loaded now so that their latency passes under the forward
+    float in3a[3] = {0.f, 0.f, 0.f}, in3b[3] = {0.f, 0.f, 0.f};
+    if (valid && half == 0) {
+      if (TRAIN) {
+        if (primary) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            in3a[c] = __ldcs(p.E + 3 * gq + c);
+            in3b[c] = __ldcs(p.w + 3 * gq + c);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) in3a[c] = __ldcs(p.d_rgb + 3 * gq + c);
+      }
+    }
+    // the previous tile's tensor-memory reads come before this tile's MMAs
+    tc_fence_before_sync();
     named_sync(gbar, NTG);
 
     bool failed = false;
@@ -856,11 +897,9 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
         const float L2 = expf(__uint_as_float(r[2]));
         float d0 = 0.f, d1 = 0.f, d2 = 0.f;
         if (!TRAIN) {
-          if (valid) {
-            d0 = p.d_rgb[3 * gq];
-            d1 = p.d_rgb[3 * gq + 1];
-            d2 = p.d_rgb[3 * gq + 2];
-          }
+          d0 = in3a[0];
+          d1 = in3a[1];
+          d2 = in3a[2];
         } else {
           // Eq. 14 with the one-sample target of Eq. 3, per pair and channel:
           // T = E + w L_s, r = (L_p - T) / (L_p + T + eps) (normaliser
@@ -878,8 +917,8 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
             float dp[3], ds[3], r2 = 0.f;  // the pair's three r^2 in binary32
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-              const float ww = p.w[3 * gq + c];
-              const float T = p.E[3 * gq + c] + ww * Ls[c];
+              const float ww = in3b[c];
+              const float T = in3a[c] + ww * Ls[c];
               const float den = Lp[c] + T + p.eps;
               const float rr = (Lp[c] - T) / den;
               r2 = fmaf(rr, rr, r2);
@@ -914,6 +953,10 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
       fence_proxy_async();
       tc_fence_before_sync();
       named_sync(gbar, NTG);
+    }
+    if (g == 0 && skew_pending) {  // releases group 1 (also after a failed forward)
+      named_arrive(SKEW_BAR, S::NTB);
+      skew_pending = false;
     }
 
     // ---- backward through the decoder
@@ -989,7 +1032,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
         for (int o = 0; o < KO; ++o) {
           const int l = o * TPR + half;
           if (l >= S::KPAD) continue;
-          const int64_t mo = base_sm[l * NT + t];
+          const int mo = base_sm[l * NT + t];
           if (mo < 0) continue;
           const Footprint fp = footprint(u_sm[t], u_sm[NT + t], sc.R[l]);
 #pragma unroll
@@ -1001,7 +1044,8 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               const float w = fp.w[k];
-              float4* dst = reinterpret_cast<float4*>(sc.d_tables + (mo + fp.idx[k]) * S::F) + c4;
+              float4* dst =
+                  reinterpret_cast<float4*>(sc.d_tables + (int64_t(mo) + fp.idx[k]) * S::F) + c4;
               atomicAdd(dst, make_float4(w * g0, w * g1, w * g2, w * g3));
             }
           }

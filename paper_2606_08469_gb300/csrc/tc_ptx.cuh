@@ -138,6 +138,11 @@ __device__ __forceinline__ void tmem_wait_st() {
 __device__ __forceinline__ void named_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
+// Arrival on a named barrier without waiting for it (the barrier completes
+// when `count` threads have arrived or synced).
+__device__ __forceinline__ void named_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
 // Named barrier that also ORs a predicate over its threads.
 __device__ __forceinline__ bool named_sync_or(int id, int count, bool pred) {
   uint32_t r;
