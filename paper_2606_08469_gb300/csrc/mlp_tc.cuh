@@ -362,7 +362,9 @@ struct BShape : Shape<F_, WP_, H_, NH_> {
   static constexpr uint32_t GR_BYTES = (GR_XCH + 64 * 4 * 4 + 1023) & ~1023u;
   static constexpr uint32_t OFF_GROUP = (B::W_BYTES + 1023) & ~1023u;
   static constexpr uint32_t OFF_BAR = OFF_GROUP + G * GR_BYTES;
-  static constexpr uint32_t OFF_TREE = (OFF_BAR + 8 * G + 8 + 15) & ~15u;
+  // two mbarriers per group (the MMAs of its two issuing threads), then the
+  // tensor-memory address slot
+  static constexpr uint32_t OFF_TREE = (OFF_BAR + 16 * G + 8 + 15) & ~15u;
   static constexpr int TREE_NODES = tree_capacity(OFF_TREE, 1);
   static constexpr size_t SMEM = OFF_TREE + 8u * TREE_NODES;
   static constexpr int WORK = WP_ > H_ ? WP_ : H_;
@@ -693,17 +695,21 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   int2* tree_sm = S::TREE_NODES > 0 ? reinterpret_cast<int2*>(smem + S::OFF_TREE) : nullptr;
   const int2* tree = nullptr;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::OFF_BAR);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::OFF_BAR + 8 * S::G);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::OFF_BAR + 16 * S::G);
   __shared__ int abort_flag;
   const uint32_t mbar = smem_addr(bars + g);
+  const uint32_t mbar2 = smem_addr(bars + S::G + g);  // the second issuer's
   const uint32_t base_sa = smem_addr(smem);
   const uint32_t dl_sa = base_sa + S::off_dl(g);
   const int gbar = 1 + g;                         // named barrier of this group
   const int xbar = TPR == 1 ? gbar : 1 + S::G + g;  // its half-0 threads alone
   const bool lead = t == 0 && half == 0;           // issues the group's MMAs
+  // the backward's G = delta W_i MMAs come from a second thread (another
+  // warp), so that its issue runs beside the lead's dW MMAs
+  const bool issuer2 = t == 32 && half == 0;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < S::G; ++i) mbar_init(smem_addr(bars + i), 1);
+    for (int i = 0; i < 2 * S::G; ++i) mbar_init(smem_addr(bars + i), 1);
     abort_flag = 0;
   }
   if (warp == 0) {
@@ -728,7 +734,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   tc_fence_before_sync();
   __syncthreads();
   tc_fence_after_sync();
-  uint32_t phase = 0;
+  uint32_t phase = 0, phase2 = 0;
   int cur = -1;
   double loss_acc = 0.0;
   const float lscale = TRAIN ? (p.scaler ? p.scaler->scale : 1.f) : 1.f;
@@ -974,6 +980,9 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
         for (int kq = 0; kq < NT; kq += 16)
           mma_bf16(tmem + S::dw_col(i), mnmajor_desc(act_sa, kq, in), mnmajor_desc(d_sa, kq, dk),
                    idw, 1u);
+        mma_commit(mbar);
+      } else if (issuer2) {
+        tc_fence_after_sync();
         // G = delta_{i+1} W_i: M = 128 queries, N = in, K = out
         const uint32_t ig = idesc_bf16(128, in, 0, 1);
         const uint32_t w_sa = base_sa + S::w_off(i);
@@ -981,10 +990,12 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
         for (int ko = 0; ko < out; ko += 16)
           mma_bf16(work, kmajor_desc(d_sa, ko, dk), mnmajor_desc(w_sa, ko, in), ig,
                    ko > 0 ? 1u : 0u);
-        mma_commit(mbar);
+        mma_commit(mbar2);
       }
-      const bool ok = mbar_wait_bounded(mbar, phase, wait_ns);
+      const bool ok = mbar_wait_bounded(mbar, phase, wait_ns) &&
+                      mbar_wait_bounded(mbar2, phase2, wait_ns);
       phase ^= 1u;
+      phase2 ^= 1u;
       if (named_sync_or(gbar, NTG, !ok)) {
         failed = true;
         break;
