@@ -415,8 +415,9 @@ def inference_leg(dev, flush, stream, steps, peaks):
                 fn()
             from paper_2606_08469_gb300 import autotune as T
             if prec == "bf16":
-                best, rep = T.autotune(fn, {"fwd_threads_per_query": [1, 2], "fwd_order": [1, 2]},
-                                       f"config3-forward-{w_}x{h_}", reps=5)
+                best, rep = T.autotune(fn, {"fwd_threads_per_query": [1, 2], "fwd_order": [1, 2],
+                                            "fwd_run": [1, 2, 4], "fwd_ctas_per_sm": [0, 2, 3]},
+                                       f"gbuffer-forward-{w_}x{h_}", reps=5)
             g = _graph(fn, stream)
             g.replay()
             t = _timed(g.replay, steps, flush, stream)
@@ -808,8 +809,9 @@ def batched_leg(dev, flush, stream, steps):
     log-uniform pair counts; the whole training step of all scenes (forward,
     Eq. 14 gradient, backward, Adam with the loss scaler) as one persistent
     cooperative launch captured in a CUDA graph; beside it the same step as
-    the fused pass + adam_step (two launches, one graph).  The persistent
-    kernels' work order is autotuned on this workload."""
+    the fused pass + adam_step (two launches, one graph).  The training
+    kernels' launch knobs (work order, tiles per CTA work unit, threads per
+    tile row) are autotuned on this workload, every trial reported."""
     from paper_2606_08469_gb300 import inputs as I
     from paper_2606_08469_gb300 import workloads as WL
     from paper_2606_08469_gb300 import autotune as T
@@ -822,8 +824,9 @@ def batched_leg(dev, flush, stream, steps):
         step, _ = WL.batched_train_step(device=dev, fused=True, persistent=mode == "one_launch")
         for _ in range(3):
             step.step()
-        best, rep = T.autotune(step.step, {"train_order": [1, 2], "fwd_order": [1, 2]},
-                               f"config4-batched-{mode}", reps=5)
+        best, rep = T.autotune(step.step, {"train_order": [1, 2], "train_run": [1, 2, 4],
+                                           "train_threads_per_row": [1, 2]},
+                               f"batched-step-{mode}", reps=5)
         g = _graph(step.step, stream)
         g.replay()
         t = _timed(g.replay, steps, flush, stream)
@@ -831,7 +834,7 @@ def batched_leg(dev, flush, stream, steps):
         leg = {"ms_per_step": round(t, 4), "Mq/s": round(nq / t / 1e3, 1),
                "launches_per_step": 1 if mode == "one_launch" else 3,
                "autotune": {"best": best, "best_ms": rep["best_ms"], "default_ms": rep["default_ms"],
-                            "gain": rep["gain"]}}
+                            "gain": rep["gain"], "trials": rep["trials"]}}
         if mode == "one_launch":
             out.update(leg)
             out["path"] = "octa_train_step_batched (one cooperative launch), CUDA-graph replay"

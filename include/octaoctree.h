@@ -502,6 +502,15 @@ typedef struct octa_tuning {
                                   cell form: 2 (default: 512-thread CTAs,
                                   the two threads of a tile row splitting
                                   its levels and epilogue columns) or 1   */
+  int32_t fwd_run;             /* queries per CTA work unit, in tiles of 128
+                                  queries: with the interleaved order a
+                                  persistent CTA of the forward, encoding
+                                  and FP32 forward kernels takes fwd_run
+                                  consecutive tiles at a time (1..64;
+                                  default 1)                               */
+  int32_t train_run;           /* the same for the backward and training
+                                  kernels (work units: tensor-core items of
+                                  two 128-row tiles, FP32 tiles)           */
 } octa_tuning;
 int octa_set_tuning(const octa_tuning* t);   /* NULL restores the defaults */
 int octa_get_tuning(octa_tuning* t);

@@ -21,7 +21,8 @@ import torch
 from . import _lib as L
 
 KNOBS = ("fwd_ctas_per_sm", "encode_ctas_per_sm", "engine_ctas_per_sm", "fwd_order", "train_order",
-         "fwd_threads_per_query", "encode_threads_per_query")
+         "fwd_threads_per_query", "encode_threads_per_query", "train_threads_per_row", "fwd_run",
+         "train_run")
 
 
 def get_tuning():

@@ -23,14 +23,14 @@ int run_engine_form(const QueryParams& p, Mode mode, cudaStream_t stream) {
   if (mode == Mode::kForward) {
     using S = Shape<F, WP, H, NH, false>;
     return launch_persistent(engine_kernel<S, TT, false, SHIFT>, S::SMEM, p, stream, NT,
-                             tu.engine_ctas_per_sm, tu.fwd_order);
+                             tu.engine_ctas_per_sm, tu.fwd_order, tu.fwd_run);
   }
   using S = Shape<F, WP, H, NH, true>;
   if (mode == Mode::kBackward)
     return launch_persistent(engine_kernel<S, TT, false, SHIFT>, S::SMEM, p, stream, NT,
-                             tu.engine_ctas_per_sm, tu.train_order);
+                             tu.engine_ctas_per_sm, tu.train_order, tu.train_run);
   return launch_persistent(engine_kernel<S, TT, true, SHIFT>, S::SMEM, p, stream, NT,
-                           tu.engine_ctas_per_sm, tu.train_order);
+                           tu.engine_ctas_per_sm, tu.train_order, tu.train_run);
 }
 
 // Built shapes of the FP32 engine: (F, padded input width, hidden width,

@@ -731,13 +731,13 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const __grid_constant__ Q
     const int64_t gq = sc.q_begin + (tile - sc.tile_begin) * ROWS + qrow;
     return load_query(xs, ws, gq, qrow < ROWS && gq < sc.q_end);
   };
-  const WorkRange wr = work_range(p.n_tiles, p.order);
+  const WorkRange wr = work_range(p.n_tiles, p.order, p.run);
   QueryIn next = wr.begin < wr.end ? tile_query(wr.begin) : QueryIn{};
-  for (int64_t tile = wr.begin; tile < wr.end; tile += wr.step) {
+  for (int64_t tile = wr.begin; tile < wr.end; tile = wr.next(tile)) {
     const int s = scene_of_tile(p, tile);
     const DevScene& sc = p.sc[s];
     const QueryIn in = next;
-    if (tile + wr.step < wr.end) next = tile_query(tile + wr.step);
+    if (wr.next(tile) < wr.end) next = tile_query(wr.next(tile));
     __syncthreads();  // previous tile finished with shared memory
     if (s != cur) {
       if (S::BWD && cur >= 0) {

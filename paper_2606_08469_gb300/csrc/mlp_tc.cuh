@@ -238,13 +238,13 @@ __global__ void __launch_bounds__(NT * TPQ, 4)
   int cur = -1;
   bool failed = false;
 
-  const WorkRange wr = work_range(p.n_tiles, p.order);
+  const WorkRange wr = work_range(p.n_tiles, p.order, p.run);
   QueryIn next = wr.begin < wr.end ? load_tile_query(p, wr.begin, q, NT) : QueryIn{};
-  for (int64_t tile = wr.begin; tile < wr.end && !failed; tile += wr.step) {
+  for (int64_t tile = wr.begin; tile < wr.end && !failed; tile = wr.next(tile)) {
     const int s = scene_of_tile(p, tile);
     const DevScene& sc = p.sc[s];
     const QueryIn in = next;
-    if (tile + wr.step < wr.end) next = load_tile_query(p, tile + wr.step, q, NT);
+    if (wr.next(tile) < wr.end) next = load_tile_query(p, wr.next(tile), q, NT);
     __syncthreads();
     if (s != cur) {
       load_weights_bf16<S>(sc, smem, NTF);
@@ -770,14 +770,14 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   // work, so every barrier sees both groups.
   constexpr int SKEW_BAR = 1 + 2 * S::G;
   bool skew_pending = false;
-  const WorkRange wr = work_range(p.n_items, p.order);
+  const WorkRange wr = work_range(p.n_items, p.order, p.run);
   QueryIn next = wr.begin < wr.end ? item_query(wr.begin) : QueryIn{};
-  for (int64_t item = wr.begin; item < wr.end; item += wr.step) {
+  for (int64_t item = wr.begin; item < wr.end; item = wr.next(item)) {
     int s = 0;
     while (s + 1 < p.n_scenes && item >= p.item_begin[s + 1]) ++s;
     const DevScene& sc = p.sc[s];
     const QueryIn in = next;
-    if (item + wr.step < wr.end) next = item_query(item + wr.step);
+    if (wr.next(item) < wr.end) next = item_query(wr.next(item));
     if (s != cur) {
       tc_fence_before_sync();
       __syncthreads();  // both groups are done with the previous scene
@@ -1185,6 +1185,7 @@ int launch_fwd_tpq(const QueryParams& p, const octa_tuning& tu, cudaStream_t str
   per_sm = apply_cap(per_sm, tu.fwd_ctas_per_sm);
   QueryParams pp = p;
   pp.order = tu.fwd_order == 1 ? 1 : 0;
+  pp.run = tu.fwd_run > 1 ? tu.fwd_run : 1;
   const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * device_sm_count());
   kern<<<static_cast<unsigned>(grid), NT * TPQ, S::SMEM, stream>>>(pp);
   cudaError_t e = cudaGetLastError();
@@ -1220,7 +1221,9 @@ int launch_bwd(const QueryParams& p0, const AdamBlock* adam, cudaStream_t stream
   }
   p.item_begin[p.n_scenes] = items;
   p.n_items = items;
-  p.order = tuning_snapshot().train_order == 1 ? 1 : 0;
+  const octa_tuning tu = tuning_snapshot();
+  p.order = tu.train_order == 1 ? 1 : 0;
+  p.run = tu.train_run > 1 ? tu.train_run : 1;
   if (items == 0 && !PERSIST) return OCTA_OK;
   auto kern = bwd_kernel<S, TT, TRAIN, PERSIST, FORMS>;
   int per_sm = 0;

@@ -65,6 +65,7 @@ struct QueryParams {
   float eps;
   int32_t rhs_grad;
   int32_t order;  // how persistent CTAs take work: 0 interleaved, 1 contiguous chunks
+  int32_t run;    // interleaved order: consecutive work units a CTA takes at a time
   // staged octree of kernels with a run-time shared-memory layout: capacity
   // in nodes (0: walk in global memory) and byte offset in dynamic memory
   int32_t tree_cap;
@@ -105,18 +106,24 @@ __device__ __forceinline__ void attr_columns(const QueryParams& p, int K, int l,
   }
 }
 
-// Work units [0, n) of this CTA: interleaved (u = block + k * grid) or one
-// contiguous chunk per CTA (fewer scene switches in a multi-scene launch).
+// Work units [0, n) of this CTA, visited begin, next(begin), ... while < end:
+// interleaved in runs of `run` consecutive units (the CTA's run k starts at
+// (block + k grid) run; run = 1: u = block + k grid), or one contiguous chunk
+// per CTA (order 1: fewer scene switches in a multi-scene launch).
 struct WorkRange {
-  int64_t begin, end, step;
+  int64_t begin, end, step, run;
+  __device__ __forceinline__ int64_t next(int64_t u) const {
+    return ((u + 1) % run) ? u + 1 : u + 1 + step - run;
+  }
 };
-__device__ __forceinline__ WorkRange work_range(int64_t n, int order) {
+__device__ __forceinline__ WorkRange work_range(int64_t n, int order, int run = 1) {
   if (order == 1) {
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t b = int64_t(blockIdx.x) * chunk;
-    return WorkRange{b, b + chunk < n ? b + chunk : n, 1};
+    return WorkRange{b, b + chunk < n ? b + chunk : n, 1, 1};
   }
-  return WorkRange{int64_t(blockIdx.x), n, int64_t(gridDim.x)};
+  const int64_t r = run > 1 ? run : 1;
+  return WorkRange{int64_t(blockIdx.x) * r, n, int64_t(gridDim.x) * r, r};
 }
 
 // Scene owning global tile t (tiles never straddle scenes).

@@ -35,13 +35,13 @@ __global__ void __launch_bounds__(ENC_NT * TPQ) encode_kernel(const __grid_const
   int2* tree_sm = p.tree_cap > 0 ? reinterpret_cast<int2*>(stage + p.tree_off) : nullptr;
   const int2* tree = nullptr;
   int cur = -1;
-  const WorkRange wr = work_range(p.n_tiles, p.order);
+  const WorkRange wr = work_range(p.n_tiles, p.order, p.run);
   QueryIn next = wr.begin < wr.end ? load_tile_query(p, wr.begin, q, ENC_NT) : QueryIn{};
-  for (int64_t tile = wr.begin; tile < wr.end; tile += wr.step) {
+  for (int64_t tile = wr.begin; tile < wr.end; tile = wr.next(tile)) {
     const int s = scene_of_tile(p, tile);
     const DevScene& sc = p.sc[s];
     const QueryIn in = next;
-    if (tile + wr.step < wr.end) next = load_tile_query(p, tile + wr.step, q, ENC_NT);
+    if (wr.next(tile) < wr.end) next = load_tile_query(p, wr.next(tile), q, ENC_NT);
     if (s != cur) {
       __syncthreads();
       tree = stage_tree(p, sc, tree_sm, p.tree_cap, threadIdx.x, NTH);
@@ -285,9 +285,9 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
   const octa_tuning tu = tuning_snapshot();
 #define OCTA_ENC_FORM(F_, TT_, KP_, FORM_)                                                       \
   return bf ? launch_persistent(encode_kernel<F_, TT_, __nv_bfloat16, KP_, FORM_>, smem, p, st,  \
-                                ENC_NT, tu.encode_ctas_per_sm, tu.fwd_order)                     \
+                                ENC_NT, tu.encode_ctas_per_sm, tu.fwd_order, tu.fwd_run)                     \
             : launch_persistent(encode_kernel<F_, TT_, float, KP_, FORM_>, smem, p, st, ENC_NT,  \
-                                tu.encode_ctas_per_sm, tu.fwd_order);
+                                tu.encode_ctas_per_sm, tu.fwd_order, tu.fwd_run);
 #define OCTA_ENC(F_, TT_, KP_)                                    \
   if (form == OCTA_FORM_SHIFTED) {                                \
     OCTA_ENC_FORM(F_, TT_, KP_, OCTA_FORM_SHIFTED)                \
@@ -298,9 +298,9 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
   if (tu.encode_threads_per_query == 2) {                         \
     return bf ? launch_persistent(                                \
                     encode_kernel<F_, TT_, __nv_bfloat16, KP_, OCTA_FORM_CELL_BILINEAR, 2>, \
-                    smem, p, st, 2 * ENC_NT, tu.encode_ctas_per_sm, tu.fwd_order)           \
+                    smem, p, st, 2 * ENC_NT, tu.encode_ctas_per_sm, tu.fwd_order, tu.fwd_run)           \
               : launch_persistent(encode_kernel<F_, TT_, float, KP_, OCTA_FORM_CELL_BILINEAR, 2>, \
-                                  smem, p, st, 2 * ENC_NT, tu.encode_ctas_per_sm, tu.fwd_order); \
+                                  smem, p, st, 2 * ENC_NT, tu.encode_ctas_per_sm, tu.fwd_order, tu.fwd_run); \
   }                                                               \
   OCTA_ENC_FORM(F_, TT_, KP_, OCTA_FORM_CELL_BILINEAR)
 #define OCTA_ENC_KP(F_, TT_)      \
@@ -522,7 +522,8 @@ extern "C" int octa_set_tuning(const octa_tuning* t) {
       t->fwd_order < 0 || t->fwd_order > 2 || t->train_order < 0 || t->train_order > 2 ||
       t->fwd_threads_per_query < 0 || t->fwd_threads_per_query > 2 ||
       t->encode_threads_per_query < 0 || t->encode_threads_per_query > 2 ||
-      t->train_threads_per_row < 0 || t->train_threads_per_row > 2)
+      t->train_threads_per_row < 0 || t->train_threads_per_row > 2 || t->fwd_run < 0 ||
+      t->fwd_run > 64 || t->train_run < 0 || t->train_run > 64)
     return fail(OCTA_EINVAL, "tuning values out of range");
   tuning() = *t;
   return OCTA_OK;

@@ -34,7 +34,9 @@ def test_forward_results_independent_of_knobs():
     ref2, _, _ = A.octa_query_fwd([sc, sc], X, W, counts)
     for setting in ({"fwd_ctas_per_sm": 1}, {"fwd_ctas_per_sm": 2, "fwd_order": 1},
                     {"fwd_order": 1}, {"fwd_threads_per_query": 2},
-                    {"fwd_threads_per_query": 2, "fwd_order": 1, "fwd_ctas_per_sm": 3}):
+                    {"fwd_threads_per_query": 2, "fwd_order": 1, "fwd_ctas_per_sm": 3},
+                    {"fwd_run": 3}, {"fwd_run": 8, "fwd_ctas_per_sm": 2},
+                    {"fwd_run": 64, "fwd_threads_per_query": 2}):
         T.set_tuning(setting)
         got, gn, ga = A.octa_query_fwd(sc, X, W, want_nodes=True, want_addr=True)
         torch.testing.assert_close(got, ref, rtol=0, atol=0)
@@ -50,12 +52,18 @@ def test_training_results_independent_of_order():
     a, _ = WL.batched_train_step(counts=counts, fused=True)
     b, _ = WL.batched_train_step(counts=counts, fused=True)
     a.fused_pass()
-    T.set_tuning({"train_order": 1})
-    b.fused_pass()
     torch.cuda.synchronize()
-    torch.testing.assert_close(b.loss, a.loss, rtol=1e-6, atol=0)
-    for sa, sb in zip(a.states, b.states):
-        assert torch.linalg.norm(sa.grad_t - sb.grad_t) <= 1e-5 * torch.linalg.norm(sa.grad_t)
+    for setting in ({"train_order": 1}, {"train_run": 3}, {"train_run": 16, "train_order": 2}):
+        for st in b.states:
+            st.grad_t.zero_()
+            st.grad_w.zero_()
+        T.set_tuning(setting)
+        b.fused_pass()
+        torch.cuda.synchronize()
+        torch.testing.assert_close(b.loss, a.loss, rtol=1e-6, atol=0)
+        for sa, sb in zip(a.states, b.states):
+            assert torch.linalg.norm(sa.grad_t - sb.grad_t) <= 1e-5 * torch.linalg.norm(sa.grad_t)
+            assert torch.linalg.norm(sa.grad_w - sb.grad_w) <= 1e-5 * torch.linalg.norm(sa.grad_w)
 
 
 def test_autotune_picks_and_caches(tmp_path):

@@ -45,7 +45,7 @@ def test_struct_sizes_match_header(lib):
     """The ctypes mirrors have the C layout (checked through a sizing call)."""
     from paper_2606_08469_gb300 import _lib as L
     assert C.sizeof(L.octa_tree_desc) == 4 + 4 + 8 + 4 * 16 + 4 * 17 + 4 + 8 * 17
-    assert lib.octa_abi_version() == 6
+    assert lib.octa_abi_version() == 7
     assert C.sizeof(L.octa_prims) == 8 + 8 + 4 + 4
     assert C.sizeof(L.octa_queries) == 8 + 8 + 8 + 8 * 17 + 8 + 8 + 8 + 4 + 4 + 8
     assert C.sizeof(L.octa_predictor) == 8 + 8 + 8 + 4 + 4 + 4 * 16
