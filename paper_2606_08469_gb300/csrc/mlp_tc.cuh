@@ -762,12 +762,15 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
     const int64_t gq = sc.q_begin + (2 * (item - p.item_begin[s]) + g) * ROWS + row;
     return load_query(xs, ws, gq, gq < sc.q_end);
   };
-  // The two groups run half a tile apart: group 1 starts its first tile of
-  // a scene when group 0 has finished that tile's forward, so that one
-  // group's gather and scatter (memory) overlap the other's decoder
-  // (tensor cores).  Beyond that they synchronise only at scene changes and
-  // at the end; after an abort both keep stepping through the items without
-  // work, so every barrier sees both groups.
+  // Cell form: the two groups run half a tile apart (group 1 starts its
+  // first tile of a scene when group 0 has finished that tile's forward),
+  // so that one group's gather and scatter (memory) overlap the other's
+  // decoder (tensor cores); beyond that they synchronise only at scene
+  // changes and at the end.  The full and shifted forms, whose gather and
+  // scatter dominate, keep the groups in step (a CTA barrier per item:
+  // their gathers overlap each other).  After an abort both groups keep
+  // stepping through the items without work, so every barrier sees both.
+  constexpr bool SKEW = !FORMS;
   constexpr int SKEW_BAR = 1 + 2 * S::G;
   bool skew_pending = false;
   const WorkRange wr = work_range(p.n_items, p.order, p.run);
@@ -778,6 +781,10 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
     const DevScene& sc = p.sc[s];
     const QueryIn in = next;
     if (wr.next(item) < wr.end) next = item_query(wr.next(item));
+    if constexpr (!SKEW) {
+      tc_fence_before_sync();
+      __syncthreads();
+    }
     if (s != cur) {
       tc_fence_before_sync();
       __syncthreads();  // both groups are done with the previous scene
@@ -801,7 +808,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
       tree = stage_tree(p, sc, tree_sm, S::TREE_NODES, threadIdx.x, S::NTB);
       cur = s;
       __syncthreads();
-      skew_pending = true;
+      skew_pending = SKEW;
     }
     if (abort_flag) {  // keep the skew barrier's count, skip the work
       if (skew_pending) {
