@@ -866,14 +866,14 @@ def job_rate(units_per_rank, world, steps, total_ms):
     return world * units_per_rank * steps / (total_ms / 1e3) / 1e6
 
 
-LEGS = ("bf16_vs_f32", "inference", "small_forward", "encode", "encode_full", "encode_stress",
+LEGS = ("bf16_vs_f32", "train_f32", "inference", "small_forward", "encode", "encode_full", "encode_stress",
         "train_full", "multi_rhs", "shifted_train", "full_inference", "batched")
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
 # launch of each fused training pass, from one ncu capture of the current
 # kernel; None until taken, and reset to None whenever the kernel changes.
-F32_PASS_DRAM_BYTES = 22947072   # train_f32, 262,144 pairs, FP32 engine
-BF16_PASS_DRAM_BYTES = 89209600  # train_bf16, 1,048,576 pairs, tcgen05 kernel
+F32_PASS_DRAM_BYTES = 22947328   # train_f32, 262,144 pairs, FP32 engine
+BF16_PASS_DRAM_BYTES = 89768448  # train_bf16, 1,048,576 pairs, tcgen05 kernel
 
 
 def run_legs(args, names):
@@ -889,6 +889,7 @@ def run_legs(args, names):
     peaks, _ = _peaks()
     steps = max(3, args.steps)
     fns = {"bf16_vs_f32": lambda: bf16_vs_f32_leg(dev, flush, stream, steps, peaks),
+           "train_f32": lambda: train_f32_leg(dev, flush, stream, steps, peaks),
            "inference": lambda: inference_leg(dev, flush, stream, steps, peaks),
            "small_forward": lambda: small_forward_leg(dev, flush, stream, steps),
            "encode": lambda: encode_leg(dev, flush, stream, steps, peaks),
