@@ -311,11 +311,14 @@ int octa_disparity(const octa_predictor* pred, const octa_queries* q, float* dis
 
 /* octa_disparity_bwd -- g_psi's backward (Section 3.3: d is trained through
  * the radiance objective alone): the gradients of sum_q d_disp[q] d_q with
- * respect to the hash tables and the MLP weights.  Recomputes the forward in
- * FP32 on the CUDA cores (pred->weights; weights_bf16 is not read), back-
- * propagates through exp (dd/dz = d) and the ReLU layers, and scatter-adds
- * each level's two feature gradients into its cell's eight vertices with the
- * trilinear weights (float2 atomics).  ACCUMULATES (+=) into d_table
+ * respect to the hash tables and the MLP weights.  Recomputes the forward,
+ * back-propagates through exp (dd/dz = d) and the ReLU layers, and scatter-
+ * adds each level's two feature gradients into its cell's eight vertices
+ * with the trilinear weights (float2 atomics).  With pred->weights_bf16 NULL
+ * everything runs in FP32 on the CUDA cores (pred->weights); otherwise the
+ * MLP's forward and backward run on the tcgen05 tensor cores from the BF16
+ * weights (BF16 operands, FP32 accumulation; levels <= 14), as octa_disparity
+ * does.  ACCUMULATES (+=) into d_table
  * (device float32, layout of pred->table, 8-byte aligned) and d_weights
  * (device float32, layout of pred->weights), which the caller zeroes.
  * d_disp: device [n] float32 (the shifted backward's d_disparity).        */

@@ -258,6 +258,33 @@ __device__ __forceinline__ float2 hash_level(const float2* __restrict__ tab, con
   return make_float2(s0, s1);
 }
 
+// The trilinear scatter of one level's two feature gradients (g0, g1) into
+// the 8 vertices of x's cell, with the forward's cell, weights and entries.
+__device__ __forceinline__ void hash_level_scatter(float2* __restrict__ dtab, const float (&xs)[3],
+                                                   int N, bool dense, uint32_t tmask, float g0,
+                                                   float g1) {
+  const float fN = static_cast<float>(N);
+  uint32_t i0[3];
+  float f[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float pa = __fmul_rn(xs[a], fN);
+    const int c = min(static_cast<int>(floorf(pa)), N - 1);
+    i0[a] = static_cast<uint32_t>(c);
+    f[a] = __fsub_rn(pa, static_cast<float>(c));
+  }
+  const uint32_t side = static_cast<uint32_t>(N + 1);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const uint32_t i = i0[0] + (c & 1), j = i0[1] + ((c >> 1) & 1), k = i0[2] + (c >> 2);
+    const uint32_t e = dense ? i + side * (j + side * k)
+                             : (i ^ (j * 2654435761u) ^ (k * 805459861u)) & tmask;
+    const float w = ((c & 1) ? f[0] : 1.f - f[0]) * (((c >> 1) & 1) ? f[1] : 1.f - f[1]) *
+                    ((c >> 2) ? f[2] : 1.f - f[2]);
+    atomicAdd(dtab + e, make_float2(w * g0, w * g1));
+  }
+}
+
 // Cell j's shifted direction v_j = (x - c_j) d + omega_r (Eq. 9; c_j =
 // (c0 + offset_j + 1/2) 2^-l, exact) and e = x - c_j, one rounding per
 // operation.

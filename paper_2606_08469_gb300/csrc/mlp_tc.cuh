@@ -679,8 +679,14 @@ __device__ __forceinline__ void flush_loss(double& acc, double* loss, int64_t n_
 // launch applies Adam to every parameter group (persistent_adam).
 // FORMS: the kernel also serves the full and shifted query forms (scenes in
 // the cell form alone launch the FORMS = false instance, free of their code).
-template <class S, typename TT, bool TRAIN, bool PERSIST = false, bool FORMS = true>
+// PRED: the backward of the disparity predictor g_psi instead of the
+// decoder (input row = hash encoding and omega_r, one output channel
+// d = exp(z) whose upstream gradient is p.d_rgb[q] (one float a query), and
+// the input gradient's hash columns scattered into p.pred_dtable).
+template <class S, typename TT, bool TRAIN, bool PERSIST = false, bool FORMS = true,
+          bool PRED = false>
 __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ BwdParams bp) {
+  static_assert(!PRED || (!TRAIN && !FORMS && S::TPR == 1), "the predictor's backward");
   const QueryParams& p = bp.p;
   constexpr int H = S::H, NL = S::NL, TPR = S::TPR, NTG = S::NTG;
   static_assert(!FORMS || TPR == 1, "the full and shifted forms run one thread per row");
@@ -805,7 +811,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
               (n < out && k < in) ? Wg[sc.w_offset[l] + n * in + k] : __float2bfloat16_rn(0.f);
         }
       }
-      tree = stage_tree(p, sc, tree_sm, S::TREE_NODES, threadIdx.x, S::NTB);
+      if constexpr (!PRED) tree = stage_tree(p, sc, tree_sm, S::TREE_NODES, threadIdx.x, S::NTB);
       cur = s;
       __syncthreads();
       skew_pending = SKEW;
@@ -844,6 +850,8 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
       else
         locate_gather_bf16<S, TT>(p, sc, tree, in, gq, valid, 0, smem + S::off_act(g, 0), base_sm,
                                   u_sm, t);
+    } else if constexpr (PRED) {
+      predictor_gather<S>(p, in, gq, valid, smem + S::off_act(g, 0), t);
     } else {
       locate_gather_bf16<S, TT, TPR>(p, sc, tree, in, gq, valid, half, smem + S::off_act(g, 0),
                                      base_sm, u_sm, t);
@@ -861,6 +869,8 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
             in3b[c] = __ldcs(p.w + 3 * gq + c);
           }
         }
+      } else if constexpr (PRED) {
+        in3a[0] = __ldcs(p.d_rgb + gq);  // the output channel's gradient
       } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c) in3a[c] = __ldcs(p.d_rgb + 3 * gq + c);
@@ -1035,6 +1045,24 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
         fence_proxy_async();
         tc_fence_before_sync();
         named_sync(gbar, NTG);
+      } else if (PRED) {
+        // G = the gradient of g_psi's input row: each level's two hash
+        // features go to the 8 vertices of x's cell (trilinear weights)
+        uint32_t r[32];
+        tmem_ld16(lane_work, *reinterpret_cast<uint32_t(*)[16]>(r));
+        tmem_ld16(lane_work + 16, *reinterpret_cast<uint32_t(*)[16]>(r + 16));
+        tmem_wait_ld();
+        tc_fence_before_sync();
+        if (valid) {
+          const float xs[3] = {clamp01(qry.x0), clamp01(qry.x1), clamp01(qry.x2)};
+#pragma unroll
+          for (int l = 0; l < 14; ++l) {
+            if (l >= p.pred_levels) break;
+            float2* dtab = reinterpret_cast<float2*>(p.pred_dtable) + size_t(l) * (p.pred_tmask + 1u);
+            hash_level_scatter(dtab, xs, p.pred_res[l], p.pred_dense[l] != 0, p.pred_tmask,
+                               __uint_as_float(r[2 * l]), __uint_as_float(r[2 * l + 1]));
+          }
+        }
       } else if (!full && !shifted) {
         // dh = G; scatter w_k * dh_l into the four texels of each present
         // level of this thread's parity
@@ -1212,7 +1240,7 @@ int launch_fwd(const QueryParams& p, cudaStream_t stream) {
                                                          : launch_fwd_tpq<S, TT, 1>(p, tu, stream);
 }
 
-template <class S, typename TT, bool TRAIN, bool PERSIST, bool FORMS>
+template <class S, typename TT, bool TRAIN, bool PERSIST, bool FORMS, bool PRED = false>
 int launch_bwd(const QueryParams& p0, const AdamBlock* adam, cudaStream_t stream) {
   if (p0.n_tiles == 0 && !PERSIST) return OCTA_OK;
   constexpr int ROWS = TRAIN ? NT / 2 : NT;
@@ -1232,7 +1260,7 @@ int launch_bwd(const QueryParams& p0, const AdamBlock* adam, cudaStream_t stream
   p.order = tu.train_order == 1 ? 1 : 0;
   p.run = tu.train_run > 1 ? tu.train_run : 1;
   if (items == 0 && !PERSIST) return OCTA_OK;
-  auto kern = bwd_kernel<S, TT, TRAIN, PERSIST, FORMS>;
+  auto kern = bwd_kernel<S, TT, TRAIN, PERSIST, FORMS, PRED>;
   int per_sm = 0;
   int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, S::NTB,
                               static_cast<int>(S::TMEM_COLS), &per_sm);
@@ -1320,6 +1348,51 @@ int query_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cuda
 
 int train_fused(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream) {
   return dispatch_bwd<true, false>(scenes, n_scenes, p, nullptr, stream);
+}
+
+// g_psi's backward on the tensor cores: the decoder's backward kernel with the
+// predictor's input row, one output channel and the hash-table scatter.
+int predictor_bwd(const octa_predictor* pred, const octa_queries* q, const float* d_disp,
+                  float* d_table, float* d_weights, cudaStream_t stream) {
+  QueryParams p;
+  std::memset(&p, 0, sizeof(p));
+  const int L = pred->levels;
+  DevScene& d = p.sc[0];
+  d.weights = pred->weights_bf16;
+  d.d_weights = d_weights;
+  d.n_layers = 3;
+  d.K = 1;
+  d.widths[0] = 2 * L + 3;
+  d.widths[1] = OCTA_PRED_HIDDEN;
+  d.widths[2] = OCTA_PRED_HIDDEN;
+  d.widths[3] = 1;
+  int off = 0;
+  for (int i = 0; i <= 3; ++i) {
+    d.w_offset[i] = off;
+    if (i < 3) off += d.widths[i] * d.widths[i + 1];
+  }
+  d.q_begin = 0;
+  d.q_end = q->n;
+  d.norm_pairs = q->n;
+  p.n_scenes = 1;
+  p.n_tiles = (q->n + NT - 1) / NT;
+  p.x = q->x;
+  p.omega = q->omega;
+  p.normal = q->normal;
+  p.d_rgb = d_disp;
+  p.pred_table = pred->table;
+  p.pred_dtable = d_table;
+  p.pred_levels = L;
+  const int64_t T = int64_t(1) << pred->log2_T;
+  p.pred_tmask = static_cast<uint32_t>(T - 1);
+  for (int l = 0; l < L; ++l) {
+    p.pred_res[l] = pred->res[l];
+    const int64_t side = pred->res[l] + 1;
+    p.pred_dense[l] = side * side * side <= T ? 1 : 0;
+  }
+  if (p.n_tiles == 0) return OCTA_OK;
+  return launch_bwd<BShape<8, 32, 64, 2, 1>, __half, false, false, false, true>(p, nullptr,
+                                                                                 stream);
 }
 #endif  // OCTA_TC_BWD
 

@@ -92,6 +92,7 @@ struct QueryParams {
   int32_t pred_res[OCTA_PRED_MAX_LEVELS];
   int32_t pred_dense[OCTA_PRED_MAX_LEVELS];
   float* disparity_out;
+  float* pred_dtable;  // g_psi's backward: the hash tables' gradient (float2 entries)
 };
 
 // Decoder-input columns of level l >= K (past the features): Eq. 12's

@@ -155,33 +155,6 @@ struct PredBwdParams {
   int64_t n_tiles;
 };
 
-// The trilinear scatter of one level's two feature gradients (g0, g1) into
-// the 8 vertices of x's cell, with the forward's cell, weights and entries.
-__device__ __forceinline__ void hash_level_scatter(float2* __restrict__ dtab, const float (&xs)[3],
-                                                   int N, bool dense, uint32_t tmask, float g0,
-                                                   float g1) {
-  const float fN = static_cast<float>(N);
-  uint32_t i0[3];
-  float f[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float pa = __fmul_rn(xs[a], fN);
-    const int c = min(static_cast<int>(floorf(pa)), N - 1);
-    i0[a] = static_cast<uint32_t>(c);
-    f[a] = __fsub_rn(pa, static_cast<float>(c));
-  }
-  const uint32_t side = static_cast<uint32_t>(N + 1);
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const uint32_t i = i0[0] + (c & 1), j = i0[1] + ((c >> 1) & 1), k = i0[2] + (c >> 2);
-    const uint32_t e = dense ? i + side * (j + side * k)
-                             : (i ^ (j * 2654435761u) ^ (k * 805459861u)) & tmask;
-    const float w = ((c & 1) ? f[0] : 1.f - f[0]) * (((c >> 1) & 1) ? f[1] : 1.f - f[1]) *
-                    ((c >> 2) ? f[2] : 1.f - f[2]);
-    atomicAdd(dtab + e, make_float2(w * g0, w * g1));
-  }
-}
-
 __global__ void __launch_bounds__(kBwdThreads, 1) disparity_bwd_kernel(
     const __grid_constant__ PredBwdParams bp) {
   const PredParams& p = bp.p;
@@ -448,6 +421,14 @@ extern "C" int octa_disparity_bwd(const octa_predictor* pred, const octa_queries
     return fail(OCTA_EINVAL, "x, omega, normal, d_disp, d_table and d_weights must be non-NULL");
   if ((reinterpret_cast<uintptr_t>(pred->table) | reinterpret_cast<uintptr_t>(d_table)) & 7u)
     return fail(OCTA_EINVAL, "predictor table and its gradient must be 8-byte aligned");
+  if (pred->weights_bf16) {  // the MLP on the tensor cores
+    if (pred->levels > 14)
+      return fail(OCTA_ERANGE, "the tensor-core predictor takes at most 14 levels");
+    for (int l = 0; l < pred->levels; ++l)
+      if (pred->res[l] < 1 || pred->res[l] > 65535)
+        return fail(OCTA_ERANGE, "predictor res[%d] = %d outside [1, 65535]", l, pred->res[l]);
+    return tc::predictor_bwd(pred, q, d_disp, d_table, d_weights, static_cast<cudaStream_t>(stream));
+  }
   PredBwdParams bp{};
   PredParams& p = bp.p;
   p.table = pred->table;

@@ -29,6 +29,8 @@ int query_fwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cuda
 // weights_bf16, FP32 accumulation); the caller has validated pred and q.
 int predictor_fwd(const octa_predictor* pred, const octa_queries* q, float* disparity,
                   cudaStream_t stream);
+int predictor_bwd(const octa_predictor* pred, const octa_queries* q, const float* d_disp,
+                  float* d_table, float* d_weights, cudaStream_t stream);
 int query_bwd(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream);
 int train_fused(const octa_scene* scenes, int n_scenes, const QueryParams& p, cudaStream_t stream);
 int train_step_persistent(const octa_scene* scenes, int n_scenes, const QueryParams& p,

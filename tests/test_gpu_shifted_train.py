@@ -168,6 +168,45 @@ def test_disparity_backward_matches_oracle(levels, log2_T, n):
     assert max(errs) <= 1e-5, errs
 
 
+@pytest.mark.parametrize("levels,log2_T,n", [(8, 16, 3 * SMS * 256 + 33), (14, 12, 20001)])
+def test_disparity_backward_tensor_cores(levels, log2_T, n):
+    """octa_disparity_bwd on the tcgen05 path (the BF16 working copy of g_psi's
+    weights given): hash-table and weight gradients against the oracle's
+    disparity_backward on the BF16-rounded weights, within the BF16 path's
+    bound for gradients behind ReLU masks (3 sqrt(f) + 1e-2, f the fraction of
+    g_psi's hidden pre-activations within the BF16 forward error 2^-7 sum|w||a|
+    of zero), the last layer's within 1e-2; more than three tiles per group
+    slot and a ragged tail in the first case."""
+    from paper_2606_08469_gb300 import api as A
+    res = O.hash_resolutions(levels, 16, 512)
+    table, pw = I.predictor_params(2350 + levels, levels, log2_T, table_scale=0.3)
+    pw = [W * F32(2.0) for W in pw]
+    x, w, nrm, _, g = _queries(2360 + levels, n)
+    c = g.normal(size=n).astype(F32)
+    pred = A.Predictor(table, res, pw, device=DEV, tensor_cores=True)
+    pq = [W.astype(np.float32) for W in
+          np.split(pred.weights_bf16.float().cpu().numpy(),
+                   np.cumsum([W.size for W in pw])[:-1])]
+    pq = [Wf.reshape(W.shape) for Wf, W in zip(pq, pw)]
+    d_tab = torch.zeros(pred.table.shape, device=DEV)
+    d_w = torch.zeros(pred.weights.shape, device=DEV)
+    A.octa_disparity_bwd(pred, dev(x), dev(w), dev(nrm), dev(c), d_tab, d_w)
+    rtab, rWs = O.disparity_backward(table, res, pq, x, w, nrm, c)
+    inp = np.concatenate([O.hash_encode(table, res, x), O.reflect_f32(w, nrm).astype(np.float64)],
+                         axis=1)
+    a, flags = inp, []
+    for W in [np.asarray(W, np.float64) for W in pq][:-1]:
+        z = a @ W.T
+        flags.append((np.abs(z) < 2.0 ** -7 * (np.abs(a) @ np.abs(W).T)).ravel())
+        a = np.maximum(z, 0.0)
+    frac = float(np.mean(np.concatenate(flags)))
+    errs = [normwise(d_tab.cpu().numpy(), rtab)] + weight_errors(d_w.cpu().numpy(), rWs)
+    bound = 3.0 * np.sqrt(frac) + 1e-2
+    print(f"tensor-core g_psi backward levels={levels}", [f"{e:.2e}" for e in errs],
+          "mask fraction", round(frac, 5), "bound", round(bound, 4))
+    assert errs[-1] <= 1e-2 and max(errs) <= bound
+
+
 def _step_inputs(n_pairs, seed=2400):
     """A shifted-form training batch: depth-5 tree with vertex maps, F = 8
     FP32 tables, decoder 48-64-64-3, an 8-level g_psi, pairs with normals."""
