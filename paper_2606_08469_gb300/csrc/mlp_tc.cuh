@@ -1097,17 +1097,23 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
           }
         }
       } else {
-        // full and shifted forms (one thread per row): dh by level from a
-        // thread-local copy (their level loops stay rolled)
-        uint32_t r[S::WP];
+        // full and shifted forms (one thread per row): the row's dh is copied
+        // once into shared memory -- the group's h, delta_1 and delta_2
+        // tiles, whose MMAs have all completed -- and read there level by
+        // level (the level loops stay rolled; no register copy of the row)
+        constexpr int DHS = S::WP + 4;  // row stride (floats): conflict-free float4 rows
+        static_assert(NT * DHS * 4 <= S::H_TILE + 2 * S::A_TILE, "dh rows in h, a_1, a_2");
+        float* dh = reinterpret_cast<float*>(smem + S::off_act(g, 0)) + t * DHS;
 #pragma unroll
-        for (int c = 0; c < S::WP; c += 16)
-          tmem_ld16(lane_work + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
-        tmem_wait_ld();
+        for (int c = 0; c < S::WP; c += 16) {
+          uint32_t r[16];
+          tmem_ld16(lane_work + c, r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int k = 0; k < 16; k += 4)
+            *reinterpret_cast<uint4*>(dh + c + k) = make_uint4(r[k], r[k + 1], r[k + 2], r[k + 3]);
+        }
         tc_fence_before_sync();
-        float dh[S::WP];
-#pragma unroll
-        for (int c = 0; c < S::WP; ++c) dh[c] = __uint_as_float(r[c]);
         if (full) {  // the 24 vertices of each level (Eq. 10 with Eq. 6)
           if (valid) {
             float ux, uy;

@@ -456,3 +456,58 @@ def test_shifted_train_step_wrapper_and_graph():
                  (a.pred_state.pred.table, b.pred_state.pred.table),
                  (a.pred_state.pred.weights, b.pred_state.pred.weights)):
         assert e(u, v) <= 1e-6, e(u, v)
+
+
+def test_training_entry_point_errors():
+    """Refusals of the new arguments: d_disparity outside the shifted form,
+    the shifted fused pass without the secondaries' inputs, the one-launch
+    step in the shifted form, and octa_disparity_bwd with missing arrays or
+    more than 14 levels on the tensor cores; an empty batch does nothing."""
+    from paper_2606_08469_gb300 import _lib as L
+    from paper_2606_08469_gb300 import api as A
+    V = [5, 5, 3]
+    tree = A.octree_build(2700, 2, 0.8, V)
+    tables = I.make_tables(2701, tree.num_texels, 8, 0.3)
+    weights = [dev(W) for W in I.make_mlp(2702, [24, 64, 64, 3])]
+    cell = A.Scene(tree, dev(tables), weights, device=DEV)
+    sh = A.Scene(tree, dev(tables), weights, device=DEV, query_form=L.OCTA_FORM_SHIFTED)
+    x, w, nrm, d, g = _queries(2703, 300)
+    X, Wd, Nd, Dd = dev(x), dev(w), dev(nrm), dev(d)
+    d_rgb = dev(g.normal(size=(300, 3)).astype(F32))
+    dT = torch.zeros((tree.num_texels, 8), device=DEV)
+    dW = torch.zeros(cell.weights.shape, device=DEV)
+    dd = torch.zeros(300, device=DEV)
+    with pytest.raises(L.OctaError) as e:
+        A.octa_query_bwd(cell, X, Wd, d_rgb, [(dT, dW)], d_disparity=dd)
+    assert e.value.code == L.OCTA_EINVAL
+    loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+    E = torch.zeros((300, 3), device=DEV)
+    with pytest.raises(L.OctaError) as e:      # no normal2 / disparity2
+        A.octa_train_fused(sh, X, Wd, X, -Wd, E, E, [(dT, dW)], loss,
+                           shift=(Nd, None, Dd, None, None, None))
+    assert e.value.code == L.OCTA_EINVAL
+    scaler = A.make_scaler(device=DEV)
+    ws = A.workspace(L.OCTA_OP_STEP, 0, device=DEV)
+    groups = [A.ParamGroup(dT.reshape(-1).clone(), dT.reshape(-1), torch.zeros_like(dT).reshape(-1),
+                           torch.zeros_like(dT).reshape(-1), 1e-2)]
+    with pytest.raises(L.OctaError) as e:      # the one-launch step: no shifted form
+        A.octa_train_step_batched(sh, X, Wd, X, -Wd, E, E, [(dT, dW)], groups, loss, scaler, ws)
+    assert e.value.code == L.OCTA_EUNSUPPORTED
+    table, pw = I.predictor_params(2704, 15, 10)
+    res = O.hash_resolutions(15, 4, 64)
+    pred = A.Predictor(table, res, pw, device=DEV, tensor_cores=True)
+    d_tab = torch.zeros(pred.table.shape, device=DEV)
+    d_w = torch.zeros(pred.weights.shape, device=DEV)
+    with pytest.raises(L.OctaError) as e:      # 15 levels on the tensor cores
+        A.octa_disparity_bwd(pred, X, Wd, Nd, dd, d_tab, d_w)
+    assert e.value.code == L.OCTA_ERANGE
+    pred32 = A.Predictor(table, res, pw, device=DEV)
+    q = A._queries(X, Wd, None)                # no normal
+    with pytest.raises(L.OctaError) as e:
+        L.check(A._lib().octa_disparity_bwd(A.C.byref(pred32.as_c()), A.C.byref(q),
+                                            A._ptr(dd), A._ptr(d_tab), A._ptr(d_w),
+                                            A._stream()), "octa_disparity_bwd")
+    assert e.value.code == L.OCTA_EINVAL
+    A.octa_disparity_bwd(pred32, X[:0], Wd[:0], Nd[:0], dd[:0], d_tab, d_w)
+    torch.cuda.synchronize()
+    assert float(d_tab.abs().sum()) == 0.0 and float(d_w.abs().sum()) == 0.0
