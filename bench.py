@@ -418,7 +418,8 @@ def inference_leg(dev, flush, stream, steps, peaks):
             from paper_2606_08469_gb300 import autotune as T
             if prec == "bf16":
                 best, rep = T.autotune(fn, {"fwd_threads_per_query": [1, 2], "fwd_order": [1, 2],
-                                            "fwd_run": [1, 2, 4], "fwd_ctas_per_sm": [0, 2, 3]},
+                                            "fwd_run": [1, 2, 4], "fwd_ctas_per_sm": [0, 2, 3],
+                                            "l1_carveout": [1, 2]},
                                        f"gbuffer-forward-{w_}x{h_}", reps=5)
             g = _graph(fn, stream)
             g.replay()
@@ -462,7 +463,13 @@ def encode_leg(dev, flush, stream, steps, peaks):
                                     None, None, None, api._stream()), "octa_encode")
     for _ in range(3):
         fn()
+    from paper_2606_08469_gb300 import autotune as T
+    best, rep = T.autotune(fn, {"gather_stages": [1, 2, 3, 4], "l1_carveout": [1, 2]},
+                           "gbuffer-encode-1280x720", reps=5)
+    for _ in range(3):
+        fn()
     t = _timed(fn, steps, flush, stream)
+    T.set_tuning(None)
     table_bytes = tree.num_texels * cfg.F * 2
     alg = len(x) * (24 + 2 * W) + table_bytes
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -470,6 +477,8 @@ def encode_leg(dev, flush, stream, steps, peaks):
     return {"workload": f"gbuffer_frame encoding alone: {len(x)} queries, depth-8 octree, FP16 table, "
                         f"{W} BF16 features per query out",
             "ms": round(t, 4), "Mq/s": round(len(x) / t / 1e3, 1),
+            "autotune": {"best": best, "best_ms": rep["best_ms"], "default_ms": rep["default_ms"],
+                         "gain": rep["gain"], "trials": rep["trials"]},
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(ach / peak, 4),
                          "algorithmic_bytes": alg,

@@ -514,6 +514,20 @@ typedef struct octa_tuning {
   int32_t train_run;           /* the same for the backward and training
                                   kernels (work units: tensor-core items of
                                   two 128-row tiles, FP32 tiles)           */
+  int32_t gather_stages;       /* cell-form gathers of 16-byte texels at one
+                                  thread per query (octa_encode): 1 (default)
+                                  = the texel loads land in registers, two
+                                  levels in flight; 2..4 = they land in a shared-
+                                  memory ring (cp.async) of that many
+                                  levels, all in flight (8 KB of shared
+                                  memory per level and 128-query CTA)      */
+  int32_t l1_carveout;         /* shared-memory carveout of the gather,
+                                  forward and FP32 kernels: 1 = the largest
+                                  (least L1 cache), 2 (default) = the smallest that
+                                  holds their resident CTAs, the rest of
+                                  the SM's L1 / shared array caching the
+                                  texel loads.  The one-launch training
+                                  step always takes the largest.           */
 } octa_tuning;
 int octa_set_tuning(const octa_tuning* t);   /* NULL restores the defaults */
 int octa_get_tuning(octa_tuning* t);

@@ -145,7 +145,8 @@ class octa_tuning(C.Structure):
                 ("engine_ctas_per_sm", C.c_int32), ("fwd_order", C.c_int32),
                 ("train_order", C.c_int32), ("fwd_threads_per_query", C.c_int32),
                 ("encode_threads_per_query", C.c_int32), ("train_threads_per_row", C.c_int32),
-                ("fwd_run", C.c_int32), ("train_run", C.c_int32)]
+                ("fwd_run", C.c_int32), ("train_run", C.c_int32), ("gather_stages", C.c_int32),
+                ("l1_carveout", C.c_int32)]
 
 
 class octa_step_options(C.Structure):

@@ -22,7 +22,7 @@ from . import _lib as L
 
 KNOBS = ("fwd_ctas_per_sm", "encode_ctas_per_sm", "engine_ctas_per_sm", "fwd_order", "train_order",
          "fwd_threads_per_query", "encode_threads_per_query", "train_threads_per_row", "fwd_run",
-         "train_run")
+         "train_run", "gather_stages", "l1_carveout")
 
 
 def get_tuning():

@@ -29,4 +29,4 @@ int fail(int code, const char* fmt, ...) {
 }  // namespace octa
 
 extern "C" const char* octa_last_error(void) { return octa::g_msg; }
-extern "C" int32_t octa_abi_version(void) { return 7; }
+extern "C" int32_t octa_abi_version(void) { return 8; }

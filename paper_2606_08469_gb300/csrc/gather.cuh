@@ -14,6 +14,50 @@ __device__ __forceinline__ void fma_f16x2_f32(float& s0, float& s1, uint16_t w, 
       : "r"(t), "h"(w));
 }
 
+// The fold of omega (Eq. 4, 5) and the walk of one query down the octree
+// (Section 3.4): mo[o] = map base of level o * TPQ + par on the query's path
+// (-1: absent or not this thread's level); returns the path's depth (0 for
+// an invalid row).  Node records come from the staged tree (global memory
+// when tree is nullptr); thread par 0 writes node_idx when requested.
+template <int KP, int TPQ>
+__device__ __forceinline__ int walk_query(const QueryParams& p, const DevScene& sc, const int2* tree,
+                                          const QueryIn& in, int64_t gq, bool valid, int par,
+                                          int (&mo)[(KP + TPQ - 1) / TPQ], float& ux, float& uy) {
+  constexpr int KO = (KP + TPQ - 1) / TPQ;
+  octa_fold(in.w0, in.w1, in.w2, ux, uy);
+  const int cx = min(static_cast<int>(clamp01(in.x0) * 32768.f), 32767);
+  const int cy = min(static_cast<int>(clamp01(in.x1) * 32768.f), 32767);
+  const int cz = min(static_cast<int>(clamp01(in.x2) * 32768.f), 32767);
+  const bool out_nodes = p.node_idx != nullptr && valid && par == 0;
+#pragma unroll
+  for (int o = 0; o < KO; ++o) mo[o] = -1;
+  int depth = 0;
+  int nd = valid ? 0 : -1;
+#pragma unroll
+  for (int l = 0; l < KP; ++l) {
+    if (nd < 0) break;
+    depth = l + 1;
+    if (out_nodes && l < p.kmax_out) p.node_idx[gq * p.kmax_out + l] = nd;
+    int2 rec;
+    if (tree) {
+      rec = tree[nd];
+    } else {
+      rec = make_int2(__ldg(sc.first_child + nd), __ldg(sc.map_offset + nd));
+      if (rec.x >= 0 && rec.x > sc.num_nodes - 8) {
+        if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
+        rec.x = -1;
+      }
+    }
+    if (l % TPQ == par) mo[l / TPQ] = checked_map_base(p, sc, rec.y, sc.R[l]);
+    if (l + 1 >= KP || l + 1 >= sc.K || rec.x < 0) break;
+    const int sh = 14 - l;  // level l + 1
+    nd = rec.x + (((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2));
+  }
+  if (out_nodes)
+    for (int l = depth; l < p.kmax_out; ++l) p.node_idx[gq * p.kmax_out + l] = -1;
+  return depth;
+}
+
 // One query per TPQ threads: each folds omega (Eq. 4, 5, canonical
 // binary32) and walks the query's path down the octree (Section 3.4),
 // reading node records from the staged tree (global memory when tree is
@@ -45,38 +89,8 @@ __device__ __forceinline__ void locate_gather_query(const QueryParams& p, const 
   constexpr int WIN = (TexelRaw<TT, F>::BYTES <= 16 && TPQ == 1) ? 2 : 1;
   constexpr int KO = (KP + TPQ - 1) / TPQ;  // level slots of one thread
   float ux, uy;
-  octa_fold(in.w0, in.w1, in.w2, ux, uy);
-  const int cx = min(static_cast<int>(clamp01(in.x0) * 32768.f), 32767);
-  const int cy = min(static_cast<int>(clamp01(in.x1) * 32768.f), 32767);
-  const int cz = min(static_cast<int>(clamp01(in.x2) * 32768.f), 32767);
-  const bool out_nodes = p.node_idx != nullptr && valid && par == 0;
   int mo[KO];  // map base of level o * TPQ + par, -1 when absent
-#pragma unroll
-  for (int o = 0; o < KO; ++o) mo[o] = -1;
-  int depth = 0;  // levels on the query's path (0 for an invalid row)
-  int nd = valid ? 0 : -1;
-#pragma unroll
-  for (int l = 0; l < KP; ++l) {
-    if (nd < 0) break;
-    depth = l + 1;
-    if (out_nodes && l < p.kmax_out) p.node_idx[gq * p.kmax_out + l] = nd;
-    int2 rec;
-    if (tree) {
-      rec = tree[nd];
-    } else {
-      rec = make_int2(__ldg(sc.first_child + nd), __ldg(sc.map_offset + nd));
-      if (rec.x >= 0 && rec.x > sc.num_nodes - 8) {
-        if (p.status) atomicOr(p.status, OCTA_STATUS_BAD_CHILD);
-        rec.x = -1;
-      }
-    }
-    if (l % TPQ == par) mo[l / TPQ] = checked_map_base(p, sc, rec.y, sc.R[l]);
-    if (l + 1 >= KP || l + 1 >= sc.K || rec.x < 0) break;
-    const int sh = 14 - l;  // level l + 1
-    nd = rec.x + (((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2));
-  }
-  if (out_nodes)
-    for (int l = depth; l < p.kmax_out; ++l) p.node_idx[gq * p.kmax_out + l] = -1;
+  const int depth = walk_query<KP, TPQ>(p, sc, tree, in, gq, valid, par, mo, ux, uy);
   if (base_sm) {
 #pragma unroll
     for (int o = 0; o < KO; ++o)
@@ -157,6 +171,132 @@ __device__ __forceinline__ void locate_gather_query(const QueryParams& p, const 
     }
   }
   if (p.texel_addr && valid && par == 0)
+    for (int l = KP; l < p.kmax_out; ++l)
+      *reinterpret_cast<int4*>(p.texel_addr + (gq * p.kmax_out + l) * 4) = make_int4(-1, -1, -1, -1);
+}
+
+// Asynchronous 16-byte global -> shared copies (cp.async, allocating in L1),
+// their commit groups and the wait for all but the N newest groups.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ uint4 ld_shared_v4(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(a)
+               : "memory");
+  return v;
+}
+
+// locate_gather_query for 16-byte texels at one thread per query with the
+// texel loads landing in shared memory instead of registers: after the walk,
+// the four texels of NS levels are in flight at once (one cp.async group a
+// level); level o is blended when its group has arrived, handed to
+// store(o, v), and its slot then refilled with level o + NS.  ring: the
+// CTA's [NS][4][nt] staging area of 16-byte chunks (16-byte aligned shared
+// address); thread q owns chunk q of each (slot, corner) row, so a warp's
+// copies and reads of one corner are 512 contiguous bytes.  store must write
+// shared memory (it orders the slot's reads before the refill).  Results are
+// those of locate_gather_query<F, TT, KP, F16W, 1>.
+template <int F, typename TT, int KP, bool F16W, int NS, class Store>
+__device__ __forceinline__ void locate_gather_query_staged(const QueryParams& p, const DevScene& sc,
+                                                           const int2* tree, const QueryIn& in,
+                                                           int64_t gq, bool valid, uint32_t ring,
+                                                           int q, int nt, Store&& store) {
+  static_assert(TexelRaw<TT, F>::BYTES == 16, "16-byte texels");
+  static_assert(NS >= 2 && NS <= KP, "stages");
+  float ux, uy;
+  int mo[KP];
+  const int depth = walk_query<KP, 1>(p, sc, tree, in, gq, valid, 0, mo, ux, uy);
+  const int dw = __reduce_max_sync(0xffffffffu, depth);
+  const uint4* tab = static_cast<const uint4*>(sc.tables);
+  float wt[NS][4];
+  auto chunk = [&](int slot, int k) {
+    return ring + static_cast<uint32_t>(((slot * 4 + k) * nt + q) * 16);
+  };
+  auto issue = [&](int o) {
+    if (o < KP && mo[o] >= 0) {
+      const Footprint fp = footprint(ux, uy, sc.R[o]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        wt[o % NS][k] = fp.w[k];
+        cp_async16(chunk(o % NS, k), tab + static_cast<uint32_t>(mo[o] + fp.idx[k]));
+      }
+    }
+    cp_async_commit();  // an empty group past the path keeps the count
+  };
+#pragma unroll
+  for (int o = 0; o < NS; ++o) issue(o);
+#pragma unroll
+  for (int o = 0; o < KP; ++o) {
+    float v[F];
+    if (o >= dw) {  // warp-uniform: no lane has these levels
+#pragma unroll
+      for (int f = 0; f < F; ++f) v[f] = 0.f;
+      store(o, v);
+      if (p.texel_addr && valid && o < p.kmax_out)
+        *reinterpret_cast<int4*>(p.texel_addr + (gq * p.kmax_out + o) * 4) =
+            make_int4(-1, -1, -1, -1);
+      continue;
+    }
+    cp_async_wait<NS - 1>();  // level o's group has landed
+    if (mo[o] >= 0) {
+      TexelRaw<TT, F> t[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint4 a = ld_shared_v4(chunk(o % NS, k));
+        t[k].w[0] = a.x;
+        t[k].w[1] = a.y;
+        t[k].w[2] = a.z;
+        t[k].w[3] = a.w;
+      }
+      if constexpr (F16W && sizeof(TT) == 2) {
+        uint16_t w16[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w16[k] = __half_as_ushort(__float2half_rn(wt[o % NS][k]));
+#pragma unroll
+        for (int i = 0; i < F / 2; ++i) {
+          float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) fma_f16x2_f32(s0, s1, w16[k], t[k].w[i]);
+          v[2 * i] = s0;
+          v[2 * i + 1] = s1;
+        }
+      } else {
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+          float s = wt[o % NS][0] * t[0].get(f);
+          s = fmaf(wt[o % NS][1], t[1].get(f), s);
+          s = fmaf(wt[o % NS][2], t[2].get(f), s);
+          s = fmaf(wt[o % NS][3], t[3].get(f), s);
+          v[f] = s;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int f = 0; f < F; ++f) v[f] = 0.f;
+    }
+    store(o, v);
+    if (p.texel_addr && valid && o < p.kmax_out) {
+      int4 a = make_int4(-1, -1, -1, -1);
+      if (mo[o] >= 0) {
+        const Footprint fp = footprint(ux, uy, sc.R[o]);
+        a = make_int4(mo[o] + fp.idx[0], mo[o] + fp.idx[1], mo[o] + fp.idx[2], mo[o] + fp.idx[3]);
+      }
+      *reinterpret_cast<int4*>(p.texel_addr + (gq * p.kmax_out + o) * 4) = a;
+    }
+    issue(o + NS);
+  }
+  cp_async_wait<0>();
+  if (p.texel_addr && valid)
     for (int l = KP; l < p.kmax_out; ++l)
       *reinterpret_cast<int4*>(p.texel_addr + (gq * p.kmax_out + l) * 4) = make_int4(-1, -1, -1, -1);
 }

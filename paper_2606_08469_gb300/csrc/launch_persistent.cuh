@@ -12,13 +12,14 @@ namespace octa {
 // Persistent grid: as many CTAs as fit on the device, never more than tiles.
 // cap bounds the resident CTAs per SM (0: none); order is the work order of
 // work_range (1: contiguous chunks, else interleaved, `run` consecutive
-// tiles at a time).
+// tiles at a time); the shared-memory carveout follows the l1_carveout knob.
 template <class Kern>
 int launch_persistent(Kern kernel, size_t smem, const QueryParams& p0, cudaStream_t stream,
                       int threads, int cap, int order, int run = 1) {
   if (p0.n_tiles == 0) return OCTA_OK;
   int per_sm = 0;
-  int rc = launch_cache().get(reinterpret_cast<const void*>(kernel), smem, threads, 0, &per_sm);
+  int rc = launch_cache().get(reinterpret_cast<const void*>(kernel), smem, threads, 0, &per_sm,
+                              carve_mode(tuning_snapshot()));
   if (rc) return rc;
   per_sm = apply_cap(per_sm, cap);
   QueryParams p = p0;

@@ -40,6 +40,28 @@ inline int ctas_from_resources(const void* fn, size_t smem, int threads) {
   return std::max(1, n);
 }
 
+// Shared-memory carveout modes of the launch cache: the largest carveout
+// (least L1), or the smallest one that still holds the resident CTAs (the
+// rest of the SM's 256 KB of L1 / shared memory stays L1 cache).
+constexpr int kCarveMaxShared = 1, kCarveFit = 2;
+
+// The carveout preference, in percent of the SM's shared memory, that holds
+// per_sm CTAs of smem dynamic bytes (plus static and reserved bytes); the
+// driver rounds a preference up to the next configuration it supports.
+inline int fit_carveout_percent(const void* fn, size_t smem, int per_sm) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) return 100;
+  int dev = 0, sm_smem = 0, rsv = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (sm_smem <= 0) return 100;
+  const size_t need = static_cast<size_t>(per_sm) *
+                      (smem + a.sharedSizeBytes + static_cast<size_t>(rsv));
+  const size_t pct = (need * 100 + static_cast<size_t>(sm_smem) - 1) / static_cast<size_t>(sm_smem);
+  return static_cast<int>(std::min<size_t>(100, pct + 1));  // one percent of slack
+}
+
 // Sets the kernel's dynamic shared-memory limit and the largest shared-memory
 // carveout, then returns the resident CTAs per SM.  For kernels that
 // allocate tensor memory (tmem_cols > 0) the count comes from the kernel's
@@ -66,27 +88,45 @@ inline int resident_ctas(const void* fn, size_t smem, size_t attr_smem, int thre
   return OCTA_OK;
 }
 
-// Cache of resident_ctas() per (kernel, device, shared-memory size).
+// Cache of resident_ctas() per (kernel, device, shared-memory size), and the
+// carveout each kernel was last given: get() applies the requested mode's
+// carveout for that launch when it differs from the kernel's current one
+// (a host-side attribute change; launches of one stream capture keep one
+// mode per kernel).
 class LaunchCache {
  public:
-  int get(const void* fn, size_t smem, int threads, int tmem_cols, int* out) {
+  int get(const void* fn, size_t smem, int threads, int tmem_cols, int* out,
+          int carve = kCarveMaxShared) {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu_);
     size_t attr = smem;
+    int hit = -1;
     for (int i = 0; i < n_; ++i) {
       if (e_[i].fn != fn || e_[i].dev != dev) continue;
-      if (e_[i].smem == smem) {
-        *out = e_[i].per_sm;
-        return OCTA_OK;
-      }
+      if (e_[i].smem == smem) hit = i;
       attr = std::max(attr, e_[i].smem);
     }
-    int per_sm = 0;
-    int rc = resident_ctas(fn, smem, attr, threads, tmem_cols, &per_sm);
-    if (rc) return rc;
-    if (n_ < kMax) e_[n_++] = Entry{fn, dev, smem, per_sm};
-    *out = per_sm;
+    if (hit < 0) {
+      int per_sm = 0;
+      int rc = resident_ctas(fn, smem, attr, threads, tmem_cols, &per_sm);
+      if (rc) return rc;
+      if (n_ >= kMax) {
+        *out = per_sm;
+        return OCTA_OK;  // the largest carveout stays set
+      }
+      e_[n_] = Entry{fn, dev, smem, per_sm, fit_carveout_percent(fn, smem, per_sm)};
+      hit = n_++;
+      set_current(fn, dev, 100);
+    }
+    const int want = carve == kCarveFit ? e_[hit].fit_pct : 100;
+    if (current(fn, dev) != want) {
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, want);
+      if (e != cudaSuccess)
+        return fail(OCTA_ECUDA, "cudaFuncSetAttribute(carveout): %s", cudaGetErrorString(e));
+      set_current(fn, dev, want);
+    }
+    *out = e_[hit].per_sm;
     return OCTA_OK;
   }
 
@@ -96,10 +136,31 @@ class LaunchCache {
     int dev;
     size_t smem;
     int per_sm;
+    int fit_pct;  // carveout percent that holds per_sm CTAs
   };
+  struct Carve {
+    const void* fn;
+    int dev;
+    int pct;
+  };
+  int current(const void* fn, int dev) const {
+    for (int i = 0; i < nc_; ++i)
+      if (c_[i].fn == fn && c_[i].dev == dev) return c_[i].pct;
+    return 100;
+  }
+  void set_current(const void* fn, int dev, int pct) {
+    for (int i = 0; i < nc_; ++i)
+      if (c_[i].fn == fn && c_[i].dev == dev) {
+        c_[i].pct = pct;
+        return;
+      }
+    if (nc_ < kMax) c_[nc_++] = Carve{fn, dev, pct};
+  }
   static constexpr int kMax = 256;
   Entry e_[kMax];
   int n_ = 0;
+  Carve c_[kMax];
+  int nc_ = 0;
   std::mutex mu_;
 };
 
@@ -120,6 +181,13 @@ inline std::mutex& tuning_mutex() {
 inline octa_tuning tuning_snapshot() {
   std::lock_guard<std::mutex> lock(tuning_mutex());
   return tuning();
+}
+// The carveout mode of the launch-cache kernels (l1_carveout knob, 0 = the
+// default).
+constexpr int kDefaultCarve = kCarveFit;
+inline int carve_mode(const octa_tuning& t) {
+  return t.l1_carveout == kCarveFit || t.l1_carveout == kCarveMaxShared ? t.l1_carveout
+                                                                        : kDefaultCarve;
 }
 // Resident CTAs per SM after an optional cap (0 = no cap).
 inline int apply_cap(int per_sm, int cap) { return cap > 0 ? std::max(1, std::min(per_sm, cap)) : per_sm; }

@@ -214,7 +214,9 @@ __global__ void __launch_bounds__(NT * TPQ, 4)
   static_assert(HC % 16 == 0, "epilogue column split");
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* act = smem + S::OFF_ACT;
-  int2* tree_sm = S::TREE_NODES > 0 ? reinterpret_cast<int2*>(smem + S::OFF_TREE) : nullptr;
+  // staged octree: p.tree_cap nodes (sized by the launcher, at most
+  // S::TREE_NODES) after the fixed part of the layout
+  int2* tree_sm = p.tree_cap > 0 ? reinterpret_cast<int2*>(smem + S::OFF_TREE) : nullptr;
   const int2* tree = nullptr;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::OFF_BAR);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::OFF_BAR + 8);
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(NT * TPQ, 4)
     if (s != cur) {
       load_weights_bf16<S>(sc, smem, NTF);
       if constexpr (FORM != FORM_PREDICTOR)
-        tree = stage_tree(p, sc, tree_sm, S::TREE_NODES, threadIdx.x, NTF);
+        tree = stage_tree(p, sc, tree_sm, p.tree_cap, threadIdx.x, NTF);
       cur = s;
       __syncthreads();
     }
@@ -1219,16 +1221,25 @@ namespace {
 template <class S, typename TT, int TPQ, int FORM = OCTA_FORM_CELL_BILINEAR>
 int launch_fwd_tpq(const QueryParams& p, const octa_tuning& tu, cudaStream_t stream) {
   auto kern = fwd_kernel<S, TT, TPQ, FORM>;
+  // the staged tree holds the largest scene that fits S::TREE_NODES, in
+  // granules of 16 nodes; shared memory past it can stay L1 cache
+  int nodes = 0;
+  if constexpr (FORM != FORM_PREDICTOR)
+    for (int s = 0; s < p.n_scenes; ++s)
+      if (p.sc[s].num_nodes <= S::TREE_NODES) nodes = std::max(nodes, p.sc[s].num_nodes);
+  const int cap = std::min(S::TREE_NODES, (nodes + 15) & ~15);
+  const size_t smem = S::OFF_TREE + 8u * static_cast<size_t>(cap);
   int per_sm = 0;
-  int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, NT * TPQ,
-                              static_cast<int>(S::TMEM_COLS), &per_sm);
+  int rc = launch_cache().get(reinterpret_cast<const void*>(kern), smem, NT * TPQ,
+                              static_cast<int>(S::TMEM_COLS), &per_sm, carve_mode(tu));
   if (rc) return rc;
   per_sm = apply_cap(per_sm, tu.fwd_ctas_per_sm);
   QueryParams pp = p;
   pp.order = tu.fwd_order == 1 ? 1 : 0;
   pp.run = tu.fwd_run > 1 ? tu.fwd_run : 1;
+  pp.tree_cap = cap;
   const int64_t grid = std::min<int64_t>(p.n_tiles, int64_t(per_sm) * device_sm_count());
-  kern<<<static_cast<unsigned>(grid), NT * TPQ, S::SMEM, stream>>>(pp);
+  kern<<<static_cast<unsigned>(grid), NT * TPQ, smem, stream>>>(pp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(OCTA_ECUDA, "tc fwd launch: %s", cudaGetErrorString(e));
   return OCTA_OK;
@@ -1268,8 +1279,10 @@ int launch_bwd(const QueryParams& p0, const AdamBlock* adam, cudaStream_t stream
   if (items == 0 && !PERSIST) return OCTA_OK;
   auto kern = bwd_kernel<S, TT, TRAIN, PERSIST, FORMS, PRED>;
   int per_sm = 0;
+  // the cooperative launch keeps the largest carveout: all CTAs co-resident
   int rc = launch_cache().get(reinterpret_cast<const void*>(kern), S::SMEM, S::NTB,
-                              static_cast<int>(S::TMEM_COLS), &per_sm);
+                              static_cast<int>(S::TMEM_COLS), &per_sm,
+                              PERSIST ? kCarveMaxShared : carve_mode(tu));
   if (rc) return rc;
   cudaError_t e;
   if (PERSIST) {  // every CTA co-resident: the grid barriers need it

@@ -70,6 +70,8 @@ struct QueryParams {
   // in nodes (0: walk in global memory) and byte offset in dynamic memory
   int32_t tree_cap;
   int32_t tree_off;
+  // byte offset in dynamic shared memory of the staged gather's texel ring
+  int32_t ring_off;
   // the shifted form's per-query inputs (normal [n][3], disparity [n]); in
   // the fused training pass those of the primaries, the secondaries' in
   // normal2 / disparity2

@@ -24,10 +24,13 @@ namespace octa {
 // output rows are packed), so the feature stream is written coalesced.
 constexpr int ENC_NT = 128;
 
+// NS > 0: the cell form's texels staged through a ring of NS levels in
+// shared memory (locate_gather_query_staged) at p.ring_off.
 template <int F, typename TT, typename OT, int KP, int FORM = OCTA_FORM_CELL_BILINEAR,
-          int TPQ = 1>
+          int TPQ = 1, int NS = 0>
 __global__ void __launch_bounds__(ENC_NT * TPQ) encode_kernel(const __grid_constant__ QueryParams p) {
   static_assert(TPQ == 1 || FORM == OCTA_FORM_CELL_BILINEAR, "threads per query: cell form");
+  static_assert(NS == 0 || (TPQ == 1 && FORM == OCTA_FORM_CELL_BILINEAR), "staged: cell form");
   constexpr int NTH = ENC_NT * TPQ;  // TPQ threads per query, thread par gathers levels l % TPQ
   extern __shared__ __align__(16) uint8_t stage[];
   const int q = threadIdx.x % ENC_NT, par = threadIdx.x / ENC_NT;
@@ -76,6 +79,10 @@ __global__ void __launch_bounds__(ENC_NT * TPQ) encode_kernel(const __grid_const
                                       stage_row);
     else if constexpr (FORM == OCTA_FORM_TRILINEAR_VERTEX)
       gather_full_query<F, TT, KP>(p, sc, tree, in, q0 + q, q < nq, stage_row);
+    else if constexpr (NS > 0)
+      locate_gather_query_staged<F, TT, KP, sizeof(OT) == 2, NS>(
+          p, sc, tree, in, q0 + q, q < nq,
+          static_cast<uint32_t>(__cvta_generic_to_shared(stage + p.ring_off)), q, ENC_NT, stage_row);
     else
       locate_gather_query<F, TT, KP, sizeof(OT) == 2, TPQ>(p, sc, tree, in, q0 + q, q < nq, par,
                                                             nullptr, nullptr, q, ENC_NT, stage_row);
@@ -102,6 +109,37 @@ namespace {
 bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
 
 }  // namespace
+
+// Texel-ring depth of the staged cell-form gathers (16-byte texels, one
+// thread per query): the gather_stages knob, 0 = the default.
+constexpr int kDefaultGatherStages = 1;
+int gather_stages(const octa_tuning& tu) {
+  return tu.gather_stages > 0 ? tu.gather_stages : kDefaultGatherStages;
+}
+
+// The cell-form encoding at one thread per query: texel loads into
+// registers (ns < 2) or a shared-memory ring of ns (2..4) levels (16-byte
+// texels only); smem: the staging rows and the tree, the ring after them.
+template <int F, typename TT, typename OT, int KP, int NS>
+int launch_encode_cell_ns(size_t smem, QueryParams& p, cudaStream_t st, const octa_tuning& tu) {
+  return launch_persistent(encode_kernel<F, TT, OT, KP, OCTA_FORM_CELL_BILINEAR, 1, NS>, smem, p,
+                           st, ENC_NT, tu.encode_ctas_per_sm, tu.fwd_order, tu.fwd_run);
+}
+
+template <int F, typename TT, typename OT, int KP>
+int launch_encode_cell(int ns, size_t smem, QueryParams& p, cudaStream_t st,
+                       const octa_tuning& tu) {
+  if constexpr (F * sizeof(TT) == 16) {
+    if (ns >= 2) {
+      p.ring_off = static_cast<int32_t>((smem + 15) & ~size_t(15));
+      smem = size_t(p.ring_off) + size_t(ns) * 4 * ENC_NT * 16;
+      if (ns == 2) return launch_encode_cell_ns<F, TT, OT, KP, 2>(smem, p, st, tu);
+      if (ns == 3) return launch_encode_cell_ns<F, TT, OT, KP, 3>(smem, p, st, tu);
+      return launch_encode_cell_ns<F, TT, OT, KP, 4>(smem, p, st, tu);
+    }
+  }
+  return launch_encode_cell_ns<F, TT, OT, KP, 0>(smem, p, st, tu);
+}
 
 // Validates scenes + queries and fills the kernel parameter block.
 int build_query_params(const octa_scene* scenes, int32_t n_scenes, const octa_queries* q,
@@ -267,11 +305,11 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
   p.status = status;
   const size_t ot = feat_dtype == OCTA_BF16 ? 2 : 4;
   size_t smem = size_t(ENC_NT) * ((size_t(kmax) * F * ot + 15) & ~size_t(15));
-  // staged octree: the largest scene's nodes in granules of 256, at most 2048
+  // staged octree: the largest scene's nodes in granules of 16, at most 2048
   int max_nodes = 0;
   for (int s = 0; s < n_scenes; ++s) max_nodes = std::max(max_nodes, scenes[s].num_nodes);
   if (max_nodes <= 2048) {
-    p.tree_cap = (max_nodes + 255) & ~255;
+    p.tree_cap = (max_nodes + 15) & ~15;
     p.tree_off = static_cast<int32_t>(smem);
     smem += size_t(p.tree_cap) * 8;
   }
@@ -295,14 +333,16 @@ extern "C" int octa_encode(const octa_scene* scenes, int32_t n_scenes, const oct
   if (form == OCTA_FORM_TRILINEAR_VERTEX) {                       \
     OCTA_ENC_FORM(F_, TT_, KP_, OCTA_FORM_TRILINEAR_VERTEX)       \
   }                                                               \
-  if (tu.encode_threads_per_query == 2) {                         \
-    return bf ? launch_persistent(                                \
-                    encode_kernel<F_, TT_, __nv_bfloat16, KP_, OCTA_FORM_CELL_BILINEAR, 2>, \
-                    smem, p, st, 2 * ENC_NT, tu.encode_ctas_per_sm, tu.fwd_order, tu.fwd_run)           \
-              : launch_persistent(encode_kernel<F_, TT_, float, KP_, OCTA_FORM_CELL_BILINEAR, 2>, \
-                                  smem, p, st, 2 * ENC_NT, tu.encode_ctas_per_sm, tu.fwd_order, tu.fwd_run); \
-  }                                                               \
-  OCTA_ENC_FORM(F_, TT_, KP_, OCTA_FORM_CELL_BILINEAR)
+  if (tu.encode_threads_per_query != 2)                            \
+    return bf ? launch_encode_cell<F_, TT_, __nv_bfloat16, KP_>(gather_stages(tu), smem, p, st, \
+                                                                tu)                         \
+              : launch_encode_cell<F_, TT_, float, KP_>(gather_stages(tu), smem, p, st, tu);  \
+  return bf ? launch_persistent(                                  \
+                  encode_kernel<F_, TT_, __nv_bfloat16, KP_, OCTA_FORM_CELL_BILINEAR, 2>, smem, p, \
+                  st, 2 * ENC_NT, tu.encode_ctas_per_sm, tu.fwd_order, tu.fwd_run)         \
+            : launch_persistent(encode_kernel<F_, TT_, float, KP_, OCTA_FORM_CELL_BILINEAR, 2>, \
+                                smem, p, st, 2 * ENC_NT, tu.encode_ctas_per_sm, tu.fwd_order, \
+                                tu.fwd_run);
 #define OCTA_ENC_KP(F_, TT_)      \
   if (kmax <= 10) {               \
     OCTA_ENC(F_, TT_, 10)         \
@@ -523,7 +563,8 @@ extern "C" int octa_set_tuning(const octa_tuning* t) {
       t->fwd_threads_per_query < 0 || t->fwd_threads_per_query > 2 ||
       t->encode_threads_per_query < 0 || t->encode_threads_per_query > 2 ||
       t->train_threads_per_row < 0 || t->train_threads_per_row > 2 || t->fwd_run < 0 ||
-      t->fwd_run > 64 || t->train_run < 0 || t->train_run > 64)
+      t->fwd_run > 64 || t->train_run < 0 || t->train_run > 64 || t->gather_stages < 0 ||
+      t->gather_stages > 4 || t->l1_carveout < 0 || t->l1_carveout > 2)
     return fail(OCTA_EINVAL, "tuning values out of range");
   tuning() = *t;
   return OCTA_OK;

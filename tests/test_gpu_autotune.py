@@ -36,7 +36,8 @@ def test_forward_results_independent_of_knobs():
                     {"fwd_order": 1}, {"fwd_threads_per_query": 2},
                     {"fwd_threads_per_query": 2, "fwd_order": 1, "fwd_ctas_per_sm": 3},
                     {"fwd_run": 3}, {"fwd_run": 8, "fwd_ctas_per_sm": 2},
-                    {"fwd_run": 64, "fwd_threads_per_query": 2}):
+                    {"fwd_run": 64, "fwd_threads_per_query": 2}, {"l1_carveout": 2},
+                    {"l1_carveout": 2, "fwd_threads_per_query": 2}, {"l1_carveout": 1}):
         T.set_tuning(setting)
         got, gn, ga = A.octa_query_fwd(sc, X, W, want_nodes=True, want_addr=True)
         torch.testing.assert_close(got, ref, rtol=0, atol=0)
@@ -85,3 +86,34 @@ def test_autotune_picks_and_caches(tmp_path):
         assert any(k.endswith("|test-fwd") for k in json.load(f))
     best2, rep2 = T.autotune(fn, {"fwd_ctas_per_sm": [2, 4]}, "test-fwd", cache)
     assert best2 == best and rep2["best_ms"] == rep["best_ms"]     # served from the cache
+
+
+@pytest.mark.parametrize("name,dtypes", [("gbuffer_frame", (torch.bfloat16, torch.float32)),
+                                         ("forward_small", (torch.float32,))])
+def test_encode_results_independent_of_gather_stages(name, dtypes):
+    """The texel ring (gather_stages 2..4, cp.async into shared memory) gives
+    the register window's features, node indices and texel addresses bit for
+    bit: FP16 texels of 8 features and FP32 texels of 4 (both 16 bytes)."""
+    from paper_2606_08469_gb300 import api as A
+    from paper_2606_08469_gb300 import autotune as T
+    from paper_2606_08469_gb300 import workloads as WL
+    cfg = I.WORKLOADS[name]
+    sc, _ = WL.forward_scene(cfg)
+    x, w = I.uniform_queries(5, 40000)
+    X, W = WL.to_dev(x), WL.to_dev(w)
+    counts = [333, len(x) - 333]              # two scenes, a ragged first tile
+    for dt in dtypes:
+        T.set_tuning({"gather_stages": 1})
+        ref, rn, ra = A.octa_encode(sc, X, W, feat_dtype=dt, want_nodes=True, want_addr=True)
+        ref2, _, _ = A.octa_encode([sc, sc], X, W, counts, feat_dtype=dt)
+        for setting in ({"gather_stages": 2}, {"gather_stages": 3},
+                        {"gather_stages": 4, "encode_ctas_per_sm": 2},
+                        {"gather_stages": 3, "fwd_order": 1, "fwd_run": 4},
+                        {"l1_carveout": 1}, {"l1_carveout": 2, "gather_stages": 2},
+                        {"l1_carveout": 1, "gather_stages": 4, "fwd_run": 3}):
+            T.set_tuning(setting)
+            got, gn, ga = A.octa_encode(sc, X, W, feat_dtype=dt, want_nodes=True, want_addr=True)
+            assert torch.equal(got, ref), setting
+            assert torch.equal(gn, rn) and torch.equal(ga, ra)
+            got2, _, _ = A.octa_encode([sc, sc], X, W, counts, feat_dtype=dt)
+            assert torch.equal(got2, ref2), setting

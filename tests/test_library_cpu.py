@@ -45,7 +45,7 @@ def test_struct_sizes_match_header(lib):
     """The ctypes mirrors have the C layout (checked through a sizing call)."""
     from paper_2606_08469_gb300 import _lib as L
     assert C.sizeof(L.octa_tree_desc) == 4 + 4 + 8 + 4 * 16 + 4 * 17 + 4 + 8 * 17
-    assert lib.octa_abi_version() == 7
+    assert lib.octa_abi_version() == 8
     assert C.sizeof(L.octa_prims) == 8 + 8 + 4 + 4
     assert C.sizeof(L.octa_queries) == 8 + 8 + 8 + 8 * 17 + 8 + 8 + 8 + 4 + 4 + 8
     assert C.sizeof(L.octa_predictor) == 8 + 8 + 8 + 4 + 4 + 4 * 16
@@ -129,6 +129,14 @@ def test_tuning_knobs_round_trip(lib):
     bad = L.octa_tuning()
     bad.fwd_order = 7
     assert lib.octa_set_tuning(C.byref(bad)) == L.OCTA_EINVAL
+    for field, value in (("gather_stages", 5), ("l1_carveout", 3), ("fwd_run", 65)):
+        bad = L.octa_tuning()
+        setattr(bad, field, value)
+        assert lib.octa_set_tuning(C.byref(bad)) == L.OCTA_EINVAL, field
+    T.set_tuning({"gather_stages": 3, "l1_carveout": 1})
+    got = T.get_tuning()
+    assert got["gather_stages"] == 3 and got["l1_carveout"] == 1
+    assert C.sizeof(L.octa_tuning) == 12 * 4
     T.set_tuning(None)
     assert all(v == 0 for v in T.get_tuning().values())
 
