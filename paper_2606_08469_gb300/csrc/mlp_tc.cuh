@@ -360,11 +360,14 @@ struct BShape : Shape<F_, WP_, H_, NH_> {
   static constexpr uint32_t GR_DL = H_TILE + NH_ * A_TILE;
   static constexpr uint32_t GR_NODE = GR_DL + DL_TILE + 2048;
   static constexpr uint32_t GR_U = GR_NODE + B::NODE_BYTES;
-  static constexpr uint32_t GR_XCH = GR_U + B::U_BYTES;  // [64][4] floats (fused pass)
+  // folded direction of each row, one copy per thread of the row: with two
+  // threads per row, one may start the next tile's gather while the other
+  // still scatters the current one
+  static constexpr uint32_t GR_XCH = GR_U + TPR_ * B::U_BYTES;  // [64][4] floats (fused pass)
   static constexpr uint32_t GR_BYTES = (GR_XCH + 64 * 4 * 4 + 1023) & ~1023u;
   static constexpr uint32_t OFF_GROUP = (B::W_BYTES + 1023) & ~1023u;
   static constexpr uint32_t OFF_BAR = OFF_GROUP + G * GR_BYTES;
-  // two mbarriers per group (the MMAs of its two issuing threads), then the
+  // two mbarriers per group (the backward's dW^T and G MMAs), then the
   // tensor-memory address slot
   static constexpr uint32_t OFF_TREE = (OFF_BAR + 16 * G + 8 + 15) & ~15u;
   static constexpr int TREE_NODES = tree_capacity(OFF_TREE, 1);
@@ -699,22 +702,19 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
   const int half = (threadIdx.x % NTG) / NT;  // column half / level parity of the row
   uint8_t* gbase = smem + S::OFF_GROUP + g * S::GR_BYTES;
   int* base_sm = reinterpret_cast<int*>(gbase + S::GR_NODE);  // map base per level
-  float* u_sm = reinterpret_cast<float*>(gbase + S::GR_U);
+  float* u_sm = reinterpret_cast<float*>(gbase + S::GR_U) + half * 2 * NT;  // this thread's copy
   int2* tree_sm = S::TREE_NODES > 0 ? reinterpret_cast<int2*>(smem + S::OFF_TREE) : nullptr;
   const int2* tree = nullptr;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::OFF_BAR);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::OFF_BAR + 16 * S::G);
   __shared__ int abort_flag;
   const uint32_t mbar = smem_addr(bars + g);
-  const uint32_t mbar2 = smem_addr(bars + S::G + g);  // the second issuer's
+  const uint32_t mbar2 = smem_addr(bars + S::G + g);  // the backward's G MMAs
   const uint32_t base_sa = smem_addr(smem);
   const uint32_t dl_sa = base_sa + S::off_dl(g);
   const int gbar = 1 + g;                         // named barrier of this group
   const int xbar = TPR == 1 ? gbar : 1 + S::G + g;  // its half-0 threads alone
   const bool lead = t == 0 && half == 0;           // issues the group's MMAs
-  // the backward's G = delta W_i MMAs come from a second thread (another
-  // warp), so that its issue runs beside the lead's dW MMAs
-  const bool issuer2 = t == 32 && half == 0;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2 * S::G; ++i) mbar_init(smem_addr(bars + i), 1);
@@ -992,17 +992,9 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
       const int dk = out;  // row length of the delta tile
       if (lead) {
         tc_fence_after_sync();
-        // dW_i^T += a_i^T delta_{i+1}: M = 128 input features, N = out, K = 128 queries
-        const uint32_t act_sa = base_sa + S::off_act(g, i);
-        const uint32_t idw = idesc_bf16(128, out, 1, 1);
-#pragma unroll 1
-        for (int kq = 0; kq < NT; kq += 16)
-          mma_bf16(tmem + S::dw_col(i), mnmajor_desc(act_sa, kq, in), mnmajor_desc(d_sa, kq, dk),
-                   idw, 1u);
-        mma_commit(mbar);
-      } else if (issuer2) {
-        tc_fence_after_sync();
-        // G = delta_{i+1} W_i: M = 128 queries, N = in, K = out
+        // G = delta_{i+1} W_i first (M = 128 queries, N = in, K = out): the
+        // epilogue needs it; then dW_i^T += a_i^T delta_{i+1} (M = 128 input
+        // features, N = out, K = 128 queries), which runs under the epilogue
         const uint32_t ig = idesc_bf16(128, in, 0, 1);
         const uint32_t w_sa = base_sa + S::w_off(i);
 #pragma unroll 1
@@ -1010,18 +1002,21 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
           mma_bf16(work, kmajor_desc(d_sa, ko, dk), mnmajor_desc(w_sa, ko, in), ig,
                    ko > 0 ? 1u : 0u);
         mma_commit(mbar2);
+        const uint32_t act_sa = base_sa + S::off_act(g, i);
+        const uint32_t idw = idesc_bf16(128, out, 1, 1);
+#pragma unroll 1
+        for (int kq = 0; kq < NT; kq += 16)
+          mma_bf16(tmem + S::dw_col(i), mnmajor_desc(act_sa, kq, in), mnmajor_desc(d_sa, kq, dk),
+                   idw, 1u);
+        mma_commit(mbar);
       }
-      const bool ok = mbar_wait_bounded(mbar, phase, wait_ns) &&
-                      mbar_wait_bounded(mbar2, phase2, wait_ns);
-      phase ^= 1u;
+      bool ok = mbar_wait_bounded(mbar2, phase2, wait_ns);  // G
       phase2 ^= 1u;
-      if (named_sync_or(gbar, NTG, !ok)) {
-        failed = true;
-        break;
-      }
-      tc_fence_after_sync();
       if (i > 0) {
-        // delta_i = G * 1[a_i > 0], written over a_i (its MMAs have completed)
+        // delta_i = G * 1[a_i > 0], formed while dW_i^T still reads a_i and
+        // written over a_i once it has completed; a wait that ran out is
+        // reported at the closing barrier
+        tc_fence_after_sync();
         const int c0 = half * HC;
         uint32_t r[HC];
 #pragma unroll
@@ -1029,10 +1024,10 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
           tmem_ld16(lane_work + c0 + c, *reinterpret_cast<uint32_t(*)[16]>(r + c));
         tmem_wait_ld();
         uint8_t* act = smem + S::off_act(g, i);
+        uint4 dv[HC / 8];
 #pragma unroll
         for (int c = 0; c < HC; c += 8) {
-          uint4* pa = reinterpret_cast<uint4*>(act + kmajor_offset(t, c0 + c, H));
-          const uint4 a = *pa;
+          const uint4 a = *reinterpret_cast<const uint4*>(act + kmajor_offset(t, c0 + c, H));
           const uint32_t av[4] = {a.x, a.y, a.z, a.w};
           uint32_t ov[4];
 #pragma unroll
@@ -1042,12 +1037,30 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
             const float g1 = ((av[j] >> 16) & 0x7FFFu) ? __uint_as_float(r[c + 2 * j + 1]) : 0.f;
             ov[j] = pack_bf16x2(g0, g1);
           }
-          *pa = make_uint4(ov[0], ov[1], ov[2], ov[3]);
+          dv[c / 8] = make_uint4(ov[0], ov[1], ov[2], ov[3]);
         }
+        ok = mbar_wait_bounded(mbar, phase, wait_ns) && ok;  // dW_i^T
+        phase ^= 1u;
+#pragma unroll
+        for (int c = 0; c < HC; c += 8)
+          *reinterpret_cast<uint4*>(act + kmajor_offset(t, c0 + c, H)) = dv[c / 8];
         fence_proxy_async();
         tc_fence_before_sync();
-        named_sync(gbar, NTG);
-      } else if (PRED) {
+        if (named_sync_or(gbar, NTG, !ok)) {
+          failed = true;
+          break;
+        }
+        continue;
+      }
+      // layer 0: both MMAs complete before the input gradient leaves
+      ok = mbar_wait_bounded(mbar, phase, wait_ns) && ok;
+      phase ^= 1u;
+      if (named_sync_or(gbar, NTG, !ok)) {
+        failed = true;
+        break;
+      }
+      tc_fence_after_sync();
+      if (PRED) {
         // G = the gradient of g_psi's input row: each level's two hash
         // features go to the 8 vertices of x's cell (trilinear weights)
         uint32_t r[32];
