@@ -818,16 +818,6 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
       __syncthreads();
       skew_pending = SKEW;
     }
-    if (abort_flag) {  // keep the skew barrier's count, skip the work
-      if (skew_pending) {
-        if (g == 0)
-          named_arrive(SKEW_BAR, S::NTB);
-        else
-          named_sync(SKEW_BAR, S::NTB);
-        skew_pending = false;
-      }
-      continue;
-    }
     if (g == 1 && skew_pending) {  // group 0's first tile of the scene is past its forward
       named_sync(SKEW_BAR, S::NTB);
       skew_pending = false;
@@ -878,9 +868,18 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
         for (int c = 0; c < 3; ++c) in3a[c] = __ldcs(p.d_rgb + 3 * gq + c);
       }
     }
-    // the previous tile's tensor-memory reads come before this tile's MMAs
+    // the previous tile's tensor-memory reads come before this tile's MMAs;
+    // an abort (a bounded wait that ran out, in any group) is read here by
+    // the whole group at once: the group then steps through its remaining
+    // items without MMAs, keeping the skew barrier's count
     tc_fence_before_sync();
-    named_sync(gbar, NTG);
+    if (named_sync_or(gbar, NTG, abort_flag != 0)) {
+      if (g == 0 && skew_pending) {
+        named_arrive(SKEW_BAR, S::NTB);
+        skew_pending = false;
+      }
+      continue;
+    }
 
     bool failed = false;
     // ---- forward, keeping a_1 .. a_NH and delta_L
@@ -1052,7 +1051,9 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
         }
         continue;
       }
-      // layer 0: both MMAs complete before the input gradient leaves
+      // layer 0: both MMAs complete before the input gradient leaves (the
+      // full and shifted forms write dh over h and a_1, and the next tile's
+      // gather overwrites h)
       ok = mbar_wait_bounded(mbar, phase, wait_ns) && ok;
       phase ^= 1u;
       if (named_sync_or(gbar, NTG, !ok)) {
@@ -1209,7 +1210,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
         }
       }
     }
-    if (failed && lead) {
+    if (failed) {  // read by every group at its next post-gather barrier
       abort_flag = 1;
       if (p.status) atomicOr(p.status, OCTA_STATUS_TIMEOUT);
     }
