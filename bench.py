@@ -384,6 +384,30 @@ def measure_ffma_peak(dev, reps=5):
                    "FMA chains, best of 5"}
 
 
+def measure_mma_cost(dev, reps=41):
+    """Cycles per tcgen05.mma (M = 128, K = 16, BF16 in, FP32 accumulate) of
+    the decoders' shapes, issued from one thread in runs of k_steps along K
+    and committed (octa_measure_mma, one CTA): issue cycles and issue-to-
+    completion cycles per MMA, one or two issuing threads per SM, and the
+    math-only bound at the measured burst BF16 peak per SM for comparison."""
+    import torch
+    from paper_2606_08469_gb300 import api
+    lib = api._lib()
+    out = torch.zeros(3, dtype=torch.int64, device=dev)
+    res = {}
+    for n, k, iss in ((64, 4, 1), (64, 5, 1), (64, 4, 2), (128, 4, 1), (256, 4, 1)):
+        api.L.check(lib.octa_measure_mma(api._ptr(out), n, k, reps, iss, api._stream()),
+                    "octa_measure_mma")
+        h = out.tolist()
+        m = (reps - 1) * k
+        res[f"n{n}_k{16 * k}_issuers{iss}"] = {"issue_cyc_per_mma": round(h[0] / m, 1),
+                                               "complete_cyc_per_mma": round(h[1] / m, 1),
+                                               "ok": bool(h[2])}
+    return {"shapes": res,
+            "how": f"octa_measure_mma: M = 128, K = 16 per MMA, k_steps MMAs then a commit, "
+                   f"{reps - 1} timed repetitions, clock64 of the issuing thread"}
+
+
 def _f32_peak(peaks):
     """FP32 FFMA peak: the measured microbenchmark figure when one is on
     record, else 152 SMs x 128 lanes x 2 flop at the maximum SM clock."""
@@ -1171,6 +1195,7 @@ def run_ours(args):
         extra_steps = max(5, args.steps // 2)
         out["ffma_peak"] = measure_ffma_peak(dev)
         peaks = dict(peaks, f32_ffma_tflops=out["ffma_peak"]["f32_ffma_tflops"])
+        out["mma_cost"] = measure_mma_cost(dev)
         if not args.no_extra:
             out["bf16_vs_f32"] = bf16_vs_f32_leg(dev, flush, stream, extra_steps, peaks,
                                                  out["value"])

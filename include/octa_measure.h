@@ -2,7 +2,9 @@
  * octa_measure.h -- measurement utilities of the OctaOctree library (no
  * counterpart in the paper): a microbenchmark that gives the FP32 CUDA-core
  * kernels (the FP32 decoder engine) a measured peak to report their
- * roofline against, in place of a figure derived from unit counts.
+ * roofline against, in place of a figure derived from unit counts, and one
+ * that measures the cost of a tensor-core MMA of the decoders' shapes (the
+ * instruction rate that bounds the tensor-core training pass).
  */
 #ifndef OCTA_MEASURE_H
 #define OCTA_MEASURE_H
@@ -26,6 +28,25 @@ extern "C" {
  * 1024), OCTA_ECUDA (launch error).                                       */
 int octa_measure_ffma(float* out, int32_t blocks, int32_t threads, int32_t iters, int32_t packed,
                       void* stream);
+
+/* octa_measure_mma -- enqueue one single-CTA launch that times the 5th-
+ * generation tensor-core MMA of the decoders (tcgen05.mma kind::f16: BF16
+ * operands in canonical K-major shared-memory tiles without swizzle, FP32
+ * accumulator in tensor memory, M = 128 rows, N = n columns, K = 16 per
+ * instruction).  `issuers` threads (1 or 2, each with its own tiles,
+ * accumulator columns and mbarrier) each issue k_steps MMAs along K
+ * (descriptors advancing 16 elements per step) and commit, `reps` times;
+ * the operands are pseudo-random BF16 values.  out: device int64[3],
+ * written when the launch completes: [0] the first issuer's cycles
+ * (clock64) spent issuing, [1] its cycles from the first issue to the
+ * commit's completion, both summed over reps - 1 repetitions (the first is
+ * a warm-up), [2] 1, or 0 if a completion wait ran out (100 ms bound).
+ * Divide by (reps - 1) * k_steps for cycles per MMA.  n: multiple of 16 in
+ * [16, 256]; k_steps in [1, 8]; reps in [2, 10000].  Uses 193 KB of shared
+ * memory and 512 tensor-memory columns of one SM.
+ * Errors: OCTA_EINVAL (argument out of range, NULL out), OCTA_ECUDA.     */
+int octa_measure_mma(int64_t* out, int32_t n, int32_t k_steps, int32_t reps, int32_t issuers,
+                     void* stream);
 
 #ifdef __cplusplus
 }

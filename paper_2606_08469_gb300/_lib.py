@@ -210,6 +210,7 @@ _SIGNATURES = {
     "octa_last_error": (C.c_char_p, []),
     "octa_abi_version": (C.c_int32, []),
     "octa_measure_ffma": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P]),
+    "octa_measure_mma": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P]),
 }
 
 _lib = None

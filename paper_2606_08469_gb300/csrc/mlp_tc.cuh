@@ -268,6 +268,9 @@ __global__ void __launch_bounds__(NT * TPQ, 4)
 #pragma unroll 1
     for (int layer = 0; layer < S::NL; ++layer) {
       if (threadIdx.x == 0) issue_layer<S>(layer, act_sa, w_sa, tmem, mbar);
+      // warp 0 reconverges before its other threads poll the mbarrier:
+      // their polls would otherwise interleave with the issue
+      __syncwarp();
       const bool ok = mbar_wait_bounded(mbar, phase);
       phase ^= 1u;
       if (__syncthreads_or(!ok)) {
@@ -887,13 +890,14 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
     for (int layer = 0; layer < NL; ++layer) {
       if (lead && !(skip_hook && layer == 0))
         issue_layer<S>(layer, base_sa + S::off_act(g, layer), base_sa, work, mbar);
+      // the issuing warp reconverges before its other threads poll the
+      // mbarrier: their polls would otherwise interleave with the issue
+      __syncwarp();
       skip_hook = false;
+      // a wait that ran out is reported at the barrier that closes the
+      // epilogue (the epilogue then reads undefined accumulators, unused)
       const bool ok = mbar_wait_bounded(mbar, phase, wait_ns);
       phase ^= 1u;
-      if (named_sync_or(gbar, NTG, !ok)) {
-        failed = true;
-        break;
-      }
       tc_fence_after_sync();
       if (layer < NL - 1) {
         const int c0 = half * HC;
@@ -976,7 +980,10 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
       }
       fence_proxy_async();
       tc_fence_before_sync();
-      named_sync(gbar, NTG);
+      if (named_sync_or(gbar, NTG, !ok)) {
+        failed = true;
+        break;
+      }
     }
     if (g == 0 && skew_pending) {  // releases group 1 (also after a failed forward)
       named_arrive(SKEW_BAR, S::NTB);
@@ -1009,6 +1016,7 @@ __global__ void __launch_bounds__(S::NTB, 1) bwd_kernel(const __grid_constant__ 
                    idw, 1u);
         mma_commit(mbar);
       }
+      __syncwarp();  // as in the forward
       bool ok = mbar_wait_bounded(mbar2, phase2, wait_ns);  // G
       phase2 ^= 1u;
       if (i > 0) {

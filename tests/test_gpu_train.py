@@ -268,3 +268,22 @@ def test_pair_inputs_can_be_swapped():
     bad = dict(copies, Px=copies["Px"][:-1])
     with pytest.raises(ValueError):
         b.set_pair_inputs(bad)
+
+
+def test_measure_mma_reports_cycles():
+    """The MMA microbenchmark completes and reports positive cycle counts,
+    the completion after the issue, more cycles for wider N."""
+    import torch
+    from paper_2606_08469_gb300 import api
+    lib = api._lib()
+    out = torch.zeros(3, dtype=torch.int64, device="cuda")
+    got = {}
+    for n in (64, 256):
+        api.L.check(lib.octa_measure_mma(api._ptr(out), n, 4, 11, 1, api._stream()),
+                    "octa_measure_mma")
+        issue, done, ok = out.tolist()
+        assert ok == 1 and 0 < issue <= done
+        got[n] = done
+    assert got[256] > got[64]
+    api.L.check(lib.octa_measure_mma(api._ptr(out), 64, 5, 3, 2, api._stream()), "octa_measure_mma")
+    assert out.tolist()[2] == 1

@@ -34,11 +34,22 @@ def _declared_functions():
 def test_header_symbols_exported(lib):
     names = _declared_functions()
     assert {"octree_build", "octa_query_fwd", "octa_query_bwd", "residual_loss",
-            "adam_step", "octa_measure_ffma"} <= set(names)
+            "adam_step", "octa_measure_ffma", "octa_measure_mma"} <= set(names)
     for n in names:
         assert hasattr(lib, n), n
     from paper_2606_08469_gb300 import _lib
     assert set(_lib._SIGNATURES) >= set(names)
+
+
+def test_measure_mma_validation_without_gpu(lib):
+    """octa_measure_mma checks its arguments on the host before any launch."""
+    from paper_2606_08469_gb300 import _lib as L
+    buf = (C.c_int64 * 3)()
+    ptr = C.cast(buf, C.c_void_p)
+    assert lib.octa_measure_mma(None, 64, 4, 5, 1, None) == L.OCTA_EINVAL
+    for n, k, reps, iss in ((8, 4, 5, 1), (72, 4, 5, 1), (272, 4, 5, 1), (64, 0, 5, 1),
+                            (64, 9, 5, 1), (64, 4, 1, 1), (64, 4, 5, 3), (64, 4, 5, 0)):
+        assert lib.octa_measure_mma(ptr, n, k, reps, iss, None) == L.OCTA_EINVAL, (n, k, reps, iss)
 
 
 def test_struct_sizes_match_header(lib):
