@@ -24,6 +24,26 @@ namespace octa {
 // output rows are packed), so the feature stream is written coalesced.
 constexpr int ENC_NT = 128;
 
+// Bulk asynchronous copy of `bytes` (multiple of 16) from shared to global
+// memory (both addresses 16-byte aligned), committed as one bulk group; the
+// waits for the source to have been read, and for the copy to have landed.
+__device__ __forceinline__ void bulk_copy_s2g(void* dst, uint32_t src, uint32_t bytes) {
+  asm volatile(
+      "cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
+      "cp.async.bulk.commit_group;\n" ::"l"(dst),
+      "r"(src), "r"(bytes)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
 // NS > 0: the cell form's texels staged through a ring of NS levels in
 // shared memory (locate_gather_query_staged) at p.ring_off.
 template <int F, typename TT, typename OT, int KP, int FORM = OCTA_FORM_CELL_BILINEAR,
@@ -40,22 +60,43 @@ __global__ void __launch_bounds__(ENC_NT * TPQ) encode_kernel(const __grid_const
   int cur = -1;
   const WorkRange wr = work_range(p.n_tiles, p.order, p.run);
   QueryIn next = wr.begin < wr.end ? load_tile_query(p, wr.begin, q, ENC_NT) : QueryIn{};
+  // a bulk copy of staging rows in flight (thread 0 of the CTA, or lane 0
+  // of a warp that copies its own rows)
+  bool bulk_pending = false;
+  // the previous tile's rows were read out warp by warp (no CTA-wide reads
+  // of them can be in flight)
+  bool prev_warp_rows = true;
+  const int lane = threadIdx.x & 31;
   for (int64_t tile = wr.begin; tile < wr.end; tile = wr.next(tile)) {
     const int s = scene_of_tile(p, tile);
     const DevScene& sc = p.sc[s];
     const QueryIn in = next;
     if (wr.next(tile) < wr.end) next = load_tile_query(p, wr.next(tile), q, ENC_NT);
     if (s != cur) {
-      __syncthreads();
+      __syncthreads();  // no thread walks the previous scene's tree any more
       tree = stage_tree(p, sc, tree_sm, p.tree_cap, threadIdx.x, NTH);
       cur = s;
+      __syncthreads();
     }
     const int64_t q0 = sc.q_begin + (tile - sc.tile_begin) * ENC_NT;
     const int nq = static_cast<int>(sc.q_end - q0 < ENC_NT ? sc.q_end - q0 : int64_t(ENC_NT));
     const int W = sc.K * F;
     const int row_bytes = W * int(sizeof(OT));
     const int rb = (row_bytes + 15) & ~15;  // staging row stride
-    __syncthreads();
+    const bool packed = p.row_stride == W && rb == row_bytes &&
+                        (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+    // one thread per query with packed rows: each warp writes, copies out
+    // and rewrites only its own 32 rows, so the warps need no CTA barrier
+    const bool warp_rows = TPQ == 1 && packed;
+    if (bulk_pending) {  // the previous tile's rows have been read out before they are rewritten
+      bulk_wait_read_all();
+      bulk_pending = false;
+    }
+    if (warp_rows && prev_warp_rows)
+      __syncwarp();
+    else
+      __syncthreads();
+    prev_warp_rows = warp_rows;
     auto stage_row = [&](int l, const float (&v)[F]) {
       if (l >= sc.K) return;
       uint8_t* dst = stage + q * rb + l * F * int(sizeof(OT));
@@ -86,14 +127,31 @@ __global__ void __launch_bounds__(ENC_NT * TPQ) encode_kernel(const __grid_const
     else
       locate_gather_query<F, TT, KP, sizeof(OT) == 2, TPQ>(p, sc, tree, in, q0 + q, q < nq, par,
                                                             nullptr, nullptr, q, ENC_NT, stage_row);
+    if (packed) fence_proxy_async_smem();  // the rows' generic writes, before the bulk copy reads them
+    if (warp_rows) {  // this warp's rows: one bulk copy by its lane 0
+      __syncwarp();
+      const int r0 = threadIdx.x & ~31;
+      const int nr = nq - r0 < 32 ? nq - r0 : 32;
+      if (lane == 0 && nr > 0) {
+        bulk_copy_s2g(reinterpret_cast<uint8_t*>(out + (q0 + r0) * W),
+                      static_cast<uint32_t>(__cvta_generic_to_shared(stage + r0 * rb)),
+                      static_cast<uint32_t>(nr * row_bytes));
+        bulk_pending = true;
+      }
+      continue;
+    }
     __syncthreads();
-    const bool packed = p.row_stride == W && rb == row_bytes &&
-                        (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
-    if (packed) {  // the tile's rows are one contiguous block in global memory
-      const int chunks = nq * row_bytes / 16;
-      uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(out + q0 * W));
-      const uint4* src = reinterpret_cast<const uint4*>(stage);
-      for (int c = threadIdx.x; c < chunks; c += NTH) dst[c] = src[c];
+    if (packed) {
+      // the tile's rows are one contiguous block in global memory: one bulk
+      // asynchronous copy (nq * row_bytes bytes, a multiple of 16; both
+      // addresses 16-byte aligned), issued by thread 0 while the others
+      // start the next tile's walk
+      if (threadIdx.x == 0) {
+        bulk_copy_s2g(reinterpret_cast<uint8_t*>(out + q0 * W),
+                      static_cast<uint32_t>(__cvta_generic_to_shared(stage)),
+                      static_cast<uint32_t>(nq * row_bytes));
+        bulk_pending = true;
+      }
     } else {
       for (int i = threadIdx.x; i < nq * W; i += NTH) {
         const int r = i / W, k = i % W;
@@ -102,6 +160,7 @@ __global__ void __launch_bounds__(ENC_NT * TPQ) encode_kernel(const __grid_const
       }
     }
   }
+  if (bulk_pending) bulk_wait_all();  // the last copy has landed before the CTA's memory is freed
 }
 
 namespace {

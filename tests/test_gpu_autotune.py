@@ -117,3 +117,37 @@ def test_encode_results_independent_of_gather_stages(name, dtypes):
             assert torch.equal(gn, rn) and torch.equal(ga, ra)
             got2, _, _ = A.octa_encode([sc, sc], X, W, counts, feat_dtype=dt)
             assert torch.equal(got2, ref2), setting
+
+
+def test_encode_mixed_row_layouts_in_one_call():
+    """Scenes of 5 and 7 levels in one call with the deeper scene's row
+    stride: its tiles leave through per-warp bulk copies, the shallower
+    scene's (rows shorter than the stride) through the strided copy, and a
+    persistent CTA alternates between the two; the features equal each
+    scene encoded alone, bit for bit, whatever the work order."""
+    from paper_2606_08469_gb300 import api as A
+    from paper_2606_08469_gb300 import autotune as T
+    scenes = []
+    for s, depth in enumerate((4, 6)):
+        R = I.R_DEEP[:depth + 1]
+        tree = A.octree_build(1400 + 2 * s, depth, 0.6, R)
+        tables = I.make_tables(2400 + s, tree.num_texels, 8, 0.3)
+        weights = I.make_mlp(3400 + s, [(depth + 1) * 8, 64, 64, 3])
+        scenes.append(A.Scene(tree, torch.from_numpy(tables).cuda(),
+                              [torch.from_numpy(W).cuda() for W in weights], device="cuda"))
+    counts = [40000, 50000]
+    xs, ws = zip(*[I.uniform_queries(90 + s, n) for s, n in enumerate(counts)])
+    X = torch.from_numpy(np.concatenate(xs)).cuda()
+    Wd = torch.from_numpy(np.concatenate(ws)).cuda()
+    for dt in (torch.bfloat16, torch.float32):
+        T.set_tuning(None)
+        alone = [A.octa_encode(scenes[s], torch.from_numpy(xs[s]).cuda(),
+                               torch.from_numpy(ws[s]).cuda(), feat_dtype=dt)[0]
+                 for s in range(2)]
+        for setting in (None, {"encode_ctas_per_sm": 1}, {"encode_ctas_per_sm": 1, "fwd_order": 1},
+                        {"encode_ctas_per_sm": 2, "fwd_run": 3}):
+            T.set_tuning(setting)
+            feat, _, _ = A.octa_encode(scenes, X, Wd, counts, feat_dtype=dt)
+            assert torch.equal(feat[:counts[0], :40], alone[0]), setting
+            assert not feat[:counts[0], 40:].any()
+            assert torch.equal(feat[counts[0]:], alone[1]), setting
