@@ -19,9 +19,11 @@ namespace octa {
 // Standalone encoding kernel (Eq. 10 single-cell bilinear form + Eq. 11)
 // ---------------------------------------------------------------------------
 // One query per thread (fold, walk, gather; see gather.cuh), its K*F
-// features written into a shared-memory staging row in the output type; the
-// tile's rows then leave as 16-byte stores (a contiguous block when the
-// output rows are packed), so the feature stream is written coalesced.
+// features written into a shared-memory staging row in the output type.
+// When the output rows are packed, the rows leave in bulk asynchronous
+// copies (each warp's 32 rows by its lane 0 at one thread per query, the
+// whole tile by thread 0 at two); otherwise as element stores at the row
+// stride.  Either way the feature stream is written coalesced.
 constexpr int ENC_NT = 128;
 
 // Bulk asynchronous copy of `bytes` (multiple of 16) from shared to global
