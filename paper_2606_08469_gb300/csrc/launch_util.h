@@ -58,8 +58,9 @@ inline int fit_carveout_percent(const void* fn, size_t smem, int per_sm) {
   if (sm_smem <= 0) return 100;
   const size_t need = static_cast<size_t>(per_sm) *
                       (smem + a.sharedSizeBytes + static_cast<size_t>(rsv));
+  // rounded up: the preference covers `need` bytes
   const size_t pct = (need * 100 + static_cast<size_t>(sm_smem) - 1) / static_cast<size_t>(sm_smem);
-  return static_cast<int>(std::min<size_t>(100, pct + 1));  // one percent of slack
+  return static_cast<int>(std::min<size_t>(100, pct));
 }
 
 // Sets the kernel's dynamic shared-memory limit and the largest shared-memory
