@@ -488,7 +488,8 @@ def encode_leg(dev, flush, stream, steps, peaks):
     for _ in range(3):
         fn()
     from paper_2606_08469_gb300 import autotune as T
-    best, rep = T.autotune(fn, {"gather_stages": [1, 2, 3, 4], "l1_carveout": [1, 2]},
+    best, rep = T.autotune(fn, {"gather_stages": [1, 2, 3, 4], "l1_carveout": [1, 2],
+                                "encode_ctas_per_sm": [0, 4]},
                            "gbuffer-encode-1280x720", reps=5)
     for _ in range(3):
         fn()

@@ -19,7 +19,7 @@ int launch_persistent(Kern kernel, size_t smem, const QueryParams& p0, cudaStrea
   if (p0.n_tiles == 0) return OCTA_OK;
   int per_sm = 0;
   int rc = launch_cache().get(reinterpret_cast<const void*>(kernel), smem, threads, 0, &per_sm,
-                              carve_mode(tuning_snapshot()));
+                              carve_mode(tuning_snapshot()), cap);
   if (rc) return rc;
   per_sm = apply_cap(per_sm, cap);
   QueryParams p = p0;

@@ -45,20 +45,27 @@ inline int ctas_from_resources(const void* fn, size_t smem, int threads) {
 // rest of the SM's 256 KB of L1 / shared memory stays L1 cache).
 constexpr int kCarveMaxShared = 1, kCarveFit = 2;
 
-// The carveout preference, in percent of the SM's shared memory, that holds
-// per_sm CTAs of smem dynamic bytes (plus static and reserved bytes); the
-// driver rounds a preference up to the next configuration it supports.
-inline int fit_carveout_percent(const void* fn, size_t smem, int per_sm) {
+// Shared memory one CTA of the kernel takes (smem dynamic bytes plus its
+// static and reserved bytes) and the SM's shared memory: the inputs of the
+// carveout preference below.
+inline void cta_shared_bytes(const void* fn, size_t smem, size_t* cta_bytes, int* sm_smem) {
   cudaFuncAttributes a;
-  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) return 100;
-  int dev = 0, sm_smem = 0, rsv = 0;
+  int dev = 0, rsv = 0;
+  *sm_smem = 0;
+  *cta_bytes = smem;
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) return;
   cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  *cta_bytes = smem + a.sharedSizeBytes + static_cast<size_t>(rsv);
+}
+
+// The carveout preference, in percent of the SM's shared memory, that holds
+// n CTAs of cta_bytes each, rounded up (the preference covers the bytes; the
+// driver rounds a preference up to the next configuration it supports).
+inline int fit_carveout_percent(size_t cta_bytes, int sm_smem, int n) {
   if (sm_smem <= 0) return 100;
-  const size_t need = static_cast<size_t>(per_sm) *
-                      (smem + a.sharedSizeBytes + static_cast<size_t>(rsv));
-  // rounded up: the preference covers `need` bytes
+  const size_t need = static_cast<size_t>(n) * cta_bytes;
   const size_t pct = (need * 100 + static_cast<size_t>(sm_smem) - 1) / static_cast<size_t>(sm_smem);
   return static_cast<int>(std::min<size_t>(100, pct));
 }
@@ -93,11 +100,12 @@ inline int resident_ctas(const void* fn, size_t smem, size_t attr_smem, int thre
 // carveout each kernel was last given: get() applies the requested mode's
 // carveout for that launch when it differs from the kernel's current one
 // (a host-side attribute change; launches of one stream capture keep one
-// mode per kernel).
+// mode per kernel).  cap (> 0): the launch keeps at most that many CTAs per
+// SM resident, and the fitted carveout holds only those.
 class LaunchCache {
  public:
   int get(const void* fn, size_t smem, int threads, int tmem_cols, int* out,
-          int carve = kCarveMaxShared) {
+          int carve = kCarveMaxShared, int cap = 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu_);
@@ -116,11 +124,17 @@ class LaunchCache {
         *out = per_sm;
         return OCTA_OK;  // the largest carveout stays set
       }
-      e_[n_] = Entry{fn, dev, smem, per_sm, fit_carveout_percent(fn, smem, per_sm)};
+      size_t cta_bytes = smem;
+      int sm_smem = 0;
+      cta_shared_bytes(fn, smem, &cta_bytes, &sm_smem);
+      e_[n_] = Entry{fn, dev, smem, per_sm, cta_bytes, sm_smem};
       hit = n_++;
       set_current(fn, dev, 100);
     }
-    const int want = carve == kCarveFit ? e_[hit].fit_pct : 100;
+    const Entry& en = e_[hit];
+    const int resident = cap > 0 ? std::min(en.per_sm, cap) : en.per_sm;
+    const int want =
+        carve == kCarveFit ? fit_carveout_percent(en.cta_bytes, en.sm_smem, resident) : 100;
     if (current(fn, dev) != want) {
       cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, want);
       if (e != cudaSuccess)
@@ -137,7 +151,8 @@ class LaunchCache {
     int dev;
     size_t smem;
     int per_sm;
-    int fit_pct;  // carveout percent that holds per_sm CTAs
+    size_t cta_bytes;  // shared memory of one CTA incl. static and reserved bytes
+    int sm_smem;       // the SM's shared memory (0: unknown, largest carveout)
   };
   struct Carve {
     const void* fn;

@@ -1253,7 +1253,8 @@ int launch_fwd_tpq(const QueryParams& p, const octa_tuning& tu, cudaStream_t str
   const size_t smem = S::OFF_TREE + 8u * static_cast<size_t>(cap);
   int per_sm = 0;
   int rc = launch_cache().get(reinterpret_cast<const void*>(kern), smem, NT * TPQ,
-                              static_cast<int>(S::TMEM_COLS), &per_sm, carve_mode(tu));
+                              static_cast<int>(S::TMEM_COLS), &per_sm, carve_mode(tu),
+                              tu.fwd_ctas_per_sm);
   if (rc) return rc;
   per_sm = apply_cap(per_sm, tu.fwd_ctas_per_sm);
   QueryParams pp = p;

@@ -37,7 +37,8 @@ def test_forward_results_independent_of_knobs():
                     {"fwd_threads_per_query": 2, "fwd_order": 1, "fwd_ctas_per_sm": 3},
                     {"fwd_run": 3}, {"fwd_run": 8, "fwd_ctas_per_sm": 2},
                     {"fwd_run": 64, "fwd_threads_per_query": 2}, {"l1_carveout": 2},
-                    {"l1_carveout": 2, "fwd_threads_per_query": 2}, {"l1_carveout": 1}):
+                    {"l1_carveout": 2, "fwd_threads_per_query": 2}, {"l1_carveout": 1},
+                    {"fwd_threads_per_query": 1}, {"fwd_threads_per_query": 1, "fwd_run": 4}):
         T.set_tuning(setting)
         got, gn, ga = A.octa_query_fwd(sc, X, W, want_nodes=True, want_addr=True)
         torch.testing.assert_close(got, ref, rtol=0, atol=0)
